@@ -1,0 +1,172 @@
+"""FP64 CPU oracle for the SPIIR hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA path
+(``paper_1602_05573_b300``) and neither imports the other.
+
+What it computes (paper, section "GPU accelerated SPIIR method", subsection
+"SPIIR method"): each template is a parallel bank of single-pole complex IIR
+filters ``y_l[k] = a_l y_l[k-1] + b_l x[k-d_l]`` whose outputs are summed into
+the template's SNR series ``z[k] = sum_l y_l[k]``; the peak is the largest
+``|z|`` (first index on ties).  The arithmetic lives in ``spiir_ref.c`` as
+plain double-precision loops; this module only compiles it with gcc and
+marshals numpy arrays.
+
+Every function here is pinned by ``tests/test_oracle_pins.py`` against
+closed forms, brute force and exact rational arithmetic.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "spiir_ref.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libspiir_ref.so")
+_lock = threading.Lock()
+_lib = None
+
+# planted mistakes understood by spiir_ref_filter (mutation tests only)
+MUTATIONS = {
+    "conj_pole": 1,
+    "delay_off_by_one": 2,
+    "drop_gain_imag": 3,
+    "skip_last_filter": 4,
+    "peak_last_on_tie": 5,
+    "swap_re_im_out": 6,
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (-O2, no FMA contraction, OpenMP)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+           "-fPIC", "-shared", "-std=c99", _SRC, "-o", tmp, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            i64 = ctypes.c_int64
+            lib.spiir_ref_filter.argtypes = [i64, i64, P, P, P, P, P, i64, P, P, P,
+                                             ctypes.c_int, ctypes.c_int]
+            lib.spiir_ref_filter.restype = ctypes.c_int
+            lib.spiir_ref_filter_multirate.argtypes = [
+                i64, i64, P, P, P, P, P, ctypes.c_int32, P, P, i64, P, P, P, ctypes.c_int]
+            lib.spiir_ref_filter_multirate.restype = ctypes.c_int
+            lib.spiir_ref_adjoint.argtypes = [i64, i64, P, P, P, P, P, i64, P, P, P, P,
+                                              ctypes.c_int]
+            lib.spiir_ref_adjoint.restype = ctypes.c_int
+            lib.spiir_ref_max_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def max_threads() -> int:
+    return int(_load().spiir_ref_max_threads())
+
+
+def _ptr(arr):
+    return None if arr is None else arr.ctypes.data_as(ctypes.c_void_p)
+
+
+def _as_reim(v) -> np.ndarray:
+    """complex array -> contiguous float64 [N][2], promoted exactly."""
+    v = np.asarray(v)
+    out = np.empty((v.shape[0], 2), np.float64)
+    out[:, 0] = v.real
+    out[:, 1] = v.imag
+    return out
+
+
+def _bank_arrays(off, a, b, d):
+    off = np.ascontiguousarray(off, np.int64)
+    return (off, _as_reim(a), _as_reim(b), np.ascontiguousarray(d, np.int32))
+
+
+def filter_bank(off, a, b, d, x, *, want_z=True, n_threads=None, mutation=0):
+    """Summed single-rate IIR bank on every detector stream.
+
+    off: int64 [T+1] CSR offsets; a, b: complex [Ltot]; d: int [Ltot];
+    x: real [D][n].  Returns (z, peak_abs2, peak_idx): z complex128
+    [D][T][n] (None unless want_z), peak_abs2 float64 [D][T] (largest |z|^2),
+    peak_idx int64 [D][T] (first index attaining it).
+    """
+    lib = _load()
+    off, a2, b2, d = _bank_arrays(off, a, b, d)
+    x = np.ascontiguousarray(np.atleast_2d(x), np.float64)
+    D, n = x.shape
+    T = off.shape[0] - 1
+    z = np.zeros((D, T, n, 2), np.float64) if want_z else None
+    pa = np.zeros((D, T), np.float64)
+    pi = np.zeros((D, T), np.int64)
+    nt = n_threads or max_threads()
+    rc = lib.spiir_ref_filter(T, D, _ptr(off), _ptr(a2), _ptr(b2), _ptr(d), _ptr(x), n,
+                              _ptr(z), _ptr(pa), _ptr(pi), nt, int(mutation))
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    zc = None if z is None else (z[..., 0] + 1j * z[..., 1])
+    return zc, pa, pi
+
+
+def filter_multirate(off, a, b, d, band_of, decim, x, *, want_z=True, n_threads=None):
+    """Multirate bank: each band filtered at its own rate (plain subsampling
+    by decim[band]), linearly interpolated back to the top rate, summed."""
+    lib = _load()
+    off, a2, b2, d = _bank_arrays(off, a, b, d)
+    band_of = np.ascontiguousarray(band_of, np.int32)
+    decim = np.ascontiguousarray(decim, np.int32)
+    x = np.ascontiguousarray(np.atleast_2d(x), np.float64)
+    D, n = x.shape
+    T = off.shape[0] - 1
+    z = np.zeros((D, T, n, 2), np.float64) if want_z else None
+    pa = np.zeros((D, T), np.float64)
+    pi = np.zeros((D, T), np.int64)
+    nt = n_threads or max_threads()
+    rc = lib.spiir_ref_filter_multirate(T, D, _ptr(off), _ptr(a2), _ptr(b2), _ptr(d),
+                                        _ptr(band_of), int(decim.shape[0]), _ptr(decim),
+                                        _ptr(x), n, _ptr(z), _ptr(pa), _ptr(pi), nt)
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    zc = None if z is None else (z[..., 0] + 1j * z[..., 1])
+    return zc, pa, pi
+
+
+def adjoint(off, a, b, d, x, gz, *, want_gx=True, n_threads=None):
+    """Vector-Jacobian product of filter_bank: given g_z (PyTorch convention,
+    dL/dRe z + i dL/dIm z, complex [D][T][n]) return (g_a, g_b, g_x):
+    complex128 [Ltot], complex128 [Ltot], float64 [D][n] (or None)."""
+    lib = _load()
+    off, a2, b2, d = _bank_arrays(off, a, b, d)
+    x = np.ascontiguousarray(np.atleast_2d(x), np.float64)
+    D, n = x.shape
+    T = off.shape[0] - 1
+    gz = np.asarray(gz)
+    g2 = np.empty(gz.shape + (2,), np.float64)
+    g2[..., 0] = gz.real
+    g2[..., 1] = gz.imag
+    ltot = int(off[-1])
+    ga = np.zeros((ltot, 2), np.float64)
+    gb = np.zeros((ltot, 2), np.float64)
+    gx = np.zeros((D, n), np.float64) if want_gx else None
+    nt = n_threads or max_threads()
+    rc = lib.spiir_ref_adjoint(T, D, _ptr(off), _ptr(a2), _ptr(b2), _ptr(d), _ptr(x), n,
+                               _ptr(g2), _ptr(ga), _ptr(gb), _ptr(gx), nt)
+    if rc != 0:
+        raise MemoryError("oracle allocation failed")
+    return ga[:, 0] + 1j * ga[:, 1], gb[:, 0] + 1j * gb[:, 1], gx

@@ -1,0 +1,310 @@
+"""Pins of the FP64 oracle to facts that do not come from the oracle itself.
+
+The paper prints no worked example and no coefficients, so every pin comes
+from the mathematics of the recurrence in the SPIIR method (section "GPU
+accelerated SPIIR method", subsection "SPIIR method"):
+  y_l[k] = a_l y_l[k-1] + b_l x[k-d_l],   z[k] = sum_l y_l[k]
+Pins: a hand-worked example (tests/golden), the impulse and step responses in
+closed form, linearity and time invariance, brute-force direct convolution
+with the summed impulse response, exact rational arithmetic, the stationary
+noise variance, brute-force argmax, the multirate definition against
+numpy.interp, and the adjoint against central differences and the
+transpose identity.  The mutation tests at the end plant mistakes in the
+oracle and check that some pin fails for each.
+"""
+import json
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from spiir_inputs import make_bank, make_multirate_bank, make_strain
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def one_filter(a, b, d):
+    return (np.array([0, 1]), np.array([a], np.complex128), np.array([b], np.complex128),
+            np.array([d], np.int32))
+
+
+def rel_err(got, want):
+    scale = max(np.max(np.abs(want)), 1e-300)
+    return float(np.max(np.abs(np.asarray(got) - np.asarray(want))) / scale)
+
+
+# ----------------------------------------------------------------- pins ---
+
+def pin_hand_example(mutation=0):
+    g = json.load(open(os.path.join(HERE, "golden", "hand_example.json")))
+    a = np.array([complex(*v) for v in g["a"]])
+    b = np.array([complex(*v) for v in g["b"]])
+    z, pa, pi = oracle.filter_bank(g["off"], a, b, g["d"], [g["x"]], n_threads=1,
+                                   mutation=mutation)
+    want = np.array([complex(*v) for v in g["z"]])
+    return (np.array_equal(z[0, 0], want) and pa[0, 0] == g["peak_abs2"]
+            and pi[0, 0] == g["peak_idx"])
+
+
+def pin_impulse(mutation=0):
+    """Impulse at k0: z[k] = b a^(k-k0-d) for k >= k0+d, else 0."""
+    ok = True
+    for a, b, d in [(0.97 * np.exp(0.7j), 0.3 - 0.8j, 5), (-0.5 + 0.6j, 1.25j, 0),
+                    (0.999 * np.exp(2.9j), -0.01 + 0.02j, 17)]:
+        n, k0 = 300, 11
+        x = np.zeros((1, n))
+        x[0, k0] = 1.0
+        z, _, _ = oracle.filter_bank(*one_filter(a, b, d), x, n_threads=1, mutation=mutation)
+        k = np.arange(n)
+        want = np.where(k >= k0 + d, b * np.power(a, np.maximum(k - k0 - d, 0)), 0)
+        ok &= rel_err(z[0, 0], want) < 1e-12
+    return ok
+
+
+def pin_step(mutation=0):
+    """x = 1 from k = 0: y[k] = b (1 - a^(k-d+1)) / (1 - a) for k >= d."""
+    a, b, d, n = 0.995 * np.exp(0.05j), 0.4 + 0.1j, 9, 2000
+    x = np.ones((1, n))
+    z, _, _ = oracle.filter_bank(*one_filter(a, b, d), x, n_threads=1, mutation=mutation)
+    k = np.arange(n)
+    want = np.where(k >= d, b * (1 - np.power(a, np.maximum(k - d + 1, 0))) / (1 - a), 0)
+    return rel_err(z[0, 0], want) < 1e-11
+
+
+def pin_direct_convolution(mutation=0):
+    """Tiny banks: z = x * h with h[m] = sum_l b_l a_l^(m-d_l) [m >= d_l],
+    truncated at n (exact for the first n outputs)."""
+    ok = True
+    rng = np.random.default_rng(7)
+    for L, n in [(1, 64), (3, 200), (4, 256)]:
+        a = rng.uniform(0.5, 0.99, L) * np.exp(1j * rng.uniform(0, np.pi, L))
+        b = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+        d = rng.integers(0, 20, L).astype(np.int32)
+        x = rng.standard_normal(n)
+        m = np.arange(n)
+        h = np.zeros(n, np.complex128)
+        for l in range(L):
+            h += np.where(m >= d[l], b[l] * np.power(a[l], np.maximum(m - d[l], 0)), 0)
+        want = np.convolve(x, h)[:n]
+        z, _, _ = oracle.filter_bank([0, L], a, b, d, x[None], n_threads=1,
+                                     mutation=mutation)
+        ok &= rel_err(z[0, 0], want) < 1e-12
+    return ok
+
+
+def pin_exact_rational(mutation=0):
+    """Exact recurrence in Fractions on binary-exact inputs (<= 64 samples)."""
+    bank = make_bank(1, 3, (0.9, 0.99), 6, seed=11)
+    x = make_strain(1, 64, seed=12)
+    A = [(Fraction(float(v.real)), Fraction(float(v.imag))) for v in bank.a]
+    B = [(Fraction(float(v.real)), Fraction(float(v.imag))) for v in bank.b]
+    X = [Fraction(float(v)) for v in x[0]]
+    n = len(X)
+    zr = [Fraction(0)] * n
+    zi = [Fraction(0)] * n
+    for l in range(3):
+        yr, yi = Fraction(0), Fraction(0)
+        (ar, ai), (br, bi), dl = A[l], B[l], int(bank.d[l])
+        for k in range(n):
+            xk = X[k - dl] if k >= dl else Fraction(0)
+            yr, yi = ar * yr - ai * yi + br * xk, ar * yi + ai * yr + bi * xk
+            zr[k] += yr
+            zi[k] += yi
+    want = np.array([float(r) + 1j * float(i) for r, i in zip(zr, zi)])
+    z, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x, n_threads=1,
+                                 mutation=mutation)
+    return rel_err(z[0, 0], want) < 1e-14
+
+
+def pin_time_shift(mutation=0):
+    """Prepending s zeros shifts z by s samples, bit for bit."""
+    bank = make_bank(2, 5, (0.9, 0.999), 30, seed=13)
+    x = make_strain(1, 500, seed=14)
+    s = 37
+    xs = np.concatenate([np.zeros((1, s), np.float32), x], axis=1)
+    z, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x, mutation=mutation)
+    zs, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, xs, mutation=mutation)
+    return np.array_equal(zs[:, :, s:], z) and not np.any(zs[:, :, :s])
+
+
+def pin_linearity(mutation=0):
+    """z(2 x1 - 3 x2) = 2 z(x1) - 3 z(x2) (integer inputs, so the combined
+    input is exact); z with gains 2b is exactly 2 z."""
+    bank = make_bank(3, 6, (0.9, 0.999), 40, seed=15)
+    rng = np.random.default_rng(16)
+    x1 = rng.integers(-8, 9, (1, 400)).astype(np.float64)
+    x2 = rng.integers(-8, 9, (1, 400)).astype(np.float64)
+    f = lambda x, b=bank.b: oracle.filter_bank(bank.off, bank.a, b, bank.d, x,
+                                                mutation=mutation)[0]
+    ok = rel_err(f(2 * x1 - 3 * x2), 2 * f(x1) - 3 * f(x2)) < 1e-12
+    ok &= np.array_equal(f(x1, 2 * bank.b.astype(np.complex128)), 2 * f(x1))
+    return ok
+
+
+def pin_superposition(mutation=0):
+    """A template's z is the sum of its filters run as one-filter templates."""
+    bank = make_bank(1, 7, (0.9, 0.999), 50, seed=17)
+    x = make_strain(1, 300, seed=18)
+    z, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x, mutation=mutation)
+    L = bank.n_filters
+    zs, _, _ = oracle.filter_bank(np.arange(L + 1), bank.a, bank.b, bank.d, x,
+                                  mutation=mutation)
+    return rel_err(z[0, 0], zs[0].sum(axis=0)) < 1e-12
+
+
+def pin_peak_bruteforce(mutation=0):
+    """Peak = first argmax of |z|^2, including exact ties.  With a = 0 each
+    filter is a pure delayed gain, z[k] = sum_l b_l x[k-d_l], so repeated
+    input values give exactly tied peaks."""
+    ok = True
+    x = np.zeros((1, 64))
+    x[0, [5, 20, 41]] = 3.0            # three equal maxima
+    x[0, [9, 30]] = -2.0
+    z, pa, pi = oracle.filter_bank([0, 1], [0j], [0.5 + 0.5j], [4], x, mutation=mutation)
+    p = z[0, 0].real ** 2 + z[0, 0].imag ** 2
+    ok &= pi[0, 0] == int(np.argmax(p)) == 9 and pa[0, 0] == p.max()
+    bank = make_bank(4, 8, (0.9, 0.999), 30, seed=19)
+    xs = make_strain(1, 700, seed=20)
+    z, pa, pi = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, xs, mutation=mutation)
+    p = z[0].real ** 2 + z[0].imag ** 2
+    ok &= np.array_equal(pi[0], np.argmax(p, axis=1))
+    ok &= np.array_equal(pa[0], p.max(axis=1))
+    return ok
+
+
+PINS = [pin_hand_example, pin_impulse, pin_step, pin_direct_convolution,
+        pin_exact_rational, pin_time_shift, pin_linearity, pin_superposition,
+        pin_peak_bruteforce]
+
+
+@pytest.mark.parametrize("pin", PINS, ids=lambda p: p.__name__)
+def test_pin(pin):
+    assert pin()
+
+
+@pytest.mark.parametrize("name", sorted(oracle.MUTATIONS))
+def test_planted_mistake_is_caught(name):
+    """Each planted slip in the oracle makes at least one pin fail."""
+    m = oracle.MUTATIONS[name]
+    failed = [p.__name__ for p in PINS if not p(mutation=m)]
+    assert failed, f"mutation {name} slipped past every pin"
+
+
+# ------------------------------------------------------- noise variance ---
+
+def test_noise_variance_closed_form():
+    """For unit white noise the stationary E|z|^2 is
+    sum_{l,m} b_l conj(b_m) a_l^(D-d_l) conj(a_m)^(D-d_m) / (1 - a_l conj(a_m)),
+    D = max(d_l, d_m).  Checked statistically over many templates."""
+    T, L, n, burn = 64, 4, 40000, 2000
+    bank = make_bank(T, L, (0.5, 0.9), 12, seed=21)
+    x = make_strain(1, n, seed=22)
+    z, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
+    a = bank.a.astype(np.complex128)
+    b = bank.b.astype(np.complex128)
+    for t in range(T):
+        sl = slice(bank.off[t], bank.off[t + 1])
+        at, bt, dt = a[sl], b[sl], bank.d[sl].astype(np.int64)
+        D = np.maximum(dt[:, None], dt[None, :])
+        num = bt[:, None] * np.conj(bt)[None, :] * at[:, None] ** (D - dt[:, None]) \
+            * np.conj(at)[None, :] ** (D - dt[None, :])
+        var = float(np.real(np.sum(num / (1 - at[:, None] * np.conj(at)[None, :]))))
+        est = float(np.mean(np.abs(z[0, t, burn:]) ** 2))
+        # correlation time <= 1/(1-0.9) = 10 samples; allow 6 standard errors
+        se = var * np.sqrt(2 * 20.0 / (n - burn))
+        assert abs(est - var) < 6 * se, (t, est, var)
+
+
+# ------------------------------------------------------------ multirate ---
+
+def test_multirate_single_band_is_plain_filter():
+    bank = make_multirate_bank(3, (6,), (1,), (0.9, 0.999), 20, seed=23)
+    x = make_strain(1, 500, seed=24)
+    z1, p1, i1 = oracle.filter_multirate(bank.off, bank.a, bank.b, bank.d, bank.band_of,
+                                         bank.decim, x)
+    z0, p0, i0 = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
+    assert np.array_equal(z1, z0) and np.array_equal(i1, i0)
+
+
+@pytest.mark.parametrize("n", [512, 509])
+def test_multirate_matches_subsample_and_interp(n):
+    """Each band = plain filter on x[::R], brought to the top rate by
+    numpy.interp (which holds the last value past the end)."""
+    bank = make_multirate_bank(2, (3, 4, 5), (1, 4, 16), (0.9, 0.999), 10, seed=25)
+    x = make_strain(1, n, seed=26)
+    z, pa, pi = oracle.filter_multirate(bank.off, bank.a, bank.b, bank.d, bank.band_of,
+                                        bank.decim, x)
+    m = np.arange(n)
+    for t in range(2):
+        want = np.zeros(n, np.complex128)
+        for j, R in enumerate(bank.decim):
+            sel = [l for l in range(bank.off[t], bank.off[t + 1]) if bank.band_of[l] == j]
+            xb = x[:, ::R]
+            zb, _, _ = oracle.filter_bank([0, len(sel)], bank.a[sel], bank.b[sel],
+                                          bank.d[sel], xb)
+            zb = zb[0, 0]
+            nb = np.arange(zb.shape[0])
+            want += np.interp(m / R, nb, zb.real) + 1j * np.interp(m / R, nb, zb.imag)
+        assert rel_err(z[0, t], want) < 1e-12
+        p = np.abs(z[0, t]) ** 2
+        assert pi[0, t] == np.argmax(p)
+
+
+# -------------------------------------------------------------- adjoint ---
+
+def _loss(bank_off, a, b, d, x, target):
+    z, _, _ = oracle.filter_bank(bank_off, a, b, d, x)
+    return float(np.sum(np.abs(z - target) ** 2)), z
+
+
+def test_adjoint_central_differences():
+    """g_a, g_b, g_x of L = sum |z - z_t|^2 against central differences
+    (h = 1e-6, FP64) on sampled coordinates."""
+    bank = make_bank(3, 5, (0.9, 0.995), 25, seed=27, n_det=2)
+    x = make_strain(2, 300, seed=28).astype(np.float64)
+    a = bank.a.astype(np.complex128)
+    b = bank.b.astype(np.complex128)
+    rng = np.random.default_rng(29)
+    target = 0.05 * (rng.standard_normal((2, 3, 300)) + 1j * rng.standard_normal((2, 3, 300)))
+    L0, z = _loss(bank.off, a, b, bank.d, x, target)
+    ga, gb, gx = oracle.adjoint(bank.off, a, b, bank.d, x, 2 * (z - target))
+    h = 1e-6
+    for l in rng.choice(bank.n_filters, 6, replace=False):
+        for unit, g in [(1.0, ga[l].real), (1j, ga[l].imag)]:
+            ap, am = a.copy(), a.copy()
+            ap[l] += unit * h
+            am[l] -= unit * h
+            fd = (_loss(bank.off, ap, b, bank.d, x, target)[0]
+                  - _loss(bank.off, am, b, bank.d, x, target)[0]) / (2 * h)
+            assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (l, unit, fd, g)
+        for unit, g in [(1.0, gb[l].real), (1j, gb[l].imag)]:
+            bp, bm = b.copy(), b.copy()
+            bp[l] += unit * h
+            bm[l] -= unit * h
+            fd = (_loss(bank.off, a, bp, bank.d, x, target)[0]
+                  - _loss(bank.off, a, bm, bank.d, x, target)[0]) / (2 * h)
+            assert abs(fd - g) <= 1e-6 * max(1.0, abs(g)), (l, unit, fd, g)
+    for det, m in [(0, 0), (0, 150), (1, 299), (1, 17)]:
+        xp, xm = x.copy(), x.copy()
+        xp[det, m] += h
+        xm[det, m] -= h
+        fd = (_loss(bank.off, a, b, bank.d, xp, target)[0]
+              - _loss(bank.off, a, b, bank.d, xm, target)[0]) / (2 * h)
+        assert abs(fd - gx[det, m]) <= 1e-6 * max(1.0, abs(gx[det, m]))
+
+
+def test_adjoint_transpose_identity():
+    """x -> z is linear (z = A x), so for any G and x':
+    Re <G, A x'> = <x', g_x>, where g_x is the adjoint's input gradient."""
+    bank = make_bank(4, 6, (0.9, 0.999), 40, seed=30, n_det=2)
+    x = make_strain(2, 400, seed=31)
+    rng = np.random.default_rng(32)
+    G = rng.standard_normal((2, 4, 400)) + 1j * rng.standard_normal((2, 4, 400))
+    xp = rng.standard_normal((2, 400))
+    _, _, gx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, G)
+    Axp, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, xp)
+    lhs = float(np.real(np.sum(np.conj(G) * Axp)))
+    rhs = float(np.sum(xp * gx))
+    assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), 1.0)
