@@ -1,0 +1,240 @@
+/*
+ * spiir.h -- C ABI of the SPIIR filter-bank library for NVIDIA B300 (sm_103a).
+ *
+ * The operation (paper, section "GPU accelerated SPIIR method", subsection
+ * "SPIIR method"): every template of a bank is approximated by a parallel
+ * bank of single-pole complex IIR filters,
+ *
+ *     y_l[k] = a_l * y_l[k-1] + b_l * x[k - d_l],      z[k] = sum_l y_l[k],
+ *
+ * run on whitened detector strain x; z is the template's complex SNR series
+ * and its peak (largest |z|) flags a candidate signal.  The per-template
+ * parameter triples (a_l, b_l, d_l) are the "parameter array" of subsection
+ * "Optimized GPU implementation of SPIIR", which this library repacks into an
+ * aligned, coalesced device layout when a plan is created.
+ *
+ * Conventions shared by every call:
+ *  - Complex numbers are interleaved (re, im) float32 pairs (complex64).
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; the
+ *    library never frees them.  Pointers without the suffix are host memory,
+ *    read (or written) only during the call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued asynchronously on it; a call returning
+ *    SPIIR_OK means the work was enqueued, not that it finished.
+ *  - No call aborts, exits or throws.  Every failure returns a status and
+ *    records a one-line reason readable with spiir_last_error_detail()
+ *    (per host thread).
+ *  - A plan is not thread-safe; distinct plans may be used from distinct host
+ *    threads.  All calls on one plan must use streams ordered with each other
+ *    (the plan owns the filter state and the strain history).
+ *  - There is no CPU fallback: without a B300-class device the compute calls
+ *    return SPIIR_EUNSUPPORTED or SPIIR_ECUDA.
+ */
+#ifndef SPIIR_H
+#define SPIIR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum spiir_status {
+    SPIIR_OK = 0,
+    SPIIR_EINVAL = 1,       /* bad argument: null pointer, size, |a| >= 1, d < 0 ... */
+    SPIIR_ENOMEM = 2,       /* host or device allocation failed                     */
+    SPIIR_ECUDA = 3,        /* a CUDA runtime call failed                           */
+    SPIIR_ETIMEOUT = 4,     /* a bounded device-side wait gave up (error word set)  */
+    SPIIR_EUNSUPPORTED = 5  /* device is not sm_103, or a size beyond a kernel limit */
+} spiir_status;
+
+/* How the recurrence is evaluated (see spiir_options.precision). */
+typedef enum spiir_precision {
+    SPIIR_PREC_PLAIN = 0,       /* complex FP32 state, one pass over time          */
+    SPIIR_PREC_COMPENSATED = 1, /* float-float (two-sum/two-prod) state            */
+    SPIIR_PREC_CHUNKED_FP64 = 2,/* time-chunked scan, FP64 carry of the state      */
+    SPIIR_PREC_CHUNKED_TC = 3   /* chunked scan, split-BF16 tensor-core projection */
+} spiir_precision;
+
+/*
+ * A template bank in CSR form.  Template t owns filters
+ * filter_off[t] .. filter_off[t+1]-1.  All arrays are host memory, read only
+ * during spiir_plan_create; the plan copies what it needs.
+ *   n_templates      >= 1
+ *   n_detectors      >= 1; every template is run on every detector stream
+ *   filter_off       [n_templates + 1], filter_off[0] = 0, non-decreasing
+ *   a_reim, b_reim   [2 * Ltot] complex64 pole and gain; |a_l| < 1 required
+ *   delay            [Ltot] delay d_l >= 0, in samples of the filter's band
+ *   n_bands          0 (or 1 with band_decim[0] = 1): single-rate bank.
+ *                    > 1: multirate bank (see spiir_filter)
+ *   band_of_filter   [Ltot] band index of each filter, or NULL if n_bands <= 1
+ *   band_decim       [n_bands] decimation factor of each band relative to the
+ *                    top rate (1 = top rate), or NULL if n_bands <= 1
+ */
+typedef struct spiir_bank_desc {
+    int64_t n_templates;
+    int32_t n_detectors;
+    int32_t n_bands;
+    const int64_t *filter_off;
+    const float *a_reim;
+    const float *b_reim;
+    const int32_t *delay;
+    const int32_t *band_of_filter;
+    const int32_t *band_decim;
+} spiir_bank_desc;
+
+/* Plan options.  Fill with spiir_options_default() and override fields. */
+typedef struct spiir_options {
+    int32_t precision;      /* spiir_precision                                   */
+    int32_t chunk_len;      /* chunked forms: samples per chunk (default 256)     */
+    int32_t block_len;      /* samples per staged strain block; 0 = default       */
+    int32_t warps_per_cta;  /* templates per CTA; 0 = chosen from the bank size   */
+    int32_t ring_copies;    /* bank-skewed copies of the strain ring: 1, 2 or 4;  */
+                            /* 0 = default                                        */
+    int32_t device;         /* CUDA device ordinal; -1 = host-only plan (layout    */
+                            /* and statistics, no device memory, no compute)       */
+    int32_t autotune;       /* nonzero: time candidate block/copy settings on the  */
+                            /* first spiir_filter call and keep the fastest        */
+    int32_t reserved;
+} spiir_options;
+
+/* Plan statistics (spiir_plan_get_info). */
+typedef struct spiir_plan_info {
+    int64_t n_templates;
+    int64_t n_filters;          /* Ltot                                          */
+    int64_t n_slots;            /* filter slots incl. padding (per detector)      */
+    int64_t n_units;            /* CTA work units per spiir_filter launch         */
+    int32_t n_detectors;
+    int32_t warps_per_cta;
+    int32_t block_len;
+    int32_t ring_copies;
+    int32_t history_len;        /* strain samples kept between calls (>= max d)   */
+    int32_t smem_bytes;         /* dynamic shared memory per CTA                  */
+    int32_t max_filters_per_lane;
+    int32_t precision;
+    double bank_conflict_ratio; /* mean shared-memory wavefronts per strain load  */
+} spiir_plan_info;
+
+typedef struct spiir_plan spiir_plan;
+
+/* Fill *opt with defaults (plain precision, device 0). */
+void spiir_options_default(spiir_options *opt);
+
+/*
+ * Validate the bank, sort templates by filter count, pack the parameter
+ * array, and (device >= 0) allocate the plan's device state on that device.
+ * Errors: EINVAL (bad bank or options), ENOMEM, ECUDA, EUNSUPPORTED (device
+ * is not compute capability 10.3, or a template is beyond the kernels'
+ * limits).  On error *out is set to NULL.
+ */
+spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options *opt,
+                               spiir_plan **out);
+
+/* Free everything the plan owns (waits for its device work).  NULL is OK. */
+spiir_status spiir_plan_destroy(spiir_plan *plan);
+
+/* Statistics of the plan's layout.  Works for host-only plans. */
+spiir_status spiir_plan_get_info(const spiir_plan *plan, spiir_plan_info *info);
+
+/*
+ * Slot map of a plan, for inspection: slot_filter[s] is the bank filter index
+ * packed in slot s, or -1 for padding; slot_template[s] the template it
+ * serves (-1 for an empty warp).  Both arrays are host memory of
+ * info.n_slots entries (for multirate banks: the slots of every band, band
+ * after band).
+ */
+spiir_status spiir_plan_get_slots(const spiir_plan *plan, int64_t *slot_filter,
+                                  int64_t *slot_template);
+
+/* Zero the filter state, the strain history, the running peaks and the
+ * sample counter (enqueued on `stream`). */
+spiir_status spiir_reset(spiir_plan *plan, void *stream);
+
+/*
+ * Filter the next n samples of every detector stream.
+ *   x_dev  [n_detectors][n] float32, row stride n (detector-major)
+ *   n      >= 0 samples (top rate for multirate banks)
+ *   z_dev  [n_detectors][n_templates][n] complex64 output in the bank's
+ *          template order, or NULL to skip storing z (the running peak is
+ *          still updated).
+ * Consecutive calls continue one stream: the result equals one call on the
+ * concatenated samples (the plan keeps each filter's state and the last
+ * history_len samples of strain).  Multirate banks: band j sees
+ * x[R_j * k] (R_j = band_decim[j]) counted from the stream start, and its
+ * summed output is linearly interpolated to the top rate; within one call
+ * the samples after the last band sample use that sample (hold).  For
+ * multirate banks every call's n must be a multiple of the largest R_j
+ * except the last one.
+ * Errors: EINVAL, ENOMEM (workspace growth), ECUDA.
+ */
+spiir_status spiir_filter(spiir_plan *plan, const float *x_dev, int64_t n, float *z_dev,
+                          void *stream);
+
+/*
+ * Running peak of every (detector, template) since the last reset:
+ *   peak_abs_dev [n_detectors][n_templates] float32  max_k |z[k]|
+ *   peak_idx_dev [n_detectors][n_templates] int64    its absolute sample index
+ *                                                    (top rate); ties keep the
+ *                                                    earliest; -1 if no sample
+ * |z|^2 is evaluated as re*re + im*im in float32 without fused multiply-add
+ * and peak_abs is its correctly rounded square root.
+ */
+spiir_status spiir_peak(spiir_plan *plan, float *peak_abs_dev, int64_t *peak_idx_dev,
+                        void *stream);
+
+/*
+ * Vector-Jacobian product of one spiir_filter call made from zero state on
+ * x_dev (single-rate banks).  grad_z_dev [n_detectors][n_templates][n]
+ * complex64 holds g_z = dL/dRe z + i dL/dIm z (the PyTorch convention);
+ * outputs use the same convention and are OVERWRITTEN:
+ *   grad_a_dev, grad_b_dev  [Ltot] complex64 (summed over detectors)
+ *   grad_x_dev              [n_detectors][n] float32, or NULL
+ * The forward is recomputed from state checkpoints kept in plan workspace.
+ * Does not touch the plan's streaming state.
+ * Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED (multirate bank).
+ */
+spiir_status spiir_filter_backward(spiir_plan *plan, const float *x_dev, int64_t n,
+                                   const float *grad_z_dev, float *grad_a_dev,
+                                   float *grad_b_dev, float *grad_x_dev, void *stream);
+
+/*
+ * Streaming state, for checkpoint and resume.  Synchronous (waits for the
+ * plan's device work).  Host buffers:
+ *   state   [n_detectors][Ltot] complex64 filter outputs y_l at the last
+ *           processed sample (multirate: at the last sample of its band)
+ *   history [n_detectors][history_len] float32 last strain samples, oldest
+ *           first (zeros before the stream start; single-rate banks)
+ *   samples total samples processed since the last reset
+ * Either array pointer may be NULL to skip it.
+ */
+spiir_status spiir_state_get(spiir_plan *plan, float *state, float *history,
+                             int64_t *samples);
+spiir_status spiir_state_set(spiir_plan *plan, const float *state, const float *history,
+                             int64_t samples);
+
+/*
+ * Wait for the plan's work on `stream` and read its device error word.
+ * Returns ETIMEOUT if a bounded device wait gave up since the last reset.
+ */
+spiir_status spiir_check(spiir_plan *plan, void *stream);
+
+/*
+ * Self-test of the bounded-wait path: launches one CTA that waits on an
+ * mbarrier nothing completes, for at most limit_ns nanoseconds, then records
+ * the timeout in the plan's error word (so spiir_check returns ETIMEOUT).
+ * No kernel traps or hangs.
+ */
+spiir_status spiir_selftest_bounded_wait(spiir_plan *plan, uint64_t limit_ns, void *stream);
+
+/* Static description of a status code. */
+const char *spiir_status_str(spiir_status status);
+
+/* One-line reason for the last failure on this host thread ("" if none). */
+const char *spiir_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPIIR_H */

@@ -1,0 +1,495 @@
+// Plain FP32 SPIIR filter kernel for sm_103a.
+//
+// Computes, for every (detector, template) work item, the summed single-pole
+// IIR bank of the SPIIR method (section "GPU accelerated SPIIR method",
+// subsection "SPIIR method"):
+//     y_l[k] = a_l y_l[k-1] + b_l x[k-d_l],   z[k] = sum_l y_l[k]
+// stores z (optional) and keeps the running peak max |z|^2 with its first
+// index.
+//
+// Mapping (subsection "Optimized GPU implementation of SPIIR" describes the
+// prior-art Maxwell version; this is its sm_103a redesign):
+//  * strain: one shared-memory ring per CTA holds the last Dh samples (>= the
+//    largest delay) plus the current and the next block of Tb samples; blocks
+//    arrive by 1-D TMA bulk copies (cp.async.bulk) signalled on mbarriers,
+//    double buffered.  This replaces the read-only-cache reuse of the paper.
+//    The ring exists in C copies whose bank offsets differ, and the layout
+//    places filters so the 32 lanes of a round read 32 different banks;
+//  * state in registers: lane i of warp w keeps the complex outputs of its F
+//    filters across the whole call, as the paper keeps each filter's output
+//    in a register;
+//  * the recurrence runs two filters per packed FP32x2 instruction
+//    (fma/mul/add .f32x2), 8 packed operations per filter pair and sample;
+//  * the sum over filters: each lane first adds its own filters, then the
+//    warp sums across lanes with a transpose-reduce over 8 samples (the
+//    paper's shuffle sum, with explicit __shfl_*_sync since sm_70 warps are
+//    not implicitly synchronous).  Odd lanes hold their filters in (im, re)
+//    order, so the first exchange level needs no lane-dependent select;
+//  * no atomics: each warp owns one (detector, template) and writes its z
+//    and its peak directly (the paper's cross-warp atomics are not needed).
+#include "spiir_kernels.h"
+#include "spiir_layout.h"
+
+#include <cstdint>
+
+namespace spiir {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// ---- packed FP32x2 arithmetic (two filters per instruction) -------------
+__device__ __forceinline__ uint64_t pk(float lo, float hi)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk(uint64_t v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
+{
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// ---- mbarrier + TMA bulk copy --------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p)
+{
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
+                                         uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
+        "[%3];" ::"r"(dst),
+        "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns()
+{
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait for the phase with the given parity; give up after limit_ns.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t start = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_ns() - start > limit_ns) return false;
+    }
+    return true;
+}
+
+// Bytes one strain block brings into the ring (every copy, plus the mirror
+// of slot 0 placed after the ring so windows never wrap).
+__device__ __forceinline__ uint32_t block_bytes(const K1Args &A, int64_t eblk)
+{
+    const uint32_t one = (uint32_t)A.Tb * 4u * (uint32_t)A.C;
+    return (eblk % A.S) == 0 ? 2u * one : one;
+}
+
+// Issue the copies of strain block eblk (xe samples [eblk*Tb, (eblk+1)*Tb)).
+__device__ __forceinline__ void issue_block(const K1Args &A, const float *xrow, float *ring,
+                                            int64_t eblk, uint32_t bar)
+{
+    const int slot = (int)(eblk % A.S);
+    const float *src = xrow + eblk * A.Tb;
+    const uint32_t bytes = (uint32_t)A.Tb * 4u;
+    for (int c = 0; c < A.C; ++c) {
+        float *dst = ring + (int64_t)c * A.CS + (int64_t)slot * A.Tb;
+        bulk_g2s(smem_addr(dst), src, bytes, bar);
+        if (slot == 0) bulk_g2s(smem_addr(dst + A.R), src, bytes, bar);
+    }
+}
+
+// ---- cross-lane sum of 8 samples, store, running peak ---------------------
+// zr/zi: this lane's partial sums (its filters) for 8 consecutive samples.
+// Even lanes hold (re, im), odd lanes (im, re).  After the exchange, lane i
+// (and lane i^16) holds component (i & 1) of sample s(i) summed over the warp.
+__device__ __forceinline__ void warp_sum_store_peak(const float (&zr)[kTS],
+                                                    const float (&zi)[kTS], int lane,
+                                                    int kbase, int valid, float *zrow,
+                                                    float &best, int &bidx)
+{
+    float v[kTS];
+#pragma unroll
+    for (int j = 0; j < kTS; ++j) v[j] = zr[j] + __shfl_xor_sync(kFull, zi[j], 1);
+    const bool b1 = (lane & 2) != 0, b2 = (lane & 4) != 0, b3 = (lane & 8) != 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float send = b1 ? v[i] : v[i + 4];
+        const float keep = b1 ? v[i + 4] : v[i];
+        v[i] = keep + __shfl_xor_sync(kFull, send, 2);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float send = b2 ? v[i] : v[i + 2];
+        const float keep = b2 ? v[i + 2] : v[i];
+        v[i] = keep + __shfl_xor_sync(kFull, send, 4);
+    }
+    {
+        const float send = b3 ? v[0] : v[1];
+        const float keep = b3 ? v[1] : v[0];
+        v[0] = keep + __shfl_xor_sync(kFull, send, 8);
+    }
+    v[0] += __shfl_xor_sync(kFull, v[0], 16);
+    const int s = (b1 ? 4 : 0) + (b2 ? 2 : 0) + (b3 ? 1 : 0);
+    const float other = __shfl_xor_sync(kFull, v[0], 1);
+    if (s < valid) {
+        if (zrow != nullptr && lane < 16) zrow[2 * (int64_t)(kbase + s) + (lane & 1)] = v[0];
+        // |z|^2 = re*re + im*im, no contraction (reproducible on the host)
+        const float p = __fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(other, other));
+        if (p > best) {
+            best = p;
+            bidx = kbase + s;
+        }
+    }
+}
+
+// ---- one CTA work unit: W templates x one detector, whole call -----------
+template <int F>
+__device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float *ring,
+                                         uint32_t bar0, uint32_t bar1)
+{
+    constexpr int NP = F / 2;              // filter pairs (packed FP32x2)
+    constexpr bool ODD = (F & 1) != 0;     // one more filter in scalar FP32
+    constexpr int NPA = NP > 0 ? NP : 1;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tmpl = A.slot_tmpl[(int64_t)g * A.W + warp];
+    const bool active = tmpl >= 0;
+    const int64_t pb = A.group_pbase[g];
+    const int n = A.n;
+    const int nblk = (n + A.Tb - 1) / A.Tb;
+    const float *xrow = A.xe + (int64_t)det * A.xe_stride;
+
+    // parameters and state of this lane's F filters
+    uint64_t AR[NPA], AI[NPA], NAI[NPA], BR[NPA], BI[NPA], YR[NPA], YI[NPA];
+    float ar1 = 0.f, ai1 = 0.f, br1 = 0.f, bi1 = 0.f, yr1 = 0.f, yi1 = 0.f;
+    int pos[F], cb[F];
+#pragma unroll
+    for (int r = 0; r < F; ++r) {
+        pos[r] = 0;
+        cb[r] = 0;
+    }
+    if (active) {
+        float4 p[F];
+        float2 st[F];
+#pragma unroll
+        for (int r = 0; r < F; ++r) {
+            const int64_t s = pb + ((int64_t)r * A.W + warp) * 32 + lane;
+            p[r] = A.params[s];
+            st[r] = A.state[(int64_t)det * A.n_slots + s];
+            const int2 ro = A.ringoff[s];
+            pos[r] = ro.x;
+            cb[r] = ro.y;
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) {
+            AR[q] = pk(p[2 * q].x, p[2 * q + 1].x);
+            AI[q] = pk(p[2 * q].y, p[2 * q + 1].y);
+            NAI[q] = pk(-p[2 * q].y, -p[2 * q + 1].y);
+            BR[q] = pk(p[2 * q].z, p[2 * q + 1].z);
+            BI[q] = pk(p[2 * q].w, p[2 * q + 1].w);
+            YR[q] = pk(st[2 * q].x, st[2 * q + 1].x);
+            YI[q] = pk(st[2 * q].y, st[2 * q + 1].y);
+        }
+        if (ODD) {
+            ar1 = p[F - 1].x;
+            ai1 = p[F - 1].y;
+            br1 = p[F - 1].z;
+            bi1 = p[F - 1].w;
+            yr1 = st[F - 1].x;
+            yi1 = st[F - 1].y;
+        }
+    }
+    float *zrow = (A.z != nullptr && active)
+                      ? A.z + ((int64_t)det * A.T + tmpl) * 2 * A.z_len
+                      : nullptr;
+    float best = -1.0f;
+    int bidx = -1;
+
+    // prologue: history blocks + block 0 on bar0, block 1 on bar1
+    if (threadIdx.x == 0) {
+        uint32_t bytes = 0;
+        for (int64_t e = 0; e <= A.H; ++e) bytes += block_bytes(A, e);
+        mbar_expect_tx(bar0, bytes);
+        for (int64_t e = 0; e <= A.H; ++e) issue_block(A, xrow, ring, e, bar0);
+        if (nblk > 1) {
+            mbar_expect_tx(bar1, block_bytes(A, A.H + 1));
+            issue_block(A, xrow, ring, A.H + 1, bar1);
+        }
+    }
+
+    int failed_at = -1;
+    for (int j = 0; j < nblk; ++j) {
+        const uint32_t bar = (j & 1) ? bar1 : bar0;
+        const bool ok = mbar_wait(bar, (uint32_t)((j >> 1) & 1), A.wait_limit_ns);
+        if (__syncthreads_or(!ok)) {
+            failed_at = j;
+            break;
+        }
+        if (active) {
+            const int k0 = j * A.Tb;
+            const int nv = min(A.Tb, n - k0);
+            int base[F];
+#pragma unroll
+            for (int r = 0; r < F; ++r) base[r] = cb[r] + pos[r];
+            for (int sb = 0; sb < nv; sb += kTS) {
+                const int valid = nv - sb;
+                float zr[kTS], zi[kTS];
+#pragma unroll
+                for (int t = 0; t < kTS; ++t) {
+                    if (valid < kTS && t >= valid) {  // ragged tail: state stays put
+                        zr[t] = 0.f;
+                        zi[t] = 0.f;
+                        continue;
+                    }
+                    uint64_t ZR = 0, ZI = 0;
+#pragma unroll
+                    for (int q = 0; q < NP; ++q) {
+                        const float xf = ring[base[2 * q] + t];
+                        const float xg = ring[base[2 * q + 1] + t];
+                        const uint64_t X = pk(xf, xg);
+                        uint64_t TR = mul2(BR[q], X);
+                        uint64_t TI = mul2(BI[q], X);
+                        TR = fma2(NAI[q], YI[q], TR);   // br x - ai yi
+                        TI = fma2(AI[q], YR[q], TI);    // bi x + ai yr
+                        YR[q] = fma2(AR[q], YR[q], TR); // ar yr - ai yi + br x
+                        YI[q] = fma2(AR[q], YI[q], TI); // ar yi + ai yr + bi x
+                        if (q == 0) {
+                            ZR = YR[0];
+                            ZI = YI[0];
+                        } else {
+                            ZR = add2(ZR, YR[q]);
+                            ZI = add2(ZI, YI[q]);
+                        }
+                    }
+                    float sr = 0.f, si = 0.f;
+                    if (NP > 0) {
+                        float lo, hi;
+                        upk(ZR, lo, hi);
+                        sr = lo + hi;
+                        upk(ZI, lo, hi);
+                        si = lo + hi;
+                    }
+                    if (ODD) {
+                        const float x1 = ring[base[F - 1] + t];
+                        const float nr = fmaf(ar1, yr1, fmaf(-ai1, yi1, br1 * x1));
+                        const float ni = fmaf(ar1, yi1, fmaf(ai1, yr1, bi1 * x1));
+                        yr1 = nr;
+                        yi1 = ni;
+                        sr = NP > 0 ? sr + yr1 : yr1;
+                        si = NP > 0 ? si + yi1 : yi1;
+                    }
+                    zr[t] = sr;
+                    zi[t] = si;
+                }
+                warp_sum_store_peak(zr, zi, lane, k0 + sb, valid, zrow, best, bidx);
+#pragma unroll
+                for (int r = 0; r < F; ++r) base[r] += kTS;
+            }
+#pragma unroll
+            for (int r = 0; r < F; ++r) {
+                pos[r] += A.Tb;
+                if (pos[r] >= A.R) pos[r] -= A.R;
+            }
+        }
+        __syncthreads();  // every warp is done with the slot the next copy overwrites
+        if (threadIdx.x == 0 && j + 2 < nblk) {
+            const int64_t e = (int64_t)A.H + j + 2;
+            mbar_expect_tx(bar, block_bytes(A, e));
+            issue_block(A, xrow, ring, e, bar);
+        }
+    }
+    if (failed_at >= 0) {
+        if (threadIdx.x == 0) {
+            atomicOr(A.err, 1);
+            // let copies still in flight land before the CTA's memory is reused:
+            // the block that timed out, and the one issued after it (bounded)
+            const int j = failed_at;
+            mbar_wait((j & 1) ? bar1 : bar0, (uint32_t)((j >> 1) & 1), A.wait_limit_ns);
+            if (j + 1 < nblk)
+                mbar_wait(((j + 1) & 1) ? bar1 : bar0, (uint32_t)(((j + 1) >> 1) & 1),
+                          A.wait_limit_ns);
+        }
+        return;
+    }
+    if (!active) return;
+
+    // state out
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+        float r0, r1, i0, i1;
+        upk(YR[q], r0, r1);
+        upk(YI[q], i0, i1);
+        const int64_t s0 = pb + ((int64_t)(2 * q) * A.W + warp) * 32 + lane;
+        const int64_t s1 = pb + ((int64_t)(2 * q + 1) * A.W + warp) * 32 + lane;
+        A.state[(int64_t)det * A.n_slots + s0] = make_float2(r0, i0);
+        A.state[(int64_t)det * A.n_slots + s1] = make_float2(r1, i1);
+    }
+    if (ODD) {
+        const int64_t s = pb + ((int64_t)(F - 1) * A.W + warp) * 32 + lane;
+        A.state[(int64_t)det * A.n_slots + s] = make_float2(yr1, yi1);
+    }
+    // running peak: largest |z|^2, earliest index on ties
+    if (A.peak_best != nullptr) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const float ob = __shfl_xor_sync(kFull, best, off);
+            const int oi = __shfl_xor_sync(kFull, bidx, off);
+            if (ob > best || (ob == best && oi >= 0 && (bidx < 0 || oi < bidx))) {
+                best = ob;
+                bidx = oi;
+            }
+        }
+        if (lane == 0 && bidx >= 0) {
+            const int64_t i = (int64_t)det * A.T + tmpl;
+            if (best > A.peak_best[i]) {
+                A.peak_best[i] = best;
+                A.peak_idx[i] = A.t0 + bidx;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256, 2) k1_plain(const K1Args A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    float *ring = reinterpret_cast<float *>(smem + 128);
+    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+    if (threadIdx.x == 0) {
+        mbar_init(bar0, 1);
+        mbar_init(bar1, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int g = A.units[2 * blockIdx.x];
+    const int det = A.units[2 * blockIdx.x + 1];
+    switch (A.group_F[g]) {
+    case 1: run_unit<1>(A, g, det, ring, bar0, bar1); break;
+    case 2: run_unit<2>(A, g, det, ring, bar0, bar1); break;
+    case 3: run_unit<3>(A, g, det, ring, bar0, bar1); break;
+    case 4: run_unit<4>(A, g, det, ring, bar0, bar1); break;
+    case 5: run_unit<5>(A, g, det, ring, bar0, bar1); break;
+    case 6: run_unit<6>(A, g, det, ring, bar0, bar1); break;
+    case 7: run_unit<7>(A, g, det, ring, bar0, bar1); break;
+    case 8: run_unit<8>(A, g, det, ring, bar0, bar1); break;
+    case 9: run_unit<9>(A, g, det, ring, bar0, bar1); break;
+    case 10: run_unit<10>(A, g, det, ring, bar0, bar1); break;
+    default:
+        if (threadIdx.x == 0) atomicOr(A.err, 4);
+        break;
+    }
+}
+
+__global__ void peak_out_kernel(const float *best, const int64_t *idx, int64_t count,
+                                float *out_abs, int64_t *out_idx)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    const float b = best[i];
+    out_abs[i] = b < 0.f ? 0.f : sqrtf(b);
+    out_idx[i] = idx[i];
+}
+
+__global__ void peak_reset_kernel(float *best, int64_t *idx, int64_t count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    best[i] = -1.0f;
+    idx[i] = -1;
+}
+
+__global__ void bounded_wait_probe(int32_t *err, uint64_t limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    const uint32_t b = smem_addr(&bar);
+    if (threadIdx.x == 0) {
+        mbar_init(b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // nothing arrives on this barrier: the wait must give up by itself
+    const bool ok = mbar_wait(b, 0, limit_ns);
+    if (!ok && threadIdx.x == 0) atomicOr(err, 2);
+}
+
+}  // namespace
+
+cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
+{
+    if (n_units <= 0 || a.n <= 0) return cudaSuccess;
+    if (smem_bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(
+            k1_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    k1_plain<<<(unsigned)n_units, a.W * 32, smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count,
+                            float *out_abs, int64_t *out_idx, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    peak_out_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(best, idx, count, out_abs,
+                                                                    out_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_peak_reset(float *best, int64_t *idx, int64_t count, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    peak_reset_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(best, idx, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bounded_wait_probe(int32_t *err, uint64_t limit_ns, cudaStream_t s)
+{
+    bounded_wait_probe<<<1, 32, 0, s>>>(err, limit_ns);
+    return cudaGetLastError();
+}
+
+}  // namespace spiir

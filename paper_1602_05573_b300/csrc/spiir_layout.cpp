@@ -1,0 +1,243 @@
+// Host-side layout builder: template sorting, CTA grouping and the
+// bank-aware placement of filters into (round, lane, ring copy) cells.
+#include "spiir_layout.h"
+
+#include <algorithm>
+#include <numeric>
+
+namespace spiir {
+
+namespace {
+
+inline int mod32(int64_t v) { return (int)(((v % 32) + 32) % 32); }
+
+// One (round, lane) cell of a template's warp.
+struct Cell {
+    int64_t filter = -1;
+    int copy = 0;
+    int delay = 0;
+};
+
+// Place the filters `fl` of one template into F rounds x 32 lanes.  Filter l
+// read through copy c hits bank (c*CS - d_l) mod 32 at every sample (the ring
+// length, history and block length are multiples of 32).  Greedy: each filter
+// goes to the round with the most free lanes among those where one of its C
+// banks is still free; if there is none it takes a free lane anyway (a bank
+// conflict).  Empty cells become padding filters (a = b = 0) whose delay is
+// chosen to hit a bank nobody in the round uses.  Returns the number of
+// conflicting placements; *wavefronts gets the summed worst-bank load.
+int place_template(const std::vector<int64_t> &fl, const int32_t *d, int F, int C, int CS,
+                   std::vector<Cell> &cells, double *wavefronts)
+{
+    cells.assign((size_t)F * 32, Cell());
+    std::vector<uint32_t> used(F, 0u);
+    std::vector<int> nfree(F, 32);
+    int conflicts = 0;
+    for (int64_t l : fl) {
+        const int dl = d[l];
+        int br = -1, bc = -1;
+        for (int r = 0; r < F; ++r) {
+            if (nfree[r] == 0) continue;
+            if (br >= 0 && nfree[r] <= nfree[br]) continue;
+            for (int c = 0; c < C; ++c) {
+                int bank = mod32((int64_t)c * CS - dl);
+                if (!((used[r] >> bank) & 1u)) {
+                    br = r;
+                    bc = c;
+                    break;
+                }
+            }
+        }
+        if (br < 0) {  // no conflict-free cell: most free round, copy 0
+            for (int r = 0; r < F; ++r)
+                if (nfree[r] > 0 && (br < 0 || nfree[r] > nfree[br])) br = r;
+            bc = 0;
+            ++conflicts;
+        }
+        int lane = 32 - nfree[br];
+        Cell &cell = cells[(size_t)br * 32 + lane];
+        cell.filter = l;
+        cell.copy = bc;
+        cell.delay = dl;
+        used[br] |= 1u << mod32((int64_t)bc * CS - dl);
+        --nfree[br];
+    }
+    // padding: a free bank per empty lane, copy 0, delay < 32
+    for (int r = 0; r < F; ++r) {
+        for (int lane = 32 - nfree[r]; lane < 32; ++lane) {
+            int bank = 0;
+            while (bank < 32 && ((used[r] >> bank) & 1u)) ++bank;
+            if (bank == 32) bank = 0;
+            used[r] |= 1u << bank;
+            Cell &cell = cells[(size_t)r * 32 + lane];
+            cell.filter = -1;
+            cell.copy = 0;
+            cell.delay = (32 - bank) % 32;  // (0 - delay) mod 32 == bank
+        }
+    }
+    // wavefronts per round: largest number of distinct addresses in one bank
+    double wf = 0.0;
+    for (int r = 0; r < F; ++r) {
+        int worst = 1;
+        for (int bank = 0; bank < 32; ++bank) {
+            std::vector<std::pair<int, int>> addr;
+            for (int lane = 0; lane < 32; ++lane) {
+                const Cell &c = cells[(size_t)r * 32 + lane];
+                if (mod32((int64_t)c.copy * CS - c.delay) == bank)
+                    addr.emplace_back(c.copy, c.delay);
+            }
+            std::sort(addr.begin(), addr.end());
+            int distinct = (int)(std::unique(addr.begin(), addr.end()) - addr.begin());
+            worst = std::max(worst, distinct);
+        }
+        wf += worst;
+    }
+    *wavefronts = wf;
+    return conflicts;
+}
+
+}  // namespace
+
+bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const float *a,
+                  const float *b, const int32_t *d, const LayoutOptions &opt, Layout *out,
+                  std::string *err)
+{
+    Layout L;
+    L.T = (int64_t)filters.size();
+    L.D = D;
+    L.Tb = opt.Tb;
+    if (L.T < 1 || D < 1) {
+        *err = "layout: empty bank";
+        return false;
+    }
+    if (L.Tb < 32 || L.Tb % 32 != 0 || L.Tb > 4096) {
+        *err = "layout: block_len must be a multiple of 32 in [32, 4096]";
+        return false;
+    }
+    L.C = opt.C == 0 ? 4 : opt.C;
+    if (L.C != 1 && L.C != 2 && L.C != 4) {
+        *err = "layout: ring_copies must be 1, 2 or 4";
+        return false;
+    }
+    // filters per lane, and the largest delay
+    int64_t maxd = 0;
+    std::vector<int> F(L.T);
+    for (int64_t t = 0; t < L.T; ++t) {
+        int64_t n = (int64_t)filters[t].size();
+        F[t] = (int)std::max<int64_t>(1, (n + 31) / 32);
+        if (F[t] > kMaxF) {
+            *err = "layout: template " + std::to_string(t) + " has " + std::to_string(n) +
+                   " filters; the plain kernel holds at most " + std::to_string(32 * kMaxF);
+            return false;
+        }
+        for (int64_t l : filters[t]) maxd = std::max<int64_t>(maxd, d[l]);
+        L.n_filters += n;
+    }
+    // warps per CTA: enough CTAs to cover the GPU twice over, at most 8
+    if (opt.W > 0) {
+        L.W = opt.W;
+    } else {
+        int64_t work = L.T * D;
+        int w = 8;
+        while (w > 1 && work / w < 2 * (int64_t)opt.n_sm) w /= 2;
+        L.W = w;
+    }
+    if (L.W < 1 || L.W > 8) {
+        *err = "layout: warps_per_cta must be in [1, 8]";
+        return false;
+    }
+    // ring geometry
+    L.H = (int)std::max<int64_t>(1, (maxd + L.Tb - 1) / L.Tb);
+    L.S = L.H + 2;
+    L.R = L.S * L.Tb;
+    L.Dh = L.H * L.Tb;
+    const int skew = L.C == 1 ? 0 : 32 / L.C;   // bank offset between copies
+    L.CS = L.R + L.Tb + skew;                    // R + Tb is a multiple of 32
+    if (L.smem_bytes() > 227 * 1024) {
+        *err = "layout: strain ring needs " + std::to_string(L.smem_bytes()) +
+               " bytes of shared memory (max delay " + std::to_string(maxd) +
+               "); use fewer ring_copies or a shorter block_len";
+        return false;
+    }
+    // sort templates: F descending, then filter count descending, then index
+    std::vector<int64_t> order(L.T);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        if (F[x] != F[y]) return F[x] > F[y];
+        return filters[x].size() > filters[y].size();
+    });
+    const int64_t G = (L.T + L.W - 1) / L.W;
+    L.group_F.resize(G);
+    L.group_pbase.resize(G);
+    L.slot_tmpl.assign((size_t)G * L.W, -1);
+    int64_t base = 0;
+    for (int64_t g = 0; g < G; ++g) {
+        L.group_F[g] = F[order[g * L.W]];
+        L.group_pbase[g] = base;
+        base += (int64_t)L.group_F[g] * L.W * 32;
+        for (int w = 0; w < L.W; ++w) {
+            int64_t i = g * L.W + w;
+            if (i < L.T) L.slot_tmpl[g * L.W + w] = (int32_t)order[i];
+        }
+    }
+    L.n_slots = base;
+    L.maxF = *std::max_element(L.group_F.begin(), L.group_F.end());
+    L.params.assign((size_t)L.n_slots * 4, 0.f);
+    L.ringoff.assign((size_t)L.n_slots * 2, 0);
+    L.slot_filter.assign((size_t)L.n_slots, -1);
+    L.slot_template.assign((size_t)L.n_slots, -1);
+    double wf_total = 0.0;
+    int64_t rounds_total = 0;
+    std::vector<Cell> cells;
+    static const std::vector<int64_t> none;
+    for (int64_t g = 0; g < G; ++g) {
+        const int Fg = L.group_F[g];
+        for (int w = 0; w < L.W; ++w) {
+            const int64_t t = L.slot_tmpl[g * L.W + w];
+            const std::vector<int64_t> &fl = t >= 0 ? filters[t] : none;
+            double wf = 0.0;
+            place_template(fl, d, Fg, L.C, L.CS, cells, &wf);
+            if (t >= 0) {
+                wf_total += wf;
+                rounds_total += Fg;
+            }
+            for (int r = 0; r < Fg; ++r) {
+                for (int i = 0; i < 32; ++i) {
+                    const Cell &c = cells[(size_t)r * 32 + i];
+                    const int64_t s = L.slot(g, r, w, i);
+                    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+                    if (c.filter >= 0) {
+                        ar = a[2 * c.filter];
+                        ai = a[2 * c.filter + 1];
+                        br = b[2 * c.filter];
+                        bi = b[2 * c.filter + 1];
+                    }
+                    if (i & 1) {  // (im, re) order: pole conj(a), gain (Im b, Re b)
+                        ai = -ai;
+                        std::swap(br, bi);
+                    }
+                    L.params[4 * s + 0] = ar;
+                    L.params[4 * s + 1] = ai;
+                    L.params[4 * s + 2] = br;
+                    L.params[4 * s + 3] = bi;
+                    L.ringoff[2 * s + 0] = L.Dh - c.delay;  // window start at block 0
+                    L.ringoff[2 * s + 1] = c.copy * L.CS;   // copy base word
+                    L.slot_filter[s] = c.filter;
+                    L.slot_template[s] = t;
+                }
+            }
+        }
+    }
+    L.conflict_ratio = rounds_total ? wf_total / (double)rounds_total : 1.0;
+    // work units: groups in sorted (largest-first) order, detectors inner
+    L.units.resize((size_t)G * D * 2);
+    for (int64_t g = 0; g < G; ++g)
+        for (int det = 0; det < D; ++det) {
+            L.units[2 * (g * D + det)] = (int32_t)g;
+            L.units[2 * (g * D + det) + 1] = det;
+        }
+    *out = std::move(L);
+    return true;
+}
+
+}  // namespace spiir
