@@ -1,0 +1,283 @@
+"""SPIIR filter bank on NVIDIA B300 (sm_103a): thin Python binding.
+
+The compute path is the C-ABI library ``_lib/libspiir.so`` (declared in
+``include/spiir.h``), built from ``csrc/`` by ``build.py``.  This module only
+marshals arguments: numpy arrays for the bank (host), torch CUDA tensors for
+strain, SNR series and gradients (device memory and streams).  Every step of
+the filtering runs in the library's CUDA kernels; there is no CPU fallback,
+and importing this package fails if the library is missing.
+
+The method (paper, section "GPU accelerated SPIIR method", subsection "SPIIR
+method"): each template is a bank of single-pole complex IIR filters
+``y_l[k] = a_l y_l[k-1] + b_l x[k-d_l]`` summed into ``z[k] = sum_l y_l[k]``,
+whose peak ``max_k |z[k]|`` flags a candidate signal.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libspiir.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"SPIIR CUDA library not built ({LIB_PATH} missing); run "
+        "`python -m paper_1602_05573_b300.build` (nvcc, sm_103a)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
+PRECISIONS = {"plain": 0, "compensated": 1, "chunked_fp64": 2, "chunked_tc": 3}
+
+# exported symbols (include/spiir.h)
+SYMBOLS = [
+    "spiir_options_default", "spiir_plan_create", "spiir_plan_destroy",
+    "spiir_plan_get_info", "spiir_plan_get_slots", "spiir_reset", "spiir_filter",
+    "spiir_peak", "spiir_filter_backward", "spiir_state_get", "spiir_state_set",
+    "spiir_check", "spiir_selftest_bounded_wait", "spiir_status_str",
+    "spiir_last_error_detail",
+]
+
+
+class BankDesc(ctypes.Structure):
+    _fields_ = [("n_templates", ctypes.c_int64), ("n_detectors", ctypes.c_int32),
+                ("n_bands", ctypes.c_int32), ("filter_off", ctypes.c_void_p),
+                ("a_reim", ctypes.c_void_p), ("b_reim", ctypes.c_void_p),
+                ("delay", ctypes.c_void_p), ("band_of_filter", ctypes.c_void_p),
+                ("band_decim", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("chunk_len", ctypes.c_int32),
+                ("block_len", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("ring_copies", ctypes.c_int32), ("device", ctypes.c_int32),
+                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("n_templates", ctypes.c_int64), ("n_filters", ctypes.c_int64),
+                ("n_slots", ctypes.c_int64), ("n_units", ctypes.c_int64),
+                ("n_detectors", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
+                ("block_len", ctypes.c_int32), ("ring_copies", ctypes.c_int32),
+                ("history_len", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
+                ("max_filters_per_lane", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("bank_conflict_ratio", ctypes.c_double)]
+
+
+_P = ctypes.c_void_p
+_st = ctypes.c_int
+_lib.spiir_options_default.argtypes = [ctypes.POINTER(Options)]
+_lib.spiir_options_default.restype = None
+_lib.spiir_plan_create.argtypes = [ctypes.POINTER(BankDesc), ctypes.POINTER(Options),
+                                   ctypes.POINTER(_P)]
+_lib.spiir_plan_create.restype = _st
+_lib.spiir_plan_destroy.argtypes = [_P]
+_lib.spiir_plan_destroy.restype = _st
+_lib.spiir_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
+_lib.spiir_plan_get_info.restype = _st
+_lib.spiir_plan_get_slots.argtypes = [_P, _P, _P]
+_lib.spiir_plan_get_slots.restype = _st
+_lib.spiir_reset.argtypes = [_P, _P]
+_lib.spiir_reset.restype = _st
+_lib.spiir_filter.argtypes = [_P, _P, ctypes.c_int64, _P, _P]
+_lib.spiir_filter.restype = _st
+_lib.spiir_peak.argtypes = [_P, _P, _P, _P]
+_lib.spiir_peak.restype = _st
+_lib.spiir_filter_backward.argtypes = [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]
+_lib.spiir_filter_backward.restype = _st
+_lib.spiir_state_get.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int64)]
+_lib.spiir_state_get.restype = _st
+_lib.spiir_state_set.argtypes = [_P, _P, _P, ctypes.c_int64]
+_lib.spiir_state_set.restype = _st
+_lib.spiir_check.argtypes = [_P, _P]
+_lib.spiir_check.restype = _st
+_lib.spiir_selftest_bounded_wait.argtypes = [_P, ctypes.c_uint64, _P]
+_lib.spiir_selftest_bounded_wait.restype = _st
+_lib.spiir_status_str.argtypes = [_st]
+_lib.spiir_status_str.restype = ctypes.c_char_p
+_lib.spiir_last_error_detail.argtypes = []
+_lib.spiir_last_error_detail.restype = ctypes.c_char_p
+
+
+class SpiirError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        detail = _lib.spiir_last_error_detail().decode()
+        super().__init__(f"{where}: {_lib.spiir_status_str(status).decode()}"
+                         + (f" ({detail})" if detail else ""))
+
+
+def _check(status: int, where: str):
+    if status != OK:
+        raise SpiirError(status, where)
+
+
+def library():
+    """The loaded ctypes library (for tests that call the C-ABI directly)."""
+    return _lib
+
+
+def _ptr(arr) -> Optional[int]:
+    if arr is None:
+        return None
+    if hasattr(arr, "data_ptr"):
+        return arr.data_ptr()
+    return arr.ctypes.data
+
+
+def _stream_handle(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Plan:
+    """A SPIIR bank prepared for the GPU (or host-only, device=-1).
+
+    bank: object with numpy fields off (int64 [T+1]), a, b (complex64 [Ltot]),
+    d (int32 [Ltot]), n_det, and optionally band_of (int32 [Ltot]) and
+    decim (int32 [n_bands]).
+    """
+
+    def __init__(self, bank, *, precision: str = "plain", device: int = 0,
+                 block_len: int = 0, warps_per_cta: int = 0, ring_copies: int = 0,
+                 chunk_len: int = 256, autotune: bool = False):
+        self._h = None
+        off = np.ascontiguousarray(bank.off, np.int64)
+        a = np.ascontiguousarray(bank.a, np.complex64).view(np.float32)
+        b = np.ascontiguousarray(bank.b, np.complex64).view(np.float32)
+        d = np.ascontiguousarray(bank.d, np.int32)
+        band_of = getattr(bank, "band_of", None)
+        decim = getattr(bank, "decim", None)
+        self._keep = [off, a, b, d]
+        desc = BankDesc()
+        desc.n_templates = off.shape[0] - 1
+        desc.n_detectors = int(bank.n_det)
+        desc.filter_off, desc.a_reim, desc.b_reim, desc.delay = (
+            _ptr(off), _ptr(a), _ptr(b), _ptr(d))
+        if band_of is not None and decim is not None and len(decim) > 1:
+            band_of = np.ascontiguousarray(band_of, np.int32)
+            decim = np.ascontiguousarray(decim, np.int32)
+            self._keep += [band_of, decim]
+            desc.n_bands = int(decim.shape[0])
+            desc.band_of_filter, desc.band_decim = _ptr(band_of), _ptr(decim)
+        opt = Options()
+        _lib.spiir_options_default(ctypes.byref(opt))
+        opt.precision = PRECISIONS[precision]
+        opt.device = int(device)
+        opt.block_len = int(block_len)
+        opt.warps_per_cta = int(warps_per_cta)
+        opt.ring_copies = int(ring_copies)
+        opt.chunk_len = int(chunk_len)
+        opt.autotune = int(bool(autotune))
+        h = _P()
+        _check(_lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
+               "spiir_plan_create")
+        self._h = h
+        self.device = int(device)
+        self.n_templates = int(desc.n_templates)
+        self.n_det = int(bank.n_det)
+        self.n_filters = int(off[-1])
+
+    # -- lifecycle ------------------------------------------------------------
+    def close(self):
+        if self._h is not None and self._h.value:
+            _lib.spiir_plan_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self) -> dict:
+        inf = PlanInfo()
+        _check(_lib.spiir_plan_get_info(self._h, ctypes.byref(inf)), "spiir_plan_get_info")
+        return {name: getattr(inf, name) for name, _ in PlanInfo._fields_}
+
+    def slots(self):
+        n = self.info()["n_slots"]
+        sf = np.empty(n, np.int64)
+        st = np.empty(n, np.int64)
+        _check(_lib.spiir_plan_get_slots(self._h, _ptr(sf), _ptr(st)), "spiir_plan_get_slots")
+        return sf, st
+
+    # -- streaming ------------------------------------------------------------
+    def reset(self, stream=None):
+        _check(_lib.spiir_reset(self._h, _stream_handle(stream)), "spiir_reset")
+
+    def filter(self, x, z=None, *, emit_z: bool = True, stream=None):
+        """Filter the next samples.  x: CUDA float32 [D][n] (contiguous).
+        Returns z (complex64 [D][T][n]) or None when emit_z is False."""
+        import torch
+        assert x.is_cuda and x.dtype == torch.float32 and x.is_contiguous()
+        D, n = x.shape
+        assert D == self.n_det
+        if emit_z and z is None:
+            z = torch.empty((D, self.n_templates, n), dtype=torch.complex64, device=x.device)
+        if z is not None:
+            assert z.is_cuda and z.dtype == torch.complex64 and z.is_contiguous()
+            assert tuple(z.shape) == (D, self.n_templates, n)
+        _check(_lib.spiir_filter(self._h, _ptr(x), n, _ptr(z) if z is not None else None,
+                                 _stream_handle(stream)), "spiir_filter")
+        return z
+
+    def peak(self, out_abs=None, out_idx=None, *, stream=None):
+        """Running peak since reset: (abs float32 [D][T], idx int64 [D][T]) on the GPU."""
+        import torch
+        dev = torch.device("cuda", self.device)
+        if out_abs is None:
+            out_abs = torch.empty((self.n_det, self.n_templates), dtype=torch.float32, device=dev)
+        if out_idx is None:
+            out_idx = torch.empty((self.n_det, self.n_templates), dtype=torch.int64, device=dev)
+        _check(_lib.spiir_peak(self._h, _ptr(out_abs), _ptr(out_idx), _stream_handle(stream)),
+               "spiir_peak")
+        return out_abs, out_idx
+
+    def backward(self, x, grad_z, *, want_gx: bool = True, stream=None):
+        """VJP of one zero-state filter call: (g_a, g_b complex64 [Ltot], g_x float32 [D][n])."""
+        import torch
+        D, n = x.shape
+        ga = torch.empty(self.n_filters, dtype=torch.complex64, device=x.device)
+        gb = torch.empty(self.n_filters, dtype=torch.complex64, device=x.device)
+        gx = torch.empty((D, n), dtype=torch.float32, device=x.device) if want_gx else None
+        gz = grad_z.contiguous()
+        _check(_lib.spiir_filter_backward(self._h, _ptr(x), n, _ptr(gz), _ptr(ga), _ptr(gb),
+                                          _ptr(gx), _stream_handle(stream)),
+               "spiir_filter_backward")
+        return ga, gb, gx
+
+    def state_get(self):
+        inf = self.info()
+        st = np.zeros((self.n_det, self.n_filters), np.complex64)
+        hist = np.zeros((self.n_det, inf["history_len"]), np.float32)
+        t = ctypes.c_int64()
+        _check(_lib.spiir_state_get(self._h, _ptr(st), _ptr(hist), ctypes.byref(t)),
+               "spiir_state_get")
+        return st, hist, int(t.value)
+
+    def state_set(self, state, history, samples):
+        state = np.ascontiguousarray(state, np.complex64)
+        history = np.ascontiguousarray(history, np.float32)
+        _check(_lib.spiir_state_set(self._h, _ptr(state), _ptr(history), int(samples)),
+               "spiir_state_set")
+
+    def check(self, stream=None):
+        """Wait for the plan's work; raise SpiirError(ETIMEOUT) if a bounded wait gave up."""
+        _check(_lib.spiir_check(self._h, _stream_handle(stream)), "spiir_check")

@@ -1,0 +1,634 @@
+// C-ABI entry points (include/spiir.h): plan lifecycle, streaming state,
+// workspace, and the launch sequence of each call.  Device compute lives in
+// the kernel files; this file only validates, allocates and enqueues.
+#include "spiir.h"
+#include "spiir_kernels.h"
+#include "spiir_layout.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace {
+
+thread_local std::string g_detail;
+
+spiir_status fail(spiir_status st, const std::string &why)
+{
+    g_detail = why;
+    return st;
+}
+
+spiir_status cuda_fail(cudaError_t e, const char *what)
+{
+    g_detail = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) +
+               ")";
+    (void)cudaGetLastError();  // clear a sticky launch error for the next call
+    return SPIIR_ECUDA;
+}
+
+// Keeps the caller's current device and restores it on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        err = cudaSetDevice(dev);
+        ok = err == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename T> cudaError_t dalloc(T **p, size_t count)
+{
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+template <typename T> cudaError_t h2d(T *dst, const std::vector<T> &src)
+{
+    if (src.empty()) return cudaSuccess;
+    return cudaMemcpy(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+}
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s bound on any device wait
+
+}  // namespace
+
+// One rate band of a plan (a single-rate bank has one band with R = 1).
+struct Band {
+    int R = 1;
+    spiir::Layout lay;
+    float4 *params = nullptr;
+    int2 *ringoff = nullptr;
+    int32_t *units = nullptr;
+    int32_t *group_F = nullptr;
+    int64_t *group_pbase = nullptr;
+    int32_t *slot_tmpl = nullptr;
+    float2 *state = nullptr;   // [D][n_slots]
+    float *hist = nullptr;     // [D][Dh]
+    float *xe = nullptr;       // [D][xe_stride] workspace
+    int64_t xe_stride = 0;
+    int64_t xe_cap = 0;        // samples the workspace holds after the history
+};
+
+struct spiir_plan {
+    int device = -1;
+    int precision = 0;
+    int D = 1;
+    int64_t T = 0;
+    int64_t Ltot = 0;
+    spiir_options opt{};
+    std::vector<Band> bands;
+    float *peak_best = nullptr;   // [D][T]
+    int64_t *peak_idx = nullptr;  // [D][T]
+    int32_t *err = nullptr;
+    int64_t t0 = 0;               // samples since reset
+};
+
+namespace {
+
+void free_band(Band &b)
+{
+    cudaFree(b.params);
+    cudaFree(b.ringoff);
+    cudaFree(b.units);
+    cudaFree(b.group_F);
+    cudaFree(b.group_pbase);
+    cudaFree(b.slot_tmpl);
+    cudaFree(b.state);
+    cudaFree(b.hist);
+    cudaFree(b.xe);
+    b = Band();
+}
+
+spiir_status validate_bank(const spiir_bank_desc *bank)
+{
+    if (!bank) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (bank->n_templates < 1) return fail(SPIIR_EINVAL, "n_templates must be >= 1");
+    if (bank->n_detectors < 1) return fail(SPIIR_EINVAL, "n_detectors must be >= 1");
+    if (!bank->filter_off || !bank->a_reim || !bank->b_reim || !bank->delay)
+        return fail(SPIIR_EINVAL, "filter_off, a_reim, b_reim and delay are required");
+    const int64_t *off = bank->filter_off;
+    if (off[0] != 0) return fail(SPIIR_EINVAL, "filter_off[0] must be 0");
+    for (int64_t t = 0; t < bank->n_templates; ++t)
+        if (off[t + 1] < off[t])
+            return fail(SPIIR_EINVAL, "filter_off must be non-decreasing (template " +
+                                          std::to_string(t) + ")");
+    const int64_t L = off[bank->n_templates];
+    for (int64_t l = 0; l < L; ++l) {
+        const double ar = bank->a_reim[2 * l], ai = bank->a_reim[2 * l + 1];
+        const double br = bank->b_reim[2 * l], bi = bank->b_reim[2 * l + 1];
+        if (!std::isfinite(ar) || !std::isfinite(ai) || !std::isfinite(br) || !std::isfinite(bi))
+            return fail(SPIIR_EINVAL, "non-finite pole or gain at filter " + std::to_string(l));
+        if (ar * ar + ai * ai >= 1.0)
+            return fail(SPIIR_EINVAL, "|a| >= 1 (unstable pole) at filter " + std::to_string(l));
+        if (bank->delay[l] < 0)
+            return fail(SPIIR_EINVAL, "negative delay at filter " + std::to_string(l));
+    }
+    if (bank->n_bands > 1) {
+        if (!bank->band_of_filter || !bank->band_decim)
+            return fail(SPIIR_EINVAL, "multirate bank needs band_of_filter and band_decim");
+        int minR = 1 << 30;
+        for (int j = 0; j < bank->n_bands; ++j) {
+            if (bank->band_decim[j] < 1 || bank->band_decim[j] > 4096)
+                return fail(SPIIR_EINVAL, "band_decim must be in [1, 4096]");
+            minR = std::min(minR, bank->band_decim[j]);
+        }
+        if (minR != 1) return fail(SPIIR_EINVAL, "a multirate bank needs a band with decim 1");
+        for (int64_t l = 0; l < L; ++l)
+            if (bank->band_of_filter[l] < 0 || bank->band_of_filter[l] >= bank->n_bands)
+                return fail(SPIIR_EINVAL, "band_of_filter out of range at filter " +
+                                              std::to_string(l));
+    } else if (bank->n_bands == 1 && bank->band_decim && bank->band_decim[0] != 1) {
+        return fail(SPIIR_EINVAL, "a single band must have decim 1");
+    } else if (bank->n_bands < 0) {
+        return fail(SPIIR_EINVAL, "n_bands must be >= 0");
+    }
+    return SPIIR_OK;
+}
+
+spiir_status upload_band(Band &b, int D)
+{
+    const spiir::Layout &L = b.lay;
+    cudaError_t e;
+    if ((e = dalloc(&b.params, L.n_slots)) != cudaSuccess ||
+        (e = dalloc(&b.ringoff, L.n_slots)) != cudaSuccess ||
+        (e = dalloc(&b.units, L.units.size())) != cudaSuccess ||
+        (e = dalloc(&b.group_F, L.group_F.size())) != cudaSuccess ||
+        (e = dalloc(&b.group_pbase, L.group_pbase.size())) != cudaSuccess ||
+        (e = dalloc(&b.slot_tmpl, L.slot_tmpl.size())) != cudaSuccess ||
+        (e = dalloc(&b.state, (size_t)D * L.n_slots)) != cudaSuccess ||
+        (e = dalloc(&b.hist, (size_t)D * L.Dh)) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "device allocation failed")
+                                              : cuda_fail(e, "cudaMalloc");
+    if ((e = cudaMemcpy(b.params, L.params.data(), L.params.size() * sizeof(float),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b.ringoff, L.ringoff.data(), L.ringoff.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = h2d(b.units, L.units)) != cudaSuccess ||
+        (e = h2d(b.group_F, L.group_F)) != cudaSuccess ||
+        (e = h2d(b.group_pbase, L.group_pbase)) != cudaSuccess ||
+        (e = h2d(b.slot_tmpl, L.slot_tmpl)) != cudaSuccess ||
+        (e = cudaMemset(b.state, 0, sizeof(float2) * (size_t)D * L.n_slots)) != cudaSuccess ||
+        (e = cudaMemset(b.hist, 0, sizeof(float) * (size_t)D * L.Dh)) != cudaSuccess)
+        return cuda_fail(e, "plan upload");
+    return SPIIR_OK;
+}
+
+// Make the band's strain workspace hold n more samples (after the history).
+spiir_status ensure_xe(spiir_plan *p, Band &b, int64_t n, cudaStream_t s)
+{
+    const int64_t need = ((n + b.lay.Tb - 1) / b.lay.Tb) * b.lay.Tb;
+    if (b.xe && b.xe_cap >= need) return SPIIR_OK;
+    if (b.xe) {
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+        cudaFree(b.xe);
+        b.xe = nullptr;
+    }
+    const int64_t cap = std::max<int64_t>(need, 4096);
+    const int64_t stride = b.lay.Dh + cap;
+    cudaError_t e = dalloc(&b.xe, (size_t)p->D * stride);
+    if (e != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "strain workspace allocation")
+                                              : cuda_fail(e, "cudaMalloc");
+    b.xe_cap = cap;
+    b.xe_stride = stride;
+    return SPIIR_OK;
+}
+
+spiir::K1Args k1_args(const spiir_plan *p, const Band &b, int64_t n, float *z, int64_t z_len,
+                      bool with_peak)
+{
+    const spiir::Layout &L = b.lay;
+    spiir::K1Args a{};
+    a.xe = b.xe;
+    a.xe_stride = b.xe_stride;
+    a.n = (int32_t)n;
+    a.Tb = L.Tb;
+    a.H = L.H;
+    a.S = L.S;
+    a.R = L.R;
+    a.CS = L.CS;
+    a.C = L.C;
+    a.W = L.W;
+    a.units = b.units;
+    a.group_F = b.group_F;
+    a.group_pbase = b.group_pbase;
+    a.slot_tmpl = b.slot_tmpl;
+    a.params = b.params;
+    a.ringoff = b.ringoff;
+    a.state = b.state;
+    a.n_slots = L.n_slots;
+    a.z = z;
+    a.z_len = z_len;
+    a.T = p->T;
+    a.peak_best = with_peak ? p->peak_best : nullptr;
+    a.peak_idx = with_peak ? p->peak_idx : nullptr;
+    a.t0 = p->t0;
+    a.err = p->err;
+    a.wait_limit_ns = kWaitLimitNs;
+    return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+void spiir_options_default(spiir_options *opt)
+{
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = SPIIR_PREC_PLAIN;
+    opt->chunk_len = 256;
+    opt->block_len = 0;
+    opt->warps_per_cta = 0;
+    opt->ring_copies = 0;
+    opt->device = 0;
+    opt->autotune = 0;
+}
+
+const char *spiir_status_str(spiir_status st)
+{
+    switch (st) {
+    case SPIIR_OK: return "ok";
+    case SPIIR_EINVAL: return "invalid argument";
+    case SPIIR_ENOMEM: return "out of memory";
+    case SPIIR_ECUDA: return "CUDA runtime error";
+    case SPIIR_ETIMEOUT: return "bounded device wait timed out";
+    case SPIIR_EUNSUPPORTED: return "unsupported device or size";
+    }
+    return "unknown status";
+}
+
+const char *spiir_last_error_detail(void) { return g_detail.c_str(); }
+
+spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options *opt_in,
+                               spiir_plan **out)
+{
+    if (!out) return fail(SPIIR_EINVAL, "out is NULL");
+    *out = nullptr;
+    spiir_status st = validate_bank(bank);
+    if (st != SPIIR_OK) return st;
+    spiir_options opt;
+    spiir_options_default(&opt);
+    if (opt_in) opt = *opt_in;
+    if (opt.precision != SPIIR_PREC_PLAIN)
+        return fail(SPIIR_EUNSUPPORTED, "precision mode not built yet");
+    if (opt.block_len != 0 && (opt.block_len < 32 || opt.block_len % 32 != 0))
+        return fail(SPIIR_EINVAL, "block_len must be 0 or a multiple of 32");
+
+    int n_sm = 148;
+    if (opt.device >= 0) {
+        int count = 0;
+        cudaError_t e = cudaGetDeviceCount(&count);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+        if (opt.device >= count)
+            return fail(SPIIR_EINVAL, "device ordinal " + std::to_string(opt.device) +
+                                          " out of range");
+        cudaDeviceProp prop;
+        e = cudaGetDeviceProperties(&prop, opt.device);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+        if (prop.major != 10 || prop.minor != 3)
+            return fail(SPIIR_EUNSUPPORTED,
+                        std::string("kernels are built for sm_103a; device is ") + prop.name +
+                            " (sm_" + std::to_string(prop.major) + std::to_string(prop.minor) +
+                            ")");
+        n_sm = prop.multiProcessorCount;
+    }
+
+    spiir_plan *p = new (std::nothrow) spiir_plan();
+    if (!p) return fail(SPIIR_ENOMEM, "host allocation");
+    p->device = opt.device;
+    p->precision = opt.precision;
+    p->D = bank->n_detectors;
+    p->T = bank->n_templates;
+    p->Ltot = bank->filter_off[bank->n_templates];
+    p->opt = opt;
+
+    // bands: filter lists per template and band
+    std::vector<int> decims;
+    if (bank->n_bands > 1)
+        decims.assign(bank->band_decim, bank->band_decim + bank->n_bands);
+    else
+        decims.push_back(1);
+    spiir::LayoutOptions lo;
+    lo.W = opt.warps_per_cta;
+    lo.Tb = opt.block_len ? opt.block_len : 256;
+    lo.C = opt.ring_copies;
+    lo.n_sm = n_sm;
+    p->bands.resize(decims.size());
+    for (size_t j = 0; j < decims.size(); ++j) {
+        std::vector<std::vector<int64_t>> lists((size_t)p->T);
+        for (int64_t t = 0; t < p->T; ++t)
+            for (int64_t l = bank->filter_off[t]; l < bank->filter_off[t + 1]; ++l)
+                if (decims.size() == 1 || bank->band_of_filter[l] == (int)j)
+                    lists[t].push_back(l);
+        p->bands[j].R = decims[j];
+        std::string err;
+        if (!spiir::build_layout(lists, p->D, bank->a_reim, bank->b_reim, bank->delay, lo,
+                                 &p->bands[j].lay, &err)) {
+            delete p;
+            return fail(SPIIR_EUNSUPPORTED, err);
+        }
+    }
+    if (p->bands.size() > 1) {
+        delete p;
+        return fail(SPIIR_EUNSUPPORTED, "multirate banks are not built yet");
+    }
+    if (p->device < 0) {  // host-only plan
+        *out = p;
+        return SPIIR_OK;
+    }
+    DeviceGuard guard(p->device);
+    if (!guard.ok) {
+        delete p;
+        return cuda_fail(guard.err, "cudaSetDevice");
+    }
+    for (Band &b : p->bands) {
+        st = upload_band(b, p->D);
+        if (st != SPIIR_OK) {
+            spiir_plan_destroy(p);
+            return st;
+        }
+    }
+    cudaError_t e;
+    if ((e = dalloc(&p->peak_best, (size_t)p->D * p->T)) != cudaSuccess ||
+        (e = dalloc(&p->peak_idx, (size_t)p->D * p->T)) != cudaSuccess ||
+        (e = dalloc(&p->err, 1)) != cudaSuccess) {
+        spiir_plan_destroy(p);
+        return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "device allocation failed")
+                                              : cuda_fail(e, "cudaMalloc");
+    }
+    st = spiir_reset(p, nullptr);
+    if (st == SPIIR_OK) {
+        e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) st = cuda_fail(e, "plan init");
+    }
+    if (st != SPIIR_OK) {
+        spiir_plan_destroy(p);
+        return st;
+    }
+    *out = p;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_plan_destroy(spiir_plan *p)
+{
+    if (!p) return SPIIR_OK;
+    if (p->device >= 0) {
+        DeviceGuard guard(p->device);
+        cudaDeviceSynchronize();
+        for (Band &b : p->bands) free_band(b);
+        cudaFree(p->peak_best);
+        cudaFree(p->peak_idx);
+        cudaFree(p->err);
+    }
+    delete p;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_plan_get_info(const spiir_plan *p, spiir_plan_info *info)
+{
+    if (!p || !info) return fail(SPIIR_EINVAL, "plan or info is NULL");
+    std::memset(info, 0, sizeof(*info));
+    info->n_templates = p->T;
+    info->n_filters = p->Ltot;
+    info->n_detectors = p->D;
+    info->precision = p->precision;
+    double wf = 0.0, rounds = 0.0;
+    for (const Band &b : p->bands) {
+        const spiir::Layout &L = b.lay;
+        info->n_slots += L.n_slots;
+        info->n_units += L.n_units();
+        info->warps_per_cta = L.W;
+        info->block_len = L.Tb;
+        info->ring_copies = L.C;
+        info->history_len = std::max(info->history_len, L.Dh);
+        info->smem_bytes = std::max(info->smem_bytes, L.smem_bytes());
+        info->max_filters_per_lane = std::max(info->max_filters_per_lane, L.maxF);
+        wf += L.conflict_ratio * (double)L.n_slots;
+        rounds += (double)L.n_slots;
+    }
+    info->bank_conflict_ratio = rounds > 0 ? wf / rounds : 1.0;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_plan_get_slots(const spiir_plan *p, int64_t *slot_filter,
+                                  int64_t *slot_template)
+{
+    if (!p || !slot_filter || !slot_template) return fail(SPIIR_EINVAL, "NULL argument");
+    int64_t at = 0;
+    for (const Band &b : p->bands) {
+        std::memcpy(slot_filter + at, b.lay.slot_filter.data(), sizeof(int64_t) * b.lay.n_slots);
+        std::memcpy(slot_template + at, b.lay.slot_template.data(),
+                    sizeof(int64_t) * b.lay.n_slots);
+        at += b.lay.n_slots;
+    }
+    return SPIIR_OK;
+}
+
+spiir_status spiir_reset(spiir_plan *p, void *stream)
+{
+    if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
+    if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan has no device state");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e;
+    for (Band &b : p->bands) {
+        if ((e = cudaMemsetAsync(b.state, 0, sizeof(float2) * (size_t)p->D * b.lay.n_slots, s)) !=
+                cudaSuccess ||
+            (e = cudaMemsetAsync(b.hist, 0, sizeof(float) * (size_t)p->D * b.lay.Dh, s)) !=
+                cudaSuccess)
+            return cuda_fail(e, "reset");
+    }
+    if ((e = spiir::launch_peak_reset(p->peak_best, p->peak_idx, (int64_t)p->D * p->T, s)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s)) != cudaSuccess)
+        return cuda_fail(e, "reset");
+    p->t0 = 0;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z_dev,
+                          void *stream)
+{
+    if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
+    if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan cannot filter");
+    if (n < 0) return fail(SPIIR_EINVAL, "n must be >= 0");
+    if (n == 0) return SPIIR_OK;
+    if (!x_dev) return fail(SPIIR_EINVAL, "x_dev is NULL");
+    if (n > (int64_t)1 << 30) return fail(SPIIR_EINVAL, "n above 2^30 samples per call");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    Band &b = p->bands[0];
+    spiir_status st = ensure_xe(p, b, n, s);
+    if (st != SPIIR_OK) return st;
+    const int D = p->D;
+    const int64_t Dh = b.lay.Dh;
+    cudaError_t e;
+    // xe[:, 0:Dh] = history, xe[:, Dh:Dh+n] = x
+    if ((e = cudaMemcpy2DAsync(b.xe, b.xe_stride * 4, b.hist, Dh * 4, Dh * 4, D,
+                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpy2DAsync(b.xe + Dh, b.xe_stride * 4, x_dev, n * 4, n * 4, D,
+                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "strain staging copy");
+    spiir::K1Args a = k1_args(p, b, n, z_dev, n, true);
+    if ((e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s)) != cudaSuccess)
+        return cuda_fail(e, "filter kernel launch");
+    // history for the next call: the last Dh samples of (history, x)
+    if ((e = cudaMemcpy2DAsync(b.hist, Dh * 4, b.xe + n, b.xe_stride * 4, Dh * 4, D,
+                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "history copy");
+    p->t0 += n;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_peak(spiir_plan *p, float *peak_abs_dev, int64_t *peak_idx_dev, void *stream)
+{
+    if (!p || !peak_abs_dev || !peak_idx_dev) return fail(SPIIR_EINVAL, "NULL argument");
+    if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan has no peaks");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaError_t e = spiir::launch_peak_out(p->peak_best, p->peak_idx, (int64_t)p->D * p->T,
+                                           peak_abs_dev, peak_idx_dev, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "peak kernel launch");
+    return SPIIR_OK;
+}
+
+spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
+                                   const float *grad_z_dev, float *grad_a_dev,
+                                   float *grad_b_dev, float *grad_x_dev, void *stream)
+{
+    (void)x_dev;
+    (void)n;
+    (void)grad_z_dev;
+    (void)grad_a_dev;
+    (void)grad_b_dev;
+    (void)grad_x_dev;
+    (void)stream;
+    if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
+    return fail(SPIIR_EUNSUPPORTED, "backward not built yet");
+}
+
+spiir_status spiir_state_get(spiir_plan *p, float *state, float *history, int64_t *samples)
+{
+    if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
+    if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan has no state");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    if (state) {
+        std::memset(state, 0, sizeof(float) * 2 * (size_t)p->D * p->Ltot);
+        for (const Band &b : p->bands) {
+            const spiir::Layout &L = b.lay;
+            std::vector<float> dev((size_t)2 * p->D * L.n_slots);
+            e = cudaMemcpy(dev.data(), b.state, dev.size() * sizeof(float),
+                           cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) return cuda_fail(e, "state copy");
+            for (int det = 0; det < p->D; ++det)
+                for (int64_t s = 0; s < L.n_slots; ++s) {
+                    const int64_t f = L.slot_filter[s];
+                    if (f < 0) continue;
+                    const float u = dev[2 * ((size_t)det * L.n_slots + s)];
+                    const float v = dev[2 * ((size_t)det * L.n_slots + s) + 1];
+                    const bool swapped = (s & 1) != 0;  // odd lane: (im, re) order
+                    state[2 * ((size_t)det * p->Ltot + f)] = swapped ? v : u;
+                    state[2 * ((size_t)det * p->Ltot + f) + 1] = swapped ? u : v;
+                }
+        }
+    }
+    if (history) {
+        const Band &b = p->bands[0];
+        e = cudaMemcpy(history, b.hist, sizeof(float) * (size_t)p->D * b.lay.Dh,
+                       cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "history copy");
+    }
+    if (samples) *samples = p->t0;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_state_set(spiir_plan *p, const float *state, const float *history,
+                             int64_t samples)
+{
+    if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
+    if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan has no state");
+    if (samples < 0) return fail(SPIIR_EINVAL, "samples must be >= 0");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    if (state) {
+        for (Band &b : p->bands) {
+            const spiir::Layout &L = b.lay;
+            std::vector<float> dev((size_t)2 * p->D * L.n_slots, 0.f);
+            for (int det = 0; det < p->D; ++det)
+                for (int64_t s = 0; s < L.n_slots; ++s) {
+                    const int64_t f = L.slot_filter[s];
+                    if (f < 0) continue;
+                    const float re = state[2 * ((size_t)det * p->Ltot + f)];
+                    const float im = state[2 * ((size_t)det * p->Ltot + f) + 1];
+                    const bool swapped = (s & 1) != 0;
+                    dev[2 * ((size_t)det * L.n_slots + s)] = swapped ? im : re;
+                    dev[2 * ((size_t)det * L.n_slots + s) + 1] = swapped ? re : im;
+                }
+            e = cudaMemcpy(b.state, dev.data(), dev.size() * sizeof(float),
+                           cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) return cuda_fail(e, "state copy");
+        }
+    }
+    if (history) {
+        Band &b = p->bands[0];
+        e = cudaMemcpy(b.hist, history, sizeof(float) * (size_t)p->D * b.lay.Dh,
+                       cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "history copy");
+    }
+    p->t0 = samples;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_check(spiir_plan *p, void *stream)
+{
+    if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
+    if (p->device < 0) return SPIIR_OK;
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int32_t word = 0;
+    e = cudaMemcpy(&word, p->err, sizeof(word), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "error word copy");
+    if (word & 3) return fail(SPIIR_ETIMEOUT, "a bounded device wait gave up (error word " +
+                                                  std::to_string(word) + ")");
+    if (word) return fail(SPIIR_ECUDA, "device error word " + std::to_string(word));
+    return SPIIR_OK;
+}
+
+spiir_status spiir_selftest_bounded_wait(spiir_plan *p, uint64_t limit_ns, void *stream)
+{
+    if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
+    if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan");
+    if (limit_ns == 0 || limit_ns > 10000000000ull)
+        return fail(SPIIR_EINVAL, "limit_ns must be in (0, 1e10]");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaError_t e = spiir::launch_bounded_wait_probe(p->err, limit_ns, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "probe launch");
+    return SPIIR_OK;
+}
+
+}  // extern "C"

@@ -19,56 +19,93 @@ struct Cell {
 };
 
 // Place the filters `fl` of one template into F rounds x 32 lanes.  Filter l
-// read through copy c hits bank (c*CS - d_l) mod 32 at every sample (the ring
-// length, history and block length are multiples of 32).  Greedy: each filter
-// goes to the round with the most free lanes among those where one of its C
-// banks is still free; if there is none it takes a free lane anyway (a bank
-// conflict).  Empty cells become padding filters (a = b = 0) whose delay is
-// chosen to hit a bank nobody in the round uses.  Returns the number of
-// conflicting placements; *wavefronts gets the summed worst-bank load.
+// read through ring copy c hits bank (c*CS - d_l) mod 32 at every sample (the
+// ring length, history and block length are multiples of 32), and copy c is
+// offset by c * (32/C) banks, so filter l can use any of the C banks of its
+// class (-d_l) mod (32/C).  A round is conflict-free when its 32 lanes use 32
+// different banks.  Each bank can therefore take F filters (one per round):
+// the filters of a class are dealt round-robin over the class's C banks,
+// filling rounds from 0 upwards.  Filters beyond a class's C*F capacity
+// (unavoidable conflicts) are packed into the last rounds, so that as few
+// rounds as possible pay a second shared-memory wavefront.  Empty cells
+// become padding filters (a = b = 0) whose delay hits a bank unused in their
+// round.  Returns the number of overflow filters; *wavefronts gets the summed
+// worst-bank load over the rounds.
 int place_template(const std::vector<int64_t> &fl, const int32_t *d, int F, int C, int CS,
                    std::vector<Cell> &cells, double *wavefronts)
 {
     cells.assign((size_t)F * 32, Cell());
-    std::vector<uint32_t> used(F, 0u);
-    std::vector<int> nfree(F, 32);
-    int conflicts = 0;
-    for (int64_t l : fl) {
+    const int width = 32 / C;                      // number of classes
+    std::vector<std::vector<int64_t>> cls(width);
+    for (int64_t l : fl) cls[mod32(-(int64_t)d[l]) % width].push_back(l);
+    std::vector<int> load((size_t)F * 32, 0);      // filters per (round, bank)
+    std::vector<char> lane_used((size_t)F * 32, 0);
+    auto copy_for_bank = [&](int bank, int dl) {   // c with (c*CS - dl) mod 32 == bank
+        for (int c = 0; c < C; ++c)
+            if (mod32((int64_t)c * CS - dl) == bank) return c;
+        return 0;
+    };
+    std::vector<int64_t> overflow;
+    for (int r0 = 0; r0 < width; ++r0) {
+        const std::vector<int64_t> &v = cls[r0];
+        for (size_t i = 0; i < v.size(); ++i) {
+            const int round = (int)(i / C);
+            if (round >= F) {
+                overflow.push_back(v[i]);
+                continue;
+            }
+            const int dl = d[v[i]];
+            const int bank = (r0 + (int)(i % C) * width) % 32;
+            Cell &cell = cells[(size_t)round * 32 + bank];  // lane = bank
+            cell.filter = v[i];
+            cell.delay = dl;
+            cell.copy = copy_for_bank(bank, dl);
+            load[(size_t)round * 32 + bank] += 1;
+            lane_used[(size_t)round * 32 + bank] = 1;
+        }
+    }
+    // overflow: last rounds first, least-loaded bank of the filter's class
+    for (int64_t l : overflow) {
         const int dl = d[l];
-        int br = -1, bc = -1;
-        for (int r = 0; r < F; ++r) {
-            if (nfree[r] == 0) continue;
-            if (br >= 0 && nfree[r] <= nfree[br]) continue;
+        int best_r = -1, best_bank = -1, best_cost = 1 << 30;
+        for (int r = F - 1; r >= 0; --r) {
+            int free_lanes = 0;
+            int worst = 0;
+            for (int i = 0; i < 32; ++i) {
+                free_lanes += !lane_used[(size_t)r * 32 + i];
+                worst = std::max(worst, load[(size_t)r * 32 + i]);
+            }
+            if (free_lanes == 0) continue;
             for (int c = 0; c < C; ++c) {
-                int bank = mod32((int64_t)c * CS - dl);
-                if (!((used[r] >> bank) & 1u)) {
-                    br = r;
-                    bc = c;
-                    break;
+                const int bank = mod32((int64_t)c * CS - dl);
+                const int after = load[(size_t)r * 32 + bank] + 1;
+                const int cost = std::max(0, after - worst);  // added wavefronts
+                if (cost < best_cost) {
+                    best_cost = cost;
+                    best_r = r;
+                    best_bank = bank;
                 }
             }
+            if (best_cost == 0) break;
         }
-        if (br < 0) {  // no conflict-free cell: most free round, copy 0
-            for (int r = 0; r < F; ++r)
-                if (nfree[r] > 0 && (br < 0 || nfree[r] > nfree[br])) br = r;
-            bc = 0;
-            ++conflicts;
-        }
-        int lane = 32 - nfree[br];
-        Cell &cell = cells[(size_t)br * 32 + lane];
+        int lane = 0;
+        while (lane_used[(size_t)best_r * 32 + lane]) ++lane;
+        Cell &cell = cells[(size_t)best_r * 32 + lane];
         cell.filter = l;
-        cell.copy = bc;
         cell.delay = dl;
-        used[br] |= 1u << mod32((int64_t)bc * CS - dl);
-        --nfree[br];
+        cell.copy = copy_for_bank(best_bank, dl);
+        load[(size_t)best_r * 32 + best_bank] += 1;
+        lane_used[(size_t)best_r * 32 + lane] = 1;
     }
-    // padding: a free bank per empty lane, copy 0, delay < 32
+    // padding: every empty lane gets a bank nobody in its round uses
     for (int r = 0; r < F; ++r) {
-        for (int lane = 32 - nfree[r]; lane < 32; ++lane) {
+        for (int lane = 0; lane < 32; ++lane) {
+            if (lane_used[(size_t)r * 32 + lane]) continue;
             int bank = 0;
-            while (bank < 32 && ((used[r] >> bank) & 1u)) ++bank;
-            if (bank == 32) bank = 0;
-            used[r] |= 1u << bank;
+            while (bank < 32 && load[(size_t)r * 32 + bank] > 0) ++bank;
+            if (bank == 32) bank = lane;
+            load[(size_t)r * 32 + bank] += 1;
+            lane_used[(size_t)r * 32 + lane] = 1;
             Cell &cell = cells[(size_t)r * 32 + lane];
             cell.filter = -1;
             cell.copy = 0;
@@ -93,7 +130,7 @@ int place_template(const std::vector<int64_t> &fl, const int32_t *d, int F, int 
         wf += worst;
     }
     *wavefronts = wf;
-    return conflicts;
+    return (int)overflow.size();
 }
 
 }  // namespace

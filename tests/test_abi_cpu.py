@@ -1,0 +1,121 @@
+"""C-ABI checks that need no GPU: the library loads, exports every function
+include/spiir.h declares, validates banks, and builds a correct slot layout
+(host-only plans, device = -1)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1602_05573_b300 as sp
+from spiir_inputs import Bank, make_bank, workload_bank
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(spiir_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_every_declared_function_is_exported():
+    lib = sp.library()
+    names = declared_functions()
+    assert len(names) >= 15
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) <= set(sp.SYMBOLS) | set(names)
+
+
+def test_status_strings():
+    lib = sp.library()
+    for st in range(6):
+        assert lib.spiir_status_str(st)
+
+
+def bank_of(off, a, b, d, n_det=1):
+    return Bank(np.asarray(off, np.int64), np.asarray(a, np.complex64),
+                np.asarray(b, np.complex64), np.asarray(d, np.int32), n_det)
+
+
+@pytest.mark.parametrize("bad,status", [
+    (dict(a=[1.0 + 0j]), sp.EINVAL),           # |a| = 1
+    (dict(a=[0.8 + 0.7j]), sp.EINVAL),         # |a| > 1
+    (dict(d=[-1]), sp.EINVAL),                 # negative delay
+    (dict(b=[np.nan + 0j]), sp.EINVAL),        # non-finite gain
+    (dict(off=[0, 2]), None),                  # CSR inconsistent with arrays -> below
+])
+def test_invalid_banks_rejected(bad, status):
+    kw = dict(off=[0, 1], a=[0.5 + 0j], b=[1 + 0j], d=[0])
+    kw.update(bad)
+    if status is None:
+        kw = dict(off=[0, 1, 0], a=[0.5 + 0j], b=[1 + 0j], d=[0])  # decreasing offsets
+        status = sp.EINVAL
+    with pytest.raises(sp.SpiirError) as e:
+        sp.Plan(bank_of(**kw), device=-1)
+    assert e.value.status == status
+
+
+def test_template_too_large_is_unsupported():
+    bank = make_bank(1, 321, (0.9, 0.99), 10, seed=1)
+    with pytest.raises(sp.SpiirError) as e:
+        sp.Plan(bank, device=-1)
+    assert e.value.status == sp.EUNSUPPORTED
+
+
+def test_bad_options_rejected():
+    bank = make_bank(2, 8, (0.9, 0.99), 10, seed=1)
+    for kw in [dict(block_len=48), dict(ring_copies=3), dict(warps_per_cta=9)]:
+        with pytest.raises(sp.SpiirError) as e:
+            sp.Plan(bank, device=-1, **kw)
+        assert e.value.status in (sp.EINVAL, sp.EUNSUPPORTED)
+
+
+def test_host_only_plan_refuses_compute():
+    bank = make_bank(2, 8, (0.9, 0.99), 10, seed=1)
+    p = sp.Plan(bank, device=-1)
+    lib = sp.library()
+    assert lib.spiir_filter(p.handle, None, 16, None, None) == sp.EINVAL
+    assert lib.spiir_reset(p.handle, None) == sp.EINVAL
+
+
+@pytest.mark.parametrize("counts,W,C", [
+    ([1, 31, 32, 33, 64, 65, 100, 320], 0, 4),
+    ([5] * 37, 4, 2),
+    ([0, 3, 200, 17], 2, 1),
+])
+def test_slot_layout_covers_every_filter_once(counts, W, C):
+    rng = np.random.default_rng(3)
+    off = np.zeros(len(counts) + 1, np.int64)
+    off[1:] = np.cumsum(counts)
+    L = int(off[-1])
+    a = (rng.uniform(0.5, 0.99, L) * np.exp(1j * rng.uniform(0, np.pi, L))).astype(np.complex64)
+    b = (rng.standard_normal(L) + 1j * rng.standard_normal(L)).astype(np.complex64)
+    d = rng.integers(0, 700, L).astype(np.int32)
+    p = sp.Plan(Bank(off, a, b, d, 2), device=-1, warps_per_cta=W, ring_copies=C)
+    sf, st = p.slots()
+    real = sf[sf >= 0]
+    assert np.array_equal(np.sort(real), np.arange(L))
+    # every real slot serves the template that owns the filter
+    tmpl_of = np.repeat(np.arange(len(counts)), counts)
+    assert np.array_equal(st[sf >= 0], tmpl_of[sf[sf >= 0]])
+    info = p.info()
+    assert info["n_units"] * info["warps_per_cta"] >= len(counts) * 2
+    assert info["history_len"] >= int(d.max())
+    assert info["history_len"] % info["block_len"] == 0
+    assert 1.0 <= info["bank_conflict_ratio"] <= 4.0
+
+
+def test_batched_layout_statistics():
+    """The 4096-template bank packs with < 10% padding and few bank conflicts."""
+    p = sp.Plan(workload_bank("batched"), device=-1)
+    info = p.info()
+    assert info["n_slots"] / info["n_filters"] < 1.10
+    assert info["bank_conflict_ratio"] < 1.4
+    assert info["smem_bytes"] <= 227 * 1024
