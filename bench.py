@@ -1,0 +1,364 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the SPIIR filter bank on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batched|plain|adjoint|precision]
+
+Workload (default): the batched bank -- 4096 templates with 100..300 complex
+single-pole filters each, 3 detectors, 65536 samples (64 s at 1024 Hz) of
+white N(0,1) strain, synthetic and seeded.  One step = one spiir_filter call
+over the 64 s block (strain staging, recurrence, filter sum, z store of
+6.4 GB, running peak) plus spiir_peak.  The stream continues across steps.
+
+Metric: complex IIR filter-updates/s (one update = one filter advanced by one
+sample), whole job over all ranks.  N > 1: one process per GPU (torchrun);
+templates are independent, so each rank filters its own 4096-template shard
+(weak scaling) with no collective on the data path.
+
+Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(the reference arm of this build) on the host cores, each step a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from spiir_inputs import WORKLOADS, updates, workload_bank, workload_strain  # noqa: E402
+
+LANE_OPS_PER_UPDATE = 8      # 4 FMA + 2 MUL + 2 ADD (FP32 lane operations)
+B300_SMS = 148
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="batched",
+                    choices=["batched", "plain", "adjoint", "precision"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def describe(name, bank, n):
+    w = WORKLOADS[name]
+    counts = bank.counts()
+    return {
+        "workload": f"{name} bank: {bank.n_templates} templates x "
+                    f"{int(counts.min())}..{int(counts.max())} filters x {bank.n_det} "
+                    f"detectors x {n} samples @ {w['rate']} Hz",
+        "templates": bank.n_templates, "filters": bank.n_filters, "detectors": bank.n_det,
+        "samples": n, "rate_hz": w["rate"], "pole_r": list(w["r_range"]),
+        "max_delay": w["d_max"],
+    }
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------ clocks ---
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------ CPU baseline ---
+def cpu_baseline(name, bank, x, seconds=15.0):
+    """The FP64 oracle, as it stands, on the host cores: a bounded sample of
+    the workload's templates (all detectors, full length)."""
+    import oracle
+    n = x.shape[1]
+    cal = bank.subset(range(min(4, bank.n_templates)))
+    t = time.perf_counter()
+    oracle.filter_bank(cal.off, cal.a, cal.b, cal.d, x, want_z=False)
+    rate = updates(cal, n) / (time.perf_counter() - t)
+    per_t = updates(bank, n) / bank.n_templates
+    k = int(max(1, min(bank.n_templates, seconds * rate / per_t)))
+    sub = bank.subset(range(k))
+    t = time.perf_counter()
+    oracle.filter_bank(sub.off, sub.a, sub.b, sub.d, x, want_z=False)
+    dt = time.perf_counter() - t
+    return {"value": updates(sub, n) / dt, "unit": "filter-updates/s",
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"first {k} of {bank.n_templates} templates, all {bank.n_det} "
+                      f"detectors, {n} samples ({dt:.1f} s of CPU time, FP64, "
+                      f"OpenMP over template x detector)"}
+
+
+# --------------------------------------------------------- reference ---
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import oracle
+    bank = workload_bank(args.workload)
+    x = workload_strain(args.workload)
+    n = x.shape[1]
+    # size each step to ~3 s of host time
+    cal = bank.subset(range(2))
+    t = time.perf_counter()
+    oracle.filter_bank(cal.off, cal.a, cal.b, cal.d, x, want_z=False)
+    rate = updates(cal, n) / (time.perf_counter() - t)
+    per_t = updates(bank, n) / bank.n_templates
+    k = int(max(1, min(bank.n_templates, 3.0 * rate / per_t)))
+    times = []
+    for step in range(args.warmup + args.steps):
+        lo = (step * k) % max(1, bank.n_templates - k)
+        sub = bank.subset(range(lo, lo + k))
+        t = time.perf_counter()
+        oracle.filter_bank(sub.off, sub.a, sub.b, sub.d, x, want_z=False)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            times.append((updates(sub, n), dt))
+    total_u = sum(u for u, _ in times)
+    total_t = sum(t for _, t in times)
+    value = total_u / total_t
+    sample = (f"{k} templates of {bank.n_templates} per step, all {bank.n_det} detectors, "
+              f"{n} samples; FP64, OpenMP over template x detector")
+    line = {
+        "impl": "reference", "metric": "filter-updates/s", "value": value,
+        "unit": "filter-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_t / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded)", "config": describe(args.workload, bank, n),
+        "cpu_baseline": {"value": value, "unit": "filter-updates/s",
+                         "cores": oracle.max_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "filter-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# -------------------------------------------------------------- ours ---
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1602_05573_b300 as sp
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    from spiir_inputs import WORKLOADS as W_, make_bank
+    w = W_[args.workload]
+    if rank == 0:
+        bank = workload_bank(args.workload)
+    else:  # this rank's shard of a world x larger bank (independent templates)
+        bank = make_bank(w["n_templates"], w["filters"], w["r_range"], w["d_max"],
+                         w["seed"] + 1000 * rank, w["n_det"])
+    x_host = workload_strain(args.workload)
+    n = x_host.shape[1]
+    T, D = bank.n_templates, bank.n_det
+    upd = updates(bank, n)
+
+    plan = sp.Plan(bank, device=local_rank)
+    stream = torch.cuda.Stream(device=dev)
+    x = torch.from_numpy(x_host).to(dev)
+    z = torch.empty((D, T, n), dtype=torch.complex64, device=dev)
+    pa = torch.empty((D, T), dtype=torch.float32, device=dev)
+    pi = torch.empty((D, T), dtype=torch.int64, device=dev)
+    lib = sp.library()
+    sh = stream.cuda_stream
+
+    def step():
+        st = lib.spiir_filter(plan.handle, x.data_ptr(), n, z.data_ptr(), sh)
+        st |= lib.spiir_peak(plan.handle, pa.data_ptr(), pi.data_ptr(), sh)
+        if st != 0:
+            raise RuntimeError("spiir call failed: " + lib.spiir_last_error_detail().decode())
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if dist is not None:
+            dist.barrier()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+        with ClockSampler(local_rank) as clk:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            for i in range(args.steps):
+                ev[i][0].record(stream)
+                lib.spiir_filter(plan.handle, x.data_ptr(), n, z.data_ptr(), sh)
+                ev[i][1].record(stream)
+                lib.spiir_peak(plan.handle, pa.data_ptr(), pi.data_ptr(), sh)
+            t1.record(stream)
+            barrier()
+        plan.check(stream)
+    total_ms = t0.elapsed_time(t1)
+    filt_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    if dist is not None:
+        tt = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_step = total_ms / args.steps
+    value = upd * world * args.steps / (total_ms / 1e3)
+
+    # end to end through the public API: pinned host strain in, peaks out
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_host).pin_memory()
+        pah = torch.empty((D, T), dtype=torch.float32).pin_memory()
+        pih = torch.empty((D, T), dtype=torch.int64).pin_memory()
+        with torch.cuda.stream(stream):
+            def e2e_step():
+                x.copy_(xh, non_blocking=True)
+                plan.filter(x, z, stream=stream)
+                plan.peak(pa, pi, stream=stream)
+                pah.copy_(pa, non_blocking=True)
+                pih.copy_(pi, non_blocking=True)
+            for _ in range(2):
+                e2e_step()
+            barrier()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            for _ in range(args.steps):
+                e2e_step()
+            a1.record(stream)
+            barrier()
+        e_ms = a0.elapsed_time(a1)
+        if dist is not None:
+            tt = torch.tensor([e_ms], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e_ms = float(tt.item())
+        e2e = {"value": upd * world * args.steps / (e_ms / 1e3), "unit": "filter-updates/s",
+               "h2d_bytes_per_step": int(xh.numel() * 4),
+               "d2h_bytes_per_step": int(pah.numel() * 4 + pih.numel() * 8),
+               "ms_per_step": e_ms / args.steps}
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    info = plan.info()
+    clocks = clk.summary()
+    peaks = measured_peaks()
+    sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2032.0
+    peak_lane = B300_SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12   # T lane-ops/s
+    achieved = LANE_OPS_PER_UPDATE * upd / (filt_ms / 1e3) / 1e12
+    line = {
+        "metric": "filter-updates/s", "value": value, "unit": "filter-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded N(0,1) strain, random poles/gains/delays)",
+        "config": dict(describe(args.workload, bank, n),
+                       parallelism=f"template shards x{world}" if world > 1 else "1 GPU",
+                       l2="each step writes the 6.4 GB z series (> 126 MB L2), which "
+                          "evicts the previous step; the 0.8 MB strain stays L2-resident "
+                          "as in streaming use",
+                       plan={k: info[k] for k in ("warps_per_cta", "block_len", "ring_copies",
+                                                  "history_len", "smem_bytes",
+                                                  "bank_conflict_ratio", "n_slots")}),
+        "roofline": {"bound": "alu", "kernel": "k1_plain", "achieved": achieved,
+                     "peak": peak_lane, "unit": "T FP32 lane-ops/s",
+                     "frac": achieved / peak_lane, "traffic": None,
+                     "note": f"8 lane-ops per filter-update x {upd:.4g} updates per launch / "
+                             f"mean spiir_filter time {filt_ms:.3f} ms; peak = 148 SMs x 128 "
+                             f"FP32 lanes x {sm_max:.0f} MHz (derived; of measured max clock)"},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "filter_ms": filt_ms,
+        "templates_realtime": upd * world / (ms_step / 1e3) / (bank.n_filters / T * D)
+                              / WORKLOADS[args.workload]["rate"],
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, bank, x_host)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

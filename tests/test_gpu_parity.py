@@ -1,0 +1,211 @@
+"""Parity of the CUDA filter path (through the C-ABI) with the FP64 oracle.
+
+Every test runs spiir_plan_create / spiir_filter / spiir_peak on the GPU and
+compares element by element with oracle.filter_bank on the same seeded
+inputs.  Tolerances and the peak rule are in parity_util.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from parity_util import REL_TOL, check_peaks, rel_errors
+from spiir_inputs import Bank, make_bank, make_strain, workload_bank, workload_strain
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sp(cuda_device):
+    import paper_1602_05573_b300
+    return paper_1602_05573_b300
+
+
+def run_gpu(sp, bank, x, chunks=None, **opts):
+    plan = sp.Plan(bank, **opts)
+    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    n = x.shape[1]
+    if chunks is None:
+        z = plan.filter(xt).cpu().numpy()
+    else:
+        parts, at = [], 0
+        for c in chunks + [n - sum(chunks)]:
+            parts.append(plan.filter(xt[:, at:at + c].contiguous()).cpu().numpy())
+            at += c
+        z = np.concatenate(parts, axis=-1)
+    pa, pi = plan.peak()
+    plan.check()
+    return z, pa.cpu().numpy(), pi.cpu().numpy(), plan
+
+
+def oracle_z(bank, x):
+    z, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
+    return z
+
+
+def assert_parity(z, pa, pi, zref, t0=0):
+    rel, _ = rel_errors(z, zref)
+    assert rel.max() <= REL_TOL, f"max rel error {rel.max():.3e}"
+    check_peaks(z, zref, pa, pi, t0)
+    return rel.max()
+
+
+def test_plain_workload_full_size(sp):
+    """16 templates x 64 filters, 16384 samples (the plain workload)."""
+    bank = workload_bank("plain")
+    x = workload_strain("plain")
+    z, pa, pi, _ = run_gpu(sp, bank, x)
+    assert_parity(z, pa, pi, oracle_z(bank, x))
+
+
+@pytest.mark.parametrize("n", [1, 7, 8, 9, 31, 255, 256, 257, 1000, 4099])
+def test_ragged_lengths(sp, n):
+    bank = make_bank(5, (20, 90), (0.99, 0.9995), 300, seed=40 + n)
+    x = make_strain(1, n, seed=41)
+    z, pa, pi, _ = run_gpu(sp, bank, x)
+    assert_parity(z, pa, pi, oracle_z(bank, x))
+
+
+def test_template_size_edges(sp):
+    """Templates at and around the warp (32) and per-lane (32 F) boundaries."""
+    counts = [1, 2, 31, 32, 33, 63, 64, 65, 100, 255, 256, 257, 300, 320]
+    rng = np.random.default_rng(50)
+    off = np.zeros(len(counts) + 1, np.int64)
+    off[1:] = np.cumsum(counts)
+    L = int(off[-1])
+    r = rng.uniform(0.99, 0.9995, L)
+    a = (r * np.exp(1j * rng.uniform(0, np.pi, L))).astype(np.complex64)
+    b = ((rng.standard_normal(L) + 1j * rng.standard_normal(L)) / 64).astype(np.complex64)
+    d = rng.integers(0, 1500, L).astype(np.int32)
+    bank = Bank(off, a, b, d, 1)
+    x = make_strain(1, 3005, seed=51)
+    z, pa, pi, _ = run_gpu(sp, bank, x)
+    assert_parity(z, pa, pi, oracle_z(bank, x))
+
+
+def test_delay_edges(sp):
+    """d = 0 everywhere; delays past the end of the call (z = 0 there)."""
+    n = 700
+    bank = make_bank(3, 40, (0.99, 0.999), 0, seed=52)
+    x = make_strain(1, n, seed=53)
+    z, pa, pi, _ = run_gpu(sp, bank, x)
+    assert_parity(z, pa, pi, oracle_z(bank, x))
+    far = make_bank(2, 10, (0.99, 0.999), 10, seed=54)
+    far.d[:] = n + 5  # nothing reaches the output in this call
+    z, pa, pi, _ = run_gpu(sp, far, x)
+    assert not np.any(z)
+    assert np.all(pa == 0) and np.all(pi == 0)
+
+
+def test_multi_detector_batched_shape(sp):
+    """The batched workload's distributions (100..300 filters, delays up to
+    4096, 3 detectors) on 64 templates and 9000 samples."""
+    bank = make_bank(64, (100, 300), (0.99, 0.9999), 4096, seed=55, n_det=3)
+    x = make_strain(3, 9000, seed=56)
+    z, pa, pi, plan = run_gpu(sp, bank, x)
+    assert_parity(z, pa, pi, oracle_z(bank, x))
+
+
+@pytest.mark.parametrize("W,C,Tb", [(1, 1, 32), (2, 2, 64), (8, 4, 128), (4, 4, 512),
+                                    (3, 2, 1024)])
+def test_launch_options_agree_with_oracle(sp, W, C, Tb):
+    bank = make_bank(13, (30, 200), (0.99, 0.9995), 900, seed=57, n_det=2)
+    x = make_strain(2, 2500, seed=58)
+    z, pa, pi, _ = run_gpu(sp, bank, x, warps_per_cta=W, ring_copies=C, block_len=Tb)
+    assert_parity(z, pa, pi, oracle_z(bank, x))
+
+
+def test_streaming_calls_equal_one_call(sp):
+    """Consecutive calls continue the stream: bit-identical to one call."""
+    bank = make_bank(9, (20, 150), (0.99, 0.9995), 1200, seed=59, n_det=2)
+    x = make_strain(2, 5000, seed=60)
+    z1, pa1, pi1, _ = run_gpu(sp, bank, x)
+    z2, pa2, pi2, _ = run_gpu(sp, bank, x, chunks=[1, 100, 3, 256, 1000, 7])
+    assert np.array_equal(z1, z2)
+    assert np.array_equal(pa1, pa2) and np.array_equal(pi1, pi2)
+    assert_parity(z2, pa2, pi2, oracle_z(bank, x))
+
+
+def test_state_export_import_resumes(sp):
+    bank = make_bank(6, (10, 80), (0.99, 0.999), 500, seed=61, n_det=2)
+    x = make_strain(2, 3000, seed=62)
+    xt = torch.from_numpy(x).cuda()
+    p1 = sp.Plan(bank)
+    p1.filter(xt[:, :1700].contiguous())
+    state, hist, t = p1.state_get()
+    assert t == 1700
+    ref = p1.filter(xt[:, 1700:].contiguous()).cpu().numpy()
+    p2 = sp.Plan(bank)
+    p2.state_set(state, hist, t)
+    got = p2.filter(xt[:, 1700:].contiguous()).cpu().numpy()
+    assert np.array_equal(ref, got)
+    # the exported state is y_l at the last sample: check one filter by the oracle
+    zr, _, _ = oracle.filter_bank(np.arange(bank.n_filters + 1), bank.a, bank.b, bank.d,
+                                  x[:, :1700])
+    want = zr[:, :, -1]
+    assert np.abs(state - want).max() <= 1e-4 * np.abs(want).max()
+
+
+def test_peak_without_z_output(sp):
+    bank = make_bank(7, (20, 64), (0.99, 0.999), 200, seed=63)
+    x = make_strain(1, 2000, seed=64)
+    z, pa, pi, _ = run_gpu(sp, bank, x)
+    plan = sp.Plan(bank)
+    assert plan.filter(torch.from_numpy(x).cuda(), emit_z=False) is None
+    pa2, pi2 = plan.peak()
+    assert np.array_equal(pa, pa2.cpu().numpy()) and np.array_equal(pi, pi2.cpu().numpy())
+
+
+def test_reset_restarts_stream(sp):
+    bank = make_bank(4, 30, (0.99, 0.999), 100, seed=65)
+    x = torch.from_numpy(make_strain(1, 1500, seed=66)).cuda()
+    plan = sp.Plan(bank)
+    z1 = plan.filter(x).cpu().numpy()
+    plan.reset()
+    z2 = plan.filter(x).cpu().numpy()
+    assert np.array_equal(z1, z2)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(sp):
+    """A device wait on a barrier nothing completes gives up by itself; the
+    host reads ETIMEOUT and the context stays usable."""
+    bank = make_bank(2, 8, (0.9, 0.99), 10, seed=67)
+    plan = sp.Plan(bank)
+    plan.check()
+    rc = sp.library().spiir_selftest_bounded_wait(plan.handle, 2_000_000, None)
+    assert rc == sp.OK
+    with pytest.raises(sp.SpiirError) as e:
+        plan.check()
+    assert e.value.status == sp.ETIMEOUT
+    plan.reset()
+    plan.check()
+    x = make_strain(1, 300, seed=68)
+    z = plan.filter(torch.from_numpy(x).cuda()).cpu().numpy()
+    rel, _ = rel_errors(z, oracle_z(bank, x))
+    assert rel.max() <= REL_TOL
+
+
+def test_batched_workload_full_size_sampled(sp):
+    """The full batched workload (4096 templates x 100..300 filters x 3
+    detectors x 65536 samples) in the launch configuration the benchmark
+    times; 12 sampled (detector, template) series checked against the oracle
+    on the matching sub-bank."""
+    bank = workload_bank("batched")
+    x = workload_strain("batched")
+    plan = sp.Plan(bank)
+    xt = torch.from_numpy(x).cuda()
+    z = plan.filter(xt)
+    pa, pi = plan.peak()
+    plan.check()
+    rng = np.random.default_rng(70)
+    picks = [(int(rng.integers(0, 3)), int(t)) for t in rng.choice(4096, 12, replace=False)]
+    for det, t in picks:
+        sub = bank.subset([t])
+        zref, _, _ = oracle.filter_bank(sub.off, sub.a, sub.b, sub.d, x[det:det + 1])
+        zg = z[det, t].cpu().numpy()[None, None]
+        rel, _ = rel_errors(zg, zref)
+        assert rel.max() <= REL_TOL, (det, t, rel.max())
+        check_peaks(zg, zref, pa[det, t].cpu().numpy()[None, None],
+                    pi[det, t].cpu().numpy()[None, None])
+    del z
+    torch.cuda.empty_cache()
