@@ -139,7 +139,8 @@ def cpu_baseline(name, bank, x, seconds=15.0):
     the workload's templates (all detectors, full length)."""
     import oracle
     n = x.shape[1]
-    cal = bank.subset(range(min(4, bank.n_templates)))
+    # calibrate on enough templates to occupy every core
+    cal = bank.subset(range(min(bank.n_templates, 2 * oracle.max_threads())))
     t = time.perf_counter()
     oracle.filter_bank(cal.off, cal.a, cal.b, cal.d, x, want_z=False)
     rate = updates(cal, n) / (time.perf_counter() - t)
@@ -165,7 +166,7 @@ def run_reference(args, rank, world):
     x = workload_strain(args.workload)
     n = x.shape[1]
     # size each step to ~3 s of host time
-    cal = bank.subset(range(2))
+    cal = bank.subset(range(min(bank.n_templates, 2 * oracle.max_threads())))
     t = time.perf_counter()
     oracle.filter_bank(cal.off, cal.a, cal.b, cal.d, x, want_z=False)
     rate = updates(cal, n) / (time.perf_counter() - t)
@@ -337,6 +338,8 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
         "filter_ms": filt_ms,
+        # templates (all detectors, mean filter count) whose 1 s of data is
+        # filtered in 1 s at this throughput
         "templates_realtime": upd * world / (ms_step / 1e3) / (bank.n_filters / T * D)
                               / WORKLOADS[args.workload]["rate"],
     }
