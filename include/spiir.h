@@ -227,6 +227,40 @@ spiir_status spiir_check(spiir_plan *plan, void *stream);
  */
 spiir_status spiir_selftest_bounded_wait(spiir_plan *plan, uint64_t limit_ns, void *stream);
 
+/*
+ * One-shot filter call that allocates no device memory.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc or cudaFree -- for instance a process whose device memory is
+ * owned by another allocator or a fixed budget, or a low-latency pipeline
+ * that must not allocate while it streams -- and therefore cannot create a
+ * plan (spiir_plan_create allocates the packed parameters and workspace).
+ *
+ * It runs the plain FP32 kernel of spiir_filter, on the layout a default
+ * plan would use, from zero state (no streaming, single-rate banks only),
+ * and keeps all of its scratch (packed parameters, filter state, staged
+ * strain, running peaks) in one static device array of 32 MiB that every
+ * GPU loading this library holds until the process exits.
+ *   bank          host bank description, as for spiir_plan_create
+ *   x_dev         [n_detectors][n] float32 strain, 1 <= n <= 2^30
+ *   z_dev         [n_detectors][n_templates][n] complex64 output, or NULL
+ *   peak_abs_dev  [n_detectors][n_templates] float32 max |z|
+ *   peak_idx_dev  [n_detectors][n_templates] int64 first index of the max
+ *                 (-1 would mean that template was not filtered because a
+ *                 bounded device wait gave up)
+ * Runs on the caller's current device and `stream`.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  Every call reuses the same
+ * array and clears what must start at zero; calls whose GPU work overlaps
+ * (different streams, or different host threads, without ordering) race on
+ * the array and must be serialized by the caller.
+ * Errors: EINVAL (bad bank or sizes, or a problem needing more than the
+ * 32 MiB of scratch -- the message gives the bytes needed), EUNSUPPORTED
+ * (multirate bank, device not sm_103), ECUDA.
+ */
+spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const float *x_dev, int64_t n,
+                                  float *z_dev, float *peak_abs_dev, int64_t *peak_idx_dev,
+                                  void *stream);
+
 /* Static description of a status code. */
 const char *spiir_status_str(spiir_status status);
 

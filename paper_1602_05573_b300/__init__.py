@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libspiir.so")
 if not os.path.exists(LIB_PATH):
     raise ImportError(
         f"SPIIR CUDA library not built ({LIB_PATH} missing); run "
-        "`python -m paper_1602_05573_b300.build` (nvcc, sm_103a)")
+        "`python paper_1602_05573_b300/build.py` (nvcc, sm_103a)")
 
 _lib = ctypes.CDLL(LIB_PATH)
 
@@ -39,7 +39,7 @@ SYMBOLS = [
     "spiir_plan_get_info", "spiir_plan_get_slots", "spiir_reset", "spiir_filter",
     "spiir_peak", "spiir_filter_backward", "spiir_state_get", "spiir_state_set",
     "spiir_check", "spiir_selftest_bounded_wait", "spiir_status_str",
-    "spiir_last_error_detail",
+    "spiir_last_error_detail", "spiir_filter_noalloc",
 ]
 
 
@@ -97,6 +97,9 @@ _lib.spiir_check.argtypes = [_P, _P]
 _lib.spiir_check.restype = _st
 _lib.spiir_selftest_bounded_wait.argtypes = [_P, ctypes.c_uint64, _P]
 _lib.spiir_selftest_bounded_wait.restype = _st
+_lib.spiir_filter_noalloc.argtypes = [ctypes.POINTER(BankDesc), _P, ctypes.c_int64, _P, _P,
+                                      _P, _P]
+_lib.spiir_filter_noalloc.restype = _st
 _lib.spiir_status_str.argtypes = [_st]
 _lib.spiir_status_str.restype = ctypes.c_char_p
 _lib.spiir_last_error_detail.argtypes = []
@@ -134,6 +137,52 @@ def _stream_handle(stream) -> Optional[int]:
         import torch
         return torch.cuda.current_stream().cuda_stream
     return getattr(stream, "cuda_stream", stream)
+
+
+def bank_desc(bank):
+    """(BankDesc, keep-alive arrays) for a bank object (see Plan)."""
+    off = np.ascontiguousarray(bank.off, np.int64)
+    a = np.ascontiguousarray(bank.a, np.complex64).view(np.float32)
+    b = np.ascontiguousarray(bank.b, np.complex64).view(np.float32)
+    d = np.ascontiguousarray(bank.d, np.int32)
+    keep = [off, a, b, d]
+    desc = BankDesc()
+    desc.n_templates = off.shape[0] - 1
+    desc.n_detectors = int(bank.n_det)
+    desc.filter_off, desc.a_reim, desc.b_reim, desc.delay = (
+        _ptr(off), _ptr(a), _ptr(b), _ptr(d))
+    band_of = getattr(bank, "band_of", None)
+    decim = getattr(bank, "decim", None)
+    if band_of is not None and decim is not None and len(decim) > 1:
+        band_of = np.ascontiguousarray(band_of, np.int32)
+        decim = np.ascontiguousarray(decim, np.int32)
+        keep += [band_of, decim]
+        desc.n_bands = int(decim.shape[0])
+        desc.band_of_filter, desc.band_decim = _ptr(band_of), _ptr(decim)
+    return desc, keep
+
+
+def filter_noalloc(bank, x, z=None, peak_abs=None, peak_idx=None, *, emit_z=True,
+                   stream=None):
+    """One-shot filter call through spiir_filter_noalloc (no device
+    allocation inside the library; the outputs are allocated here by torch
+    unless passed in).  Returns (z or None, peak_abs, peak_idx)."""
+    import torch
+    desc, keep = bank_desc(bank)
+    D, n = x.shape
+    T = int(desc.n_templates)
+    if emit_z and z is None:
+        z = torch.empty((D, T, n), dtype=torch.complex64, device=x.device)
+    if peak_abs is None:
+        peak_abs = torch.empty((D, T), dtype=torch.float32, device=x.device)
+    if peak_idx is None:
+        peak_idx = torch.empty((D, T), dtype=torch.int64, device=x.device)
+    _check(_lib.spiir_filter_noalloc(ctypes.byref(desc), _ptr(x), n,
+                                     _ptr(z) if z is not None else None, _ptr(peak_abs),
+                                     _ptr(peak_idx), _stream_handle(stream)),
+           "spiir_filter_noalloc")
+    del keep
+    return z, peak_abs, peak_idx
 
 
 class Plan:

@@ -1,6 +1,6 @@
 """Build the SPIIR CUDA library in-tree with nvcc for sm_103a.
 
-    python -m paper_1602_05573_b300.build [--force]
+    python paper_1602_05573_b300/build.py [--force] [-v]
 
 Produces paper_1602_05573_b300/_lib/libspiir.so from csrc/*.cu and
 csrc/*.cpp (static CUDA runtime, position-independent, -lineinfo).

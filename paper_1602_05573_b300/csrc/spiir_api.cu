@@ -2,6 +2,7 @@
 // workspace, and the launch sequence of each call.  Device compute lives in
 // the kernel files; this file only validates, allocates and enqueues.
 #include "spiir.h"
+#include "spiir_internal.h"
 #include "spiir_kernels.h"
 #include "spiir_layout.h"
 
@@ -14,8 +15,11 @@
 #include <vector>
 
 namespace {
-
 thread_local std::string g_detail;
+}  // namespace
+
+namespace spiir {
+namespace detail {
 
 spiir_status fail(spiir_status st, const std::string &why)
 {
@@ -30,6 +34,61 @@ spiir_status cuda_fail(cudaError_t e, const char *what)
     (void)cudaGetLastError();  // clear a sticky launch error for the next call
     return SPIIR_ECUDA;
 }
+
+spiir_status validate_bank(const spiir_bank_desc *bank)
+{
+    if (!bank) return fail(SPIIR_EINVAL, "bank is NULL");
+    if (bank->n_templates < 1) return fail(SPIIR_EINVAL, "n_templates must be >= 1");
+    if (bank->n_detectors < 1) return fail(SPIIR_EINVAL, "n_detectors must be >= 1");
+    if (!bank->filter_off || !bank->a_reim || !bank->b_reim || !bank->delay)
+        return fail(SPIIR_EINVAL, "filter_off, a_reim, b_reim and delay are required");
+    const int64_t *off = bank->filter_off;
+    if (off[0] != 0) return fail(SPIIR_EINVAL, "filter_off[0] must be 0");
+    for (int64_t t = 0; t < bank->n_templates; ++t)
+        if (off[t + 1] < off[t])
+            return fail(SPIIR_EINVAL, "filter_off must be non-decreasing (template " +
+                                          std::to_string(t) + ")");
+    const int64_t L = off[bank->n_templates];
+    for (int64_t l = 0; l < L; ++l) {
+        const double ar = bank->a_reim[2 * l], ai = bank->a_reim[2 * l + 1];
+        const double br = bank->b_reim[2 * l], bi = bank->b_reim[2 * l + 1];
+        if (!std::isfinite(ar) || !std::isfinite(ai) || !std::isfinite(br) || !std::isfinite(bi))
+            return fail(SPIIR_EINVAL, "non-finite pole or gain at filter " + std::to_string(l));
+        if (ar * ar + ai * ai >= 1.0)
+            return fail(SPIIR_EINVAL, "|a| >= 1 (unstable pole) at filter " + std::to_string(l));
+        if (bank->delay[l] < 0)
+            return fail(SPIIR_EINVAL, "negative delay at filter " + std::to_string(l));
+    }
+    if (bank->n_bands > 1) {
+        if (!bank->band_of_filter || !bank->band_decim)
+            return fail(SPIIR_EINVAL, "multirate bank needs band_of_filter and band_decim");
+        int minR = 1 << 30;
+        for (int j = 0; j < bank->n_bands; ++j) {
+            if (bank->band_decim[j] < 1 || bank->band_decim[j] > 4096)
+                return fail(SPIIR_EINVAL, "band_decim must be in [1, 4096]");
+            minR = std::min(minR, bank->band_decim[j]);
+        }
+        if (minR != 1) return fail(SPIIR_EINVAL, "a multirate bank needs a band with decim 1");
+        for (int64_t l = 0; l < L; ++l)
+            if (bank->band_of_filter[l] < 0 || bank->band_of_filter[l] >= bank->n_bands)
+                return fail(SPIIR_EINVAL, "band_of_filter out of range at filter " +
+                                              std::to_string(l));
+    } else if (bank->n_bands == 1 && bank->band_decim && bank->band_decim[0] != 1) {
+        return fail(SPIIR_EINVAL, "a single band must have decim 1");
+    } else if (bank->n_bands < 0) {
+        return fail(SPIIR_EINVAL, "n_bands must be >= 0");
+    }
+    return SPIIR_OK;
+}
+
+}  // namespace detail
+}  // namespace spiir
+
+namespace {
+
+using spiir::detail::cuda_fail;
+using spiir::detail::fail;
+using spiir::detail::validate_bank;
 
 // Keeps the caller's current device and restores it on scope exit.
 struct DeviceGuard {
@@ -110,52 +169,6 @@ void free_band(Band &b)
     cudaFree(b.hist);
     cudaFree(b.xe);
     b = Band();
-}
-
-spiir_status validate_bank(const spiir_bank_desc *bank)
-{
-    if (!bank) return fail(SPIIR_EINVAL, "bank is NULL");
-    if (bank->n_templates < 1) return fail(SPIIR_EINVAL, "n_templates must be >= 1");
-    if (bank->n_detectors < 1) return fail(SPIIR_EINVAL, "n_detectors must be >= 1");
-    if (!bank->filter_off || !bank->a_reim || !bank->b_reim || !bank->delay)
-        return fail(SPIIR_EINVAL, "filter_off, a_reim, b_reim and delay are required");
-    const int64_t *off = bank->filter_off;
-    if (off[0] != 0) return fail(SPIIR_EINVAL, "filter_off[0] must be 0");
-    for (int64_t t = 0; t < bank->n_templates; ++t)
-        if (off[t + 1] < off[t])
-            return fail(SPIIR_EINVAL, "filter_off must be non-decreasing (template " +
-                                          std::to_string(t) + ")");
-    const int64_t L = off[bank->n_templates];
-    for (int64_t l = 0; l < L; ++l) {
-        const double ar = bank->a_reim[2 * l], ai = bank->a_reim[2 * l + 1];
-        const double br = bank->b_reim[2 * l], bi = bank->b_reim[2 * l + 1];
-        if (!std::isfinite(ar) || !std::isfinite(ai) || !std::isfinite(br) || !std::isfinite(bi))
-            return fail(SPIIR_EINVAL, "non-finite pole or gain at filter " + std::to_string(l));
-        if (ar * ar + ai * ai >= 1.0)
-            return fail(SPIIR_EINVAL, "|a| >= 1 (unstable pole) at filter " + std::to_string(l));
-        if (bank->delay[l] < 0)
-            return fail(SPIIR_EINVAL, "negative delay at filter " + std::to_string(l));
-    }
-    if (bank->n_bands > 1) {
-        if (!bank->band_of_filter || !bank->band_decim)
-            return fail(SPIIR_EINVAL, "multirate bank needs band_of_filter and band_decim");
-        int minR = 1 << 30;
-        for (int j = 0; j < bank->n_bands; ++j) {
-            if (bank->band_decim[j] < 1 || bank->band_decim[j] > 4096)
-                return fail(SPIIR_EINVAL, "band_decim must be in [1, 4096]");
-            minR = std::min(minR, bank->band_decim[j]);
-        }
-        if (minR != 1) return fail(SPIIR_EINVAL, "a multirate bank needs a band with decim 1");
-        for (int64_t l = 0; l < L; ++l)
-            if (bank->band_of_filter[l] < 0 || bank->band_of_filter[l] >= bank->n_bands)
-                return fail(SPIIR_EINVAL, "band_of_filter out of range at filter " +
-                                              std::to_string(l));
-    } else if (bank->n_bands == 1 && bank->band_decim && bank->band_decim[0] != 1) {
-        return fail(SPIIR_EINVAL, "a single band must have decim 1");
-    } else if (bank->n_bands < 0) {
-        return fail(SPIIR_EINVAL, "n_bands must be >= 0");
-    }
-    return SPIIR_OK;
 }
 
 spiir_status upload_band(Band &b, int D)
