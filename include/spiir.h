@@ -96,7 +96,9 @@ typedef struct spiir_options {
                             /* and statistics, no device memory, no compute)       */
     int32_t autotune;       /* nonzero: time candidate block/copy settings on the  */
                             /* first spiir_filter call and keep the fastest        */
-    int32_t reserved;
+    int32_t max_filters_per_lane; /* 1..10 filters held per thread; templates with */
+                            /* more than 32x this many filters span several warps; */
+                            /* 0 = default (10)                                    */
 } spiir_options;
 
 /* Plan statistics (spiir_plan_get_info). */
@@ -111,7 +113,7 @@ typedef struct spiir_plan_info {
     int32_t ring_copies;
     int32_t history_len;        /* strain samples kept between calls (>= max d)   */
     int32_t smem_bytes;         /* dynamic shared memory per CTA                  */
-    int32_t max_filters_per_lane;
+    int32_t max_filters_per_lane; /* largest filters per thread in any CTA        */
     int32_t precision;
     double bank_conflict_ratio; /* mean shared-memory wavefronts per strain load  */
 } spiir_plan_info;

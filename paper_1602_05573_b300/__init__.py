@@ -55,7 +55,7 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("chunk_len", ctypes.c_int32),
                 ("block_len", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ring_copies", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("max_filters_per_lane", ctypes.c_int32)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -70,53 +70,68 @@ class PlanInfo(ctypes.Structure):
 
 _P = ctypes.c_void_p
 _st = ctypes.c_int
-_lib.spiir_options_default.argtypes = [ctypes.POINTER(Options)]
-_lib.spiir_options_default.restype = None
-_lib.spiir_plan_create.argtypes = [ctypes.POINTER(BankDesc), ctypes.POINTER(Options),
-                                   ctypes.POINTER(_P)]
-_lib.spiir_plan_create.restype = _st
-_lib.spiir_plan_destroy.argtypes = [_P]
-_lib.spiir_plan_destroy.restype = _st
-_lib.spiir_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
-_lib.spiir_plan_get_info.restype = _st
-_lib.spiir_plan_get_slots.argtypes = [_P, _P, _P]
-_lib.spiir_plan_get_slots.restype = _st
-_lib.spiir_reset.argtypes = [_P, _P]
-_lib.spiir_reset.restype = _st
-_lib.spiir_filter.argtypes = [_P, _P, ctypes.c_int64, _P, _P]
-_lib.spiir_filter.restype = _st
-_lib.spiir_peak.argtypes = [_P, _P, _P, _P]
-_lib.spiir_peak.restype = _st
-_lib.spiir_filter_backward.argtypes = [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]
-_lib.spiir_filter_backward.restype = _st
-_lib.spiir_state_get.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int64)]
-_lib.spiir_state_get.restype = _st
-_lib.spiir_state_set.argtypes = [_P, _P, _P, ctypes.c_int64]
-_lib.spiir_state_set.restype = _st
-_lib.spiir_check.argtypes = [_P, _P]
-_lib.spiir_check.restype = _st
-_lib.spiir_selftest_bounded_wait.argtypes = [_P, ctypes.c_uint64, _P]
-_lib.spiir_selftest_bounded_wait.restype = _st
-_lib.spiir_filter_noalloc.argtypes = [ctypes.POINTER(BankDesc), _P, ctypes.c_int64, _P, _P,
-                                      _P, _P]
-_lib.spiir_filter_noalloc.restype = _st
-_lib.spiir_status_str.argtypes = [_st]
-_lib.spiir_status_str.restype = ctypes.c_char_p
-_lib.spiir_last_error_detail.argtypes = []
-_lib.spiir_last_error_detail.restype = ctypes.c_char_p
+
+
+def _configure(lib):
+    """Declare the C signatures of include/spiir.h on a loaded library."""
+    lib.spiir_options_default.argtypes = [ctypes.POINTER(Options)]
+    lib.spiir_options_default.restype = None
+    lib.spiir_plan_create.argtypes = [ctypes.POINTER(BankDesc), ctypes.POINTER(Options),
+                                       ctypes.POINTER(_P)]
+    lib.spiir_plan_create.restype = _st
+    lib.spiir_plan_destroy.argtypes = [_P]
+    lib.spiir_plan_destroy.restype = _st
+    lib.spiir_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
+    lib.spiir_plan_get_info.restype = _st
+    lib.spiir_plan_get_slots.argtypes = [_P, _P, _P]
+    lib.spiir_plan_get_slots.restype = _st
+    lib.spiir_reset.argtypes = [_P, _P]
+    lib.spiir_reset.restype = _st
+    lib.spiir_filter.argtypes = [_P, _P, ctypes.c_int64, _P, _P]
+    lib.spiir_filter.restype = _st
+    lib.spiir_peak.argtypes = [_P, _P, _P, _P]
+    lib.spiir_peak.restype = _st
+    lib.spiir_filter_backward.argtypes = [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]
+    lib.spiir_filter_backward.restype = _st
+    lib.spiir_state_get.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int64)]
+    lib.spiir_state_get.restype = _st
+    lib.spiir_state_set.argtypes = [_P, _P, _P, ctypes.c_int64]
+    lib.spiir_state_set.restype = _st
+    lib.spiir_check.argtypes = [_P, _P]
+    lib.spiir_check.restype = _st
+    lib.spiir_selftest_bounded_wait.argtypes = [_P, ctypes.c_uint64, _P]
+    lib.spiir_selftest_bounded_wait.restype = _st
+    lib.spiir_filter_noalloc.argtypes = [ctypes.POINTER(BankDesc), _P, ctypes.c_int64, _P, _P,
+                                          _P, _P]
+    lib.spiir_filter_noalloc.restype = _st
+    lib.spiir_status_str.argtypes = [_st]
+    lib.spiir_status_str.restype = ctypes.c_char_p
+    lib.spiir_last_error_detail.argtypes = []
+    lib.spiir_last_error_detail.restype = ctypes.c_char_p
+    return lib
+
+
+def load_library(path: str):
+    """Load and configure a build of the SPIIR library (e.g. another build
+    of the same sources); the package itself uses LIB_PATH."""
+    return _configure(ctypes.CDLL(path))
+
+
+_configure(_lib)
 
 
 class SpiirError(RuntimeError):
-    def __init__(self, status: int, where: str):
+    def __init__(self, status: int, where: str, lib=None):
+        lib = lib if lib is not None else _lib
         self.status = status
-        detail = _lib.spiir_last_error_detail().decode()
-        super().__init__(f"{where}: {_lib.spiir_status_str(status).decode()}"
+        detail = lib.spiir_last_error_detail().decode()
+        super().__init__(f"{where}: {lib.spiir_status_str(status).decode()}"
                          + (f" ({detail})" if detail else ""))
 
 
-def _check(status: int, where: str):
+def _check(status: int, where: str, lib=None):
     if status != OK:
-        raise SpiirError(status, where)
+        raise SpiirError(status, where, lib)
 
 
 def library():
@@ -195,8 +210,10 @@ class Plan:
 
     def __init__(self, bank, *, precision: str = "plain", device: int = 0,
                  block_len: int = 0, warps_per_cta: int = 0, ring_copies: int = 0,
-                 chunk_len: int = 256, autotune: bool = False):
+                 chunk_len: int = 256, autotune: bool = False,
+                 max_filters_per_lane: int = 0, lib=None):
         self._h = None
+        self._lib = lib if lib is not None else _lib
         off = np.ascontiguousarray(bank.off, np.int64)
         a = np.ascontiguousarray(bank.a, np.complex64).view(np.float32)
         b = np.ascontiguousarray(bank.b, np.complex64).view(np.float32)
@@ -216,7 +233,7 @@ class Plan:
             desc.n_bands = int(decim.shape[0])
             desc.band_of_filter, desc.band_decim = _ptr(band_of), _ptr(decim)
         opt = Options()
-        _lib.spiir_options_default(ctypes.byref(opt))
+        self._lib.spiir_options_default(ctypes.byref(opt))
         opt.precision = PRECISIONS[precision]
         opt.device = int(device)
         opt.block_len = int(block_len)
@@ -224,9 +241,10 @@ class Plan:
         opt.ring_copies = int(ring_copies)
         opt.chunk_len = int(chunk_len)
         opt.autotune = int(bool(autotune))
+        opt.max_filters_per_lane = int(max_filters_per_lane)
         h = _P()
-        _check(_lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
-               "spiir_plan_create")
+        _check(self._lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
+               "spiir_plan_create", self._lib)
         self._h = h
         self.device = int(device)
         self.n_templates = int(desc.n_templates)
@@ -236,7 +254,7 @@ class Plan:
     # -- lifecycle ------------------------------------------------------------
     def close(self):
         if self._h is not None and self._h.value:
-            _lib.spiir_plan_destroy(self._h)
+            self._lib.spiir_plan_destroy(self._h)
         self._h = None
 
     def __del__(self):
@@ -257,19 +275,19 @@ class Plan:
 
     def info(self) -> dict:
         inf = PlanInfo()
-        _check(_lib.spiir_plan_get_info(self._h, ctypes.byref(inf)), "spiir_plan_get_info")
+        _check(self._lib.spiir_plan_get_info(self._h, ctypes.byref(inf)), "spiir_plan_get_info", self._lib)
         return {name: getattr(inf, name) for name, _ in PlanInfo._fields_}
 
     def slots(self):
         n = self.info()["n_slots"]
         sf = np.empty(n, np.int64)
         st = np.empty(n, np.int64)
-        _check(_lib.spiir_plan_get_slots(self._h, _ptr(sf), _ptr(st)), "spiir_plan_get_slots")
+        _check(self._lib.spiir_plan_get_slots(self._h, _ptr(sf), _ptr(st)), "spiir_plan_get_slots", self._lib)
         return sf, st
 
     # -- streaming ------------------------------------------------------------
     def reset(self, stream=None):
-        _check(_lib.spiir_reset(self._h, _stream_handle(stream)), "spiir_reset")
+        _check(self._lib.spiir_reset(self._h, _stream_handle(stream)), "spiir_reset", self._lib)
 
     def filter(self, x, z=None, *, emit_z: bool = True, stream=None):
         """Filter the next samples.  x: CUDA float32 [D][n] (contiguous).
@@ -283,8 +301,8 @@ class Plan:
         if z is not None:
             assert z.is_cuda and z.dtype == torch.complex64 and z.is_contiguous()
             assert tuple(z.shape) == (D, self.n_templates, n)
-        _check(_lib.spiir_filter(self._h, _ptr(x), n, _ptr(z) if z is not None else None,
-                                 _stream_handle(stream)), "spiir_filter")
+        _check(self._lib.spiir_filter(self._h, _ptr(x), n, _ptr(z) if z is not None else None,
+                                 _stream_handle(stream)), "spiir_filter", self._lib)
         return z
 
     def peak(self, out_abs=None, out_idx=None, *, stream=None):
@@ -295,8 +313,8 @@ class Plan:
             out_abs = torch.empty((self.n_det, self.n_templates), dtype=torch.float32, device=dev)
         if out_idx is None:
             out_idx = torch.empty((self.n_det, self.n_templates), dtype=torch.int64, device=dev)
-        _check(_lib.spiir_peak(self._h, _ptr(out_abs), _ptr(out_idx), _stream_handle(stream)),
-               "spiir_peak")
+        _check(self._lib.spiir_peak(self._h, _ptr(out_abs), _ptr(out_idx), _stream_handle(stream)),
+               "spiir_peak", self._lib)
         return out_abs, out_idx
 
     def backward(self, x, grad_z, *, want_gx: bool = True, stream=None):
@@ -307,9 +325,9 @@ class Plan:
         gb = torch.empty(self.n_filters, dtype=torch.complex64, device=x.device)
         gx = torch.empty((D, n), dtype=torch.float32, device=x.device) if want_gx else None
         gz = grad_z.contiguous()
-        _check(_lib.spiir_filter_backward(self._h, _ptr(x), n, _ptr(gz), _ptr(ga), _ptr(gb),
+        _check(self._lib.spiir_filter_backward(self._h, _ptr(x), n, _ptr(gz), _ptr(ga), _ptr(gb),
                                           _ptr(gx), _stream_handle(stream)),
-               "spiir_filter_backward")
+               "spiir_filter_backward", self._lib)
         return ga, gb, gx
 
     def state_get(self):
@@ -317,16 +335,16 @@ class Plan:
         st = np.zeros((self.n_det, self.n_filters), np.complex64)
         hist = np.zeros((self.n_det, inf["history_len"]), np.float32)
         t = ctypes.c_int64()
-        _check(_lib.spiir_state_get(self._h, _ptr(st), _ptr(hist), ctypes.byref(t)),
-               "spiir_state_get")
+        _check(self._lib.spiir_state_get(self._h, _ptr(st), _ptr(hist), ctypes.byref(t)),
+               "spiir_state_get", self._lib)
         return st, hist, int(t.value)
 
     def state_set(self, state, history, samples):
         state = np.ascontiguousarray(state, np.complex64)
         history = np.ascontiguousarray(history, np.float32)
-        _check(_lib.spiir_state_set(self._h, _ptr(state), _ptr(history), int(samples)),
-               "spiir_state_set")
+        _check(self._lib.spiir_state_set(self._h, _ptr(state), _ptr(history), int(samples)),
+               "spiir_state_set", self._lib)
 
     def check(self, stream=None):
         """Wait for the plan's work; raise SpiirError(ETIMEOUT) if a bounded wait gave up."""
-        _check(_lib.spiir_check(self._h, _stream_handle(stream)), "spiir_check")
+        _check(self._lib.spiir_check(self._h, _stream_handle(stream)), "spiir_check", self._lib)

@@ -133,7 +133,7 @@ struct Band {
     int32_t *units = nullptr;
     int32_t *group_F = nullptr;
     int64_t *group_pbase = nullptr;
-    int32_t *slot_tmpl = nullptr;
+    int4 *warp_info = nullptr;
     float2 *state = nullptr;   // [D][n_slots]
     float *hist = nullptr;     // [D][Dh]
     float *xe = nullptr;       // [D][xe_stride] workspace
@@ -164,7 +164,7 @@ void free_band(Band &b)
     cudaFree(b.units);
     cudaFree(b.group_F);
     cudaFree(b.group_pbase);
-    cudaFree(b.slot_tmpl);
+    cudaFree(b.warp_info);
     cudaFree(b.state);
     cudaFree(b.hist);
     cudaFree(b.xe);
@@ -180,7 +180,7 @@ spiir_status upload_band(Band &b, int D)
         (e = dalloc(&b.units, L.units.size())) != cudaSuccess ||
         (e = dalloc(&b.group_F, L.group_F.size())) != cudaSuccess ||
         (e = dalloc(&b.group_pbase, L.group_pbase.size())) != cudaSuccess ||
-        (e = dalloc(&b.slot_tmpl, L.slot_tmpl.size())) != cudaSuccess ||
+        (e = dalloc(&b.warp_info, L.warp_info.size() / 4)) != cudaSuccess ||
         (e = dalloc(&b.state, (size_t)D * L.n_slots)) != cudaSuccess ||
         (e = dalloc(&b.hist, (size_t)D * L.Dh)) != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "device allocation failed")
@@ -192,7 +192,8 @@ spiir_status upload_band(Band &b, int D)
         (e = h2d(b.units, L.units)) != cudaSuccess ||
         (e = h2d(b.group_F, L.group_F)) != cudaSuccess ||
         (e = h2d(b.group_pbase, L.group_pbase)) != cudaSuccess ||
-        (e = h2d(b.slot_tmpl, L.slot_tmpl)) != cudaSuccess ||
+        (e = cudaMemcpy(b.warp_info, L.warp_info.data(), L.warp_info.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemset(b.state, 0, sizeof(float2) * (size_t)D * L.n_slots)) != cudaSuccess ||
         (e = cudaMemset(b.hist, 0, sizeof(float) * (size_t)D * L.Dh)) != cudaSuccess)
         return cuda_fail(e, "plan upload");
@@ -239,7 +240,8 @@ spiir::K1Args k1_args(const spiir_plan *p, const Band &b, int64_t n, float *z, i
     a.units = b.units;
     a.group_F = b.group_F;
     a.group_pbase = b.group_pbase;
-    a.slot_tmpl = b.slot_tmpl;
+    a.warp_info = b.warp_info;
+    a.fcap = L.Fcap;
     a.params = b.params;
     a.ringoff = b.ringoff;
     a.state = b.state;
@@ -338,8 +340,9 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
         decims.push_back(1);
     spiir::LayoutOptions lo;
     lo.W = opt.warps_per_cta;
-    lo.Tb = opt.block_len ? opt.block_len : 256;
+    lo.Tb = opt.block_len ? opt.block_len : 512;
     lo.C = opt.ring_copies;
+    lo.Fcap = opt.max_filters_per_lane;
     lo.n_sm = n_sm;
     p->bands.resize(decims.size());
     for (size_t j = 0; j < decims.size(); ++j) {

@@ -17,7 +17,10 @@
 //    places filters so the 32 lanes of a round read 32 different banks;
 //  * state in registers: lane i of warp w keeps the complex outputs of its F
 //    filters across the whole call, as the paper keeps each filter's output
-//    in a register;
+//    in a register.  F is capped (the kernel is compiled per cap, with launch
+//    bounds that follow its register need); a template with more filters
+//    than 32*cap spans several warps of the CTA (the paper maps such a
+//    template to a block);
 //  * the recurrence runs two filters per packed FP32x2 instruction
 //    (fma/mul/add .f32x2), 8 packed operations per filter pair and sample;
 //  * the sum over filters: each lane first adds its own filters, then the
@@ -25,8 +28,11 @@
 //    paper's shuffle sum, with explicit __shfl_*_sync since sm_70 warps are
 //    not implicitly synchronous).  Odd lanes hold their filters in (im, re)
 //    order, so the first exchange level needs no lane-dependent select;
-//  * no atomics: each warp owns one (detector, template) and writes its z
-//    and its peak directly (the paper's cross-warp atomics are not needed).
+//  * no atomics: each warp writes its per-sample sums for the block into
+//    shared memory; after the block barrier the template's first warp adds
+//    its warps' sums in a fixed order, stores z with coalesced 8-byte stores
+//    and keeps the running peak (the paper sums across warps with atomics,
+//    which would make the peak's argmax depend on timing).
 #include "spiir_kernels.h"
 #include "spiir_layout.h"
 
@@ -143,14 +149,13 @@ __device__ __forceinline__ void issue_block(const K1Args &A, const float *xrow, 
     }
 }
 
-// ---- cross-lane sum of 8 samples, store, running peak ---------------------
+// ---- cross-lane sum of 8 samples -----------------------------------------
 // zr/zi: this lane's partial sums (its filters) for 8 consecutive samples.
 // Even lanes hold (re, im), odd lanes (im, re).  After the exchange, lane i
-// (and lane i^16) holds component (i & 1) of sample s(i) summed over the warp.
-__device__ __forceinline__ void warp_sum_store_peak(const float (&zr)[kTS],
-                                                    const float (&zi)[kTS], int lane,
-                                                    int kbase, int valid, float *zrow,
-                                                    float &best, int &bidx)
+// (and lane i^16) holds component (i & 1) of sample s(i) summed over the
+// warp; lanes 0..15 write the 8 complex sums to out[0..15].
+__device__ __forceinline__ void warp_sum8(const float (&zr)[kTS], const float (&zi)[kTS],
+                                          int lane, float *out)
 {
     float v[kTS];
 #pragma unroll
@@ -175,29 +180,44 @@ __device__ __forceinline__ void warp_sum_store_peak(const float (&zr)[kTS],
     }
     v[0] += __shfl_xor_sync(kFull, v[0], 16);
     const int s = (b1 ? 4 : 0) + (b2 ? 2 : 0) + (b3 ? 1 : 0);
-    const float other = __shfl_xor_sync(kFull, v[0], 1);
-    if (s < valid) {
-        if (zrow != nullptr && lane < 16) zrow[2 * (int64_t)(kbase + s) + (lane & 1)] = v[0];
+    if (lane < 16) out[2 * s + (lane & 1)] = v[0];
+}
+
+// ---- the first warp of a template: add its warps' sums, store, peak ------
+__device__ __forceinline__ void combine_block(const float2 *zb, int Tb, int first, int nw,
+                                              int lane, int k0, int nv, float *zrow,
+                                              float &best, int &bidx)
+{
+    for (int i = lane; i < nv; i += 32) {
+        float2 acc = zb[(int64_t)first * Tb + i];
+        for (int w = 1; w < nw; ++w) {
+            const float2 o = zb[(int64_t)(first + w) * Tb + i];
+            acc.x += o.x;
+            acc.y += o.y;
+        }
+        if (zrow != nullptr) reinterpret_cast<float2 *>(zrow)[k0 + i] = acc;
         // |z|^2 = re*re + im*im, no contraction (reproducible on the host)
-        const float p = __fadd_rn(__fmul_rn(v[0], v[0]), __fmul_rn(other, other));
+        const float p = __fadd_rn(__fmul_rn(acc.x, acc.x), __fmul_rn(acc.y, acc.y));
         if (p > best) {
             best = p;
-            bidx = kbase + s;
+            bidx = k0 + i;
         }
     }
 }
 
-// ---- one CTA work unit: W templates x one detector, whole call -----------
+// ---- one CTA work unit: W warps x one detector, whole call ----------------
 template <int F>
 __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float *ring,
-                                         uint32_t bar0, uint32_t bar1)
+                                         float *zbuf, uint32_t bar0, uint32_t bar1)
 {
     constexpr int NP = F / 2;              // filter pairs (packed FP32x2)
     constexpr bool ODD = (F & 1) != 0;     // one more filter in scalar FP32
     constexpr int NPA = NP > 0 ? NP : 1;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int tmpl = A.slot_tmpl[(int64_t)g * A.W + warp];
+    const int4 wi = A.warp_info[(int64_t)g * A.W + warp];
+    const int tmpl = wi.x;
     const bool active = tmpl >= 0;
+    const bool leader = active && wi.y == warp;
     const int64_t pb = A.group_pbase[g];
     const int n = A.n;
     const int nblk = (n + A.Tb - 1) / A.Tb;
@@ -243,7 +263,7 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             yi1 = st[F - 1].y;
         }
     }
-    float *zrow = (A.z != nullptr && active)
+    float *zrow = (A.z != nullptr && leader)
                       ? A.z + ((int64_t)det * A.T + tmpl) * 2 * A.z_len
                       : nullptr;
     float best = -1.0f;
@@ -269,12 +289,14 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             failed_at = j;
             break;
         }
+        const int k0 = j * A.Tb;
+        const int nv = min(A.Tb, n - k0);
+        float *zb = zbuf + (int64_t)((j & 1) * A.W) * A.Tb * 2;   // this block's sums
         if (active) {
-            const int k0 = j * A.Tb;
-            const int nv = min(A.Tb, n - k0);
             int base[F];
 #pragma unroll
             for (int r = 0; r < F; ++r) base[r] = cb[r] + pos[r];
+            float *zw = zb + (int64_t)warp * A.Tb * 2;
             for (int sb = 0; sb < nv; sb += kTS) {
                 const int valid = nv - sb;
                 float zr[kTS], zi[kTS];
@@ -325,7 +347,7 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
                     zr[t] = sr;
                     zi[t] = si;
                 }
-                warp_sum_store_peak(zr, zi, lane, k0 + sb, valid, zrow, best, bidx);
+                warp_sum8(zr, zi, lane, zw + 2 * sb);
 #pragma unroll
                 for (int r = 0; r < F; ++r) base[r] += kTS;
             }
@@ -335,12 +357,17 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
                 if (pos[r] >= A.R) pos[r] -= A.R;
             }
         }
-        __syncthreads();  // every warp is done with the slot the next copy overwrites
+        // every warp is done with the ring slot the next copy overwrites, and
+        // this block's per-warp sums are visible
+        __syncthreads();
         if (threadIdx.x == 0 && j + 2 < nblk) {
             const int64_t e = (int64_t)A.H + j + 2;
             mbar_expect_tx(bar, block_bytes(A, e));
             issue_block(A, xrow, ring, e, bar);
         }
+        if (leader)
+            combine_block(reinterpret_cast<const float2 *>(zb), A.Tb, wi.y, wi.z, lane, k0, nv,
+                          zrow, best, bidx);
     }
     if (failed_at >= 0) {
         if (threadIdx.x == 0) {
@@ -373,7 +400,7 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
         A.state[(int64_t)det * A.n_slots + s] = make_float2(yr1, yi1);
     }
     // running peak: largest |z|^2, earliest index on ties
-    if (A.peak_best != nullptr) {
+    if (leader && A.peak_best != nullptr) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             const float ob = __shfl_xor_sync(kFull, best, off);
@@ -393,11 +420,23 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     }
 }
 
-__global__ void __launch_bounds__(256, 2) k1_plain(const K1Args A)
+// Registers per thread follow the filters-per-lane cap: CTAs of up to 256
+// threads, min resident CTAs chosen so the cap's register need fits (cap 10
+// is held to 128 registers: two CTAs per SM beat the spill-free 170).
+template <int FCAP> struct K1Bounds;
+template <> struct K1Bounds<2> { static constexpr int kMinBlocks = 4; };
+template <> struct K1Bounds<4> { static constexpr int kMinBlocks = 3; };
+template <> struct K1Bounds<6> { static constexpr int kMinBlocks = 2; };
+template <> struct K1Bounds<8> { static constexpr int kMinBlocks = 2; };
+template <> struct K1Bounds<10> { static constexpr int kMinBlocks = 2; };
+
+template <int FCAP>
+__global__ void __launch_bounds__(256, K1Bounds<FCAP>::kMinBlocks) k1_plain(const K1Args A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     float *ring = reinterpret_cast<float *>(smem + 128);
+    float *zbuf = ring + (int64_t)A.C * A.CS;
     const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
     if (threadIdx.x == 0) {
         mbar_init(bar0, 1);
@@ -407,21 +446,19 @@ __global__ void __launch_bounds__(256, 2) k1_plain(const K1Args A)
     __syncthreads();
     const int g = A.units[2 * blockIdx.x];
     const int det = A.units[2 * blockIdx.x + 1];
-    switch (A.group_F[g]) {
-    case 1: run_unit<1>(A, g, det, ring, bar0, bar1); break;
-    case 2: run_unit<2>(A, g, det, ring, bar0, bar1); break;
-    case 3: run_unit<3>(A, g, det, ring, bar0, bar1); break;
-    case 4: run_unit<4>(A, g, det, ring, bar0, bar1); break;
-    case 5: run_unit<5>(A, g, det, ring, bar0, bar1); break;
-    case 6: run_unit<6>(A, g, det, ring, bar0, bar1); break;
-    case 7: run_unit<7>(A, g, det, ring, bar0, bar1); break;
-    case 8: run_unit<8>(A, g, det, ring, bar0, bar1); break;
-    case 9: run_unit<9>(A, g, det, ring, bar0, bar1); break;
-    case 10: run_unit<10>(A, g, det, ring, bar0, bar1); break;
-    default:
-        if (threadIdx.x == 0) atomicOr(A.err, 4);
-        break;
-    }
+    const int F = A.group_F[g];
+    // the CTA's F is uniform, so every warp takes the same case
+    if (F == 1) run_unit<1>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (F == 2) run_unit<2>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 3 && F == 3) run_unit<(FCAP >= 3 ? 3 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 4 && F == 4) run_unit<(FCAP >= 4 ? 4 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 5 && F == 5) run_unit<(FCAP >= 5 ? 5 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 6 && F == 6) run_unit<(FCAP >= 6 ? 6 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 7 && F == 7) run_unit<(FCAP >= 7 ? 7 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 8 && F == 8) run_unit<(FCAP >= 8 ? 8 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 9 && F == 9) run_unit<(FCAP >= 9 ? 9 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 10 && F == 10) run_unit<(FCAP >= 10 ? 10 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (threadIdx.x == 0) atomicOr(A.err, 4);
 }
 
 __global__ void peak_out_kernel(const float *best, const int64_t *idx, int64_t count,
@@ -458,16 +495,28 @@ __global__ void bounded_wait_probe(int32_t *err, uint64_t limit_ns)
 
 }  // namespace
 
+template <int FCAP>
+cudaError_t launch_k1_cap(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
+{
+    if (smem_bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(
+            k1_plain<FCAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    k1_plain<FCAP><<<(unsigned)n_units, a.W * 32, smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
 {
     if (n_units <= 0 || a.n <= 0) return cudaSuccess;
-    if (smem_bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(
-            k1_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e != cudaSuccess) return e;
-    }
-    k1_plain<<<(unsigned)n_units, a.W * 32, smem_bytes, s>>>(a);
-    return cudaGetLastError();
+    // the smallest compiled cap that holds the layout's cap
+    if (a.fcap <= 2) return launch_k1_cap<2>(a, n_units, smem_bytes, s);
+    if (a.fcap <= 4) return launch_k1_cap<4>(a, n_units, smem_bytes, s);
+    if (a.fcap <= 6) return launch_k1_cap<6>(a, n_units, smem_bytes, s);
+    if (a.fcap <= 8) return launch_k1_cap<8>(a, n_units, smem_bytes, s);
+    if (a.fcap <= 10) return launch_k1_cap<10>(a, n_units, smem_bytes, s);
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count,

@@ -12,10 +12,11 @@ struct K1Args {
     int64_t xe_stride;         // floats per detector row (multiple of 4)
     int32_t n;                 // samples in this call (band rate)
     int32_t Tb, H, S, R, CS, C, W;
+    int32_t fcap;              // filters-per-lane cap of the layout (selects the kernel)
     const int32_t *units;      // [n_units][2] (group, detector)
     const int32_t *group_F;    // [G]
     const int64_t *group_pbase;// [G]
-    const int32_t *slot_tmpl;  // [G*W]
+    const int4 *warp_info;     // [G*W] (template or -1, first warp of it, its warps, 0)
     const float4 *params;      // [n_slots] (ar, ai, br, bi) kernel form
     const int2 *ringoff;       // [n_slots] (pos0, copy base)
     float2 *state;             // [D][n_slots] filter outputs, kernel form

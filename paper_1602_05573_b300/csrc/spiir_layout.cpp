@@ -151,36 +151,54 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
         *err = "layout: block_len must be a multiple of 32 in [32, 4096]";
         return false;
     }
-    L.C = opt.C == 0 ? 4 : opt.C;
+    L.C = opt.C == 0 ? 1 : opt.C;
     if (L.C != 1 && L.C != 2 && L.C != 4) {
         *err = "layout: ring_copies must be 1, 2 or 4";
         return false;
     }
-    // filters per lane, and the largest delay
-    int64_t maxd = 0;
-    std::vector<int> F(L.T);
+    L.Fcap = opt.Fcap == 0 ? kMaxF : opt.Fcap;
+    if (L.Fcap < 1 || L.Fcap > kMaxF) {
+        *err = "layout: max_filters_per_lane must be in [1, " + std::to_string(kMaxF) + "]";
+        return false;
+    }
+    // per template: rounds of 32 filters, warps w, filters per lane F
+    int64_t maxd = 0, max_nw = 1, total_warps = 0;
+    std::vector<int> F(L.T), nw(L.T);
     for (int64_t t = 0; t < L.T; ++t) {
-        int64_t n = (int64_t)filters[t].size();
-        F[t] = (int)std::max<int64_t>(1, (n + 31) / 32);
-        if (F[t] > kMaxF) {
+        const int64_t n = (int64_t)filters[t].size();
+        const int64_t rounds = std::max<int64_t>(1, (n + 31) / 32);
+        const int64_t w = (rounds + L.Fcap - 1) / L.Fcap;
+        if (w > 8) {
             *err = "layout: template " + std::to_string(t) + " has " + std::to_string(n) +
-                   " filters; the plain kernel holds at most " + std::to_string(32 * kMaxF);
+                   " filters; with " + std::to_string(L.Fcap) + " filters per lane at most " +
+                   std::to_string(32 * L.Fcap * 8) + " fit in a CTA";
             return false;
         }
+        nw[t] = (int)w;
+        max_nw = std::max<int64_t>(max_nw, w);
+        total_warps += w;
+        F[t] = (int)((rounds + w - 1) / w);
         for (int64_t l : filters[t]) maxd = std::max<int64_t>(maxd, d[l]);
         L.n_filters += n;
     }
-    // warps per CTA: enough CTAs to cover the GPU twice over, at most 8
+    // warps per CTA: enough CTAs to cover the GPU twice over, at most 4 (more
+    // warps per CTA wait longer at the per-block barrier)
     if (opt.W > 0) {
         L.W = opt.W;
     } else {
-        int64_t work = L.T * D;
-        int w = 8;
-        while (w > 1 && work / w < 2 * (int64_t)opt.n_sm) w /= 2;
+        const int64_t work = total_warps * D;
+        int w = max_nw > 4 ? 8 : 4;
+        while (w > 1 && w / 2 >= max_nw && work / w < 2 * (int64_t)opt.n_sm) w /= 2;
         L.W = w;
     }
     if (L.W < 1 || L.W > 8) {
         *err = "layout: warps_per_cta must be in [1, 8]";
+        return false;
+    }
+    if (max_nw > L.W) {
+        *err = "layout: a template needs " + std::to_string(max_nw) + " warps at " +
+               std::to_string(L.Fcap) + " filters per lane; warps_per_cta is " +
+               std::to_string(L.W);
         return false;
     }
     // ring geometry
@@ -191,30 +209,69 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
     const int skew = L.C == 1 ? 0 : 32 / L.C;   // bank offset between copies
     L.CS = L.R + L.Tb + skew;                    // R + Tb is a multiple of 32
     if (L.smem_bytes() > 227 * 1024) {
-        *err = "layout: strain ring needs " + std::to_string(L.smem_bytes()) +
+        *err = "layout: strain ring and partial sums need " + std::to_string(L.smem_bytes()) +
                " bytes of shared memory (max delay " + std::to_string(maxd) +
-               "); use fewer ring_copies or a shorter block_len";
+               "); use fewer ring_copies, fewer warps per CTA or a shorter block_len";
         return false;
     }
-    // sort templates: F descending, then filter count descending, then index
+    // sort templates: F descending, warps descending, filter count descending
     std::vector<int64_t> order(L.T);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
         if (F[x] != F[y]) return F[x] > F[y];
+        if (nw[x] != nw[y]) return nw[x] > nw[y];
         return filters[x].size() > filters[y].size();
     });
-    const int64_t G = (L.T + L.W - 1) / L.W;
+    // first-fit packing of each template's warps into CTAs of the same F
+    struct Group {
+        int F;
+        int used;
+        std::vector<int64_t> tmpl;  // per warp
+        std::vector<int> first;     // per warp: first warp of its template
+    };
+    std::vector<Group> groups;
+    std::vector<size_t> open;       // groups of the current F with free warps
+    int curF = -1;
+    for (int64_t t : order) {
+        if (F[t] != curF) {
+            open.clear();
+            curF = F[t];
+        }
+        size_t gi = groups.size();
+        for (size_t k = 0; k < open.size(); ++k)
+            if (groups[open[k]].used + nw[t] <= L.W) {
+                gi = open[k];
+                break;
+            }
+        if (gi == groups.size()) {
+            groups.push_back(Group{F[t], 0, std::vector<int64_t>(L.W, -1),
+                                   std::vector<int>(L.W, -1)});
+            open.push_back(gi);
+        }
+        Group &grp = groups[gi];
+        for (int k = 0; k < nw[t]; ++k) {
+            grp.tmpl[grp.used + k] = t;
+            grp.first[grp.used + k] = grp.used;
+        }
+        grp.used += nw[t];
+        if (grp.used == L.W) open.erase(std::find(open.begin(), open.end(), gi));
+    }
+    const int64_t G = (int64_t)groups.size();
     L.group_F.resize(G);
     L.group_pbase.resize(G);
-    L.slot_tmpl.assign((size_t)G * L.W, -1);
+    L.warp_info.assign((size_t)G * L.W * 4, 0);
     int64_t base = 0;
     for (int64_t g = 0; g < G; ++g) {
-        L.group_F[g] = F[order[g * L.W]];
+        L.group_F[g] = groups[g].F;
         L.group_pbase[g] = base;
-        base += (int64_t)L.group_F[g] * L.W * 32;
+        base += (int64_t)groups[g].F * L.W * 32;
         for (int w = 0; w < L.W; ++w) {
-            int64_t i = g * L.W + w;
-            if (i < L.T) L.slot_tmpl[g * L.W + w] = (int32_t)order[i];
+            const int64_t t = groups[g].tmpl[w];
+            int32_t *wi = &L.warp_info[(g * L.W + w) * 4];
+            wi[0] = (int32_t)t;
+            wi[1] = t >= 0 ? groups[g].first[w] : w;
+            wi[2] = t >= 0 ? nw[t] : 1;
+            wi[3] = 0;
         }
     }
     L.n_slots = base;
@@ -230,18 +287,22 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
     for (int64_t g = 0; g < G; ++g) {
         const int Fg = L.group_F[g];
         for (int w = 0; w < L.W; ++w) {
-            const int64_t t = L.slot_tmpl[g * L.W + w];
+            const int64_t t = groups[g].tmpl[w];
+            if (t >= 0 && groups[g].first[w] != w) continue;  // placed with its first warp
+            const int nwt = t >= 0 ? nw[t] : 1;
+            const int rounds = Fg * nwt;   // the template's rounds over its warps
             const std::vector<int64_t> &fl = t >= 0 ? filters[t] : none;
             double wf = 0.0;
-            place_template(fl, d, Fg, L.C, L.CS, cells, &wf);
+            place_template(fl, d, rounds, L.C, L.CS, cells, &wf);
             if (t >= 0) {
                 wf_total += wf;
-                rounds_total += Fg;
+                rounds_total += rounds;
             }
-            for (int r = 0; r < Fg; ++r) {
+            for (int r = 0; r < rounds; ++r) {
+                const int ww = w + r / Fg, rl = r % Fg;  // warp and its local round
                 for (int i = 0; i < 32; ++i) {
                     const Cell &c = cells[(size_t)r * 32 + i];
-                    const int64_t s = L.slot(g, r, w, i);
+                    const int64_t s = L.slot(g, rl, ww, i);
                     float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
                     if (c.filter >= 0) {
                         ar = a[2 * c.filter];

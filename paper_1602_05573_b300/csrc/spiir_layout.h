@@ -6,10 +6,14 @@
 // more than 32 filters to more threads than a warp and a smaller one to a
 // warp, and lets the filters of a template share the staged strain window.
 // This layout keeps those ideas and re-plans them for sm_103a:
-//  * one warp serves one template: lane i holds the filters of "rounds"
-//    r = 0..F-1 (F = ceil(L/32) filters per lane, state in registers);
-//  * templates are sorted by F (then L) and packed W per CTA, so a CTA's
-//    warps do equal work and the CTAs run largest-first;
+//  * a template of L filters is served by w warps of one CTA: lane i of each
+//    warp holds the filters of "rounds" r = 0..F-1 (state in registers),
+//    with F <= Fcap filters per lane, w = ceil(ceil(L/32) / Fcap) and
+//    F = ceil(ceil(L/32) / w).  A small Fcap keeps registers per thread low
+//    (more resident warps); the warps' partial sums meet in shared memory;
+//  * templates are sorted by F and packed into CTAs of W warps (all warps of
+//    a template in one CTA), so a CTA's warps do equal work and the CTAs run
+//    largest-first;
 //  * the strain window is one shared-memory ring per CTA; each filter reads
 //    x[k - d_l] from it.  Lanes of one round read 32 different delays, so the
 //    filters are placed in rounds (and in one of C bank-skewed copies of the
@@ -25,13 +29,14 @@
 
 namespace spiir {
 
-constexpr int kMaxF = 10;   // filters per lane handled by the plain kernel
+constexpr int kMaxF = 10;   // largest filters-per-lane cap the plain kernel is built for
 constexpr int kTS = 8;      // samples per register sub-block (cross-lane sum width)
 
 struct LayoutOptions {
-    int W = 0;          // warps (templates) per CTA; 0 = from the bank size
-    int Tb = 256;       // samples per staged strain block (multiple of 32)
-    int C = 0;          // ring copies (1, 2, 4); 0 = default
+    int W = 0;          // warps per CTA; 0 = from the bank size
+    int Fcap = 0;       // filters per lane cap (1..kMaxF); 0 = default (kMaxF)
+    int Tb = 512;       // samples per staged strain block (multiple of 32)
+    int C = 0;          // ring copies (1, 2, 4); 0 = default (1)
     int n_sm = 148;     // used to pick W when W == 0
 };
 
@@ -45,13 +50,15 @@ struct Layout {
     int R = 0;              // ring length in samples = S * Tb
     int CS = 0;             // words between ring copies (>= R + Tb, bank-skewed)
     int Dh = 0;             // history samples kept = H * Tb
-    int maxF = 1;
+    int maxF = 1;           // largest F of any CTA (<= Fcap)
+    int Fcap = 4;
     int64_t n_slots = 0;    // filter slots including padding (per detector)
     int64_t n_filters = 0;  // real filters in this layout
 
     std::vector<int32_t> group_F;       // [G]
     std::vector<int64_t> group_pbase;   // [G] first slot of the group
-    std::vector<int32_t> slot_tmpl;     // [G * W] template served by warp, -1 = empty
+    std::vector<int32_t> warp_info;     // [G * W][4] (template or -1, first warp of the
+                                        //  template, its warp count, 0)
     std::vector<float> params;          // [n_slots][4] kernel-form (ar, ai, br, bi)
     std::vector<int32_t> ringoff;       // [n_slots][2] (pos0, copy base word)
     std::vector<int64_t> slot_filter;   // [n_slots] bank filter index, -1 = padding
@@ -61,7 +68,8 @@ struct Layout {
 
     int64_t n_groups() const { return (int64_t)group_F.size(); }
     int64_t n_units() const { return (int64_t)units.size() / 2; }
-    int smem_bytes() const { return 128 + C * CS * 4; }
+    // mbarriers, C ring copies, and two Tb-sample partial-sum buffers per warp
+    int smem_bytes() const { return 128 + C * CS * 4 + 2 * W * Tb * 8; }
     // slot of (group g, round r, warp w, lane i)
     int64_t slot(int64_t g, int r, int w, int i) const {
         return group_pbase[g] + ((int64_t)r * W + w) * 32 + i;

@@ -117,7 +117,7 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const 
     const size_t o_units = take(sizeof(int32_t) * L.units.size());
     const size_t o_groupF = take(sizeof(int32_t) * (size_t)G);
     const size_t o_pbase = take(sizeof(int64_t) * (size_t)G);
-    const size_t o_tmpl = take(sizeof(int32_t) * L.slot_tmpl.size());
+    const size_t o_winfo = take(sizeof(int32_t) * L.warp_info.size());
     const size_t o_state = take(sizeof(float2) * (size_t)D * L.n_slots);
     const size_t o_xe = take(sizeof(float) * (size_t)D * stride);
     const size_t o_best = take(sizeof(float) * (size_t)D * T);
@@ -139,7 +139,7 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const 
     auto *units = reinterpret_cast<int32_t *>(base + o_units);
     auto *groupF = reinterpret_cast<int32_t *>(base + o_groupF);
     auto *pbase = reinterpret_cast<int64_t *>(base + o_pbase);
-    auto *tmpl = reinterpret_cast<int32_t *>(base + o_tmpl);
+    auto *winfo = reinterpret_cast<int4 *>(base + o_winfo);
     auto *state = reinterpret_cast<float2 *>(base + o_state);
     auto *xe = reinterpret_cast<float *>(base + o_xe);
     auto *best = reinterpret_cast<float *>(base + o_best);
@@ -160,7 +160,7 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const 
                              cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(pbase, L.group_pbase.data(), L.group_pbase.size() * sizeof(int64_t),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpyAsync(tmpl, L.slot_tmpl.data(), L.slot_tmpl.size() * sizeof(int32_t),
+        (e = cudaMemcpyAsync(winfo, L.warp_info.data(), L.warp_info.size() * sizeof(int32_t),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(state, 0, sizeof(float2) * (size_t)D * L.n_slots, s)) !=
             cudaSuccess ||
@@ -187,7 +187,8 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const 
     a.units = units;
     a.group_F = groupF;
     a.group_pbase = pbase;
-    a.slot_tmpl = tmpl;
+    a.warp_info = winfo;
+    a.fcap = L.Fcap;
     a.params = params;
     a.ringoff = ringoff;
     a.state = state;

@@ -68,7 +68,7 @@ def test_ragged_lengths(sp, n):
 
 def test_template_size_edges(sp):
     """Templates at and around the warp (32) and per-lane (32 F) boundaries."""
-    counts = [1, 2, 31, 32, 33, 63, 64, 65, 100, 255, 256, 257, 300, 320]
+    counts = [1, 2, 31, 32, 33, 63, 64, 65, 100, 255, 256, 257, 300, 320, 1000]
     rng = np.random.default_rng(50)
     off = np.zeros(len(counts) + 1, np.int64)
     off[1:] = np.cumsum(counts)
@@ -106,12 +106,14 @@ def test_multi_detector_batched_shape(sp):
     assert_parity(z, pa, pi, oracle_z(bank, x))
 
 
-@pytest.mark.parametrize("W,C,Tb", [(1, 1, 32), (2, 2, 64), (8, 4, 128), (4, 4, 512),
-                                    (3, 2, 1024)])
-def test_launch_options_agree_with_oracle(sp, W, C, Tb):
+@pytest.mark.parametrize("W,C,Tb,Fcap", [(1, 1, 32, 10), (2, 2, 64, 4), (8, 4, 128, 1),
+                                         (4, 4, 512, 2), (3, 2, 1024, 6), (8, 2, 256, 8),
+                                         (7, 1, 96, 3)])
+def test_launch_options_agree_with_oracle(sp, W, C, Tb, Fcap):
     bank = make_bank(13, (30, 200), (0.99, 0.9995), 900, seed=57, n_det=2)
     x = make_strain(2, 2500, seed=58)
-    z, pa, pi, _ = run_gpu(sp, bank, x, warps_per_cta=W, ring_copies=C, block_len=Tb)
+    z, pa, pi, _ = run_gpu(sp, bank, x, warps_per_cta=W, ring_copies=C, block_len=Tb,
+                           max_filters_per_lane=Fcap)
     assert_parity(z, pa, pi, oracle_z(bank, x))
 
 
