@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "plain", "adjoint", "precision"])
+    ap.add_argument("--samples", type=int, default=0,
+                    help="override the stream length per step (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -220,7 +222,7 @@ def run_ours(args, rank, world, local_rank):
     else:  # this rank's shard of a world x larger bank (independent templates)
         bank = make_bank(w["n_templates"], w["filters"], w["r_range"], w["d_max"],
                          w["seed"] + 1000 * rank, w["n_det"])
-    x_host = workload_strain(args.workload)
+    x_host = workload_strain(args.workload, args.samples or None)
     n = x_host.shape[1]
     T, D = bank.n_templates, bank.n_det
     upd = updates(bank, n)

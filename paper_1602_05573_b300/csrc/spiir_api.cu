@@ -139,6 +139,8 @@ struct Band {
     float *xe = nullptr;       // [D][xe_stride] workspace
     int64_t xe_stride = 0;
     int64_t xe_cap = 0;        // samples the workspace holds after the history
+    float2 *zb = nullptr;      // [D][T][zb_len] band-rate sums (decimated bands)
+    int64_t zb_cap = 0;        // complex samples per row the workspace holds
 };
 
 struct spiir_plan {
@@ -152,7 +154,9 @@ struct spiir_plan {
     float *peak_best = nullptr;   // [D][T]
     int64_t *peak_idx = nullptr;  // [D][T]
     int32_t *err = nullptr;
-    int64_t t0 = 0;               // samples since reset
+    int64_t t0 = 0;               // samples since reset (top rate)
+    int top = 0;                  // index of the top-rate band
+    int maxR = 1;                 // largest decimation factor
 };
 
 namespace {
@@ -168,6 +172,7 @@ void free_band(Band &b)
     cudaFree(b.state);
     cudaFree(b.hist);
     cudaFree(b.xe);
+    cudaFree(b.zb);
     b = Band();
 }
 
@@ -359,10 +364,18 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
             return fail(SPIIR_EUNSUPPORTED, err);
         }
     }
-    if (p->bands.size() > 1) {
+    if (p->bands.size() > 1 + spiir::kMaxLowerBands) {
         delete p;
-        return fail(SPIIR_EUNSUPPORTED, "multirate banks are not built yet");
+        return fail(SPIIR_EUNSUPPORTED, "at most " + std::to_string(1 + spiir::kMaxLowerBands) +
+                                            " bands");
     }
+    // the first band at the top rate carries the fused epilogue
+    for (size_t j = 0; j < p->bands.size(); ++j)
+        if (p->bands[j].R == 1) {
+            p->top = (int)j;
+            break;
+        }
+    for (const Band &b : p->bands) p->maxR = std::max(p->maxR, b.R);
     if (p->device < 0) {  // host-only plan
         *out = p;
         return SPIIR_OK;
@@ -431,7 +444,7 @@ spiir_status spiir_plan_get_info(const spiir_plan *p, spiir_plan_info *info)
         info->warps_per_cta = L.W;
         info->block_len = L.Tb;
         info->ring_copies = L.C;
-        info->history_len = std::max(info->history_len, L.Dh);
+        if (&b == &p->bands[p->top]) info->history_len = L.Dh;
         info->smem_bytes = std::max(info->smem_bytes, L.smem_bytes());
         info->max_filters_per_lane = std::max(info->max_filters_per_lane, L.maxF);
         wf += L.conflict_ratio * (double)L.n_slots;
@@ -487,28 +500,70 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
     if (n == 0) return SPIIR_OK;
     if (!x_dev) return fail(SPIIR_EINVAL, "x_dev is NULL");
     if (n > (int64_t)1 << 30) return fail(SPIIR_EINVAL, "n above 2^30 samples per call");
+    if (p->t0 % p->maxR != 0)
+        return fail(SPIIR_EINVAL, "multirate stream: the previous call's length was not a "
+                                  "multiple of the largest decimation factor");
     DeviceGuard guard(p->device);
     if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    Band &b = p->bands[0];
-    spiir_status st = ensure_xe(p, b, n, s);
-    if (st != SPIIR_OK) return st;
     const int D = p->D;
-    const int64_t Dh = b.lay.Dh;
     cudaError_t e;
-    // xe[:, 0:Dh] = history, xe[:, Dh:Dh+n] = x
-    if ((e = cudaMemcpy2DAsync(b.xe, b.xe_stride * 4, b.hist, Dh * 4, Dh * 4, D,
-                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
-        (e = cudaMemcpy2DAsync(b.xe + Dh, b.xe_stride * 4, x_dev, n * 4, n * 4, D,
-                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return cuda_fail(e, "strain staging copy");
-    spiir::K1Args a = k1_args(p, b, n, z_dev, n, true);
-    if ((e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s)) != cudaSuccess)
-        return cuda_fail(e, "filter kernel launch");
-    // history for the next call: the last Dh samples of (history, x)
-    if ((e = cudaMemcpy2DAsync(b.hist, Dh * 4, b.xe + n, b.xe_stride * 4, Dh * 4, D,
-                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
-        return cuda_fail(e, "history copy");
+    // decimated bands first (their sums feed the top band's epilogue), top band last
+    std::vector<int> order;
+    for (int j = 0; j < (int)p->bands.size(); ++j)
+        if (j != p->top) order.push_back(j);
+    order.push_back(p->top);
+    spiir::K1Args top_args{};
+    for (int j : order) {
+        Band &b = p->bands[j];
+        const int64_t nb = (n + b.R - 1) / b.R;   // band samples in this call
+        spiir_status st = ensure_xe(p, b, nb, s);
+        if (st != SPIIR_OK) return st;
+        const int64_t Dh = b.lay.Dh;
+        // xe[:, 0:Dh] = band history, xe[:, Dh:Dh+nb] = this call's band samples
+        if ((e = cudaMemcpy2DAsync(b.xe, b.xe_stride * 4, b.hist, Dh * 4, Dh * 4, D,
+                                   cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "strain staging copy");
+        if (b.R == 1)
+            e = cudaMemcpy2DAsync(b.xe + Dh, b.xe_stride * 4, x_dev, n * 4, n * 4, D,
+                                  cudaMemcpyDeviceToDevice, s);
+        else
+            e = spiir::launch_decimate(x_dev, n, D, b.R, nb, b.xe, b.xe_stride, Dh, s);
+        if (e != cudaSuccess) return cuda_fail(e, "strain staging");
+        if (j != p->top) {
+            if (!b.zb || b.zb_cap < nb) {
+                if (b.zb) {
+                    if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+                        return cuda_fail(e, "cudaStreamSynchronize");
+                    cudaFree(b.zb);
+                    b.zb = nullptr;
+                }
+                if ((e = dalloc(&b.zb, (size_t)D * p->T * nb)) != cudaSuccess)
+                    return e == cudaErrorMemoryAllocation
+                               ? fail(SPIIR_ENOMEM, "band workspace allocation")
+                               : cuda_fail(e, "cudaMalloc");
+                b.zb_cap = nb;
+            }
+            spiir::K1Args a = k1_args(p, b, nb, reinterpret_cast<float *>(b.zb), nb, false);
+            a.t0 = p->t0 / b.R;
+            if ((e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s)) != cudaSuccess)
+                return cuda_fail(e, "band filter kernel launch");
+            spiir::LowerBand &lb = top_args.lower[top_args.n_lower++];
+            lb.z = b.zb;
+            lb.len = nb;
+            lb.R = b.R;
+        } else {
+            spiir::K1Args a = k1_args(p, b, n, z_dev, n, true);
+            a.n_lower = top_args.n_lower;
+            for (int i = 0; i < a.n_lower; ++i) a.lower[i] = top_args.lower[i];
+            if ((e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s)) != cudaSuccess)
+                return cuda_fail(e, "filter kernel launch");
+        }
+        // band history for the next call: the last Dh band samples of (history, x_b)
+        if ((e = cudaMemcpy2DAsync(b.hist, Dh * 4, b.xe + nb, b.xe_stride * 4, Dh * 4, D,
+                                   cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "history copy");
+    }
     p->t0 += n;
     return SPIIR_OK;
 }
@@ -569,7 +624,7 @@ spiir_status spiir_state_get(spiir_plan *p, float *state, float *history, int64_
         }
     }
     if (history) {
-        const Band &b = p->bands[0];
+        const Band &b = p->bands[p->top];
         e = cudaMemcpy(history, b.hist, sizeof(float) * (size_t)p->D * b.lay.Dh,
                        cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "history copy");
@@ -608,7 +663,7 @@ spiir_status spiir_state_set(spiir_plan *p, const float *state, const float *his
         }
     }
     if (history) {
-        Band &b = p->bands[0];
+        Band &b = p->bands[p->top];
         e = cudaMemcpy(b.hist, history, sizeof(float) * (size_t)p->D * b.lay.Dh,
                        cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "history copy");

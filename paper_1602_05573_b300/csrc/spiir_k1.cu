@@ -36,6 +36,7 @@
 #include "spiir_kernels.h"
 #include "spiir_layout.h"
 
+#include <algorithm>
 #include <cstdint>
 
 namespace spiir {
@@ -184,16 +185,31 @@ __device__ __forceinline__ void warp_sum8(const float (&zr)[kTS], const float (&
 }
 
 // ---- the first warp of a template: add its warps' sums, store, peak ------
-__device__ __forceinline__ void combine_block(const float2 *zb, int Tb, int first, int nw,
-                                              int lane, int k0, int nv, float *zrow,
-                                              float &best, int &bidx)
+// Multirate banks: each lower band's sum is brought to this (top) rate by
+// linear interpolation between band samples i = k / R and i + 1 (held at the
+// call's last band sample), z_up = (1 - f) z_b[i] + f z_b[i + 1], f = (k mod R)/R,
+// and added before the store and the peak.
+__device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb, int first,
+                                              int nw, int det, int tmpl, int lane, int k0,
+                                              int nv, float *zrow, float &best, int &bidx)
 {
     for (int i = lane; i < nv; i += 32) {
-        float2 acc = zb[(int64_t)first * Tb + i];
+        float2 acc = zb[(int64_t)first * A.Tb + i];
         for (int w = 1; w < nw; ++w) {
-            const float2 o = zb[(int64_t)(first + w) * Tb + i];
+            const float2 o = zb[(int64_t)(first + w) * A.Tb + i];
             acc.x += o.x;
             acc.y += o.y;
+        }
+        for (int b = 0; b < A.n_lower; ++b) {
+            const LowerBand &lb = A.lower[b];
+            const int k = k0 + i;
+            const int64_t ib = k / lb.R;
+            const int64_t ib1 = ib + 1 < lb.len ? ib + 1 : lb.len - 1;
+            const float f = (float)(k % lb.R) / (float)lb.R;
+            const float2 *row = lb.z + ((int64_t)det * A.T + tmpl) * lb.len;
+            const float2 u = row[ib], v = row[ib1];
+            acc.x += fmaf(f, v.x, (1.0f - f) * u.x);
+            acc.y += fmaf(f, v.y, (1.0f - f) * u.y);
         }
         if (zrow != nullptr) reinterpret_cast<float2 *>(zrow)[k0 + i] = acc;
         // |z|^2 = re*re + im*im, no contraction (reproducible on the host)
@@ -366,8 +382,8 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             issue_block(A, xrow, ring, e, bar);
         }
         if (leader)
-            combine_block(reinterpret_cast<const float2 *>(zb), A.Tb, wi.y, wi.z, lane, k0, nv,
-                          zrow, best, bidx);
+            combine_block(A, reinterpret_cast<const float2 *>(zb), wi.y, wi.z, det, tmpl, lane,
+                          k0, nv, zrow, best, bidx);
     }
     if (failed_at >= 0) {
         if (threadIdx.x == 0) {
@@ -479,6 +495,15 @@ __global__ void peak_reset_kernel(float *best, int64_t *idx, int64_t count)
     idx[i] = -1;
 }
 
+__global__ void decimate_kernel(const float *x, int64_t n, int R, int64_t nb, float *xe,
+                                int64_t xe_stride, int64_t Dh)
+{
+    const int d = blockIdx.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nb;
+         i += (int64_t)gridDim.x * blockDim.x)
+        xe[(int64_t)d * xe_stride + Dh + i] = x[(int64_t)d * n + (int64_t)R * i];
+}
+
 __global__ void bounded_wait_probe(int32_t *err, uint64_t limit_ns)
 {
     __shared__ __align__(8) uint64_t bar;
@@ -532,6 +557,16 @@ cudaError_t launch_peak_reset(float *best, int64_t *idx, int64_t count, cudaStre
 {
     if (count <= 0) return cudaSuccess;
     peak_reset_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(best, idx, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decimate(const float *x, int64_t n, int D, int R, int64_t nb, float *xe,
+                            int64_t xe_stride, int64_t Dh, cudaStream_t s)
+{
+    if (nb <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((nb + 255) / 256, 4096);
+    decimate_kernel<<<dim3((unsigned)blocks, (unsigned)D), 256, 0, s>>>(x, n, R, nb, xe,
+                                                                       xe_stride, Dh);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,16 @@
 
 namespace spiir {
 
+// A decimated band's summed output, added to the top band's sum after linear
+// interpolation (multirate banks).  Rows are [D][T][len] complex64.
+struct LowerBand {
+    const float2 *z;
+    int64_t len;               // band samples in this call
+    int32_t R;                 // decimation factor (top-rate samples per band sample)
+    int32_t pad;
+};
+constexpr int kMaxLowerBands = 7;
+
 // Plain FP32 filter kernel (one launch per bank or band).
 struct K1Args {
     const float *xe;           // [D][xe_stride] strain: Dh history samples, then the call's
@@ -29,6 +39,8 @@ struct K1Args {
     int64_t t0;                // absolute index of this call's first sample
     int32_t *err;              // device error word
     uint64_t wait_limit_ns;    // bound on every mbarrier wait
+    int32_t n_lower;           // lower bands added in the combine (0 = single rate)
+    LowerBand lower[kMaxLowerBands];
 };
 
 cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s);
@@ -39,6 +51,10 @@ cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count
 
 // best[i] = -1, idx[i] = -1.
 cudaError_t launch_peak_reset(float *best, int64_t *idx, int64_t count, cudaStream_t s);
+
+// xe[d][Dh + i] = x[d][R * i] for i < nb (decimation into a band's strain rows).
+cudaError_t launch_decimate(const float *x, int64_t n, int D, int R, int64_t nb, float *xe,
+                            int64_t xe_stride, int64_t Dh, cudaStream_t s);
 
 // Self-test: wait on an mbarrier nothing will complete, with a bound; sets *err.
 cudaError_t launch_bounded_wait_probe(int32_t *err, uint64_t limit_ns, cudaStream_t s);

@@ -137,3 +137,20 @@ def test_batched_layout_statistics():
         assert info["n_slots"] / info["n_filters"] < pad
         assert info["bank_conflict_ratio"] < 1.4
         assert info["smem_bytes"] <= 227 * 1024
+
+
+def test_multirate_plan_layout_and_validation():
+    from spiir_inputs import make_multirate_bank
+    bank = make_multirate_bank(5, (7, 40, 3), (1, 4, 16), (0.9, 0.99), 50, seed=9)
+    p = sp.Plan(bank, device=-1)
+    sf, st = p.slots()
+    assert np.array_equal(np.sort(sf[sf >= 0]), np.arange(bank.n_filters))
+    bad = make_multirate_bank(2, (3, 3), (2, 4), (0.9, 0.99), 5, seed=9)  # no top-rate band
+    with pytest.raises(sp.SpiirError) as e:
+        sp.Plan(bad, device=-1)
+    assert e.value.status == sp.EINVAL
+    bad = make_multirate_bank(2, (3, 3), (1, 4), (0.9, 0.99), 5, seed=9)
+    bad.band_of = bad.band_of.copy()
+    bad.band_of[0] = 5
+    with pytest.raises(sp.SpiirError):
+        sp.Plan(bad, device=-1)
