@@ -201,6 +201,15 @@ spiir_status spiir_filter_backward(spiir_plan *plan, const float *x_dev, int64_t
                                    float *grad_b_dev, float *grad_x_dev, void *stream);
 
 /*
+ * Replace every filter's pole and gain (device arrays, [Ltot] complex64 in
+ * bank order, read on `stream`); delays and the layout are unchanged.  Used
+ * when the coefficients are being fitted (see spiir_filter_backward).  The
+ * caller keeps |a_l| < 1; the device values are not validated.
+ */
+spiir_status spiir_set_coefficients(spiir_plan *plan, const float *a_reim_dev,
+                                    const float *b_reim_dev, void *stream);
+
+/*
  * Streaming state, for checkpoint and resume.  Synchronous (waits for the
  * plan's device work).  Host buffers:
  *   state   [n_detectors][Ltot] complex64 filter outputs y_l at the last

@@ -39,7 +39,7 @@ SYMBOLS = [
     "spiir_plan_get_info", "spiir_plan_get_slots", "spiir_reset", "spiir_filter",
     "spiir_peak", "spiir_filter_backward", "spiir_state_get", "spiir_state_set",
     "spiir_check", "spiir_selftest_bounded_wait", "spiir_status_str",
-    "spiir_last_error_detail", "spiir_filter_noalloc",
+    "spiir_last_error_detail", "spiir_filter_noalloc", "spiir_set_coefficients",
 ]
 
 
@@ -101,6 +101,8 @@ def _configure(lib):
     lib.spiir_check.restype = _st
     lib.spiir_selftest_bounded_wait.argtypes = [_P, ctypes.c_uint64, _P]
     lib.spiir_selftest_bounded_wait.restype = _st
+    lib.spiir_set_coefficients.argtypes = [_P, _P, _P, _P]
+    lib.spiir_set_coefficients.restype = _st
     lib.spiir_filter_noalloc.argtypes = [ctypes.POINTER(BankDesc), _P, ctypes.c_int64, _P, _P,
                                           _P, _P]
     lib.spiir_filter_noalloc.restype = _st
@@ -330,6 +332,16 @@ class Plan:
                "spiir_filter_backward", self._lib)
         return ga, gb, gx
 
+    def set_coefficients(self, a, b, *, stream=None):
+        """Replace every filter's pole and gain: a, b CUDA complex64 [Ltot]."""
+        import torch
+        a = a.detach().to(torch.complex64).contiguous()
+        b = b.detach().to(torch.complex64).contiguous()
+        assert a.is_cuda and b.is_cuda and a.numel() == b.numel() == self.n_filters
+        _check(self._lib.spiir_set_coefficients(self._h, _ptr(a), _ptr(b),
+                                                _stream_handle(stream)),
+               "spiir_set_coefficients", self._lib)
+
     def state_get(self):
         inf = self.info()
         st = np.zeros((self.n_det, self.n_filters), np.complex64)
@@ -348,3 +360,37 @@ class Plan:
     def check(self, stream=None):
         """Wait for the plan's work; raise SpiirError(ETIMEOUT) if a bounded wait gave up."""
         _check(self._lib.spiir_check(self._h, _stream_handle(stream)), "spiir_check", self._lib)
+
+
+def _autograd_function():
+    import torch
+
+    class SpiirFilterFunction(torch.autograd.Function):
+        """z = SPIIR bank (poles a, gains b, the plan's delays) applied to x
+        from zero state; backward runs spiir_filter_backward (the adjoint
+        kernel).  Gradients follow PyTorch's complex convention."""
+
+        @staticmethod
+        def forward(ctx, x, a, b, plan):
+            plan.set_coefficients(a, b)
+            plan.reset()
+            z = plan.filter(x.contiguous())
+            ctx.save_for_backward(x)
+            ctx.plan = plan
+            return z
+
+        @staticmethod
+        def backward(ctx, gz):
+            (x,) = ctx.saved_tensors
+            ga, gb, gx = ctx.plan.backward(x.contiguous(), gz.contiguous(),
+                                          want_gx=ctx.needs_input_grad[0])
+            return gx, ga, gb, None
+
+    return SpiirFilterFunction
+
+
+def spiir_filter(x, a, b, plan):
+    """Differentiable filter: z[D][T][n] from strain x[D][n] (float32) and
+    complex64 coefficient tensors a, b [Ltot] (bank order).  The plan fixes
+    the bank's structure and delays; its streaming state is reset."""
+    return _autograd_function().apply(x, a, b, plan)

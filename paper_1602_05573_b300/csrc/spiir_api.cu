@@ -141,6 +141,14 @@ struct Band {
     int64_t xe_cap = 0;        // samples the workspace holds after the history
     float2 *zb = nullptr;      // [D][T][zb_len] band-rate sums (decimated bands)
     int64_t zb_cap = 0;        // complex samples per row the workspace holds
+    int64_t *slot_filter = nullptr;  // [n_slots] bank filter of each slot, -1 = padding
+    // adjoint workspace
+    float *bw_xe = nullptr;
+    int64_t bw_xe_stride = 0, bw_cap = 0;
+    float2 *bw_state = nullptr;
+    float2 *ckpt = nullptr;
+    int64_t ckpt_cap = 0;      // checkpoints the buffer holds
+    float *acc = nullptr;
 };
 
 struct spiir_plan {
@@ -173,6 +181,11 @@ void free_band(Band &b)
     cudaFree(b.hist);
     cudaFree(b.xe);
     cudaFree(b.zb);
+    cudaFree(b.slot_filter);
+    cudaFree(b.bw_xe);
+    cudaFree(b.bw_state);
+    cudaFree(b.ckpt);
+    cudaFree(b.acc);
     b = Band();
 }
 
@@ -187,7 +200,8 @@ spiir_status upload_band(Band &b, int D)
         (e = dalloc(&b.group_pbase, L.group_pbase.size())) != cudaSuccess ||
         (e = dalloc(&b.warp_info, L.warp_info.size() / 4)) != cudaSuccess ||
         (e = dalloc(&b.state, (size_t)D * L.n_slots)) != cudaSuccess ||
-        (e = dalloc(&b.hist, (size_t)D * L.Dh)) != cudaSuccess)
+        (e = dalloc(&b.hist, (size_t)D * L.Dh)) != cudaSuccess ||
+        (e = dalloc(&b.slot_filter, L.n_slots)) != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "device allocation failed")
                                               : cuda_fail(e, "cudaMalloc");
     if ((e = cudaMemcpy(b.params, L.params.data(), L.params.size() * sizeof(float),
@@ -196,6 +210,7 @@ spiir_status upload_band(Band &b, int D)
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = h2d(b.units, L.units)) != cudaSuccess ||
         (e = h2d(b.group_F, L.group_F)) != cudaSuccess ||
+        (e = h2d(b.slot_filter, L.slot_filter)) != cudaSuccess ||
         (e = h2d(b.group_pbase, L.group_pbase)) != cudaSuccess ||
         (e = cudaMemcpy(b.warp_info, L.warp_info.data(), L.warp_info.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -584,15 +599,118 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
                                    const float *grad_z_dev, float *grad_a_dev,
                                    float *grad_b_dev, float *grad_x_dev, void *stream)
 {
-    (void)x_dev;
-    (void)n;
-    (void)grad_z_dev;
-    (void)grad_a_dev;
-    (void)grad_b_dev;
-    (void)grad_x_dev;
-    (void)stream;
     if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
-    return fail(SPIIR_EUNSUPPORTED, "backward not built yet");
+    if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan cannot run the adjoint");
+    if (p->bands.size() != 1)
+        return fail(SPIIR_EUNSUPPORTED, "the adjoint is built for single-rate banks");
+    if (n < 1 || n > ((int64_t)1 << 30)) return fail(SPIIR_EINVAL, "n must be in [1, 2^30]");
+    if (!x_dev || !grad_z_dev || !grad_a_dev || !grad_b_dev)
+        return fail(SPIIR_EINVAL, "x_dev, grad_z_dev, grad_a_dev and grad_b_dev are required");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    Band &b = p->bands[0];
+    const spiir::Layout &L = b.lay;
+    const int D = p->D;
+    // checkpoint interval: a whole number of blocks, about 1024 samples
+    const int Cc = L.Tb * std::max(1, (1024 + L.Tb - 1) / L.Tb);
+    const int64_t nc = (n + Cc - 1) / Cc;
+    const int64_t need = ((n + L.Tb - 1) / L.Tb) * L.Tb;
+    cudaError_t e;
+    auto oom = [&](cudaError_t err) {
+        return err == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "adjoint workspace")
+                                                : cuda_fail(err, "cudaMalloc");
+    };
+    if (!b.bw_xe || b.bw_cap < need || b.ckpt_cap < nc) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamSynchronize");
+        cudaFree(b.bw_xe);
+        cudaFree(b.ckpt);
+        b.bw_xe = nullptr;
+        b.ckpt = nullptr;
+        b.bw_xe_stride = L.Dh + need;
+        if ((e = dalloc(&b.bw_xe, (size_t)D * b.bw_xe_stride)) != cudaSuccess) return oom(e);
+        if ((e = dalloc(&b.ckpt, (size_t)nc * D * L.n_slots)) != cudaSuccess) return oom(e);
+        b.bw_cap = need;
+        b.ckpt_cap = nc;
+    }
+    if (!b.bw_state) {
+        if ((e = dalloc(&b.bw_state, (size_t)D * L.n_slots)) != cudaSuccess) return oom(e);
+        if ((e = dalloc(&b.acc, (size_t)D * L.n_slots * 6)) != cudaSuccess) return oom(e);
+    }
+    // zero history + x, zero state and accumulators, zero g_x
+    if ((e = cudaMemset2DAsync(b.bw_xe, b.bw_xe_stride * 4, 0, (size_t)L.Dh * 4, D, s)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy2DAsync(b.bw_xe + L.Dh, b.bw_xe_stride * 4, x_dev, n * 4, n * 4, D,
+                               cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(b.bw_state, 0, sizeof(float2) * (size_t)D * L.n_slots, s)) !=
+            cudaSuccess ||
+        (e = cudaMemsetAsync(b.acc, 0, sizeof(float) * 6 * (size_t)D * L.n_slots, s)) !=
+            cudaSuccess ||
+        (grad_x_dev &&
+         (e = cudaMemsetAsync(grad_x_dev, 0, sizeof(float) * (size_t)D * n, s)) != cudaSuccess))
+        return cuda_fail(e, "adjoint staging");
+    // forward pass from zero state, keeping the state every Cc samples
+    spiir::K1Args f{};
+    f = k1_args(p, b, n, nullptr, n, false);
+    f.xe = b.bw_xe;
+    f.xe_stride = b.bw_xe_stride;
+    f.state = b.bw_state;
+    f.t0 = 0;
+    f.ckpt = b.ckpt;
+    f.ckpt_blocks = Cc / L.Tb;
+    f.n_det = D;
+    if ((e = spiir::launch_k1(f, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
+        return cuda_fail(e, "adjoint forward launch");
+    // reverse pass
+    spiir::K6Args a{};
+    a.xe = b.bw_xe;
+    a.xe_stride = b.bw_xe_stride;
+    a.n = (int32_t)n;
+    a.Dh = L.Dh;
+    a.W = L.W;
+    a.Cc = Cc;
+    a.gz = reinterpret_cast<const float2 *>(grad_z_dev);
+    a.T = p->T;
+    a.units = b.units;
+    a.group_F = b.group_F;
+    a.group_pbase = b.group_pbase;
+    a.warp_info = b.warp_info;
+    a.params = b.params;
+    a.ringoff = b.ringoff;
+    a.ckpt = b.ckpt;
+    a.n_slots = L.n_slots;
+    a.n_det = D;
+    a.acc = b.acc;
+    a.gx = grad_x_dev;
+    if (spiir::k6_smem_bytes(L.W, Cc, L.Dh) > 227 * 1024)
+        return fail(SPIIR_EUNSUPPORTED, "adjoint shared memory above 227 KB for this plan; "
+                                        "use fewer warps per CTA");
+    if ((e = spiir::launch_k6(a, L.n_units(), s)) != cudaSuccess)
+        return cuda_fail(e, "adjoint kernel launch");
+    if ((e = spiir::launch_adj_finalize(b.acc, b.slot_filter, L.n_slots, D,
+                                        reinterpret_cast<float2 *>(grad_a_dev),
+                                        reinterpret_cast<float2 *>(grad_b_dev), s)) !=
+        cudaSuccess)
+        return cuda_fail(e, "adjoint finalize launch");
+    return SPIIR_OK;
+}
+
+spiir_status spiir_set_coefficients(spiir_plan *p, const float *a_reim_dev,
+                                    const float *b_reim_dev, void *stream)
+{
+    if (!p || !a_reim_dev || !b_reim_dev) return fail(SPIIR_EINVAL, "NULL argument");
+    if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan has no device coefficients");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    for (Band &b : p->bands) {
+        cudaError_t e = spiir::launch_set_coefficients(
+            reinterpret_cast<const float2 *>(a_reim_dev),
+            reinterpret_cast<const float2 *>(b_reim_dev), b.slot_filter, b.lay.n_slots, b.params,
+            (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "coefficient update launch");
+    }
+    return SPIIR_OK;
 }
 
 spiir_status spiir_state_get(spiir_plan *p, float *state, float *history, int64_t *samples)

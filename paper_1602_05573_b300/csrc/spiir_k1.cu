@@ -373,6 +373,20 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
                 if (pos[r] >= A.R) pos[r] -= A.R;
             }
         }
+        // checkpoint of the filter state (for the adjoint's recompute)
+        if (A.ckpt != nullptr && active && (j + 1) % A.ckpt_blocks == 0 && j + 1 < nblk) {
+            const int64_t c = (j + 1) / A.ckpt_blocks;
+            float2 *row = A.ckpt + (c * A.n_det + det) * A.n_slots;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                float r0, r1, i0, i1;
+                upk(YR[q], r0, r1);
+                upk(YI[q], i0, i1);
+                row[pb + ((int64_t)(2 * q) * A.W + warp) * 32 + lane] = make_float2(r0, i0);
+                row[pb + ((int64_t)(2 * q + 1) * A.W + warp) * 32 + lane] = make_float2(r1, i1);
+            }
+            if (ODD) row[pb + ((int64_t)(F - 1) * A.W + warp) * 32 + lane] = make_float2(yr1, yi1);
+        }
         // every warp is done with the ring slot the next copy overwrites, and
         // this block's per-warp sums are visible
         __syncthreads();

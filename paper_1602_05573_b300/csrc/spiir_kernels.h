@@ -41,7 +41,45 @@ struct K1Args {
     uint64_t wait_limit_ns;    // bound on every mbarrier wait
     int32_t n_lower;           // lower bands added in the combine (0 = single rate)
     LowerBand lower[kMaxLowerBands];
+    float2 *ckpt;              // [nc][D][n_slots] state after sample c*ckpt_blocks*Tb - 1
+                               // (c >= 1), kernel form; null = no checkpoints
+    int32_t ckpt_blocks;       // blocks between checkpoints
+    int32_t n_det;             // detectors (checkpoint row stride)
 };
+
+// Adjoint (reverse-time) kernel of one zero-state filter call.
+struct K6Args {
+    const float *xe;           // [D][xe_stride]: Dh zeros, then the call's strain
+    int64_t xe_stride;
+    int32_t n;                 // samples
+    int32_t Dh;                // history samples before x in xe (>= max delay)
+    int32_t W, Cc;             // warps per CTA, checkpoint interval (samples)
+    const float2 *gz;          // [D][T][n] dL/dRe z + i dL/dIm z
+    int64_t T;
+    const int32_t *units;
+    const int32_t *group_F;
+    const int64_t *group_pbase;
+    const int4 *warp_info;
+    const float4 *params;      // kernel form (odd lanes hold conj(a), (Im b, Re b))
+    const int2 *ringoff;
+    const float2 *ckpt;        // [nc][D][n_slots] from the forward pass
+    int64_t n_slots;
+    int32_t n_det;
+    float *acc;                // [D][n_slots][6] (mu re, im, g_a re, im, g_b re, im)
+    float *gx;                 // [D][n] accumulated with atomics, or null
+};
+constexpr int kAdjSub = 16;    // samples per recomputed span in the adjoint
+
+cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s);
+// smem bytes the adjoint kernel needs
+int k6_smem_bytes(int W, int Cc, int Dh);
+// g_a[f] = sum_det acc[det][s].ga, g_b likewise, for every slot s holding filter f
+cudaError_t launch_adj_finalize(const float *acc, const int64_t *slot_filter, int64_t n_slots,
+                                int D, float2 *ga, float2 *gb, cudaStream_t s);
+// params[s] = kernel form of (a[f], b[f]) for every slot s holding filter f
+cudaError_t launch_set_coefficients(const float2 *a, const float2 *b,
+                                    const int64_t *slot_filter, int64_t n_slots,
+                                    float4 *params, cudaStream_t s);
 
 cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s);
 
