@@ -106,4 +106,4 @@ def test_autograd_function_and_a_fitting_step(sp):
     with torch.no_grad():
         b2 = b - 1e-3 * b.grad / b.grad.abs().max() * b.abs().max()
         loss2 = torch.sum(torch.abs(sp.spiir_filter(x, a.detach(), b2, plan) - z_t) ** 2)
-    assert float(loss2) < float(loss)
+    assert float(loss2) < float(loss.detach())
