@@ -142,6 +142,8 @@ struct Band {
     float2 *zb = nullptr;      // [D][T][zb_len] band-rate sums (decimated bands)
     int64_t zb_cap = 0;        // complex samples per row the workspace holds
     int64_t *slot_filter = nullptr;  // [n_slots] bank filter of each slot, -1 = padding
+    void *state_ext = nullptr;       // compensated / chunked state, 16 B per slot and detector
+    double2 *aT = nullptr;           // chunked: a^chunk per slot (FP64)
     // adjoint workspace
     float *bw_xe = nullptr;
     int64_t bw_xe_stride = 0, bw_cap = 0;
@@ -182,6 +184,8 @@ void free_band(Band &b)
     cudaFree(b.xe);
     cudaFree(b.zb);
     cudaFree(b.slot_filter);
+    cudaFree(b.state_ext);
+    cudaFree(b.aT);
     cudaFree(b.bw_xe);
     cudaFree(b.bw_state);
     cudaFree(b.ckpt);
@@ -189,10 +193,48 @@ void free_band(Band &b)
     b = Band();
 }
 
-spiir_status upload_band(Band &b, int D)
+// a^T in double for every slot, from the kernel-form (stored) pole
+std::vector<double2> powers(const spiir::Layout &L, int T)
+{
+    std::vector<double2> out((size_t)L.n_slots);
+    for (int64_t s = 0; s < L.n_slots; ++s) {
+        double br = L.params[4 * s], bi = L.params[4 * s + 1];  // base
+        double rr = 1.0, ri = 0.0;                              // result
+        for (int e = T; e > 0; e >>= 1) {
+            if (e & 1) {
+                const double nr = rr * br - ri * bi, ni = rr * bi + ri * br;
+                rr = nr;
+                ri = ni;
+            }
+            const double nr = br * br - bi * bi, ni = 2.0 * br * bi;
+            br = nr;
+            bi = ni;
+        }
+        out[(size_t)s] = make_double2(rr, ri);
+    }
+    return out;
+}
+
+spiir_status upload_band(Band &b, int D, int precision, int chunk)
 {
     const spiir::Layout &L = b.lay;
     cudaError_t e;
+    if (precision != SPIIR_PREC_PLAIN) {
+        if ((e = dalloc(reinterpret_cast<double2 **>(&b.state_ext), (size_t)D * L.n_slots)) !=
+            cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "device allocation failed")
+                                                  : cuda_fail(e, "cudaMalloc");
+        if ((e = cudaMemset(b.state_ext, 0, sizeof(double2) * (size_t)D * L.n_slots)) !=
+            cudaSuccess)
+            return cuda_fail(e, "plan upload");
+    }
+    if (precision == SPIIR_PREC_CHUNKED_FP64) {
+        const std::vector<double2> aT = powers(L, chunk);
+        if ((e = dalloc(&b.aT, aT.size())) != cudaSuccess ||
+            (e = cudaMemcpy(b.aT, aT.data(), aT.size() * sizeof(double2),
+                            cudaMemcpyHostToDevice)) != cudaSuccess)
+            return cuda_fail(e, "plan upload");
+    }
     if ((e = dalloc(&b.params, L.n_slots)) != cudaSuccess ||
         (e = dalloc(&b.ringoff, L.n_slots)) != cudaSuccess ||
         (e = dalloc(&b.units, L.units.size())) != cudaSuccess ||
@@ -262,6 +304,13 @@ spiir::K1Args k1_args(const spiir_plan *p, const Band &b, int64_t n, float *z, i
     a.group_pbase = b.group_pbase;
     a.warp_info = b.warp_info;
     a.fcap = L.Fcap;
+    a.mode = p->precision == SPIIR_PREC_COMPENSATED
+                 ? spiir::kModeCompensated
+                 : (p->precision == SPIIR_PREC_CHUNKED_FP64 ? spiir::kModeChunked
+                                                            : spiir::kModePlain);
+    a.chunk = p->opt.chunk_len;
+    a.state_ext = b.state_ext;
+    a.aT = b.aT;
     a.params = b.params;
     a.ringoff = b.ringoff;
     a.state = b.state;
@@ -319,8 +368,11 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     spiir_options opt;
     spiir_options_default(&opt);
     if (opt_in) opt = *opt_in;
-    if (opt.precision != SPIIR_PREC_PLAIN)
-        return fail(SPIIR_EUNSUPPORTED, "precision mode not built yet");
+    if (opt.precision == SPIIR_PREC_CHUNKED_TC)
+        return fail(SPIIR_EUNSUPPORTED, "the tensor-core chunked projection is not built yet");
+    if (opt.precision < SPIIR_PREC_PLAIN || opt.precision > SPIIR_PREC_CHUNKED_TC)
+        return fail(SPIIR_EINVAL, "unknown precision mode");
+    if (opt.chunk_len == 0) opt.chunk_len = 256;
     if (opt.block_len != 0 && (opt.block_len < 32 || opt.block_len % 32 != 0))
         return fail(SPIIR_EINVAL, "block_len must be 0 or a multiple of 32");
 
@@ -363,6 +415,13 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     lo.Tb = opt.block_len ? opt.block_len : 512;
     lo.C = opt.ring_copies;
     lo.Fcap = opt.max_filters_per_lane;
+    if (opt.precision != SPIIR_PREC_PLAIN) {
+        // the compensated and chunked kernels hold at most kPreciseFcap filters per lane
+        if (lo.Fcap == 0 || lo.Fcap > spiir::kPreciseFcap) lo.Fcap = spiir::kPreciseFcap;
+        if (opt.chunk_len < 8 || opt.chunk_len % 8 != 0 || lo.Tb % opt.chunk_len != 0)
+            return fail(SPIIR_EINVAL, "chunk_len must be a multiple of 8 dividing block_len (" +
+                                          std::to_string(lo.Tb) + ")");
+    }
     lo.n_sm = n_sm;
     p->bands.resize(decims.size());
     for (size_t j = 0; j < decims.size(); ++j) {
@@ -401,7 +460,7 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
         return cuda_fail(guard.err, "cudaSetDevice");
     }
     for (Band &b : p->bands) {
-        st = upload_band(b, p->D);
+        st = upload_band(b, p->D, p->precision, p->opt.chunk_len);
         if (st != SPIIR_OK) {
             spiir_plan_destroy(p);
             return st;
@@ -495,7 +554,10 @@ spiir_status spiir_reset(spiir_plan *p, void *stream)
         if ((e = cudaMemsetAsync(b.state, 0, sizeof(float2) * (size_t)p->D * b.lay.n_slots, s)) !=
                 cudaSuccess ||
             (e = cudaMemsetAsync(b.hist, 0, sizeof(float) * (size_t)p->D * b.lay.Dh, s)) !=
-                cudaSuccess)
+                cudaSuccess ||
+            (b.state_ext &&
+             (e = cudaMemsetAsync(b.state_ext, 0, sizeof(double2) * (size_t)p->D * b.lay.n_slots,
+                                  s)) != cudaSuccess))
             return cuda_fail(e, "reset");
     }
     if ((e = spiir::launch_peak_reset(p->peak_best, p->peak_idx, (int64_t)p->D * p->T, s)) !=
@@ -653,6 +715,7 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     // forward pass from zero state, keeping the state every Cc samples
     spiir::K1Args f{};
     f = k1_args(p, b, n, nullptr, n, false);
+    f.mode = spiir::kModePlain;   // checkpoints come from the FP32 recurrence
     f.xe = b.bw_xe;
     f.xe_stride = b.bw_xe_stride;
     f.state = b.bw_state;
@@ -726,8 +789,24 @@ spiir_status spiir_state_get(spiir_plan *p, float *state, float *history, int64_
         for (const Band &b : p->bands) {
             const spiir::Layout &L = b.lay;
             std::vector<float> dev((size_t)2 * p->D * L.n_slots);
-            e = cudaMemcpy(dev.data(), b.state, dev.size() * sizeof(float),
-                           cudaMemcpyDeviceToHost);
+            if (p->precision == SPIIR_PREC_PLAIN) {
+                e = cudaMemcpy(dev.data(), b.state, dev.size() * sizeof(float),
+                               cudaMemcpyDeviceToHost);
+            } else {  // 16-byte extended state, rounded to complex64
+                std::vector<double2> ext((size_t)p->D * L.n_slots);
+                e = cudaMemcpy(ext.data(), b.state_ext, ext.size() * sizeof(double2),
+                               cudaMemcpyDeviceToHost);
+                for (size_t i = 0; i < ext.size(); ++i) {
+                    if (p->precision == SPIIR_PREC_COMPENSATED) {
+                        const float4 v = *reinterpret_cast<const float4 *>(&ext[i]);
+                        dev[2 * i] = v.x + v.y;
+                        dev[2 * i + 1] = v.z + v.w;
+                    } else {
+                        dev[2 * i] = (float)ext[i].x;
+                        dev[2 * i + 1] = (float)ext[i].y;
+                    }
+                }
+            }
             if (e != cudaSuccess) return cuda_fail(e, "state copy");
             for (int det = 0; det < p->D; ++det)
                 for (int64_t s = 0; s < L.n_slots; ++s) {
@@ -775,8 +854,21 @@ spiir_status spiir_state_set(spiir_plan *p, const float *state, const float *his
                     dev[2 * ((size_t)det * L.n_slots + s)] = swapped ? im : re;
                     dev[2 * ((size_t)det * L.n_slots + s) + 1] = swapped ? re : im;
                 }
-            e = cudaMemcpy(b.state, dev.data(), dev.size() * sizeof(float),
-                           cudaMemcpyHostToDevice);
+            if (p->precision == SPIIR_PREC_PLAIN) {
+                e = cudaMemcpy(b.state, dev.data(), dev.size() * sizeof(float),
+                               cudaMemcpyHostToDevice);
+            } else {  // extended state from complex64 (low parts zero)
+                std::vector<double2> ext((size_t)p->D * L.n_slots);
+                for (size_t i = 0; i < ext.size(); ++i) {
+                    if (p->precision == SPIIR_PREC_COMPENSATED)
+                        *reinterpret_cast<float4 *>(&ext[i]) =
+                            make_float4(dev[2 * i], 0.f, dev[2 * i + 1], 0.f);
+                    else
+                        ext[i] = make_double2(dev[2 * i], dev[2 * i + 1]);
+                }
+                e = cudaMemcpy(b.state_ext, ext.data(), ext.size() * sizeof(double2),
+                               cudaMemcpyHostToDevice);
+            }
             if (e != cudaSuccess) return cuda_fail(e, "state copy");
         }
     }

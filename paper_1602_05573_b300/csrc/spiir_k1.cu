@@ -221,34 +221,22 @@ __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb,
     }
 }
 
-// ---- one CTA work unit: W warps x one detector, whole call ----------------
-template <int F>
-__device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float *ring,
-                                         float *zbuf, uint32_t bar0, uint32_t bar1)
-{
-    constexpr int NP = F / 2;              // filter pairs (packed FP32x2)
-    constexpr bool ODD = (F & 1) != 0;     // one more filter in scalar FP32
-    constexpr int NPA = NP > 0 ? NP : 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int4 wi = A.warp_info[(int64_t)g * A.W + warp];
-    const int tmpl = wi.x;
-    const bool active = tmpl >= 0;
-    const bool leader = active && wi.y == warp;
-    const int64_t pb = A.group_pbase[g];
-    const int n = A.n;
-    const int nblk = (n + A.Tb - 1) / A.Tb;
-    const float *xrow = A.xe + (int64_t)det * A.xe_stride;
+// ---- arithmetic policies: one lane's F filters --------------------------
+// Each policy keeps its filters' coefficients and state in registers and
+// advances them 8 samples at a time, returning this lane's per-sample sums.
+// ring[base[r] + t] is the strain sample filter r reads at sample t.
 
-    // parameters and state of this lane's F filters
+// Plain FP32: two filters per packed FP32x2 instruction (8 packed ops per
+// filter pair and sample), an odd filter in scalar FP32.
+template <int F> struct PackedLanes {
+    static constexpr int NP = F / 2;
+    static constexpr bool ODD = (F & 1) != 0;
+    static constexpr int NPA = NP > 0 ? NP : 1;
     uint64_t AR[NPA], AI[NPA], NAI[NPA], BR[NPA], BI[NPA], YR[NPA], YI[NPA];
     float ar1 = 0.f, ai1 = 0.f, br1 = 0.f, bi1 = 0.f, yr1 = 0.f, yi1 = 0.f;
-    int pos[F], cb[F];
-#pragma unroll
-    for (int r = 0; r < F; ++r) {
-        pos[r] = 0;
-        cb[r] = 0;
-    }
-    if (active) {
+
+    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    {
         float4 p[F];
         float2 st[F];
 #pragma unroll
@@ -256,9 +244,6 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             const int64_t s = pb + ((int64_t)r * A.W + warp) * 32 + lane;
             p[r] = A.params[s];
             st[r] = A.state[(int64_t)det * A.n_slots + s];
-            const int2 ro = A.ringoff[s];
-            pos[r] = ro.x;
-            cb[r] = ro.y;
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
@@ -278,6 +263,313 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             yr1 = st[F - 1].x;
             yi1 = st[F - 1].y;
         }
+    }
+    __device__ __forceinline__ float2 state_of(int r) const
+    {
+        float lo, hi, ilo, ihi;
+        if (ODD && r == F - 1) return make_float2(yr1, yi1);
+        upk(YR[r / 2], lo, hi);
+        upk(YI[r / 2], ilo, ihi);
+        return (r & 1) ? make_float2(hi, ihi) : make_float2(lo, ilo);
+    }
+    __device__ __forceinline__ void step8(const float *ring, const int (&base)[F], int valid,
+                                          float (&zr)[kTS], float (&zi)[kTS])
+    {
+#pragma unroll
+        for (int t = 0; t < kTS; ++t) {
+            if (valid < kTS && t >= valid) {  // ragged tail: state stays put
+                zr[t] = 0.f;
+                zi[t] = 0.f;
+                continue;
+            }
+            uint64_t ZR = 0, ZI = 0;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) {
+                const float xf = ring[base[2 * q] + t];
+                const float xg = ring[base[2 * q + 1] + t];
+                const uint64_t X = pk(xf, xg);
+                uint64_t TR = mul2(BR[q], X);
+                uint64_t TI = mul2(BI[q], X);
+                TR = fma2(NAI[q], YI[q], TR);   // br x - ai yi
+                TI = fma2(AI[q], YR[q], TI);    // bi x + ai yr
+                YR[q] = fma2(AR[q], YR[q], TR); // ar yr - ai yi + br x
+                YI[q] = fma2(AR[q], YI[q], TI); // ar yi + ai yr + bi x
+                if (q == 0) {
+                    ZR = YR[0];
+                    ZI = YI[0];
+                } else {
+                    ZR = add2(ZR, YR[q]);
+                    ZI = add2(ZI, YI[q]);
+                }
+            }
+            float sr = 0.f, si = 0.f;
+            if (NP > 0) {
+                float lo, hi;
+                upk(ZR, lo, hi);
+                sr = lo + hi;
+                upk(ZI, lo, hi);
+                si = lo + hi;
+            }
+            if (ODD) {
+                const float x1 = ring[base[F - 1] + t];
+                const float nr = fmaf(ar1, yr1, fmaf(-ai1, yi1, br1 * x1));
+                const float ni = fmaf(ar1, yi1, fmaf(ai1, yr1, bi1 * x1));
+                yr1 = nr;
+                yi1 = ni;
+                sr = NP > 0 ? sr + yr1 : yr1;
+                si = NP > 0 ? si + yi1 : yi1;
+            }
+            zr[t] = sr;
+            zi[t] = si;
+        }
+    }
+    __device__ __forceinline__ void after8(const K1Args &, int) {}
+    __device__ __forceinline__ void finish(const K1Args &, int) {}
+    __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    {
+#pragma unroll
+        for (int r = 0; r < F; ++r)
+            A.state[(int64_t)det * A.n_slots + pb + ((int64_t)r * A.W + warp) * 32 + lane] =
+                state_of(r);
+    }
+};
+
+// Float-float helpers (Dekker/Knuth): exact product error by FMA, exact sum
+// error by the six-operation two-sum; explicit round-to-nearest intrinsics
+// keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e)
+{
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// Compensated: each filter's state is a float-float pair (hi + lo, about 48
+// significant bits); the update is exact up to the low-order sum.
+template <int F> struct CompLanes {
+    float ar[F], ai[F], br[F], bi[F], yrh[F], yrl[F], yih[F], yil[F];
+
+    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    {
+        const float4 *st = reinterpret_cast<const float4 *>(A.state_ext);
+#pragma unroll
+        for (int r = 0; r < F; ++r) {
+            const int64_t s = pb + ((int64_t)r * A.W + warp) * 32 + lane;
+            const float4 p = A.params[s];
+            const float4 y = st[(int64_t)det * A.n_slots + s];
+            ar[r] = p.x;
+            ai[r] = p.y;
+            br[r] = p.z;
+            bi[r] = p.w;
+            yrh[r] = y.x;
+            yrl[r] = y.y;
+            yih[r] = y.z;
+            yil[r] = y.w;
+        }
+    }
+    __device__ __forceinline__ void step8(const float *ring, const int (&base)[F], int valid,
+                                          float (&zr)[kTS], float (&zi)[kTS])
+    {
+#pragma unroll
+        for (int t = 0; t < kTS; ++t) {
+            if (valid < kTS && t >= valid) {
+                zr[t] = 0.f;
+                zi[t] = 0.f;
+                continue;
+            }
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int r = 0; r < F; ++r) {
+                const float x = ring[base[r] + t];
+                float p1, e1, p2, e2, p3, e3, s1, t1, s2, t2;
+                // Re: ar yr - ai yi + br x
+                two_prod(ar[r], yrh[r], p1, e1);
+                two_prod(-ai[r], yih[r], p2, e2);
+                two_prod(br[r], x, p3, e3);
+                two_sum(p1, p2, s1, t1);
+                two_sum(s1, p3, s2, t2);
+                const float lr = __fadd_rn(__fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, t1)),
+                                           __fadd_rn(t2, __fmaf_rn(ar[r], yrl[r],
+                                                                   __fmul_rn(-ai[r], yil[r]))));
+                // Im: ar yi + ai yr + bi x
+                float q1, f1, q2, f2, q3, f3, u1, v1, u2, v2;
+                two_prod(ar[r], yih[r], q1, f1);
+                two_prod(ai[r], yrh[r], q2, f2);
+                two_prod(bi[r], x, q3, f3);
+                two_sum(q1, q2, u1, v1);
+                two_sum(u1, q3, u2, v2);
+                const float li = __fadd_rn(__fadd_rn(__fadd_rn(f1, f2), __fadd_rn(f3, v1)),
+                                           __fadd_rn(v2, __fmaf_rn(ar[r], yil[r],
+                                                                   __fmul_rn(ai[r], yrl[r]))));
+                fast_two_sum(s2, lr, yrh[r], yrl[r]);
+                fast_two_sum(u2, li, yih[r], yil[r]);
+                sr += __fadd_rn(yrh[r], yrl[r]);
+                si += __fadd_rn(yih[r], yil[r]);
+            }
+            zr[t] = sr;
+            zi[t] = si;
+        }
+    }
+    __device__ __forceinline__ void after8(const K1Args &, int) {}
+    __device__ __forceinline__ void finish(const K1Args &, int) {}
+    __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    {
+        float4 *st = reinterpret_cast<float4 *>(A.state_ext);
+#pragma unroll
+        for (int r = 0; r < F; ++r)
+            st[(int64_t)det * A.n_slots + pb + ((int64_t)r * A.W + warp) * 32 + lane] =
+                make_float4(yrh[r], yrl[r], yih[r], yil[r]);
+    }
+    __device__ __forceinline__ float2 state_of(int r) const
+    {
+        return make_float2(yrh[r] + yrl[r], yih[r] + yil[r]);
+    }
+};
+
+// Chunked scan with an FP64 carry (chunks of A.chunk samples from the start
+// of the call).  Per chunk each filter runs two FP32 recurrences on the same
+// strain: y from the anchored state (its outputs feed z) and u from zero
+// state (the chunk's input projection S = sum_j a^(T-1-j) b x[...]).  At the
+// chunk end the anchor advances in FP64, s <- a^T s + S, and y restarts from
+// s rounded to FP32, so FP32 error never builds up over more than one chunk.
+template <int F> struct ChunkLanes {
+    float ar[F], ai[F], br[F], bi[F], yr[F], yi[F], ur[F], ui[F];
+    double aTr[F], aTi[F], sr64[F], si64[F];
+
+    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    {
+        const double2 *st = reinterpret_cast<const double2 *>(A.state_ext);
+#pragma unroll
+        for (int r = 0; r < F; ++r) {
+            const int64_t s = pb + ((int64_t)r * A.W + warp) * 32 + lane;
+            const float4 p = A.params[s];
+            const double2 y = st[(int64_t)det * A.n_slots + s];
+            const double2 t = A.aT[s];
+            ar[r] = p.x;
+            ai[r] = p.y;
+            br[r] = p.z;
+            bi[r] = p.w;
+            sr64[r] = y.x;
+            si64[r] = y.y;
+            yr[r] = (float)y.x;
+            yi[r] = (float)y.y;
+            ur[r] = 0.f;
+            ui[r] = 0.f;
+            aTr[r] = t.x;
+            aTi[r] = t.y;
+        }
+    }
+    __device__ __forceinline__ void step8(const float *ring, const int (&base)[F], int valid,
+                                          float (&zr)[kTS], float (&zi)[kTS])
+    {
+#pragma unroll
+        for (int t = 0; t < kTS; ++t) {
+            if (valid < kTS && t >= valid) {
+                zr[t] = 0.f;
+                zi[t] = 0.f;
+                continue;
+            }
+            float sr = 0.f, si = 0.f;
+#pragma unroll
+            for (int r = 0; r < F; ++r) {
+                const float x = ring[base[r] + t];
+                const float bx = br[r] * x, by = bi[r] * x;
+                const float nr = fmaf(ar[r], yr[r], fmaf(-ai[r], yi[r], bx));
+                const float ni = fmaf(ar[r], yi[r], fmaf(ai[r], yr[r], by));
+                const float mr = fmaf(ar[r], ur[r], fmaf(-ai[r], ui[r], bx));
+                const float mi = fmaf(ar[r], ui[r], fmaf(ai[r], ur[r], by));
+                yr[r] = nr;
+                yi[r] = ni;
+                ur[r] = mr;
+                ui[r] = mi;
+                sr += nr;
+                si += ni;
+            }
+            zr[t] = sr;
+            zi[t] = si;
+        }
+    }
+    __device__ __forceinline__ void carry()
+    {
+#pragma unroll
+        for (int r = 0; r < F; ++r) {
+            const double nr = fma(aTr[r], sr64[r], fma(-aTi[r], si64[r], (double)ur[r]));
+            const double ni = fma(aTr[r], si64[r], fma(aTi[r], sr64[r], (double)ui[r]));
+            sr64[r] = nr;
+            si64[r] = ni;
+            yr[r] = (float)nr;
+            yi[r] = (float)ni;
+            ur[r] = 0.f;
+            ui[r] = 0.f;
+        }
+    }
+    // kend: samples of the call processed so far
+    __device__ __forceinline__ void after8(const K1Args &A, int kend)
+    {
+        if (kend % A.chunk == 0) carry();
+    }
+    // a call that ends inside a chunk keeps the FP32 state as its anchor
+    __device__ __forceinline__ void finish(const K1Args &A, int n)
+    {
+        if (n % A.chunk != 0) {
+#pragma unroll
+            for (int r = 0; r < F; ++r) {
+                sr64[r] = yr[r];
+                si64[r] = yi[r];
+            }
+        }
+    }
+    __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    {
+        double2 *st = reinterpret_cast<double2 *>(A.state_ext);
+#pragma unroll
+        for (int r = 0; r < F; ++r)
+            st[(int64_t)det * A.n_slots + pb + ((int64_t)r * A.W + warp) * 32 + lane] =
+                make_double2(sr64[r], si64[r]);
+    }
+    __device__ __forceinline__ float2 state_of(int r) const { return make_float2(yr[r], yi[r]); }
+};
+
+// ---- one CTA work unit: W warps x one detector, whole call ----------------
+template <template <int> class LANES, int F>
+__device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float *ring,
+                                         float *zbuf, uint32_t bar0, uint32_t bar1)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int4 wi = A.warp_info[(int64_t)g * A.W + warp];
+    const int tmpl = wi.x;
+    const bool active = tmpl >= 0;
+    const bool leader = active && wi.y == warp;
+    const int64_t pb = A.group_pbase[g];
+    const int n = A.n;
+    const int nblk = (n + A.Tb - 1) / A.Tb;
+    const float *xrow = A.xe + (int64_t)det * A.xe_stride;
+
+    LANES<F> L;
+    int pos[F], cb[F];
+#pragma unroll
+    for (int r = 0; r < F; ++r) {
+        pos[r] = 0;
+        cb[r] = 0;
+    }
+    if (active) {
+#pragma unroll
+        for (int r = 0; r < F; ++r) {
+            const int2 ro = A.ringoff[pb + ((int64_t)r * A.W + warp) * 32 + lane];
+            pos[r] = ro.x;
+            cb[r] = ro.y;
+        }
+        L.load(A, pb, warp, lane, det);
     }
     float *zrow = (A.z != nullptr && leader)
                       ? A.z + ((int64_t)det * A.T + tmpl) * 2 * A.z_len
@@ -316,54 +608,9 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             for (int sb = 0; sb < nv; sb += kTS) {
                 const int valid = nv - sb;
                 float zr[kTS], zi[kTS];
-#pragma unroll
-                for (int t = 0; t < kTS; ++t) {
-                    if (valid < kTS && t >= valid) {  // ragged tail: state stays put
-                        zr[t] = 0.f;
-                        zi[t] = 0.f;
-                        continue;
-                    }
-                    uint64_t ZR = 0, ZI = 0;
-#pragma unroll
-                    for (int q = 0; q < NP; ++q) {
-                        const float xf = ring[base[2 * q] + t];
-                        const float xg = ring[base[2 * q + 1] + t];
-                        const uint64_t X = pk(xf, xg);
-                        uint64_t TR = mul2(BR[q], X);
-                        uint64_t TI = mul2(BI[q], X);
-                        TR = fma2(NAI[q], YI[q], TR);   // br x - ai yi
-                        TI = fma2(AI[q], YR[q], TI);    // bi x + ai yr
-                        YR[q] = fma2(AR[q], YR[q], TR); // ar yr - ai yi + br x
-                        YI[q] = fma2(AR[q], YI[q], TI); // ar yi + ai yr + bi x
-                        if (q == 0) {
-                            ZR = YR[0];
-                            ZI = YI[0];
-                        } else {
-                            ZR = add2(ZR, YR[q]);
-                            ZI = add2(ZI, YI[q]);
-                        }
-                    }
-                    float sr = 0.f, si = 0.f;
-                    if (NP > 0) {
-                        float lo, hi;
-                        upk(ZR, lo, hi);
-                        sr = lo + hi;
-                        upk(ZI, lo, hi);
-                        si = lo + hi;
-                    }
-                    if (ODD) {
-                        const float x1 = ring[base[F - 1] + t];
-                        const float nr = fmaf(ar1, yr1, fmaf(-ai1, yi1, br1 * x1));
-                        const float ni = fmaf(ar1, yi1, fmaf(ai1, yr1, bi1 * x1));
-                        yr1 = nr;
-                        yi1 = ni;
-                        sr = NP > 0 ? sr + yr1 : yr1;
-                        si = NP > 0 ? si + yi1 : yi1;
-                    }
-                    zr[t] = sr;
-                    zi[t] = si;
-                }
+                L.step8(ring, base, valid, zr, zi);
                 warp_sum8(zr, zi, lane, zw + 2 * sb);
+                L.after8(A, k0 + sb + min(valid, kTS));
 #pragma unroll
                 for (int r = 0; r < F; ++r) base[r] += kTS;
             }
@@ -372,20 +619,14 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
                 pos[r] += A.Tb;
                 if (pos[r] >= A.R) pos[r] -= A.R;
             }
-        }
-        // checkpoint of the filter state (for the adjoint's recompute)
-        if (A.ckpt != nullptr && active && (j + 1) % A.ckpt_blocks == 0 && j + 1 < nblk) {
-            const int64_t c = (j + 1) / A.ckpt_blocks;
-            float2 *row = A.ckpt + (c * A.n_det + det) * A.n_slots;
+            // checkpoint of the filter state (for the adjoint's recompute)
+            if (A.ckpt != nullptr && (j + 1) % A.ckpt_blocks == 0 && j + 1 < nblk) {
+                const int64_t c = (j + 1) / A.ckpt_blocks;
+                float2 *row = A.ckpt + (c * A.n_det + det) * A.n_slots;
 #pragma unroll
-            for (int q = 0; q < NP; ++q) {
-                float r0, r1, i0, i1;
-                upk(YR[q], r0, r1);
-                upk(YI[q], i0, i1);
-                row[pb + ((int64_t)(2 * q) * A.W + warp) * 32 + lane] = make_float2(r0, i0);
-                row[pb + ((int64_t)(2 * q + 1) * A.W + warp) * 32 + lane] = make_float2(r1, i1);
+                for (int r = 0; r < F; ++r)
+                    row[pb + ((int64_t)r * A.W + warp) * 32 + lane] = L.state_of(r);
             }
-            if (ODD) row[pb + ((int64_t)(F - 1) * A.W + warp) * 32 + lane] = make_float2(yr1, yi1);
         }
         // every warp is done with the ring slot the next copy overwrites, and
         // this block's per-warp sums are visible
@@ -413,22 +654,8 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
         return;
     }
     if (!active) return;
-
-    // state out
-#pragma unroll
-    for (int q = 0; q < NP; ++q) {
-        float r0, r1, i0, i1;
-        upk(YR[q], r0, r1);
-        upk(YI[q], i0, i1);
-        const int64_t s0 = pb + ((int64_t)(2 * q) * A.W + warp) * 32 + lane;
-        const int64_t s1 = pb + ((int64_t)(2 * q + 1) * A.W + warp) * 32 + lane;
-        A.state[(int64_t)det * A.n_slots + s0] = make_float2(r0, i0);
-        A.state[(int64_t)det * A.n_slots + s1] = make_float2(r1, i1);
-    }
-    if (ODD) {
-        const int64_t s = pb + ((int64_t)(F - 1) * A.W + warp) * 32 + lane;
-        A.state[(int64_t)det * A.n_slots + s] = make_float2(yr1, yi1);
-    }
+    L.finish(A, n);
+    L.store(A, pb, warp, lane, det);
     // running peak: largest |z|^2, earliest index on ties
     if (leader && A.peak_best != nullptr) {
 #pragma unroll
@@ -460,35 +687,70 @@ template <> struct K1Bounds<6> { static constexpr int kMinBlocks = 2; };
 template <> struct K1Bounds<8> { static constexpr int kMinBlocks = 2; };
 template <> struct K1Bounds<10> { static constexpr int kMinBlocks = 2; };
 
-template <int FCAP>
-__global__ void __launch_bounds__(256, K1Bounds<FCAP>::kMinBlocks) k1_plain(const K1Args A)
+// The CTA's F is uniform, so every warp takes the same case.
+template <template <int> class LANES, int FCAP>
+__device__ __forceinline__ void dispatch_f(const K1Args &A, int g, int det, float *ring,
+                                           float *zbuf, uint32_t bar0, uint32_t bar1)
 {
-    extern __shared__ __align__(128) unsigned char smem[];
+    const int F = A.group_F[g];
+    if (F == 1) run_unit<LANES, 1>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (threadIdx.x == 0) atomicOr(A.err, 4);
+}
+
+__device__ __forceinline__ void cta_setup(unsigned char *smem, const K1Args &A, float *&ring,
+                                          float *&zbuf, uint32_t &bar0, uint32_t &bar1)
+{
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
-    float *ring = reinterpret_cast<float *>(smem + 128);
-    float *zbuf = ring + (int64_t)A.C * A.CS;
-    const uint32_t bar0 = smem_addr(&bars[0]), bar1 = smem_addr(&bars[1]);
+    ring = reinterpret_cast<float *>(smem + 128);
+    zbuf = ring + (int64_t)A.C * A.CS;
+    bar0 = smem_addr(&bars[0]);
+    bar1 = smem_addr(&bars[1]);
     if (threadIdx.x == 0) {
         mbar_init(bar0, 1);
         mbar_init(bar1, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    const int g = A.units[2 * blockIdx.x];
-    const int det = A.units[2 * blockIdx.x + 1];
-    const int F = A.group_F[g];
-    // the CTA's F is uniform, so every warp takes the same case
-    if (F == 1) run_unit<1>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (F == 2) run_unit<2>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 3 && F == 3) run_unit<(FCAP >= 3 ? 3 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 4 && F == 4) run_unit<(FCAP >= 4 ? 4 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 5 && F == 5) run_unit<(FCAP >= 5 ? 5 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 6 && F == 6) run_unit<(FCAP >= 6 ? 6 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 7 && F == 7) run_unit<(FCAP >= 7 ? 7 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 8 && F == 8) run_unit<(FCAP >= 8 ? 8 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 9 && F == 9) run_unit<(FCAP >= 9 ? 9 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 10 && F == 10) run_unit<(FCAP >= 10 ? 10 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (threadIdx.x == 0) atomicOr(A.err, 4);
+}
+
+template <int FCAP>
+__global__ void __launch_bounds__(256, K1Bounds<FCAP>::kMinBlocks) k1_plain(const K1Args A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *ring, *zbuf;
+    uint32_t bar0, bar1;
+    cta_setup(smem, A, ring, zbuf, bar0, bar1);
+    dispatch_f<PackedLanes, FCAP>(A, A.units[2 * blockIdx.x], A.units[2 * blockIdx.x + 1], ring,
+                                  zbuf, bar0, bar1);
+}
+
+__global__ void __launch_bounds__(256, 2) k1_compensated(const K1Args A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *ring, *zbuf;
+    uint32_t bar0, bar1;
+    cta_setup(smem, A, ring, zbuf, bar0, bar1);
+    dispatch_f<CompLanes, kPreciseFcap>(A, A.units[2 * blockIdx.x], A.units[2 * blockIdx.x + 1],
+                                        ring, zbuf, bar0, bar1);
+}
+
+__global__ void __launch_bounds__(256, 2) k1_chunked(const K1Args A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *ring, *zbuf;
+    uint32_t bar0, bar1;
+    cta_setup(smem, A, ring, zbuf, bar0, bar1);
+    dispatch_f<ChunkLanes, kPreciseFcap>(A, A.units[2 * blockIdx.x], A.units[2 * blockIdx.x + 1],
+                                         ring, zbuf, bar0, bar1);
 }
 
 __global__ void peak_out_kernel(const float *best, const int64_t *idx, int64_t count,
@@ -534,21 +796,33 @@ __global__ void bounded_wait_probe(int32_t *err, uint64_t limit_ns)
 
 }  // namespace
 
+template <typename Kernel>
+cudaError_t launch_kernel(Kernel k, const K1Args &a, int64_t n_units, int smem_bytes,
+                          cudaStream_t s)
+{
+    if (smem_bytes > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)n_units, a.W * 32, smem_bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
 template <int FCAP>
 cudaError_t launch_k1_cap(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
 {
-    if (smem_bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(
-            k1_plain<FCAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
-        if (e != cudaSuccess) return e;
-    }
-    k1_plain<FCAP><<<(unsigned)n_units, a.W * 32, smem_bytes, s>>>(a);
-    return cudaGetLastError();
+    return launch_kernel(k1_plain<FCAP>, a, n_units, smem_bytes, s);
 }
 
 cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
 {
     if (n_units <= 0 || a.n <= 0) return cudaSuccess;
+    if (a.mode == kModeCompensated || a.mode == kModeChunked) {
+        if (a.fcap > kPreciseFcap) return cudaErrorInvalidValue;
+        return launch_kernel(a.mode == kModeCompensated ? k1_compensated : k1_chunked, a,
+                             n_units, smem_bytes, s);
+    }
     // the smallest compiled cap that holds the layout's cap
     if (a.fcap <= 2) return launch_k1_cap<2>(a, n_units, smem_bytes, s);
     if (a.fcap <= 4) return launch_k1_cap<4>(a, n_units, smem_bytes, s);

@@ -16,6 +16,12 @@ struct LowerBand {
 };
 constexpr int kMaxLowerBands = 7;
 
+// Arithmetic of the filter kernel (spiir_options.precision).
+constexpr int kModePlain = 0;
+constexpr int kModeCompensated = 1;
+constexpr int kModeChunked = 2;
+constexpr int kPreciseFcap = 4;   // filters per lane in the compensated / chunked kernels
+
 // Plain FP32 filter kernel (one launch per bank or band).
 struct K1Args {
     const float *xe;           // [D][xe_stride] strain: Dh history samples, then the call's
@@ -45,6 +51,11 @@ struct K1Args {
                                // (c >= 1), kernel form; null = no checkpoints
     int32_t ckpt_blocks;       // blocks between checkpoints
     int32_t n_det;             // detectors (checkpoint row stride)
+    int32_t mode;              // kModePlain / kModeCompensated / kModeChunked
+    int32_t chunk;             // chunked: samples per chunk (divides Tb, multiple of 8)
+    void *state_ext;           // compensated: float4 [D][n_slots] (re hi, re lo, im hi, im lo);
+                               // chunked: double2 [D][n_slots] FP64 anchor
+    const double2 *aT;         // chunked: [n_slots] a^chunk in FP64 (kernel form)
 };
 
 // Adjoint (reverse-time) kernel of one zero-state filter call.
