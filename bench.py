@@ -48,7 +48,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched",
-                    choices=["batched", "plain", "adjoint", "precision"])
+                    choices=["batched", "plain", "multirate", "adjoint", "precision"])
+    ap.add_argument("--precision", default="plain",
+                    choices=["plain", "compensated", "chunked_fp64"])
+    ap.add_argument("--graph", action="store_true",
+                    help="time replays of a captured CUDA graph of the step")
+    ap.add_argument("--autotune", action="store_true",
+                    help="let the plan time candidate layouts on its first call")
     ap.add_argument("--samples", type=int, default=0,
                     help="override the stream length per step (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -136,6 +142,15 @@ class ClockSampler:
 
 
 # ------------------------------------------------------ CPU baseline ---
+def oracle_run(bank, x):
+    """The oracle on a (sub-)bank, peaks only."""
+    import oracle
+    if bank.band_of is not None:
+        return oracle.filter_multirate(bank.off, bank.a, bank.b, bank.d, bank.band_of,
+                                       bank.decim, x, want_z=False)
+    return oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x, want_z=False)
+
+
 def cpu_baseline(name, bank, x, seconds=15.0):
     """The FP64 oracle, as it stands, on the host cores: a bounded sample of
     the workload's templates (all detectors, full length)."""
@@ -144,13 +159,13 @@ def cpu_baseline(name, bank, x, seconds=15.0):
     # calibrate on enough templates to occupy every core
     cal = bank.subset(range(min(bank.n_templates, 2 * oracle.max_threads())))
     t = time.perf_counter()
-    oracle.filter_bank(cal.off, cal.a, cal.b, cal.d, x, want_z=False)
+    oracle_run(cal, x)
     rate = updates(cal, n) / (time.perf_counter() - t)
     per_t = updates(bank, n) / bank.n_templates
     k = int(max(1, min(bank.n_templates, seconds * rate / per_t)))
     sub = bank.subset(range(k))
     t = time.perf_counter()
-    oracle.filter_bank(sub.off, sub.a, sub.b, sub.d, x, want_z=False)
+    oracle_run(sub, x)
     dt = time.perf_counter() - t
     return {"value": updates(sub, n) / dt, "unit": "filter-updates/s",
             "cores": oracle.max_threads(), "kind": "oracle",
@@ -170,7 +185,7 @@ def run_reference(args, rank, world):
     # size each step to ~3 s of host time
     cal = bank.subset(range(min(bank.n_templates, 2 * oracle.max_threads())))
     t = time.perf_counter()
-    oracle.filter_bank(cal.off, cal.a, cal.b, cal.d, x, want_z=False)
+    oracle_run(cal, x)
     rate = updates(cal, n) / (time.perf_counter() - t)
     per_t = updates(bank, n) / bank.n_templates
     k = int(max(1, min(bank.n_templates, 3.0 * rate / per_t)))
@@ -179,7 +194,7 @@ def run_reference(args, rank, world):
         lo = (step * k) % max(1, bank.n_templates - k)
         sub = bank.subset(range(lo, lo + k))
         t = time.perf_counter()
-        oracle.filter_bank(sub.off, sub.a, sub.b, sub.d, x, want_z=False)
+        oracle_run(sub, x)
         dt = time.perf_counter() - t
         if step >= args.warmup:
             times.append((updates(sub, n), dt))
@@ -204,6 +219,20 @@ def run_reference(args, rank, world):
 
 
 # -------------------------------------------------------------- ours ---
+def shard_bank(name, rank):
+    """Rank 0 filters the workload's bank; rank r > 0 its own shard of a
+    world-times-larger bank (independent templates, same distributions)."""
+    from spiir_inputs import make_bank, make_multirate_bank
+    if rank == 0:
+        return workload_bank(name)
+    w = WORKLOADS[name]
+    if w["kind"] == "multirate":
+        return make_multirate_bank(w["n_templates"], w["band_filters"], w["decim"],
+                                   w["r_range"], w["d_max"], w["seed"] + 1000 * rank, w["n_det"])
+    return make_bank(w["n_templates"], w["filters"], w["r_range"], w["d_max"],
+                     w["seed"] + 1000 * rank, w["n_det"])
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1602_05573_b300 as sp
@@ -215,29 +244,42 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
 
-    from spiir_inputs import WORKLOADS as W_, make_bank
-    w = W_[args.workload]
-    if rank == 0:
-        bank = workload_bank(args.workload)
-    else:  # this rank's shard of a world x larger bank (independent templates)
-        bank = make_bank(w["n_templates"], w["filters"], w["r_range"], w["d_max"],
-                         w["seed"] + 1000 * rank, w["n_det"])
+    bank = shard_bank(args.workload, rank)
     x_host = workload_strain(args.workload, args.samples or None)
     n = x_host.shape[1]
     T, D = bank.n_templates, bank.n_det
     upd = updates(bank, n)
+    # z is stored for the workloads whose series fit comfortably in HBM
+    emit_z = args.workload in ("batched", "plain")
+    adjoint = args.workload == "adjoint"
 
-    plan = sp.Plan(bank, device=local_rank)
+    plan = sp.Plan(bank, device=local_rank, precision=args.precision,
+                   autotune=args.autotune)
     stream = torch.cuda.Stream(device=dev)
     x = torch.from_numpy(x_host).to(dev)
-    z = torch.empty((D, T, n), dtype=torch.complex64, device=dev)
+    z = torch.empty((D, T, n), dtype=torch.complex64, device=dev) if emit_z else None
     pa = torch.empty((D, T), dtype=torch.float32, device=dev)
     pi = torch.empty((D, T), dtype=torch.int64, device=dev)
+    gz = None
+    if adjoint:
+        g = torch.Generator(device=dev).manual_seed(7)
+        gz = torch.randn((D, T, n), dtype=torch.complex64, device=dev, generator=g)
     lib = sp.library()
     sh = stream.cuda_stream
+    zp = z.data_ptr() if z is not None else None
+    # our kernels per step: K1 (+ decimation and K1 per lower band), the
+    # sample-counter advance and the peak copy; the adjoint: K1 with
+    # checkpoints, K6 and the gradient finalize
+    n_lower = (len(bank.decim) - 1) if bank.decim is not None else 0
+    launches_per_step = 3 + 2 * n_lower
+    if adjoint:
+        launches_per_step = 3
 
-    def step():
-        st = lib.spiir_filter(plan.handle, x.data_ptr(), n, z.data_ptr(), sh)
+    def call():
+        if adjoint:
+            plan.backward(x, gz, stream=stream)
+            return
+        st = lib.spiir_filter(plan.handle, x.data_ptr(), n, zp, sh)
         st |= lib.spiir_peak(plan.handle, pa.data_ptr(), pi.data_ptr(), sh)
         if st != 0:
             raise RuntimeError("spiir call failed: " + lib.spiir_last_error_detail().decode())
@@ -247,10 +289,15 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
+    graph = None
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
-            step()
+            call()
         barrier()
+        if args.graph and not adjoint:
+            graph, _, _, _ = plan.capture(x, z, pa, pi, emit_z=emit_z, warmup=False)
+            barrier()
+        step = graph.replay if graph is not None else call
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
         with ClockSampler(local_rank) as clk:
@@ -259,14 +306,14 @@ def run_ours(args, rank, world, local_rank):
             t0.record(stream)
             for i in range(args.steps):
                 ev[i][0].record(stream)
-                lib.spiir_filter(plan.handle, x.data_ptr(), n, z.data_ptr(), sh)
+                step()
                 ev[i][1].record(stream)
-                lib.spiir_peak(plan.handle, pa.data_ptr(), pi.data_ptr(), sh)
             t1.record(stream)
             barrier()
         plan.check(stream)
     total_ms = t0.elapsed_time(t1)
-    filt_ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    step_times = [a.elapsed_time(b) for a, b in ev]
+    filt_ms = float(np.mean(step_times))
     if dist is not None:
         tt = torch.tensor([total_ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -274,16 +321,48 @@ def run_ours(args, rank, world, local_rank):
     ms_step = total_ms / args.steps
     value = upd * world * args.steps / (total_ms / 1e3)
 
+    extra = {}
+    if adjoint:  # forward time on the same plan, for the backward/forward ratio
+        with torch.cuda.stream(stream):
+            plan.filter(x, emit_z=False, stream=stream)
+            barrier()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            for _ in range(args.steps):
+                plan.filter(x, emit_z=False, stream=stream)
+            f1.record(stream)
+            barrier()
+        fwd_ms = f0.elapsed_time(f1) / args.steps
+        extra["adjoint"] = {"backward_ms": ms_step, "forward_ms": fwd_ms,
+                            "backward_over_forward": ms_step / fwd_ms}
+    if args.workload == "plain" and not adjoint:
+        # peak-SNR latency: graph replay of one call (strain resident), median of 100
+        with torch.cuda.stream(stream):
+            g2, _, _, _ = plan.capture(x, z, pa, pi, emit_z=True, warmup=False)
+            lat = []
+            for _ in range(100):
+                a0 = torch.cuda.Event(enable_timing=True)
+                a1 = torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                g2.replay()
+                a1.record(stream)
+                a1.synchronize()
+                lat.append(a0.elapsed_time(a1))
+        extra["latency_ms"] = {"median": float(np.median(lat)), "min": float(np.min(lat)),
+                               "what": "graph replay of filter+peak for one 4 s block, "
+                                       "strain resident"}
+
     # end to end through the public API: pinned host strain in, peaks out
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and not adjoint:
         xh = torch.from_numpy(x_host).pin_memory()
         pah = torch.empty((D, T), dtype=torch.float32).pin_memory()
         pih = torch.empty((D, T), dtype=torch.int64).pin_memory()
         with torch.cuda.stream(stream):
             def e2e_step():
                 x.copy_(xh, non_blocking=True)
-                plan.filter(x, z, stream=stream)
+                plan.filter(x, z, emit_z=emit_z, stream=stream)
                 plan.peak(pa, pi, stream=stream)
                 pah.copy_(pa, non_blocking=True)
                 pih.copy_(pi, non_blocking=True)
@@ -318,26 +397,36 @@ def run_ours(args, rank, world, local_rank):
     sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2032.0
     peak_lane = B300_SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12   # T lane-ops/s
     achieved = LANE_OPS_PER_UPDATE * upd / (filt_ms / 1e3) / 1e12
+    kernel = {"plain": "k1_plain", "compensated": "k1_compensated",
+              "chunked_fp64": "k1_chunked"}[args.precision]
+    if adjoint:
+        kernel = "k6_adjoint (+ k1_plain checkpoint pass)"
     line = {
         "metric": "filter-updates/s", "value": value, "unit": "filter-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded N(0,1) strain, random poles/gains/delays)",
         "config": dict(describe(args.workload, bank, n),
+                       precision=args.precision, graph=bool(graph is not None),
+                       z_stored=emit_z,
                        parallelism=f"template shards x{world}" if world > 1 else "1 GPU",
-                       l2="each step writes the 6.4 GB z series (> 126 MB L2), which "
-                          "evicts the previous step; the 0.8 MB strain stays L2-resident "
-                          "as in streaming use",
+                       l2=("each step writes the z series (> 126 MB L2), which evicts the "
+                           "previous step; the strain stays L2-resident as in streaming use")
+                       if emit_z else "strain (<= 4 MB) L2-resident as in streaming use; "
+                                      "no z stored",
                        plan={k: info[k] for k in ("warps_per_cta", "block_len", "ring_copies",
                                                   "history_len", "smem_bytes",
+                                                  "max_filters_per_lane",
                                                   "bank_conflict_ratio", "n_slots")}),
-        "roofline": {"bound": "alu", "kernel": "k1_plain", "achieved": achieved,
+        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                      "peak": peak_lane, "unit": "T FP32 lane-ops/s",
                      "frac": achieved / peak_lane, "traffic": None,
-                     "note": f"8 lane-ops per filter-update x {upd:.4g} updates per launch / "
-                             f"mean spiir_filter time {filt_ms:.3f} ms; peak = 148 SMs x 128 "
-                             f"FP32 lanes x {sm_max:.0f} MHz (derived; of measured max clock)"},
-        "gpu_launches": 2 * args.steps,
+                     "note": f"8 algorithmic lane-ops per filter-update x {upd:.4g} updates "
+                             f"per step / mean step time {filt_ms:.3f} ms (CUDA events on the "
+                             f"launching stream); peak = 148 SMs x 128 FP32 lanes x "
+                             f"{sm_max:.0f} MHz (derived from unit counts and the measured "
+                             f"max clock)"},
+        "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "filter_ms": filt_ms,
         # templates (all detectors, mean filter count) whose 1 s of data is
@@ -345,9 +434,10 @@ def run_ours(args, rank, world, local_rank):
         "templates_realtime": upd * world / (ms_step / 1e3) / (bank.n_filters / T * D)
                               / WORKLOADS[args.workload]["rate"],
     }
+    line.update(extra)
     if e2e:
         line["e2e"] = e2e
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and not adjoint:
         line["cpu_baseline"] = cpu_baseline(args.workload, bank, x_host)
     print(json.dumps(line), flush=True)
     if dist is not None:

@@ -319,6 +319,36 @@ class Plan:
                "spiir_peak", self._lib)
         return out_abs, out_idx
 
+    def capture(self, x, z=None, peak_abs=None, peak_idx=None, *, emit_z: bool = True,
+                warmup: bool = True):
+        """Record one spiir_filter + spiir_peak call on fixed buffers into a
+        CUDA graph; each replay() filters the next len(x) samples of the
+        stream (the sample counter lives on the device).  The warm-up call
+        (which allocates workspace outside the capture) advances the stream;
+        reset() afterwards to start from zero.  Returns (graph, z, abs, idx)."""
+        import torch
+        D, n = x.shape
+        if emit_z and z is None:
+            z = torch.empty((D, self.n_templates, n), dtype=torch.complex64, device=x.device)
+        if peak_abs is None:
+            peak_abs = torch.empty((D, self.n_templates), dtype=torch.float32, device=x.device)
+        if peak_idx is None:
+            peak_idx = torch.empty((D, self.n_templates), dtype=torch.int64, device=x.device)
+        side = torch.cuda.Stream(device=x.device)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            if warmup:
+                self.filter(x, z, emit_z=emit_z, stream=side)
+                self.peak(peak_abs, peak_idx, stream=side)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize(x.device)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            cur = torch.cuda.current_stream()
+            self.filter(x, z, emit_z=emit_z, stream=cur)
+            self.peak(peak_abs, peak_idx, stream=cur)
+        return g, z, peak_abs, peak_idx
+
     def backward(self, x, grad_z, *, want_gx: bool = True, stream=None):
         """VJP of one zero-state filter call: (g_a, g_b complex64 [Ltot], g_x float32 [D][n])."""
         import torch

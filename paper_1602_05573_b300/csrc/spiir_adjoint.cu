@@ -210,11 +210,8 @@ cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s)
 {
     if (n_units <= 0 || a.n <= 0) return cudaSuccess;
     const int smem = k6_smem_bytes(a.W, a.Cc, a.Dh);
-    if (smem > 48 * 1024) {
-        cudaError_t e =
-            cudaFuncSetAttribute(k6_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k6_adjoint), smem);
+    if (e != cudaSuccess) return e;
     k6_adjoint<<<(unsigned)n_units, a.W * 32, smem, s>>>(a);
     return cudaGetLastError();
 }

@@ -164,9 +164,17 @@ struct spiir_plan {
     float *peak_best = nullptr;   // [D][T]
     int64_t *peak_idx = nullptr;  // [D][T]
     int32_t *err = nullptr;
-    int64_t t0 = 0;               // samples since reset (top rate)
+    int64_t *t0_dev = nullptr;    // samples since reset, on the device (graph replays advance it)
+    int64_t t0 = 0;               // the same, as enqueued by this host (alignment checks)
     int top = 0;                  // index of the top-rate band
     int maxR = 1;                 // largest decimation factor
+    // kept for the autotuner (single-rate plans with autotune set)
+    bool tuned = false;
+    int n_sm = 148;
+    std::vector<std::vector<int64_t>> lists;
+    std::vector<float> a_host, b_host;
+    std::vector<int32_t> d_host;
+    std::string tune_report;
 };
 
 namespace {
@@ -450,6 +458,19 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
             break;
         }
     for (const Band &b : p->bands) p->maxR = std::max(p->maxR, b.R);
+    p->n_sm = n_sm;
+    if (opt.autotune && p->bands.size() == 1 && opt.precision == SPIIR_PREC_PLAIN) {
+        const int64_t L = p->Ltot;
+        p->a_host.assign(bank->a_reim, bank->a_reim + 2 * L);
+        p->b_host.assign(bank->b_reim, bank->b_reim + 2 * L);
+        p->d_host.assign(bank->delay, bank->delay + L);
+        p->lists.assign((size_t)p->T, {});
+        for (int64_t t = 0; t < p->T; ++t)
+            for (int64_t l = bank->filter_off[t]; l < bank->filter_off[t + 1]; ++l)
+                p->lists[t].push_back(l);
+    } else {
+        p->tuned = true;
+    }
     if (p->device < 0) {  // host-only plan
         *out = p;
         return SPIIR_OK;
@@ -469,7 +490,8 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     cudaError_t e;
     if ((e = dalloc(&p->peak_best, (size_t)p->D * p->T)) != cudaSuccess ||
         (e = dalloc(&p->peak_idx, (size_t)p->D * p->T)) != cudaSuccess ||
-        (e = dalloc(&p->err, 1)) != cudaSuccess) {
+        (e = dalloc(&p->err, 1)) != cudaSuccess ||
+        (e = dalloc(&p->t0_dev, 1)) != cudaSuccess) {
         spiir_plan_destroy(p);
         return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "device allocation failed")
                                               : cuda_fail(e, "cudaMalloc");
@@ -497,6 +519,7 @@ spiir_status spiir_plan_destroy(spiir_plan *p)
         cudaFree(p->peak_best);
         cudaFree(p->peak_idx);
         cudaFree(p->err);
+        cudaFree(p->t0_dev);
     }
     delete p;
     return SPIIR_OK;
@@ -562,9 +585,96 @@ spiir_status spiir_reset(spiir_plan *p, void *stream)
     }
     if ((e = spiir::launch_peak_reset(p->peak_best, p->peak_idx, (int64_t)p->D * p->T, s)) !=
             cudaSuccess ||
-        (e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s)) != cudaSuccess)
+        (e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(p->t0_dev, 0, sizeof(int64_t), s)) != cudaSuccess)
         return cuda_fail(e, "reset");
     p->t0 = 0;
+    return SPIIR_OK;
+}
+
+// Time candidate layouts on a prefix of the first call's strain (zero state,
+// no z, no peak) and keep the fastest.  Synchronous; runs once per plan.
+spiir_status autotune(spiir_plan *p, const float *x_dev, int64_t n, cudaStream_t s)
+{
+    struct Cand {
+        int Fcap, W, C, Tb;
+    };
+    static const Cand cands[] = {{10, 4, 1, 512}, {10, 4, 2, 512}, {10, 4, 1, 256},
+                                 {10, 2, 1, 512}, {10, 8, 1, 256}, {8, 4, 1, 512},
+                                 {4, 8, 2, 256},  {4, 4, 1, 512},  {2, 8, 1, 256}};
+    const int64_t nt = std::min<int64_t>(n, 8192);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e;
+    if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
+        return cuda_fail(e, "autotune events");
+    float best_ms = 1e30f;
+    Band best;
+    bool have = false;
+    std::string report;
+    for (const Cand &c : cands) {
+        Band b;
+        spiir::LayoutOptions lo;
+        lo.Fcap = c.Fcap;
+        lo.W = c.W;
+        lo.C = c.C;
+        lo.Tb = c.Tb;
+        lo.n_sm = p->n_sm;
+        std::string err;
+        if (!spiir::build_layout(p->lists, p->D, p->a_host.data(), p->b_host.data(),
+                                 p->d_host.data(), lo, &b.lay, &err))
+            continue;
+        spiir_status st = upload_band(b, p->D, p->precision, p->opt.chunk_len);
+        if (st == SPIIR_OK) st = ensure_xe(p, b, nt, s);
+        if (st != SPIIR_OK) {
+            free_band(b);
+            continue;
+        }
+        const int64_t Dh = b.lay.Dh;
+        if ((e = cudaMemset2DAsync(b.xe, b.xe_stride * 4, 0, Dh * 4, p->D, s)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(b.xe + Dh, b.xe_stride * 4, x_dev, n * 4, nt * 4, p->D,
+                                   cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+            free_band(b);
+            continue;
+        }
+        spiir::K1Args a = k1_args(p, b, nt, nullptr, nt, false);
+        // one untimed launch, then the timed one
+        e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        if (e == cudaSuccess) e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            free_band(b);
+            return cuda_fail(e, "autotune launch");
+        }
+        report += "cap" + std::to_string(c.Fcap) + "/W" + std::to_string(c.W) + "/C" +
+                  std::to_string(c.C) + "/Tb" + std::to_string(c.Tb) + "=" +
+                  std::to_string(ms) + "ms ";
+        if (ms < best_ms) {
+            if (have) free_band(best);
+            best = b;
+            best_ms = ms;
+            have = true;
+        } else {
+            free_band(b);
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (have) {
+        // the candidate's state and history were zero-initialised by the upload
+        if ((e = cudaMemsetAsync(best.state, 0, sizeof(float2) * (size_t)p->D * best.lay.n_slots,
+                                 s)) != cudaSuccess)
+            return cuda_fail(e, "autotune reset");
+        free_band(p->bands[0]);
+        p->bands[0] = best;
+    }
+    p->tune_report = report;
+    p->tuned = true;
     return SPIIR_OK;
 }
 
@@ -583,6 +693,10 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
     DeviceGuard guard(p->device);
     if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
+    if (!p->tuned && p->t0 == 0) {
+        spiir_status st = autotune(p, x_dev, n, s);
+        if (st != SPIIR_OK) return st;
+    }
     const int D = p->D;
     cudaError_t e;
     // decimated bands first (their sums feed the top band's epilogue), top band last
@@ -631,9 +745,12 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
             lb.R = b.R;
         } else {
             spiir::K1Args a = k1_args(p, b, n, z_dev, n, true);
+            a.t0 = 0;
+            a.t0_dev = p->t0_dev;
             a.n_lower = top_args.n_lower;
             for (int i = 0; i < a.n_lower; ++i) a.lower[i] = top_args.lower[i];
-            if ((e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s)) != cudaSuccess)
+            if ((e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s)) != cudaSuccess ||
+                (e = spiir::launch_advance(p->t0_dev, n, s)) != cudaSuccess)
                 return cuda_fail(e, "filter kernel launch");
         }
         // band history for the next call: the last Dh band samples of (history, x_b)
@@ -826,7 +943,10 @@ spiir_status spiir_state_get(spiir_plan *p, float *state, float *history, int64_
                        cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return cuda_fail(e, "history copy");
     }
-    if (samples) *samples = p->t0;
+    if (samples) {
+        e = cudaMemcpy(samples, p->t0_dev, sizeof(int64_t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "sample counter copy");
+    }
     return SPIIR_OK;
 }
 
@@ -879,6 +999,8 @@ spiir_status spiir_state_set(spiir_plan *p, const float *state, const float *his
         if (e != cudaSuccess) return cuda_fail(e, "history copy");
     }
     p->t0 = samples;
+    e = cudaMemcpy(p->t0_dev, &samples, sizeof(int64_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "sample counter copy");
     return SPIIR_OK;
 }
 

@@ -38,6 +38,9 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <map>
+#include <mutex>
+#include <utility>
 
 namespace spiir {
 
@@ -671,7 +674,7 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             const int64_t i = (int64_t)det * A.T + tmpl;
             if (best > A.peak_best[i]) {
                 A.peak_best[i] = best;
-                A.peak_idx[i] = A.t0 + bidx;
+                A.peak_idx[i] = (A.t0_dev != nullptr ? *A.t0_dev : 0) + A.t0 + bidx;
             }
         }
     }
@@ -763,6 +766,11 @@ __global__ void peak_out_kernel(const float *best, const int64_t *idx, int64_t c
     out_idx[i] = idx[i];
 }
 
+__global__ void advance_kernel(int64_t *t0, int64_t n)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *t0 += n;
+}
+
 __global__ void peak_reset_kernel(float *best, int64_t *idx, int64_t count)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -800,11 +808,8 @@ template <typename Kernel>
 cudaError_t launch_kernel(Kernel k, const K1Args &a, int64_t n_units, int smem_bytes,
                           cudaStream_t s)
 {
-    if (smem_bytes > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem_bytes);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k), smem_bytes);
+    if (e != cudaSuccess) return e;
     k<<<(unsigned)n_units, a.W * 32, smem_bytes, s>>>(a);
     return cudaGetLastError();
 }
@@ -832,12 +837,36 @@ cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStre
     return cudaErrorInvalidValue;
 }
 
+cudaError_t ensure_smem_limit(const void *kernel, int smem_bytes)
+{
+    // the attribute is set once per (kernel, device, size): later launches,
+    // including those recorded during stream capture, make no attribute call
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> done;
+    if (smem_bytes <= 48 * 1024) return cudaSuccess;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    int &have = done[std::make_pair(kernel, dev)];
+    if (have >= smem_bytes) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bytes);
+    if (e == cudaSuccess) have = smem_bytes;
+    return e;
+}
+
 cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count,
                             float *out_abs, int64_t *out_idx, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
     peak_out_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(best, idx, count, out_abs,
                                                                     out_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_advance(int64_t *t0, int64_t n, cudaStream_t s)
+{
+    advance_kernel<<<1, 32, 0, s>>>(t0, n);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,9 @@ struct K1Args {
     int64_t T;
     float *peak_best;          // [D][T] running max |z|^2, or null (no peak)
     int64_t *peak_idx;         // [D][T]
-    int64_t t0;                // absolute index of this call's first sample
+    int64_t t0;                // absolute index of this call's first sample, added to
+    const int64_t *t0_dev;     // ... *t0_dev when non-null (device-side stream counter,
+                               //     so a captured graph's replays keep counting)
     int32_t *err;              // device error word
     uint64_t wait_limit_ns;    // bound on every mbarrier wait
     int32_t n_lower;           // lower bands added in the combine (0 = single rate)
@@ -94,9 +96,15 @@ cudaError_t launch_set_coefficients(const float2 *a, const float2 *b,
 
 cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s);
 
+// Raise a kernel's dynamic shared-memory limit once per (kernel, device, size).
+cudaError_t ensure_smem_limit(const void *kernel, int smem_bytes);
+
 // Finalize running peaks into the caller's buffers (sqrt of |z|^2).
 cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count,
                             float *out_abs, int64_t *out_idx, cudaStream_t s);
+
+// *t0 += n (device-side sample counter of a plan).
+cudaError_t launch_advance(int64_t *t0, int64_t n, cudaStream_t s);
 
 // best[i] = -1, idx[i] = -1.
 cudaError_t launch_peak_reset(float *best, int64_t *idx, int64_t count, cudaStream_t s);
