@@ -17,14 +17,16 @@
 // reverse, recomputes the span into registers (pass B) and runs the adjoint
 // over it.
 //
-// Mapping: one CTA per (group of W templates, detector), as in the forward
-// kernel; lane i of a warp walks the warp's filter rounds one at a time (mu,
-// g_a and g_b of each filter live in global memory between chunks, so
-// registers do not grow with the filter count).  The strain window of a
-// chunk is staged in shared memory; g_z of the template is read by lanes
-// 0..kAdjSub-1 once per span and broadcast with shuffles; g_x is scattered
-// into a shared ring with shared-memory atomics (the layout places a round's
-// 32 delays on 32 different banks) and added to global memory per chunk.
+// Mapping: filters are independent in the adjoint, so the unit of work is a
+// task of kAdjRounds filter rounds (32 filters each) of one template; lane i
+// runs its kAdjRounds filters together (independent chains for the
+// scheduler) and keeps mu, g_a, g_b in registers for the whole call.  A CTA
+// runs W tasks of one detector and stages each chunk's strain window in
+// shared memory; the 16-sample state checkpoints of pass A go to an
+// L2-resident workspace; g_z of the template is read by lanes 0..15 once per
+// span and broadcast with shuffles; g_x is scattered into a shared ring with
+// shared-memory atomics (the layout places a round's 32 delays on 32
+// different banks) and added to global memory per chunk.
 #include "spiir_kernels.h"
 
 #include <cstdint>
@@ -35,29 +37,51 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-__global__ void __launch_bounds__(256) k6_adjoint(const K6Args A)
+__global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
 {
+    constexpr int R = kAdjRounds;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Dw = A.Dh + A.Cc;                          // strain window per chunk
     float *xs = reinterpret_cast<float *>(smem);         // [Dw]
     float *gxs = xs + Dw;                                // [Dw]
-    float2 *sub = reinterpret_cast<float2 *>(gxs + Dw);  // [W][Cc / kAdjSub][32]
     const int nsub_max = A.Cc / kAdjSub;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = A.units[2 * blockIdx.x];
     const int det = A.units[2 * blockIdx.x + 1];
-    const int F = A.group_F[g];
-    const int4 wi = A.warp_info[(int64_t)g * A.W + warp];
-    const int tmpl = wi.x;
+    const int4 task = A.tasks[(int64_t)g * A.W + warp];
+    const int tmpl = task.z;
     const bool active = tmpl >= 0;
-    const int64_t pb = A.group_pbase[g];
+    const int nr = task.y;                   // rounds in this task (<= R)
     const int n = A.n;
     const int nc = (n + A.Cc - 1) / A.Cc;
     const float *xrow = A.xe + (int64_t)det * A.xe_stride;
     const float2 *grow = active ? A.gz + ((int64_t)det * A.T + tmpl) * n : nullptr;
-    float2 *wsub = sub + (int64_t)warp * nsub_max * 32;
+    float2 *wsub = A.sub + ((int64_t)blockIdx.x * A.W + warp) * R * nsub_max * 32;
     float *acc_det = A.acc + (int64_t)det * A.n_slots * 6;
+
+    // this lane's filters: slot of round i = task.x + i * task.w (task.w = 32 * layout warps)
+    int64_t slot[R];
+    float ar[R], ai[R], br[R], bi[R];
+    int xo[R];
+    bool odd = (lane & 1) != 0;   // stored as conj(a), (Im b, Re b)
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        slot[i] = active ? (int64_t)task.x + (int64_t)i * task.w + lane : 0;
+        ar[i] = ai[i] = br[i] = bi[i] = 0.f;
+        xo[i] = 0;
+        if (active && i < nr) {
+            const float4 p = A.params[slot[i]];
+            ar[i] = p.x;
+            ai[i] = odd ? -p.y : p.y;
+            br[i] = odd ? p.w : p.z;
+            bi[i] = odd ? p.z : p.w;
+            xo[i] = A.ringoff[slot[i]].x;   // Dh - d: xs index of x[kc - d]
+        }
+    }
+    float mr[R], mi[R], gar[R], gai[R], gbr[R], gbi[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) mr[i] = mi[i] = gar[i] = gai[i] = gbr[i] = gbi[i] = 0.f;
 
     for (int c = nc - 1; c >= 0; --c) {
         const int kc = c * A.Cc;
@@ -70,87 +94,82 @@ __global__ void __launch_bounds__(256) k6_adjoint(const K6Args A)
         __syncthreads();
         if (active) {
             const int nsub = (cv + kAdjSub - 1) / kAdjSub;
-            for (int r = 0; r < F; ++r) {
-                const int64_t s = pb + ((int64_t)r * A.W + warp) * 32 + lane;
-                const float4 p = A.params[s];
-                const bool odd = (lane & 1) != 0;   // stored as conj(a), (Im b, Re b)
-                const float ar = p.x, ai = odd ? -p.y : p.y;
-                const float br = odd ? p.w : p.z, bi = odd ? p.z : p.w;
-                const int xo = A.ringoff[s].x;   // Dh - d: xs index of x[kc - d]
-                float *acc = acc_det + s * 6;
-                float mr = acc[0], mi = acc[1];
-                float gar = acc[2], gai = acc[3], gbr = acc[4], gbi = acc[5];
-                // state y[kc - 1]
-                float yr = 0.f, yi = 0.f;
-                if (c > 0) {
-                    const float2 ck = A.ckpt[((int64_t)c * A.n_det + det) * A.n_slots + s];
-                    yr = odd ? ck.y : ck.x;
-                    yi = odd ? ck.x : ck.y;
+            float yr[R], yi[R];   // state y[kc - 1]
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                yr[i] = yi[i] = 0.f;
+                if (c > 0 && i < nr) {
+                    const float2 ck = A.ckpt[((int64_t)c * A.n_det + det) * A.n_slots + slot[i]];
+                    yr[i] = odd ? ck.y : ck.x;
+                    yi[i] = odd ? ck.x : ck.y;
                 }
-                // pass A: forward over the chunk, state kept every kAdjSub samples
-                for (int q = 0; q < nsub; ++q) {
-                    wsub[q * 32 + lane] = make_float2(yr, yi);
-                    const int k0 = q * kAdjSub;
+            }
+            // pass A: forward over the chunk, state kept every kAdjSub samples
+            for (int q = 0; q < nsub; ++q) {
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+                    wsub[((int64_t)q * R + i) * 32 + lane] = make_float2(yr[i], yi[i]);
+                const int k0 = q * kAdjSub;
+#pragma unroll
+                for (int t = 0; t < kAdjSub; ++t) {
+                    if (k0 + t < cv) {
+#pragma unroll
+                        for (int i = 0; i < R; ++i) {
+                            const float x = xs[xo[i] + k0 + t];
+                            const float nr_ = fmaf(ar[i], yr[i], fmaf(-ai[i], yi[i], br[i] * x));
+                            const float ni_ = fmaf(ar[i], yi[i], fmaf(ai[i], yr[i], bi[i] * x));
+                            yr[i] = nr_;
+                            yi[i] = ni_;
+                        }
+                    }
+                }
+            }
+            // pass B: spans in reverse; y[k-1] recomputed into registers
+            for (int q = nsub - 1; q >= 0; --q) {
+                const int k0 = q * kAdjSub;
+                float pr[R][kAdjSub], pi[R][kAdjSub];   // y[k0 + t - 1]
+#pragma unroll
+                for (int i = 0; i < R; ++i) {
+                    const float2 y0 = wsub[((int64_t)q * R + i) * 32 + lane];
+                    float ur = y0.x, ui = y0.y;
 #pragma unroll
                     for (int t = 0; t < kAdjSub; ++t) {
-                        if (k0 + t < cv) {
-                            const float x = xs[xo + k0 + t];
-                            const float nr = fmaf(ar, yr, fmaf(-ai, yi, br * x));
-                            const float ni = fmaf(ar, yi, fmaf(ai, yr, bi * x));
-                            yr = nr;
-                            yi = ni;
+                        pr[i][t] = ur;
+                        pi[i][t] = ui;
+                        if (t + 1 < kAdjSub) {
+                            const float x = xs[xo[i] + k0 + t];
+                            const float nr_ = fmaf(ar[i], ur, fmaf(-ai[i], ui, br[i] * x));
+                            const float ni_ = fmaf(ar[i], ui, fmaf(ai[i], ur, bi[i] * x));
+                            ur = nr_;
+                            ui = ni_;
                         }
                     }
                 }
-                // pass B: spans in reverse; y[k-1] recomputed into registers
-                for (int q = nsub - 1; q >= 0; --q) {
-                    const int k0 = q * kAdjSub;
-                    float pr[kAdjSub], pi[kAdjSub];   // y[k0 + t - 1]
-                    {
-                        const float2 y0 = wsub[q * 32 + lane];
-                        float ur = y0.x, ui = y0.y;
+                float2 gl = make_float2(0.f, 0.f);
+                if (lane < kAdjSub && k0 + lane < cv) gl = grow[kc + k0 + lane];
 #pragma unroll
-                        for (int t = 0; t < kAdjSub; ++t) {
-                            pr[t] = ur;
-                            pi[t] = ui;
-                            if (t + 1 < kAdjSub) {
-                                const float x = xs[xo + k0 + t];
-                                const float nr = fmaf(ar, ur, fmaf(-ai, ui, br * x));
-                                const float ni = fmaf(ar, ui, fmaf(ai, ur, bi * x));
-                                ur = nr;
-                                ui = ni;
-                            }
-                        }
-                    }
-                    float2 gl = make_float2(0.f, 0.f);
-                    if (lane < kAdjSub && k0 + lane < cv) gl = grow[kc + k0 + lane];
+                for (int t = kAdjSub - 1; t >= 0; --t) {
+                    const float Gr = __shfl_sync(kFull, gl.x, t);
+                    const float Gi = __shfl_sync(kFull, gl.y, t);
+                    if (k0 + t < cv) {
 #pragma unroll
-                    for (int t = kAdjSub - 1; t >= 0; --t) {
-                        const float Gr = __shfl_sync(kFull, gl.x, t);
-                        const float Gi = __shfl_sync(kFull, gl.y, t);
-                        if (k0 + t < cv) {
+                        for (int i = 0; i < R; ++i) {
                             // mu <- g_z + conj(a) mu
-                            const float nr = Gr + fmaf(ar, mr, ai * mi);
-                            const float ni = Gi + fmaf(ar, mi, -ai * mr);
-                            mr = nr;
-                            mi = ni;
+                            const float nr_ = Gr + fmaf(ar[i], mr[i], ai[i] * mi[i]);
+                            const float ni_ = Gi + fmaf(ar[i], mi[i], -ai[i] * mr[i]);
+                            mr[i] = nr_;
+                            mi[i] = ni_;
                             // g_a += mu conj(y[k-1]),  g_b += mu x[k-d]
-                            gar = fmaf(mr, pr[t], fmaf(mi, pi[t], gar));
-                            gai = fmaf(mi, pr[t], fmaf(-mr, pi[t], gai));
-                            const float x = xs[xo + k0 + t];
-                            gbr = fmaf(mr, x, gbr);
-                            gbi = fmaf(mi, x, gbi);
-                            if (A.gx != nullptr)
-                                atomicAdd(&gxs[xo + k0 + t], fmaf(mr, br, mi * bi));
+                            gar[i] = fmaf(mr[i], pr[i][t], fmaf(mi[i], pi[i][t], gar[i]));
+                            gai[i] = fmaf(mi[i], pr[i][t], fmaf(-mr[i], pi[i][t], gai[i]));
+                            const float x = xs[xo[i] + k0 + t];
+                            gbr[i] = fmaf(mr[i], x, gbr[i]);
+                            gbi[i] = fmaf(mi[i], x, gbi[i]);
+                            if (A.gx != nullptr && i < nr)
+                                atomicAdd(&gxs[xo[i] + k0 + t], fmaf(mr[i], br[i], mi[i] * bi[i]));
                         }
                     }
                 }
-                acc[0] = mr;
-                acc[1] = mi;
-                acc[2] = gar;
-                acc[3] = gai;
-                acc[4] = gbr;
-                acc[5] = gbi;
             }
         }
         __syncthreads();
@@ -164,6 +183,19 @@ __global__ void __launch_bounds__(256) k6_adjoint(const K6Args A)
             }
         }
         __syncthreads();
+    }
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            if (i >= nr) continue;
+            float *acc = acc_det + slot[i] * 6;
+            acc[0] = mr[i];
+            acc[1] = mi[i];
+            acc[2] = gar[i];
+            acc[3] = gai[i];
+            acc[4] = gbr[i];
+            acc[5] = gbi[i];
+        }
     }
 }
 
@@ -201,15 +233,12 @@ __global__ void set_coefficients(const float2 *a, const float2 *b, const int64_t
 
 }  // namespace
 
-int k6_smem_bytes(int W, int Cc, int Dh)
-{
-    return (int)(2 * sizeof(float) * (Dh + Cc) + sizeof(float2) * W * (Cc / kAdjSub) * 32);
-}
+int k6_smem_bytes(int Cc, int Dh) { return (int)(2 * sizeof(float) * (Dh + Cc)); }
 
 cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s)
 {
     if (n_units <= 0 || a.n <= 0) return cudaSuccess;
-    const int smem = k6_smem_bytes(a.W, a.Cc, a.Dh);
+    const int smem = k6_smem_bytes(a.Cc, a.Dh);
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k6_adjoint), smem);
     if (e != cudaSuccess) return e;
     k6_adjoint<<<(unsigned)n_units, a.W * 32, smem, s>>>(a);

@@ -151,6 +151,12 @@ struct Band {
     float2 *ckpt = nullptr;
     int64_t ckpt_cap = 0;      // checkpoints the buffer holds
     float *acc = nullptr;
+    int4 *adj_tasks = nullptr;     // adjoint work list (built on the first backward call)
+    int32_t *adj_units = nullptr;
+    int64_t adj_n_units = 0;
+    int adj_W = 4;
+    float2 *adj_sub = nullptr;     // [adj_n_units][adj_W][kAdjRounds][Cc/kAdjSub][32]
+    int64_t adj_sub_cap = 0;
 };
 
 struct spiir_plan {
@@ -198,6 +204,9 @@ void free_band(Band &b)
     cudaFree(b.bw_state);
     cudaFree(b.ckpt);
     cudaFree(b.acc);
+    cudaFree(b.adj_tasks);
+    cudaFree(b.adj_units);
+    cudaFree(b.adj_sub);
     b = Band();
 }
 
@@ -774,6 +783,46 @@ spiir_status spiir_peak(spiir_plan *p, float *peak_abs_dev, int64_t *peak_idx_de
     return SPIIR_OK;
 }
 
+// Adjoint tasks: kAdjRounds filter rounds of one layout warp (template);
+// adj_W tasks per CTA, every detector.
+spiir_status build_adjoint_tasks(Band &b, int D)
+{
+    const spiir::Layout &L = b.lay;
+    std::vector<int32_t> tasks;
+    for (int64_t g = 0; g < L.n_groups(); ++g)
+        for (int w = 0; w < L.W; ++w) {
+            const int32_t t = L.warp_info[(g * L.W + w) * 4];
+            if (t < 0) continue;
+            for (int r0 = 0; r0 < L.group_F[g]; r0 += spiir::kAdjRounds) {
+                tasks.push_back((int32_t)(L.group_pbase[g] + ((int64_t)r0 * L.W + w) * 32));
+                tasks.push_back(std::min(spiir::kAdjRounds, L.group_F[g] - r0));
+                tasks.push_back(t);
+                tasks.push_back(L.W * 32);
+            }
+        }
+    const int64_t n_tasks = (int64_t)tasks.size() / 4;
+    const int64_t n_groups = (n_tasks + b.adj_W - 1) / b.adj_W;
+    tasks.resize((size_t)n_groups * b.adj_W * 4, 0);
+    for (int64_t i = n_tasks; i < n_groups * b.adj_W; ++i) tasks[4 * i + 2] = -1;  // empty
+    std::vector<int32_t> units((size_t)n_groups * D * 2);
+    for (int64_t g = 0; g < n_groups; ++g)
+        for (int d = 0; d < D; ++d) {
+            units[2 * (g * D + d)] = (int32_t)g;
+            units[2 * (g * D + d) + 1] = d;
+        }
+    cudaError_t e;
+    if ((e = dalloc(&b.adj_tasks, (size_t)n_groups * b.adj_W)) != cudaSuccess ||
+        (e = dalloc(&b.adj_units, units.size())) != cudaSuccess ||
+        (e = cudaMemcpy(b.adj_tasks, tasks.data(), tasks.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(b.adj_units, units.data(), units.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "adjoint task list")
+                                              : cuda_fail(e, "adjoint task upload");
+    b.adj_n_units = n_groups * D;
+    return SPIIR_OK;
+}
+
 spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
                                    const float *grad_z_dev, float *grad_a_dev,
                                    float *grad_b_dev, float *grad_x_dev, void *stream)
@@ -843,19 +892,31 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     if ((e = spiir::launch_k1(f, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
         return cuda_fail(e, "adjoint forward launch");
     // reverse pass
+    if (!b.adj_tasks) {
+        spiir_status st = build_adjoint_tasks(b, D);
+        if (st != SPIIR_OK) return st;
+    }
+    const int64_t sub_need = b.adj_n_units * b.adj_W * spiir::kAdjRounds *
+                             (Cc / spiir::kAdjSub) * 32;
+    if (b.adj_sub_cap < sub_need) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamSynchronize");
+        cudaFree(b.adj_sub);
+        b.adj_sub = nullptr;
+        if ((e = dalloc(&b.adj_sub, (size_t)sub_need)) != cudaSuccess) return oom(e);
+        b.adj_sub_cap = sub_need;
+    }
     spiir::K6Args a{};
     a.xe = b.bw_xe;
     a.xe_stride = b.bw_xe_stride;
     a.n = (int32_t)n;
     a.Dh = L.Dh;
-    a.W = L.W;
+    a.W = b.adj_W;
     a.Cc = Cc;
     a.gz = reinterpret_cast<const float2 *>(grad_z_dev);
     a.T = p->T;
-    a.units = b.units;
-    a.group_F = b.group_F;
-    a.group_pbase = b.group_pbase;
-    a.warp_info = b.warp_info;
+    a.units = b.adj_units;
+    a.tasks = b.adj_tasks;
     a.params = b.params;
     a.ringoff = b.ringoff;
     a.ckpt = b.ckpt;
@@ -863,10 +924,10 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     a.n_det = D;
     a.acc = b.acc;
     a.gx = grad_x_dev;
-    if (spiir::k6_smem_bytes(L.W, Cc, L.Dh) > 227 * 1024)
-        return fail(SPIIR_EUNSUPPORTED, "adjoint shared memory above 227 KB for this plan; "
-                                        "use fewer warps per CTA");
-    if ((e = spiir::launch_k6(a, L.n_units(), s)) != cudaSuccess)
+    a.sub = b.adj_sub;
+    if (spiir::k6_smem_bytes(Cc, L.Dh) > 227 * 1024)
+        return fail(SPIIR_EUNSUPPORTED, "adjoint strain window above 227 KB of shared memory");
+    if ((e = spiir::launch_k6(a, b.adj_n_units, s)) != cudaSuccess)
         return cuda_fail(e, "adjoint kernel launch");
     if ((e = spiir::launch_adj_finalize(b.acc, b.slot_filter, L.n_slots, D,
                                         reinterpret_cast<float2 *>(grad_a_dev),

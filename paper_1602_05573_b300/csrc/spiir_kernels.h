@@ -60,19 +60,20 @@ struct K1Args {
     const double2 *aT;         // chunked: [n_slots] a^chunk in FP64 (kernel form)
 };
 
-// Adjoint (reverse-time) kernel of one zero-state filter call.
+// Adjoint (reverse-time) kernel of one zero-state filter call.  Its work
+// unit is a task: kAdjRounds filter rounds (32 filters each) of one template
+// warp of the forward layout; a CTA runs W tasks of one detector.
 struct K6Args {
     const float *xe;           // [D][xe_stride]: Dh zeros, then the call's strain
     int64_t xe_stride;
     int32_t n;                 // samples
     int32_t Dh;                // history samples before x in xe (>= max delay)
-    int32_t W, Cc;             // warps per CTA, checkpoint interval (samples)
+    int32_t W, Cc;             // tasks (warps) per CTA, checkpoint interval (samples)
     const float2 *gz;          // [D][T][n] dL/dRe z + i dL/dIm z
     int64_t T;
-    const int32_t *units;
-    const int32_t *group_F;
-    const int64_t *group_pbase;
-    const int4 *warp_info;
+    const int32_t *units;      // [n_units][2] (task group, detector)
+    const int4 *tasks;         // [n_groups * W] (first slot of round 0, rounds, template,
+                               //  layout warps per round); template -1 = empty
     const float4 *params;      // kernel form (odd lanes hold conj(a), (Im b, Re b))
     const int2 *ringoff;
     const float2 *ckpt;        // [nc][D][n_slots] from the forward pass
@@ -80,12 +81,14 @@ struct K6Args {
     int32_t n_det;
     float *acc;                // [D][n_slots][6] (mu re, im, g_a re, im, g_b re, im)
     float *gx;                 // [D][n] accumulated with atomics, or null
+    float2 *sub;               // [n_units][W][kAdjRounds][Cc / kAdjSub][32] workspace
 };
 constexpr int kAdjSub = 16;    // samples per recomputed span in the adjoint
+constexpr int kAdjRounds = 2;  // filter rounds per adjoint task (independent chains per lane)
 
 cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s);
 // smem bytes the adjoint kernel needs
-int k6_smem_bytes(int W, int Cc, int Dh);
+int k6_smem_bytes(int Cc, int Dh);
 // g_a[f] = sum_det acc[det][s].ga, g_b likewise, for every slot s holding filter f
 cudaError_t launch_adj_finalize(const float *acc, const int64_t *slot_filter, int64_t n_slots,
                                 int D, float2 *ga, float2 *gb, cudaStream_t s);
