@@ -99,6 +99,11 @@ typedef struct spiir_options {
     int32_t max_filters_per_lane; /* 1..10 filters held per thread; templates with */
                             /* more than 32x this many filters span several warps; */
                             /* 0 = default (10)                                    */
+    int32_t lanes_per_template; /* 32, or 16 (two templates per warp, for small     */
+                            /* templates); 0 = 16 when every template has <= 64    */
+                            /* filters and the bank still fills >= 16 warps per SM */
+                            /* at 16 lanes, else 32                                */
+    int32_t reserved[3];
 } spiir_options;
 
 /* Plan statistics (spiir_plan_get_info). */
@@ -116,6 +121,8 @@ typedef struct spiir_plan_info {
     int32_t max_filters_per_lane; /* largest filters per thread in any CTA        */
     int32_t precision;
     double bank_conflict_ratio; /* mean shared-memory wavefronts per strain load  */
+    int32_t lanes_per_template; /* 32, or 16 when two templates share a warp        */
+    int32_t reserved[3];
 } spiir_plan_info;
 
 typedef struct spiir_plan spiir_plan;

@@ -55,7 +55,8 @@ class Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("chunk_len", ctypes.c_int32),
                 ("block_len", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ring_copies", ctypes.c_int32), ("device", ctypes.c_int32),
-                ("autotune", ctypes.c_int32), ("max_filters_per_lane", ctypes.c_int32)]
+                ("autotune", ctypes.c_int32), ("max_filters_per_lane", ctypes.c_int32),
+                ("lanes_per_template", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -65,7 +66,8 @@ class PlanInfo(ctypes.Structure):
                 ("block_len", ctypes.c_int32), ("ring_copies", ctypes.c_int32),
                 ("history_len", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("max_filters_per_lane", ctypes.c_int32), ("precision", ctypes.c_int32),
-                ("bank_conflict_ratio", ctypes.c_double)]
+                ("bank_conflict_ratio", ctypes.c_double),
+                ("lanes_per_template", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 _P = ctypes.c_void_p
@@ -213,7 +215,7 @@ class Plan:
     def __init__(self, bank, *, precision: str = "plain", device: int = 0,
                  block_len: int = 0, warps_per_cta: int = 0, ring_copies: int = 0,
                  chunk_len: int = 256, autotune: bool = False,
-                 max_filters_per_lane: int = 0, lib=None):
+                 max_filters_per_lane: int = 0, lanes_per_template: int = 0, lib=None):
         self._h = None
         self._lib = lib if lib is not None else _lib
         off = np.ascontiguousarray(bank.off, np.int64)
@@ -244,6 +246,7 @@ class Plan:
         opt.chunk_len = int(chunk_len)
         opt.autotune = int(bool(autotune))
         opt.max_filters_per_lane = int(max_filters_per_lane)
+        opt.lanes_per_template = int(lanes_per_template)
         h = _P()
         _check(self._lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
                "spiir_plan_create", self._lib)
@@ -278,7 +281,8 @@ class Plan:
     def info(self) -> dict:
         inf = PlanInfo()
         _check(self._lib.spiir_plan_get_info(self._h, ctypes.byref(inf)), "spiir_plan_get_info", self._lib)
-        return {name: getattr(inf, name) for name, _ in PlanInfo._fields_}
+        return {name: getattr(inf, name) for name, _ in PlanInfo._fields_
+                if name != "reserved"}
 
     def slots(self):
         n = self.info()["n_slots"]

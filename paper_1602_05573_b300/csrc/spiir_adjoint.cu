@@ -50,13 +50,15 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
     const int g = A.units[2 * blockIdx.x];
     const int det = A.units[2 * blockIdx.x + 1];
     const int4 task = A.tasks[(int64_t)g * A.W + warp];
-    const int tmpl = task.z;
-    const bool active = tmpl >= 0;
+    const bool half = A.G == 16;                      // lanes 16..31 serve task.w
+    const bool active = task.z >= 0;
+    const int tmpl = (half && lane >= 16) ? task.w : task.z;
     const int nr = task.y;                   // rounds in this task (<= R)
     const int n = A.n;
     const int nc = (n + A.Cc - 1) / A.Cc;
     const float *xrow = A.xe + (int64_t)det * A.xe_stride;
-    const float2 *grow = active ? A.gz + ((int64_t)det * A.T + tmpl) * n : nullptr;
+    const float2 *grow = tmpl >= 0 ? A.gz + ((int64_t)det * A.T + tmpl) * n : nullptr;
+    const int gsrc = half ? (lane & 16) : 0;          // lane holding this lane's g_z
     float2 *wsub = A.sub + ((int64_t)blockIdx.x * A.W + warp) * R * nsub_max * 32;
     float *acc_det = A.acc + (int64_t)det * A.n_slots * 6;
 
@@ -67,7 +69,7 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
     bool odd = (lane & 1) != 0;   // stored as conj(a), (Im b, Re b)
 #pragma unroll
     for (int i = 0; i < R; ++i) {
-        slot[i] = active ? (int64_t)task.x + (int64_t)i * task.w + lane : 0;
+        slot[i] = active ? (int64_t)task.x + (int64_t)i * A.round_stride + lane : 0;
         ar[i] = ai[i] = br[i] = bi[i] = 0.f;
         xo[i] = 0;
         if (active && i < nr) {
@@ -145,12 +147,15 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
                         }
                     }
                 }
+                // lanes gsrc + t hold g_z[k0 + t] of their half's template
                 float2 gl = make_float2(0.f, 0.f);
-                if (lane < kAdjSub && k0 + lane < cv) gl = grow[kc + k0 + lane];
+                const int tl = lane & 15;
+                if ((half || lane < 16) && grow != nullptr && k0 + tl < cv)
+                    gl = grow[kc + k0 + tl];
 #pragma unroll
                 for (int t = kAdjSub - 1; t >= 0; --t) {
-                    const float Gr = __shfl_sync(kFull, gl.x, t);
-                    const float Gi = __shfl_sync(kFull, gl.y, t);
+                    const float Gr = __shfl_sync(kFull, gl.x, gsrc + t);
+                    const float Gi = __shfl_sync(kFull, gl.y, gsrc + t);
                     if (k0 + t < cv) {
 #pragma unroll
                         for (int i = 0; i < R; ++i) {

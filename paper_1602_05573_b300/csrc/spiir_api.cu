@@ -321,6 +321,7 @@ spiir::K1Args k1_args(const spiir_plan *p, const Band &b, int64_t n, float *z, i
     a.group_pbase = b.group_pbase;
     a.warp_info = b.warp_info;
     a.fcap = L.Fcap;
+    a.G = L.G;
     a.mode = p->precision == SPIIR_PREC_COMPENSATED
                  ? spiir::kModeCompensated
                  : (p->precision == SPIIR_PREC_CHUNKED_FP64 ? spiir::kModeChunked
@@ -432,6 +433,7 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     lo.Tb = opt.block_len ? opt.block_len : 512;
     lo.C = opt.ring_copies;
     lo.Fcap = opt.max_filters_per_lane;
+    lo.G = opt.lanes_per_template;
     if (opt.precision != SPIIR_PREC_PLAIN) {
         // the compensated and chunked kernels hold at most kPreciseFcap filters per lane
         if (lo.Fcap == 0 || lo.Fcap > spiir::kPreciseFcap) lo.Fcap = spiir::kPreciseFcap;
@@ -553,6 +555,7 @@ spiir_status spiir_plan_get_info(const spiir_plan *p, spiir_plan_info *info)
         if (&b == &p->bands[p->top]) info->history_len = L.Dh;
         info->smem_bytes = std::max(info->smem_bytes, L.smem_bytes());
         info->max_filters_per_lane = std::max(info->max_filters_per_lane, L.maxF);
+        if (&b == &p->bands[p->top]) info->lanes_per_template = L.G;
         wf += L.conflict_ratio * (double)L.n_slots;
         rounds += (double)L.n_slots;
     }
@@ -792,12 +795,13 @@ spiir_status build_adjoint_tasks(Band &b, int D)
     for (int64_t g = 0; g < L.n_groups(); ++g)
         for (int w = 0; w < L.W; ++w) {
             const int32_t t = L.warp_info[(g * L.W + w) * 4];
+            const int32_t t2 = L.G == 16 ? L.warp_info[(g * L.W + w) * 4 + 3] : -1;
             if (t < 0) continue;
             for (int r0 = 0; r0 < L.group_F[g]; r0 += spiir::kAdjRounds) {
                 tasks.push_back((int32_t)(L.group_pbase[g] + ((int64_t)r0 * L.W + w) * 32));
                 tasks.push_back(std::min(spiir::kAdjRounds, L.group_F[g] - r0));
                 tasks.push_back(t);
-                tasks.push_back(L.W * 32);
+                tasks.push_back(t2);
             }
         }
     const int64_t n_tasks = (int64_t)tasks.size() / 4;
@@ -917,6 +921,8 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     a.T = p->T;
     a.units = b.adj_units;
     a.tasks = b.adj_tasks;
+    a.round_stride = L.W * 32;
+    a.G = L.G;
     a.params = b.params;
     a.ringoff = b.ringoff;
     a.ckpt = b.ckpt;

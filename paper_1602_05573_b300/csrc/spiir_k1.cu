@@ -157,9 +157,11 @@ __device__ __forceinline__ void issue_block(const K1Args &A, const float *xrow, 
 // zr/zi: this lane's partial sums (its filters) for 8 consecutive samples.
 // Even lanes hold (re, im), odd lanes (im, re).  After the exchange, lane i
 // (and lane i^16) holds component (i & 1) of sample s(i) summed over the
-// warp; lanes 0..15 write the 8 complex sums to out[0..15].
+// warp; lanes 0..15 write the 8 complex sums to out[0..15].  In half-warp
+// mode the last (lane 16) exchange is skipped and each half writes its own
+// template's sums to out[half * Tb * 2 + ...].
 __device__ __forceinline__ void warp_sum8(const float (&zr)[kTS], const float (&zi)[kTS],
-                                          int lane, float *out)
+                                          int lane, float *out, bool half, int Tb)
 {
     float v[kTS];
 #pragma unroll
@@ -182,9 +184,15 @@ __device__ __forceinline__ void warp_sum8(const float (&zr)[kTS], const float (&
         const float keep = b3 ? v[1] : v[0];
         v[0] = keep + __shfl_xor_sync(kFull, send, 8);
     }
-    v[0] += __shfl_xor_sync(kFull, v[0], 16);
     const int s = (b1 ? 4 : 0) + (b2 ? 2 : 0) + (b3 ? 1 : 0);
-    if (lane < 16) out[2 * s + (lane & 1)] = v[0];
+    if (half) {
+        // lanes 0..15 and 16..31 serve different templates: each half holds
+        // its template's 8 complex sums; write them to the half's buffer
+        out[(lane >> 4) * Tb * 2 + 2 * s + (lane & 1)] = v[0];
+    } else {
+        v[0] += __shfl_xor_sync(kFull, v[0], 16);
+        if (lane < 16) out[2 * s + (lane & 1)] = v[0];
+    }
 }
 
 // ---- the first warp of a template: add its warps' sums, store, peak ------
@@ -543,6 +551,28 @@ template <int F> struct ChunkLanes {
     __device__ __forceinline__ float2 state_of(int r) const { return make_float2(yr[r], yi[r]); }
 };
 
+// ---- running peak of one template: warp max, then merge with the plan's --
+__device__ __forceinline__ void warp_peak_merge(const K1Args &A, int det, int tmpl, int lane,
+                                                float best, int bidx)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ob = __shfl_xor_sync(kFull, best, off);
+        const int oi = __shfl_xor_sync(kFull, bidx, off);
+        if (ob > best || (ob == best && oi >= 0 && (bidx < 0 || oi < bidx))) {
+            best = ob;
+            bidx = oi;
+        }
+    }
+    if (lane == 0 && bidx >= 0) {
+        const int64_t i = (int64_t)det * A.T + tmpl;
+        if (best > A.peak_best[i]) {
+            A.peak_best[i] = best;
+            A.peak_idx[i] = (A.t0_dev != nullptr ? *A.t0_dev : 0) + A.t0 + bidx;
+        }
+    }
+}
+
 // ---- one CTA work unit: W warps x one detector, whole call ----------------
 template <template <int> class LANES, int F>
 __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float *ring,
@@ -551,6 +581,9 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int4 wi = A.warp_info[(int64_t)g * A.W + warp];
     const int tmpl = wi.x;
+    const bool half = A.G == 16;
+    const int tmpl2 = half ? wi.w : -1;      // half-warp mode: template of lanes 16..31
+    const int per_warp = half ? 2 : 1;       // template slots per warp
     const bool active = tmpl >= 0;
     const bool leader = active && wi.y == warp;
     const int64_t pb = A.group_pbase[g];
@@ -577,8 +610,11 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     float *zrow = (A.z != nullptr && leader)
                       ? A.z + ((int64_t)det * A.T + tmpl) * 2 * A.z_len
                       : nullptr;
-    float best = -1.0f;
-    int bidx = -1;
+    float *zrow2 = (A.z != nullptr && leader && tmpl2 >= 0)
+                       ? A.z + ((int64_t)det * A.T + tmpl2) * 2 * A.z_len
+                       : nullptr;
+    float best = -1.0f, best2 = -1.0f;
+    int bidx = -1, bidx2 = -1;
 
     // prologue: history blocks + block 0 on bar0, block 1 on bar1
     if (threadIdx.x == 0) {
@@ -602,17 +638,18 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
         }
         const int k0 = j * A.Tb;
         const int nv = min(A.Tb, n - k0);
-        float *zb = zbuf + (int64_t)((j & 1) * A.W) * A.Tb * 2;   // this block's sums
+        // this block's sums: [W * per_warp template slots][Tb] complex
+        float *zb = zbuf + (int64_t)((j & 1) * A.W * per_warp) * A.Tb * 2;
         if (active) {
             int base[F];
 #pragma unroll
             for (int r = 0; r < F; ++r) base[r] = cb[r] + pos[r];
-            float *zw = zb + (int64_t)warp * A.Tb * 2;
+            float *zw = zb + (int64_t)warp * per_warp * A.Tb * 2;
             for (int sb = 0; sb < nv; sb += kTS) {
                 const int valid = nv - sb;
                 float zr[kTS], zi[kTS];
                 L.step8(ring, base, valid, zr, zi);
-                warp_sum8(zr, zi, lane, zw + 2 * sb);
+                warp_sum8(zr, zi, lane, zw + 2 * sb, half, A.Tb);
                 L.after8(A, k0 + sb + min(valid, kTS));
 #pragma unroll
                 for (int r = 0; r < F; ++r) base[r] += kTS;
@@ -639,9 +676,13 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             mbar_expect_tx(bar, block_bytes(A, e));
             issue_block(A, xrow, ring, e, bar);
         }
-        if (leader)
-            combine_block(A, reinterpret_cast<const float2 *>(zb), wi.y, wi.z, det, tmpl, lane,
-                          k0, nv, zrow, best, bidx);
+        if (leader) {
+            combine_block(A, reinterpret_cast<const float2 *>(zb), wi.y * per_warp, wi.z, det,
+                          tmpl, lane, k0, nv, zrow, best, bidx);
+            if (tmpl2 >= 0)
+                combine_block(A, reinterpret_cast<const float2 *>(zb), warp * 2 + 1, 1, det,
+                              tmpl2, lane, k0, nv, zrow2, best2, bidx2);
+        }
     }
     if (failed_at >= 0) {
         if (threadIdx.x == 0) {
@@ -661,22 +702,8 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     L.store(A, pb, warp, lane, det);
     // running peak: largest |z|^2, earliest index on ties
     if (leader && A.peak_best != nullptr) {
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const float ob = __shfl_xor_sync(kFull, best, off);
-            const int oi = __shfl_xor_sync(kFull, bidx, off);
-            if (ob > best || (ob == best && oi >= 0 && (bidx < 0 || oi < bidx))) {
-                best = ob;
-                bidx = oi;
-            }
-        }
-        if (lane == 0 && bidx >= 0) {
-            const int64_t i = (int64_t)det * A.T + tmpl;
-            if (best > A.peak_best[i]) {
-                A.peak_best[i] = best;
-                A.peak_idx[i] = (A.t0_dev != nullptr ? *A.t0_dev : 0) + A.t0 + bidx;
-            }
-        }
+        warp_peak_merge(A, det, tmpl, lane, best, bidx);
+        if (tmpl2 >= 0) warp_peak_merge(A, det, tmpl2, lane, best2, bidx2);
     }
 }
 

@@ -29,6 +29,7 @@ struct K1Args {
     int32_t n;                 // samples in this call (band rate)
     int32_t Tb, H, S, R, CS, C, W;
     int32_t fcap;              // filters-per-lane cap of the layout (selects the kernel)
+    int32_t G;                 // lanes per template (16: two templates per warp)
     const int32_t *units;      // [n_units][2] (group, detector)
     const int32_t *group_F;    // [G]
     const int64_t *group_pbase;// [G]
@@ -72,8 +73,11 @@ struct K6Args {
     const float2 *gz;          // [D][T][n] dL/dRe z + i dL/dIm z
     int64_t T;
     const int32_t *units;      // [n_units][2] (task group, detector)
-    const int4 *tasks;         // [n_groups * W] (first slot of round 0, rounds, template,
-                               //  layout warps per round); template -1 = empty
+    const int4 *tasks;         // [n_groups * W] (first slot of round 0, rounds, template of
+                               //  lanes 0..15 (or all), template of lanes 16..31 or -1);
+                               //  template -1 = empty task
+    int32_t round_stride;      // slots between a warp's consecutive rounds (32 x layout W)
+    int32_t G;                 // lanes per template of the forward layout
     const float4 *params;      // kernel form (odd lanes hold conj(a), (Im b, Re b))
     const int2 *ringoff;
     const float2 *ckpt;        // [nc][D][n_slots] from the forward pass

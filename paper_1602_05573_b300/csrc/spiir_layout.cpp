@@ -133,6 +133,78 @@ int place_template(const std::vector<int64_t> &fl, const int32_t *d, int F, int 
     return (int)overflow.size();
 }
 
+// Half-warp mode: template A in lanes 0..15, template B in lanes 16..31 of
+// F rounds.  Greedy: each filter takes the round with a free lane in its
+// half where one of its C banks is unused by the whole warp round (most free
+// lanes first); otherwise any free lane in its half (a conflict).  Empty
+// cells become padding filters on unused banks.
+void place_half(const std::vector<int64_t> &flA, const std::vector<int64_t> &flB,
+                const int32_t *d, int F, int C, int CS, std::vector<Cell> &cells,
+                double *wavefronts)
+{
+    cells.assign((size_t)F * 32, Cell());
+    std::vector<uint32_t> used(F, 0u);
+    std::vector<int> nfree(2 * F, 16);
+    const std::vector<int64_t> *lists[2] = {&flA, &flB};
+    for (int h = 0; h < 2; ++h) {
+        for (int64_t l : *lists[h]) {
+            const int dl = d[l];
+            int br = -1, bc = -1;
+            for (int r = 0; r < F; ++r) {
+                if (nfree[2 * r + h] == 0) continue;
+                if (br >= 0 && nfree[2 * r + h] <= nfree[2 * br + h]) continue;
+                for (int c = 0; c < C; ++c)
+                    if (!((used[r] >> mod32((int64_t)c * CS - dl)) & 1u)) {
+                        br = r;
+                        bc = c;
+                        break;
+                    }
+            }
+            if (br < 0) {
+                for (int r = 0; r < F; ++r)
+                    if (nfree[2 * r + h] > 0 && (br < 0 || nfree[2 * r + h] > nfree[2 * br + h]))
+                        br = r;
+                bc = 0;
+            }
+            const int lane = h * 16 + (16 - nfree[2 * br + h]);
+            Cell &cell = cells[(size_t)br * 32 + lane];
+            cell.filter = l;
+            cell.copy = bc;
+            cell.delay = dl;
+            used[br] |= 1u << mod32((int64_t)bc * CS - dl);
+            --nfree[2 * br + h];
+        }
+    }
+    for (int r = 0; r < F; ++r)
+        for (int h = 0; h < 2; ++h)
+            for (int lane = h * 16 + (16 - nfree[2 * r + h]); lane < h * 16 + 16; ++lane) {
+                int bank = 0;
+                while (bank < 32 && ((used[r] >> bank) & 1u)) ++bank;
+                if (bank == 32) bank = lane;
+                used[r] |= 1u << (bank & 31);
+                Cell &cell = cells[(size_t)r * 32 + lane];
+                cell.filter = -1;
+                cell.copy = 0;
+                cell.delay = (32 - bank) % 32;
+            }
+    double wf = 0.0;
+    for (int r = 0; r < F; ++r) {
+        int worst = 1;
+        for (int bank = 0; bank < 32; ++bank) {
+            std::vector<std::pair<int, int>> addr;
+            for (int lane = 0; lane < 32; ++lane) {
+                const Cell &c = cells[(size_t)r * 32 + lane];
+                if (mod32((int64_t)c.copy * CS - c.delay) == bank)
+                    addr.emplace_back(c.copy, c.delay);
+            }
+            std::sort(addr.begin(), addr.end());
+            worst = std::max(worst, (int)(std::unique(addr.begin(), addr.end()) - addr.begin()));
+        }
+        wf += worst;
+    }
+    *wavefronts = wf;
+}
+
 }  // namespace
 
 bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const float *a,
@@ -161,12 +233,29 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
         *err = "layout: max_filters_per_lane must be in [1, " + std::to_string(kMaxF) + "]";
         return false;
     }
-    // per template: rounds of 32 filters, warps w, filters per lane F
+    // lanes per template: half warps for small templates (more filters per lane)
+    int64_t maxL = 0;
+    for (int64_t t = 0; t < L.T; ++t) maxL = std::max<int64_t>(maxL, (int64_t)filters[t].size());
+    // (only when the bank is large enough that halving the warp count still
+    // leaves >= 16 warps per SM; small banks are latency-bound and need warps)
+    const bool small = (maxL + 31) / 32 <= 2 && (maxL + 15) / 16 <= L.Fcap;
+    const bool many = (L.T * D + 1) / 2 >= 16 * (int64_t)opt.n_sm;
+    L.G = opt.G != 0 ? opt.G : (small && many ? 16 : 32);
+    if (L.G != 16 && L.G != 32) {
+        *err = "layout: lanes per template must be 16 or 32";
+        return false;
+    }
+    if (L.G == 16 && (maxL + 15) / 16 > L.Fcap) {
+        *err = "layout: half-warp templates hold at most " + std::to_string(16 * L.Fcap) +
+               " filters";
+        return false;
+    }
+    // per template: rounds of G filters, warps w, filters per lane F
     int64_t maxd = 0, max_nw = 1, total_warps = 0;
     std::vector<int> F(L.T), nw(L.T);
     for (int64_t t = 0; t < L.T; ++t) {
         const int64_t n = (int64_t)filters[t].size();
-        const int64_t rounds = std::max<int64_t>(1, (n + 31) / 32);
+        const int64_t rounds = std::max<int64_t>(1, (n + L.G - 1) / L.G);
         const int64_t w = (rounds + L.Fcap - 1) / L.Fcap;
         if (w > 8) {
             *err = "layout: template " + std::to_string(t) + " has " + std::to_string(n) +
@@ -186,7 +275,7 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
     if (opt.W > 0) {
         L.W = opt.W;
     } else {
-        const int64_t work = total_warps * D;
+        const int64_t work = (L.G == 16 ? (total_warps + 1) / 2 : total_warps) * D;
         int w = max_nw > 4 ? 8 : 4;
         while (w > 1 && w / 2 >= max_nw && work / w < 2 * (int64_t)opt.n_sm) w /= 2;
         L.W = w;
@@ -228,10 +317,29 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
         int used;
         std::vector<int64_t> tmpl;  // per warp
         std::vector<int> first;     // per warp: first warp of its template
+        std::vector<int64_t> tmpl2; // per warp: the second template (half-warp mode)
     };
     std::vector<Group> groups;
     std::vector<size_t> open;       // groups of the current F with free warps
     int curF = -1;
+    if (L.G == 16) {
+        // two consecutive templates (sorted, so of similar F) per warp, W warps per CTA
+        for (size_t i = 0; i < order.size(); i += 2) {
+            const int64_t ta = order[i];
+            const int64_t tb = i + 1 < order.size() ? order[i + 1] : -1;
+            if (groups.empty() || groups.back().used == L.W) {
+                groups.push_back(Group{F[ta], 0, std::vector<int64_t>(L.W, -1),
+                                       std::vector<int>(L.W, -1),
+                                       std::vector<int64_t>(L.W, -1)});
+            }
+            Group &grp = groups.back();
+            grp.tmpl[grp.used] = ta;
+            grp.tmpl2[grp.used] = tb;
+            grp.first[grp.used] = grp.used;
+            grp.used += 1;
+        }
+        order.clear();
+    }
     for (int64_t t : order) {
         if (F[t] != curF) {
             open.clear();
@@ -245,7 +353,7 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
             }
         if (gi == groups.size()) {
             groups.push_back(Group{F[t], 0, std::vector<int64_t>(L.W, -1),
-                                   std::vector<int>(L.W, -1)});
+                                   std::vector<int>(L.W, -1), std::vector<int64_t>(L.W, -1)});
             open.push_back(gi);
         }
         Group &grp = groups[gi];
@@ -271,7 +379,7 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
             wi[0] = (int32_t)t;
             wi[1] = t >= 0 ? groups[g].first[w] : w;
             wi[2] = t >= 0 ? nw[t] : 1;
-            wi[3] = 0;
+            wi[3] = (int32_t)groups[g].tmpl2[w];
         }
     }
     L.n_slots = base;
@@ -292,8 +400,12 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
             const int nwt = t >= 0 ? nw[t] : 1;
             const int rounds = Fg * nwt;   // the template's rounds over its warps
             const std::vector<int64_t> &fl = t >= 0 ? filters[t] : none;
+            const int64_t t2 = groups[g].tmpl2[w];
             double wf = 0.0;
-            place_template(fl, d, rounds, L.C, L.CS, cells, &wf);
+            if (L.G == 16)
+                place_half(fl, t2 >= 0 ? filters[t2] : none, d, rounds, L.C, L.CS, cells, &wf);
+            else
+                place_template(fl, d, rounds, L.C, L.CS, cells, &wf);
             if (t >= 0) {
                 wf_total += wf;
                 rounds_total += rounds;
@@ -321,7 +433,7 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
                     L.ringoff[2 * s + 0] = L.Dh - c.delay;  // window start at block 0
                     L.ringoff[2 * s + 1] = c.copy * L.CS;   // copy base word
                     L.slot_filter[s] = c.filter;
-                    L.slot_template[s] = t;
+                    L.slot_template[s] = (L.G == 16 && i >= 16) ? t2 : t;
                 }
             }
         }

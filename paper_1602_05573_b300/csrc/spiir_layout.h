@@ -35,6 +35,8 @@ constexpr int kTS = 8;      // samples per register sub-block (cross-lane sum wi
 struct LayoutOptions {
     int W = 0;          // warps per CTA; 0 = from the bank size
     int Fcap = 0;       // filters per lane cap (1..kMaxF); 0 = default (kMaxF)
+    int G = 0;          // lanes per template: 32, or 16 (two templates per warp);
+                        // 0 = 16 when every template fits in <= 2 rounds of 32
     int Tb = 512;       // samples per staged strain block (multiple of 32)
     int C = 0;          // ring copies (1, 2, 4); 0 = default (1)
     int n_sm = 148;     // used to pick W when W == 0
@@ -52,13 +54,15 @@ struct Layout {
     int Dh = 0;             // history samples kept = H * Tb
     int maxF = 1;           // largest F of any CTA (<= Fcap)
     int Fcap = 4;
+    int G = 32;             // lanes per template (16: a warp serves two templates)
     int64_t n_slots = 0;    // filter slots including padding (per detector)
     int64_t n_filters = 0;  // real filters in this layout
 
     std::vector<int32_t> group_F;       // [G]
     std::vector<int64_t> group_pbase;   // [G] first slot of the group
     std::vector<int32_t> warp_info;     // [G * W][4] (template or -1, first warp of the
-                                        //  template, its warp count, 0)
+                                        //  template, its warp count, second template
+                                        //  of a half-warp pair or -1)
     std::vector<float> params;          // [n_slots][4] kernel-form (ar, ai, br, bi)
     std::vector<int32_t> ringoff;       // [n_slots][2] (pos0, copy base word)
     std::vector<int64_t> slot_filter;   // [n_slots] bank filter index, -1 = padding
@@ -68,8 +72,9 @@ struct Layout {
 
     int64_t n_groups() const { return (int64_t)group_F.size(); }
     int64_t n_units() const { return (int64_t)units.size() / 2; }
-    // mbarriers, C ring copies, and two Tb-sample partial-sum buffers per warp
-    int smem_bytes() const { return 128 + C * CS * 4 + 2 * W * Tb * 8; }
+    // mbarriers, C ring copies, and two Tb-sample partial-sum buffers per
+    // template slot (two per warp in half-warp mode)
+    int smem_bytes() const { return 128 + C * CS * 4 + 2 * W * (32 / G) * Tb * 8; }
     // slot of (group g, round r, warp w, lane i)
     int64_t slot(int64_t g, int r, int w, int i) const {
         return group_pbase[g] + ((int64_t)r * W + w) * 32 + i;

@@ -119,7 +119,8 @@ def test_slot_layout_covers_every_filter_once(counts, W, C, Fcap):
     tmpl_of = np.repeat(np.arange(len(counts)), counts)
     assert np.array_equal(st[sf >= 0], tmpl_of[sf[sf >= 0]])
     info = p.info()
-    assert info["n_units"] * info["warps_per_cta"] >= len(counts) * 2
+    per_warp = 32 // info["lanes_per_template"]
+    assert info["n_units"] * info["warps_per_cta"] * per_warp >= len(counts) * 2
     assert info["max_filters_per_lane"] <= (Fcap or 10)
     assert info["history_len"] >= int(d.max())
     assert info["history_len"] % info["block_len"] == 0
@@ -154,3 +155,16 @@ def test_multirate_plan_layout_and_validation():
     bad.band_of[0] = 5
     with pytest.raises(sp.SpiirError):
         sp.Plan(bad, device=-1)
+
+
+def test_half_warp_mode_for_small_templates():
+    """Templates of <= 64 filters pair up in a warp (16 lanes each), so each
+    lane holds twice the filters; larger ones keep 32 lanes."""
+    many = make_bank(4800, (20, 64), (0.9, 0.99), 100, seed=5)
+    assert sp.Plan(many, device=-1).info()["lanes_per_template"] == 16
+    # few templates: keep one per warp (latency-bound, needs warps)
+    few = make_bank(10, (20, 64), (0.9, 0.99), 100, seed=5)
+    assert sp.Plan(few, device=-1).info()["lanes_per_template"] == 32
+    assert sp.Plan(few, device=-1, lanes_per_template=16).info()["lanes_per_template"] == 16
+    big = make_bank(4800, (20, 65), (0.9, 0.99), 100, seed=5)
+    assert sp.Plan(big, device=-1).info()["lanes_per_template"] == 32

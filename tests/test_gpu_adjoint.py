@@ -51,6 +51,21 @@ def test_adjoint_matches_oracle(sp, n, D, opts):
     assert rel_inf(gx, rx) <= GRAD_TOL
 
 
+def test_adjoint_half_warp_templates(sp):
+    """Templates of <= 64 filters share warps (16 lanes each) in the forward
+    layout; the adjoint reads each half's own g_z."""
+    bank = make_bank(5, (10, 64), (0.99, 0.9995), 500, seed=98, n_det=2)
+    x = make_strain(2, 2100, seed=99)
+    rng = np.random.default_rng(100)
+    gz = (rng.standard_normal((2, 5, 2100)) + 1j * rng.standard_normal((2, 5, 2100))).astype(
+        np.complex64)
+    ga, gb, gx = gpu_backward(sp, bank, x, gz, lanes_per_template=16)
+    ra, rb, rx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, gz)
+    assert rel_inf(ga, ra) <= GRAD_TOL
+    assert rel_inf(gb, rb) <= GRAD_TOL
+    assert rel_inf(gx, rx) <= GRAD_TOL
+
+
 def test_adjoint_leaves_streaming_state_alone(sp):
     bank = make_bank(3, 40, (0.99, 0.999), 100, seed=93)
     x = torch.from_numpy(make_strain(1, 2000, seed=94)).cuda()

@@ -211,3 +211,14 @@ def test_batched_workload_full_size_sampled(sp):
                     pi[det, t].cpu().numpy()[None, None])
     del z
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("n_templates,W", [(9, 0), (1, 1), (16, 3)])
+def test_half_warp_templates(sp, n_templates, W):
+    """Small templates pair up in a warp (16 lanes each); an odd count leaves
+    the last warp's second half empty."""
+    bank = make_bank(n_templates, (10, 64), (0.99, 0.9995), 800, seed=71, n_det=2)
+    x = make_strain(2, 3001, seed=72)
+    z, pa, pi, plan = run_gpu(sp, bank, x, warps_per_cta=W, lanes_per_template=16)
+    assert plan.info()["lanes_per_template"] == 16
+    assert_parity(z, pa, pi, oracle_z(bank, x))
