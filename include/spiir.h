@@ -103,7 +103,14 @@ typedef struct spiir_options {
                             /* templates); 0 = 16 when every template has <= 64    */
                             /* filters and the bank still fills >= 16 warps per SM */
                             /* at 16 lanes, else 32                                */
-    int32_t reserved[3];
+    int32_t time_segments;  /* plain precision: split each call into this many time */
+                            /* segments run in parallel (a zero-state pass plus an  */
+                            /* FP64 carry of the segment start states; segments are */
+                            /* >= 2 blocks long); 0 = auto: banks that fill < 1/8   */
+                            /* of the GPU's warps get up to 8 warps/SM worth (>= 4  */
+                            /* segments, <= 64), others none; 1 = off.  Results of  */
+                            /* different splits agree to rounding, not bit for bit  */
+    int32_t reserved[2];
 } spiir_options;
 
 /* Plan statistics (spiir_plan_get_info). */

@@ -56,7 +56,8 @@ class Options(ctypes.Structure):
                 ("block_len", ctypes.c_int32), ("warps_per_cta", ctypes.c_int32),
                 ("ring_copies", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("max_filters_per_lane", ctypes.c_int32),
-                ("lanes_per_template", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("lanes_per_template", ctypes.c_int32), ("time_segments", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -215,7 +216,8 @@ class Plan:
     def __init__(self, bank, *, precision: str = "plain", device: int = 0,
                  block_len: int = 0, warps_per_cta: int = 0, ring_copies: int = 0,
                  chunk_len: int = 256, autotune: bool = False,
-                 max_filters_per_lane: int = 0, lanes_per_template: int = 0, lib=None):
+                 max_filters_per_lane: int = 0, lanes_per_template: int = 0,
+                 time_segments: int = 0, lib=None):
         self._h = None
         self._lib = lib if lib is not None else _lib
         off = np.ascontiguousarray(bank.off, np.int64)
@@ -247,6 +249,7 @@ class Plan:
         opt.autotune = int(bool(autotune))
         opt.max_filters_per_lane = int(max_filters_per_lane)
         opt.lanes_per_template = int(lanes_per_template)
+        opt.time_segments = int(time_segments)
         h = _P()
         _check(self._lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
                "spiir_plan_create", self._lib)

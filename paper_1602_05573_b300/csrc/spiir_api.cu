@@ -151,6 +151,11 @@ struct Band {
     float2 *ckpt = nullptr;
     int64_t ckpt_cap = 0;      // checkpoints the buffer holds
     float *acc = nullptr;
+    float2 *seg_end = nullptr;     // time segments: [P][D][n_slots] projection end states
+    float2 *seg_init = nullptr;    //                [P][D][n_slots] segment start states
+    float *seg_best = nullptr;     //                [P][D][T] per-segment peaks
+    int64_t *seg_idx = nullptr;
+    int seg_cap = 0;               // segments the workspaces hold
     int4 *adj_tasks = nullptr;     // adjoint work list (built on the first backward call)
     int32_t *adj_units = nullptr;
     int64_t adj_n_units = 0;
@@ -204,6 +209,10 @@ void free_band(Band &b)
     cudaFree(b.bw_state);
     cudaFree(b.ckpt);
     cudaFree(b.acc);
+    cudaFree(b.seg_end);
+    cudaFree(b.seg_init);
+    cudaFree(b.seg_best);
+    cudaFree(b.seg_idx);
     cudaFree(b.adj_tasks);
     cudaFree(b.adj_units);
     cudaFree(b.adj_sub);
@@ -329,6 +338,13 @@ spiir::K1Args k1_args(const spiir_plan *p, const Band &b, int64_t n, float *z, i
     a.chunk = p->opt.chunk_len;
     a.state_ext = b.state_ext;
     a.aT = b.aT;
+    a.n_det = p->D;
+    a.n_units = (int32_t)L.n_units();
+    a.n_seg = (int32_t)n;          // one segment unless spiir_filter splits the call
+    a.zero_init = 0;
+    a.seg_init = nullptr;
+    a.seg_end = nullptr;
+    a.peak_seg_stride = 0;
     a.params = b.params;
     a.ringoff = b.ringoff;
     a.state = b.state;
@@ -604,6 +620,100 @@ spiir_status spiir_reset(spiir_plan *p, void *stream)
     return SPIIR_OK;
 }
 
+// Time segments for a band call of nb samples, each at least 2 blocks long.
+// Segmenting costs a second (zero-state) pass over all but the last segment,
+// so by default it is used only for banks that fill under 1/8 of the GPU's
+// warp slots (8 warps per SM as the target), and only when it gives at
+// least 4 segments; a time_segments option above 0 forces the count.
+int segments_for(const spiir_plan *p, const Band &b, int64_t nb)
+{
+    if (p->precision != SPIIR_PREC_PLAIN) return 1;
+    const int req = p->opt.time_segments;
+    const int64_t warps = b.lay.n_units() * b.lay.W;
+    int P = 1;
+    if (req >= 1) {
+        P = req;
+    } else {
+        const int64_t target = 8 * (int64_t)p->n_sm;
+        const int64_t want = std::min<int64_t>(64, target / std::max<int64_t>(warps, 1));
+        if (want >= 4) P = (int)want;
+    }
+    const int64_t max_p = std::max<int64_t>(1, nb / (2 * (int64_t)b.lay.Tb));
+    P = (int)std::max<int64_t>(1, std::min<int64_t>(P, max_p));
+    return (req < 1 && P < 4) ? 1 : P;
+}
+
+// Launch K1 for one band call split into time segments: a zero-state pass
+// over all but the last segment keeps each segment's end state, an FP64 carry
+// turns those into the true start state of every segment, and the main pass
+// runs every segment from its start state; per-segment peaks are merged in
+// time order.
+spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cudaStream_t s)
+{
+    const spiir::Layout &L = b.lay;
+    const int D = p->D;
+    const int64_t per = (int64_t)D * L.n_slots;
+    const int64_t n = a.n;
+    const int64_t n_seg = ((n + P - 1) / P + L.Tb - 1) / L.Tb * L.Tb;
+    P = (int)((n + n_seg - 1) / n_seg);
+    cudaError_t e;
+    if (P <= 1) {
+        if ((e = spiir::launch_k1(a, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
+            return cuda_fail(e, "filter kernel launch");
+        return SPIIR_OK;
+    }
+    if (b.seg_cap < P) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamSynchronize");
+        cudaFree(b.seg_end);
+        cudaFree(b.seg_init);
+        cudaFree(b.seg_best);
+        cudaFree(b.seg_idx);
+        b.seg_end = b.seg_init = nullptr;
+        b.seg_best = nullptr;
+        b.seg_idx = nullptr;
+        if ((e = dalloc(&b.seg_end, (size_t)P * per)) != cudaSuccess ||
+            (e = dalloc(&b.seg_init, (size_t)P * per)) != cudaSuccess ||
+            (e = dalloc(&b.seg_best, (size_t)P * D * p->T)) != cudaSuccess ||
+            (e = dalloc(&b.seg_idx, (size_t)P * D * p->T)) != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "segment workspace")
+                                                  : cuda_fail(e, "cudaMalloc");
+        b.seg_cap = P;
+    }
+    a.n_seg = (int32_t)n_seg;
+    // projection: segments 0..P-2 from zero state, no z, no peak
+    spiir::K1Args proj = a;
+    proj.zero_init = 1;
+    proj.seg_end = b.seg_end;
+    proj.z = nullptr;
+    proj.peak_best = nullptr;
+    proj.peak_idx = nullptr;
+    proj.n_lower = 0;
+    if ((e = spiir::launch_k1(proj, L.n_units(), L.smem_bytes(), s)) != cudaSuccess ||
+        (e = spiir::launch_segment_carry(b.params, b.state, b.seg_end, b.seg_init, L.n_slots, D,
+                                         P, (int)n_seg, s)) != cudaSuccess)
+        return cuda_fail(e, "segment projection launch");
+    // main pass: every segment from its start state
+    float *best = a.peak_best;
+    int64_t *idx = a.peak_idx;
+    a.seg_init = b.seg_init;
+    if (best != nullptr) {
+        a.peak_best = b.seg_best;
+        a.peak_idx = b.seg_idx;
+        a.peak_seg_stride = (int64_t)D * p->T;
+        if ((e = spiir::launch_peak_reset(b.seg_best, b.seg_idx, (int64_t)P * D * p->T, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "segment peak reset");
+    }
+    if ((e = spiir::launch_k1(a, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
+        return cuda_fail(e, "filter kernel launch");
+    if (best != nullptr &&
+        (e = spiir::launch_peak_merge(b.seg_best, b.seg_idx, P, (int64_t)D * p->T, best, idx,
+                                      s)) != cudaSuccess)
+        return cuda_fail(e, "segment peak merge");
+    return SPIIR_OK;
+}
+
 // Time candidate layouts on a prefix of the first call's strain (zero state,
 // no z, no peak) and keep the fastest.  Synchronous; runs once per plan.
 spiir_status autotune(spiir_plan *p, const float *x_dev, int64_t n, cudaStream_t s)
@@ -749,8 +859,8 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
             }
             spiir::K1Args a = k1_args(p, b, nb, reinterpret_cast<float *>(b.zb), nb, false);
             a.t0 = p->t0 / b.R;
-            if ((e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s)) != cudaSuccess)
-                return cuda_fail(e, "band filter kernel launch");
+            st = launch_segmented(p, b, a, segments_for(p, b, nb), s);
+            if (st != SPIIR_OK) return st;
             spiir::LowerBand &lb = top_args.lower[top_args.n_lower++];
             lb.z = b.zb;
             lb.len = nb;
@@ -761,8 +871,9 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
             a.t0_dev = p->t0_dev;
             a.n_lower = top_args.n_lower;
             for (int i = 0; i < a.n_lower; ++i) a.lower[i] = top_args.lower[i];
-            if ((e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s)) != cudaSuccess ||
-                (e = spiir::launch_advance(p->t0_dev, n, s)) != cudaSuccess)
+            st = launch_segmented(p, b, a, segments_for(p, b, n), s);
+            if (st != SPIIR_OK) return st;
+            if ((e = spiir::launch_advance(p->t0_dev, n, s)) != cudaSuccess)
                 return cuda_fail(e, "filter kernel launch");
         }
         // band history for the next call: the last Dh band samples of (history, x_b)

@@ -246,7 +246,8 @@ template <int F> struct PackedLanes {
     uint64_t AR[NPA], AI[NPA], NAI[NPA], BR[NPA], BI[NPA], YR[NPA], YI[NPA];
     float ar1 = 0.f, ai1 = 0.f, br1 = 0.f, bi1 = 0.f, yr1 = 0.f, yi1 = 0.f;
 
-    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det,
+                                         const float2 *sin)
     {
         float4 p[F];
         float2 st[F];
@@ -254,7 +255,7 @@ template <int F> struct PackedLanes {
         for (int r = 0; r < F; ++r) {
             const int64_t s = pb + ((int64_t)r * A.W + warp) * 32 + lane;
             p[r] = A.params[s];
-            st[r] = A.state[(int64_t)det * A.n_slots + s];
+            st[r] = sin != nullptr ? sin[(int64_t)det * A.n_slots + s] : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) {
@@ -336,11 +337,13 @@ template <int F> struct PackedLanes {
     }
     __device__ __forceinline__ void after8(const K1Args &, int) {}
     __device__ __forceinline__ void finish(const K1Args &, int) {}
-    __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det,
+                                          float2 *sout)
     {
+        if (sout == nullptr) return;
 #pragma unroll
         for (int r = 0; r < F; ++r)
-            A.state[(int64_t)det * A.n_slots + pb + ((int64_t)r * A.W + warp) * 32 + lane] =
+            sout[(int64_t)det * A.n_slots + pb + ((int64_t)r * A.W + warp) * 32 + lane] =
                 state_of(r);
     }
 };
@@ -370,7 +373,8 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
 template <int F> struct CompLanes {
     float ar[F], ai[F], br[F], bi[F], yrh[F], yrl[F], yih[F], yil[F];
 
-    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det,
+                                         const float2 *)
     {
         const float4 *st = reinterpret_cast<const float4 *>(A.state_ext);
 #pragma unroll
@@ -433,7 +437,8 @@ template <int F> struct CompLanes {
     }
     __device__ __forceinline__ void after8(const K1Args &, int) {}
     __device__ __forceinline__ void finish(const K1Args &, int) {}
-    __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det,
+                                          float2 *)
     {
         float4 *st = reinterpret_cast<float4 *>(A.state_ext);
 #pragma unroll
@@ -457,7 +462,8 @@ template <int F> struct ChunkLanes {
     float ar[F], ai[F], br[F], bi[F], yr[F], yi[F], ur[F], ui[F];
     double aTr[F], aTi[F], sr64[F], si64[F];
 
-    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det,
+                                         const float2 *)
     {
         const double2 *st = reinterpret_cast<const double2 *>(A.state_ext);
 #pragma unroll
@@ -540,7 +546,8 @@ template <int F> struct ChunkLanes {
             }
         }
     }
-    __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det)
+    __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det,
+                                          float2 *)
     {
         double2 *st = reinterpret_cast<double2 *>(A.state_ext);
 #pragma unroll
@@ -552,7 +559,8 @@ template <int F> struct ChunkLanes {
 };
 
 // ---- running peak of one template: warp max, then merge with the plan's --
-__device__ __forceinline__ void warp_peak_merge(const K1Args &A, int det, int tmpl, int lane,
+__device__ __forceinline__ void warp_peak_merge(const K1Args &A, float *peak_best,
+                                                int64_t *peak_idx, int det, int tmpl, int lane,
                                                 float best, int bidx)
 {
 #pragma unroll
@@ -566,15 +574,15 @@ __device__ __forceinline__ void warp_peak_merge(const K1Args &A, int det, int tm
     }
     if (lane == 0 && bidx >= 0) {
         const int64_t i = (int64_t)det * A.T + tmpl;
-        if (best > A.peak_best[i]) {
-            A.peak_best[i] = best;
-            A.peak_idx[i] = (A.t0_dev != nullptr ? *A.t0_dev : 0) + A.t0 + bidx;
+        if (best > peak_best[i]) {
+            peak_best[i] = best;
+            peak_idx[i] = (A.t0_dev != nullptr ? *A.t0_dev : 0) + A.t0 + bidx;
         }
     }
 }
 
 // ---- one CTA work unit: W warps x one detector, whole call ----------------
-template <template <int> class LANES, int F>
+template <template <int> class LANES, int F, bool SEG>
 __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float *ring,
                                          float *zbuf, uint32_t bar0, uint32_t bar1)
 {
@@ -587,9 +595,15 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     const bool active = tmpl >= 0;
     const bool leader = active && wi.y == warp;
     const int64_t pb = A.group_pbase[g];
-    const int n = A.n;
+    // this CTA's time segment: call samples [s0, s0 + n) (SEG == false: the
+    // whole call, and the segment arithmetic compiles away)
+    const int seg = SEG ? (int)(blockIdx.x / A.n_units) : 0;
+    const int nseg_total = SEG ? (A.n + A.n_seg - 1) / A.n_seg : 1;
+    const int s0 = SEG ? seg * A.n_seg : 0;
+    const int n = SEG ? min(A.n_seg, A.n - s0) : A.n;
+    const int sblk = s0 / A.Tb;              // first block of the segment
     const int nblk = (n + A.Tb - 1) / A.Tb;
-    const float *xrow = A.xe + (int64_t)det * A.xe_stride;
+    const float *xrow = A.xe + (int64_t)det * A.xe_stride + (int64_t)sblk * A.Tb;
 
     LANES<F> L;
     int pos[F], cb[F];
@@ -602,10 +616,15 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
 #pragma unroll
         for (int r = 0; r < F; ++r) {
             const int2 ro = A.ringoff[pb + ((int64_t)r * A.W + warp) * 32 + lane];
-            pos[r] = ro.x;
+            pos[r] = ro.x;   // xrow starts at the segment: same ring phase
             cb[r] = ro.y;
         }
-        L.load(A, pb, warp, lane, det);
+        // segments read their start state from seg_init (segment 0's is a copy
+        // of the call's start state: the last segment overwrites A.state)
+        const float2 *sin =
+            !SEG ? A.state
+                 : (A.zero_init ? nullptr : A.seg_init + (int64_t)seg * A.n_det * A.n_slots);
+        L.load(A, pb, warp, lane, det, sin);
     }
     float *zrow = (A.z != nullptr && leader)
                       ? A.z + ((int64_t)det * A.T + tmpl) * 2 * A.z_len
@@ -636,8 +655,8 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             failed_at = j;
             break;
         }
-        const int k0 = j * A.Tb;
-        const int nv = min(A.Tb, n - k0);
+        const int k0 = s0 + j * A.Tb;              // call-relative sample index
+        const int nv = min(A.Tb, n - j * A.Tb);
         // this block's sums: [W * per_warp template slots][Tb] complex
         float *zb = zbuf + (int64_t)((j & 1) * A.W * per_warp) * A.Tb * 2;
         if (active) {
@@ -650,7 +669,7 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
                 float zr[kTS], zi[kTS];
                 L.step8(ring, base, valid, zr, zi);
                 warp_sum8(zr, zi, lane, zw + 2 * sb, half, A.Tb);
-                L.after8(A, k0 + sb + min(valid, kTS));
+                L.after8(A, j * A.Tb + sb + min(valid, kTS));
 #pragma unroll
                 for (int r = 0; r < F; ++r) base[r] += kTS;
             }
@@ -699,11 +718,19 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     }
     if (!active) return;
     L.finish(A, n);
-    L.store(A, pb, warp, lane, det);
+    {
+        float2 *sout = !SEG ? A.state
+                            : (A.seg_end != nullptr
+                                   ? A.seg_end + (int64_t)seg * A.n_det * A.n_slots
+                                   : (seg == nseg_total - 1 ? A.state : nullptr));
+        L.store(A, pb, warp, lane, det, sout);
+    }
     // running peak: largest |z|^2, earliest index on ties
     if (leader && A.peak_best != nullptr) {
-        warp_peak_merge(A, det, tmpl, lane, best, bidx);
-        if (tmpl2 >= 0) warp_peak_merge(A, det, tmpl2, lane, best2, bidx2);
+        float *peak_best = A.peak_best + (SEG ? seg * A.peak_seg_stride : 0);
+        int64_t *peak_idx = A.peak_idx + (SEG ? seg * A.peak_seg_stride : 0);
+        warp_peak_merge(A, peak_best, peak_idx, det, tmpl, lane, best, bidx);
+        if (tmpl2 >= 0) warp_peak_merge(A, peak_best, peak_idx, det, tmpl2, lane, best2, bidx2);
     }
 }
 
@@ -718,21 +745,21 @@ template <> struct K1Bounds<8> { static constexpr int kMinBlocks = 2; };
 template <> struct K1Bounds<10> { static constexpr int kMinBlocks = 2; };
 
 // The CTA's F is uniform, so every warp takes the same case.
-template <template <int> class LANES, int FCAP>
+template <template <int> class LANES, int FCAP, bool SEG = false>
 __device__ __forceinline__ void dispatch_f(const K1Args &A, int g, int det, float *ring,
                                            float *zbuf, uint32_t bar0, uint32_t bar1)
 {
     const int F = A.group_F[g];
-    if (F == 1) run_unit<LANES, 1>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    if (F == 1) run_unit<LANES, 1, SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
     else if (threadIdx.x == 0) atomicOr(A.err, 4);
 }
 
@@ -752,15 +779,16 @@ __device__ __forceinline__ void cta_setup(unsigned char *smem, const K1Args &A, 
     __syncthreads();
 }
 
-template <int FCAP>
+template <int FCAP, bool SEG>
 __global__ void __launch_bounds__(256, K1Bounds<FCAP>::kMinBlocks) k1_plain(const K1Args A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     float *ring, *zbuf;
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
-    dispatch_f<PackedLanes, FCAP>(A, A.units[2 * blockIdx.x], A.units[2 * blockIdx.x + 1], ring,
-                                  zbuf, bar0, bar1);
+    const int u = SEG ? (int)(blockIdx.x % A.n_units) : (int)blockIdx.x;
+    dispatch_f<PackedLanes, FCAP, SEG>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
+                                       bar1);
 }
 
 __global__ void __launch_bounds__(256, 2) k1_compensated(const K1Args A)
@@ -769,8 +797,9 @@ __global__ void __launch_bounds__(256, 2) k1_compensated(const K1Args A)
     float *ring, *zbuf;
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
-    dispatch_f<CompLanes, kPreciseFcap>(A, A.units[2 * blockIdx.x], A.units[2 * blockIdx.x + 1],
-                                        ring, zbuf, bar0, bar1);
+    const int u = blockIdx.x % A.n_units;
+    dispatch_f<CompLanes, kPreciseFcap>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
+                                        bar1);
 }
 
 __global__ void __launch_bounds__(256, 2) k1_chunked(const K1Args A)
@@ -779,8 +808,9 @@ __global__ void __launch_bounds__(256, 2) k1_chunked(const K1Args A)
     float *ring, *zbuf;
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
-    dispatch_f<ChunkLanes, kPreciseFcap>(A, A.units[2 * blockIdx.x], A.units[2 * blockIdx.x + 1],
-                                         ring, zbuf, bar0, bar1);
+    const int u = blockIdx.x % A.n_units;
+    dispatch_f<ChunkLanes, kPreciseFcap>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
+                                         bar1);
 }
 
 __global__ void peak_out_kernel(const float *best, const int64_t *idx, int64_t count,
@@ -791,6 +821,57 @@ __global__ void peak_out_kernel(const float *best, const int64_t *idx, int64_t c
     const float b = best[i];
     out_abs[i] = b < 0.f ? 0.f : sqrtf(b);
     out_idx[i] = idx[i];
+}
+
+__global__ void segment_carry_kernel(const float4 *params, const float2 *state,
+                                     const float2 *seg_end, float2 *seg_init, int64_t n_slots,
+                                     int D, int P, int n_seg)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // det * n_slots + slot
+    if (i >= (int64_t)D * n_slots) return;
+    const int64_t s = i % n_slots;
+    const float4 p = params[s];   // kernel form: the pole matches the stored state's form
+    // a^n_seg by repeated squaring in FP64
+    double br = p.x, bi = p.y, rr = 1.0, ri = 0.0;
+    for (int e = n_seg; e > 0; e >>= 1) {
+        if (e & 1) {
+            const double nr = rr * br - ri * bi, ni = rr * bi + ri * br;
+            rr = nr;
+            ri = ni;
+        }
+        const double nr = br * br - bi * bi, ni = 2.0 * br * bi;
+        br = nr;
+        bi = ni;
+    }
+    const float2 y0 = state[i];
+    seg_init[i] = y0;
+    double yr = y0.x, yi = y0.y;
+    for (int q = 0; q + 1 < P; ++q) {
+        const float2 e = seg_end[(int64_t)q * D * n_slots + i];
+        const double nr = rr * yr - ri * yi + (double)e.x;
+        const double ni = rr * yi + ri * yr + (double)e.y;
+        yr = nr;
+        yi = ni;
+        seg_init[(int64_t)(q + 1) * D * n_slots + i] = make_float2((float)yr, (float)yi);
+    }
+}
+
+__global__ void peak_merge_kernel(const float *seg_best, const int64_t *seg_idx, int P,
+                                  int64_t count, float *best, int64_t *idx)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    float b = best[i];
+    int64_t k = idx[i];
+    for (int q = 0; q < P; ++q) {
+        const float v = seg_best[(int64_t)q * count + i];
+        if (v > b) {
+            b = v;
+            k = seg_idx[(int64_t)q * count + i];
+        }
+    }
+    best[i] = b;
+    idx[i] = k;
 }
 
 __global__ void advance_kernel(int64_t *t0, int64_t n)
@@ -837,14 +918,19 @@ cudaError_t launch_kernel(Kernel k, const K1Args &a, int64_t n_units, int smem_b
 {
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k), smem_bytes);
     if (e != cudaSuccess) return e;
-    k<<<(unsigned)n_units, a.W * 32, smem_bytes, s>>>(a);
+    const int P = a.n_seg > 0 ? (a.n + a.n_seg - 1) / a.n_seg : 1;
+    const int P_launch = a.seg_end != nullptr ? P - 1 : P;   // the projection skips the last
+    if (P_launch <= 0) return cudaSuccess;
+    k<<<(unsigned)(n_units * P_launch), a.W * 32, smem_bytes, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int FCAP>
 cudaError_t launch_k1_cap(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
 {
-    return launch_kernel(k1_plain<FCAP>, a, n_units, smem_bytes, s);
+    if (a.n_seg < a.n)   // several time segments
+        return launch_kernel(k1_plain<FCAP, true>, a, n_units, smem_bytes, s);
+    return launch_kernel(k1_plain<FCAP, false>, a, n_units, smem_bytes, s);
 }
 
 cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
@@ -888,6 +974,26 @@ cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count
     if (count <= 0) return cudaSuccess;
     peak_out_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(best, idx, count, out_abs,
                                                                     out_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_segment_carry(const float4 *params, const float2 *state,
+                                 const float2 *seg_end, float2 *seg_init, int64_t n_slots, int D,
+                                 int P, int n_seg, cudaStream_t s)
+{
+    const int64_t count = (int64_t)D * n_slots;
+    if (count <= 0 || P < 2) return cudaSuccess;
+    segment_carry_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(
+        params, state, seg_end, seg_init, n_slots, D, P, n_seg);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_peak_merge(const float *seg_best, const int64_t *seg_idx, int P,
+                              int64_t count, float *best, int64_t *idx, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    peak_merge_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(seg_best, seg_idx, P,
+                                                                       count, best, idx);
     return cudaGetLastError();
 }
 

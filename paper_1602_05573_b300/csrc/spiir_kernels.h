@@ -56,6 +56,14 @@ struct K1Args {
     int32_t n_det;             // detectors (checkpoint row stride)
     int32_t mode;              // kModePlain / kModeCompensated / kModeChunked
     int32_t chunk;             // chunked: samples per chunk (divides Tb, multiple of 8)
+    // time segments (plain mode): the grid is n_units x P, CTA b serves unit
+    // b % n_units and segment b / n_units of n_seg samples
+    int32_t n_units;           // (group, detector) units per segment
+    int32_t n_seg;             // samples per segment (multiple of Tb; = n when P == 1)
+    int32_t zero_init;         // segments start from zero state (the projection pass)
+    const float2 *seg_init;    // [P][D][n_slots] start state of every segment (or null)
+    float2 *seg_end;           // [P][D][n_slots] end states of the projection pass (or null)
+    int64_t peak_seg_stride;   // peak arrays per segment (0: one shared array)
     void *state_ext;           // compensated: float4 [D][n_slots] (re hi, re lo, im hi, im lo);
                                // chunked: double2 [D][n_slots] FP64 anchor
     const double2 *aT;         // chunked: [n_slots] a^chunk in FP64 (kernel form)
@@ -109,6 +117,15 @@ cudaError_t ensure_smem_limit(const void *kernel, int smem_bytes);
 // Finalize running peaks into the caller's buffers (sqrt of |z|^2).
 cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count,
                             float *out_abs, int64_t *out_idx, cudaStream_t s);
+
+// Segment start states: for every (detector, slot), s_0 = state,
+// s_{p+1} = a^n_seg s_p + seg_end[p] (FP64), seg_init[p] = s_p, p < P.
+cudaError_t launch_segment_carry(const float4 *params, const float2 *state,
+                                 const float2 *seg_end, float2 *seg_init, int64_t n_slots, int D,
+                                 int P, int n_seg, cudaStream_t s);
+// Running peaks merged over segments in time order (earlier wins ties).
+cudaError_t launch_peak_merge(const float *seg_best, const int64_t *seg_idx, int P,
+                              int64_t count, float *best, int64_t *idx, cudaStream_t s);
 
 // *t0 += n (device-side sample counter of a plan).
 cudaError_t launch_advance(int64_t *t0, int64_t n, cudaStream_t s);

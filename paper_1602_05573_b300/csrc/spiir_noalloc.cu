@@ -189,6 +189,9 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const 
     a.group_pbase = pbase;
     a.warp_info = winfo;
     a.fcap = L.Fcap;
+    a.G = L.G;
+    a.n_units = (int32_t)L.n_units();
+    a.n_seg = (int32_t)n;
     a.params = params;
     a.ringoff = ringoff;
     a.state = state;

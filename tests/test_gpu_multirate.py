@@ -67,9 +67,9 @@ def test_multirate_streaming_matches_one_call_outside_hold(sp):
     with the hold rule) differ from one call."""
     bank = c3_bank(8)
     x = make_strain(1, 12000, seed=311)
-    z1, _, _ = gpu_mr(sp, bank, x)
+    z1, _, _ = gpu_mr(sp, bank, x, time_segments=1)
     chunks = [4096, 16, 3200]
-    z2, _, _ = gpu_mr(sp, bank, x, chunks=chunks)
+    z2, _, _ = gpu_mr(sp, bank, x, chunks=chunks, time_segments=1)
     mask = np.ones(x.shape[1], bool)
     for end in np.cumsum(chunks):
         mask[end - 16:end] = False

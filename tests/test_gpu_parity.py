@@ -118,11 +118,12 @@ def test_launch_options_agree_with_oracle(sp, W, C, Tb, Fcap):
 
 
 def test_streaming_calls_equal_one_call(sp):
-    """Consecutive calls continue the stream: bit-identical to one call."""
+    """Consecutive calls continue the stream: bit-identical to one call when
+    no call is split into time segments."""
     bank = make_bank(9, (20, 150), (0.99, 0.9995), 1200, seed=59, n_det=2)
     x = make_strain(2, 5000, seed=60)
-    z1, pa1, pi1, _ = run_gpu(sp, bank, x)
-    z2, pa2, pi2, _ = run_gpu(sp, bank, x, chunks=[1, 100, 3, 256, 1000, 7])
+    z1, pa1, pi1, _ = run_gpu(sp, bank, x, time_segments=1)
+    z2, pa2, pi2, _ = run_gpu(sp, bank, x, chunks=[1, 100, 3, 256, 1000, 7], time_segments=1)
     assert np.array_equal(z1, z2)
     assert np.array_equal(pa1, pa2) and np.array_equal(pi1, pi2)
     assert_parity(z2, pa2, pi2, oracle_z(bank, x))
