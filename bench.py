@@ -267,13 +267,6 @@ def run_ours(args, rank, world, local_rank):
     lib = sp.library()
     sh = stream.cuda_stream
     zp = z.data_ptr() if z is not None else None
-    # our kernels per step: K1 (+ decimation and K1 per lower band), the
-    # sample-counter advance and the peak copy; the adjoint: K1 with
-    # checkpoints, K6 and the gradient finalize
-    n_lower = (len(bank.decim) - 1) if bank.decim is not None else 0
-    launches_per_step = 3 + 2 * n_lower
-    if adjoint:
-        launches_per_step = 3
 
     def call():
         if adjoint:
@@ -392,6 +385,10 @@ def run_ours(args, rank, world, local_rank):
         return 0
 
     info = plan.info()
+    # our kernels per step, as the plan counted them for the last call (K1
+    # passes, decimation, segment carry/merge, counter advance; the adjoint:
+    # checkpointed K1, K6, finalize), plus the spiir_peak copy
+    launches_per_step = info["last_call_launches"] + (0 if adjoint else 1)
     clocks = clk.summary()
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2032.0
@@ -417,7 +414,8 @@ def run_ours(args, rank, world, local_rank):
                        plan={k: info[k] for k in ("warps_per_cta", "block_len", "ring_copies",
                                                   "history_len", "smem_bytes",
                                                   "max_filters_per_lane",
-                                                  "bank_conflict_ratio", "n_slots")}),
+                                                  "bank_conflict_ratio", "n_slots",
+                                                  "last_call_segments")}),
         "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                      "peak": peak_lane, "unit": "T FP32 lane-ops/s",
                      "frac": achieved / peak_lane, "traffic": None,

@@ -106,7 +106,7 @@ typedef struct spiir_options {
     int32_t time_segments;  /* plain precision: split each call into this many time */
                             /* segments run in parallel (a zero-state pass plus an  */
                             /* FP64 carry of the segment start states; segments are */
-                            /* >= 2 blocks long); 0 = auto: banks that fill < 1/8   */
+                            /* >= 1 block long);  0 = auto: banks that fill < 1/8   */
                             /* of the GPU's warps get up to 8 warps/SM worth (>= 4  */
                             /* segments, <= 64), others none; 1 = off.  Results of  */
                             /* different splits agree to rounding, not bit for bit  */
@@ -129,7 +129,11 @@ typedef struct spiir_plan_info {
     int32_t precision;
     double bank_conflict_ratio; /* mean shared-memory wavefronts per strain load  */
     int32_t lanes_per_template; /* 32, or 16 when two templates share a warp        */
-    int32_t reserved[3];
+    int32_t last_call_launches; /* kernels the last spiir_filter or                 */
+                                /* spiir_filter_backward call launched (not counting */
+                                /* the autotuner's first-call timing launches)       */
+    int32_t last_call_segments; /* time segments of the last spiir_filter call      */
+    int32_t reserved[1];
 } spiir_plan_info;
 
 typedef struct spiir_plan spiir_plan;

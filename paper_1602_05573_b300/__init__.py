@@ -68,7 +68,8 @@ class PlanInfo(ctypes.Structure):
                 ("history_len", ctypes.c_int32), ("smem_bytes", ctypes.c_int32),
                 ("max_filters_per_lane", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("bank_conflict_ratio", ctypes.c_double),
-                ("lanes_per_template", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("lanes_per_template", ctypes.c_int32), ("last_call_launches", ctypes.c_int32),
+                ("last_call_segments", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 _P = ctypes.c_void_p

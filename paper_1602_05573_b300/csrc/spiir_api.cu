@@ -186,6 +186,8 @@ struct spiir_plan {
     std::vector<float> a_host, b_host;
     std::vector<int32_t> d_host;
     std::string tune_report;
+    int32_t last_launches = 0;    // kernels the last filter/backward call launched
+    int32_t last_segments = 1;    // time segments of the last call's top band
 };
 
 namespace {
@@ -472,6 +474,18 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
             delete p;
             return fail(SPIIR_EUNSUPPORTED, err);
         }
+        // a band small enough for automatic time segments gets 256-sample
+        // blocks: shorter segments, more of them
+        const spiir::Layout &L0 = p->bands[j].lay;
+        if (opt.block_len == 0 && opt.precision == SPIIR_PREC_PLAIN && opt.time_segments == 0 &&
+            L0.n_units() * L0.W * 4 <= 8 * (int64_t)n_sm && L0.Tb != 256) {
+            spiir::LayoutOptions lo2 = lo;
+            lo2.Tb = 256;
+            spiir::Layout L2;
+            if (spiir::build_layout(lists, p->D, bank->a_reim, bank->b_reim, bank->delay, lo2,
+                                    &L2, &err))
+                p->bands[j].lay = std::move(L2);
+        }
     }
     if (p->bands.size() > 1 + spiir::kMaxLowerBands) {
         delete p;
@@ -576,6 +590,8 @@ spiir_status spiir_plan_get_info(const spiir_plan *p, spiir_plan_info *info)
         rounds += (double)L.n_slots;
     }
     info->bank_conflict_ratio = rounds > 0 ? wf / rounds : 1.0;
+    info->last_call_launches = p->last_launches;
+    info->last_call_segments = p->last_segments;
     return SPIIR_OK;
 }
 
@@ -620,7 +636,7 @@ spiir_status spiir_reset(spiir_plan *p, void *stream)
     return SPIIR_OK;
 }
 
-// Time segments for a band call of nb samples, each at least 2 blocks long.
+// Time segments for a band call of nb samples, each at least one block long.
 // Segmenting costs a second (zero-state) pass over all but the last segment,
 // so by default it is used only for banks that fill under 1/8 of the GPU's
 // warp slots (8 warps per SM as the target), and only when it gives at
@@ -638,7 +654,7 @@ int segments_for(const spiir_plan *p, const Band &b, int64_t nb)
         const int64_t want = std::min<int64_t>(64, target / std::max<int64_t>(warps, 1));
         if (want >= 4) P = (int)want;
     }
-    const int64_t max_p = std::max<int64_t>(1, nb / (2 * (int64_t)b.lay.Tb));
+    const int64_t max_p = std::max<int64_t>(1, nb / (int64_t)b.lay.Tb);
     P = (int)std::max<int64_t>(1, std::min<int64_t>(P, max_p));
     return (req < 1 && P < 4) ? 1 : P;
 }
@@ -648,7 +664,8 @@ int segments_for(const spiir_plan *p, const Band &b, int64_t nb)
 // turns those into the true start state of every segment, and the main pass
 // runs every segment from its start state; per-segment peaks are merged in
 // time order.
-spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cudaStream_t s)
+spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cudaStream_t s,
+                              int64_t *t0_advance = nullptr)
 {
     const spiir::Layout &L = b.lay;
     const int D = p->D;
@@ -657,9 +674,14 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
     const int64_t n_seg = ((n + P - 1) / P + L.Tb - 1) / L.Tb * L.Tb;
     P = (int)((n + n_seg - 1) / n_seg);
     cudaError_t e;
+    if (t0_advance != nullptr) p->last_segments = std::max(P, 1);
     if (P <= 1) {
         if ((e = spiir::launch_k1(a, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
             return cuda_fail(e, "filter kernel launch");
+        p->last_launches += 1;
+        if (t0_advance != nullptr && (e = spiir::launch_advance(t0_advance, n, s)) != cudaSuccess)
+            return cuda_fail(e, "sample counter launch");
+        p->last_launches += t0_advance != nullptr ? 1 : 0;
         return SPIIR_OK;
     }
     if (b.seg_cap < P) {
@@ -697,20 +719,22 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
     float *best = a.peak_best;
     int64_t *idx = a.peak_idx;
     a.seg_init = b.seg_init;
-    if (best != nullptr) {
+    if (best != nullptr) {   // every entry is written by the one CTA that owns it
         a.peak_best = b.seg_best;
         a.peak_idx = b.seg_idx;
         a.peak_seg_stride = (int64_t)D * p->T;
-        if ((e = spiir::launch_peak_reset(b.seg_best, b.seg_idx, (int64_t)P * D * p->T, s)) !=
-            cudaSuccess)
-            return cuda_fail(e, "segment peak reset");
     }
     if ((e = spiir::launch_k1(a, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
         return cuda_fail(e, "filter kernel launch");
-    if (best != nullptr &&
-        (e = spiir::launch_peak_merge(b.seg_best, b.seg_idx, P, (int64_t)D * p->T, best, idx,
-                                      s)) != cudaSuccess)
-        return cuda_fail(e, "segment peak merge");
+    p->last_launches += 3 + ((best != nullptr || t0_advance != nullptr) ? 1 : 0);
+    if (best != nullptr) {
+        if ((e = spiir::launch_peak_merge(b.seg_best, b.seg_idx, P, (int64_t)D * p->T, best, idx,
+                                          t0_advance, n, s)) != cudaSuccess)
+            return cuda_fail(e, "segment peak merge");
+    } else if (t0_advance != nullptr &&
+               (e = spiir::launch_advance(t0_advance, n, s)) != cudaSuccess) {
+        return cuda_fail(e, "sample counter launch");
+    }
     return SPIIR_OK;
 }
 
@@ -821,6 +845,7 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
     }
     const int D = p->D;
     cudaError_t e;
+    p->last_launches = 0;
     // decimated bands first (their sums feed the top band's epilogue), top band last
     std::vector<int> order;
     for (int j = 0; j < (int)p->bands.size(); ++j)
@@ -837,11 +862,13 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
         if ((e = cudaMemcpy2DAsync(b.xe, b.xe_stride * 4, b.hist, Dh * 4, Dh * 4, D,
                                    cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return cuda_fail(e, "strain staging copy");
-        if (b.R == 1)
+        if (b.R == 1) {
             e = cudaMemcpy2DAsync(b.xe + Dh, b.xe_stride * 4, x_dev, n * 4, n * 4, D,
                                   cudaMemcpyDeviceToDevice, s);
-        else
+        } else {
             e = spiir::launch_decimate(x_dev, n, D, b.R, nb, b.xe, b.xe_stride, Dh, s);
+            p->last_launches += 1;
+        }
         if (e != cudaSuccess) return cuda_fail(e, "strain staging");
         if (j != p->top) {
             if (!b.zb || b.zb_cap < nb) {
@@ -871,10 +898,8 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
             a.t0_dev = p->t0_dev;
             a.n_lower = top_args.n_lower;
             for (int i = 0; i < a.n_lower; ++i) a.lower[i] = top_args.lower[i];
-            st = launch_segmented(p, b, a, segments_for(p, b, n), s);
+            st = launch_segmented(p, b, a, segments_for(p, b, n), s, p->t0_dev);
             if (st != SPIIR_OK) return st;
-            if ((e = spiir::launch_advance(p->t0_dev, n, s)) != cudaSuccess)
-                return cuda_fail(e, "filter kernel launch");
         }
         // band history for the next call: the last Dh band samples of (history, x_b)
         if ((e = cudaMemcpy2DAsync(b.hist, Dh * 4, b.xe + nb, b.xe_stride * 4, Dh * 4, D,
@@ -1051,6 +1076,7 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
                                         reinterpret_cast<float2 *>(grad_b_dev), s)) !=
         cudaSuccess)
         return cuda_fail(e, "adjoint finalize launch");
+    p->last_launches = 3;   // checkpointed forward, reverse pass, finalize
     return SPIIR_OK;
 }
 

@@ -559,9 +559,11 @@ template <int F> struct ChunkLanes {
 };
 
 // ---- running peak of one template: warp max, then merge with the plan's --
+// overwrite: the CTA is the only writer of this (segment, detector, template)
+// entry, which then needs no reset before the launch.
 __device__ __forceinline__ void warp_peak_merge(const K1Args &A, float *peak_best,
                                                 int64_t *peak_idx, int det, int tmpl, int lane,
-                                                float best, int bidx)
+                                                float best, int bidx, bool overwrite)
 {
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
@@ -572,7 +574,11 @@ __device__ __forceinline__ void warp_peak_merge(const K1Args &A, float *peak_bes
             bidx = oi;
         }
     }
-    if (lane == 0 && bidx >= 0) {
+    if (lane == 0 && overwrite) {
+        const int64_t i = (int64_t)det * A.T + tmpl;
+        peak_best[i] = bidx >= 0 ? best : -1.0f;
+        peak_idx[i] = bidx >= 0 ? (A.t0_dev != nullptr ? *A.t0_dev : 0) + A.t0 + bidx : -1;
+    } else if (lane == 0 && bidx >= 0) {
         const int64_t i = (int64_t)det * A.T + tmpl;
         if (best > peak_best[i]) {
             peak_best[i] = best;
@@ -727,10 +733,12 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     }
     // running peak: largest |z|^2, earliest index on ties
     if (leader && A.peak_best != nullptr) {
-        float *peak_best = A.peak_best + (SEG ? seg * A.peak_seg_stride : 0);
-        int64_t *peak_idx = A.peak_idx + (SEG ? seg * A.peak_seg_stride : 0);
-        warp_peak_merge(A, peak_best, peak_idx, det, tmpl, lane, best, bidx);
-        if (tmpl2 >= 0) warp_peak_merge(A, peak_best, peak_idx, det, tmpl2, lane, best2, bidx2);
+        const bool own = SEG && A.peak_seg_stride != 0;   // per-segment entries
+        float *peak_best = A.peak_best + (own ? seg * A.peak_seg_stride : 0);
+        int64_t *peak_idx = A.peak_idx + (own ? seg * A.peak_seg_stride : 0);
+        warp_peak_merge(A, peak_best, peak_idx, det, tmpl, lane, best, bidx, own);
+        if (tmpl2 >= 0)
+            warp_peak_merge(A, peak_best, peak_idx, det, tmpl2, lane, best2, bidx2, own);
     }
 }
 
@@ -847,7 +855,7 @@ __global__ void segment_carry_kernel(const float4 *params, const float2 *state,
     seg_init[i] = y0;
     double yr = y0.x, yi = y0.y;
     for (int q = 0; q + 1 < P; ++q) {
-        const float2 e = seg_end[(int64_t)q * D * n_slots + i];
+        const float2 e = __ldg(&seg_end[(int64_t)q * D * n_slots + i]);
         const double nr = rr * yr - ri * yi + (double)e.x;
         const double ni = rr * yi + ri * yr + (double)e.y;
         yr = nr;
@@ -857,9 +865,11 @@ __global__ void segment_carry_kernel(const float4 *params, const float2 *state,
 }
 
 __global__ void peak_merge_kernel(const float *seg_best, const int64_t *seg_idx, int P,
-                                  int64_t count, float *best, int64_t *idx)
+                                  int64_t count, float *best, int64_t *idx, int64_t *t0,
+                                  int64_t advance)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && t0 != nullptr) *t0 += advance;   // nothing here reads the counter
     if (i >= count) return;
     float b = best[i];
     int64_t k = idx[i];
@@ -983,17 +993,19 @@ cudaError_t launch_segment_carry(const float4 *params, const float2 *state,
 {
     const int64_t count = (int64_t)D * n_slots;
     if (count <= 0 || P < 2) return cudaSuccess;
-    segment_carry_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(
+    // FP64 is a narrow pipe: 32-thread blocks spread the work over the SMs
+    segment_carry_kernel<<<(unsigned)((count + 31) / 32), 32, 0, s>>>(
         params, state, seg_end, seg_init, n_slots, D, P, n_seg);
     return cudaGetLastError();
 }
 
 cudaError_t launch_peak_merge(const float *seg_best, const int64_t *seg_idx, int P,
-                              int64_t count, float *best, int64_t *idx, cudaStream_t s)
+                              int64_t count, float *best, int64_t *idx, int64_t *t0,
+                              int64_t advance, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
-    peak_merge_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(seg_best, seg_idx, P,
-                                                                       count, best, idx);
+    peak_merge_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(
+        seg_best, seg_idx, P, count, best, idx, t0, advance);
     return cudaGetLastError();
 }
 

@@ -63,7 +63,8 @@ struct K1Args {
     int32_t zero_init;         // segments start from zero state (the projection pass)
     const float2 *seg_init;    // [P][D][n_slots] start state of every segment (or null)
     float2 *seg_end;           // [P][D][n_slots] end states of the projection pass (or null)
-    int64_t peak_seg_stride;   // peak arrays per segment (0: one shared array)
+    int64_t peak_seg_stride;   // per-segment peak entries, overwritten by their one
+                               // writer (0: merge into one shared array)
     void *state_ext;           // compensated: float4 [D][n_slots] (re hi, re lo, im hi, im lo);
                                // chunked: double2 [D][n_slots] FP64 anchor
     const double2 *aT;         // chunked: [n_slots] a^chunk in FP64 (kernel form)
@@ -123,9 +124,11 @@ cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count
 cudaError_t launch_segment_carry(const float4 *params, const float2 *state,
                                  const float2 *seg_end, float2 *seg_init, int64_t n_slots, int D,
                                  int P, int n_seg, cudaStream_t s);
-// Running peaks merged over segments in time order (earlier wins ties).
+// Running peaks merged over segments in time order (earlier wins ties); with
+// t0 non-null the same launch advances the plan's sample counter by advance.
 cudaError_t launch_peak_merge(const float *seg_best, const int64_t *seg_idx, int P,
-                              int64_t count, float *best, int64_t *idx, cudaStream_t s);
+                              int64_t count, float *best, int64_t *idx, int64_t *t0,
+                              int64_t advance, cudaStream_t s);
 
 // *t0 += n (device-side sample counter of a plan).
 cudaError_t launch_advance(int64_t *t0, int64_t n, cudaStream_t s);

@@ -76,7 +76,7 @@ def test_segments_in_half_warp_mode(sp):
 
 
 def test_segment_count_is_clamped_by_call_length(sp):
-    """More segments than 2-block pieces of the call: fewer segments run,
+    """More segments than 1-block pieces of the call: fewer segments run,
     and a call shorter than that runs unsegmented."""
     bank = make_bank(3, 40, (0.99, 0.999), 100, seed=407)
     for n in [300, 1100]:
