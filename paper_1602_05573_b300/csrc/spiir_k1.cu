@@ -83,6 +83,14 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+__device__ __forceinline__ float lds_f32(uint32_t a)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
 {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -235,7 +243,10 @@ __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb,
 // ---- arithmetic policies: one lane's F filters --------------------------
 // Each policy keeps its filters' coefficients and state in registers and
 // advances them 8 samples at a time, returning this lane's per-sample sums.
-// ring[base[r] + t] is the strain sample filter r reads at sample t.
+// ad[r] is the shared-memory byte address of the strain sample filter r
+// reads at the step's first sample; sample t of the step is at ad[r] + 4 t.
+// step8 runs FULL = true for 8 whole samples, false for a ragged tail of
+// `valid` samples (the state stays put past the tail).
 
 // Plain FP32: two filters per packed FP32x2 instruction (8 packed ops per
 // filter pair and sample), an odd filter in scalar FP32.
@@ -284,12 +295,13 @@ template <int F> struct PackedLanes {
         upk(YI[r / 2], ilo, ihi);
         return (r & 1) ? make_float2(hi, ihi) : make_float2(lo, ilo);
     }
-    __device__ __forceinline__ void step8(const float *ring, const int (&base)[F], int valid,
-                                          float (&zr)[kTS], float (&zi)[kTS])
+    template <bool FULL>
+    __device__ __forceinline__ void step8(const uint32_t (&ad)[F], int valid, float (&zr)[kTS],
+                                          float (&zi)[kTS])
     {
 #pragma unroll
         for (int t = 0; t < kTS; ++t) {
-            if (valid < kTS && t >= valid) {  // ragged tail: state stays put
+            if (!FULL && t >= valid) {  // ragged tail: state stays put
                 zr[t] = 0.f;
                 zi[t] = 0.f;
                 continue;
@@ -297,9 +309,7 @@ template <int F> struct PackedLanes {
             uint64_t ZR = 0, ZI = 0;
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
-                const float xf = ring[base[2 * q] + t];
-                const float xg = ring[base[2 * q + 1] + t];
-                const uint64_t X = pk(xf, xg);
+                const uint64_t X = pk(lds_f32(ad[2 * q] + 4u * t), lds_f32(ad[2 * q + 1] + 4u * t));
                 uint64_t TR = mul2(BR[q], X);
                 uint64_t TI = mul2(BI[q], X);
                 TR = fma2(NAI[q], YI[q], TR);   // br x - ai yi
@@ -323,7 +333,7 @@ template <int F> struct PackedLanes {
                 si = lo + hi;
             }
             if (ODD) {
-                const float x1 = ring[base[F - 1] + t];
+                const float x1 = lds_f32(ad[F - 1] + 4u * t);
                 const float nr = fmaf(ar1, yr1, fmaf(-ai1, yi1, br1 * x1));
                 const float ni = fmaf(ar1, yi1, fmaf(ai1, yr1, bi1 * x1));
                 yr1 = nr;
@@ -392,12 +402,13 @@ template <int F> struct CompLanes {
             yil[r] = y.w;
         }
     }
-    __device__ __forceinline__ void step8(const float *ring, const int (&base)[F], int valid,
-                                          float (&zr)[kTS], float (&zi)[kTS])
+    template <bool FULL>
+    __device__ __forceinline__ void step8(const uint32_t (&ad)[F], int valid, float (&zr)[kTS],
+                                          float (&zi)[kTS])
     {
 #pragma unroll
         for (int t = 0; t < kTS; ++t) {
-            if (valid < kTS && t >= valid) {
+            if (!FULL && t >= valid) {
                 zr[t] = 0.f;
                 zi[t] = 0.f;
                 continue;
@@ -405,7 +416,7 @@ template <int F> struct CompLanes {
             float sr = 0.f, si = 0.f;
 #pragma unroll
             for (int r = 0; r < F; ++r) {
-                const float x = ring[base[r] + t];
+                const float x = lds_f32(ad[r] + 4u * t);
                 float p1, e1, p2, e2, p3, e3, s1, t1, s2, t2;
                 // Re: ar yr - ai yi + br x
                 two_prod(ar[r], yrh[r], p1, e1);
@@ -486,12 +497,13 @@ template <int F> struct ChunkLanes {
             aTi[r] = t.y;
         }
     }
-    __device__ __forceinline__ void step8(const float *ring, const int (&base)[F], int valid,
-                                          float (&zr)[kTS], float (&zi)[kTS])
+    template <bool FULL>
+    __device__ __forceinline__ void step8(const uint32_t (&ad)[F], int valid, float (&zr)[kTS],
+                                          float (&zi)[kTS])
     {
 #pragma unroll
         for (int t = 0; t < kTS; ++t) {
-            if (valid < kTS && t >= valid) {
+            if (!FULL && t >= valid) {
                 zr[t] = 0.f;
                 zi[t] = 0.f;
                 continue;
@@ -499,7 +511,7 @@ template <int F> struct ChunkLanes {
             float sr = 0.f, si = 0.f;
 #pragma unroll
             for (int r = 0; r < F; ++r) {
-                const float x = ring[base[r] + t];
+                const float x = lds_f32(ad[r] + 4u * t);
                 const float bx = br[r] * x, by = bi[r] * x;
                 const float nr = fmaf(ar[r], yr[r], fmaf(-ai[r], yi[r], bx));
                 const float ni = fmaf(ar[r], yi[r], fmaf(ai[r], yr[r], by));
@@ -612,18 +624,18 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     const float *xrow = A.xe + (int64_t)det * A.xe_stride + (int64_t)sblk * A.Tb;
 
     LANES<F> L;
-    int pos[F], cb[F];
+    // per filter: shared byte address of its strain window (ring copy base +
+    // ring position), advanced 32 bytes per 8-sample step and wrapped per block
+    const uint32_t ring_u32 = smem_addr(ring);
+    uint32_t ad[F];
 #pragma unroll
-    for (int r = 0; r < F; ++r) {
-        pos[r] = 0;
-        cb[r] = 0;
-    }
+    for (int r = 0; r < F; ++r) ad[r] = ring_u32;
     if (active) {
 #pragma unroll
         for (int r = 0; r < F; ++r) {
+            // xrow starts at the segment: the same ring phase as a whole call
             const int2 ro = A.ringoff[pb + ((int64_t)r * A.W + warp) * 32 + lane];
-            pos[r] = ro.x;   // xrow starts at the segment: same ring phase
-            cb[r] = ro.y;
+            ad[r] = ring_u32 + 4u * (uint32_t)(ro.y + ro.x);
         }
         // segments read their start state from seg_init (segment 0's is a copy
         // of the call's start state: the last segment overwrites A.state)
@@ -666,23 +678,28 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
         // this block's sums: [W * per_warp template slots][Tb] complex
         float *zb = zbuf + (int64_t)((j & 1) * A.W * per_warp) * A.Tb * 2;
         if (active) {
-            int base[F];
-#pragma unroll
-            for (int r = 0; r < F; ++r) base[r] = cb[r] + pos[r];
             float *zw = zb + (int64_t)warp * per_warp * A.Tb * 2;
             for (int sb = 0; sb < nv; sb += kTS) {
                 const int valid = nv - sb;
                 float zr[kTS], zi[kTS];
-                L.step8(ring, base, valid, zr, zi);
+                if (valid >= kTS)
+                    L.template step8<true>(ad, valid, zr, zi);
+                else
+                    L.template step8<false>(ad, valid, zr, zi);
                 warp_sum8(zr, zi, lane, zw + 2 * sb, half, A.Tb);
                 L.after8(A, j * A.Tb + sb + min(valid, kTS));
 #pragma unroll
-                for (int r = 0; r < F; ++r) base[r] += kTS;
+                for (int r = 0; r < F; ++r) ad[r] += 4u * kTS;
             }
+            // a whole block moved every window by Tb samples: wrap those that
+            // left the ring (position within its copy >= R)
+            const uint32_t cs4 = 4u * (uint32_t)A.CS, r4 = 4u * (uint32_t)A.R;
 #pragma unroll
             for (int r = 0; r < F; ++r) {
-                pos[r] += A.Tb;
-                if (pos[r] >= A.R) pos[r] -= A.R;
+                const uint32_t off = ad[r] - ring_u32;
+                uint32_t c = 0;
+                for (int cc = 1; cc < A.C; ++cc) c += off >= (uint32_t)cc * cs4 ? 1u : 0u;
+                if (off - c * cs4 >= r4) ad[r] -= r4;
             }
             // checkpoint of the filter state (for the adjoint's recompute)
             if (A.ckpt != nullptr && (j + 1) % A.ckpt_blocks == 0 && j + 1 < nblk) {
