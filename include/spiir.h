@@ -57,6 +57,13 @@ typedef enum spiir_precision {
     SPIIR_PREC_CHUNKED_TC = 3   /* chunked scan, split-BF16 tensor-core projection */
 } spiir_precision;
 
+/* Segment start states of time-segmented calls (spiir_options.projection). */
+typedef enum spiir_projection {
+    SPIIR_PROJECT_AUTO = 0,
+    SPIIR_PROJECT_RECURRENCE = 1,
+    SPIIR_PROJECT_TENSOR = 2
+} spiir_projection;
+
 /*
  * A template bank in CSR form.  Template t owns filters
  * filter_off[t] .. filter_off[t+1]-1.  All arrays are host memory, read only
@@ -110,7 +117,12 @@ typedef struct spiir_options {
                             /* of the GPU's warps get up to 8 warps/SM worth (>= 4  */
                             /* segments, <= 64), others none; 1 = off.  Results of  */
                             /* different splits agree to rounding, not bit for bit  */
-    int32_t reserved[2];
+    int32_t projection;     /* how segmented calls get their segment start states: */
+                            /* SPIIR_PROJECT_AUTO (= TENSOR), _RECURRENCE (a zero-  */
+                            /* state FP32 pass over all but the last segment, FP64 */
+                            /* carry) or _TENSOR (chunk sums by split-BF16 tcgen05 */
+                            /* GEMM, FP32 chunk scan)                              */
+    int32_t reserved[1];
 } spiir_options;
 
 /* Plan statistics (spiir_plan_get_info). */

@@ -32,6 +32,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 PRECISIONS = {"plain": 0, "compensated": 1, "chunked_fp64": 2, "chunked_tc": 3}
+PROJECTIONS = {"auto": 0, "recurrence": 1, "tensor": 2}
 
 # exported symbols (include/spiir.h)
 SYMBOLS = [
@@ -57,7 +58,7 @@ class Options(ctypes.Structure):
                 ("ring_copies", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("max_filters_per_lane", ctypes.c_int32),
                 ("lanes_per_template", ctypes.c_int32), ("time_segments", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("projection", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -218,7 +219,7 @@ class Plan:
                  block_len: int = 0, warps_per_cta: int = 0, ring_copies: int = 0,
                  chunk_len: int = 256, autotune: bool = False,
                  max_filters_per_lane: int = 0, lanes_per_template: int = 0,
-                 time_segments: int = 0, lib=None):
+                 time_segments: int = 0, projection: str = "auto", lib=None):
         self._h = None
         self._lib = lib if lib is not None else _lib
         off = np.ascontiguousarray(bank.off, np.int64)
@@ -251,6 +252,7 @@ class Plan:
         opt.max_filters_per_lane = int(max_filters_per_lane)
         opt.lanes_per_template = int(lanes_per_template)
         opt.time_segments = int(time_segments)
+        opt.projection = PROJECTIONS[projection]
         h = _P()
         _check(self._lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
                "spiir_plan_create", self._lib)

@@ -156,6 +156,11 @@ struct Band {
     float *seg_best = nullptr;     //                [P][D][T] per-segment peaks
     int64_t *seg_idx = nullptr;
     int seg_cap = 0;               // segments the workspaces hold
+    unsigned char *tc_w = nullptr; // tensor-core projection: weight tiles (split BF16)
+    float2 *tc_aT = nullptr;       //   a^256 per slot
+    bool tc_valid = false;         //   weights match the current coefficients
+    unsigned char *tc_b = nullptr; //   strain-window tiles of a call
+    int64_t tc_b_cap = 0;          //   bytes
     int4 *adj_tasks = nullptr;     // adjoint work list (built on the first backward call)
     int32_t *adj_units = nullptr;
     int64_t adj_n_units = 0;
@@ -215,6 +220,9 @@ void free_band(Band &b)
     cudaFree(b.seg_init);
     cudaFree(b.seg_best);
     cudaFree(b.seg_idx);
+    cudaFree(b.tc_w);
+    cudaFree(b.tc_aT);
+    cudaFree(b.tc_b);
     cudaFree(b.adj_tasks);
     cudaFree(b.adj_units);
     cudaFree(b.adj_sub);
@@ -409,6 +417,8 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     if (opt.precision < SPIIR_PREC_PLAIN || opt.precision > SPIIR_PREC_CHUNKED_TC)
         return fail(SPIIR_EINVAL, "unknown precision mode");
     if (opt.chunk_len == 0) opt.chunk_len = 256;
+    if (opt.projection < SPIIR_PROJECT_AUTO || opt.projection > SPIIR_PROJECT_TENSOR)
+        return fail(SPIIR_EINVAL, "projection must be 0 (auto), 1 (recurrence) or 2 (tensor)");
     if (opt.block_len != 0 && (opt.block_len < 32 || opt.block_len % 32 != 0))
         return fail(SPIIR_EINVAL, "block_len must be 0 or a multiple of 32");
 
@@ -664,6 +674,14 @@ int segments_for(const spiir_plan *p, const Band &b, int64_t nb)
 // turns those into the true start state of every segment, and the main pass
 // runs every segment from its start state; per-segment peaks are merged in
 // time order.
+// Dynamic shared memory of a K1 launch: the layout's ring and block sums,
+// plus the lower-band prefetch buffers of a multirate top band.
+int k1_smem(const Band &b, const spiir::K1Args &a)
+{
+    return b.lay.smem_bytes() +
+           (a.n_lower > 0 ? b.lay.W * (32 / b.lay.G) * a.low_len * (int)sizeof(float2) : 0);
+}
+
 spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cudaStream_t s,
                               int64_t *t0_advance = nullptr)
 {
@@ -671,12 +689,18 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
     const int D = p->D;
     const int64_t per = (int64_t)D * L.n_slots;
     const int64_t n = a.n;
-    const int64_t n_seg = ((n + P - 1) / P + L.Tb - 1) / L.Tb * L.Tb;
+    // segment starts on block boundaries, and on chunk boundaries for the
+    // tensor-core projection
+    const bool tc = p->opt.projection != SPIIR_PROJECT_RECURRENCE;
+    int64_t unit = L.Tb;
+    if (tc)
+        while (unit % spiir::kTcT != 0) unit += L.Tb;
+    const int64_t n_seg = ((n + P - 1) / P + unit - 1) / unit * unit;
     P = (int)((n + n_seg - 1) / n_seg);
     cudaError_t e;
     if (t0_advance != nullptr) p->last_segments = std::max(P, 1);
     if (P <= 1) {
-        if ((e = spiir::launch_k1(a, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
+        if ((e = spiir::launch_k1(a, L.n_units(), k1_smem(b, a), s)) != cudaSuccess)
             return cuda_fail(e, "filter kernel launch");
         p->last_launches += 1;
         if (t0_advance != nullptr && (e = spiir::launch_advance(t0_advance, n, s)) != cudaSuccess)
@@ -703,18 +727,71 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         b.seg_cap = P;
     }
     a.n_seg = (int32_t)n_seg;
-    // projection: segments 0..P-2 from zero state, no z, no peak
-    spiir::K1Args proj = a;
-    proj.zero_init = 1;
-    proj.seg_end = b.seg_end;
-    proj.z = nullptr;
-    proj.peak_best = nullptr;
-    proj.peak_idx = nullptr;
-    proj.n_lower = 0;
-    if ((e = spiir::launch_k1(proj, L.n_units(), L.smem_bytes(), s)) != cudaSuccess ||
-        (e = spiir::launch_segment_carry(b.params, b.state, b.seg_end, b.seg_init, L.n_slots, D,
-                                         P, (int)n_seg, s)) != cudaSuccess)
-        return cuda_fail(e, "segment projection launch");
+    if (tc) {
+        // segment start states from the split-BF16 GEMM of chunk sums + scan
+        if (!b.tc_valid) {
+            if (!b.tc_w) {
+                if ((e = cudaMalloc(&b.tc_w, (size_t)spiir::tc_weight_bytes(L.n_slots))) !=
+                        cudaSuccess ||
+                    (e = dalloc(&b.tc_aT, (size_t)L.n_slots)) != cudaSuccess)
+                    return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "projection weights")
+                                                          : cuda_fail(e, "cudaMalloc");
+            }
+            if ((e = spiir::launch_tc_weights(b.params, b.ringoff, L.n_slots, (int)L.Dh, b.tc_w,
+                                              b.tc_aT, s)) != cudaSuccess)
+                return cuda_fail(e, "projection weights launch");
+            b.tc_valid = true;
+            p->last_launches += 1;
+        }
+        const int64_t cps = n_seg / spiir::kTcT;
+        const int64_t c_last = (int64_t)(P - 1) * cps - 1;
+        const int64_t hq = L.Dh / spiir::kTcT;
+        const int64_t n_cols = c_last + hq + 1;
+        const int64_t need = spiir::tc_strain_bytes(n_cols, D);
+        if (b.tc_b_cap < need) {
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(b.tc_b);
+            b.tc_b = nullptr;
+            if ((e = cudaMalloc(&b.tc_b, (size_t)need)) != cudaSuccess)
+                return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "projection workspace")
+                                                      : cuda_fail(e, "cudaMalloc");
+            b.tc_b_cap = need;
+        }
+        spiir::TcArgs t{};
+        t.W = b.tc_w;
+        t.B = b.tc_b;
+        t.ringoff = b.ringoff;
+        t.aT = b.tc_aT;
+        t.state = b.state;
+        t.seg_init = b.seg_init;
+        t.n_slots = L.n_slots;
+        t.D = D;
+        t.Dh = (int32_t)L.Dh;
+        t.n_ntiles = (int32_t)((n_cols + 127) / 128);
+        t.col0 = (int32_t)(-hq - 1);
+        t.c_last = (int32_t)c_last;
+        t.cps = (int32_t)cps;
+        t.err = p->err;
+        t.wait_limit_ns = a.wait_limit_ns;
+        if ((e = spiir::launch_tc_strain(b.xe, b.xe_stride, (int)L.Dh, n, D, n_cols, t.col0,
+                                         b.tc_b, s)) != cudaSuccess ||
+            (e = spiir::launch_tc_project(t, s)) != cudaSuccess)
+            return cuda_fail(e, "tensor-core projection launch");
+    } else {
+        // projection: segments 0..P-2 from zero state, no z, no peak
+        spiir::K1Args proj = a;
+        proj.zero_init = 1;
+        proj.seg_end = b.seg_end;
+        proj.z = nullptr;
+        proj.peak_best = nullptr;
+        proj.peak_idx = nullptr;
+        proj.n_lower = 0;
+        if ((e = spiir::launch_k1(proj, L.n_units(), L.smem_bytes(), s)) != cudaSuccess ||
+            (e = spiir::launch_segment_carry(b.params, b.state, b.seg_end, b.seg_init, L.n_slots,
+                                             D, P, (int)n_seg, s)) != cudaSuccess)
+            return cuda_fail(e, "segment projection launch");
+    }
     // main pass: every segment from its start state
     float *best = a.peak_best;
     int64_t *idx = a.peak_idx;
@@ -724,7 +801,7 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         a.peak_idx = b.seg_idx;
         a.peak_seg_stride = (int64_t)D * p->T;
     }
-    if ((e = spiir::launch_k1(a, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
+    if ((e = spiir::launch_k1(a, L.n_units(), k1_smem(b, a), s)) != cudaSuccess)
         return cuda_fail(e, "filter kernel launch");
     p->last_launches += 3 + ((best != nullptr || t0_advance != nullptr) ? 1 : 0);
     if (best != nullptr) {
@@ -892,12 +969,22 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
             lb.z = b.zb;
             lb.len = nb;
             lb.R = b.R;
+            lb.shift = -1;
+            for (int sh = 0; sh < 31; ++sh)
+                if ((1 << sh) == b.R) lb.shift = sh;
         } else {
             spiir::K1Args a = k1_args(p, b, n, z_dev, n, true);
             a.t0 = 0;
             a.t0_dev = p->t0_dev;
             a.n_lower = top_args.n_lower;
-            for (int i = 0; i < a.n_lower; ++i) a.lower[i] = top_args.lower[i];
+            // per template: the band samples one block interpolates from
+            int32_t off = 0;
+            for (int i = 0; i < a.n_lower; ++i) {
+                a.lower[i] = top_args.lower[i];
+                a.lower[i].buf_off = off;
+                off += (int32_t)((b.lay.Tb + a.lower[i].R - 1) / a.lower[i].R + 2);
+            }
+            a.low_len = (off + 1) / 2 * 2;
             st = launch_segmented(p, b, a, segments_for(p, b, n), s, p->t0_dev);
             if (st != SPIIR_OK) return st;
         }
@@ -1093,6 +1180,7 @@ spiir_status spiir_set_coefficients(spiir_plan *p, const float *a_reim_dev,
             reinterpret_cast<const float2 *>(b_reim_dev), b.slot_filter, b.lay.n_slots, b.params,
             (cudaStream_t)stream);
         if (e != cudaSuccess) return cuda_fail(e, "coefficient update launch");
+        b.tc_valid = false;   // projection weights are rebuilt on the next segmented call
     }
     return SPIIR_OK;
 }
@@ -1219,7 +1307,7 @@ spiir_status spiir_check(spiir_plan *p, void *stream)
     int32_t word = 0;
     e = cudaMemcpy(&word, p->err, sizeof(word), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "error word copy");
-    if (word & 3) return fail(SPIIR_ETIMEOUT, "a bounded device wait gave up (error word " +
+    if (word & (1 | 2 | 8)) return fail(SPIIR_ETIMEOUT, "a bounded device wait gave up (error word " +
                                                   std::to_string(word) + ")");
     if (word) return fail(SPIIR_ECUDA, "device error word " + std::to_string(word));
     return SPIIR_OK;

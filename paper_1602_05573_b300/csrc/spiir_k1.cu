@@ -35,6 +35,7 @@
 //    which would make the peak's argmax depend on timing).
 #include "spiir_kernels.h"
 #include "spiir_layout.h"
+#include "spiir_ptx.h"
 
 #include <algorithm>
 #include <cstdint>
@@ -78,66 +79,6 @@ __device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b)
     return d;
 }
 
-// ---- mbarrier + TMA bulk copy --------------------------------------------
-__device__ __forceinline__ uint32_t smem_addr(const void *p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ float lds_f32(uint32_t a)
-{
-    float v;
-    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
-    return v;
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
-                                         uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, "
-        "[%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ uint64_t global_ns()
-{
-    uint64_t t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-// Wait for the phase with the given parity; give up after limit_ns.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const uint64_t start = global_ns();
-    while (!mbar_try_wait(bar, parity)) {
-        if (global_ns() - start > limit_ns) return false;
-    }
-    return true;
-}
 
 // Bytes one strain block brings into the ring (every copy, plus the mirror
 // of slot 0 placed after the ring so windows never wrap).
@@ -207,11 +148,42 @@ __device__ __forceinline__ void warp_sum8(const float (&zr)[kTS], const float (&
 // Multirate banks: each lower band's sum is brought to this (top) rate by
 // linear interpolation between band samples i = k / R and i + 1 (held at the
 // call's last band sample), z_up = (1 - f) z_b[i] + f z_b[i + 1], f = (k mod R)/R,
-// and added before the store and the peak.
+// and added before the store and the peak.  The band samples a block needs
+// were prefetched into `low` (this template's buffer) when the block began.
+__device__ __forceinline__ int band_index(const LowerBand &lb, int k)
+{
+    return lb.shift >= 0 ? (k >> lb.shift) : k / lb.R;
+}
+
+// Asynchronous copies (no register round trip) of the band samples block
+// [k0, k0 + nv) interpolates from, into this template's prefetch buffer.
+__device__ __forceinline__ void prefetch_lower(const K1Args &A, float2 *low, int det, int tmpl,
+                                               int lane, int k0, int nv)
+{
+    for (int b = 0; b < A.n_lower; ++b) {
+        const LowerBand &lb = A.lower[b];
+        const int lo = band_index(lb, k0);
+        const int hi = min(band_index(lb, k0 + nv - 1) + 1, (int)lb.len - 1);
+        const float2 *row = lb.z + ((int64_t)det * A.T + tmpl) * lb.len;
+        for (int e = lane; e <= hi - lo; e += 32)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                             smem_addr(low + lb.buf_off + e)),
+                         "l"(row + lo + e)
+                         : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+template <bool LOW>
 __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb, int first,
-                                              int nw, int det, int tmpl, int lane, int k0,
+                                              int nw, const float2 *low, int lane, int k0,
                                               int nv, float *zrow, float &best, int &bidx)
 {
+    const int n_lower = LOW ? A.n_lower : 0;
+    if (n_lower > 0) {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+    }
     for (int i = lane; i < nv; i += 32) {
         float2 acc = zb[(int64_t)first * A.Tb + i];
         for (int w = 1; w < nw; ++w) {
@@ -219,14 +191,15 @@ __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb,
             acc.x += o.x;
             acc.y += o.y;
         }
-        for (int b = 0; b < A.n_lower; ++b) {
+        for (int b = 0; b < n_lower; ++b) {
             const LowerBand &lb = A.lower[b];
             const int k = k0 + i;
-            const int64_t ib = k / lb.R;
-            const int64_t ib1 = ib + 1 < lb.len ? ib + 1 : lb.len - 1;
-            const float f = (float)(k % lb.R) / (float)lb.R;
-            const float2 *row = lb.z + ((int64_t)det * A.T + tmpl) * lb.len;
-            const float2 u = row[ib], v = row[ib1];
+            const int lo = band_index(lb, k0);
+            const int ib = band_index(lb, k);
+            const int ib1 = ib + 1 < lb.len ? ib + 1 : (int)lb.len - 1;
+            const int rem = lb.shift >= 0 ? (k & (lb.R - 1)) : k % lb.R;
+            const float f = (float)rem / (float)lb.R;
+            const float2 u = low[lb.buf_off + ib - lo], v = low[lb.buf_off + ib1 - lo];
             acc.x += fmaf(f, v.x, (1.0f - f) * u.x);
             acc.y += fmaf(f, v.y, (1.0f - f) * u.y);
         }
@@ -600,7 +573,10 @@ __device__ __forceinline__ void warp_peak_merge(const K1Args &A, float *peak_bes
 }
 
 // ---- one CTA work unit: W warps x one detector, whole call ----------------
-template <template <int> class LANES, int F, bool SEG>
+// SEG: the CTA serves one time segment of the call; LOW: the call adds lower
+// bands (multirate top band).  Both are compile-time so the plain single-band
+// kernel carries neither's code.
+template <template <int> class LANES, int F, bool SEG, bool LOW>
 __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float *ring,
                                          float *zbuf, uint32_t bar0, uint32_t bar1)
 {
@@ -610,6 +586,8 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     const bool half = A.G == 16;
     const int tmpl2 = half ? wi.w : -1;      // half-warp mode: template of lanes 16..31
     const int per_warp = half ? 2 : 1;       // template slots per warp
+    // lower-band prefetch buffers follow the two block-sum buffers
+    float2 *lowbuf = reinterpret_cast<float2 *>(zbuf + (int64_t)2 * A.W * per_warp * A.Tb * 2);
     const bool active = tmpl >= 0;
     const bool leader = active && wi.y == warp;
     const int64_t pb = A.group_pbase[g];
@@ -677,6 +655,13 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
         const int nv = min(A.Tb, n - j * A.Tb);
         // this block's sums: [W * per_warp template slots][Tb] complex
         float *zb = zbuf + (int64_t)((j & 1) * A.W * per_warp) * A.Tb * 2;
+        if (LOW && leader && A.n_lower > 0) {   // lower-band samples for this block's combine
+            prefetch_lower(A, lowbuf + (int64_t)(wi.y * per_warp) * A.low_len, det, tmpl, lane,
+                           k0, nv);
+            if (tmpl2 >= 0)
+                prefetch_lower(A, lowbuf + (int64_t)(warp * 2 + 1) * A.low_len, det, tmpl2,
+                               lane, k0, nv);
+        }
         if (active) {
             float *zw = zb + (int64_t)warp * per_warp * A.Tb * 2;
             for (int sb = 0; sb < nv; sb += kTS) {
@@ -719,11 +704,13 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             issue_block(A, xrow, ring, e, bar);
         }
         if (leader) {
-            combine_block(A, reinterpret_cast<const float2 *>(zb), wi.y * per_warp, wi.z, det,
-                          tmpl, lane, k0, nv, zrow, best, bidx);
+            combine_block<LOW>(A, reinterpret_cast<const float2 *>(zb), wi.y * per_warp, wi.z,
+                          lowbuf + (int64_t)(wi.y * per_warp) * A.low_len, lane, k0, nv, zrow,
+                          best, bidx);
             if (tmpl2 >= 0)
-                combine_block(A, reinterpret_cast<const float2 *>(zb), warp * 2 + 1, 1, det,
-                              tmpl2, lane, k0, nv, zrow2, best2, bidx2);
+                combine_block<LOW>(A, reinterpret_cast<const float2 *>(zb), warp * 2 + 1, 1,
+                              lowbuf + (int64_t)(warp * 2 + 1) * A.low_len, lane, k0, nv, zrow2,
+                              best2, bidx2);
         }
     }
     if (failed_at >= 0) {
@@ -770,21 +757,21 @@ template <> struct K1Bounds<8> { static constexpr int kMinBlocks = 2; };
 template <> struct K1Bounds<10> { static constexpr int kMinBlocks = 2; };
 
 // The CTA's F is uniform, so every warp takes the same case.
-template <template <int> class LANES, int FCAP, bool SEG = false>
+template <template <int> class LANES, int FCAP, bool SEG, bool LOW>
 __device__ __forceinline__ void dispatch_f(const K1Args &A, int g, int det, float *ring,
                                            float *zbuf, uint32_t bar0, uint32_t bar1)
 {
     const int F = A.group_F[g];
-    if (F == 1) run_unit<LANES, 1, SEG>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1), SEG>(A, g, det, ring, zbuf, bar0, bar1);
+    if (F == 1) run_unit<LANES, 1, SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
     else if (threadIdx.x == 0) atomicOr(A.err, 4);
 }
 
@@ -804,7 +791,7 @@ __device__ __forceinline__ void cta_setup(unsigned char *smem, const K1Args &A, 
     __syncthreads();
 }
 
-template <int FCAP, bool SEG>
+template <int FCAP, bool SEG, bool LOW>
 __global__ void __launch_bounds__(256, K1Bounds<FCAP>::kMinBlocks) k1_plain(const K1Args A)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -812,7 +799,7 @@ __global__ void __launch_bounds__(256, K1Bounds<FCAP>::kMinBlocks) k1_plain(cons
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
     const int u = SEG ? (int)(blockIdx.x % A.n_units) : (int)blockIdx.x;
-    dispatch_f<PackedLanes, FCAP, SEG>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
+    dispatch_f<PackedLanes, FCAP, SEG, LOW>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
                                        bar1);
 }
 
@@ -823,7 +810,7 @@ __global__ void __launch_bounds__(256, 2) k1_compensated(const K1Args A)
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
     const int u = blockIdx.x % A.n_units;
-    dispatch_f<CompLanes, kPreciseFcap>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
+    dispatch_f<CompLanes, kPreciseFcap, false, true>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
                                         bar1);
 }
 
@@ -834,7 +821,7 @@ __global__ void __launch_bounds__(256, 2) k1_chunked(const K1Args A)
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
     const int u = blockIdx.x % A.n_units;
-    dispatch_f<ChunkLanes, kPreciseFcap>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
+    dispatch_f<ChunkLanes, kPreciseFcap, false, true>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
                                          bar1);
 }
 
@@ -955,9 +942,12 @@ cudaError_t launch_kernel(Kernel k, const K1Args &a, int64_t n_units, int smem_b
 template <int FCAP>
 cudaError_t launch_k1_cap(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
 {
-    if (a.n_seg < a.n)   // several time segments
-        return launch_kernel(k1_plain<FCAP, true>, a, n_units, smem_bytes, s);
-    return launch_kernel(k1_plain<FCAP, false>, a, n_units, smem_bytes, s);
+    const bool seg = a.n_seg < a.n;   // several time segments
+    if (a.n_lower > 0)
+        return seg ? launch_kernel(k1_plain<FCAP, true, true>, a, n_units, smem_bytes, s)
+                   : launch_kernel(k1_plain<FCAP, false, true>, a, n_units, smem_bytes, s);
+    return seg ? launch_kernel(k1_plain<FCAP, true, false>, a, n_units, smem_bytes, s)
+               : launch_kernel(k1_plain<FCAP, false, false>, a, n_units, smem_bytes, s);
 }
 
 cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)

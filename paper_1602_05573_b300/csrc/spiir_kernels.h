@@ -12,6 +12,8 @@ struct LowerBand {
     const float2 *z;
     int64_t len;               // band samples in this call
     int32_t R;                 // decimation factor (top-rate samples per band sample)
+    int32_t shift;             // log2(R) when R is a power of two, else -1
+    int32_t buf_off;           // this band's float2 offset in a template's prefetch buffer
     int32_t pad;
 };
 constexpr int kMaxLowerBands = 7;
@@ -48,7 +50,8 @@ struct K1Args {
                                //     so a captured graph's replays keep counting)
     int32_t *err;              // device error word
     uint64_t wait_limit_ns;    // bound on every mbarrier wait
-    int32_t n_lower;           // lower bands added in the combine (0 = single rate)
+    int32_t n_lower;
+    int32_t low_len;           // float2 per template slot in the lower-band prefetch buffer           // lower bands added in the combine (0 = single rate)
     LowerBand lower[kMaxLowerBands];
     float2 *ckpt;              // [nc][D][n_slots] state after sample c*ckpt_blocks*Tb - 1
                                // (c >= 1), kernel form; null = no checkpoints
@@ -114,6 +117,39 @@ cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStre
 
 // Raise a kernel's dynamic shared-memory limit once per (kernel, device, size).
 cudaError_t ensure_smem_limit(const void *kernel, int smem_bytes);
+
+// Tensor-core projection of segment start states (spiir_tc.cu): chunks of
+// kTcT samples, windows of kTcK = 2 kTcT strain samples per GEMM column.
+constexpr int kTcT = 256;
+constexpr int kTcK = 2 * kTcT;
+
+struct TcArgs {
+    const unsigned char *W;    // weight tiles (tc_weight_bytes), split BF16
+    const unsigned char *B;    // strain-window tiles of this call (tc_strain_bytes)
+    const int2 *ringoff;       // (Dh - d, copy base) per slot
+    const float2 *aT;          // a^kTcT per slot (kernel form)
+    const float2 *state;       // [D][n_slots] state before the call
+    float2 *seg_init;          // [P][D][n_slots] out: state at each segment start
+    int64_t n_slots;
+    int32_t D;
+    int32_t Dh;
+    int32_t n_ntiles;          // column tiles of 128 windows
+    int32_t col0;              // window of column 0: c'' = col + col0 = -(Dh / kTcT) - 1
+    int32_t c_last;            // last chunk the scan needs ((P - 1) * cps - 1)
+    int32_t cps;               // chunks per segment
+    int32_t *err;              // bit 8: a wait timed out
+    uint64_t wait_limit_ns;
+};
+int64_t tc_weight_bytes(int64_t n_slots);
+int64_t tc_strain_bytes(int64_t n_cols, int D);
+// V_l (split BF16, tile layout) and a^kTcT for every slot of a band.
+cudaError_t launch_tc_weights(const float4 *params, const int2 *ringoff, int64_t n_slots, int Dh,
+                              unsigned char *W, float2 *aT, cudaStream_t s);
+// Strain windows of the call staged in xe, split BF16, tile layout.
+cudaError_t launch_tc_strain(const float *xe, int64_t xe_stride, int Dh, int64_t n, int D,
+                             int64_t n_cols, int col0, unsigned char *B, cudaStream_t s);
+// GEMM + chunk scan: seg_init for every segment (segment 0 = state).
+cudaError_t launch_tc_project(const TcArgs &a, cudaStream_t s);
 
 // Finalize running peaks into the caller's buffers (sqrt of |z|^2).
 cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count,

@@ -1,0 +1,426 @@
+// Tensor-core projection of segment start states (split-BF16 tcgen05 GEMM +
+// chunk scan) for time-segmented filter calls.
+//
+// A call split into time segments needs every filter's state at each
+// segment start.  With chunks of T = 256 samples, the zero-state response of
+// filter l over chunk c is (section "GPU accelerated SPIIR method",
+// subsection "SPIIR method": the single-pole recurrence summed in closed form)
+//     S_l(c) = sum_{j<T} a_l^{T-1-j} b_l x[cT + j - d_l],
+// and the states follow the chunk recurrence s_l(c+1) = a_l^T s_l(c) + S_l(c).
+// Writing d_l = q_l T + r_l, S_l(c) = G_l(c - q_l - 1) with the delay-free
+// window product
+//     G_l(c'') = sum_{m<2T} V_l[m] x[c''T + m],
+//     V_l[m]   = a_l^{2T-1-r_l-m} b_l  for T - r_l <= m < 2T - r_l, else 0,
+// which for all filters and windows is one dense GEMM: rows (Re V_l, Im V_l),
+// K = 2T, one column per window.  It runs on the 5th-generation tensor cores
+// (tcgen05.mma kind::f16, BF16 operands, FP32 accumulate in TMEM) with each
+// operand split in two BF16 parts, hi + lo, and three products
+// hi*hi + hi*lo + lo*hi (~2^-16 relative per term).  The epilogue warps read
+// their accumulator rows from TMEM and run the chunk recurrence over the
+// columns in order, in FP32 (the recurrence contracts by |a|^T per chunk, so
+// rounding does not grow along it), writing the state at each segment start.
+//
+// Operands live in HBM already in the tensor cores' shared-memory layout
+// (K-major, no swizzle: 8-row x 16-byte core matrices, K-direction core
+// stride 128 B, row-group stride 1024 B, 128 x 64 tiles of 16 KB), so each
+// tile arrives with one 1-D TMA bulk copy.  One CTA serves 128 GEMM rows
+// (64 filter slots) of one detector for the whole call: warp 4 issues the
+// copies (two stages) and the MMAs; warps 0-3 own TMEM lanes 0-127 and scan.
+#include "spiir_kernels.h"
+#include "spiir_ptx.h"
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+namespace spiir {
+
+namespace {
+
+constexpr int kRowsTile = 128;                  // GEMM rows per CTA (64 slots x re/im)
+constexpr int kColsTile = 128;                  // windows per accumulator tile
+constexpr int kKBlk = 64;                       // K per staged block
+constexpr int kKBlocks = kTcK / kKBlk;          // 8
+constexpr uint32_t kTileBytes = 128u * kKBlk * 2u;   // 16 KB: 128 rows x 64 BF16
+constexpr uint32_t kStageBytes = 4u * kTileBytes;    // A hi, A lo, B hi, B lo
+constexpr int kStages = 2;
+constexpr int kEpiThreads = 128;
+
+// byte offset of element (row, k) inside a 128 x 64 tile
+__host__ __device__ __forceinline__ uint32_t tile_off(int row, int k)
+{
+    return (uint32_t)(((row >> 3) * 8 + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint16_t bf16_bits(float v)
+{
+    return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+__device__ __forceinline__ float bf16_val(uint16_t b)
+{
+    return __bfloat162float(__ushort_as_bfloat16(b));
+}
+// v = hi + lo with hi, lo in BF16
+__device__ __forceinline__ void split_bf16(float v, uint16_t &hi, uint16_t &lo)
+{
+    hi = bf16_bits(v);
+    lo = bf16_bits(v - bf16_val(hi));
+}
+
+// ---- weights: V_l[m] for every slot, re and im rows -------------------------
+// One thread per (slot, group of 8 m).  a^p by binary powering in FP64.
+__global__ void tc_weights_kernel(const float4 *params, const int2 *ringoff, int64_t n_slots,
+                                  int Dh, unsigned char *W, float2 *aT)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_slots * (kTcK / 8)) return;
+    const int64_t s = i / (kTcK / 8);
+    const int m0 = (int)(i % (kTcK / 8)) * 8;
+    const float4 p = params[s];
+    const int d = Dh - ringoff[s].x;
+    const int r = d % kTcT;
+    // the largest m of the group has the smallest power; walk m downwards
+    double ar = p.x, ai = p.y;
+    uint16_t hr[8], lr[8], hi_[8], li[8];
+    double vr = 0.0, vi = 0.0;   // a^p at the current m (valid window only)
+    bool have = false;
+    for (int j = 7; j >= 0; --j) {
+        const int m = m0 + j;
+        const int pw = 2 * kTcT - 1 - r - m;
+        float fr = 0.f, fi = 0.f;
+        if (pw >= 0 && pw < kTcT) {
+            if (!have) {
+                double br = ar, bi = ai, rr = 1.0, ri = 0.0;
+                for (int e = pw; e > 0; e >>= 1) {
+                    if (e & 1) {
+                        const double t = rr * br - ri * bi;
+                        ri = rr * bi + ri * br;
+                        rr = t;
+                    }
+                    const double t = br * br - bi * bi;
+                    bi = 2.0 * br * bi;
+                    br = t;
+                }
+                vr = rr;
+                vi = ri;
+                have = true;
+            } else {
+                const double t = vr * ar - vi * ai;
+                vi = vr * ai + vi * ar;
+                vr = t;
+            }
+            fr = (float)(vr * p.z - vi * p.w);   // a^pw * b
+            fi = (float)(vr * p.w + vi * p.z);
+        }
+        split_bf16(fr, hr[j], lr[j]);
+        split_bf16(fi, hi_[j], li[j]);
+    }
+    const int64_t row = 2 * s;
+    const int64_t mt = row / kRowsTile;
+    const int rl = (int)(row % kRowsTile);
+    const int kb = m0 / kKBlk, kl = m0 % kKBlk;
+    unsigned char *base = W + ((mt * kKBlocks + kb) * 2) * (int64_t)kTileBytes;
+    uint4 v;
+    v.x = hr[0] | ((uint32_t)hr[1] << 16); v.y = hr[2] | ((uint32_t)hr[3] << 16);
+    v.z = hr[4] | ((uint32_t)hr[5] << 16); v.w = hr[6] | ((uint32_t)hr[7] << 16);
+    *reinterpret_cast<uint4 *>(base + tile_off(rl, kl)) = v;
+    v.x = lr[0] | ((uint32_t)lr[1] << 16); v.y = lr[2] | ((uint32_t)lr[3] << 16);
+    v.z = lr[4] | ((uint32_t)lr[5] << 16); v.w = lr[6] | ((uint32_t)lr[7] << 16);
+    *reinterpret_cast<uint4 *>(base + kTileBytes + tile_off(rl, kl)) = v;
+    v.x = hi_[0] | ((uint32_t)hi_[1] << 16); v.y = hi_[2] | ((uint32_t)hi_[3] << 16);
+    v.z = hi_[4] | ((uint32_t)hi_[5] << 16); v.w = hi_[6] | ((uint32_t)hi_[7] << 16);
+    *reinterpret_cast<uint4 *>(base + tile_off(rl + 1, kl)) = v;
+    v.x = li[0] | ((uint32_t)li[1] << 16); v.y = li[2] | ((uint32_t)li[3] << 16);
+    v.z = li[4] | ((uint32_t)li[5] << 16); v.w = li[6] | ((uint32_t)li[7] << 16);
+    *reinterpret_cast<uint4 *>(base + kTileBytes + tile_off(rl + 1, kl)) = v;
+    if (m0 == 0) {   // a^T, FP64 then rounded once
+        double br = ar, bi = ai, rr = 1.0, ri = 0.0;
+        for (int e = kTcT; e > 0; e >>= 1) {
+            if (e & 1) {
+                const double t = rr * br - ri * bi;
+                ri = rr * bi + ri * br;
+                rr = t;
+            }
+            const double t = br * br - bi * bi;
+            bi = 2.0 * br * bi;
+            br = t;
+        }
+        aT[s] = make_float2((float)rr, (float)ri);
+    }
+}
+
+// ---- strain windows: B[col][m] = x[(col + col0) T + m], split in BF16 ------
+// xe holds [Dh history | n call samples] per detector (call sample k at
+// Dh + k); samples outside [-Dh, n) read as zero.
+__global__ void tc_strain_kernel(const float *xe, int64_t xe_stride, int Dh, int64_t n, int D,
+                                 int64_t n_cols_pad, int col0, unsigned char *B)
+{
+    const int64_t per_det = n_cols_pad * (kTcK / 8);
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= per_det * D) return;
+    const int det = (int)(i / per_det);
+    const int64_t col = (i % per_det) / (kTcK / 8);
+    const int m0 = (int)(i % (kTcK / 8)) * 8;
+    const int64_t k0 = (col + col0) * (int64_t)kTcT + m0;   // call sample of m0
+    const float *row = xe + (int64_t)det * xe_stride + Dh;
+    uint16_t h[8], l[8];
+    for (int j = 0; j < 8; ++j) {
+        const int64_t k = k0 + j;
+        const float v = (k >= -(int64_t)Dh && k < n) ? row[k] : 0.f;
+        split_bf16(v, h[j], l[j]);
+    }
+    const int64_t nt = col / kColsTile;
+    const int rl = (int)(col % kColsTile);
+    const int kb = m0 / kKBlk, kl = m0 % kKBlk;
+    const int64_t n_ntiles = n_cols_pad / kColsTile;
+    unsigned char *base =
+        B + (((int64_t)det * n_ntiles + nt) * kKBlocks + kb) * 2 * (int64_t)kTileBytes;
+    uint4 v;
+    v.x = h[0] | ((uint32_t)h[1] << 16); v.y = h[2] | ((uint32_t)h[3] << 16);
+    v.z = h[4] | ((uint32_t)h[5] << 16); v.w = h[6] | ((uint32_t)h[7] << 16);
+    *reinterpret_cast<uint4 *>(base + tile_off(rl, kl)) = v;
+    v.x = l[0] | ((uint32_t)l[1] << 16); v.y = l[2] | ((uint32_t)l[3] << 16);
+    v.z = l[4] | ((uint32_t)l[5] << 16); v.w = l[6] | ((uint32_t)l[7] << 16);
+    *reinterpret_cast<uint4 *>(base + kTileBytes + tile_off(rl, kl)) = v;
+}
+
+// ---- tcgen05 helpers -------------------------------------------------------
+// Shared-memory matrix descriptor, K-major without swizzle: start address,
+// K-direction core-matrix stride (leading byte offset), row-group stride
+// (stride byte offset), descriptor version 1 (bits 46-48 = 0b001).
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr)
+{
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128u >> 4) << 16) |
+           ((uint64_t)(1024u >> 4) << 32) | (1ull << 46);
+}
+// Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
+// and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            ((uint32_t)(kColsTile >> 3) << 17) |
+                            ((uint32_t)(kRowsTile >> 4) << 24);
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_after()
+{
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// ---- projection: GEMM tile loop + chunk scan ---------------------------------
+__global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[2 * kStages + 2];
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t mt = blockIdx.x;
+    const int det = blockIdx.y;
+    const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[kStages]);
+    const uint32_t acc_full = smem_addr(&bars[2 * kStages]);
+    const uint32_t acc_empty = smem_addr(&bars[2 * kStages + 1]);
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) {
+            mbar_init(full0 + 8 * st, 1);
+            mbar_init(empty0 + 8 * st, 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, kEpiThreads);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile(
+            "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                smem_addr(&tmem_slot)),
+            "r"(kColsTile)
+            : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int n_ntiles = A.n_ntiles;
+    bool ok = true;
+
+    if (warp == 4) {
+        if (lane == 0) {
+            // producer + MMA issue, two stages
+            const int total = n_ntiles * kKBlocks;
+            const unsigned char *wt = A.W + mt * kKBlocks * 2 * (int64_t)kTileBytes;
+            const unsigned char *bt = A.B + (int64_t)det * n_ntiles * kKBlocks * 2 * kTileBytes;
+            auto fill = [&](int it) {
+                const int st = it % kStages;
+                const int nt = it / kKBlocks, kb = it % kKBlocks;
+                const uint32_t dst = smem_addr(smem) + st * kStageBytes;
+                const uint32_t full = full0 + 8 * st;
+                mbar_expect_tx(full, kStageBytes);
+                bulk_g2s(dst, wt + (int64_t)kb * 2 * kTileBytes, 2 * kTileBytes, full);
+                bulk_g2s(dst + 2 * kTileBytes,
+                         bt + ((int64_t)nt * kKBlocks + kb) * 2 * kTileBytes, 2 * kTileBytes,
+                         full);
+            };
+            // block it+1 is copied while the MMAs of block it run; a stage is
+            // refilled once the MMAs that read it (block it-1) have finished
+            if (total > 0) fill(0);
+            for (int it = 0; it < total && ok; ++it) {
+                const int st = it % kStages;
+                const int nt = it / kKBlocks, kb = it % kKBlocks;
+                ok = mbar_wait(full0 + 8 * st, (uint32_t)((it / kStages) & 1), A.wait_limit_ns);
+                if (ok && kb == 0 && nt > 0)   // epilogue has read the previous tile
+                    ok = mbar_wait(acc_empty, (uint32_t)((nt - 1) & 1), A.wait_limit_ns);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t s0 = smem_addr(smem) + st * kStageBytes;
+#pragma unroll
+                for (int kk = 0; kk < kKBlk / 16; ++kk) {
+                    const uint32_t adv = kk * 256u;   // 16 K = two core matrices
+                    const uint64_t ah = umma_desc(s0 + adv), al = umma_desc(s0 + kTileBytes + adv);
+                    const uint64_t bh = umma_desc(s0 + 2 * kTileBytes + adv);
+                    const uint64_t bl = umma_desc(s0 + 3 * kTileBytes + adv);
+                    umma_bf16(tmem, ah, bh, (kb > 0 || kk > 0) ? 1u : 0u);
+                    umma_bf16(tmem, ah, bl, 1u);
+                    umma_bf16(tmem, al, bh, 1u);
+                }
+                umma_commit(empty0 + 8 * st);          // stage free once these MMAs finish
+                if (kb == kKBlocks - 1) umma_commit(acc_full);
+                if (it + 1 < total) {
+                    const int nx = it + 1, sx = nx % kStages;
+                    if (nx >= kStages)
+                        ok = mbar_wait(empty0 + 8 * sx, (uint32_t)((nx / kStages - 1) & 1),
+                                       A.wait_limit_ns);
+                    if (ok) fill(nx);
+                }
+            }
+            if (!ok) atomicOr(A.err, 8);
+        }
+    } else {
+        // epilogue: row = TMEM lane; rows 2s, 2s+1 are Re and Im of slot s
+        const int row = warp * 32 + lane;
+        const int comp = row & 1;
+        const int64_t slot = mt * (kRowsTile / 2) + (row >> 1);
+        const bool valid = slot < A.n_slots;
+        float2 aT = make_float2(0.f, 0.f), s = make_float2(0.f, 0.f);
+        int q = 0;
+        if (valid) {
+            aT = A.aT[slot];
+            s = A.state[(int64_t)det * A.n_slots + slot];
+            q = (A.Dh - A.ringoff[slot].x) / kTcT;
+            if (comp == 0) A.seg_init[(int64_t)det * A.n_slots + slot] = s;
+        }
+        for (int nt = 0; nt < n_ntiles; ++nt) {
+            ok = mbar_wait(acc_full, (uint32_t)(nt & 1), A.wait_limit_ns) && ok;
+            if (!__all_sync(0xffffffffu, ok)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            for (int c0 = 0; c0 < kColsTile; c0 += 16) {
+                uint32_t v[16];
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,"
+                    "%11,%12,%13,%14,%15}, [%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
+                      "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
+                      "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const float mine = __uint_as_float(v[j]);
+                    const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+                    const float gr = comp ? other : mine, gi = comp ? mine : other;
+                    // window c'' = col + col0 feeds chunk c = c'' + q + 1
+                    const int64_t c = (int64_t)nt * kColsTile + c0 + j + A.col0 + q + 1;
+                    if (valid && c >= 0 && c <= A.c_last) {
+                        const float nr = fmaf(aT.x, s.x, fmaf(-aT.y, s.y, gr));
+                        const float ni = fmaf(aT.x, s.y, fmaf(aT.y, s.x, gi));
+                        s = make_float2(nr, ni);
+                        if ((c + 1) % A.cps == 0 && comp == 0) {
+                            const int64_t b = (c + 1) / A.cps;   // segment that starts here
+                            A.seg_init[(b * A.D + det) * A.n_slots + slot] = s;
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty);
+        }
+        if (!ok && lane == 0) atomicOr(A.err, 8);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(kColsTile)
+                     : "memory");
+}
+
+}  // namespace
+
+int64_t tc_weight_bytes(int64_t n_slots)
+{
+    const int64_t mtiles = (2 * n_slots + kRowsTile - 1) / kRowsTile;
+    return mtiles * kKBlocks * 2 * (int64_t)kTileBytes;
+}
+
+int64_t tc_strain_bytes(int64_t n_cols, int D)
+{
+    const int64_t ntiles = (n_cols + kColsTile - 1) / kColsTile;
+    return (int64_t)D * ntiles * kKBlocks * 2 * (int64_t)kTileBytes;
+}
+
+cudaError_t launch_tc_weights(const float4 *params, const int2 *ringoff, int64_t n_slots, int Dh,
+                              unsigned char *W, float2 *aT, cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(W, 0, (size_t)tc_weight_bytes(n_slots), s);
+    if (e != cudaSuccess) return e;
+    const int64_t threads = n_slots * (kTcK / 8);
+    if (threads == 0) return cudaSuccess;
+    tc_weights_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(params, ringoff, n_slots,
+                                                                         Dh, W, aT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_strain(const float *xe, int64_t xe_stride, int Dh, int64_t n, int D,
+                             int64_t n_cols, int col0, unsigned char *B, cudaStream_t s)
+{
+    const int64_t n_cols_pad = (n_cols + kColsTile - 1) / kColsTile * kColsTile;
+    const int64_t threads = (int64_t)D * n_cols_pad * (kTcK / 8);
+    if (threads == 0) return cudaSuccess;
+    tc_strain_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(xe, xe_stride, Dh, n, D,
+                                                                        n_cols_pad, col0, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tc_project(const TcArgs &a, cudaStream_t s)
+{
+    const int smem = kStages * (int)kStageBytes;
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(tc_project_kernel), smem);
+    if (e != cudaSuccess) return e;
+    const int64_t mtiles = (2 * a.n_slots + kRowsTile - 1) / kRowsTile;
+    if (mtiles == 0 || a.n_ntiles == 0) return cudaSuccess;
+    tc_project_kernel<<<dim3((unsigned)mtiles, (unsigned)a.D), 160, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace spiir

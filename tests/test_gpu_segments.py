@@ -5,8 +5,11 @@ zero-state pass gives each segment's contribution to its end state, an FP64
 carry y_start(q+1) = a^n_seg y_start(q) + y_end^0(q) gives every segment its
 true start state (the same linear recurrence of the SPIIR filter, applied a
 segment at a time), and the filtering pass runs each segment from there.
-The result must meet the same element-wise bar as the unsegmented path, and
-the peak must be the earliest largest |z| over the whole call.
+The start states come either from a zero-state FP32 pass with an FP64 carry
+("recurrence") or from chunk sums computed as a split-BF16 tensor-core GEMM
+followed by an FP32 chunk scan ("tensor").  Either way the result must meet
+the same element-wise bar as the unsegmented path, and the peak must be the
+earliest largest |z| over the whole call.
 """
 import numpy as np
 import pytest
@@ -39,35 +42,43 @@ def run(sp, bank, x, chunks=None, **opts):
     return np.concatenate(parts, axis=-1), pa.cpu().numpy(), pi.cpu().numpy(), plan
 
 
+PROJ = ["tensor", "recurrence"]
+
+
+@pytest.mark.parametrize("projection", PROJ)
 @pytest.mark.parametrize("P", [2, 3, 7])
 @pytest.mark.parametrize("n", [6000, 4096 + 513])
-def test_forced_segments_match_oracle(sp, P, n):
+def test_forced_segments_match_oracle(sp, P, n, projection):
     bank = make_bank(11, (20, 150), (0.99, 0.9995), 900, seed=401, n_det=2)
     x = make_strain(2, n, seed=402)
-    z, pa, pi, _ = run(sp, bank, x, time_segments=P, block_len=256)
+    z, pa, pi, _ = run(sp, bank, x, time_segments=P, block_len=256, projection=projection)
     zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
     rel, _ = rel_errors(z, zref)
     assert rel.max() <= REL_TOL, rel.max()
     check_peaks(z, zref, pa, pi)
 
 
-def test_segments_continue_a_stream(sp):
+@pytest.mark.parametrize("projection", PROJ)
+def test_segments_continue_a_stream(sp, projection):
     """Segmented calls of assorted lengths (the first one starting from a
     non-zero state) continue the stream to within the parity bar, and peak
     indices count from the stream start."""
     bank = make_bank(6, (30, 120), (0.995, 0.9999), 700, seed=403)
     x = make_strain(1, 20000, seed=404)
-    z, pa, pi, _ = run(sp, bank, x, chunks=[3000, 257, 9000], time_segments=5, block_len=256)
+    z, pa, pi, _ = run(sp, bank, x, chunks=[3000, 257, 9000], time_segments=5, block_len=256,
+                       projection=projection)
     zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
     rel, _ = rel_errors(z, zref)
     assert rel.max() <= REL_TOL, rel.max()
     check_peaks(z, zref, pa, pi)
 
 
-def test_segments_in_half_warp_mode(sp):
+@pytest.mark.parametrize("projection", PROJ)
+def test_segments_in_half_warp_mode(sp, projection):
     bank = make_bank(20, (8, 60), (0.99, 0.999), 400, seed=405, n_det=2)
     x = make_strain(2, 7000, seed=406)
-    z, pa, pi, plan = run(sp, bank, x, time_segments=4, lanes_per_template=16, block_len=256)
+    z, pa, pi, plan = run(sp, bank, x, time_segments=4, lanes_per_template=16, block_len=256,
+                          projection=projection)
     assert plan.info()["lanes_per_template"] == 16
     zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
     rel, _ = rel_errors(z, zref)
@@ -88,10 +99,11 @@ def test_segment_count_is_clamped_by_call_length(sp):
         check_peaks(z, zref, pa, pi)
 
 
-def test_segments_on_multirate_bank(sp):
+@pytest.mark.parametrize("projection", PROJ)
+def test_segments_on_multirate_bank(sp, projection):
     bank = make_multirate_bank(12, (60, 120, 120), (1, 4, 16), (0.99, 0.9995), 1024, 409)
     x = make_strain(1, 40000, seed=410)
-    plan = sp.Plan(bank, time_segments=6)
+    plan = sp.Plan(bank, time_segments=6, projection=projection)
     z = plan.filter(torch.from_numpy(x).cuda()).cpu().numpy()
     pa, pi = plan.peak()
     plan.check()
@@ -133,3 +145,36 @@ def test_segmented_graph_replay(sp):
         g.replay()
         assert np.array_equal(z.cpu().numpy(), zs[i])
     assert torch.equal(pa, pa_ref) and torch.equal(pi, pi_ref)
+
+
+def test_tensor_projection_long_delays_and_slow_poles(sp):
+    """Delays up to 4096 (16 chunks of history) and poles up to r = 0.99999:
+    the chunk scan carries states across many chunks."""
+    bank = make_bank(8, (100, 300), (0.999, 0.99999), 4096, seed=413, n_det=3)
+    x = make_strain(3, 30000, seed=414)
+    z, pa, pi, _ = run(sp, bank, x, chunks=[12000], time_segments=6, projection="tensor")
+    zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
+    rel, _ = rel_errors(z, zref)
+    assert rel.max() <= REL_TOL, rel.max()
+    check_peaks(z, zref, pa, pi)
+
+
+def test_tensor_projection_follows_new_coefficients(sp):
+    """spiir_set_coefficients invalidates the projection weights: the next
+    segmented call uses the new poles and gains."""
+    bank = make_bank(6, 64, (0.99, 0.9995), 500, seed=415)
+    new = make_bank(6, 64, (0.99, 0.9995), 500, seed=416)
+    x = make_strain(1, 8000, seed=417)
+    plan = sp.Plan(bank, time_segments=4, projection="tensor")
+    xt = torch.from_numpy(x).cuda()
+    plan.filter(xt)
+    plan.reset()
+    # same template sizes and delays, new poles and gains
+    a2 = torch.from_numpy(new.a.astype(np.complex64)).cuda()
+    b2 = torch.from_numpy(new.b.astype(np.complex64)).cuda()
+    plan.set_coefficients(a2, b2)
+    z = plan.filter(xt).cpu().numpy()
+    plan.check()
+    zref, _, _ = oracle.filter_bank(bank.off, new.a, new.b, bank.d, x)
+    rel, _ = rel_errors(z, zref)
+    assert rel.max() <= REL_TOL, rel.max()
