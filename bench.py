@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 from spiir_inputs import WORKLOADS, updates, workload_bank, workload_strain  # noqa: E402
 
 LANE_OPS_PER_UPDATE = 8      # 4 FMA + 2 MUL + 2 ADD (FP32 lane operations)
+LANE_OPS_ADJOINT = 20        # reverse pass per filter-update: recompute 6, adjoint 6, grads 8
 B300_SMS = 148
 FP32_LANES_PER_SM = 128
 
@@ -50,7 +51,7 @@ def parse():
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "plain", "multirate", "adjoint", "precision"])
     ap.add_argument("--precision", default="plain",
-                    choices=["plain", "compensated", "chunked_fp64"])
+                    choices=["plain", "compensated", "chunked_fp64", "chunked_tc"])
     ap.add_argument("--graph", action="store_true",
                     help="time replays of a captured CUDA graph of the step")
     ap.add_argument("--autotune", action="store_true",
@@ -253,8 +254,10 @@ def run_ours(args, rank, world, local_rank):
     emit_z = args.workload in ("batched", "plain")
     adjoint = args.workload == "adjoint"
 
+    # kernel_timing: the plan records CUDA events around each of its filter,
+    # projection and adjoint launches, on the launching stream (not in graphs)
     plan = sp.Plan(bank, device=local_rank, precision=args.precision,
-                   autotune=args.autotune)
+                   autotune=args.autotune, kernel_timing=True)
     stream = torch.cuda.Stream(device=dev)
     x = torch.from_numpy(x_host).to(dev)
     z = torch.empty((D, T, n), dtype=torch.complex64, device=dev) if emit_z else None
@@ -293,6 +296,7 @@ def run_ours(args, rank, world, local_rank):
         step = graph.replay if graph is not None else call
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
+        plan.kernel_times()   # drop the warm-up launches' events
         with ClockSampler(local_rank) as clk:
             t0 = torch.cuda.Event(enable_timing=True)
             t1 = torch.cuda.Event(enable_timing=True)
@@ -304,6 +308,7 @@ def run_ours(args, rank, world, local_rank):
             t1.record(stream)
             barrier()
         plan.check(stream)
+    ktimes = plan.kernel_times()   # the timed steps' kernels, per class
     total_ms = t0.elapsed_time(t1)
     step_times = [a.elapsed_time(b) for a, b in ev]
     filt_ms = float(np.mean(step_times))
@@ -393,11 +398,26 @@ def run_ours(args, rank, world, local_rank):
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2032.0
     peak_lane = B300_SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12   # T lane-ops/s
-    achieved = LANE_OPS_PER_UPDATE * upd / (filt_ms / 1e3) / 1e12
     kernel = {"plain": "k1_plain", "compensated": "k1_compensated",
-              "chunked_fp64": "k1_chunked"}[args.precision]
+              "chunked_fp64": "k1_chunked", "chunked_tc": "k1_anchored"}[args.precision]
+    # the dominant kernel's own device time over the timed steps (events the
+    # plan records around each launch); graph replays record none, then the
+    # step time stands in
+    k_ms, k_n = ktimes["adjoint" if adjoint else "filter"]
+    lane_ops = (LANE_OPS_ADJOINT if adjoint else LANE_OPS_PER_UPDATE) * upd
+    if k_n > 0:
+        kernel_ms = k_ms / args.steps
+        timing = (f"{k_n / args.steps:.0f} launch(es) per step, {kernel_ms:.3f} ms per step "
+                  f"(CUDA events around each launch on the launching stream)")
+    else:
+        kernel_ms = filt_ms
+        timing = f"mean step time {filt_ms:.3f} ms (graph replay: no per-launch events)"
+    achieved = lane_ops / (kernel_ms / 1e3) / 1e12
     if adjoint:
-        kernel = "k6_adjoint (+ k1_plain checkpoint pass)"
+        kernel = "k6_adjoint"
+    ops_note = ("20 algorithmic lane-ops per filter-update of the reverse pass (recompute 6, "
+                "adjoint recurrence 6, grad a 4, grad b 2, grad x 2)" if adjoint else
+                "8 algorithmic lane-ops per filter-update")
     line = {
         "metric": "filter-updates/s", "value": value, "unit": "filter-updates/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -419,11 +439,9 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                      "peak": peak_lane, "unit": "T FP32 lane-ops/s",
                      "frac": achieved / peak_lane, "traffic": None,
-                     "note": f"8 algorithmic lane-ops per filter-update x {upd:.4g} updates "
-                             f"per step / mean step time {filt_ms:.3f} ms (CUDA events on the "
-                             f"launching stream); peak = 148 SMs x 128 FP32 lanes x "
-                             f"{sm_max:.0f} MHz (derived from unit counts and the measured "
-                             f"max clock)"},
+                     "note": f"{ops_note} x {upd:.4g} updates per step / {timing}; "
+                             f"peak = 148 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived "
+                             f"from unit counts and the measured max clock)"},
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
         "filter_ms": filt_ms,
@@ -432,6 +450,21 @@ def run_ours(args, rank, world, local_rank):
         "templates_realtime": upd * world / (ms_step / 1e3) / (bank.n_filters / T * D)
                               / WORKLOADS[args.workload]["rate"],
     }
+    tc_ms, tc_n = ktimes["projection"]
+    if tc_n > 0:
+        # tensor-core projection: 3 split-BF16 products of the (2 rows per
+        # filter) x (2 x 256 window) weights against one window per 256-sample
+        # chunk, i.e. 24 algorithmic flops per filter-update
+        tc_flops = 24.0 * upd
+        tc_peak = peaks.get("bf16_tflops") or 1800.0
+        tc_ach = tc_flops / (tc_ms / args.steps / 1e3) / 1e12
+        line["roofline_projection"] = {
+            "bound": "tensor", "kernel": "tc_project_kernel", "achieved": tc_ach,
+            "peak": tc_peak, "unit": "TFLOP/s", "frac": tc_ach / tc_peak, "traffic": None,
+            "ms_per_step": tc_ms / args.steps, "launches_per_step": tc_n / args.steps,
+            "note": "24 algorithmic BF16 flops per filter-update / its own CUDA-event time; "
+                    "peak = measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"
+                    if peaks.get("bf16_tflops") else "peak = fallback 1.8 PFLOP/s bf16"}
     line.update(extra)
     if e2e:
         line["e2e"] = e2e

@@ -122,6 +122,9 @@ typedef struct spiir_options {
                             /* state FP32 pass over all but the last segment, FP64 */
                             /* carry) or _TENSOR (chunk sums by split-BF16 tcgen05 */
                             /* GEMM, FP32 chunk scan)                              */
+    int32_t kernel_timing;  /* nonzero: record CUDA events around every filter   */
+                            /* (K1) and tensor-core projection launch, outside     */
+                            /* stream capture; read them with spiir_kernel_times  */
     int32_t reserved[1];
 } spiir_options;
 
@@ -301,6 +304,18 @@ spiir_status spiir_selftest_bounded_wait(spiir_plan *plan, uint64_t limit_ns, vo
 spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const float *x_dev, int64_t n,
                                   float *z_dev, float *peak_abs_dev, int64_t *peak_idx_dev,
                                   void *stream);
+
+/* Device time of the kernels launched since the last read (plans created
+ * with kernel_timing set; events recorded on the call's stream around each
+ * launch).  Waits for the recorded events, sums their durations per kernel
+ * class and clears the record.
+ *   ms[SPIIR_KERNEL_CLASSES]  total milliseconds per class (host array)
+ *   n[SPIIR_KERNEL_CLASSES]   launches per class (host array, may be NULL)
+ * Classes: 0 the filter kernel (all K1 passes), 1 the tensor-core
+ * projection, 2 the adjoint's reverse pass.
+ * Errors: EINVAL (NULL plan or ms), ECUDA. */
+#define SPIIR_KERNEL_CLASSES 3
+spiir_status spiir_kernel_times(spiir_plan *plan, double *ms, int64_t *n);
 
 /* Static description of a status code. */
 const char *spiir_status_str(spiir_status status);

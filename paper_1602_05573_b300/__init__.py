@@ -33,6 +33,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
 PRECISIONS = {"plain": 0, "compensated": 1, "chunked_fp64": 2, "chunked_tc": 3}
 PROJECTIONS = {"auto": 0, "recurrence": 1, "tensor": 2}
+KERNEL_CLASSES = 3
 
 # exported symbols (include/spiir.h)
 SYMBOLS = [
@@ -58,7 +59,8 @@ class Options(ctypes.Structure):
                 ("ring_copies", ctypes.c_int32), ("device", ctypes.c_int32),
                 ("autotune", ctypes.c_int32), ("max_filters_per_lane", ctypes.c_int32),
                 ("lanes_per_template", ctypes.c_int32), ("time_segments", ctypes.c_int32),
-                ("projection", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("projection", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -115,6 +117,9 @@ def _configure(lib):
     lib.spiir_status_str.restype = ctypes.c_char_p
     lib.spiir_last_error_detail.argtypes = []
     lib.spiir_last_error_detail.restype = ctypes.c_char_p
+    if hasattr(lib, "spiir_kernel_times"):
+        lib.spiir_kernel_times.argtypes = [_P, _P, _P]
+        lib.spiir_kernel_times.restype = _st
     return lib
 
 
@@ -219,7 +224,8 @@ class Plan:
                  block_len: int = 0, warps_per_cta: int = 0, ring_copies: int = 0,
                  chunk_len: int = 256, autotune: bool = False,
                  max_filters_per_lane: int = 0, lanes_per_template: int = 0,
-                 time_segments: int = 0, projection: str = "auto", lib=None):
+                 time_segments: int = 0, projection: str = "auto",
+                 kernel_timing: bool = False, lib=None):
         self._h = None
         self._lib = lib if lib is not None else _lib
         off = np.ascontiguousarray(bank.off, np.int64)
@@ -253,6 +259,7 @@ class Plan:
         opt.lanes_per_template = int(lanes_per_template)
         opt.time_segments = int(time_segments)
         opt.projection = PROJECTIONS[projection]
+        opt.kernel_timing = 1 if kernel_timing else 0
         h = _P()
         _check(self._lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
                "spiir_plan_create", self._lib)
@@ -396,6 +403,15 @@ class Plan:
         history = np.ascontiguousarray(history, np.float32)
         _check(self._lib.spiir_state_set(self._h, _ptr(state), _ptr(history), int(samples)),
                "spiir_state_set", self._lib)
+
+    def kernel_times(self) -> dict:
+        """Device milliseconds and launch counts per kernel class since the last
+        read (plans made with kernel_timing=True): filter, tensor-core
+        projection, adjoint reverse pass."""
+        ms = (ctypes.c_double * KERNEL_CLASSES)()
+        n = (ctypes.c_int64 * KERNEL_CLASSES)()
+        _check(self._lib.spiir_kernel_times(self._h, ms, n), "spiir_kernel_times", self._lib)
+        return {name: (ms[i], n[i]) for i, name in enumerate(("filter", "projection", "adjoint"))}
 
     def check(self, stream=None):
         """Wait for the plan's work; raise SpiirError(ETIMEOUT) if a bounded wait gave up."""

@@ -161,6 +161,9 @@ struct Band {
     bool tc_valid = false;         //   weights match the current coefficients
     unsigned char *tc_b = nullptr; //   strain-window tiles of a call
     int64_t tc_b_cap = 0;          //   bytes
+    double2 *tc_aT64 = nullptr;    //   a^256 per slot in FP64
+    float2 *tc_anchor = nullptr;   // chunked tensor-core form: anchors of a time tile
+    int64_t tc_anchor_cap = 0;     //   float2 elements
     int4 *adj_tasks = nullptr;     // adjoint work list (built on the first backward call)
     int32_t *adj_units = nullptr;
     int64_t adj_n_units = 0;
@@ -193,7 +196,39 @@ struct spiir_plan {
     std::string tune_report;
     int32_t last_launches = 0;    // kernels the last filter/backward call launched
     int32_t last_segments = 1;    // time segments of the last call's top band
+    // kernel timing (opt.kernel_timing): event pairs since the last read
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, int>> ev_used;   // (first event index, kernel class)
 };
+
+namespace {
+constexpr int kTimeK1 = 0, kTimeTc = 1, kTimeAdj = 2;
+constexpr size_t kMaxTimedLaunches = 4096;
+
+// Records an event before a timed launch; returns its pool index or -1.
+int time_begin(spiir_plan *p, cudaStream_t s)
+{
+    if (!p->opt.kernel_timing) return -1;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return -1;
+    const size_t i = p->ev_used.size() * 2;
+    if (p->ev_used.size() >= kMaxTimedLaunches) return -1;
+    while (p->ev_pool.size() < i + 2) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) return -1;
+        p->ev_pool.push_back(ev);
+    }
+    if (cudaEventRecord(p->ev_pool[i], s) != cudaSuccess) return -1;
+    return (int)i;
+}
+void time_end(spiir_plan *p, cudaStream_t s, int i, int cls)
+{
+    if (i < 0) return;
+    if (cudaEventRecord(p->ev_pool[(size_t)i + 1], s) == cudaSuccess)
+        p->ev_used.push_back(std::make_pair(i, cls));
+}
+}  // namespace
 
 namespace {
 
@@ -223,6 +258,8 @@ void free_band(Band &b)
     cudaFree(b.tc_w);
     cudaFree(b.tc_aT);
     cudaFree(b.tc_b);
+    cudaFree(b.tc_aT64);
+    cudaFree(b.tc_anchor);
     cudaFree(b.adj_tasks);
     cudaFree(b.adj_units);
     cudaFree(b.adj_sub);
@@ -412,11 +449,12 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     spiir_options opt;
     spiir_options_default(&opt);
     if (opt_in) opt = *opt_in;
-    if (opt.precision == SPIIR_PREC_CHUNKED_TC)
-        return fail(SPIIR_EUNSUPPORTED, "the tensor-core chunked projection is not built yet");
     if (opt.precision < SPIIR_PREC_PLAIN || opt.precision > SPIIR_PREC_CHUNKED_TC)
         return fail(SPIIR_EINVAL, "unknown precision mode");
     if (opt.chunk_len == 0) opt.chunk_len = 256;
+    if (opt.precision == SPIIR_PREC_CHUNKED_TC && opt.chunk_len != spiir::kTcT)
+        return fail(SPIIR_EINVAL, "the tensor-core chunked form uses chunks of " +
+                                      std::to_string(spiir::kTcT) + " samples");
     if (opt.projection < SPIIR_PROJECT_AUTO || opt.projection > SPIIR_PROJECT_TENSOR)
         return fail(SPIIR_EINVAL, "projection must be 0 (auto), 1 (recurrence) or 2 (tensor)");
     if (opt.block_len != 0 && (opt.block_len < 32 || opt.block_len % 32 != 0))
@@ -462,7 +500,10 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     lo.C = opt.ring_copies;
     lo.Fcap = opt.max_filters_per_lane;
     lo.G = opt.lanes_per_template;
-    if (opt.precision != SPIIR_PREC_PLAIN) {
+    if (opt.precision == SPIIR_PREC_CHUNKED_TC) {
+        // the anchored kernel holds at most kAnchorFcap filters per lane
+        if (lo.Fcap == 0 || lo.Fcap > spiir::kAnchorFcap) lo.Fcap = spiir::kAnchorFcap;
+    } else if (opt.precision != SPIIR_PREC_PLAIN) {
         // the compensated and chunked kernels hold at most kPreciseFcap filters per lane
         if (lo.Fcap == 0 || lo.Fcap > spiir::kPreciseFcap) lo.Fcap = spiir::kPreciseFcap;
         if (opt.chunk_len < 8 || opt.chunk_len % 8 != 0 || lo.Tb % opt.chunk_len != 0)
@@ -571,6 +612,7 @@ spiir_status spiir_plan_destroy(spiir_plan *p)
         cudaFree(p->peak_idx);
         cudaFree(p->err);
         cudaFree(p->t0_dev);
+        for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
     }
     delete p;
     return SPIIR_OK;
@@ -674,6 +716,42 @@ int segments_for(const spiir_plan *p, const Band &b, int64_t nb)
 // turns those into the true start state of every segment, and the main pass
 // runs every segment from its start state; per-segment peaks are merged in
 // time order.
+// Projection weights (tile layout, split BF16) and a^256 of a band, built on
+// first use and after every coefficient update.
+spiir_status ensure_tc_weights(spiir_plan *p, Band &b, cudaStream_t s)
+{
+    if (b.tc_valid) return SPIIR_OK;
+    const spiir::Layout &L = b.lay;
+    cudaError_t e;
+    if (!b.tc_w) {
+        if ((e = cudaMalloc(&b.tc_w, (size_t)spiir::tc_weight_bytes(L.n_slots))) != cudaSuccess ||
+            (e = dalloc(&b.tc_aT, (size_t)L.n_slots)) != cudaSuccess ||
+            (e = dalloc(&b.tc_aT64, (size_t)L.n_slots)) != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "projection weights")
+                                                  : cuda_fail(e, "cudaMalloc");
+    }
+    if ((e = spiir::launch_tc_weights(b.params, b.ringoff, L.n_slots, (int)L.Dh, b.tc_w, b.tc_aT,
+                                      b.tc_aT64, s)) != cudaSuccess)
+        return cuda_fail(e, "projection weights launch");
+    b.tc_valid = true;
+    p->last_launches += 1;
+    return SPIIR_OK;
+}
+
+spiir_status ensure_tc_strain(Band &b, int64_t bytes, cudaStream_t s)
+{
+    if (b.tc_b_cap >= bytes) return SPIIR_OK;
+    cudaError_t e;
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    cudaFree(b.tc_b);
+    b.tc_b = nullptr;
+    if ((e = cudaMalloc(&b.tc_b, (size_t)bytes)) != cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "projection workspace")
+                                              : cuda_fail(e, "cudaMalloc");
+    b.tc_b_cap = bytes;
+    return SPIIR_OK;
+}
+
 // Dynamic shared memory of a K1 launch: the layout's ring and block sums,
 // plus the lower-band prefetch buffers of a multirate top band.
 int k1_smem(const Band &b, const spiir::K1Args &a)
@@ -682,9 +760,108 @@ int k1_smem(const Band &b, const spiir::K1Args &a)
            (a.n_lower > 0 ? b.lay.W * (32 / b.lay.G) * a.low_len * (int)sizeof(float2) : 0);
 }
 
+// The chunked tensor-core form over one band call, in time tiles whose
+// anchors fit a bounded workspace.  Per tile: strain windows, the split-BF16
+// GEMM of chunk sums with the FP64 chunk scan (anchors of every chunk, the
+// FP64 state carried to the next tile), then the anchored FP32 pass (z and
+// running peaks).
+spiir_status launch_anchored(spiir_plan *p, Band &b, spiir::K1Args a, cudaStream_t s,
+                             int64_t *t0_advance)
+{
+    const spiir::Layout &L = b.lay;
+    const int D = p->D;
+    const int64_t n = a.n;
+    const int64_t per = (int64_t)D * L.n_slots;
+    cudaError_t e;
+    spiir_status st = ensure_tc_weights(p, b, s);
+    if (st != SPIIR_OK) return st;
+    // tile: whole blocks and whole chunks, anchors within a quarter of the
+    // free device memory (at most 16 GiB): fewer tiles, fewer weight passes
+    int64_t unit = L.Tb;
+    while (unit % spiir::kTcT != 0) unit += L.Tb;
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)4 << 30;
+    const int64_t budget = std::min<int64_t>((int64_t)16 << 30,
+                                             std::max<int64_t>((int64_t)1 << 30, (int64_t)(free_b / 4)));
+    const int64_t max_chunks = std::max<int64_t>(1, budget / (8 * per));
+    int64_t n_tile = std::max<int64_t>(unit, max_chunks * spiir::kTcT / unit * unit);
+    n_tile = std::min<int64_t>(n_tile, (n + unit - 1) / unit * unit);
+    const int64_t chunks = n_tile / spiir::kTcT;
+    if (b.tc_anchor_cap < chunks * per) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamSynchronize");
+        cudaFree(b.tc_anchor);
+        b.tc_anchor = nullptr;
+        if ((e = dalloc(&b.tc_anchor, (size_t)(chunks * per))) != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "anchor workspace")
+                                                  : cuda_fail(e, "cudaMalloc");
+        b.tc_anchor_cap = chunks * per;
+    }
+    const int64_t hq = L.Dh / spiir::kTcT;
+    st = ensure_tc_strain(b, spiir::tc_strain_bytes(chunks + hq, D), s);
+    if (st != SPIIR_OK) return st;
+    const int64_t tiles = (n + n_tile - 1) / n_tile;
+    a.n_seg = (int32_t)n_tile;
+    a.anchors = b.tc_anchor;
+    a.seg_count = 1;
+    a.peak_seg_stride = 0;
+    for (int64_t q = 0; q < tiles; ++q) {
+        const int64_t c_first = q * chunks;
+        const int64_t c_end = std::min<int64_t>(c_first + chunks, (n + spiir::kTcT - 1) / spiir::kTcT);
+        // windows c'' = c - q_l - 1 for chunks c of the tile, q_l <= hq
+        const int64_t n_cols = c_end - c_first + hq;
+        spiir::TcArgs t{};
+        t.W = b.tc_w;
+        t.B = b.tc_b;
+        t.ringoff = b.ringoff;
+        t.aT = b.tc_aT;
+        t.aT64 = b.tc_aT64;
+        t.state = b.state;
+        t.s64 = reinterpret_cast<double2 *>(b.state_ext);
+        t.anchors = b.tc_anchor;
+        t.n_slots = L.n_slots;
+        t.D = D;
+        t.Dh = (int32_t)L.Dh;
+        t.n_ntiles = (int32_t)((n_cols + spiir::tc_cols_per_tile() - 1) / spiir::tc_cols_per_tile());
+        t.col0 = (int32_t)(c_first - hq - 1);
+        t.c_first = (int32_t)c_first;
+        t.c_end = (int32_t)c_end;
+        t.c_full = (int32_t)(n / spiir::kTcT);
+        t.err = p->err;
+        t.wait_limit_ns = a.wait_limit_ns;
+        a.seg_first = (int32_t)q;
+        if ((e = spiir::launch_tc_strain(b.xe, b.xe_stride, (int)L.Dh, n, D, n_cols, t.col0,
+                                         b.tc_b, s)) != cudaSuccess)
+            return cuda_fail(e, "chunked tensor-core launch");
+        const int tt = time_begin(p, s);
+        if ((e = spiir::launch_tc_project(t, s)) != cudaSuccess)
+            return cuda_fail(e, "chunked tensor-core launch");
+        time_end(p, s, tt, kTimeTc);
+        const int tk = time_begin(p, s);
+        if ((e = spiir::launch_k1(a, L.n_units(), k1_smem(b, a), s)) != cudaSuccess)
+            return cuda_fail(e, "chunked tensor-core launch");
+        time_end(p, s, tk, kTimeK1);
+        p->last_launches += 3;
+    }
+    if (n % spiir::kTcT != 0) {   // the call ended inside a chunk
+        if ((e = spiir::launch_state_to_fp64(b.state, reinterpret_cast<double2 *>(b.state_ext),
+                                             per, s)) != cudaSuccess)
+            return cuda_fail(e, "end state launch");
+        p->last_launches += 1;
+    }
+    if (t0_advance != nullptr) {
+        if ((e = spiir::launch_advance(t0_advance, n, s)) != cudaSuccess)
+            return cuda_fail(e, "sample counter launch");
+        p->last_launches += 1;
+    }
+    p->last_segments = (int)tiles;
+    return SPIIR_OK;
+}
+
 spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cudaStream_t s,
                               int64_t *t0_advance = nullptr)
 {
+    if (p->precision == SPIIR_PREC_CHUNKED_TC) return launch_anchored(p, b, a, s, t0_advance);
     const spiir::Layout &L = b.lay;
     const int D = p->D;
     const int64_t per = (int64_t)D * L.n_slots;
@@ -700,8 +877,10 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
     cudaError_t e;
     if (t0_advance != nullptr) p->last_segments = std::max(P, 1);
     if (P <= 1) {
+        const int tk = time_begin(p, s);
         if ((e = spiir::launch_k1(a, L.n_units(), k1_smem(b, a), s)) != cudaSuccess)
             return cuda_fail(e, "filter kernel launch");
+        time_end(p, s, tk, kTimeK1);
         p->last_launches += 1;
         if (t0_advance != nullptr && (e = spiir::launch_advance(t0_advance, n, s)) != cudaSuccess)
             return cuda_fail(e, "sample counter launch");
@@ -729,35 +908,14 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
     a.n_seg = (int32_t)n_seg;
     if (tc) {
         // segment start states from the split-BF16 GEMM of chunk sums + scan
-        if (!b.tc_valid) {
-            if (!b.tc_w) {
-                if ((e = cudaMalloc(&b.tc_w, (size_t)spiir::tc_weight_bytes(L.n_slots))) !=
-                        cudaSuccess ||
-                    (e = dalloc(&b.tc_aT, (size_t)L.n_slots)) != cudaSuccess)
-                    return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "projection weights")
-                                                          : cuda_fail(e, "cudaMalloc");
-            }
-            if ((e = spiir::launch_tc_weights(b.params, b.ringoff, L.n_slots, (int)L.Dh, b.tc_w,
-                                              b.tc_aT, s)) != cudaSuccess)
-                return cuda_fail(e, "projection weights launch");
-            b.tc_valid = true;
-            p->last_launches += 1;
-        }
+        spiir_status st = ensure_tc_weights(p, b, s);
+        if (st != SPIIR_OK) return st;
         const int64_t cps = n_seg / spiir::kTcT;
         const int64_t c_last = (int64_t)(P - 1) * cps - 1;
         const int64_t hq = L.Dh / spiir::kTcT;
         const int64_t n_cols = c_last + hq + 1;
-        const int64_t need = spiir::tc_strain_bytes(n_cols, D);
-        if (b.tc_b_cap < need) {
-            if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
-                return cuda_fail(e, "cudaStreamSynchronize");
-            cudaFree(b.tc_b);
-            b.tc_b = nullptr;
-            if ((e = cudaMalloc(&b.tc_b, (size_t)need)) != cudaSuccess)
-                return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "projection workspace")
-                                                      : cuda_fail(e, "cudaMalloc");
-            b.tc_b_cap = need;
-        }
+        st = ensure_tc_strain(b, spiir::tc_strain_bytes(n_cols, D), s);
+        if (st != SPIIR_OK) return st;
         spiir::TcArgs t{};
         t.W = b.tc_w;
         t.B = b.tc_b;
@@ -768,16 +926,19 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         t.n_slots = L.n_slots;
         t.D = D;
         t.Dh = (int32_t)L.Dh;
-        t.n_ntiles = (int32_t)((n_cols + 127) / 128);
+        t.n_ntiles = (int32_t)((n_cols + spiir::tc_cols_per_tile() - 1) / spiir::tc_cols_per_tile());
         t.col0 = (int32_t)(-hq - 1);
         t.c_last = (int32_t)c_last;
         t.cps = (int32_t)cps;
         t.err = p->err;
         t.wait_limit_ns = a.wait_limit_ns;
         if ((e = spiir::launch_tc_strain(b.xe, b.xe_stride, (int)L.Dh, n, D, n_cols, t.col0,
-                                         b.tc_b, s)) != cudaSuccess ||
-            (e = spiir::launch_tc_project(t, s)) != cudaSuccess)
+                                         b.tc_b, s)) != cudaSuccess)
             return cuda_fail(e, "tensor-core projection launch");
+        const int tt = time_begin(p, s);
+        if ((e = spiir::launch_tc_project(t, s)) != cudaSuccess)
+            return cuda_fail(e, "tensor-core projection launch");
+        time_end(p, s, tt, kTimeTc);
     } else {
         // projection: segments 0..P-2 from zero state, no z, no peak
         spiir::K1Args proj = a;
@@ -787,8 +948,11 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         proj.peak_best = nullptr;
         proj.peak_idx = nullptr;
         proj.n_lower = 0;
-        if ((e = spiir::launch_k1(proj, L.n_units(), L.smem_bytes(), s)) != cudaSuccess ||
-            (e = spiir::launch_segment_carry(b.params, b.state, b.seg_end, b.seg_init, L.n_slots,
+        const int tk = time_begin(p, s);
+        if ((e = spiir::launch_k1(proj, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
+            return cuda_fail(e, "segment projection launch");
+        time_end(p, s, tk, kTimeK1);
+        if ((e = spiir::launch_segment_carry(b.params, b.state, b.seg_end, b.seg_init, L.n_slots,
                                              D, P, (int)n_seg, s)) != cudaSuccess)
             return cuda_fail(e, "segment projection launch");
     }
@@ -801,8 +965,10 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         a.peak_idx = b.seg_idx;
         a.peak_seg_stride = (int64_t)D * p->T;
     }
+    const int tk = time_begin(p, s);
     if ((e = spiir::launch_k1(a, L.n_units(), k1_smem(b, a), s)) != cudaSuccess)
         return cuda_fail(e, "filter kernel launch");
+    time_end(p, s, tk, kTimeK1);
     p->last_launches += 3 + ((best != nullptr || t0_advance != nullptr) ? 1 : 0);
     if (best != nullptr) {
         if ((e = spiir::launch_peak_merge(b.seg_best, b.seg_idx, P, (int64_t)D * p->T, best, idx,
@@ -1116,8 +1282,10 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     f.ckpt = b.ckpt;
     f.ckpt_blocks = Cc / L.Tb;
     f.n_det = D;
+    const int tf = time_begin(p, s);
     if ((e = spiir::launch_k1(f, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
         return cuda_fail(e, "adjoint forward launch");
+    time_end(p, s, tf, kTimeK1);
     // reverse pass
     if (!b.adj_tasks) {
         spiir_status st = build_adjoint_tasks(b, D);
@@ -1156,8 +1324,10 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     a.sub = b.adj_sub;
     if (spiir::k6_smem_bytes(Cc, L.Dh) > 227 * 1024)
         return fail(SPIIR_EUNSUPPORTED, "adjoint strain window above 227 KB of shared memory");
+    const int ta = time_begin(p, s);
     if ((e = spiir::launch_k6(a, b.adj_n_units, s)) != cudaSuccess)
         return cuda_fail(e, "adjoint kernel launch");
+    time_end(p, s, ta, kTimeAdj);
     if ((e = spiir::launch_adj_finalize(b.acc, b.slot_filter, L.n_slots, D,
                                         reinterpret_cast<float2 *>(grad_a_dev),
                                         reinterpret_cast<float2 *>(grad_b_dev), s)) !=
@@ -1293,6 +1463,36 @@ spiir_status spiir_state_set(spiir_plan *p, const float *state, const float *his
     p->t0 = samples;
     e = cudaMemcpy(p->t0_dev, &samples, sizeof(int64_t), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "sample counter copy");
+    return SPIIR_OK;
+}
+
+spiir_status spiir_kernel_times(spiir_plan *p, double *ms_out, int64_t *n_out)
+{
+    if (!p || !ms_out) return fail(SPIIR_EINVAL, "plan or ms is NULL");
+    double t[SPIIR_KERNEL_CLASSES] = {0.0, 0.0, 0.0};
+    int64_t c[SPIIR_KERNEL_CLASSES] = {0, 0, 0};
+    if (p->device >= 0 && !p->ev_used.empty()) {
+        DeviceGuard guard(p->device);
+        if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+        for (const auto &u : p->ev_used) {
+            cudaError_t e = cudaEventSynchronize(p->ev_pool[(size_t)u.first + 1]);
+            float ms = 0.f;
+            if (e == cudaSuccess)
+                e = cudaEventElapsedTime(&ms, p->ev_pool[(size_t)u.first],
+                                         p->ev_pool[(size_t)u.first + 1]);
+            if (e != cudaSuccess) {
+                p->ev_used.clear();
+                return cuda_fail(e, "kernel timing events");
+            }
+            t[u.second] += ms;
+            c[u.second] += 1;
+        }
+    }
+    p->ev_used.clear();
+    for (int k = 0; k < SPIIR_KERNEL_CLASSES; ++k) {
+        ms_out[k] = t[k];
+        if (n_out) n_out[k] = c[k];
+    }
     return SPIIR_OK;
 }
 

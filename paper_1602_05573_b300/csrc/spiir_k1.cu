@@ -318,6 +318,7 @@ template <int F> struct PackedLanes {
             zi[t] = si;
         }
     }
+    __device__ __forceinline__ void begin(const K1Args &, int) {}
     __device__ __forceinline__ void after8(const K1Args &, int) {}
     __device__ __forceinline__ void finish(const K1Args &, int) {}
     __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det,
@@ -419,6 +420,7 @@ template <int F> struct CompLanes {
             zi[t] = si;
         }
     }
+    __device__ __forceinline__ void begin(const K1Args &, int) {}
     __device__ __forceinline__ void after8(const K1Args &, int) {}
     __device__ __forceinline__ void finish(const K1Args &, int) {}
     __device__ __forceinline__ void store(const K1Args &A, int64_t pb, int warp, int lane, int det,
@@ -516,6 +518,7 @@ template <int F> struct ChunkLanes {
         }
     }
     // kend: samples of the call processed so far
+    __device__ __forceinline__ void begin(const K1Args &, int) {}
     __device__ __forceinline__ void after8(const K1Args &A, int kend)
     {
         if (kend % A.chunk == 0) carry();
@@ -541,6 +544,57 @@ template <int F> struct ChunkLanes {
                 make_double2(sr64[r], si64[r]);
     }
     __device__ __forceinline__ float2 state_of(int r) const { return make_float2(yr[r], yi[r]); }
+};
+
+// Chunked tensor-core form: plain FP32 lanes that restart, at every
+// kTcT-sample chunk start, from the chunk's anchor (the FP64-carried state of
+// the chunk scan, rounded once), so FP32 rounding never runs for more than
+// kTcT steps.  The next chunk's anchors are loaded a whole chunk ahead.
+template <int F> struct AnchorLanes : PackedLanes<F> {
+    using Base = PackedLanes<F>;
+    float2 nxt[F];
+    const float2 *arow = nullptr;   // this lane's anchor of round 0, chunk 0
+    int64_t rstride = 0, cstride = 0;
+    int nch = 0, ci = 0;
+
+    __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det,
+                                         const float2 *)
+    {
+        Base::load(A, pb, warp, lane, det, A.anchors);   // chunk 0: the segment's start
+        arow = A.anchors + (int64_t)det * A.n_slots + pb + (int64_t)warp * 32 + lane;
+        rstride = (int64_t)A.W * 32;
+        cstride = (int64_t)A.n_det * A.n_slots;
+    }
+    __device__ __forceinline__ void fetch()
+    {
+        if (ci < nch) {
+#pragma unroll
+            for (int r = 0; r < F; ++r) nxt[r] = arow[ci * cstride + r * rstride];
+        }
+    }
+    __device__ __forceinline__ void begin(const K1Args &, int n)
+    {
+        nch = (n + kTcT - 1) / kTcT;
+        ci = 1;
+        fetch();
+    }
+    // e: samples of the segment done
+    __device__ __forceinline__ void after8(const K1Args &, int e)
+    {
+        if (ci < nch && e == ci * kTcT) {
+#pragma unroll
+            for (int q = 0; q < Base::NP; ++q) {
+                this->YR[q] = pk(nxt[2 * q].x, nxt[2 * q + 1].x);
+                this->YI[q] = pk(nxt[2 * q].y, nxt[2 * q + 1].y);
+            }
+            if (Base::ODD) {
+                this->yr1 = nxt[F - 1].x;
+                this->yi1 = nxt[F - 1].y;
+            }
+            ++ci;
+            fetch();
+        }
+    }
 };
 
 // ---- running peak of one template: warp max, then merge with the plan's --
@@ -593,7 +647,7 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     const int64_t pb = A.group_pbase[g];
     // this CTA's time segment: call samples [s0, s0 + n) (SEG == false: the
     // whole call, and the segment arithmetic compiles away)
-    const int seg = SEG ? (int)(blockIdx.x / A.n_units) : 0;
+    const int seg = SEG ? A.seg_first + (int)(blockIdx.x / A.n_units) : 0;
     const int nseg_total = SEG ? (A.n + A.n_seg - 1) / A.n_seg : 1;
     const int s0 = SEG ? seg * A.n_seg : 0;
     const int n = SEG ? min(A.n_seg, A.n - s0) : A.n;
@@ -621,6 +675,7 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             !SEG ? A.state
                  : (A.zero_init ? nullptr : A.seg_init + (int64_t)seg * A.n_det * A.n_slots);
         L.load(A, pb, warp, lane, det, sin);
+        L.begin(A, n);
     }
     float *zrow = (A.z != nullptr && leader)
                       ? A.z + ((int64_t)det * A.T + tmpl) * 2 * A.z_len
@@ -825,6 +880,17 @@ __global__ void __launch_bounds__(256, 2) k1_chunked(const K1Args A)
                                          bar1);
 }
 
+__global__ void __launch_bounds__(256, 2) k1_anchored(const K1Args A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *ring, *zbuf;
+    uint32_t bar0, bar1;
+    cta_setup(smem, A, ring, zbuf, bar0, bar1);
+    const int u = (int)(blockIdx.x % A.n_units);
+    dispatch_f<AnchorLanes, kAnchorFcap, true, true>(A, A.units[2 * u], A.units[2 * u + 1], ring,
+                                                     zbuf, bar0, bar1);
+}
+
 __global__ void peak_out_kernel(const float *best, const int64_t *idx, int64_t count,
                                 float *out_abs, int64_t *out_idx)
 {
@@ -933,7 +999,9 @@ cudaError_t launch_kernel(Kernel k, const K1Args &a, int64_t n_units, int smem_b
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k), smem_bytes);
     if (e != cudaSuccess) return e;
     const int P = a.n_seg > 0 ? (a.n + a.n_seg - 1) / a.n_seg : 1;
-    const int P_launch = a.seg_end != nullptr ? P - 1 : P;   // the projection skips the last
+    const int P_launch = a.seg_count > 0 ? a.seg_count
+                         : a.seg_end != nullptr ? P - 1   // the projection skips the last
+                                                : P;
     if (P_launch <= 0) return cudaSuccess;
     k<<<(unsigned)(n_units * P_launch), a.W * 32, smem_bytes, s>>>(a);
     return cudaGetLastError();
@@ -953,6 +1021,10 @@ cudaError_t launch_k1_cap(const K1Args &a, int64_t n_units, int smem_bytes, cuda
 cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
 {
     if (n_units <= 0 || a.n <= 0) return cudaSuccess;
+    if (a.anchors != nullptr) {
+        if (a.fcap > kAnchorFcap || a.n_seg <= 0) return cudaErrorInvalidValue;
+        return launch_kernel(k1_anchored, a, n_units, smem_bytes, s);
+    }
     if (a.mode == kModeCompensated || a.mode == kModeChunked) {
         if (a.fcap > kPreciseFcap) return cudaErrorInvalidValue;
         return launch_kernel(a.mode == kModeCompensated ? k1_compensated : k1_chunked, a,

@@ -71,7 +71,16 @@ struct K1Args {
     void *state_ext;           // compensated: float4 [D][n_slots] (re hi, re lo, im hi, im lo);
                                // chunked: double2 [D][n_slots] FP64 anchor
     const double2 *aT;         // chunked: [n_slots] a^chunk in FP64 (kernel form)
+    // launches covering part of the segments: segments seg_first ..
+    // seg_first + seg_count - 1 (seg_count 0: all of them)
+    int32_t seg_first;
+    int32_t seg_count;
+    // chunked tensor-core form: the state before every kTcT-sample chunk of
+    // the launched segment, [chunks][D][n_slots]; lanes restart from it at each
+    // chunk start (null: not this form)
+    const float2 *anchors;
 };
+constexpr int kAnchorFcap = 8;   // filters per lane in the anchored kernel
 
 // Adjoint (reverse-time) kernel of one zero-state filter call.  Its work
 // unit is a task: kAdjRounds filter rounds (32 filters each) of one template
@@ -133,22 +142,34 @@ struct TcArgs {
     int64_t n_slots;
     int32_t D;
     int32_t Dh;
-    int32_t n_ntiles;          // column tiles of 128 windows
+    int32_t n_ntiles;          // column tiles of tc_cols_per_tile() windows
     int32_t col0;              // window of column 0: c'' = col + col0 = -(Dh / kTcT) - 1
     int32_t c_last;            // last chunk the scan needs ((P - 1) * cps - 1)
     int32_t cps;               // chunks per segment
     int32_t *err;              // bit 8: a wait timed out
     uint64_t wait_limit_ns;
+    // anchor mode (anchors != null): FP64 scan over chunks [c_first, c_end)
+    float2 *anchors;           // [c_end - c_first][D][n_slots] state before each chunk
+    double2 *s64;              // [D][n_slots] FP64 state, in: before c_first, out: after
+    const double2 *aT64;       // a^kTcT per slot in FP64
+    int32_t c_first;
+    int32_t c_end;
+    int32_t c_full;            // chunks below c_full are whole; they alone advance s64
 };
 int64_t tc_weight_bytes(int64_t n_slots);
 int64_t tc_strain_bytes(int64_t n_cols, int D);
+int tc_cols_per_tile();     // windows per column tile (TcArgs::n_ntiles counts these)
 // V_l (split BF16, tile layout) and a^kTcT for every slot of a band.
 cudaError_t launch_tc_weights(const float4 *params, const int2 *ringoff, int64_t n_slots, int Dh,
-                              unsigned char *W, float2 *aT, cudaStream_t s);
+                              unsigned char *W, float2 *aT, double2 *aT64, cudaStream_t s);
 // Strain windows of the call staged in xe, split BF16, tile layout.
 cudaError_t launch_tc_strain(const float *xe, int64_t xe_stride, int Dh, int64_t n, int D,
                              int64_t n_cols, int col0, unsigned char *B, cudaStream_t s);
-// GEMM + chunk scan: seg_init for every segment (segment 0 = state).
+// s64 = state (after a call that ended inside a chunk: the FP32 recompute of
+// that partial chunk is the end state).
+cudaError_t launch_state_to_fp64(const float2 *state, double2 *s64, int64_t count, cudaStream_t s);
+// GEMM + chunk scan: seg_init for every segment (segment 0 = state), or in
+// anchor mode the FP64-carried state before every chunk of [c_first, c_end).
 cudaError_t launch_tc_project(const TcArgs &a, cudaStream_t s);
 
 // Finalize running peaks into the caller's buffers (sqrt of |z|^2).

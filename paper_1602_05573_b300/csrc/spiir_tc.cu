@@ -24,8 +24,9 @@
 // (K-major, no swizzle: 8-row x 16-byte core matrices, K-direction core
 // stride 128 B, row-group stride 1024 B, 128 x 64 tiles of 16 KB), so each
 // tile arrives with one 1-D TMA bulk copy.  One CTA serves 128 GEMM rows
-// (64 filter slots) of one detector for the whole call: warp 4 issues the
-// copies (two stages) and the MMAs; warps 0-3 own TMEM lanes 0-127 and scan.
+// (64 filter slots) of one detector for the whole call, 256 windows per
+// accumulator (N = 256): warp 4 issues the copies (two stages) and the
+// MMAs; warps 0-3 own TMEM lanes 0-127 and scan.
 #include "spiir_kernels.h"
 #include "spiir_ptx.h"
 
@@ -38,11 +39,12 @@ namespace spiir {
 namespace {
 
 constexpr int kRowsTile = 128;                  // GEMM rows per CTA (64 slots x re/im)
-constexpr int kColsTile = 128;                  // windows per accumulator tile
+constexpr int kColsTile = 256;                  // windows per accumulator tile (TMEM columns)
 constexpr int kKBlk = 64;                       // K per staged block
 constexpr int kKBlocks = kTcK / kKBlk;          // 8
-constexpr uint32_t kTileBytes = 128u * kKBlk * 2u;   // 16 KB: 128 rows x 64 BF16
-constexpr uint32_t kStageBytes = 4u * kTileBytes;    // A hi, A lo, B hi, B lo
+constexpr uint32_t kTileBytes = 128u * kKBlk * 2u;   // 16 KB: 128 rows x 64 BF16 (A)
+constexpr uint32_t kBTileBytes = (uint32_t)kColsTile * kKBlk * 2u;   // B: 256 rows x 64
+constexpr uint32_t kStageBytes = 2u * kTileBytes + 2u * kBTileBytes;  // A hi, lo, B hi, lo
 constexpr int kStages = 2;
 constexpr int kEpiThreads = 128;
 
@@ -67,10 +69,44 @@ __device__ __forceinline__ void split_bf16(float v, uint16_t &hi, uint16_t &lo)
     lo = bf16_bits(v - bf16_val(hi));
 }
 
+// ---- float-float (hi + lo) arithmetic on the FP32 pipe ---------------------
+// Error-free transformations (Knuth's two-sum, the FMA two-product) keep the
+// carried state to ~2^-44 relative at FP32-pipe speed; B300's FP64 pipe is
+// a small fraction of its FP32 rate.
+struct ff {
+    float h, l;
+};
+__device__ __forceinline__ ff ff_from(double d)
+{
+    const float h = (float)d;
+    return {h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ ff ff_renorm(float s, float e)
+{
+    const float h = __fadd_rn(s, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return ff_renorm(p, e);
+}
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    return ff_renorm(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
+
 // ---- weights: V_l[m] for every slot, re and im rows -------------------------
 // One thread per (slot, group of 8 m).  a^p by binary powering in FP64.
 __global__ void tc_weights_kernel(const float4 *params, const int2 *ringoff, int64_t n_slots,
-                                  int Dh, unsigned char *W, float2 *aT)
+                                  int Dh, unsigned char *W, float2 *aT, double2 *aT64)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_slots * (kTcK / 8)) return;
@@ -146,6 +182,7 @@ __global__ void tc_weights_kernel(const float4 *params, const int2 *ringoff, int
             br = t;
         }
         aT[s] = make_float2((float)rr, (float)ri);
+        aT64[s] = make_double2(rr, ri);
     }
 }
 
@@ -174,14 +211,14 @@ __global__ void tc_strain_kernel(const float *xe, int64_t xe_stride, int Dh, int
     const int kb = m0 / kKBlk, kl = m0 % kKBlk;
     const int64_t n_ntiles = n_cols_pad / kColsTile;
     unsigned char *base =
-        B + (((int64_t)det * n_ntiles + nt) * kKBlocks + kb) * 2 * (int64_t)kTileBytes;
+        B + (((int64_t)det * n_ntiles + nt) * kKBlocks + kb) * 2 * (int64_t)kBTileBytes;
     uint4 v;
     v.x = h[0] | ((uint32_t)h[1] << 16); v.y = h[2] | ((uint32_t)h[3] << 16);
     v.z = h[4] | ((uint32_t)h[5] << 16); v.w = h[6] | ((uint32_t)h[7] << 16);
     *reinterpret_cast<uint4 *>(base + tile_off(rl, kl)) = v;
     v.x = l[0] | ((uint32_t)l[1] << 16); v.y = l[2] | ((uint32_t)l[3] << 16);
     v.z = l[4] | ((uint32_t)l[5] << 16); v.w = l[6] | ((uint32_t)l[7] << 16);
-    *reinterpret_cast<uint4 *>(base + kTileBytes + tile_off(rl, kl)) = v;
+    *reinterpret_cast<uint4 *>(base + kBTileBytes + tile_off(rl, kl)) = v;
 }
 
 // ---- tcgen05 helpers -------------------------------------------------------
@@ -227,31 +264,42 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 }
 
 // ---- projection: GEMM tile loop + chunk scan ---------------------------------
+// ANCH = false: FP32 scan from the call's start state, states written at the
+// segment starts (segmented plain calls).  ANCH = true: float-float scan
+// (~2^-44 relative, FP64-class) from the carried FP64 state over chunks
+// [c_first, c_end), the state before every chunk written as its anchor
+// (rounded to FP32) and the state after the last written back in FP64 (the
+// chunked tensor-core precision form).
+template <bool ANCH>
 __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[2 * kStages + 2];
+    __shared__ __align__(8) uint64_t bars[2 * kStages + 4];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t mt = blockIdx.x;
     const int det = blockIdx.y;
     const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[kStages]);
-    const uint32_t acc_full = smem_addr(&bars[2 * kStages]);
-    const uint32_t acc_empty = smem_addr(&bars[2 * kStages + 1]);
+    // two TMEM accumulators: the MMAs of column tile nt + 1 run while the
+    // epilogue reads tile nt
+    const uint32_t acc_full0 = smem_addr(&bars[2 * kStages]);
+    const uint32_t acc_empty0 = smem_addr(&bars[2 * kStages + 2]);
     if (tid == 0) {
         for (int st = 0; st < kStages; ++st) {
             mbar_init(full0 + 8 * st, 1);
             mbar_init(empty0 + 8 * st, 1);
         }
-        mbar_init(acc_full, 1);
-        mbar_init(acc_empty, kEpiThreads);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(acc_full0 + 8 * b, 1);
+            mbar_init(acc_empty0 + 8 * b, kEpiThreads);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
         asm volatile(
             "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                 smem_addr(&tmem_slot)),
-            "r"(kColsTile)
+            "r"(2 * kColsTile)
             : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -267,7 +315,7 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
             // producer + MMA issue, two stages
             const int total = n_ntiles * kKBlocks;
             const unsigned char *wt = A.W + mt * kKBlocks * 2 * (int64_t)kTileBytes;
-            const unsigned char *bt = A.B + (int64_t)det * n_ntiles * kKBlocks * 2 * kTileBytes;
+            const unsigned char *bt = A.B + (int64_t)det * n_ntiles * kKBlocks * 2 * kBTileBytes;
             auto fill = [&](int it) {
                 const int st = it % kStages;
                 const int nt = it / kKBlocks, kb = it % kKBlocks;
@@ -276,7 +324,7 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
                 mbar_expect_tx(full, kStageBytes);
                 bulk_g2s(dst, wt + (int64_t)kb * 2 * kTileBytes, 2 * kTileBytes, full);
                 bulk_g2s(dst + 2 * kTileBytes,
-                         bt + ((int64_t)nt * kKBlocks + kb) * 2 * kTileBytes, 2 * kTileBytes,
+                         bt + ((int64_t)nt * kKBlocks + kb) * 2 * kBTileBytes, 2 * kBTileBytes,
                          full);
             };
             // block it+1 is copied while the MMAs of block it run; a stage is
@@ -286,23 +334,25 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
                 const int st = it % kStages;
                 const int nt = it / kKBlocks, kb = it % kKBlocks;
                 ok = mbar_wait(full0 + 8 * st, (uint32_t)((it / kStages) & 1), A.wait_limit_ns);
-                if (ok && kb == 0 && nt > 0)   // epilogue has read the previous tile
-                    ok = mbar_wait(acc_empty, (uint32_t)((nt - 1) & 1), A.wait_limit_ns);
+                if (ok && kb == 0 && nt >= 2)   // epilogue has read tile nt - 2 (same TMEM)
+                    ok = mbar_wait(acc_empty0 + 8 * (nt & 1), (uint32_t)(((nt - 2) >> 1) & 1),
+                                   A.wait_limit_ns);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t s0 = smem_addr(smem) + st * kStageBytes;
+                const uint32_t acc = tmem + (uint32_t)((nt & 1) * kColsTile);
 #pragma unroll
                 for (int kk = 0; kk < kKBlk / 16; ++kk) {
                     const uint32_t adv = kk * 256u;   // 16 K = two core matrices
                     const uint64_t ah = umma_desc(s0 + adv), al = umma_desc(s0 + kTileBytes + adv);
                     const uint64_t bh = umma_desc(s0 + 2 * kTileBytes + adv);
-                    const uint64_t bl = umma_desc(s0 + 3 * kTileBytes + adv);
-                    umma_bf16(tmem, ah, bh, (kb > 0 || kk > 0) ? 1u : 0u);
-                    umma_bf16(tmem, ah, bl, 1u);
-                    umma_bf16(tmem, al, bh, 1u);
+                    const uint64_t bl = umma_desc(s0 + 2 * kTileBytes + kBTileBytes + adv);
+                    umma_bf16(acc, ah, bh, (kb > 0 || kk > 0) ? 1u : 0u);
+                    umma_bf16(acc, ah, bl, 1u);
+                    umma_bf16(acc, al, bh, 1u);
                 }
                 umma_commit(empty0 + 8 * st);          // stage free once these MMAs finish
-                if (kb == kKBlocks - 1) umma_commit(acc_full);
+                if (kb == kKBlocks - 1) umma_commit(acc_full0 + 8 * (nt & 1));
                 if (it + 1 < total) {
                     const int nx = it + 1, sx = nx % kStages;
                     if (nx >= kStages)
@@ -319,16 +369,28 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
         const int comp = row & 1;
         const int64_t slot = mt * (kRowsTile / 2) + (row >> 1);
         const bool valid = slot < A.n_slots;
+        const int64_t ds = (int64_t)det * A.n_slots + slot;
         float2 aT = make_float2(0.f, 0.f), s = make_float2(0.f, 0.f);
+        ff aTr = {0.f, 0.f}, aTi = {0.f, 0.f};
+        ff mine = {0.f, 0.f};   // ANCH: this thread's component of the carried state
         int q = 0;
         if (valid) {
-            aT = A.aT[slot];
-            s = A.state[(int64_t)det * A.n_slots + slot];
             q = (A.Dh - A.ringoff[slot].x) / kTcT;
-            if (comp == 0) A.seg_init[(int64_t)det * A.n_slots + slot] = s;
+            if (ANCH) {
+                const double2 a64 = A.aT64[slot];
+                aTr = ff_from(a64.x);
+                aTi = ff_from(a64.y);
+                const double2 s64 = A.s64[ds];
+                mine = ff_from(comp ? s64.y : s64.x);
+            } else {
+                aT = A.aT[slot];
+                s = A.state[ds];
+                if (comp == 0) A.seg_init[ds] = s;
+            }
         }
         for (int nt = 0; nt < n_ntiles; ++nt) {
-            ok = mbar_wait(acc_full, (uint32_t)(nt & 1), A.wait_limit_ns) && ok;
+            ok = mbar_wait(acc_full0 + 8 * (nt & 1), (uint32_t)((nt >> 1) & 1), A.wait_limit_ns) &&
+                 ok;
             if (!__all_sync(0xffffffffu, ok)) {
                 ok = false;
                 break;
@@ -342,28 +404,54 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]),
                       "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
                       "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+                    : "r"(tmem + ((uint32_t)(warp * 32) << 16) +
+                          (uint32_t)((nt & 1) * kColsTile + c0)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float mine = __uint_as_float(v[j]);
-                    const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
-                    const float gr = comp ? other : mine, gi = comp ? mine : other;
+                    const float g = __uint_as_float(v[j]);
                     // window c'' = col + col0 feeds chunk c = c'' + q + 1
                     const int64_t c = (int64_t)nt * kColsTile + c0 + j + A.col0 + q + 1;
-                    if (valid && c >= 0 && c <= A.c_last) {
-                        const float nr = fmaf(aT.x, s.x, fmaf(-aT.y, s.y, gr));
-                        const float ni = fmaf(aT.x, s.y, fmaf(aT.y, s.x, gi));
-                        s = make_float2(nr, ni);
-                        if ((c + 1) % A.cps == 0 && comp == 0) {
-                            const int64_t b = (c + 1) / A.cps;   // segment that starts here
-                            A.seg_init[(b * A.D + det) * A.n_slots + slot] = s;
+                    if (ANCH) {
+                        // each thread advances its own component; the other one
+                        // comes from the partner lane (Re <-> Im)
+                        const ff other = {__shfl_xor_sync(0xffffffffu, mine.h, 1),
+                                          __shfl_xor_sync(0xffffffffu, mine.l, 1)};
+                        if (valid && c >= A.c_first && c < A.c_end) {
+                            const ff sr = comp ? other : mine, si = comp ? mine : other;
+                            if (comp == 0)
+                                A.anchors[(c - A.c_first) * A.D * A.n_slots + ds] =
+                                    make_float2(__fadd_rn(sr.h, sr.l), __fadd_rn(si.h, si.l));
+                            if (c < A.c_full) {   // a partial last chunk only gets its anchor
+                                // Re: aTr sr - aTi si + g;  Im: aTr si + aTi sr + g
+                                const ff t = comp == 0 ? ff_add(ff_mul(aTr, sr), ff_mul(ff_neg(aTi), si))
+                                                       : ff_add(ff_mul(aTr, si), ff_mul(aTi, sr));
+                                mine = ff_add(t, ff{g, 0.f});
+                            }
+                        }
+                    } else {
+                        const float other = __shfl_xor_sync(0xffffffffu, g, 1);
+                        const float gr = comp ? other : g, gi = comp ? g : other;
+                        if (valid && c >= 0 && c <= A.c_last) {
+                            const float nr = fmaf(aT.x, s.x, fmaf(-aT.y, s.y, gr));
+                            const float ni = fmaf(aT.x, s.y, fmaf(aT.y, s.x, gi));
+                            s = make_float2(nr, ni);
+                            if ((c + 1) % A.cps == 0 && comp == 0) {
+                                const int64_t b = (c + 1) / A.cps;   // segment starting here
+                                A.seg_init[(b * A.D + det) * A.n_slots + slot] = s;
+                            }
                         }
                     }
                 }
             }
             tc_fence_before();
-            mbar_arrive(acc_empty);
+            mbar_arrive(acc_empty0 + 8 * (nt & 1));
+        }
+        if (ANCH) {   // carried FP64 state after the last chunk
+            const float oh = __shfl_xor_sync(0xffffffffu, mine.h, 1);
+            const float ol = __shfl_xor_sync(0xffffffffu, mine.l, 1);
+            if (ok && valid && comp == 0)
+                A.s64[ds] = make_double2((double)mine.h + (double)mine.l, (double)oh + (double)ol);
         }
         if (!ok && lane == 0) atomicOr(A.err, 8);
     }
@@ -371,11 +459,24 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(kColsTile)
+                     "r"(2 * kColsTile)
                      : "memory");
 }
 
+__global__ void state_to_fp64_kernel(const float2 *state, double2 *s64, int64_t count)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) s64[i] = make_double2(state[i].x, state[i].y);
+}
+
 }  // namespace
+
+cudaError_t launch_state_to_fp64(const float2 *state, double2 *s64, int64_t count, cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    state_to_fp64_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(state, s64, count);
+    return cudaGetLastError();
+}
 
 int64_t tc_weight_bytes(int64_t n_slots)
 {
@@ -386,18 +487,20 @@ int64_t tc_weight_bytes(int64_t n_slots)
 int64_t tc_strain_bytes(int64_t n_cols, int D)
 {
     const int64_t ntiles = (n_cols + kColsTile - 1) / kColsTile;
-    return (int64_t)D * ntiles * kKBlocks * 2 * (int64_t)kTileBytes;
+    return (int64_t)D * ntiles * kKBlocks * 2 * (int64_t)kBTileBytes;
 }
 
+int tc_cols_per_tile() { return kColsTile; }
+
 cudaError_t launch_tc_weights(const float4 *params, const int2 *ringoff, int64_t n_slots, int Dh,
-                              unsigned char *W, float2 *aT, cudaStream_t s)
+                              unsigned char *W, float2 *aT, double2 *aT64, cudaStream_t s)
 {
     cudaError_t e = cudaMemsetAsync(W, 0, (size_t)tc_weight_bytes(n_slots), s);
     if (e != cudaSuccess) return e;
     const int64_t threads = n_slots * (kTcK / 8);
     if (threads == 0) return cudaSuccess;
     tc_weights_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(params, ringoff, n_slots,
-                                                                         Dh, W, aT);
+                                                                         Dh, W, aT, aT64);
     return cudaGetLastError();
 }
 
@@ -415,11 +518,16 @@ cudaError_t launch_tc_strain(const float *xe, int64_t xe_stride, int Dh, int64_t
 cudaError_t launch_tc_project(const TcArgs &a, cudaStream_t s)
 {
     const int smem = kStages * (int)kStageBytes;
-    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(tc_project_kernel), smem);
+    const void *k = a.anchors != nullptr ? reinterpret_cast<const void *>(tc_project_kernel<true>)
+                                         : reinterpret_cast<const void *>(tc_project_kernel<false>);
+    cudaError_t e = ensure_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
     const int64_t mtiles = (2 * a.n_slots + kRowsTile - 1) / kRowsTile;
     if (mtiles == 0 || a.n_ntiles == 0) return cudaSuccess;
-    tc_project_kernel<<<dim3((unsigned)mtiles, (unsigned)a.D), 160, smem, s>>>(a);
+    if (a.anchors != nullptr)
+        tc_project_kernel<true><<<dim3((unsigned)mtiles, (unsigned)a.D), 160, smem, s>>>(a);
+    else
+        tc_project_kernel<false><<<dim3((unsigned)mtiles, (unsigned)a.D), 160, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -87,6 +87,28 @@ def test_bad_options_rejected():
         assert e.value.status in (sp.EINVAL, sp.EUNSUPPORTED)
 
 
+def test_chunked_tc_and_projection_options():
+    bank = make_bank(3, 300, (0.9, 0.99), 10, seed=1)
+    info = sp.Plan(bank, device=-1, precision="chunked_tc").info()
+    assert info["max_filters_per_lane"] <= 8      # the anchored kernel's cap
+    with pytest.raises(sp.SpiirError) as e:
+        sp.Plan(bank, device=-1, precision="chunked_tc", chunk_len=128)
+    assert e.value.status == sp.EINVAL
+    opt = sp.Options()
+    sp.library().spiir_options_default(ctypes.byref(opt))
+    opt.projection = 3
+    desc, keep = sp.bank_desc(bank)
+    h = ctypes.c_void_p()
+    assert sp.library().spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt),
+                                          ctypes.byref(h)) == sp.EINVAL
+
+
+def test_kernel_times_of_an_idle_plan_are_zero():
+    p = sp.Plan(make_bank(2, 8, (0.9, 0.99), 10, seed=1), device=-1, kernel_timing=True)
+    t = p.kernel_times()
+    assert all(ms == 0.0 and n == 0 for ms, n in t.values())
+
+
 def test_host_only_plan_refuses_compute():
     bank = make_bank(2, 8, (0.9, 0.99), 10, seed=1)
     p = sp.Plan(bank, device=-1)

@@ -3,6 +3,8 @@
 plain        complex FP32 state
 compensated  float-float state (two-product / two-sum), ~48-bit state
 chunked_fp64 FP32 inside 256-sample chunks, FP64 anchor carried across chunks
+chunked_tc   the chunk sums by split-BF16 tensor-core GEMM, FP64 chunk scan,
+             FP32 recompute inside each 256-sample chunk from its anchor
 
 On the precision-stress bank (poles 0.9999 <= |a| <= 0.999995, 2^20
 samples) the FP32 recurrence accumulates rounding over ~1/(1-|a|) steps; the
@@ -18,7 +20,7 @@ from spiir_inputs import make_bank, make_strain, workload_bank, workload_strain
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
-PRECISE = ["compensated", "chunked_fp64"]
+PRECISE = ["compensated", "chunked_fp64", "chunked_tc"]
 
 
 @pytest.fixture(scope="module")
@@ -90,4 +92,28 @@ def test_precision_workload_accuracy_table(sp):
             check_peaks(z, zref, pa, pi)
         del z
     print("\nmax relative |z| error, precision bank (64 templates x 2^20):", errs)
-    assert errs["compensated"] < errs["plain"] and errs["chunked_fp64"] < errs["plain"]
+    assert all(errs[p] < errs["plain"] for p in PRECISE)
+
+
+def test_chunked_tc_calls_ending_inside_a_chunk(sp):
+    """Call lengths that are not whole chunks: the end state of a partial
+    chunk comes from its FP32 recompute, and the stream stays within the bar."""
+    bank = make_bank(7, (40, 200), (0.999, 0.99999), 800, seed=146, n_det=2)
+    x = make_strain(2, 7000, seed=147)
+    z, pa, pi, _ = run(sp, bank, x, "chunked_tc", chunks=[1000, 77, 2600])
+    zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
+    rel, _ = rel_errors(z, zref)
+    assert rel.max() <= REL_TOL, rel.max()
+    check_peaks(z, zref, pa, pi)
+
+
+def test_chunked_tc_multirate(sp):
+    from spiir_inputs import make_multirate_bank
+    bank = make_multirate_bank(10, (60, 120, 120), (1, 4, 16), (0.99, 0.9995), 1024, 148)
+    x = make_strain(1, 40000, seed=149)
+    z, pa, pi, _ = run(sp, bank, x, "chunked_tc")
+    zref, _, _ = oracle.filter_multirate(bank.off, bank.a, bank.b, bank.d, bank.band_of,
+                                         bank.decim, x)
+    rel, _ = rel_errors(z, zref)
+    assert rel.max() <= REL_TOL, rel.max()
+    check_peaks(z, zref, pa, pi)
