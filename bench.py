@@ -58,6 +58,8 @@ def parse():
                     help="let the plan time candidate layouts on its first call")
     ap.add_argument("--samples", type=int, default=0,
                     help="override the stream length per step (profiling runs)")
+    ap.add_argument("--templates", type=int, default=0,
+                    help="keep only the bank's first N templates (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -246,6 +248,8 @@ def run_ours(args, rank, world, local_rank):
     dev = torch.device("cuda", local_rank)
 
     bank = shard_bank(args.workload, rank)
+    if args.templates:
+        bank = bank.subset(list(range(min(args.templates, bank.n_templates))))
     x_host = workload_strain(args.workload, args.samples or None)
     n = x_host.shape[1]
     T, D = bank.n_templates, bank.n_det
