@@ -47,8 +47,10 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
     const int nsub_max = A.Cc / kAdjSub;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = A.units[2 * blockIdx.x];
-    const int det = A.units[2 * blockIdx.x + 1];
+    const int seg = (int)(blockIdx.x / A.n_units);
+    const int u = (int)(blockIdx.x % A.n_units);
+    const int g = A.units[2 * u];
+    const int det = A.units[2 * u + 1];
     const int4 task = A.tasks[(int64_t)g * A.W + warp];
     const bool half = A.G == 16;                      // lanes 16..31 serve task.w
     const bool active = task.z >= 0;
@@ -56,11 +58,13 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
     const int nr = task.y;                   // rounds in this task (<= R)
     const int n = A.n;
     const int nc = (n + A.Cc - 1) / A.Cc;
+    const int c_lo = seg * A.cps;                     // this CTA's chunks [c_lo, c_hi)
+    const int c_hi = min(nc, c_lo + A.cps);
     const float *xrow = A.xe + (int64_t)det * A.xe_stride;
     const float2 *grow = tmpl >= 0 ? A.gz + ((int64_t)det * A.T + tmpl) * n : nullptr;
     const int gsrc = half ? (lane & 16) : 0;          // lane holding this lane's g_z
     float2 *wsub = A.sub + ((int64_t)blockIdx.x * A.W + warp) * R * nsub_max * 32;
-    float *acc_det = A.acc + (int64_t)det * A.n_slots * 6;
+    float *acc_det = A.acc + ((int64_t)seg * A.n_det + det) * A.n_slots * 6;
 
     // this lane's filters: slot of round i = task.x + i * task.w (task.w = 32 * layout warps)
     int64_t slot[R];
@@ -83,9 +87,16 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
     }
     float mr[R], mi[R], gar[R], gai[R], gbr[R], gbi[R];
 #pragma unroll
-    for (int i = 0; i < R; ++i) mr[i] = mi[i] = gar[i] = gai[i] = gbr[i] = gbi[i] = 0.f;
+    for (int i = 0; i < R; ++i) {
+        mr[i] = mi[i] = gar[i] = gai[i] = gbr[i] = gbi[i] = 0.f;
+        if (A.mu_end != nullptr && active && i < nr) {   // adjoint state after the segment
+            const float2 m = A.mu_end[((int64_t)seg * A.n_det + det) * A.n_slots + slot[i]];
+            mr[i] = m.x;
+            mi[i] = m.y;
+        }
+    }
 
-    for (int c = nc - 1; c >= 0; --c) {
+    for (int c = c_hi - 1; c >= c_lo; --c) {
         const int kc = c * A.Cc;
         const int cv = min(A.Cc, n - kc);
         // strain x[kc - Dh + i] = xe[kc + i] (xe holds Dh zeros before x)
@@ -212,7 +223,7 @@ __global__ void adj_finalize(const float *acc, const int64_t *slot_filter, int64
     const int64_t f = slot_filter[s];
     if (f < 0) return;
     float2 a = make_float2(0.f, 0.f), b = make_float2(0.f, 0.f);
-    for (int d = 0; d < D; ++d) {
+    for (int d = 0; d < D; ++d) {   // D here counts (segment, detector) rows
         const float *p = acc + ((int64_t)d * n_slots + s) * 6;
         a.x += p[2];
         a.y += p[3];
@@ -221,6 +232,72 @@ __global__ void adj_finalize(const float *acc, const int64_t *slot_filter, int64
     }
     ga[f] = a;
     gb[f] = b;
+}
+
+// E[q] for q = 1..P-1: one thread per (segment, detector, slot), natural form
+// (mu <- g_z + conj(a) mu, as in the reverse pass)
+__global__ void adj_project_kernel(const float4 *params, const int32_t *slot_tmpl,
+                                   const float2 *gz, int64_t n_slots, int D, int64_t T, int64_t n,
+                                   int64_t seg_len, int P, float2 *E)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)D * n_slots;
+    if (i >= (int64_t)(P - 1) * per) return;
+    const int q = 1 + (int)(i / per);
+    const int64_t ds = i % per;
+    const int det = (int)(ds / n_slots);
+    const int64_t s = ds % n_slots;
+    const int tmpl = slot_tmpl[s];
+    float mr = 0.f, mi = 0.f;
+    if (tmpl >= 0) {
+        const float4 p = params[s];
+        const float ar = p.x, ai = (s & 1) ? -p.y : p.y;   // odd slots store conj(a)
+        const float2 *g = gz + ((int64_t)det * T + tmpl) * n;
+        const int64_t j0 = (int64_t)q * seg_len, j1 = min(n, j0 + seg_len);
+        for (int64_t j = j1 - 1; j >= j0; --j) {
+            const float2 G = g[j];
+            const float nr = G.x + fmaf(ar, mr, ai * mi);
+            const float ni = G.y + fmaf(ar, mi, -ai * mr);
+            mr = nr;
+            mi = ni;
+        }
+    }
+    E[(int64_t)q * per + ds] = make_float2(mr, mi);
+}
+
+// mu_end[P-1] = 0; mu_end[q] = E[q+1] + conj(a)^len(q+1) mu_end[q+1] (FP64)
+__global__ void adj_carry_kernel(const float4 *params, const float2 *E, int64_t n_slots, int D,
+                                 int64_t n, int64_t seg_len, int P, float2 *mu_end)
+{
+    const int64_t ds = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)D * n_slots;
+    if (ds >= per) return;
+    const int64_t s = ds % n_slots;
+    const float4 p = params[s];
+    const double ar = p.x, ai = (s & 1) ? -(double)p.y : (double)p.y;
+    double mr = 0.0, mi = 0.0;
+    mu_end[(int64_t)(P - 1) * per + ds] = make_float2(0.f, 0.f);
+    for (int q = P - 2; q >= 0; --q) {
+        const int64_t len = min(seg_len, n - (int64_t)(q + 1) * seg_len);
+        // conj(a)^len by binary powering
+        double br = ar, bi = -ai, rr = 1.0, ri = 0.0;
+        for (int64_t e = len; e > 0; e >>= 1) {
+            if (e & 1) {
+                const double t = rr * br - ri * bi;
+                ri = rr * bi + ri * br;
+                rr = t;
+            }
+            const double t = br * br - bi * bi;
+            bi = 2.0 * br * bi;
+            br = t;
+        }
+        const float2 e = E[(int64_t)(q + 1) * per + ds];
+        const double nr = (double)e.x + rr * mr - ri * mi;
+        const double ni = (double)e.y + rr * mi + ri * mr;
+        mr = nr;
+        mi = ni;
+        mu_end[(int64_t)q * per + ds] = make_float2((float)mr, (float)mi);
+    }
 }
 
 __global__ void set_coefficients(const float2 *a, const float2 *b, const int64_t *slot_filter,
@@ -242,20 +319,42 @@ int k6_smem_bytes(int Cc, int Dh) { return (int)(2 * sizeof(float) * (Dh + Cc));
 
 cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s)
 {
-    if (n_units <= 0 || a.n <= 0) return cudaSuccess;
+    if (n_units <= 0 || a.n <= 0 || a.cps <= 0 || a.n_units != n_units)
+        return n_units <= 0 || a.n <= 0 ? cudaSuccess : cudaErrorInvalidValue;
     const int smem = k6_smem_bytes(a.Cc, a.Dh);
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k6_adjoint), smem);
     if (e != cudaSuccess) return e;
-    k6_adjoint<<<(unsigned)n_units, a.W * 32, smem, s>>>(a);
+    const int64_t nc = (a.n + a.Cc - 1) / a.Cc;
+    const int64_t P = (nc + a.cps - 1) / a.cps;
+    k6_adjoint<<<(unsigned)(n_units * P), a.W * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adj_finalize(const float *acc, const int64_t *slot_filter, int64_t n_slots,
-                                int D, float2 *ga, float2 *gb, cudaStream_t s)
+                                int D, int P, float2 *ga, float2 *gb, cudaStream_t s)
 {
     if (n_slots <= 0) return cudaSuccess;
-    adj_finalize<<<(unsigned)((n_slots + 255) / 256), 256, 0, s>>>(acc, slot_filter, n_slots, D,
-                                                                    ga, gb);
+    // the accumulator rows of all segments and detectors are summed alike
+    adj_finalize<<<(unsigned)((n_slots + 255) / 256), 256, 0, s>>>(acc, slot_filter, n_slots,
+                                                                    D * P, ga, gb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_project(const float4 *params, const int32_t *slot_tmpl, const float2 *gz,
+                               int64_t n_slots, int D, int64_t T, int64_t n, int64_t seg_len,
+                               int P, float2 *E, float2 *mu_end, cudaStream_t s)
+{
+    const int64_t per = (int64_t)D * n_slots;
+    if (per <= 0 || P < 1) return cudaSuccess;
+    if (P > 1) {
+        const int64_t th = (int64_t)(P - 1) * per;
+        adj_project_kernel<<<(unsigned)((th + 127) / 128), 128, 0, s>>>(
+            params, slot_tmpl, gz, n_slots, D, T, n, seg_len, P, E);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    adj_carry_kernel<<<(unsigned)((per + 63) / 64), 64, 0, s>>>(params, E, n_slots, D, n, seg_len,
+                                                                 P, mu_end);
     return cudaGetLastError();
 }
 

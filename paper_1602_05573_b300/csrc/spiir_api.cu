@@ -168,8 +168,12 @@ struct Band {
     int32_t *adj_units = nullptr;
     int64_t adj_n_units = 0;
     int adj_W = 4;
-    float2 *adj_sub = nullptr;     // [adj_n_units][adj_W][kAdjRounds][Cc/kAdjSub][32]
+    float2 *adj_sub = nullptr;     // [P][adj_n_units][adj_W][kAdjRounds][Cc/kAdjSub][32]
     int64_t adj_sub_cap = 0;
+    int32_t *adj_slot_tmpl = nullptr; // template of every slot (-1 padding)
+    float2 *adj_E = nullptr;       // [P][D][n_slots] reverse projection, segment starts
+    float2 *adj_mu = nullptr;      // [P][D][n_slots] adjoint state after each segment
+    int adj_seg_cap = 0;           // segments adj_E / adj_mu / acc hold
 };
 
 struct spiir_plan {
@@ -263,6 +267,9 @@ void free_band(Band &b)
     cudaFree(b.adj_tasks);
     cudaFree(b.adj_units);
     cudaFree(b.adj_sub);
+    cudaFree(b.adj_slot_tmpl);
+    cudaFree(b.adj_E);
+    cudaFree(b.adj_mu);
     b = Band();
 }
 
@@ -921,7 +928,7 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         t.B = b.tc_b;
         t.ringoff = b.ringoff;
         t.aT = b.tc_aT;
-        t.state = b.state;
+        t.state = a.state;   // the call's start state (the plan's, or the adjoint's zero state)
         t.seg_init = b.seg_init;
         t.n_slots = L.n_slots;
         t.D = D;
@@ -932,7 +939,7 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         t.cps = (int32_t)cps;
         t.err = p->err;
         t.wait_limit_ns = a.wait_limit_ns;
-        if ((e = spiir::launch_tc_strain(b.xe, b.xe_stride, (int)L.Dh, n, D, n_cols, t.col0,
+        if ((e = spiir::launch_tc_strain(a.xe, a.xe_stride, (int)L.Dh, n, D, n_cols, t.col0,
                                          b.tc_b, s)) != cudaSuccess)
             return cuda_fail(e, "tensor-core projection launch");
         const int tt = time_begin(p, s);
@@ -952,7 +959,7 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         if ((e = spiir::launch_k1(proj, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
             return cuda_fail(e, "segment projection launch");
         time_end(p, s, tk, kTimeK1);
-        if ((e = spiir::launch_segment_carry(b.params, b.state, b.seg_end, b.seg_init, L.n_slots,
+        if ((e = spiir::launch_segment_carry(b.params, a.state, b.seg_end, b.seg_init, L.n_slots,
                                              D, P, (int)n_seg, s)) != cudaSuccess)
             return cuda_fail(e, "segment projection launch");
     }
@@ -1203,8 +1210,12 @@ spiir_status build_adjoint_tasks(Band &b, int D)
             units[2 * (g * D + d)] = (int32_t)g;
             units[2 * (g * D + d) + 1] = d;
         }
+    std::vector<int32_t> stmpl(L.slot_template.begin(), L.slot_template.end());
     cudaError_t e;
-    if ((e = dalloc(&b.adj_tasks, (size_t)n_groups * b.adj_W)) != cudaSuccess ||
+    if ((e = dalloc(&b.adj_slot_tmpl, stmpl.size())) != cudaSuccess ||
+        (e = cudaMemcpy(b.adj_slot_tmpl, stmpl.data(), stmpl.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = dalloc(&b.adj_tasks, (size_t)n_groups * b.adj_W)) != cudaSuccess ||
         (e = dalloc(&b.adj_units, units.size())) != cudaSuccess ||
         (e = cudaMemcpy(b.adj_tasks, tasks.data(), tasks.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -1257,7 +1268,37 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     }
     if (!b.bw_state) {
         if ((e = dalloc(&b.bw_state, (size_t)D * L.n_slots)) != cudaSuccess) return oom(e);
-        if ((e = dalloc(&b.acc, (size_t)D * L.n_slots * 6)) != cudaSuccess) return oom(e);
+    }
+    if (!b.adj_tasks) {
+        spiir_status st = build_adjoint_tasks(b, D);
+        if (st != SPIIR_OK) return st;
+    }
+    // time segments of whole chunks for the reverse pass (options.time_segments,
+    // or enough CTAs for about four waves of 16 warps per SM, at most 16
+    // segments), each at least one chunk
+    int P = 1;
+    {
+        const int64_t warps = b.adj_n_units * b.adj_W;
+        const int req = p->opt.time_segments;
+        if (req >= 1) P = req;
+        else P = (int)std::min<int64_t>(16, std::max<int64_t>(1, (64 * (int64_t)p->n_sm + warps - 1) / warps));
+        P = (int)std::max<int64_t>(1, std::min<int64_t>(P, nc));
+    }
+    const int64_t cps = (nc + P - 1) / P;
+    P = (int)((nc + cps - 1) / cps);
+    if (b.adj_seg_cap < P) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamSynchronize");
+        cudaFree(b.acc);
+        cudaFree(b.adj_E);
+        cudaFree(b.adj_mu);
+        b.acc = nullptr;
+        b.adj_E = b.adj_mu = nullptr;
+        if ((e = dalloc(&b.acc, (size_t)P * D * L.n_slots * 6)) != cudaSuccess ||
+            (e = dalloc(&b.adj_E, (size_t)P * D * L.n_slots)) != cudaSuccess ||
+            (e = dalloc(&b.adj_mu, (size_t)P * D * L.n_slots)) != cudaSuccess)
+            return oom(e);
+        b.adj_seg_cap = P;
     }
     // zero history + x, zero state and accumulators, zero g_x
     if ((e = cudaMemset2DAsync(b.bw_xe, b.bw_xe_stride * 4, 0, (size_t)L.Dh * 4, D, s)) !=
@@ -1266,7 +1307,7 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
                                cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
         (e = cudaMemsetAsync(b.bw_state, 0, sizeof(float2) * (size_t)D * L.n_slots, s)) !=
             cudaSuccess ||
-        (e = cudaMemsetAsync(b.acc, 0, sizeof(float) * 6 * (size_t)D * L.n_slots, s)) !=
+        (e = cudaMemsetAsync(b.acc, 0, sizeof(float) * 6 * (size_t)P * D * L.n_slots, s)) !=
             cudaSuccess ||
         (grad_x_dev &&
          (e = cudaMemsetAsync(grad_x_dev, 0, sizeof(float) * (size_t)D * n, s)) != cudaSuccess))
@@ -1282,16 +1323,28 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     f.ckpt = b.ckpt;
     f.ckpt_blocks = Cc / L.Tb;
     f.n_det = D;
-    const int tf = time_begin(p, s);
-    if ((e = spiir::launch_k1(f, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
-        return cuda_fail(e, "adjoint forward launch");
-    time_end(p, s, tf, kTimeK1);
-    // reverse pass
-    if (!b.adj_tasks) {
-        spiir_status st = build_adjoint_tasks(b, D);
+    p->last_launches = 0;
+    if (p->precision == SPIIR_PREC_PLAIN) {
+        // time-segmented like a plain call when the bank is small (checkpoints
+        // are written at whole intervals from the call's start either way)
+        const int saved = p->last_segments;
+        spiir_status st = launch_segmented(p, b, f, segments_for(p, b, n), s);
+        p->last_segments = saved;
         if (st != SPIIR_OK) return st;
+    } else {
+        const int tf = time_begin(p, s);
+        if ((e = spiir::launch_k1(f, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
+            return cuda_fail(e, "adjoint forward launch");
+        time_end(p, s, tf, kTimeK1);
+        p->last_launches += 1;
     }
-    const int64_t sub_need = b.adj_n_units * b.adj_W * spiir::kAdjRounds *
+    // reverse pass: projection of the adjoint state to segment ends, then
+    // every segment's reverse pass at once
+    if ((e = spiir::launch_adj_project(b.params, b.adj_slot_tmpl,
+                                       reinterpret_cast<const float2 *>(grad_z_dev), L.n_slots, D,
+                                       p->T, n, cps * Cc, P, b.adj_E, b.adj_mu, s)) != cudaSuccess)
+        return cuda_fail(e, "adjoint projection launch");
+    const int64_t sub_need = (int64_t)P * b.adj_n_units * b.adj_W * spiir::kAdjRounds *
                              (Cc / spiir::kAdjSub) * 32;
     if (b.adj_sub_cap < sub_need) {
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -1322,18 +1375,22 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     a.acc = b.acc;
     a.gx = grad_x_dev;
     a.sub = b.adj_sub;
+    a.n_units = (int32_t)b.adj_n_units;
+    a.cps = (int32_t)cps;
+    a.mu_end = P > 1 ? b.adj_mu : nullptr;
     if (spiir::k6_smem_bytes(Cc, L.Dh) > 227 * 1024)
         return fail(SPIIR_EUNSUPPORTED, "adjoint strain window above 227 KB of shared memory");
     const int ta = time_begin(p, s);
     if ((e = spiir::launch_k6(a, b.adj_n_units, s)) != cudaSuccess)
         return cuda_fail(e, "adjoint kernel launch");
     time_end(p, s, ta, kTimeAdj);
-    if ((e = spiir::launch_adj_finalize(b.acc, b.slot_filter, L.n_slots, D,
+    if ((e = spiir::launch_adj_finalize(b.acc, b.slot_filter, L.n_slots, D, P,
                                         reinterpret_cast<float2 *>(grad_a_dev),
                                         reinterpret_cast<float2 *>(grad_b_dev), s)) !=
         cudaSuccess)
         return cuda_fail(e, "adjoint finalize launch");
-    p->last_launches = 3;   // checkpointed forward, reverse pass, finalize
+    // forward launches (counted above), projection (+ carry), reverse pass, finalize
+    p->last_launches += (P > 1 ? 2 : 1) + 2;
     return SPIIR_OK;
 }
 

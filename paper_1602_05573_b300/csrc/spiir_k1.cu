@@ -741,9 +741,11 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
                 for (int cc = 1; cc < A.C; ++cc) c += off >= (uint32_t)cc * cs4 ? 1u : 0u;
                 if (off - c * cs4 >= r4) ad[r] -= r4;
             }
-            // checkpoint of the filter state (for the adjoint's recompute)
-            if (A.ckpt != nullptr && (j + 1) % A.ckpt_blocks == 0 && j + 1 < nblk) {
-                const int64_t c = (j + 1) / A.ckpt_blocks;
+            // checkpoint of the filter state (for the adjoint's recompute), at
+            // whole multiples of the interval from the call's start
+            const int gblk = sblk + j + 1;
+            if (A.ckpt != nullptr && gblk % A.ckpt_blocks == 0 && (int64_t)gblk * A.Tb < A.n) {
+                const int64_t c = gblk / A.ckpt_blocks;
                 float2 *row = A.ckpt + (c * A.n_det + det) * A.n_slots;
 #pragma unroll
                 for (int r = 0; r < F; ++r)

@@ -104,19 +104,31 @@ struct K6Args {
     const float2 *ckpt;        // [nc][D][n_slots] from the forward pass
     int64_t n_slots;
     int32_t n_det;
-    float *acc;                // [D][n_slots][6] (mu re, im, g_a re, im, g_b re, im)
+    float *acc;                // [P][D][n_slots][6] (mu re, im, g_a re, im, g_b re, im)
     float *gx;                 // [D][n] accumulated with atomics, or null
-    float2 *sub;               // [n_units][W][kAdjRounds][Cc / kAdjSub][32] workspace
+    float2 *sub;               // [P][n_units][W][kAdjRounds][Cc / kAdjSub][32] workspace
+    // time segments of whole chunks: CTA b serves unit b % n_units over the
+    // chunks of segment b / n_units, from mu at the segment's end (null: 0)
+    int32_t n_units;
+    int32_t cps;               // chunks per segment
+    const float2 *mu_end;      // [P][D][n_slots] natural form
 };
 constexpr int kAdjSub = 16;    // samples per recomputed span in the adjoint
 constexpr int kAdjRounds = 2;  // filter rounds per adjoint task (independent chains per lane)
 
 cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s);
+// Reverse projection for time-segmented adjoints: for segments q = 1..P-1 of
+// seg_len samples, the adjoint state at the segment's first sample from a
+// zero state at its end, E[q][det][slot]; then mu_end[q] (the state at the
+// start of segment q + 1) for every q, carried backwards in FP64.
+cudaError_t launch_adj_project(const float4 *params, const int32_t *slot_tmpl, const float2 *gz,
+                               int64_t n_slots, int D, int64_t T, int64_t n, int64_t seg_len,
+                               int P, float2 *E, float2 *mu_end, cudaStream_t s);
 // smem bytes the adjoint kernel needs
 int k6_smem_bytes(int Cc, int Dh);
 // g_a[f] = sum_det acc[det][s].ga, g_b likewise, for every slot s holding filter f
 cudaError_t launch_adj_finalize(const float *acc, const int64_t *slot_filter, int64_t n_slots,
-                                int D, float2 *ga, float2 *gb, cudaStream_t s);
+                                int D, int P, float2 *ga, float2 *gb, cudaStream_t s);
 // params[s] = kernel form of (a[f], b[f]) for every slot s holding filter f
 cudaError_t launch_set_coefficients(const float2 *a, const float2 *b,
                                     const int64_t *slot_filter, int64_t n_slots,

@@ -122,3 +122,20 @@ def test_autograd_function_and_a_fitting_step(sp):
         b2 = b - 1e-3 * b.grad / b.grad.abs().max() * b.abs().max()
         loss2 = torch.sum(torch.abs(sp.spiir_filter(x, a.detach(), b2, plan) - z_t) ** 2)
     assert float(loss2) < float(loss.detach())
+
+
+@pytest.mark.parametrize("P", [1, 3, 5])
+def test_adjoint_time_segments(sp, P):
+    """The reverse pass split into P time segments of whole checkpoint
+    intervals (each from the adjoint state projected to its end) gives the
+    oracle's gradients."""
+    bank = make_bank(6, (40, 160), (0.995, 0.9999), 900, seed=120, n_det=2)
+    n = 9000
+    x = make_strain(2, n, seed=121)
+    rng = np.random.default_rng(122)
+    gz = (rng.standard_normal((2, 6, n)) + 1j * rng.standard_normal((2, 6, n))).astype(np.complex64)
+    ga, gb, gx = gpu_backward(sp, bank, x, gz, time_segments=P)
+    ra, rb, rx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, gz)
+    assert rel_inf(ga, ra) <= GRAD_TOL
+    assert rel_inf(gb, rb) <= GRAD_TOL
+    assert rel_inf(gx, rx) <= GRAD_TOL
