@@ -630,7 +630,7 @@ __device__ __forceinline__ void warp_peak_merge(const K1Args &A, float *peak_bes
 // SEG: the CTA serves one time segment of the call; LOW: the call adds lower
 // bands (multirate top band).  Both are compile-time so the plain single-band
 // kernel carries neither's code.
-template <template <int> class LANES, int F, bool SEG, bool LOW>
+template <template <int> class LANES, int F, bool SEG, bool LOW, int U>
 __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float *ring,
                                          float *zbuf, uint32_t bar0, uint32_t bar1)
 {
@@ -719,7 +719,25 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
         }
         if (active) {
             float *zw = zb + (int64_t)warp * per_warp * A.Tb * 2;
-            for (int sb = 0; sb < nv; sb += kTS) {
+            // few filters per lane (and registers to spare): U whole steps
+            // before their U cross-lane sums, whose shuffle chains then overlap
+            int sb = 0;
+            if (U > 1) {
+                for (; sb + U * kTS <= nv; sb += U * kTS) {
+                    float zr[U][kTS], zi[U][kTS];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        L.template step8<true>(ad, kTS, zr[u], zi[u]);
+                        L.after8(A, j * A.Tb + sb + (u + 1) * kTS);
+#pragma unroll
+                        for (int r = 0; r < F; ++r) ad[r] += 4u * kTS;
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+                        warp_sum8(zr[u], zi[u], lane, zw + 2 * (sb + u * kTS), half, A.Tb);
+                }
+            }
+            for (; sb < nv; sb += kTS) {
                 const int valid = nv - sb;
                 float zr[kTS], zi[kTS];
                 if (valid >= kTS)
@@ -813,22 +831,29 @@ template <> struct K1Bounds<6> { static constexpr int kMinBlocks = 2; };
 template <> struct K1Bounds<8> { static constexpr int kMinBlocks = 2; };
 template <> struct K1Bounds<10> { static constexpr int kMinBlocks = 2; };
 
+// Steps per cross-lane-sum batch for F filters per lane in a kernel compiled
+// for FCAP (only the 128-register kernels have room for several).
+__host__ __device__ constexpr int unroll_for(int FCAP, int F)
+{
+    return FCAP >= 6 ? (F <= 2 ? 4 : (F <= 4 ? 2 : 1)) : 1;
+}
+
 // The CTA's F is uniform, so every warp takes the same case.
 template <template <int> class LANES, int FCAP, bool SEG, bool LOW>
 __device__ __forceinline__ void dispatch_f(const K1Args &A, int g, int det, float *ring,
                                            float *zbuf, uint32_t bar0, uint32_t bar1)
 {
     const int F = A.group_F[g];
-    if (F == 1) run_unit<LANES, 1, SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1), SEG, LOW>(A, g, det, ring, zbuf, bar0, bar1);
+    if (F == 1) run_unit<LANES, 1, SEG, LOW, unroll_for(FCAP, 1)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 2 ? 2 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 3 ? 3 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 4 ? 4 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 5 ? 5 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 6 ? 6 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 7 ? 7 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 8 ? 8 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 9 ? 9 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 10 ? 10 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
     else if (threadIdx.x == 0) atomicOr(A.err, 4);
 }
 
