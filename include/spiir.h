@@ -115,8 +115,10 @@ typedef struct spiir_options {
                             /* FP64 carry of the segment start states; segments are */
                             /* >= 1 block long);  0 = auto: banks that fill < 1/8   */
                             /* of the GPU's warps get up to 8 warps/SM worth (>= 4  */
-                            /* segments, <= 64), others none; 1 = off.  Results of  */
-                            /* different splits agree to rounding, not bit for bit  */
+                            /* segments, <= 64), banks under one full wave (16     */
+                            /* warps/SM) get 2 on calls of >= 64 blocks, others    */
+                            /* none; 1 = off.  Results of different splits agree   */
+                            /* to rounding, not bit for bit                        */
     int32_t projection;     /* how segmented calls get their segment start states: */
                             /* SPIIR_PROJECT_AUTO (= TENSOR), _RECURRENCE (a zero-  */
                             /* state FP32 pass over all but the last segment, FP64 */

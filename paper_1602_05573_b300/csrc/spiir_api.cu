@@ -696,15 +696,17 @@ spiir_status spiir_reset(spiir_plan *p, void *stream)
 }
 
 // Time segments for a band call of nb samples, each at least one block long.
-// Segmenting costs a second (zero-state) pass over all but the last segment,
-// so by default it is used only for banks that fill under 1/8 of the GPU's
-// warp slots (8 warps per SM as the target), and only when it gives at
-// least 4 segments; a time_segments option above 0 forces the count.
+// By default: banks that fill under 1/8 of the GPU's warp slots get enough
+// segments for ~8 warps per SM (at least 4, at most 64); banks that fill
+// less than one full wave (16 warps per SM) over a long call (>= 64 blocks)
+// get 2, which evens out the wave; larger banks none.  A time_segments
+// option above 0 forces the count.
 int segments_for(const spiir_plan *p, const Band &b, int64_t nb)
 {
     if (p->precision != SPIIR_PREC_PLAIN) return 1;
     const int req = p->opt.time_segments;
     const int64_t warps = b.lay.n_units() * b.lay.W;
+    const int64_t nblocks = nb / (int64_t)b.lay.Tb;
     int P = 1;
     if (req >= 1) {
         P = req;
@@ -712,10 +714,11 @@ int segments_for(const spiir_plan *p, const Band &b, int64_t nb)
         const int64_t target = 8 * (int64_t)p->n_sm;
         const int64_t want = std::min<int64_t>(64, target / std::max<int64_t>(warps, 1));
         if (want >= 4) P = (int)want;
+        else if (warps < 16 * (int64_t)p->n_sm && nblocks >= 64) P = 2;
     }
-    const int64_t max_p = std::max<int64_t>(1, nb / (int64_t)b.lay.Tb);
+    const int64_t max_p = std::max<int64_t>(1, nblocks);
     P = (int)std::max<int64_t>(1, std::min<int64_t>(P, max_p));
-    return (req < 1 && P < 4) ? 1 : P;
+    return (req < 1 && P < 2) ? 1 : P;
 }
 
 // Launch K1 for one band call split into time segments: a zero-state pass
