@@ -18,9 +18,11 @@
 // over it.
 //
 // Mapping: filters are independent in the adjoint, so the unit of work is a
-// task of kAdjRounds filter rounds (32 filters each) of one template; lane i
-// runs its kAdjRounds filters together (independent chains for the
-// scheduler) and keeps mu, g_a, g_b in registers for the whole call.  A CTA
+// task of two filter rounds (32 filters each) of one template; lane i runs
+// its two filters as one packed FP32x2 pair (every recurrence and gradient
+// update is one fma/mul.rn.f32x2 for both) and keeps mu, g_a, g_b in
+// registers.  Long calls run as time segments of whole checkpoint
+// intervals, each from the adjoint state projected to its end.  A CTA
 // runs W tasks of one detector and stages each chunk's strain window in
 // shared memory; the 16-sample state checkpoints of pass A go to an
 // L2-resident workspace; g_z of the template is read by lanes 0..15 once per
@@ -28,6 +30,7 @@
 // shared-memory atomics (the layout places a round's 32 delays on 32
 // different banks) and added to global memory per chunk.
 #include "spiir_kernels.h"
+#include "spiir_ptx.h"
 
 #include <cstdint>
 
@@ -39,6 +42,8 @@ constexpr unsigned kFull = 0xffffffffu;
 
 __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
 {
+    // a lane's two filter rounds share FP32x2 registers: (round 0, round 1)
+    static_assert(kAdjRounds == 2, "the reverse pass pairs its two rounds");
     constexpr int R = kAdjRounds;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Dw = A.Dh + A.Cc;                          // strain window per chunk
@@ -66,15 +71,15 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
     float2 *wsub = A.sub + ((int64_t)blockIdx.x * A.W + warp) * R * nsub_max * 32;
     float *acc_det = A.acc + ((int64_t)seg * A.n_det + det) * A.n_slots * 6;
 
-    // this lane's filters: slot of round i = task.x + i * task.w (task.w = 32 * layout warps)
+    // this lane's filters: slot of round i = task.x + i * round_stride + lane
     int64_t slot[R];
-    float ar[R], ai[R], br[R], bi[R];
+    float ar[R], ai[R], br[R], bi[R], m0r[R], m0i[R];
     int xo[R];
-    bool odd = (lane & 1) != 0;   // stored as conj(a), (Im b, Re b)
+    const bool odd = (lane & 1) != 0;   // stored as conj(a), (Im b, Re b)
 #pragma unroll
     for (int i = 0; i < R; ++i) {
         slot[i] = active ? (int64_t)task.x + (int64_t)i * A.round_stride + lane : 0;
-        ar[i] = ai[i] = br[i] = bi[i] = 0.f;
+        ar[i] = ai[i] = br[i] = bi[i] = m0r[i] = m0i[i] = 0.f;
         xo[i] = 0;
         if (active && i < nr) {
             const float4 p = A.params[slot[i]];
@@ -83,18 +88,19 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
             br[i] = odd ? p.w : p.z;
             bi[i] = odd ? p.z : p.w;
             xo[i] = A.ringoff[slot[i]].x;   // Dh - d: xs index of x[kc - d]
+            if (A.mu_end != nullptr) {      // adjoint state after the segment
+                const float2 m =
+                    A.mu_end[((int64_t)seg * A.n_det + det) * A.n_slots + slot[i]];
+                m0r[i] = m.x;
+                m0i[i] = m.y;
+            }
         }
     }
-    float mr[R], mi[R], gar[R], gai[R], gbr[R], gbi[R];
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-        mr[i] = mi[i] = gar[i] = gai[i] = gbr[i] = gbi[i] = 0.f;
-        if (A.mu_end != nullptr && active && i < nr) {   // adjoint state after the segment
-            const float2 m = A.mu_end[((int64_t)seg * A.n_det + det) * A.n_slots + slot[i]];
-            mr[i] = m.x;
-            mi[i] = m.y;
-        }
-    }
+    const uint64_t AR = pk(ar[0], ar[1]), AI = pk(ai[0], ai[1]), NAI = pk(-ai[0], -ai[1]);
+    const uint64_t BR = pk(br[0], br[1]), BI = pk(bi[0], bi[1]);
+    uint64_t MR = pk(m0r[0], m0r[1]), MI = pk(m0i[0], m0i[1]);
+    // g_a = sum mu conj(y[k-1]): Re in GAR, Im = GAI1 - GAI2; g_b = sum mu x
+    uint64_t GAR = 0, GAI1 = 0, GAI2 = 0, GBR = 0, GBI = 0;
 
     for (int c = c_hi - 1; c >= c_lo; --c) {
         const int kc = c * A.Cc;
@@ -107,54 +113,60 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
         __syncthreads();
         if (active) {
             const int nsub = (cv + kAdjSub - 1) / kAdjSub;
-            float yr[R], yi[R];   // state y[kc - 1]
-#pragma unroll
-            for (int i = 0; i < R; ++i) {
-                yr[i] = yi[i] = 0.f;
-                if (c > 0 && i < nr) {
-                    const float2 ck = A.ckpt[((int64_t)c * A.n_det + det) * A.n_slots + slot[i]];
-                    yr[i] = odd ? ck.y : ck.x;
-                    yi[i] = odd ? ck.x : ck.y;
+            float yr0 = 0.f, yi0 = 0.f, yr1 = 0.f, yi1 = 0.f;   // state y[kc - 1]
+            if (c > 0) {
+                const float2 *row = A.ckpt + ((int64_t)c * A.n_det + det) * A.n_slots;
+                const float2 c0 = row[slot[0]];
+                yr0 = odd ? c0.y : c0.x;
+                yi0 = odd ? c0.x : c0.y;
+                if (nr > 1) {
+                    const float2 c1 = row[slot[1]];
+                    yr1 = odd ? c1.y : c1.x;
+                    yi1 = odd ? c1.x : c1.y;
                 }
             }
+            uint64_t YR = pk(yr0, yr1), YI = pk(yi0, yi1);
             // pass A: forward over the chunk, state kept every kAdjSub samples
             for (int q = 0; q < nsub; ++q) {
-#pragma unroll
-                for (int i = 0; i < R; ++i)
-                    wsub[((int64_t)q * R + i) * 32 + lane] = make_float2(yr[i], yi[i]);
+                {
+                    float a0, a1, b0, b1;
+                    upk(YR, a0, a1);
+                    upk(YI, b0, b1);
+                    wsub[((int64_t)q * R + 0) * 32 + lane] = make_float2(a0, b0);
+                    wsub[((int64_t)q * R + 1) * 32 + lane] = make_float2(a1, b1);
+                }
                 const int k0 = q * kAdjSub;
 #pragma unroll
                 for (int t = 0; t < kAdjSub; ++t) {
                     if (k0 + t < cv) {
-#pragma unroll
-                        for (int i = 0; i < R; ++i) {
-                            const float x = xs[xo[i] + k0 + t];
-                            const float nr_ = fmaf(ar[i], yr[i], fmaf(-ai[i], yi[i], br[i] * x));
-                            const float ni_ = fmaf(ar[i], yi[i], fmaf(ai[i], yr[i], bi[i] * x));
-                            yr[i] = nr_;
-                            yi[i] = ni_;
-                        }
+                        const uint64_t X = pk(xs[xo[0] + k0 + t], xs[xo[1] + k0 + t]);
+                        uint64_t TR = mul2(BR, X), TI = mul2(BI, X);
+                        TR = fma2(NAI, YI, TR);   // br x - ai yi
+                        TI = fma2(AI, YR, TI);    // bi x + ai yr
+                        YR = fma2(AR, YR, TR);
+                        YI = fma2(AR, YI, TI);
                     }
                 }
             }
             // pass B: spans in reverse; y[k-1] recomputed into registers
             for (int q = nsub - 1; q >= 0; --q) {
                 const int k0 = q * kAdjSub;
-                float pr[R][kAdjSub], pi[R][kAdjSub];   // y[k0 + t - 1]
-#pragma unroll
-                for (int i = 0; i < R; ++i) {
-                    const float2 y0 = wsub[((int64_t)q * R + i) * 32 + lane];
-                    float ur = y0.x, ui = y0.y;
+                uint64_t PR[kAdjSub], PI[kAdjSub];   // y[k0 + t - 1], both rounds
+                {
+                    const float2 s0 = wsub[((int64_t)q * R + 0) * 32 + lane];
+                    const float2 s1 = wsub[((int64_t)q * R + 1) * 32 + lane];
+                    uint64_t UR = pk(s0.x, s1.x), UI = pk(s0.y, s1.y);
 #pragma unroll
                     for (int t = 0; t < kAdjSub; ++t) {
-                        pr[i][t] = ur;
-                        pi[i][t] = ui;
+                        PR[t] = UR;
+                        PI[t] = UI;
                         if (t + 1 < kAdjSub) {
-                            const float x = xs[xo[i] + k0 + t];
-                            const float nr_ = fmaf(ar[i], ur, fmaf(-ai[i], ui, br[i] * x));
-                            const float ni_ = fmaf(ar[i], ui, fmaf(ai[i], ur, bi[i] * x));
-                            ur = nr_;
-                            ui = ni_;
+                            const uint64_t X = pk(xs[xo[0] + k0 + t], xs[xo[1] + k0 + t]);
+                            uint64_t TR = mul2(BR, X), TI = mul2(BI, X);
+                            TR = fma2(NAI, UI, TR);
+                            TI = fma2(AI, UR, TI);
+                            UR = fma2(AR, UR, TR);
+                            UI = fma2(AR, UI, TI);
                         }
                     }
                 }
@@ -168,21 +180,23 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
                     const float Gr = __shfl_sync(kFull, gl.x, gsrc + t);
                     const float Gi = __shfl_sync(kFull, gl.y, gsrc + t);
                     if (k0 + t < cv) {
-#pragma unroll
-                        for (int i = 0; i < R; ++i) {
-                            // mu <- g_z + conj(a) mu
-                            const float nr_ = Gr + fmaf(ar[i], mr[i], ai[i] * mi[i]);
-                            const float ni_ = Gi + fmaf(ar[i], mi[i], -ai[i] * mr[i]);
-                            mr[i] = nr_;
-                            mi[i] = ni_;
-                            // g_a += mu conj(y[k-1]),  g_b += mu x[k-d]
-                            gar[i] = fmaf(mr[i], pr[i][t], fmaf(mi[i], pi[i][t], gar[i]));
-                            gai[i] = fmaf(mi[i], pr[i][t], fmaf(-mr[i], pi[i][t], gai[i]));
-                            const float x = xs[xo[i] + k0 + t];
-                            gbr[i] = fmaf(mr[i], x, gbr[i]);
-                            gbi[i] = fmaf(mi[i], x, gbi[i]);
-                            if (A.gx != nullptr && i < nr)
-                                atomicAdd(&gxs[xo[i] + k0 + t], fmaf(mr[i], br[i], mi[i] * bi[i]));
+                        // mu <- g_z + conj(a) mu
+                        const uint64_t NMR = fma2(AR, MR, fma2(AI, MI, pk(Gr, Gr)));
+                        const uint64_t NMI = fma2(AR, MI, fma2(NAI, MR, pk(Gi, Gi)));
+                        MR = NMR;
+                        MI = NMI;
+                        // g_a += mu conj(y[k-1]),  g_b += mu x[k-d]
+                        GAR = fma2(MR, PR[t], fma2(MI, PI[t], GAR));
+                        GAI1 = fma2(MI, PR[t], GAI1);
+                        GAI2 = fma2(MR, PI[t], GAI2);
+                        const uint64_t X = pk(xs[xo[0] + k0 + t], xs[xo[1] + k0 + t]);
+                        GBR = fma2(MR, X, GBR);
+                        GBI = fma2(MI, X, GBI);
+                        if (A.gx != nullptr) {   // g_x[k - d] += Re(conj(mu) b)
+                            float c0, c1;
+                            upk(fma2(MR, BR, mul2(MI, BI)), c0, c1);
+                            atomicAdd(&gxs[xo[0] + k0 + t], c0);
+                            if (nr > 1) atomicAdd(&gxs[xo[1] + k0 + t], c1);
                         }
                     }
                 }
@@ -201,16 +215,23 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
         __syncthreads();
     }
     if (active) {
+        float v[6][R];
+        upk(MR, v[0][0], v[0][1]);
+        upk(MI, v[1][0], v[1][1]);
+        upk(GAR, v[2][0], v[2][1]);
+        float i1[R], i2[R];
+        upk(GAI1, i1[0], i1[1]);
+        upk(GAI2, i2[0], i2[1]);
+        v[3][0] = i1[0] - i2[0];
+        v[3][1] = i1[1] - i2[1];
+        upk(GBR, v[4][0], v[4][1]);
+        upk(GBI, v[5][0], v[5][1]);
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             if (i >= nr) continue;
             float *acc = acc_det + slot[i] * 6;
-            acc[0] = mr[i];
-            acc[1] = mi[i];
-            acc[2] = gar[i];
-            acc[3] = gai[i];
-            acc[4] = gbr[i];
-            acc[5] = gbi[i];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[k] = v[k][i];
         }
     }
 }
