@@ -832,7 +832,7 @@ spiir_status launch_anchored(spiir_plan *p, Band &b, spiir::K1Args a, cudaStream
         t.n_slots = L.n_slots;
         t.D = D;
         t.Dh = (int32_t)L.Dh;
-        t.n_ntiles = (int32_t)((n_cols + spiir::tc_cols_per_tile() - 1) / spiir::tc_cols_per_tile());
+        t.n_cols = n_cols;
         t.col0 = (int32_t)(c_first - hq - 1);
         t.c_first = (int32_t)c_first;
         t.c_end = (int32_t)c_end;
@@ -936,7 +936,7 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         t.n_slots = L.n_slots;
         t.D = D;
         t.Dh = (int32_t)L.Dh;
-        t.n_ntiles = (int32_t)((n_cols + spiir::tc_cols_per_tile() - 1) / spiir::tc_cols_per_tile());
+        t.n_cols = n_cols;
         t.col0 = (int32_t)(-hq - 1);
         t.c_last = (int32_t)c_last;
         t.cps = (int32_t)cps;

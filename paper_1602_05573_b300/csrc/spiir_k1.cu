@@ -932,24 +932,41 @@ __global__ void segment_carry_kernel(const float4 *params, const float2 *state,
     }
 }
 
+// One warp per (detector, template) entry: lanes read segments q = lane,
+// lane + 32, ..., keep their largest (earliest segment on ties), then a
+// butterfly keeps the largest with the smallest segment; the plan's running
+// peak wins ties (earlier samples).
 __global__ void peak_merge_kernel(const float *seg_best, const int64_t *seg_idx, int P,
                                   int64_t count, float *best, int64_t *idx, int64_t *t0,
                                   int64_t advance)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i == 0 && t0 != nullptr) *t0 += advance;   // nothing here reads the counter
-    if (i >= count) return;
-    float b = best[i];
-    int64_t k = idx[i];
-    for (int q = 0; q < P; ++q) {
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt == 0 && t0 != nullptr) *t0 += advance;   // nothing here reads the counter
+    const int64_t i = gt >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= count) return;                          // whole warps leave together
+    float b = -2.0f;
+    int q_b = P;
+    for (int q = lane; q < P; q += 32) {
         const float v = seg_best[(int64_t)q * count + i];
         if (v > b) {
             b = v;
-            k = seg_idx[(int64_t)q * count + i];
+            q_b = q;
         }
     }
-    best[i] = b;
-    idx[i] = k;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ob = __shfl_xor_sync(0xffffffffu, b, o);
+        const int oq = __shfl_xor_sync(0xffffffffu, q_b, o);
+        if (ob > b || (ob == b && oq < q_b)) {
+            b = ob;
+            q_b = oq;
+        }
+    }
+    if (lane == 0 && q_b < P && b > best[i]) {
+        best[i] = b;
+        idx[i] = seg_idx[(int64_t)q_b * count + i];
+    }
 }
 
 __global__ void advance_kernel(int64_t *t0, int64_t n)
@@ -1081,7 +1098,8 @@ cudaError_t launch_peak_merge(const float *seg_best, const int64_t *seg_idx, int
                               int64_t advance, cudaStream_t s)
 {
     if (count <= 0) return cudaSuccess;
-    peak_merge_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(
+    const int64_t threads = count * 32;
+    peak_merge_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(
         seg_best, seg_idx, P, count, best, idx, t0, advance);
     return cudaGetLastError();
 }

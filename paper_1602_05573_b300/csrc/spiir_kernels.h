@@ -154,7 +154,9 @@ struct TcArgs {
     int64_t n_slots;
     int32_t D;
     int32_t Dh;
-    int32_t n_ntiles;          // column tiles of tc_cols_per_tile() windows
+    int64_t n_cols;            // windows (GEMM columns) of this launch
+    int32_t n_ntiles;          // set by the launcher: accumulator tiles
+    int32_t n_btiles;          // set by the launcher: strain tiles per detector
     int32_t col0;              // window of column 0: c'' = col + col0 = -(Dh / kTcT) - 1
     int32_t c_last;            // last chunk the scan needs ((P - 1) * cps - 1)
     int32_t cps;               // chunks per segment

@@ -39,12 +39,11 @@ namespace spiir {
 namespace {
 
 constexpr int kRowsTile = 128;                  // GEMM rows per CTA (64 slots x re/im)
-constexpr int kColsTile = 256;                  // windows per accumulator tile (TMEM columns)
+constexpr int kColsTile = 256;                  // windows per strain tile in HBM
 constexpr int kKBlk = 64;                       // K per staged block
 constexpr int kKBlocks = kTcK / kKBlk;          // 8
 constexpr uint32_t kTileBytes = 128u * kKBlk * 2u;   // 16 KB: 128 rows x 64 BF16 (A)
 constexpr uint32_t kBTileBytes = (uint32_t)kColsTile * kKBlk * 2u;   // B: 256 rows x 64
-constexpr uint32_t kStageBytes = 2u * kTileBytes + 2u * kBTileBytes;  // A hi, lo, B hi, lo
 constexpr int kStages = 2;
 constexpr int kEpiThreads = 128;
 
@@ -232,16 +231,19 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t addr)
 }
 // Instruction descriptor, kind::f16: FP32 accumulator (bits 4-5 = 1), BF16 A
 // and B (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            ((uint32_t)(kColsTile >> 3) << 17) |
-                            ((uint32_t)(kRowsTile >> 4) << 24);
+template <int NT> __host__ __device__ constexpr uint32_t idesc_for()
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
+           ((uint32_t)(kRowsTile >> 4) << 24);
+}
 
-__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc)
+__device__ __forceinline__ void umma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc,
+                                          uint32_t acc)
 {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 __device__ __forceinline__ void umma_commit(uint32_t bar)
@@ -270,9 +272,15 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // [c_first, c_end), the state before every chunk written as its anchor
 // (rounded to FP32) and the state after the last written back in FP64 (the
 // chunked tensor-core precision form).
-template <bool ANCH>
+// NT: windows per accumulator (N of the MMA): 256, or 128 for calls with few
+// windows (the strain tiles in HBM are 256 wide; a 128-wide column tile is
+// one half of one).
+template <bool ANCH, int NT>
 __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
 {
+    constexpr uint32_t kBT = (uint32_t)NT * kKBlk * 2u;          // one B component
+    constexpr uint32_t kSB = 2u * kTileBytes + 2u * kBT;          // stage bytes
+    constexpr uint32_t kIdesc = idesc_for<NT>();
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[2 * kStages + 4];
     __shared__ uint32_t tmem_slot;
@@ -299,7 +307,7 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
         asm volatile(
             "tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                 smem_addr(&tmem_slot)),
-            "r"(2 * kColsTile)
+            "r"(2 * NT)
             : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -315,17 +323,26 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
             // producer + MMA issue, two stages
             const int total = n_ntiles * kKBlocks;
             const unsigned char *wt = A.W + mt * kKBlocks * 2 * (int64_t)kTileBytes;
-            const unsigned char *bt = A.B + (int64_t)det * n_ntiles * kKBlocks * 2 * kBTileBytes;
+            const unsigned char *bt =
+                A.B + (int64_t)det * A.n_btiles * kKBlocks * 2 * kBTileBytes;
             auto fill = [&](int it) {
                 const int st = it % kStages;
                 const int nt = it / kKBlocks, kb = it % kKBlocks;
-                const uint32_t dst = smem_addr(smem) + st * kStageBytes;
+                const uint32_t dst = smem_addr(smem) + st * kSB;
                 const uint32_t full = full0 + 8 * st;
-                mbar_expect_tx(full, kStageBytes);
+                mbar_expect_tx(full, kSB);
                 bulk_g2s(dst, wt + (int64_t)kb * 2 * kTileBytes, 2 * kTileBytes, full);
-                bulk_g2s(dst + 2 * kTileBytes,
-                         bt + ((int64_t)nt * kKBlocks + kb) * 2 * kBTileBytes, 2 * kBTileBytes,
-                         full);
+                // the strain tile holding windows [nt * NT, nt * NT + NT)
+                const int64_t col0 = (int64_t)nt * NT;
+                const unsigned char *src =
+                    bt + ((col0 / kColsTile) * kKBlocks + kb) * 2 * kBTileBytes;
+                if (NT == kColsTile) {
+                    bulk_g2s(dst + 2 * kTileBytes, src, 2 * kBTileBytes, full);
+                } else {   // rows of the half tile are the first or second kBT bytes
+                    const uint32_t off = (uint32_t)((col0 % kColsTile) / NT) * kBT;
+                    bulk_g2s(dst + 2 * kTileBytes, src + off, kBT, full);
+                    bulk_g2s(dst + 2 * kTileBytes + kBT, src + kBTileBytes + off, kBT, full);
+                }
             };
             // block it+1 is copied while the MMAs of block it run; a stage is
             // refilled once the MMAs that read it (block it-1) have finished
@@ -339,17 +356,17 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
                                    A.wait_limit_ns);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t s0 = smem_addr(smem) + st * kStageBytes;
-                const uint32_t acc = tmem + (uint32_t)((nt & 1) * kColsTile);
+                const uint32_t s0 = smem_addr(smem) + st * kSB;
+                const uint32_t acc = tmem + (uint32_t)((nt & 1) * NT);
 #pragma unroll
                 for (int kk = 0; kk < kKBlk / 16; ++kk) {
                     const uint32_t adv = kk * 256u;   // 16 K = two core matrices
                     const uint64_t ah = umma_desc(s0 + adv), al = umma_desc(s0 + kTileBytes + adv);
                     const uint64_t bh = umma_desc(s0 + 2 * kTileBytes + adv);
-                    const uint64_t bl = umma_desc(s0 + 2 * kTileBytes + kBTileBytes + adv);
-                    umma_bf16(acc, ah, bh, (kb > 0 || kk > 0) ? 1u : 0u);
-                    umma_bf16(acc, ah, bl, 1u);
-                    umma_bf16(acc, al, bh, 1u);
+                    const uint64_t bl = umma_desc(s0 + 2 * kTileBytes + kBT + adv);
+                    umma_bf16(acc, ah, bh, kIdesc, (kb > 0 || kk > 0) ? 1u : 0u);
+                    umma_bf16(acc, ah, bl, kIdesc, 1u);
+                    umma_bf16(acc, al, bh, kIdesc, 1u);
                 }
                 umma_commit(empty0 + 8 * st);          // stage free once these MMAs finish
                 if (kb == kKBlocks - 1) umma_commit(acc_full0 + 8 * (nt & 1));
@@ -396,7 +413,7 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
                 break;
             }
             tc_fence_after();
-            for (int c0 = 0; c0 < kColsTile; c0 += 16) {
+            for (int c0 = 0; c0 < NT; c0 += 16) {
                 uint32_t v[16];
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,"
@@ -405,13 +422,13 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
                       "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
                       "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                     : "r"(tmem + ((uint32_t)(warp * 32) << 16) +
-                          (uint32_t)((nt & 1) * kColsTile + c0)));
+                          (uint32_t)((nt & 1) * NT + c0)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
                     const float g = __uint_as_float(v[j]);
                     // window c'' = col + col0 feeds chunk c = c'' + q + 1
-                    const int64_t c = (int64_t)nt * kColsTile + c0 + j + A.col0 + q + 1;
+                    const int64_t c = (int64_t)nt * NT + c0 + j + A.col0 + q + 1;
                     if (ANCH) {
                         // each thread advances its own component; the other one
                         // comes from the partner lane (Re <-> Im)
@@ -459,7 +476,7 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
     __syncthreads();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                     "r"(2 * kColsTile)
+                     "r"(2 * NT)
                      : "memory");
 }
 
@@ -515,20 +532,28 @@ cudaError_t launch_tc_strain(const float *xe, int64_t xe_stride, int Dh, int64_t
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_project(const TcArgs &a, cudaStream_t s)
+template <bool ANCH, int NT> cudaError_t launch_project_nt(TcArgs a, int64_t mtiles, cudaStream_t s)
 {
-    const int smem = kStages * (int)kStageBytes;
-    const void *k = a.anchors != nullptr ? reinterpret_cast<const void *>(tc_project_kernel<true>)
-                                         : reinterpret_cast<const void *>(tc_project_kernel<false>);
+    constexpr int smem = kStages * (int)(2u * kTileBytes + 2u * (uint32_t)NT * kKBlk * 2u);
+    const void *k = reinterpret_cast<const void *>(tc_project_kernel<ANCH, NT>);
     cudaError_t e = ensure_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
-    const int64_t mtiles = (2 * a.n_slots + kRowsTile - 1) / kRowsTile;
-    if (mtiles == 0 || a.n_ntiles == 0) return cudaSuccess;
-    if (a.anchors != nullptr)
-        tc_project_kernel<true><<<dim3((unsigned)mtiles, (unsigned)a.D), 160, smem, s>>>(a);
-    else
-        tc_project_kernel<false><<<dim3((unsigned)mtiles, (unsigned)a.D), 160, smem, s>>>(a);
+    a.n_ntiles = (int32_t)((a.n_cols + NT - 1) / NT);
+    a.n_btiles = (int32_t)((a.n_cols + kColsTile - 1) / kColsTile);
+    tc_project_kernel<ANCH, NT><<<dim3((unsigned)mtiles, (unsigned)a.D), 160, smem, s>>>(a);
     return cudaGetLastError();
+}
+
+cudaError_t launch_tc_project(const TcArgs &a, cudaStream_t s)
+{
+    const int64_t mtiles = (2 * a.n_slots + kRowsTile - 1) / kRowsTile;
+    if (mtiles == 0 || a.n_cols <= 0) return cudaSuccess;
+    const bool narrow = a.n_cols <= 128;   // one half tile: half the strain bytes per stage
+    if (a.anchors != nullptr)
+        return narrow ? launch_project_nt<true, 128>(a, mtiles, s)
+                      : launch_project_nt<true, 256>(a, mtiles, s);
+    return narrow ? launch_project_nt<false, 128>(a, mtiles, s)
+                  : launch_project_nt<false, 256>(a, mtiles, s);
 }
 
 }  // namespace spiir
