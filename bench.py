@@ -222,6 +222,16 @@ def run_reference(args, rank, world):
 
 
 # -------------------------------------------------------------- ours ---
+def max_over_ranks(value, dist, device):
+    """The largest of every rank's value (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def shard_bank(name, rank):
     """Rank 0 filters the workload's bank; rank r > 0 its own shard of a
     world-times-larger bank (independent templates, same distributions)."""
@@ -316,10 +326,7 @@ def run_ours(args, rank, world, local_rank):
     total_ms = t0.elapsed_time(t1)
     step_times = [a.elapsed_time(b) for a, b in ev]
     filt_ms = float(np.mean(step_times))
-    if dist is not None:
-        tt = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(total_ms, dist, dev)
     ms_step = total_ms / args.steps
     value = upd * world * args.steps / (total_ms / 1e3)
 
@@ -395,11 +402,7 @@ def run_ours(args, rank, world, local_rank):
                 e2e_step()
             a1.record(stream)
             barrier()
-        e_ms = a0.elapsed_time(a1)
-        if dist is not None:
-            tt = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e_ms = float(tt.item())
+        e_ms = max_over_ranks(a0.elapsed_time(a1), dist, dev)
         e2e = {"value": upd * world * args.steps / (e_ms / 1e3), "unit": "filter-updates/s",
                "h2d_bytes_per_step": int(xh.numel() * 4),
                "d2h_bytes_per_step": int(pah.numel() * 4 + pih.numel() * 8),
