@@ -39,7 +39,7 @@ def worker(rank, world, port, out):
 
 def test_two_gloo_ranks_shard_templates_and_take_the_slowest():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:
         out = m.dict()
         mp.start_processes(worker, args=(world, free_port(), out), nprocs=world,
                            start_method="spawn")
