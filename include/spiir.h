@@ -127,6 +127,9 @@ typedef struct spiir_options {
     int32_t kernel_timing;  /* nonzero: record CUDA events around every filter   */
                             /* (K1) and tensor-core projection launch, outside     */
                             /* stream capture; read them with spiir_kernel_times  */
+    int32_t tile_chunks;    /* chunked_tc: 256-sample chunks per time tile (the    */
+                            /* anchors of one tile are held at once); 0 = auto:    */
+                            /* anchors within a quarter of free memory, <= 16 GiB */
     int32_t reserved[1];
 } spiir_options;
 

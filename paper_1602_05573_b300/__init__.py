@@ -60,7 +60,7 @@ class Options(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("max_filters_per_lane", ctypes.c_int32),
                 ("lanes_per_template", ctypes.c_int32), ("time_segments", ctypes.c_int32),
                 ("projection", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 1)]
+                ("tile_chunks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -225,7 +225,7 @@ class Plan:
                  chunk_len: int = 256, autotune: bool = False,
                  max_filters_per_lane: int = 0, lanes_per_template: int = 0,
                  time_segments: int = 0, projection: str = "auto",
-                 kernel_timing: bool = False, lib=None):
+                 kernel_timing: bool = False, tile_chunks: int = 0, lib=None):
         self._h = None
         self._lib = lib if lib is not None else _lib
         off = np.ascontiguousarray(bank.off, np.int64)
@@ -260,6 +260,7 @@ class Plan:
         opt.time_segments = int(time_segments)
         opt.projection = PROJECTIONS[projection]
         opt.kernel_timing = 1 if kernel_timing else 0
+        opt.tile_chunks = int(tile_chunks)
         h = _P()
         _check(self._lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
                "spiir_plan_create", self._lib)

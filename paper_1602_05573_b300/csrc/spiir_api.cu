@@ -459,6 +459,7 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     if (opt.precision < SPIIR_PREC_PLAIN || opt.precision > SPIIR_PREC_CHUNKED_TC)
         return fail(SPIIR_EINVAL, "unknown precision mode");
     if (opt.chunk_len == 0) opt.chunk_len = 256;
+    if (opt.tile_chunks < 0) return fail(SPIIR_EINVAL, "tile_chunks must be >= 0");
     if (opt.precision == SPIIR_PREC_CHUNKED_TC && opt.chunk_len != spiir::kTcT)
         return fail(SPIIR_EINVAL, "the tensor-core chunked form uses chunks of " +
                                       std::to_string(spiir::kTcT) + " samples");
@@ -793,7 +794,9 @@ spiir_status launch_anchored(spiir_plan *p, Band &b, spiir::K1Args a, cudaStream
     if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = (size_t)4 << 30;
     const int64_t budget = std::min<int64_t>((int64_t)16 << 30,
                                              std::max<int64_t>((int64_t)1 << 30, (int64_t)(free_b / 4)));
-    const int64_t max_chunks = std::max<int64_t>(1, budget / (8 * per));
+    const int64_t max_chunks = p->opt.tile_chunks > 0
+                                   ? (int64_t)p->opt.tile_chunks
+                                   : std::max<int64_t>(1, budget / (8 * per));
     int64_t n_tile = std::max<int64_t>(unit, max_chunks * spiir::kTcT / unit * unit);
     n_tile = std::min<int64_t>(n_tile, (n + unit - 1) / unit * unit);
     const int64_t chunks = n_tile / spiir::kTcT;
