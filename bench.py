@@ -2,7 +2,8 @@
 """Throughput benchmark of the SPIIR filter bank on B300.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload batched|plain|adjoint|precision]
+                    [--workload batched|plain|multirate|adjoint|precision]
+                    [--precision plain|compensated|chunked_fp64|chunked_tc] [--graph]
 
 Workload (default): the batched bank -- 4096 templates with 100..300 complex
 single-pole filters each, 3 detectors, 65536 samples (64 s at 1024 Hz) of
@@ -16,8 +17,8 @@ templates are independent, so each rank filters its own 4096-template shard
 (weak scaling) with no collective on the data path.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle
-(the reference arm of this build) on the host cores, each step a bounded
-sample of the same workload.
+(the reference arm: there is no other implementation) on the host cores,
+each step a bounded sample of the same workload.
 """
 from __future__ import annotations
 
