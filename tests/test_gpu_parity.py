@@ -223,3 +223,31 @@ def test_half_warp_templates(sp, n_templates, W):
     z, pa, pi, plan = run_gpu(sp, bank, x, warps_per_cta=W, lanes_per_template=16)
     assert plan.info()["lanes_per_template"] == 16
     assert_parity(z, pa, pi, oracle_z(bank, x))
+
+
+def test_degenerate_calls_and_coefficients(sp):
+    """Empty and one-sample calls continue the stream; a template whose
+    gains are all zero gives z = 0 (peak 0 at the call's first sample); a
+    zero pole makes y = b x[k - d] exactly; a one-filter template."""
+    bank = make_bank(5, (1, 40), (0.99, 0.999), 300, seed=71, n_det=2)
+    a = bank.a.copy()
+    b = bank.b.copy()
+    b[bank.off[1]:bank.off[2]] = 0          # template 1: no gain
+    a[bank.off[2]:bank.off[3]] = 0          # template 2: zero poles
+    bank = Bank(bank.off, a, b, bank.d, bank.n_det)
+    x = make_strain(2, 2000, seed=72)
+    z, pa, pi, plan = run_gpu(sp, bank, x, chunks=[0, 1, 0, 1, 700, 0], time_segments=1)
+    zref = oracle_z(bank, x)
+    assert_parity(z, pa, pi, zref)
+    assert np.all(z[:, 1] == 0) and np.all(pa[:, 1] == 0) and np.all(pi[:, 1] == 0)
+    assert z.shape[-1] == x.shape[1]
+    # segmented calls of the same stream agree with the oracle as well
+    z2, pa2, pi2, _ = run_gpu(sp, bank, x, chunks=[1, 999], time_segments=4, block_len=256)
+    assert_parity(z2, pa2, pi2, zref)
+
+
+def test_single_filter_bank(sp):
+    bank = make_bank(1, 1, (0.99, 0.999), 50, seed=73)
+    x = make_strain(1, 1234, seed=74)
+    z, pa, pi, _ = run_gpu(sp, bank, x)
+    assert_parity(z, pa, pi, oracle_z(bank, x))
