@@ -37,6 +37,15 @@ sys.path.insert(0, ROOT)
 
 from spiir_inputs import WORKLOADS, updates, workload_bank, workload_strain  # noqa: E402
 
+# DRAM bytes (read + write) per launch of the dominant kernel from an ncu
+# capture of the current kernel, by (workload, precision); None where no
+# capture of the current kernel applies.  See profiles/.
+TRAFFIC = {
+    ("batched", "plain"): (
+        6.539e9, "k1_plain: 408.7 MB per launch captured on the same bank at 4096 samples "
+                 "(profiles/k1_plain_batched_medium.md), scaled by samples to 65536 "
+                 "(z writes dominate and grow in proportion); algorithmic bytes 6.44e9"),
+}
 LANE_OPS_PER_UPDATE = 8      # 4 FMA + 2 MUL + 2 ADD (FP32 lane operations)
 LANE_OPS_ADJOINT = 20        # reverse pass per filter-update: recompute 6, adjoint 6, grads 8
 B300_SMS = 148
@@ -440,6 +449,10 @@ def run_ours(args, rank, world, local_rank):
     achieved = lane_ops / (kernel_ms / 1e3) / 1e12
     if adjoint:
         kernel = "k6_adjoint"
+    traffic, traffic_note = None, None
+    key = ("adjoint" if adjoint else args.workload, args.precision)
+    if key in TRAFFIC and not args.samples and not args.templates:
+        traffic, traffic_note = TRAFFIC[key]
     ops_note = ("20 algorithmic lane-ops per filter-update of the reverse pass (recompute 6, "
                 "adjoint recurrence 6, grad a 4, grad b 2, grad x 2)" if adjoint else
                 "8 algorithmic lane-ops per filter-update")
@@ -463,7 +476,8 @@ def run_ours(args, rank, world, local_rank):
                                                   "last_call_segments")}),
         "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
                      "peak": peak_lane, "unit": "T FP32 lane-ops/s",
-                     "frac": achieved / peak_lane, "traffic": None,
+                     "frac": achieved / peak_lane, "traffic": traffic,
+                     "traffic_note": traffic_note,
                      "note": f"{ops_note} x {upd:.4g} updates per step / {timing}; "
                              f"peak = 148 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived "
                              f"from unit counts and the measured max clock)"},
