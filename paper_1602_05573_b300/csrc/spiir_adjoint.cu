@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
 {
     // a lane's two filter rounds share FP32x2 registers: (round 0, round 1)
     static_assert(kAdjRounds == 2, "the reverse pass pairs its two rounds");
+    static_assert(kAdjSub == 16, "the forward keeps span starts every 16 samples");
     constexpr int R = kAdjRounds;
     extern __shared__ __align__(16) unsigned char smem[];
     const int Dw = A.Dh + A.Cc;                          // strain window per chunk
@@ -113,8 +114,9 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
         __syncthreads();
         if (active) {
             const int nsub = (cv + kAdjSub - 1) / kAdjSub;
+            const bool have_sub = A.sub16 != nullptr;   // the forward kept every span's start
             float yr0 = 0.f, yi0 = 0.f, yr1 = 0.f, yi1 = 0.f;   // state y[kc - 1]
-            if (c > 0) {
+            if (c > 0 && !have_sub) {
                 const float2 *row = A.ckpt + ((int64_t)c * A.n_det + det) * A.n_slots;
                 const float2 c0 = row[slot[0]];
                 yr0 = odd ? c0.y : c0.x;
@@ -127,7 +129,7 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
             }
             uint64_t YR = pk(yr0, yr1), YI = pk(yi0, yi1);
             // pass A: forward over the chunk, state kept every kAdjSub samples
-            for (int q = 0; q < nsub; ++q) {
+            for (int q = 0; q < (have_sub ? 0 : nsub); ++q) {
                 {
                     float a0, a1, b0, b1;
                     upk(YR, a0, a1);
@@ -153,8 +155,18 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
                 const int k0 = q * kAdjSub;
                 uint64_t PR[kAdjSub], PI[kAdjSub];   // y[k0 + t - 1], both rounds
                 {
-                    const float2 s0 = wsub[((int64_t)q * R + 0) * 32 + lane];
-                    const float2 s1 = wsub[((int64_t)q * R + 1) * 32 + lane];
+                    float2 s0, s1;
+                    if (have_sub) {   // kernel form from the forward: odd lanes (im, re)
+                        const float2 *row =
+                            A.sub16 + ((int64_t)((kc + k0) >> 4) * A.n_det + det) * A.n_slots;
+                        const float2 c0 = row[slot[0]];
+                        const float2 c1 = nr > 1 ? row[slot[1]] : make_float2(0.f, 0.f);
+                        s0 = odd ? make_float2(c0.y, c0.x) : c0;
+                        s1 = odd ? make_float2(c1.y, c1.x) : c1;
+                    } else {
+                        s0 = wsub[((int64_t)q * R + 0) * 32 + lane];
+                        s1 = wsub[((int64_t)q * R + 1) * 32 + lane];
+                    }
                     uint64_t UR = pk(s0.x, s1.x), UI = pk(s0.y, s1.y);
 #pragma unroll
                     for (int t = 0; t < kAdjSub; ++t) {

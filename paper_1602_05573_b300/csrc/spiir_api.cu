@@ -174,6 +174,8 @@ struct Band {
     float2 *adj_E = nullptr;       // [P][D][n_slots] reverse projection, segment starts
     float2 *adj_mu = nullptr;      // [P][D][n_slots] adjoint state after each segment
     int adj_seg_cap = 0;           // segments adj_E / adj_mu / acc hold
+    float2 *adj_sub16 = nullptr;   // [n/16][D][n_slots] forward state at every span start
+    int64_t adj_sub16_cap = 0;     //   float2 elements
 };
 
 struct spiir_plan {
@@ -270,6 +272,7 @@ void free_band(Band &b)
     cudaFree(b.adj_slot_tmpl);
     cudaFree(b.adj_E);
     cudaFree(b.adj_mu);
+    cudaFree(b.adj_sub16);
     b = Band();
 }
 
@@ -1329,6 +1332,26 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     f.ckpt = b.ckpt;
     f.ckpt_blocks = Cc / L.Tb;
     f.n_det = D;
+    // the forward also keeps the state at every 16-sample span start when that
+    // fits a quarter of free memory (at most 8 GiB): the reverse pass then
+    // skips its per-chunk recompute
+    {
+        const int64_t want = ((n + 15) / 16) * D * L.n_slots;
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        const int64_t budget = std::min<int64_t>((int64_t)8 << 30, (int64_t)(free_b / 4));
+        if (b.adj_sub16_cap < want && want * (int64_t)sizeof(float2) <= budget) {
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(b.adj_sub16);
+            b.adj_sub16 = nullptr;
+            b.adj_sub16_cap = 0;
+            if (dalloc(&b.adj_sub16, (size_t)want) == cudaSuccess) b.adj_sub16_cap = want;
+            else (void)cudaGetLastError();   // fall back to the per-chunk recompute
+        }
+        f.sub16 = (b.adj_sub16_cap >= want && p->precision == SPIIR_PREC_PLAIN) ? b.adj_sub16
+                                                                                 : nullptr;
+    }
     p->last_launches = 0;
     if (p->precision == SPIIR_PREC_PLAIN) {
         // time-segmented like a plain call when the bank is small (checkpoints
@@ -1383,6 +1406,7 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     a.sub = b.adj_sub;
     a.n_units = (int32_t)b.adj_n_units;
     a.cps = (int32_t)cps;
+    a.sub16 = f.sub16;
     a.mu_end = P > 1 ? b.adj_mu : nullptr;
     if (spiir::k6_smem_bytes(Cc, L.Dh) > 227 * 1024)
         return fail(SPIIR_EUNSUPPORTED, "adjoint strain window above 227 KB of shared memory");

@@ -195,6 +195,7 @@ __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb,
 // Plain FP32: two filters per packed FP32x2 instruction (8 packed ops per
 // filter pair and sample), an odd filter in scalar FP32.
 template <int F> struct PackedLanes {
+    static constexpr int kF = F;
     static constexpr int NP = F / 2;
     static constexpr bool ODD = (F & 1) != 0;
     static constexpr int NPA = NP > 0 ? NP : 1;
@@ -326,6 +327,7 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
 // Compensated: each filter's state is a float-float pair (hi + lo, about 48
 // significant bits); the update is exact up to the low-order sum.
 template <int F> struct CompLanes {
+    static constexpr int kF = F;
     float ar[F], ai[F], br[F], bi[F], yrh[F], yrl[F], yih[F], yil[F];
 
     __device__ __forceinline__ void load(const K1Args &A, int64_t pb, int warp, int lane, int det,
@@ -416,6 +418,7 @@ template <int F> struct CompLanes {
 // chunk end the anchor advances in FP64, s <- a^T s + S, and y restarts from
 // s rounded to FP32, so FP32 error never builds up over more than one chunk.
 template <int F> struct ChunkLanes {
+    static constexpr int kF = F;
     float ar[F], ai[F], br[F], bi[F], yr[F], yi[F], ur[F], ui[F];
     double aTr[F], aTi[F], sr64[F], si64[F];
 
@@ -598,6 +601,18 @@ __device__ __forceinline__ void warp_peak_merge(const K1Args &A, float *peak_bes
 }
 
 // ---- one CTA work unit: W warps x one detector, whole call ----------------
+// The state before the 16-sample span starting at call sample k (a multiple
+// of 16): the adjoint's recompute points.
+template <class LANES>
+__device__ __forceinline__ void save_sub16(const K1Args &A, const LANES &L, int64_t pb, int warp,
+                                           int lane, int det, int k)
+{
+    constexpr int F = LANES::kF;
+    float2 *row = A.sub16 + ((int64_t)(k >> 4) * A.n_det + det) * A.n_slots;
+#pragma unroll
+    for (int r = 0; r < F; ++r) row[pb + ((int64_t)r * A.W + warp) * 32 + lane] = L.state_of(r);
+}
+
 // SEG: the CTA serves one time segment of the call; LOW: the call adds lower
 // bands (multirate top band).  Both are compile-time so the plain single-band
 // kernel carries neither's code.
@@ -698,6 +713,8 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
                     float zr[U][kTS], zi[U][kTS];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
+                        if (SEG && A.sub16 != nullptr && ((sb + u * kTS) & 15) == 0)
+                            save_sub16(A, L, pb, warp, lane, det, s0 + j * A.Tb + sb + u * kTS);
                         L.template step8<true>(ad, kTS, zr[u], zi[u]);
                         L.after8(A, j * A.Tb + sb + (u + 1) * kTS);
 #pragma unroll
@@ -710,6 +727,8 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             }
             for (; sb < nv; sb += kTS) {
                 const int valid = nv - sb;
+                if (SEG && A.sub16 != nullptr && (sb & 15) == 0)
+                    save_sub16(A, L, pb, warp, lane, det, s0 + j * A.Tb + sb);
                 float zr[kTS], zi[kTS];
                 if (valid >= kTS)
                     L.template step8<true>(ad, valid, zr, zi);
@@ -1025,7 +1044,9 @@ cudaError_t launch_kernel(Kernel k, const K1Args &a, int64_t n_units, int smem_b
 template <int FCAP>
 cudaError_t launch_k1_cap(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s)
 {
-    const bool seg = a.n_seg < a.n;   // several time segments
+    // several time segments, or span starts to keep (only the segment-capable
+    // kernels carry that code; one segment runs there as well)
+    const bool seg = a.n_seg < a.n || a.sub16 != nullptr;
     if (a.n_lower > 0)
         return seg ? launch_kernel(k1_plain<FCAP, true, true>, a, n_units, smem_bytes, s)
                    : launch_kernel(k1_plain<FCAP, false, true>, a, n_units, smem_bytes, s);

@@ -54,6 +54,9 @@ struct K1Args {
     int32_t low_len;           // float2 per template slot in the lower-band prefetch buffer           // lower bands added in the combine (0 = single rate)
     LowerBand lower[kMaxLowerBands];
     float2 *ckpt;              // [nc][D][n_slots] state after sample c*ckpt_blocks*Tb - 1
+    float2 *sub16;             // [ceil(n/16)][D][n_slots] state before every 16-sample span
+                               // (the adjoint's recompute points), or null; plain
+                               // precision only (the segment-capable kernels write it)
                                // (c >= 1), kernel form; null = no checkpoints
     int32_t ckpt_blocks;       // blocks between checkpoints
     int32_t n_det;             // detectors (checkpoint row stride)
@@ -102,6 +105,8 @@ struct K6Args {
     const float4 *params;      // kernel form (odd lanes hold conj(a), (Im b, Re b))
     const int2 *ringoff;
     const float2 *ckpt;        // [nc][D][n_slots] from the forward pass
+    const float2 *sub16;       // [ceil(n/16)][D][n_slots] state before every kAdjSub span
+                               // from the forward pass (then no per-chunk recompute), or null
     int64_t n_slots;
     int32_t n_det;
     float *acc;                // [P][D][n_slots][6] (mu re, im, g_a re, im, g_b re, im)
