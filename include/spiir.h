@@ -111,9 +111,12 @@ typedef struct spiir_options {
                             /* filters and the bank still fills >= 16 warps per SM */
                             /* at 16 lanes, else 32                                */
     int32_t time_segments;  /* plain precision: split each call into this many time */
-                            /* segments run in parallel (a zero-state pass plus an  */
-                            /* FP64 carry of the segment start states; segments are */
-                            /* >= 1 block long);  0 = auto: banks that fill < 1/8   */
+                            /* segments run in parallel, each from its start state */
+                            /* given by the projection below (segments are >= 1    */
+                            /* block long; spiir_filter_backward splits its reverse */
+                            /* pass into as many whole checkpoint intervals, auto: */
+                            /* ~4 waves of 16 warps/SM).  0 = auto: banks that fill */
+                            /* < 1/8                                               */
                             /* of the GPU's warps get up to 8 warps/SM worth (>= 4  */
                             /* segments, <= 64), banks under one full wave (16     */
                             /* warps/SM) get 2 on calls of >= 64 blocks, others    */
