@@ -40,6 +40,7 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
+template <bool GX>
 __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
 {
     // a lane's two filter rounds share FP32x2 registers: (round 0, round 1)
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
         // strain x[kc - Dh + i] = xe[kc + i] (xe holds Dh zeros before x)
         for (int i = threadIdx.x; i < Dw; i += blockDim.x) {
             xs[i] = i < A.Dh + cv ? xrow[kc + i] : 0.f;
-            gxs[i] = 0.f;
+            if (GX) gxs[i] = 0.f;
         }
         __syncthreads();
         if (active) {
@@ -187,35 +188,40 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
                 const int tl = lane & 15;
                 if ((half || lane < 16) && grow != nullptr && k0 + tl < cv)
                     gl = grow[kc + k0 + tl];
+                // one reverse step.  Steps past the call's end (the last span
+                // of a call of n % 16 != 0) run on g_z = 0 from mu = 0 (the
+                // last segment starts from zero): mu stays exactly 0 and every
+                // update they make adds zero.
 #pragma unroll
                 for (int t = kAdjSub - 1; t >= 0; --t) {
                     const float Gr = __shfl_sync(kFull, gl.x, gsrc + t);
                     const float Gi = __shfl_sync(kFull, gl.y, gsrc + t);
-                    if (k0 + t < cv) {
-                        // mu <- g_z + conj(a) mu
-                        const uint64_t NMR = fma2(AR, MR, fma2(AI, MI, pk(Gr, Gr)));
-                        const uint64_t NMI = fma2(AR, MI, fma2(NAI, MR, pk(Gi, Gi)));
-                        MR = NMR;
-                        MI = NMI;
-                        // g_a += mu conj(y[k-1]),  g_b += mu x[k-d]
-                        GAR = fma2(MR, PR[t], fma2(MI, PI[t], GAR));
-                        GAI1 = fma2(MI, PR[t], GAI1);
-                        GAI2 = fma2(MR, PI[t], GAI2);
-                        const uint64_t X = pk(xs[xo[0] + k0 + t], xs[xo[1] + k0 + t]);
-                        GBR = fma2(MR, X, GBR);
-                        GBI = fma2(MI, X, GBI);
-                        if (A.gx != nullptr) {   // g_x[k - d] += Re(conj(mu) b)
-                            float c0, c1;
-                            upk(fma2(MR, BR, mul2(MI, BI)), c0, c1);
-                            atomicAdd(&gxs[xo[0] + k0 + t], c0);
-                            if (nr > 1) atomicAdd(&gxs[xo[1] + k0 + t], c1);
-                        }
+                    // mu <- g_z + conj(a) mu
+                    const uint64_t NMR = fma2(AR, MR, fma2(AI, MI, pk(Gr, Gr)));
+                    const uint64_t NMI = fma2(AR, MI, fma2(NAI, MR, pk(Gi, Gi)));
+                    MR = NMR;
+                    MI = NMI;
+                    // g_a += mu conj(y[k-1]),  g_b += mu x[k-d]
+                    GAR = fma2(MR, PR[t], fma2(MI, PI[t], GAR));
+                    GAI1 = fma2(MI, PR[t], GAI1);
+                    GAI2 = fma2(MR, PI[t], GAI2);
+                    const uint64_t X = pk(xs[xo[0] + k0 + t], xs[xo[1] + k0 + t]);
+                    GBR = fma2(MR, X, GBR);
+                    GBI = fma2(MI, X, GBI);
+                    if (GX) {   // g_x[k - d] += Re(conj(mu) b)
+                        float c0, c1;
+                        upk(fma2(MR, BR, mul2(MI, BI)), c0, c1);
+                        atomicAdd(&gxs[xo[0] + k0 + t], c0);
+                        if (nr > 1) atomicAdd(&gxs[xo[1] + k0 + t], c1);
                     }
+                    // keeps the compiler from hoisting later steps' loads
+                    // into registers (128 per thread at two CTAs per SM)
+                    __syncwarp();
                 }
             }
         }
         __syncthreads();
-        if (A.gx != nullptr) {
+        if (GX) {
             // g_x[kc - Dh + i] gets this chunk's contributions
             float *gxrow = A.gx + (int64_t)det * n;
             for (int i = threadIdx.x; i < A.Dh + cv; i += blockDim.x) {
@@ -267,38 +273,106 @@ __global__ void adj_finalize(const float *acc, const int64_t *slot_filter, int64
     gb[f] = b;
 }
 
-// E[q] for q = 1..P-1: one thread per (segment, detector, slot), natural form
-// (mu <- g_z + conj(a) mu, as in the reverse pass)
-__global__ void adj_project_kernel(const float4 *params, const int32_t *slot_tmpl,
-                                   const float2 *gz, int64_t n_slots, int D, int64_t T, int64_t n,
-                                   int64_t seg_len, int P, float2 *E)
+// E[q] for q = 1..P-1: the adjoint state a segment's own g_z leaves at its
+// start, mu <- g_z + conj(a) mu run backwards over the segment from zero.
+// One thread per (segment, detector, 4 slots): the 4 slots sit in one
+// 32-slot round, so they share one template and one g_z row; they run as two
+// packed FP32x2 pairs, and g_z is loaded 8 samples ahead of the chain.
+constexpr int kProjSlots = 4;
+constexpr int kProjAhead = 8;
+
+__global__ void __launch_bounds__(128) adj_project_kernel(
+    const float4 *params, const int32_t *slot_tmpl, const float2 *gz, int64_t n_slots, int D,
+    int64_t T, int64_t n, int64_t seg_len, int P, float2 *E)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t per = (int64_t)D * n_slots;
-    if (i >= (int64_t)(P - 1) * per) return;
-    const int q = 1 + (int)(i / per);
-    const int64_t ds = i % per;
-    const int det = (int)(ds / n_slots);
-    const int64_t s = ds % n_slots;
-    const int tmpl = slot_tmpl[s];
-    float mr = 0.f, mi = 0.f;
+    const int64_t per4 = (int64_t)D * n_slots / kProjSlots;
+    if (i >= (int64_t)(P - 1) * per4) return;
+    const int q = 1 + (int)(i / per4);
+    const int64_t ds0 = (i % per4) * kProjSlots;   // first (detector, slot) of the four
+    const int det = (int)(ds0 / n_slots);
+    const int64_t s0 = ds0 % n_slots;
+    int tmpl = -1;
+    float ar[kProjSlots], ai[kProjSlots];
+#pragma unroll
+    for (int k = 0; k < kProjSlots; ++k) {
+        const int t = slot_tmpl[s0 + k];
+        tmpl = max(tmpl, t);   // padding slots are -1, the others share one template
+        const float4 p = params[s0 + k];
+        ar[k] = p.x;
+        ai[k] = ((s0 + k) & 1) ? -p.y : p.y;   // odd slots store conj(a)
+    }
+    uint64_t MR0 = 0, MI0 = 0, MR1 = 0, MI1 = 0;
     if (tmpl >= 0) {
-        const float4 p = params[s];
-        const float ar = p.x, ai = (s & 1) ? -p.y : p.y;   // odd slots store conj(a)
+        const uint64_t AR0 = pk(ar[0], ar[1]), AI0 = pk(ai[0], ai[1]);
+        const uint64_t NAI0 = pk(-ai[0], -ai[1]);
+        const uint64_t AR1 = pk(ar[2], ar[3]), AI1 = pk(ai[2], ai[3]);
+        const uint64_t NAI1 = pk(-ai[2], -ai[3]);
         const float2 *g = gz + ((int64_t)det * T + tmpl) * n;
         const int64_t j0 = (int64_t)q * seg_len, j1 = min(n, j0 + seg_len);
-        for (int64_t j = j1 - 1; j >= j0; --j) {
-            const float2 G = g[j];
-            const float nr = G.x + fmaf(ar, mr, ai * mi);
-            const float ni = G.y + fmaf(ar, mi, -ai * mr);
-            mr = nr;
-            mi = ni;
+        int64_t j = j1;
+        // whole groups of kProjAhead samples from the segment's end, then the rest
+        for (; j - kProjAhead >= j0; j -= kProjAhead) {
+            float2 G[kProjAhead];
+#pragma unroll
+            for (int t = 0; t < kProjAhead; ++t) G[t] = g[j - 1 - t];
+#pragma unroll
+            for (int t = 0; t < kProjAhead; ++t) {
+                const uint64_t GR = pk(G[t].x, G[t].x), GI = pk(G[t].y, G[t].y);
+                const uint64_t nr0 = fma2(AR0, MR0, fma2(AI0, MI0, GR));
+                const uint64_t ni0 = fma2(AR0, MI0, fma2(NAI0, MR0, GI));
+                const uint64_t nr1 = fma2(AR1, MR1, fma2(AI1, MI1, GR));
+                const uint64_t ni1 = fma2(AR1, MI1, fma2(NAI1, MR1, GI));
+                MR0 = nr0;
+                MI0 = ni0;
+                MR1 = nr1;
+                MI1 = ni1;
+            }
+        }
+        for (; j > j0; --j) {
+            const float2 G1 = g[j - 1];
+            const uint64_t GR = pk(G1.x, G1.x), GI = pk(G1.y, G1.y);
+            const uint64_t nr0 = fma2(AR0, MR0, fma2(AI0, MI0, GR));
+            const uint64_t ni0 = fma2(AR0, MI0, fma2(NAI0, MR0, GI));
+            const uint64_t nr1 = fma2(AR1, MR1, fma2(AI1, MI1, GR));
+            const uint64_t ni1 = fma2(AR1, MI1, fma2(NAI1, MR1, GI));
+            MR0 = nr0;
+            MI0 = ni0;
+            MR1 = nr1;
+            MI1 = ni1;
         }
     }
-    E[(int64_t)q * per + ds] = make_float2(mr, mi);
+    float mr[kProjSlots], mi[kProjSlots];
+    upk(MR0, mr[0], mr[1]);
+    upk(MI0, mi[0], mi[1]);
+    upk(MR1, mr[2], mr[3]);
+    upk(MI1, mi[2], mi[3]);
+    float2 *e = E + (int64_t)q * D * n_slots + ds0;
+#pragma unroll
+    for (int k = 0; k < kProjSlots; ++k)
+        e[k] = slot_tmpl[s0 + k] >= 0 ? make_float2(mr[k], mi[k]) : make_float2(0.f, 0.f);
 }
 
-// mu_end[P-1] = 0; mu_end[q] = E[q+1] + conj(a)^len(q+1) mu_end[q+1] (FP64)
+// conj(a)^len in FP64 by binary powering
+__device__ void conj_pow(double ar, double ai, int64_t len, double &rr, double &ri)
+{
+    double br = ar, bi = -ai;
+    rr = 1.0;
+    ri = 0.0;
+    for (int64_t e = len; e > 0; e >>= 1) {
+        if (e & 1) {
+            const double t = rr * br - ri * bi;
+            ri = rr * bi + ri * br;
+            rr = t;
+        }
+        const double t = br * br - bi * bi;
+        bi = 2.0 * br * bi;
+        br = t;
+    }
+}
+
+// mu_end[P-1] = 0; mu_end[q] = E[q+1] + conj(a)^len(q+1) mu_end[q+1] (FP64);
+// every segment but the last has seg_len samples
 __global__ void adj_carry_kernel(const float4 *params, const float2 *E, int64_t n_slots, int D,
                                  int64_t n, int64_t seg_len, int P, float2 *mu_end)
 {
@@ -308,22 +382,14 @@ __global__ void adj_carry_kernel(const float4 *params, const float2 *E, int64_t 
     const int64_t s = ds % n_slots;
     const float4 p = params[s];
     const double ar = p.x, ai = (s & 1) ? -(double)p.y : (double)p.y;
+    double fr, fi, lr, li;   // powers for a whole segment and for the last one
+    conj_pow(ar, ai, seg_len, fr, fi);
+    conj_pow(ar, ai, n - (int64_t)(P - 1) * seg_len, lr, li);
     double mr = 0.0, mi = 0.0;
     mu_end[(int64_t)(P - 1) * per + ds] = make_float2(0.f, 0.f);
     for (int q = P - 2; q >= 0; --q) {
-        const int64_t len = min(seg_len, n - (int64_t)(q + 1) * seg_len);
-        // conj(a)^len by binary powering
-        double br = ar, bi = -ai, rr = 1.0, ri = 0.0;
-        for (int64_t e = len; e > 0; e >>= 1) {
-            if (e & 1) {
-                const double t = rr * br - ri * bi;
-                ri = rr * bi + ri * br;
-                rr = t;
-            }
-            const double t = br * br - bi * bi;
-            bi = 2.0 * br * bi;
-            br = t;
-        }
+        const bool last = q + 1 == P - 1;
+        const double rr = last ? lr : fr, ri = last ? li : fi;
         const float2 e = E[(int64_t)(q + 1) * per + ds];
         const double nr = (double)e.x + rr * mr - ri * mi;
         const double ni = (double)e.y + rr * mi + ri * mr;
@@ -355,11 +421,16 @@ cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s)
     if (n_units <= 0 || a.n <= 0 || a.cps <= 0 || a.n_units != n_units)
         return n_units <= 0 || a.n <= 0 ? cudaSuccess : cudaErrorInvalidValue;
     const int smem = k6_smem_bytes(a.Cc, a.Dh);
-    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k6_adjoint), smem);
+    const void *fn = a.gx != nullptr ? reinterpret_cast<const void *>(k6_adjoint<true>)
+                                     : reinterpret_cast<const void *>(k6_adjoint<false>);
+    cudaError_t e = ensure_smem_limit(fn, smem);
     if (e != cudaSuccess) return e;
     const int64_t nc = (a.n + a.Cc - 1) / a.Cc;
     const int64_t P = (nc + a.cps - 1) / a.cps;
-    k6_adjoint<<<(unsigned)(n_units * P), a.W * 32, smem, s>>>(a);
+    if (a.gx != nullptr)
+        k6_adjoint<true><<<(unsigned)(n_units * P), a.W * 32, smem, s>>>(a);
+    else
+        k6_adjoint<false><<<(unsigned)(n_units * P), a.W * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -380,7 +451,8 @@ cudaError_t launch_adj_project(const float4 *params, const int32_t *slot_tmpl, c
     const int64_t per = (int64_t)D * n_slots;
     if (per <= 0 || P < 1) return cudaSuccess;
     if (P > 1) {
-        const int64_t th = (int64_t)(P - 1) * per;
+        if (n_slots % kProjSlots != 0) return cudaErrorInvalidValue;
+        const int64_t th = (int64_t)(P - 1) * per / kProjSlots;
         adj_project_kernel<<<(unsigned)((th + 127) / 128), 128, 0, s>>>(
             params, slot_tmpl, gz, n_slots, D, T, n, seg_len, P, E);
         cudaError_t e = cudaGetLastError();

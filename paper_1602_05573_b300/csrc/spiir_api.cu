@@ -725,11 +725,6 @@ int segments_for(const spiir_plan *p, const Band &b, int64_t nb)
     return (req < 1 && P < 2) ? 1 : P;
 }
 
-// Launch K1 for one band call split into time segments: a zero-state pass
-// over all but the last segment keeps each segment's end state, an FP64 carry
-// turns those into the true start state of every segment, and the main pass
-// runs every segment from its start state; per-segment peaks are merged in
-// time order.
 // Projection weights (tile layout, split BF16) and a^256 of a band, built on
 // first use and after every coefficient update.
 spiir_status ensure_tc_weights(spiir_plan *p, Band &b, cudaStream_t s)
@@ -874,6 +869,13 @@ spiir_status launch_anchored(spiir_plan *p, Band &b, spiir::K1Args a, cudaStream
     return SPIIR_OK;
 }
 
+// Launch K1 for one band call split into time segments.  The start state of
+// every segment comes either from the split-BF16 tensor-core projection of
+// the strain (chunk sums scanned across segments) or from a zero-state pass
+// over all but the last segment whose end states an FP64 carry turns into
+// true start states; the main pass then runs every segment from its start
+// state and the per-segment peaks are merged in time order.  The chunked
+// tensor-core precision goes to launch_anchored instead.
 spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cudaStream_t s,
                               int64_t *t0_advance = nullptr)
 {

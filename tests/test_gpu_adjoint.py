@@ -3,9 +3,9 @@ adjoint, which tests/test_oracle_pins.py pins to central differences and to
 the transpose identity.
 
 Gradient tolerance: the kernel accumulates each g_a, g_b over n samples in
-FP32 from FP32 states, and g_x with float atomics (so its last bits depend
-on summation order); the bar is 1e-3 of the largest entry of g_a, g_b and
-|g_x|.
+FP32 from FP32 states, and g_x in shared memory, then into global memory
+with float atomics (so its last bits depend on summation order); the bar is
+1e-3 of the largest entry of g_a, g_b and |g_x|.
 """
 import numpy as np
 import pytest
@@ -135,6 +135,31 @@ def test_adjoint_time_segments(sp, P):
     rng = np.random.default_rng(122)
     gz = (rng.standard_normal((2, 6, n)) + 1j * rng.standard_normal((2, 6, n))).astype(np.complex64)
     ga, gb, gx = gpu_backward(sp, bank, x, gz, time_segments=P)
+    ra, rb, rx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, gz)
+    assert rel_inf(ga, ra) <= GRAD_TOL
+    assert rel_inf(gb, rb) <= GRAD_TOL
+    assert rel_inf(gx, rx) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("delays", ["equal", "distinct"])
+def test_adjoint_delay_extremes(sp, delays):
+    """g_x gathers every filter's contribution at k - d in shared memory:
+    equal delays everywhere make every filter of a round add to the same
+    address at once, delays equal to the filter's index in its template make
+    every address of a round different."""
+    import dataclasses
+    bank = make_bank(5, (70, 200), (0.99, 0.9995), 300, seed=140, n_det=2)
+    counts = np.diff(bank.off)
+    if delays == "equal":
+        d = np.full(bank.d.shape, 37, np.int32)
+    else:
+        d = np.concatenate([np.arange(c, dtype=np.int32) for c in counts])
+    bank = dataclasses.replace(bank, d=d)
+    n = 2600
+    x = make_strain(2, n, seed=141)
+    rng = np.random.default_rng(142)
+    gz = (rng.standard_normal((2, 5, n)) + 1j * rng.standard_normal((2, 5, n))).astype(np.complex64)
+    ga, gb, gx = gpu_backward(sp, bank, x, gz)
     ra, rb, rx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, gz)
     assert rel_inf(ga, ra) <= GRAD_TOL
     assert rel_inf(gb, rb) <= GRAD_TOL
