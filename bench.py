@@ -426,7 +426,7 @@ def run_ours(args, rank, world, local_rank):
     info = plan.info()
     # our kernels per step, as the plan counted them for the last call (K1
     # passes, decimation, segment carry/merge, counter advance; the adjoint:
-    # checkpointed K1, K6, finalize), plus the spiir_peak copy
+    # checkpointed K1, projection, K6, K7, finalize), plus the spiir_peak copy
     launches_per_step = info["last_call_launches"] + (0 if adjoint else 1)
     clocks = clk.summary()
     peaks = measured_peaks()
@@ -448,13 +448,14 @@ def run_ours(args, rank, world, local_rank):
         timing = f"mean step time {filt_ms:.3f} ms (graph replay: no per-launch events)"
     achieved = lane_ops / (kernel_ms / 1e3) / 1e12
     if adjoint:
-        kernel = "k6_adjoint"
+        kernel = "k6_adjoint + k7_adjoint_x"
     traffic, traffic_note = None, None
     key = ("adjoint" if adjoint else args.workload, args.precision)
     if key in TRAFFIC and not args.samples and not args.templates:
         traffic, traffic_note = TRAFFIC[key]
     ops_note = ("20 algorithmic lane-ops per filter-update of the reverse pass (recompute 6, "
-                "adjoint recurrence 6, grad a 4, grad b 2, grad x 2)" if adjoint else
+                "adjoint recurrence 6, grad a 4, grad b 2, grad x 2) over the device time of "
+                "the reverse pass (k6) and the input-gradient pass (k7)" if adjoint else
                 "8 algorithmic lane-ops per filter-update")
     line = {
         "metric": "filter-updates/s", "value": value, "unit": "filter-updates/s",

@@ -234,8 +234,12 @@ spiir_status spiir_peak(spiir_plan *plan, float *peak_abs_dev, int64_t *peak_idx
  *   grad_a_dev, grad_b_dev  [Ltot] complex64 (summed over detectors)
  *   grad_x_dev              [n_detectors][n] float32, or NULL
  * The forward is recomputed from state checkpoints kept in plan workspace.
+ * grad_x is summed over filters in the shifted adjoint frame (each filter
+ * reads g_z at its own delay, all meet at one output sample) and over
+ * templates with float atomics, so its last bits depend on timing.
  * Does not touch the plan's streaming state.
- * Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED (multirate bank).
+ * Errors: EINVAL, ENOMEM, ECUDA, EUNSUPPORTED (multirate bank, or delays
+ * whose adjoint windows exceed 227 KB of shared memory).
  */
 spiir_status spiir_filter_backward(spiir_plan *plan, const float *x_dev, int64_t n,
                                    const float *grad_z_dev, float *grad_a_dev,
@@ -320,7 +324,7 @@ spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const float *x_de
  *   ms[SPIIR_KERNEL_CLASSES]  total milliseconds per class (host array)
  *   n[SPIIR_KERNEL_CLASSES]   launches per class (host array, may be NULL)
  * Classes: 0 the filter kernel (all K1 passes), 1 the tensor-core
- * projection, 2 the adjoint's reverse pass.
+ * projection, 2 the adjoint's reverse pass and its input-gradient pass.
  * Errors: EINVAL (NULL plan or ms), ECUDA. */
 #define SPIIR_KERNEL_CLASSES 3
 spiir_status spiir_kernel_times(spiir_plan *plan, double *ms, int64_t *n);

@@ -40,7 +40,6 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-template <bool GX>
 __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
 {
     // a lane's two filter rounds share FP32x2 registers: (round 0, round 1)
@@ -50,7 +49,6 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
     extern __shared__ __align__(16) unsigned char smem[];
     const int Dw = A.Dh + A.Cc;                          // strain window per chunk
     float *xs = reinterpret_cast<float *>(smem);         // [Dw]
-    float *gxs = xs + Dw;                                // [Dw]
     const int nsub_max = A.Cc / kAdjSub;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -101,6 +99,20 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
     const uint64_t AR = pk(ar[0], ar[1]), AI = pk(ai[0], ai[1]), NAI = pk(-ai[0], -ai[1]);
     const uint64_t BR = pk(br[0], br[1]), BI = pk(bi[0], bi[1]);
     uint64_t MR = pk(m0r[0], m0r[1]), MI = pk(m0i[0], m0i[1]);
+    // seeds of the input-gradient pass: segment q' of that pass starts from
+    // mu at k_t = (q' + 1) S + d, which lies in this segment when
+    // q' = seg - d / S - 1; the state at the top of the 16-sample span holding
+    // k_t is kept (-1: no target here)
+    const int S = A.cps * A.Cc;
+    int span_t[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        const int d = A.Dh - xo[i];
+        const int q = seg - d / S - 1;
+        const int kt = seg * S + d % S;
+        span_t[i] = (A.seeds != nullptr && active && i < nr && q >= 0 && q + 1 < A.P && kt < n)
+                        ? (kt & ~(kAdjSub - 1)) : -1;
+    }
     // g_a = sum mu conj(y[k-1]): Re in GAR, Im = GAI1 - GAI2; g_b = sum mu x
     uint64_t GAR = 0, GAI1 = 0, GAI2 = 0, GBR = 0, GBI = 0;
 
@@ -108,10 +120,7 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
         const int kc = c * A.Cc;
         const int cv = min(A.Cc, n - kc);
         // strain x[kc - Dh + i] = xe[kc + i] (xe holds Dh zeros before x)
-        for (int i = threadIdx.x; i < Dw; i += blockDim.x) {
-            xs[i] = i < A.Dh + cv ? xrow[kc + i] : 0.f;
-            if (GX) gxs[i] = 0.f;
-        }
+        for (int i = threadIdx.x; i < Dw; i += blockDim.x) xs[i] = i < A.Dh + cv ? xrow[kc + i] : 0.f;
         __syncthreads();
         if (active) {
             const int nsub = (cv + kAdjSub - 1) / kAdjSub;
@@ -154,6 +163,16 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
             // pass B: spans in reverse; y[k-1] recomputed into registers
             for (int q = nsub - 1; q >= 0; --q) {
                 const int k0 = q * kAdjSub;
+#pragma unroll
+                for (int i = 0; i < R; ++i)
+                    if (span_t[i] == kc + k0) {   // mu at kc + k0 + 16
+                        float r0, r1, i0, i1;
+                        upk(MR, r0, r1);
+                        upk(MI, i0, i1);
+                        const int qs = seg - (A.Dh - xo[i]) / S - 1;
+                        A.seeds[((int64_t)qs * A.n_det + det) * A.n_slots + slot[i]] =
+                            i == 0 ? make_float2(r0, i0) : make_float2(r1, i1);
+                    }
                 uint64_t PR[kAdjSub], PI[kAdjSub];   // y[k0 + t - 1], both rounds
                 {
                     float2 s0, s1;
@@ -208,26 +227,10 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
                     const uint64_t X = pk(xs[xo[0] + k0 + t], xs[xo[1] + k0 + t]);
                     GBR = fma2(MR, X, GBR);
                     GBI = fma2(MI, X, GBI);
-                    if (GX) {   // g_x[k - d] += Re(conj(mu) b)
-                        float c0, c1;
-                        upk(fma2(MR, BR, mul2(MI, BI)), c0, c1);
-                        atomicAdd(&gxs[xo[0] + k0 + t], c0);
-                        if (nr > 1) atomicAdd(&gxs[xo[1] + k0 + t], c1);
-                    }
                     // keeps the compiler from hoisting later steps' loads
                     // into registers (128 per thread at two CTAs per SM)
                     __syncwarp();
                 }
-            }
-        }
-        __syncthreads();
-        if (GX) {
-            // g_x[kc - Dh + i] gets this chunk's contributions
-            float *gxrow = A.gx + (int64_t)det * n;
-            for (int i = threadIdx.x; i < A.Dh + cv; i += blockDim.x) {
-                const int m = kc - A.Dh + i;
-                const float v = gxs[i];
-                if (m >= 0 && v != 0.f) atomicAdd(&gxrow[m], v);
             }
         }
         __syncthreads();
@@ -251,6 +254,137 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
 #pragma unroll
             for (int k = 0; k < 6; ++k) acc[k] = v[k][i];
         }
+    }
+}
+
+// Input gradient (the g_x part of the adjoint).  In the shifted frame
+// nu_l[m] = mu_l[m + d_l] every filter reads its template's g_z at its own
+// delay and all filters of the bank meet at the same output m, so the sum
+// over filters is a reduction, not a scatter.  A CTA serves one unit (the
+// tasks of one template, or one half-warp pair of templates) of one detector
+// over one time segment [q S, (q + 1) S), in reverse.  Per chunk of kK7Chunk
+// outputs it stages the template's g_z window [mc, mc + kK7Chunk + Dh) as
+// re and im planes; lane i runs its two filters as one FP32x2 pair,
+//     nu <- g_z[m + d] + conj(a) nu,    c = Re(conj(nu) b)  (both summed),
+// and writes c for 32 consecutive outputs into a 32 x 32 warp tile, XOR
+// swizzled so that the writes (one row) and the reads (lane j sums row j)
+// both hit 32 banks.  The warps' sums meet in a fixed order and go to g_x
+// with one atomic per output and CTA.  Segment q < P - 1 starts from
+// nu at (q + 1) S, i.e. mu at k_t = (q + 1) S + d, which the reverse pass kept
+// at the top of the 16-sample span holding k_t: at most 16 reverse steps on
+// g_z from there give it.
+__global__ void __launch_bounds__(kK7MaxWarps * 32, 4) k7_adjoint_x(const K7Args A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    constexpr int R = kAdjRounds;
+    const int n_win = A.G == 16 ? 2 : 1;
+    const int Wd = kK7Chunk + A.Dh;                 // window length
+    float *win = reinterpret_cast<float *>(smem);   // [n_win][2][Wd]: re plane, im plane
+    float *tile = win + n_win * 2 * Wd;             // [W][32][32]
+    float *part = tile + A.W * 1024;                // [W][kK7Chunk]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int per = A.n_units * A.n_det;
+    const int seg = (int)(blockIdx.x / per);
+    const int u = (int)(blockIdx.x % per) / A.n_det, det = (int)(blockIdx.x % per) % A.n_det;
+    const int2 unit = A.units[u];
+    const bool active = warp < unit.y;
+    const int4 task = A.tasks[unit.x + (active ? warp : 0)];
+    const int4 head = A.tasks[unit.x];               // the unit's template(s)
+    const int n = A.n;
+    const int mlo = seg * A.S, mhi = min(n, mlo + A.S);
+    const int nr = task.y;
+    const bool odd = (lane & 1) != 0;               // stored as conj(a), (Im b, Re b)
+    const int wsel = (A.G == 16 && lane >= 16) ? 1 : 0;
+    const int tmpl = wsel ? task.w : task.z;
+    const float2 *grow = A.gz + ((int64_t)det * A.T + (tmpl >= 0 ? tmpl : 0)) * n;
+
+    float ar[R], ai[R], br[R], bi[R], nu_r[R], nu_i[R];
+    int dd[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+        ar[i] = ai[i] = br[i] = bi[i] = nu_r[i] = nu_i[i] = 0.f;
+        dd[i] = 0;
+        if (!active || i >= nr) continue;
+        const int64_t slot = (int64_t)task.x + (int64_t)i * A.round_stride + lane;
+        const float4 p = A.params[slot];
+        ar[i] = p.x;
+        ai[i] = odd ? -p.y : p.y;
+        br[i] = odd ? p.w : p.z;
+        bi[i] = odd ? p.z : p.w;
+        dd[i] = A.Dh - A.ringoff[slot].x;
+        // start state nu[(q + 1) S] = mu[(q + 1) S + d] (zero past the call)
+        const int kt = mhi + dd[i];
+        if (seg + 1 < A.P && kt < n && tmpl >= 0) {
+            const float2 m0 = A.seeds[((int64_t)seg * A.n_det + det) * A.n_slots + slot];
+            float mr = m0.x, mi = m0.y;
+            for (int j = (kt & ~(kAdjSub - 1)) + kAdjSub - 1; j >= kt; --j) {
+                const float2 g = j < n ? grow[j] : make_float2(0.f, 0.f);
+                const float tr = fmaf(ar[i], mr, fmaf(ai[i], mi, g.x));
+                const float ti = fmaf(ar[i], mi, fmaf(-ai[i], mr, g.y));
+                mr = tr;
+                mi = ti;
+            }
+            nu_r[i] = mr;
+            nu_i[i] = mi;
+        }
+    }
+    const uint64_t AR = pk(ar[0], ar[1]), AI = pk(ai[0], ai[1]), NAI = pk(-ai[0], -ai[1]);
+    const uint64_t BR = pk(br[0], br[1]), BI = pk(bi[0], bi[1]);
+    uint64_t NR = pk(nu_r[0], nu_r[1]), NI = pk(nu_i[0], nu_i[1]);
+    const float *pr = win + wsel * 2 * Wd, *pim = pr + Wd;
+    float *wt = tile + warp * 1024;
+    float *gxrow = A.gx + (int64_t)det * n;
+
+    const int n_chunks = (mhi - mlo + kK7Chunk - 1) / kK7Chunk;
+    for (int c = n_chunks - 1; c >= 0; --c) {
+        const int mc = mlo + c * kK7Chunk;
+        const int cv = min(kK7Chunk, mhi - mc);
+        for (int w = 0; w < n_win; ++w) {
+            const int t = w ? head.w : head.z;
+            const float2 *row = A.gz + ((int64_t)det * A.T + (t >= 0 ? t : 0)) * n;
+            float *dr = win + w * 2 * Wd;
+            for (int i = threadIdx.x; i < Wd; i += blockDim.x) {
+                const int j = mc + i;
+                const float2 v = (t >= 0 && j < n) ? row[j] : make_float2(0.f, 0.f);
+                dr[i] = v.x;
+                dr[Wd + i] = v.y;
+            }
+        }
+        __syncthreads();
+        if (active) {
+            // steps at m >= n (the top block of the call's last chunk) run on
+            // g_z = 0 from nu = 0 and give zeros
+            for (int blk = (cv + 31) / 32 - 1; blk >= 0; --blk) {
+                const int mb = blk * 32;
+                const float *r0 = pr + dd[0] + mb, *r1 = pr + dd[1] + mb;
+                const float *i0 = pim + dd[0] + mb, *i1 = pim + dd[1] + mb;
+#pragma unroll
+                for (int t = 31; t >= 0; --t) {
+                    const uint64_t GR = pk(r0[t], r1[t]), GI = pk(i0[t], i1[t]);
+                    const uint64_t nR = fma2(AR, NR, fma2(AI, NI, GR));
+                    const uint64_t nI = fma2(AR, NI, fma2(NAI, NR, GI));
+                    NR = nR;
+                    NI = nI;
+                    float c0, c1;
+                    upk(fma2(NR, BR, mul2(NI, BI)), c0, c1);
+                    wt[t * 32 + (lane ^ t)] = c0 + c1;
+                }
+                __syncwarp();
+                // lane j: the warp's sum at output mb + j, in four chains
+                float s4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                for (int e = 0; e < 32; ++e) s4[e & 3] += wt[lane * 32 + (e ^ lane)];
+                part[warp * kK7Chunk + mb + lane] = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < cv; i += blockDim.x) {
+            float v = 0.f;
+            for (int w = 0; w < unit.y; ++w) v += part[w * kK7Chunk + i];
+            if (v != 0.f) atomicAdd(&gxrow[mc + i], v);
+        }
+        __syncthreads();
     }
 }
 
@@ -414,23 +548,38 @@ __global__ void set_coefficients(const float2 *a, const float2 *b, const int64_t
 
 }  // namespace
 
-int k6_smem_bytes(int Cc, int Dh) { return (int)(2 * sizeof(float) * (Dh + Cc)); }
+int k6_smem_bytes(int Cc, int Dh) { return (int)(sizeof(float) * (Dh + Cc)); }
 
 cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s)
 {
     if (n_units <= 0 || a.n <= 0 || a.cps <= 0 || a.n_units != n_units)
         return n_units <= 0 || a.n <= 0 ? cudaSuccess : cudaErrorInvalidValue;
     const int smem = k6_smem_bytes(a.Cc, a.Dh);
-    const void *fn = a.gx != nullptr ? reinterpret_cast<const void *>(k6_adjoint<true>)
-                                     : reinterpret_cast<const void *>(k6_adjoint<false>);
-    cudaError_t e = ensure_smem_limit(fn, smem);
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k6_adjoint), smem);
     if (e != cudaSuccess) return e;
     const int64_t nc = (a.n + a.Cc - 1) / a.Cc;
-    const int64_t P = (nc + a.cps - 1) / a.cps;
-    if (a.gx != nullptr)
-        k6_adjoint<true><<<(unsigned)(n_units * P), a.W * 32, smem, s>>>(a);
-    else
-        k6_adjoint<false><<<(unsigned)(n_units * P), a.W * 32, smem, s>>>(a);
+    if ((nc + a.cps - 1) / a.cps != a.P) return cudaErrorInvalidValue;
+    k6_adjoint<<<(unsigned)(n_units * a.P), a.W * 32, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+int k7_smem_bytes(int Dh, int W, int G)
+{
+    return (int)(sizeof(float) * ((G == 16 ? 2 : 1) * 2 * (kK7Chunk + Dh) + W * 1024 +
+                                  W * kK7Chunk));
+}
+
+cudaError_t launch_k7(const K7Args &a, cudaStream_t s)
+{
+    if (a.n_units <= 0 || a.n <= 0) return cudaSuccess;
+    // segments of whole 32-output blocks: only the call's last block runs
+    // past its end (on zero input)
+    if (a.W < 1 || a.W > kK7MaxWarps || a.S % 32 != 0 || (a.P > 1 && a.seeds == nullptr))
+        return cudaErrorInvalidValue;
+    const int smem = k7_smem_bytes(a.Dh, a.W, a.G);
+    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k7_adjoint_x), smem);
+    if (e != cudaSuccess) return e;
+    k7_adjoint_x<<<(unsigned)((int64_t)a.P * a.n_units * a.n_det), a.W * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -176,6 +176,10 @@ struct Band {
     int adj_seg_cap = 0;           // segments adj_E / adj_mu / acc hold
     float2 *adj_sub16 = nullptr;   // [n/16][D][n_slots] forward state at every span start
     int64_t adj_sub16_cap = 0;     //   float2 elements
+    int2 *adj_units7 = nullptr;    // input-gradient units: (first task, tasks) of one template
+    int64_t adj_n_units7 = 0;
+    int adj_W7 = 1;                // warps per input-gradient CTA (largest unit)
+    float2 *adj_seeds = nullptr;   // [P-1][D][n_slots] input-gradient segment seeds
 };
 
 struct spiir_plan {
@@ -273,6 +277,8 @@ void free_band(Band &b)
     cudaFree(b.adj_E);
     cudaFree(b.adj_mu);
     cudaFree(b.adj_sub16);
+    cudaFree(b.adj_units7);
+    cudaFree(b.adj_seeds);
     b = Band();
 }
 
@@ -1215,6 +1221,20 @@ spiir_status build_adjoint_tasks(Band &b, int D)
     const int64_t n_groups = (n_tasks + b.adj_W - 1) / b.adj_W;
     tasks.resize((size_t)n_groups * b.adj_W * 4, 0);
     for (int64_t i = n_tasks; i < n_groups * b.adj_W; ++i) tasks[4 * i + 2] = -1;  // empty
+    // input-gradient units: runs of tasks with the same template(s), split
+    // into pieces of at most kK7MaxWarps tasks
+    std::vector<int32_t> units7;
+    int W7 = 1;
+    for (int64_t i = 0; i < n_tasks;) {
+        int64_t j = i + 1;
+        while (j < n_tasks && j - i < spiir::kK7MaxWarps && tasks[4 * j + 2] == tasks[4 * i + 2] &&
+               tasks[4 * j + 3] == tasks[4 * i + 3])
+            ++j;
+        units7.push_back((int32_t)i);
+        units7.push_back((int32_t)(j - i));
+        W7 = std::max(W7, (int)(j - i));
+        i = j;
+    }
     std::vector<int32_t> units((size_t)n_groups * D * 2);
     for (int64_t g = 0; g < n_groups; ++g)
         for (int d = 0; d < D; ++d) {
@@ -1231,10 +1251,15 @@ spiir_status build_adjoint_tasks(Band &b, int D)
         (e = cudaMemcpy(b.adj_tasks, tasks.data(), tasks.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(b.adj_units, units.data(), units.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = dalloc(&b.adj_units7, units7.size() / 2)) != cudaSuccess ||
+        (e = cudaMemcpy(b.adj_units7, units7.data(), units7.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice)) != cudaSuccess)
         return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "adjoint task list")
                                               : cuda_fail(e, "adjoint task upload");
     b.adj_n_units = n_groups * D;
+    b.adj_n_units7 = (int64_t)units7.size() / 2;
+    b.adj_W7 = W7;
     return SPIIR_OK;
 }
 
@@ -1303,11 +1328,13 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         cudaFree(b.acc);
         cudaFree(b.adj_E);
         cudaFree(b.adj_mu);
+        cudaFree(b.adj_seeds);
         b.acc = nullptr;
-        b.adj_E = b.adj_mu = nullptr;
+        b.adj_E = b.adj_mu = b.adj_seeds = nullptr;
         if ((e = dalloc(&b.acc, (size_t)P * D * L.n_slots * 6)) != cudaSuccess ||
             (e = dalloc(&b.adj_E, (size_t)P * D * L.n_slots)) != cudaSuccess ||
-            (e = dalloc(&b.adj_mu, (size_t)P * D * L.n_slots)) != cudaSuccess)
+            (e = dalloc(&b.adj_mu, (size_t)P * D * L.n_slots)) != cudaSuccess ||
+            (e = dalloc(&b.adj_seeds, (size_t)P * D * L.n_slots)) != cudaSuccess)
             return oom(e);
         b.adj_seg_cap = P;
     }
@@ -1404,18 +1431,47 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     a.n_slots = L.n_slots;
     a.n_det = D;
     a.acc = b.acc;
-    a.gx = grad_x_dev;
+    a.seeds = (P > 1 && grad_x_dev) ? b.adj_seeds : nullptr;
     a.sub = b.adj_sub;
     a.n_units = (int32_t)b.adj_n_units;
     a.cps = (int32_t)cps;
+    a.P = P;
     a.sub16 = f.sub16;
     a.mu_end = P > 1 ? b.adj_mu : nullptr;
-    if (spiir::k6_smem_bytes(Cc, L.Dh) > 227 * 1024)
-        return fail(SPIIR_EUNSUPPORTED, "adjoint strain window above 227 KB of shared memory");
+    if (spiir::k6_smem_bytes(Cc, L.Dh) > 227 * 1024 ||
+        (grad_x_dev && spiir::k7_smem_bytes(L.Dh, b.adj_W7, L.G) > 227 * 1024))
+        return fail(SPIIR_EUNSUPPORTED, "adjoint windows above 227 KB of shared memory");
     const int ta = time_begin(p, s);
     if ((e = spiir::launch_k6(a, b.adj_n_units, s)) != cudaSuccess)
         return cuda_fail(e, "adjoint kernel launch");
     time_end(p, s, ta, kTimeAdj);
+    if (grad_x_dev) {
+        // input gradient in the shifted frame, seeded by the reverse pass
+        spiir::K7Args g{};
+        g.gz = a.gz;
+        g.T = p->T;
+        g.n = (int32_t)n;
+        g.Dh = L.Dh;
+        g.S = (int32_t)(cps * Cc);
+        g.P = P;
+        g.tasks = b.adj_tasks;
+        g.units = b.adj_units7;
+        g.n_units = (int32_t)b.adj_n_units7;
+        g.W = b.adj_W7;
+        g.round_stride = a.round_stride;
+        g.G = L.G;
+        g.params = b.params;
+        g.ringoff = b.ringoff;
+        g.n_slots = L.n_slots;
+        g.n_det = D;
+        g.seeds = a.seeds;
+        g.gx = grad_x_dev;
+        const int tg = time_begin(p, s);
+        if ((e = spiir::launch_k7(g, s)) != cudaSuccess)
+            return cuda_fail(e, "adjoint input-gradient launch");
+        time_end(p, s, tg, kTimeAdj);
+        p->last_launches += 1;
+    }
     if ((e = spiir::launch_adj_finalize(b.acc, b.slot_filter, L.n_slots, D, P,
                                         reinterpret_cast<float2 *>(grad_a_dev),
                                         reinterpret_cast<float2 *>(grad_b_dev), s)) !=

@@ -110,14 +110,42 @@ struct K6Args {
     int64_t n_slots;
     int32_t n_det;
     float *acc;                // [P][D][n_slots][6] (mu re, im, g_a re, im, g_b re, im)
-    float *gx;                 // [D][n] accumulated with atomics, or null
+    float2 *seeds;             // [P-1][D][n_slots] seeds of the input-gradient pass, or null
     float2 *sub;               // [P][n_units][W][kAdjRounds][Cc / kAdjSub][32] workspace
     // time segments of whole chunks: CTA b serves unit b % n_units over the
     // chunks of segment b / n_units, from mu at the segment's end (null: 0)
     int32_t n_units;
     int32_t cps;               // chunks per segment
+    int32_t P;                 // segments
     const float2 *mu_end;      // [P][D][n_slots] natural form
 };
+
+// Input gradient of the adjoint, g_x[m] = sum_l Re(conj(nu_l[m]) b_l) with
+// nu_l[m] = mu_l[m + d_l] = g_z[m + d_l] + conj(a_l) nu_l[m + 1]: every filter
+// reads its template's g_z at its own delay and all filters meet at m.
+struct K7Args {
+    const float2 *gz;          // [D][T][n]
+    int64_t T;
+    int32_t n, Dh;             // samples; history (>= max delay)
+    int32_t S, P;              // segment length (a multiple of 32), segments
+    const int4 *tasks;         // the adjoint task list
+    const int2 *units;         // [n_units] (first task, tasks): tasks of one template
+                               //  (or one half-warp pair), at most kK7MaxWarps
+    int32_t n_units, W;        // units; warps per CTA (largest unit)
+    int32_t round_stride;
+    int32_t G;
+    const float4 *params;
+    const int2 *ringoff;
+    int64_t n_slots;
+    int32_t n_det;
+    const float2 *seeds;       // [P-1][D][n_slots]: mu at the top of the 16-sample span
+                               //  holding (q + 1) S + d, natural form
+    float *gx;                 // [D][n], zeroed by the caller; CTAs add with atomics
+};
+constexpr int kK7Chunk = 256;   // outputs per staged g_z window
+constexpr int kK7MaxWarps = 8;
+cudaError_t launch_k7(const K7Args &a, cudaStream_t s);
+int k7_smem_bytes(int Dh, int W, int G);
 constexpr int kAdjSub = 16;    // samples per recomputed span in the adjoint
 constexpr int kAdjRounds = 2;  // filter rounds per adjoint task (independent chains per lane)
 
