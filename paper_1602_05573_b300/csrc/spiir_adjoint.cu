@@ -273,7 +273,8 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
 // nu at (q + 1) S, i.e. mu at k_t = (q + 1) S + d, which the reverse pass kept
 // at the top of the 16-sample span holding k_t: at most 16 reverse steps on
 // g_z from there give it.
-__global__ void __launch_bounds__(kK7MaxWarps * 32, 4) k7_adjoint_x(const K7Args A)
+template <int NP>
+__global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int R = kAdjRounds;
@@ -287,51 +288,64 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 4) k7_adjoint_x(const K7Args
     const int seg = (int)(blockIdx.x / per);
     const int u = (int)(blockIdx.x % per) / A.n_det, det = (int)(blockIdx.x % per) % A.n_det;
     const int2 unit = A.units[u];
-    const bool active = warp < unit.y;
-    const int4 task = A.tasks[unit.x + (active ? warp : 0)];
+    const int n_warps = (unit.y + NP - 1) / NP;     // warps with tasks
+    const bool active = warp < n_warps;
     const int4 head = A.tasks[unit.x];               // the unit's template(s)
     const int n = A.n;
     const int mlo = seg * A.S, mhi = min(n, mlo + A.S);
-    const int nr = task.y;
     const bool odd = (lane & 1) != 0;               // stored as conj(a), (Im b, Re b)
     const int wsel = (A.G == 16 && lane >= 16) ? 1 : 0;
-    const int tmpl = wsel ? task.w : task.z;
+    const int tmpl = wsel ? head.w : head.z;
     const float2 *grow = A.gz + ((int64_t)det * A.T + (tmpl >= 0 ? tmpl : 0)) * n;
+    const float *pr = win + wsel * 2 * Wd;
 
-    float ar[R], ai[R], br[R], bi[R], nu_r[R], nu_i[R];
-    int dd[R];
+    // pair p of this lane: the two rounds of task unit.x + NP warp + p
+    uint64_t AR[NP], AI[NP], NAI[NP], BR[NP], BI[NP], NR[NP], NI[NP];
+    const float *rp[NP][R];
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-        ar[i] = ai[i] = br[i] = bi[i] = nu_r[i] = nu_i[i] = 0.f;
-        dd[i] = 0;
-        if (!active || i >= nr) continue;
-        const int64_t slot = (int64_t)task.x + (int64_t)i * A.round_stride + lane;
-        const float4 p = A.params[slot];
-        ar[i] = p.x;
-        ai[i] = odd ? -p.y : p.y;
-        br[i] = odd ? p.w : p.z;
-        bi[i] = odd ? p.z : p.w;
-        dd[i] = A.Dh - A.ringoff[slot].x;
-        // start state nu[(q + 1) S] = mu[(q + 1) S + d] (zero past the call)
-        const int kt = mhi + dd[i];
-        if (seg + 1 < A.P && kt < n && tmpl >= 0) {
-            const float2 m0 = A.seeds[((int64_t)seg * A.n_det + det) * A.n_slots + slot];
-            float mr = m0.x, mi = m0.y;
-            for (int j = (kt & ~(kAdjSub - 1)) + kAdjSub - 1; j >= kt; --j) {
-                const float2 g = j < n ? grow[j] : make_float2(0.f, 0.f);
-                const float tr = fmaf(ar[i], mr, fmaf(ai[i], mi, g.x));
-                const float ti = fmaf(ar[i], mi, fmaf(-ai[i], mr, g.y));
-                mr = tr;
-                mi = ti;
+    for (int p = 0; p < NP; ++p) {
+        const int k = NP * warp + p;
+        const bool on = active && k < unit.y;
+        const int4 task = A.tasks[unit.x + (on ? k : 0)];
+        const int nr = on ? task.y : 0;
+        float ar[R], ai[R], br[R], bi[R], nu_r[R], nu_i[R];
+#pragma unroll
+        for (int i = 0; i < R; ++i) {
+            ar[i] = ai[i] = br[i] = bi[i] = nu_r[i] = nu_i[i] = 0.f;
+            rp[p][i] = pr;
+            if (i >= nr) continue;
+            const int64_t slot = (int64_t)task.x + (int64_t)i * A.round_stride + lane;
+            const float4 q = A.params[slot];
+            ar[i] = q.x;
+            ai[i] = odd ? -q.y : q.y;
+            br[i] = odd ? q.w : q.z;
+            bi[i] = odd ? q.z : q.w;
+            const int d = A.Dh - A.ringoff[slot].x;
+            rp[p][i] = pr + d;
+            // start state nu[(q + 1) S] = mu[(q + 1) S + d] (zero past the call)
+            const int kt = mhi + d;
+            if (seg + 1 < A.P && kt < n && tmpl >= 0) {
+                const float2 m0 = A.seeds[((int64_t)seg * A.n_det + det) * A.n_slots + slot];
+                float mr = m0.x, mi = m0.y;
+                for (int j = (kt & ~(kAdjSub - 1)) + kAdjSub - 1; j >= kt; --j) {
+                    const float2 g = j < n ? grow[j] : make_float2(0.f, 0.f);
+                    const float tr = fmaf(ar[i], mr, fmaf(ai[i], mi, g.x));
+                    const float ti = fmaf(ar[i], mi, fmaf(-ai[i], mr, g.y));
+                    mr = tr;
+                    mi = ti;
+                }
+                nu_r[i] = mr;
+                nu_i[i] = mi;
             }
-            nu_r[i] = mr;
-            nu_i[i] = mi;
         }
+        AR[p] = pk(ar[0], ar[1]);
+        AI[p] = pk(ai[0], ai[1]);
+        NAI[p] = pk(-ai[0], -ai[1]);
+        BR[p] = pk(br[0], br[1]);
+        BI[p] = pk(bi[0], bi[1]);
+        NR[p] = pk(nu_r[0], nu_r[1]);
+        NI[p] = pk(nu_i[0], nu_i[1]);
     }
-    const uint64_t AR = pk(ar[0], ar[1]), AI = pk(ai[0], ai[1]), NAI = pk(-ai[0], -ai[1]);
-    const uint64_t BR = pk(br[0], br[1]), BI = pk(bi[0], bi[1]);
-    uint64_t NR = pk(nu_r[0], nu_r[1]), NI = pk(nu_i[0], nu_i[1]);
-    const float *pr = win + wsel * 2 * Wd, *pim = pr + Wd;
     float *wt = tile + warp * 1024;
     float *gxrow = A.gx + (int64_t)det * n;
 
@@ -356,18 +370,22 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 4) k7_adjoint_x(const K7Args
             // g_z = 0 from nu = 0 and give zeros
             for (int blk = (cv + 31) / 32 - 1; blk >= 0; --blk) {
                 const int mb = blk * 32;
-                const float *r0 = pr + dd[0] + mb, *r1 = pr + dd[1] + mb;
-                const float *i0 = pim + dd[0] + mb, *i1 = pim + dd[1] + mb;
 #pragma unroll
                 for (int t = 31; t >= 0; --t) {
-                    const uint64_t GR = pk(r0[t], r1[t]), GI = pk(i0[t], i1[t]);
-                    const uint64_t nR = fma2(AR, NR, fma2(AI, NI, GR));
-                    const uint64_t nI = fma2(AR, NI, fma2(NAI, NR, GI));
-                    NR = nR;
-                    NI = nI;
-                    float c0, c1;
-                    upk(fma2(NR, BR, mul2(NI, BI)), c0, c1);
-                    wt[t * 32 + (lane ^ t)] = c0 + c1;
+                    float c = 0.f;
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        const uint64_t GR = pk(rp[p][0][mb + t], rp[p][1][mb + t]);
+                        const uint64_t GI = pk(rp[p][0][Wd + mb + t], rp[p][1][Wd + mb + t]);
+                        const uint64_t nR = fma2(AR[p], NR[p], fma2(AI[p], NI[p], GR));
+                        const uint64_t nI = fma2(AR[p], NI[p], fma2(NAI[p], NR[p], GI));
+                        NR[p] = nR;
+                        NI[p] = nI;
+                        float c0, c1;
+                        upk(fma2(NR[p], BR[p], mul2(NI[p], BI[p])), c0, c1);
+                        c += c0 + c1;
+                    }
+                    wt[t * 32 + (lane ^ t)] = c;
                 }
                 __syncwarp();
                 // lane j: the warp's sum at output mb + j, in four chains
@@ -381,7 +399,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 4) k7_adjoint_x(const K7Args
         __syncthreads();
         for (int i = threadIdx.x; i < cv; i += blockDim.x) {
             float v = 0.f;
-            for (int w = 0; w < unit.y; ++w) v += part[w * kK7Chunk + i];
+            for (int w = 0; w < n_warps; ++w) v += part[w * kK7Chunk + i];
             if (v != 0.f) atomicAdd(&gxrow[mc + i], v);
         }
         __syncthreads();
@@ -577,9 +595,17 @@ cudaError_t launch_k7(const K7Args &a, cudaStream_t s)
     if (a.W < 1 || a.W > kK7MaxWarps || a.S % 32 != 0 || (a.P > 1 && a.seeds == nullptr))
         return cudaErrorInvalidValue;
     const int smem = k7_smem_bytes(a.Dh, a.W, a.G);
-    cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k7_adjoint_x), smem);
+    // two tasks per warp (two independent chains per lane), one for half-warp
+    // templates (a unit is then a single task)
+    const void *fn = a.G == 16 ? reinterpret_cast<const void *>(k7_adjoint_x<1>)
+                               : reinterpret_cast<const void *>(k7_adjoint_x<2>);
+    cudaError_t e = ensure_smem_limit(fn, smem);
     if (e != cudaSuccess) return e;
-    k7_adjoint_x<<<(unsigned)((int64_t)a.P * a.n_units * a.n_det), a.W * 32, smem, s>>>(a);
+    const unsigned grid = (unsigned)((int64_t)a.P * a.n_units * a.n_det);
+    if (a.G == 16)
+        k7_adjoint_x<1><<<grid, a.W * 32, smem, s>>>(a);
+    else
+        k7_adjoint_x<2><<<grid, a.W * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -1439,7 +1439,8 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     a.sub16 = f.sub16;
     a.mu_end = P > 1 ? b.adj_mu : nullptr;
     if (spiir::k6_smem_bytes(Cc, L.Dh) > 227 * 1024 ||
-        (grad_x_dev && spiir::k7_smem_bytes(L.Dh, b.adj_W7, L.G) > 227 * 1024))
+        (grad_x_dev &&
+         spiir::k7_smem_bytes(L.Dh, L.G == 16 ? b.adj_W7 : (b.adj_W7 + 1) / 2, L.G) > 227 * 1024))
         return fail(SPIIR_EUNSUPPORTED, "adjoint windows above 227 KB of shared memory");
     const int ta = time_begin(p, s);
     if ((e = spiir::launch_k6(a, b.adj_n_units, s)) != cudaSuccess)
@@ -1457,7 +1458,7 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         g.tasks = b.adj_tasks;
         g.units = b.adj_units7;
         g.n_units = (int32_t)b.adj_n_units7;
-        g.W = b.adj_W7;
+        g.W = L.G == 16 ? b.adj_W7 : (b.adj_W7 + 1) / 2;
         g.round_stride = a.round_stride;
         g.G = L.G;
         g.params = b.params;

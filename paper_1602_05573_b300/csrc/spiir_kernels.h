@@ -131,7 +131,8 @@ struct K7Args {
     const int4 *tasks;         // the adjoint task list
     const int2 *units;         // [n_units] (first task, tasks): tasks of one template
                                //  (or one half-warp pair), at most kK7MaxWarps
-    int32_t n_units, W;        // units; warps per CTA (largest unit)
+    int32_t n_units, W;        // units; warps per CTA (tasks of the largest unit / tasks
+                               //  per warp: 2, or 1 for half-warp templates)
     int32_t round_stride;
     int32_t G;
     const float4 *params;
