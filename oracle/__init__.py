@@ -170,3 +170,62 @@ def adjoint(off, a, b, d, x, gz, *, want_gx=True, n_threads=None):
     if rc != 0:
         raise MemoryError("oracle allocation failed")
     return ga[:, 0] + 1j * ga[:, 1], gb[:, 0] + 1j * gb[:, 1], gx
+
+
+# planted mistakes understood by network_peak (mutation tests only)
+NETWORK_MUTATIONS = ("window_short", "last_on_tie", "skip_detector", "shift_last")
+
+
+def network_peak(z, window, *, mutation=None):
+    """Coincidence of one template's SNR series across detectors (the network
+    SNR, maximised over arrival-time offsets that the detector separations
+    allow; the review's multi-messenger section localises a source from such
+    arrival-time differences).  Detector 0 is the reference; for detector
+    d >= 1 an offset u with |u| <= window[d] is allowed, positions outside the
+    series [0, n) excluded:
+
+        s(t) = |z_0(t)|^2 + sum_{d>=1} max_{|u| <= w_d, 0 <= t+u < n} |z_d(t+u)|^2
+
+    Per template: t* = the first t maximising s, rho = sqrt(s(t*)), and for
+    every d >= 1 the first u (from -w_d upward) whose |z_d(t*+u)|^2 reaches
+    the max at t* (0 for d = 0).
+
+    The values decide integers (t*, u), so they are taken in float32, as the
+    kernel takes them: |z|^2 = re*re + im*im with separately rounded products,
+    the detector terms added in detector order, a correctly rounded sqrt.
+    z: complex64 [D][T][n]; window: ints [D] (window[0] is ignored).
+    Returns (rho float32 [T], t int64 [T], shift int32 [T][D])."""
+    z = np.asarray(z, np.complex64)
+    D, T, n = z.shape
+    window = [int(w) - (1 if mutation == "window_short" and int(w) > 0 else 0) for w in window]
+    D_used = D - 1 if mutation == "skip_detector" and D > 1 else D
+    re = z.real.astype(np.float32)
+    im = z.imag.astype(np.float32)
+    p = re * re + im * im                       # float32, two roundings then one
+    s = p[0].copy()
+    wmax = []
+    for d in range(1, D_used):
+        w = int(window[d])
+        m = np.full((T, n), -np.inf, np.float32)
+        for u in range(-w, w + 1):
+            lo, hi = max(0, -u), min(n, n - u)
+            if lo < hi:
+                m[:, lo:hi] = np.maximum(m[:, lo:hi], p[d][:, lo + u:hi + u])
+        wmax.append(m)
+        s = s + m                               # float32, detector order
+    t = np.argmax(s, axis=1).astype(np.int64)   # first index of the max
+    if mutation == "last_on_tie":
+        t = (n - 1 - np.argmax(s[:, ::-1], axis=1)).astype(np.int64)
+    rows = np.arange(T)
+    rho = np.sqrt(s[rows, t]).astype(np.float32)
+    shift = np.zeros((T, D), np.int32)
+    for d in range(1, D_used):
+        w = int(window[d])
+        order = range(w, -w - 1, -1) if mutation == "shift_last" else range(-w, w + 1)
+        for k in range(T):
+            tk = int(t[k])
+            for u in order:
+                if 0 <= tk + u < n and p[d][k, tk + u] == wmax[d - 1][k, tk]:
+                    shift[k, d] = u
+                    break
+    return rho, t, shift

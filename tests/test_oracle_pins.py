@@ -308,3 +308,126 @@ def test_adjoint_transpose_identity():
     lhs = float(np.real(np.sum(np.conj(G) * Axp)))
     rhs = float(np.sum(xp * gx))
     assert abs(lhs - rhs) <= 1e-11 * max(abs(lhs), 1.0)
+
+
+# ------------------------------------------------- network peak (coincidence) ---
+# The network statistic maximises, per template, the sum over detectors of
+# |z|^2 over arrival-time offsets allowed by the detector separations
+# (reference detector 0; |u| <= w_d for detector d).  Pins: the single-
+# detector case is the plain argmax of |z|, a planted event with known
+# offsets gives the closed-form value, a pure-Python loop over every (t, d,
+# u) on tiny inputs (with exact ties), and shift invariance.
+
+def _net_brute(z, window):
+    """Every t, d, u by plain loops, float32 scalars in the kernel's order."""
+    z = np.asarray(z, np.complex64)
+    D, T, n = z.shape
+    f32 = np.float32
+
+    def p(d, k, t):
+        v = z[d, k, t]
+        return f32(f32(f32(v.real) * f32(v.real)) + f32(f32(v.imag) * f32(v.imag)))
+    rho = np.zeros(T, np.float32)
+    tt = np.zeros(T, np.int64)
+    sh = np.zeros((T, D), np.int32)
+    for k in range(T):
+        best, best_t, best_u = None, 0, None
+        for t in range(n):
+            s = p(0, k, t)
+            us = [0]
+            for d in range(1, D):
+                m, mu = None, 0
+                for u in range(-int(window[d]), int(window[d]) + 1):
+                    if 0 <= t + u < n and (m is None or p(d, k, t + u) > m):
+                        m, mu = p(d, k, t + u), u
+                s = f32(s + m)
+                us.append(mu)
+            if best is None or s > best:
+                best, best_t, best_u = s, t, us
+        rho[k] = np.sqrt(f32(best))
+        tt[k] = best_t
+        sh[k] = best_u
+    return rho, tt, sh
+
+
+def pin_network_single_detector(mutation=None):
+    rng = np.random.default_rng(140)
+    z = (rng.standard_normal((1, 5, 300)) + 1j * rng.standard_normal((1, 5, 300))).astype(
+        np.complex64)
+    rho, t, sh = oracle.network_peak(z, [0], mutation=mutation)
+    mag = np.abs(z[0].astype(np.complex128))
+    assert np.array_equal(t, np.argmax(mag, axis=1))
+    assert np.allclose(rho, mag[np.arange(5), t], rtol=1e-6, atol=0)
+    assert not sh.any()
+
+
+def pin_network_planted_event(mutation=None):
+    """Zero series with one spike per detector at t0 + offset_d: the peak is
+    at t0 with the offsets as shifts and rho = sqrt(sum of squared spikes);
+    an offset at the window's edge still counts, one past it does not."""
+    z = np.zeros((3, 2, 120), np.complex64)
+    z[0, 0, 50], z[1, 0, 57], z[2, 0, 45] = 3, 4j, 12            # offsets +7, -5
+    z[0, 1, 60], z[1, 1, 69], z[2, 1, 60] = 6, 8, 0.5             # +9: outside w = 7
+    rho, t, sh = oracle.network_peak(z, [0, 7, 5], mutation=mutation)
+    assert t[0] == 50 and list(sh[0]) == [0, 7, -5] and rho[0] == np.float32(13.0)
+    # template 1: detector 1's spike is out of reach of t = 60, but t = 62
+    # sees both it (u = +7) and detector 2's spike (u = -2)
+    s60 = 36 + 0 + 0.25
+    s62 = 0 + 64 + 0.25
+    assert s62 > s60
+    assert t[1] == 62 and list(sh[1]) == [0, 7, -2]
+    assert rho[1] == np.sqrt(np.float32(64.25))
+
+
+def pin_network_brute_force(mutation=None):
+    rng = np.random.default_rng(141)
+    # small integers: many exact ties in |z|^2 and in s
+    z = (rng.integers(-2, 3, (3, 4, 37)) + 1j * rng.integers(-2, 3, (3, 4, 37))).astype(
+        np.complex64)
+    window = [0, 2, 5]
+    got = oracle.network_peak(z, window, mutation=mutation)
+    want = _net_brute(z, window)
+    for g, w in zip(got, want):
+        assert np.array_equal(g, w)
+    zr = (rng.standard_normal((2, 3, 64)) + 1j * rng.standard_normal((2, 3, 64))).astype(
+        np.complex64)
+    for g, w in zip(oracle.network_peak(zr, [0, 3], mutation=mutation), _net_brute(zr, [0, 3])):
+        assert np.array_equal(g, w)
+
+
+def pin_network_shift_invariance(mutation=None):
+    """Delaying detector 2 by s samples adds s to its shift and leaves the
+    peak, when the offsets stay within the window and away from the ends."""
+    rng = np.random.default_rng(142)
+    z = 0.1 * (rng.standard_normal((3, 3, 400)) + 1j * rng.standard_normal((3, 3, 400)))
+    z = z.astype(np.complex64)
+    for k, t0 in enumerate((100, 200, 300)):
+        z[0, k, t0], z[1, k, t0 + 2], z[2, k, t0 - 1] = 5, 4, 3
+    window = [0, 6, 6]
+    rho, t, sh = oracle.network_peak(z, window, mutation=mutation)
+    z2 = z.copy()
+    z2[2] = np.roll(z[2], 3, axis=1)
+    rho2, t2, sh2 = oracle.network_peak(z2, window, mutation=mutation)
+    assert np.array_equal(t, t2) and np.array_equal(rho, rho2)
+    assert np.array_equal(sh2[:, 2], sh[:, 2] + 3) and np.array_equal(sh2[:, 1], sh[:, 1])
+    assert list(t) == [100, 200, 300] and list(sh[:, 1]) == [2, 2, 2]
+
+
+NETWORK_PINS = [pin_network_single_detector, pin_network_planted_event, pin_network_brute_force,
+                pin_network_shift_invariance]
+
+
+@pytest.mark.parametrize("pin", NETWORK_PINS, ids=lambda f: f.__name__)
+def test_network_peak_pins(pin):
+    pin()
+
+
+@pytest.mark.parametrize("mutation", oracle.NETWORK_MUTATIONS)
+def test_network_mutations_are_caught(mutation):
+    failed = 0
+    for pin in NETWORK_PINS:
+        try:
+            pin(mutation)
+        except AssertionError:
+            failed += 1
+    assert failed > 0, mutation
