@@ -227,6 +227,34 @@ spiir_status spiir_peak(spiir_plan *plan, float *peak_abs_dev, int64_t *peak_idx
                         void *stream);
 
 /*
+ * Network peak across detectors (coincidence of the SNR series).  A signal
+ * reaches the detectors at times that differ by at most their light travel
+ * time; the review's multi-messenger section localises a source from these
+ * arrival-time differences.  With detector 0 as the reference, per template
+ *   s(t) = |z_0(t)|^2 + sum_{d>=1} max_{|u| <= window[d], 0 <= t+u < n} |z_d(t+u)|^2,
+ * over t in [0, n), and returns the first t maximising s, rho = sqrt(s(t)),
+ * and per detector d >= 1 the first offset u (from -window[d] upward) whose
+ * |z_d(t+u)|^2 reaches that maximum.  |z|^2 = re*re + im*im with separately
+ * rounded float32 products, the detector terms summed in detector order and
+ * a correctly rounded sqrt, so t and the offsets are exact.
+ *   z_dev      [n_detectors][n_templates][n] complex64, device (the layout
+ *              spiir_filter writes)
+ *   window     [n_detectors] int32, host; window[0] is ignored, others in
+ *              [0, 1024] samples
+ *   rho_dev    [n_templates] float32, device
+ *   t_dev      [n_templates] int64, device
+ *   shift_dev  [n_templates][n_detectors] int32, device, or NULL (column 0 = 0)
+ * No plan: works on any series of that layout, on the current device,
+ * asynchronously on `stream`.  1 <= n_detectors <= 8, n >= 1 (n_templates
+ * = 0 is a no-op).
+ * Errors: EINVAL, EUNSUPPORTED (windows too wide for shared memory), ECUDA.
+ */
+spiir_status spiir_network_peak(const float *z_dev, int32_t n_detectors, int64_t n_templates,
+                                int64_t n, const int32_t *window, float *rho_dev,
+                                int64_t *t_dev, int32_t *shift_dev, void *stream);
+
+/*
+ * Vector-Jacobian product of one spiir_filter call made from zero state on/*
  * Vector-Jacobian product of one spiir_filter call made from zero state on
  * x_dev (single-rate banks).  grad_z_dev [n_detectors][n_templates][n]
  * complex64 holds g_z = dL/dRe z + i dL/dIm z (the PyTorch convention);

@@ -42,6 +42,7 @@ SYMBOLS = [
     "spiir_peak", "spiir_filter_backward", "spiir_state_get", "spiir_state_set",
     "spiir_check", "spiir_selftest_bounded_wait", "spiir_status_str",
     "spiir_last_error_detail", "spiir_filter_noalloc", "spiir_set_coefficients",
+    "spiir_network_peak",
 ]
 
 
@@ -100,6 +101,9 @@ def _configure(lib):
     lib.spiir_peak.restype = _st
     lib.spiir_filter_backward.argtypes = [_P, _P, ctypes.c_int64, _P, _P, _P, _P, _P]
     lib.spiir_filter_backward.restype = _st
+    lib.spiir_network_peak.argtypes = [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P,
+                                       _P, _P, _P, _P]
+    lib.spiir_network_peak.restype = _st
     lib.spiir_state_get.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int64)]
     lib.spiir_state_get.restype = _st
     lib.spiir_state_set.argtypes = [_P, _P, _P, ctypes.c_int64]
@@ -444,6 +448,27 @@ def _autograd_function():
             return gx, ga, gb, None
 
     return SpiirFilterFunction
+
+
+def network_peak(z, window, *, want_shift: bool = True, stream=None, lib=None):
+    """Network peak across detectors through spiir_network_peak: z CUDA
+    complex64 [D][T][n] (spiir_filter's layout), window ints [D] (offsets
+    allowed per detector, window[0] ignored).  Returns (rho float32 [T],
+    t int64 [T], shift int32 [T][D] or None)."""
+    import torch
+    lib = lib or library()
+    assert z.is_cuda and z.dtype == torch.complex64 and z.dim() == 3
+    z = z.contiguous()
+    D, T, n = z.shape
+    w = np.ascontiguousarray(np.asarray(window, np.int32).reshape(D))
+    rho = torch.empty(T, dtype=torch.float32, device=z.device)
+    t = torch.empty(T, dtype=torch.int64, device=z.device)
+    shift = torch.empty((T, D), dtype=torch.int32, device=z.device) if want_shift else None
+    with torch.cuda.device(z.device):
+        _check(lib.spiir_network_peak(_ptr(z), D, T, n, w.ctypes.data, _ptr(rho), _ptr(t),
+                                      _ptr(shift), _stream_handle(stream)),
+               "spiir_network_peak", lib)
+    return rho, t, shift
 
 
 def spiir_filter(x, a, b, plan):

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -1184,6 +1185,38 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
             return cuda_fail(e, "history copy");
     }
     p->t0 += n;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_network_peak(const float *z_dev, int32_t n_detectors, int64_t n_templates,
+                                int64_t n, const int32_t *window, float *rho_dev,
+                                int64_t *t_dev, int32_t *shift_dev, void *stream)
+{
+    if (!z_dev || !window || !rho_dev || !t_dev)
+        return fail(SPIIR_EINVAL, "z_dev, window, rho_dev and t_dev are required");
+    if (n_detectors < 1 || n_detectors > spiir::kNetMaxD)
+        return fail(SPIIR_EINVAL, "n_detectors must be in [1, " +
+                                      std::to_string(spiir::kNetMaxD) + "]");
+    if (n_templates < 0 || n_templates > INT32_MAX || n < 1 || n > ((int64_t)1 << 40))
+        return fail(SPIIR_EINVAL, "n_templates must be in [0, 2^31), n in [1, 2^40]");
+    spiir::NetArgs a{};
+    a.z = reinterpret_cast<const float2 *>(z_dev);
+    a.D = n_detectors;
+    a.T = n_templates;
+    a.n = n;
+    for (int d = 1; d < n_detectors; ++d) {
+        if (window[d] < 0 || window[d] > spiir::kNetMaxWindow)
+            return fail(SPIIR_EINVAL, "window[d] must be in [0, " +
+                                          std::to_string(spiir::kNetMaxWindow) + "]");
+        a.w[d] = window[d];
+    }
+    if (spiir::network_smem_words(a.w, a.D, a.off_p, a.off_g) * 4 > 200 * 1024)
+        return fail(SPIIR_EUNSUPPORTED, "detector windows too wide for shared memory");
+    a.rho = rho_dev;
+    a.t = t_dev;
+    a.shift = shift_dev;
+    cudaError_t e = spiir::launch_network_peak(a, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "network peak launch");
     return SPIIR_OK;
 }
 

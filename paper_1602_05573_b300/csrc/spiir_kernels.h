@@ -248,4 +248,22 @@ cudaError_t launch_decimate(const float *x, int64_t n, int D, int R, int64_t nb,
 // Self-test: wait on an mbarrier nothing will complete, with a bound; sets *err.
 cudaError_t launch_bounded_wait_probe(int32_t *err, uint64_t limit_ns, cudaStream_t s);
 
+// Network peak across detectors (spiir_network.cu): one CTA per template.
+constexpr int kNetMaxD = 8;       // detectors
+constexpr int kNetMaxWindow = 1024;
+struct NetArgs {
+    const float2 *z;              // [D][T][n]
+    int32_t D;
+    int64_t T, n;
+    int32_t w[kNetMaxD];          // offsets allowed per detector (w[0] = 0)
+    int32_t off_p[kNetMaxD];      // shared-memory word offsets (network_smem_words)
+    int32_t off_g[kNetMaxD];
+    float *rho;                   // [T]
+    int64_t *t;                   // [T]
+    int32_t *shift;               // [T][D] or null
+};
+// shared-memory words of a tile; fills the per-detector offsets
+int network_smem_words(const int32_t *w, int D, int32_t *off_p, int32_t *off_g);
+cudaError_t launch_network_peak(const NetArgs &a, cudaStream_t s);
+
 }  // namespace spiir
