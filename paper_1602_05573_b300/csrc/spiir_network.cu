@@ -124,8 +124,17 @@ __device__ __forceinline__ void net_add_window(const float *p, const float *g, i
 #pragma unroll
         for (int k = kNetR - 1; k >= 0; --k)
             m[k] = k == kNetR - 1 ? p[pidx(i0 + k)] : fmaxf(p[pidx(i0 + k)], m[k + 1]);
-        float run = p[pidx(i0 + kNetR - 1)];
-        for (int j = kNetR; j < 2 * w; ++j) run = fmaxf(run, p[pidx(i0 + j)]);
+        // the middle of the prefix in four independent chains (loads issue
+        // ahead of the maxima; max is exact, so the order does not matter)
+        float r4[4] = {p[pidx(i0 + kNetR - 1)], -INFINITY, -INFINITY, -INFINITY};
+        int j = kNetR;
+#pragma unroll 2
+        for (; j + 4 <= 2 * w; j += 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) r4[q] = fmaxf(r4[q], p[pidx(i0 + j + q)]);
+        }
+        for (; j < 2 * w; ++j) r4[0] = fmaxf(r4[0], p[pidx(i0 + j)]);
+        float run = fmaxf(fmaxf(r4[0], r4[1]), fmaxf(r4[2], r4[3]));
 #pragma unroll
         for (int k = 0; k < kNetR; ++k) {
             run = fmaxf(run, p[pidx(i0 + k + 2 * w)]);
@@ -165,7 +174,7 @@ __global__ void __launch_bounds__(kNetThreads) network_peak_kernel(const NetArgs
             const int M = tile + 2 * w;
             const float2 *row = A.z + ((int64_t)d * A.T + tau) * n;
             float *p = sm + A.off_p[d];
-#pragma unroll 4
+#pragma unroll 8
             for (int i = tid; i < M; i += kNetThreads) {
                 const int64_t pos = t0 - w + i;
                 p[pidx(i)] = (pos >= 0 && pos < n) ? mag2(row[pos]) : -INFINITY;
