@@ -147,6 +147,39 @@ def filter_multirate(off, a, b, d, band_of, decim, x, *, want_z=True, n_threads=
     return zc, pa, pi
 
 
+def band_input(x, taps):
+    """Front end of one band at the top rate, before its subsampling: the
+    causal FIR sum_i taps[i] x[k - i] (x[< 0] = 0; whitening and/or
+    anti-aliasing), float64.  x: [D][n]."""
+    x = np.atleast_2d(np.asarray(x, np.float64))
+    taps = np.asarray(taps, np.float64)
+    n = x.shape[1]
+    return np.stack([np.convolve(row, taps)[:n] for row in x])
+
+
+def filter_multirate_fir(off, a, b, d, band_of, decim, x, band_fir, *, n_threads=None):
+    """Multirate bank whose band j sees its front end's output subsampled,
+    sum_i band_fir[j][i] x[R_j k - i] (None: plain subsampling x[R_j k]).
+    Bands are independent until their interpolated sums add, so each band
+    runs through filter_multirate alone on its own top-rate input and the
+    band results are summed (float64).  Returns z complex128 [D][T][n]."""
+    off = np.asarray(off, np.int64)
+    band_of = np.asarray(band_of, np.int32)
+    x = np.atleast_2d(np.asarray(x, np.float64))
+    T = off.shape[0] - 1
+    z = 0.0
+    for j in range(len(decim)):
+        keep = band_of == j
+        counts = np.array([int(keep[off[t]:off[t + 1]].sum()) for t in range(T)], np.int64)
+        off_j = np.concatenate([[0], np.cumsum(counts)])
+        xj = x if band_fir[j] is None else band_input(x, band_fir[j])
+        zj, _, _ = filter_multirate(off_j, np.asarray(a)[keep], np.asarray(b)[keep],
+                                    np.asarray(d)[keep], band_of[keep], decim, xj,
+                                    n_threads=n_threads)
+        z = z + zj
+    return z
+
+
 def adjoint(off, a, b, d, x, gz, *, want_gx=True, n_threads=None):
     """Vector-Jacobian product of filter_bank: given g_z (PyTorch convention,
     dL/dRe z + i dL/dIm z, complex [D][T][n]) return (g_a, g_b, g_x):

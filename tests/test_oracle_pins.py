@@ -431,3 +431,44 @@ def test_network_mutations_are_caught(mutation):
         except AssertionError:
             failed += 1
     assert failed > 0, mutation
+
+
+# ------------------------------------------------- band front-end FIR ---
+# Band j's input becomes sum_i h_j[i] x[R_j k - i] instead of x[R_j k].
+
+def test_band_fir_identity_taps_are_plain_subsampling():
+    bank = make_multirate_bank(3, (3, 4, 2), (1, 4, 8), (0.95, 0.999), 20, seed=160, n_det=2)
+    x = make_strain(2, 640, seed=161)
+    z0, _, _ = oracle.filter_multirate(bank.off, bank.a, bank.b, bank.d, bank.band_of,
+                                       bank.decim, x)
+    z1 = oracle.filter_multirate_fir(bank.off, bank.a, bank.b, bank.d, bank.band_of,
+                                     bank.decim, x, [[1.0], None, [1.0]])
+    assert np.allclose(z1, z0, rtol=0, atol=1e-12 * np.abs(z0).max())
+
+
+def test_band_fir_single_tap_is_a_delay_and_scale():
+    """taps = c at lag m: band j sees c x[R k - m], i.e. the plain band of
+    the strain delayed by m and scaled by c (closed form, one band)."""
+    bank = make_multirate_bank(2, (0, 5, 0), (1, 4, 8), (0.95, 0.999), 10, seed=162)
+    x = make_strain(1, 400, seed=163).astype(np.float64)
+    m, c = 3, -2.5
+    taps = np.zeros(m + 1)
+    taps[m] = c
+    z1 = oracle.filter_multirate_fir(bank.off, bank.a, bank.b, bank.d, bank.band_of,
+                                     bank.decim, x, [None, taps, None])
+    xd = np.zeros_like(x)
+    xd[:, m:] = c * x[:, :-m]
+    z0, _, _ = oracle.filter_multirate(bank.off, bank.a, bank.b, bank.d, bank.band_of,
+                                       bank.decim, xd)
+    assert np.allclose(z1, z0, rtol=0, atol=1e-12 * np.abs(z0).max())
+
+
+def test_band_input_is_direct_convolution():
+    rng = np.random.default_rng(164)
+    x = rng.standard_normal((2, 50))
+    taps = rng.standard_normal(7)
+    got = oracle.band_input(x, taps)
+    for dd in range(2):
+        for k in range(50):
+            want = sum(taps[i] * x[dd, k - i] for i in range(7) if k - i >= 0)
+            assert abs(got[dd, k] - want) <= 1e-12
