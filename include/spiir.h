@@ -227,6 +227,24 @@ spiir_status spiir_peak(spiir_plan *plan, float *peak_abs_dev, int64_t *peak_idx
                         void *stream);
 
 /*
+ * Front end of one band (whitening and/or anti-aliasing before the band's
+ * subsampling): from the next spiir_filter call on, band `band` (an index
+ * into the bank's bands) sees
+ *   x_band[k] = sum_{i < n_taps} taps[i] x[R k - i]
+ * (x at the top rate counted from the stream start, x[< 0] = 0, R the
+ * band's decimation factor; R = 1 bands too) instead of x[R k].  The plan
+ * keeps the last 511 top-rate samples for this across calls; spiir_reset
+ * zeroes them.  FP32 products accumulated in tap order.
+ *   taps    [n_taps] float32, host, copied
+ *   n_taps  0 (plain subsampling again) .. 512
+ * Waits for the plan's device work to finish.  spiir_state_set refuses
+ * plans with front ends (EUNSUPPORTED): their history is not in the state.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+spiir_status spiir_set_band_fir(spiir_plan *plan, int32_t band, const float *taps,
+                                int32_t n_taps);
+
+/*
  * Network peak across detectors (coincidence of the SNR series).  A signal
  * reaches the detectors at times that differ by at most their light travel
  * time; the review's multi-messenger section localises a source from these

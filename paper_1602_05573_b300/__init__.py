@@ -42,7 +42,7 @@ SYMBOLS = [
     "spiir_peak", "spiir_filter_backward", "spiir_state_get", "spiir_state_set",
     "spiir_check", "spiir_selftest_bounded_wait", "spiir_status_str",
     "spiir_last_error_detail", "spiir_filter_noalloc", "spiir_set_coefficients",
-    "spiir_network_peak",
+    "spiir_network_peak", "spiir_set_band_fir",
 ]
 
 
@@ -104,6 +104,8 @@ def _configure(lib):
     lib.spiir_network_peak.argtypes = [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64, _P,
                                        _P, _P, _P, _P]
     lib.spiir_network_peak.restype = _st
+    lib.spiir_set_band_fir.argtypes = [_P, ctypes.c_int32, _P, ctypes.c_int32]
+    lib.spiir_set_band_fir.restype = _st
     lib.spiir_state_get.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int64)]
     lib.spiir_state_get.restype = _st
     lib.spiir_state_set.argtypes = [_P, _P, _P, ctypes.c_int64]
@@ -383,6 +385,14 @@ class Plan:
                                           _ptr(gx), _stream_handle(stream)),
                "spiir_filter_backward", self._lib)
         return ga, gb, gx
+
+    def set_band_fir(self, band: int, taps):
+        """Front end of band `band`: x_band[k] = sum_i taps[i] x[R k - i]
+        (whitening / anti-aliasing before subsampling); None or [] restores
+        plain subsampling."""
+        t = np.ascontiguousarray(np.zeros(0) if taps is None else taps, np.float32).ravel()
+        _check(self._lib.spiir_set_band_fir(self._h, int(band), t.ctypes.data if t.size else None,
+                                            int(t.size)), "spiir_set_band_fir", self._lib)
 
     def set_coefficients(self, a, b, *, stream=None):
         """Replace every filter's pole and gain: a, b CUDA complex64 [Ltot]."""

@@ -177,6 +177,8 @@ struct Band {
     int adj_seg_cap = 0;           // segments adj_E / adj_mu / acc hold
     float2 *adj_sub16 = nullptr;   // [n/16][D][n_slots] forward state at every span start
     int64_t adj_sub16_cap = 0;     //   float2 elements
+    float *fir = nullptr;          // front-end FIR taps of this band (device), or null
+    int fir_len = 0;
     int2 *adj_units7 = nullptr;    // input-gradient units: (first task, tasks) of one template
     int64_t adj_n_units7 = 0;
     int adj_W7 = 1;                // warps per input-gradient CTA (largest unit)
@@ -198,6 +200,11 @@ struct spiir_plan {
     int64_t t0 = 0;               // the same, as enqueued by this host (alignment checks)
     int top = 0;                  // index of the top-rate band
     int maxR = 1;                 // largest decimation factor
+    // band front-end FIRs: the last kFirMaxTaps - 1 top-rate samples, and a
+    // per-call staging buffer [D][kFirMaxTaps - 1 + n] of (history, x)
+    float *fir_xh = nullptr;
+    float *fir_xt = nullptr;
+    int64_t fir_xt_cap = 0;       // samples per detector row
     // kept for the autotuner (single-rate plans with autotune set)
     bool tuned = false;
     int n_sm = 148;
@@ -279,6 +286,7 @@ void free_band(Band &b)
     cudaFree(b.adj_mu);
     cudaFree(b.adj_sub16);
     cudaFree(b.adj_units7);
+    cudaFree(b.fir);
     cudaFree(b.adj_seeds);
     b = Band();
 }
@@ -630,6 +638,8 @@ spiir_status spiir_plan_destroy(spiir_plan *p)
         cudaFree(p->peak_idx);
         cudaFree(p->err);
         cudaFree(p->t0_dev);
+        cudaFree(p->fir_xh);
+        cudaFree(p->fir_xt);
         for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
     }
     delete p;
@@ -700,7 +710,10 @@ spiir_status spiir_reset(spiir_plan *p, void *stream)
     if ((e = spiir::launch_peak_reset(p->peak_best, p->peak_idx, (int64_t)p->D * p->T, s)) !=
             cudaSuccess ||
         (e = cudaMemsetAsync(p->err, 0, sizeof(int32_t), s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(p->t0_dev, 0, sizeof(int64_t), s)) != cudaSuccess)
+        (e = cudaMemsetAsync(p->t0_dev, 0, sizeof(int64_t), s)) != cudaSuccess ||
+        (p->fir_xh && (e = cudaMemsetAsync(p->fir_xh, 0,
+                                           sizeof(float) * (size_t)p->D * (spiir::kFirMaxTaps - 1),
+                                           s)) != cudaSuccess))
         return cuda_fail(e, "reset");
     p->t0 = 0;
     return SPIIR_OK;
@@ -1120,6 +1133,29 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
         if (j != p->top) order.push_back(j);
     order.push_back(p->top);
     spiir::K1Args top_args{};
+    // band front ends: stage (top-rate history, x) once for every FIR band
+    constexpr int H = spiir::kFirMaxTaps - 1;
+    bool any_fir = false;
+    for (const Band &b : p->bands) any_fir = any_fir || b.fir_len > 0;
+    if (any_fir) {
+        if (p->fir_xt_cap < H + n) {
+            if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+                return cuda_fail(e, "cudaStreamSynchronize");
+            cudaFree(p->fir_xt);
+            p->fir_xt = nullptr;
+            p->fir_xt_cap = 0;
+            if ((e = dalloc(&p->fir_xt, (size_t)D * (H + n))) != cudaSuccess)
+                return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "front-end staging")
+                                                      : cuda_fail(e, "cudaMalloc");
+            p->fir_xt_cap = H + n;
+        }
+        const int64_t st = p->fir_xt_cap;
+        if ((e = cudaMemcpy2DAsync(p->fir_xt, st * 4, p->fir_xh, H * 4, H * 4, D,
+                                   cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
+            (e = cudaMemcpy2DAsync(p->fir_xt + H, st * 4, x_dev, n * 4, n * 4, D,
+                                   cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+            return cuda_fail(e, "front-end staging");
+    }
     for (int j : order) {
         Band &b = p->bands[j];
         const int64_t nb = (n + b.R - 1) / b.R;   // band samples in this call
@@ -1130,7 +1166,11 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
         if ((e = cudaMemcpy2DAsync(b.xe, b.xe_stride * 4, b.hist, Dh * 4, Dh * 4, D,
                                    cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return cuda_fail(e, "strain staging copy");
-        if (b.R == 1) {
+        if (b.fir_len > 0) {
+            e = spiir::launch_fir_decimate(p->fir_xt, p->fir_xt_cap, H, D, b.R, nb, b.fir,
+                                           b.fir_len, b.xe, b.xe_stride, Dh, s);
+            p->last_launches += 1;
+        } else if (b.R == 1) {
             e = cudaMemcpy2DAsync(b.xe + Dh, b.xe_stride * 4, x_dev, n * 4, n * 4, D,
                                   cudaMemcpyDeviceToDevice, s);
         } else {
@@ -1184,7 +1224,44 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
                                    cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return cuda_fail(e, "history copy");
     }
+    // the last H top-rate samples of (history, x) for the next call's front ends
+    if (any_fir && (e = cudaMemcpy2DAsync(p->fir_xh, H * 4, p->fir_xt + n, p->fir_xt_cap * 4,
+                                          H * 4, D, cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+        return cuda_fail(e, "front-end history copy");
     p->t0 += n;
+    return SPIIR_OK;
+}
+
+spiir_status spiir_set_band_fir(spiir_plan *p, int32_t band, const float *taps, int32_t n_taps)
+{
+    if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
+    if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan has no front end");
+    if (band < 0 || band >= (int32_t)p->bands.size()) return fail(SPIIR_EINVAL, "no such band");
+    if (n_taps < 0 || n_taps > spiir::kFirMaxTaps || (n_taps > 0 && !taps))
+        return fail(SPIIR_EINVAL, "n_taps must be in [0, " +
+                                      std::to_string(spiir::kFirMaxTaps) + "] with taps given");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
+    cudaError_t e = cudaDeviceSynchronize();   // calls in flight may read the taps
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize");
+    Band &b = p->bands[band];
+    cudaFree(b.fir);
+    b.fir = nullptr;
+    b.fir_len = 0;
+    if (n_taps == 0) return SPIIR_OK;
+    if (!p->fir_xh) {
+        const size_t words = (size_t)p->D * (spiir::kFirMaxTaps - 1);
+        if ((e = dalloc(&p->fir_xh, words)) != cudaSuccess ||
+            (e = cudaMemset(p->fir_xh, 0, words * sizeof(float))) != cudaSuccess)
+            return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "front-end history")
+                                                  : cuda_fail(e, "cudaMalloc");
+    }
+    if ((e = dalloc(&b.fir, (size_t)n_taps)) != cudaSuccess ||
+        (e = cudaMemcpy(b.fir, taps, sizeof(float) * n_taps, cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "front-end taps")
+                                              : cuda_fail(e, "front-end taps upload");
+    b.fir_len = n_taps;
     return SPIIR_OK;
 }
 
@@ -1597,6 +1674,10 @@ spiir_status spiir_state_set(spiir_plan *p, const float *state, const float *his
     if (!p) return fail(SPIIR_EINVAL, "plan is NULL");
     if (p->device < 0) return fail(SPIIR_EINVAL, "host-only plan has no state");
     if (samples < 0) return fail(SPIIR_EINVAL, "samples must be >= 0");
+    for (const Band &b : p->bands)
+        if (b.fir_len > 0)
+            return fail(SPIIR_EUNSUPPORTED, "state import with band front-end FIRs (their "
+                                            "top-rate history is not part of the state)");
     DeviceGuard guard(p->device);
     if (!guard.ok) return cuda_fail(guard.err, "cudaSetDevice");
     cudaError_t e = cudaDeviceSynchronize();

@@ -1010,6 +1010,28 @@ __global__ void decimate_kernel(const float *x, int64_t n, int R, int64_t nb, fl
         xe[(int64_t)d * xe_stride + Dh + i] = x[(int64_t)d * n + (int64_t)R * i];
 }
 
+// Front end of a band: x_b[k] = sum_{i < L} h[i] x[R k - i] for this call's
+// band samples, from xt = [H samples of history | the call's x] per
+// detector (xr[j] = x[t0 + j] for j >= -H, L - 1 <= H).  FP32 accumulation
+// in tap order; the taps sit in shared memory.
+__global__ void fir_decimate_kernel(const float *xt, int64_t xt_stride, int H, int R, int64_t nb,
+                                    const float *taps, int L, float *xe, int64_t xe_stride,
+                                    int64_t Dh)
+{
+    extern __shared__ float th[];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) th[i] = taps[i];
+    __syncthreads();
+    const int d = blockIdx.y;
+    const float *xr = xt + (int64_t)d * xt_stride + H;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nb;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const float *c = xr + (int64_t)R * k;
+        float acc = 0.f;
+        for (int i = 0; i < L; ++i) acc = __fmaf_rn(th[i], c[-i], acc);
+        xe[(int64_t)d * xe_stride + Dh + k] = acc;
+    }
+}
+
 __global__ void bounded_wait_probe(int32_t *err, uint64_t limit_ns)
 {
     __shared__ __align__(8) uint64_t bar;
@@ -1135,6 +1157,18 @@ cudaError_t launch_peak_reset(float *best, int64_t *idx, int64_t count, cudaStre
 {
     if (count <= 0) return cudaSuccess;
     peak_reset_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(best, idx, count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fir_decimate(const float *xt, int64_t xt_stride, int H, int D, int R,
+                               int64_t nb, const float *taps, int L, float *xe,
+                               int64_t xe_stride, int64_t Dh, cudaStream_t s)
+{
+    if (nb <= 0 || D <= 0) return cudaSuccess;
+    if (L < 1 || L - 1 > H) return cudaErrorInvalidValue;
+    const int64_t blocks = std::min<int64_t>((nb + 255) / 256, 4096);
+    fir_decimate_kernel<<<dim3((unsigned)blocks, (unsigned)D), 256, L * sizeof(float), s>>>(
+        xt, xt_stride, H, R, nb, taps, L, xe, xe_stride, Dh);
     return cudaGetLastError();
 }
 

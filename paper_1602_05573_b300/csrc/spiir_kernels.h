@@ -242,6 +242,11 @@ cudaError_t launch_advance(int64_t *t0, int64_t n, cudaStream_t s);
 cudaError_t launch_peak_reset(float *best, int64_t *idx, int64_t count, cudaStream_t s);
 
 // xe[d][Dh + i] = x[d][R * i] for i < nb (decimation into a band's strain rows).
+// band front end: x_b[k] = sum_{i<L} taps[i] x[R k - i] from xt = [H history | x]
+constexpr int kFirMaxTaps = 512;
+cudaError_t launch_fir_decimate(const float *xt, int64_t xt_stride, int H, int D, int R,
+                               int64_t nb, const float *taps, int L, float *xe,
+                               int64_t xe_stride, int64_t Dh, cudaStream_t s);
 cudaError_t launch_decimate(const float *x, int64_t n, int D, int R, int64_t nb, float *xe,
                             int64_t xe_stride, int64_t Dh, cudaStream_t s);
 
