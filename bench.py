@@ -74,6 +74,9 @@ def parse():
                     help="override the stream length per step (profiling runs)")
     ap.add_argument("--templates", type=int, default=0,
                     help="keep only the bank's first N templates (profiling runs)")
+    ap.add_argument("--front-end", action="store_true",
+                    help="multirate: windowed-sinc anti-aliasing FIRs (8 R - 1 taps) on the "
+                         "decimated bands instead of plain subsampling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -286,6 +289,12 @@ def run_ours(args, rank, world, local_rank):
     # projection and adjoint launches, on the launching stream (not in graphs)
     plan = sp.Plan(bank, device=local_rank, precision=args.precision,
                    autotune=args.autotune, kernel_timing=True)
+    if args.front_end and bank.decim is not None:
+        for j, R in enumerate(bank.decim):
+            if R > 1:   # low-pass at the band's Nyquist rate, Hann-windowed sinc
+                k = np.arange(8 * R - 1) - (8 * R - 2) / 2
+                h = np.sinc(k / R) / R * np.hanning(8 * R + 1)[1:-1]
+                plan.set_band_fir(j, (h / h.sum()).astype(np.float32))
     stream = torch.cuda.Stream(device=dev)
     x = torch.from_numpy(x_host).to(dev)
     z = torch.empty((D, T, n), dtype=torch.complex64, device=dev) if emit_z else None
@@ -499,7 +508,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded N(0,1) strain, random poles/gains/delays)",
         "config": dict(describe(args.workload, bank, n),
                        precision=args.precision, graph=bool(graph is not None),
-                       z_stored=emit_z,
+                       z_stored=emit_z, front_end=bool(args.front_end),
                        parallelism=f"template shards x{world}" if world > 1 else "1 GPU",
                        l2=("each step writes the z series (> 126 MB L2), which evicts the "
                            "previous step; the strain stays L2-resident as in streaming use")
