@@ -262,3 +262,22 @@ def network_peak(z, window, *, mutation=None):
                     shift[k, d] = u
                     break
     return rho, t, shift
+
+
+def ls_gains(a, d, target):
+    """Least-squares gains of one template's filters (poles a, delays d) for
+    the impulse-response target t[0..N): argmin_b sum_k |sum_l b_l phi_l[k]
+    - t[k]|^2 with phi_l[k] = a_l^(k - d_l) for k >= d_l (the response of
+    filter l with unit gain to an impulse at k = 0), float64 lstsq on the
+    explicit N x L matrix.  Returns (b complex128 [L], response complex128 [N])."""
+    a = np.asarray(a, np.complex128)
+    d = np.asarray(d, np.int64)
+    t = np.asarray(target, np.complex128)
+    N = t.shape[0]
+    k = np.arange(N)
+    A = np.zeros((N, a.shape[0]), np.complex128)
+    for l in range(a.shape[0]):
+        m = k >= d[l]
+        A[m, l] = a[l] ** (k[m] - d[l])
+    b, *_ = np.linalg.lstsq(A, t, rcond=None)
+    return b, A @ b

@@ -117,6 +117,21 @@ def perturb(bank: Bank, seed: int, rel: float = 0.01) -> Bank:
                    bank.band_of, bank.decim)
 
 
+def chirp_template(rate: float, f_lo: float, f_hi: float, f0: float = 135.0) -> np.ndarray:
+    """Synthetic inspiral chirp from f_lo to f_hi Hz at `rate` samples/s,
+    complex128, time running forward: frequency f(tau) = f0 tau^(-3/8) at
+    tau seconds before coalescence (the leading-order chirp; f0 ~ 135 Hz for
+    a 1.2 solar-mass chirp mass), phase 2 pi times its integral, amplitude
+    growing as f^(2/3).  A stand-in waveform: no waveform library exists here."""
+    tau_lo = (f0 / f_lo) ** (8.0 / 3.0)
+    tau_hi = (f0 / f_hi) ** (8.0 / 3.0)
+    n = int(np.ceil((tau_lo - tau_hi) * rate))
+    tau = tau_lo - np.arange(n) / rate
+    phase = -2.0 * np.pi * f0 * (8.0 / 5.0) * tau ** (5.0 / 8.0)
+    amp = (tau / tau_lo) ** (-0.25)
+    return amp * np.exp(1j * phase)
+
+
 def make_strain(n_det: int, n: int, seed: int) -> np.ndarray:
     """White N(0, 1) float32 noise, [n_det][n] (whitened detector strain)."""
     rng = np.random.default_rng(seed)

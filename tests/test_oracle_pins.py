@@ -472,3 +472,44 @@ def test_band_input_is_direct_convolution():
         for k in range(50):
             want = sum(taps[i] * x[dd, k - i] for i in range(7) if k - i >= 0)
             assert abs(got[dd, k] - want) <= 1e-12
+
+
+# ------------------------------------------------- gain fit (bank design) ---
+
+def test_ls_gains_columns_are_filter_impulse_responses():
+    """The least-squares matrix's columns are the filters' unit-gain impulse
+    responses: the fitted response equals the oracle filter bank run on an
+    impulse with the fitted gains."""
+    rng = np.random.default_rng(180)
+    L, N = 9, 300
+    a = (rng.uniform(0.9, 0.99, L) * np.exp(1j * rng.uniform(0, np.pi, L))).astype(np.complex64)
+    d = rng.integers(0, 60, L).astype(np.int32)
+    t = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    b, resp = oracle.ls_gains(a, d, t)
+    x = np.zeros((1, N))
+    x[0, 0] = 1.0
+    z, _, _ = oracle.filter_bank(np.array([0, L]), a, b, d, x)
+    assert np.allclose(z[0, 0], resp, rtol=0, atol=1e-10 * np.abs(resp).max())
+
+
+def test_ls_gains_recovers_gains_in_the_span_and_leaves_an_orthogonal_residual():
+    """Least-squares facts, with the filters' responses from the oracle
+    filter bank on an impulse: a target the bank can produce gives back its
+    gains, and the residual of any target is orthogonal to every filter's
+    response (the normal equations)."""
+    rng = np.random.default_rng(181)
+    L, N = 12, 400
+    a = (rng.uniform(0.8, 0.98, L) * np.exp(1j * rng.uniform(0, np.pi, L))).astype(np.complex64)
+    d = rng.integers(0, 100, L).astype(np.int32)
+    x = np.zeros((1, N))
+    x[0, 0] = 1.0
+
+    def response(gains):
+        return oracle.filter_bank(np.array([0, L]), a, gains, d, x)[0][0, 0]
+    b0 = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    b, _ = oracle.ls_gains(a, d, response(b0))
+    assert np.allclose(b, b0, rtol=0, atol=1e-9 * np.abs(b0).max())
+    t = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    b, resp = oracle.ls_gains(a, d, t)
+    cols = np.stack([response(np.eye(L)[l]) for l in range(L)], axis=1)
+    assert np.abs(cols.conj().T @ (t - resp)).max() <= 1e-9 * np.linalg.norm(t) * np.linalg.norm(cols)
