@@ -51,60 +51,131 @@ def overlap(z, target) -> np.ndarray:
     return num / (np.linalg.norm(z, axis=-1) * np.linalg.norm(t, axis=-1))
 
 
+class BankFit:
+    """T templates of L filters (delays d [T][L] fixed) against impulse-
+    response targets [T][N], on one plan whose poles and gains change with
+    spiir_set_coefficients.  A(a, b): the bank's impulse response (one
+    spiir_filter on an impulse); adjoint(v): (g_a, g_b) of Re <v, z> by
+    spiir_filter_backward (g_b = A^H v)."""
+
+    def __init__(self, sp, a, d, targets, device: int = 0):
+        import types
+
+        import torch
+        self.torch = torch
+        a = np.asarray(a, np.complex64)
+        self.T, self.L = a.shape
+        self.N = int(np.asarray(targets).shape[-1])
+        self.dev = torch.device("cuda", device)
+        off = np.arange(self.T + 1, dtype=np.int64) * self.L
+        bank = types.SimpleNamespace(off=off, a=a.ravel(), b=np.ones(a.size, np.complex64),
+                                     d=np.asarray(d, np.int32).ravel(), n_det=1)
+        self.plan = sp.Plan(bank, device=device)
+        self.x = torch.zeros((1, self.N), dtype=torch.float32, device=self.dev)
+        self.x[0, 0] = 1.0
+        self.t = torch.from_numpy(np.asarray(targets, np.complex64)).to(self.dev).reshape(
+            1, self.T, self.N)
+        self.a = torch.from_numpy(a).to(self.dev)
+
+    def close(self):
+        self.plan.check()
+        self.plan.close()
+
+    def A(self, b, a=None):
+        a = self.a if a is None else a
+        self.plan.set_coefficients(a.reshape(-1), b.reshape(-1))
+        self.plan.reset()
+        return self.plan.filter(self.x)          # [1][T][N]
+
+    def adjoint(self, v):
+        ga, gb, _ = self.plan.backward(self.x, v, want_gx=False)
+        return ga.reshape(self.T, self.L), gb.reshape(self.T, self.L)
+
+    def loss(self, z):                           # per template sum |z - t|^2, [T]
+        return self.torch.sum(self.torch.abs(z - self.t) ** 2, dim=-1)[0]
+
+    def fit_gains(self, b, iters: int = 400, tol: float = 1e-7):
+        """Conjugate gradients on A^H A b = A^H t from b (per template)."""
+        torch = self.torch
+
+        def dot(u, v):
+            return torch.sum((torch.conj(u) * v).real, dim=-1, keepdim=True)
+        AH = lambda v: self.adjoint(v)[1]          # noqa: E731
+        r = AH(self.t - self.A(b))
+        p = r.clone()
+        rs = dot(r, r)
+        rs0 = torch.clamp(rs.clone(), min=1e-30)
+        it = 0
+        for it in range(1, iters + 1):
+            Mp = AH(self.A(p))
+            alpha = rs / torch.clamp(dot(p, Mp), min=1e-30)
+            b = b + alpha * p
+            r = r - alpha * Mp
+            rs_new = dot(r, r)
+            if bool(torch.all(rs_new <= (tol * tol) * rs0)):
+                break
+            p = r + (rs_new / torch.clamp(rs, min=1e-30)) * p
+            rs = rs_new
+        return b, it
+
+
 def fit_gains(sp, a, d, targets, *, b0=None, iters: int = 400, tol: float = 1e-7,
               device: int = 0):
     """Least-squares gains for T templates of L filters each (a, d: [T][L]
     poles and delays; targets: [T][N] complex).  Returns (b complex64 [T][L],
     the bank's impulse response [T][N] complex64, CG iterations run).  sp is
     the paper_1602_05573_b300 module."""
-    import types
-
     import torch
+    f = BankFit(sp, a, d, targets, device)
+    T, L = f.T, f.L
+    b = torch.from_numpy(np.ones((T, L), np.complex64) if b0 is None
+                         else np.asarray(b0, np.complex64)).to(f.dev)
+    b, it = f.fit_gains(b, iters, tol)
+    z = f.A(b)
+    out = b.cpu().numpy(), z[0].cpu().numpy(), it
+    f.close()
+    return out
 
-    a = np.asarray(a, np.complex64)
-    d = np.asarray(d, np.int32)
-    T, L = a.shape
-    N = int(np.asarray(targets).shape[-1])
-    dev = torch.device("cuda", device)
-    off = np.arange(T + 1, dtype=np.int64) * L
-    b_init = np.ones((T, L), np.complex64) if b0 is None else np.asarray(b0, np.complex64)
-    bank = types.SimpleNamespace(off=off, a=a.ravel(), b=b_init.ravel(), d=d.ravel(), n_det=1)
-    plan = sp.Plan(bank, device=device)
-    x = torch.zeros((1, N), dtype=torch.float32, device=dev)
-    x[0, 0] = 1.0
-    at = torch.from_numpy(a.ravel()).to(dev)
-    tg = torch.from_numpy(np.asarray(targets, np.complex64)).to(dev).reshape(1, T, N)
 
-    def A(p):                        # bank impulse response with gains p
-        plan.set_coefficients(at, p.reshape(-1))
-        plan.reset()
-        return plan.filter(x)        # [1][T][N]
-
-    def AH(v):                       # A^H v through the adjoint
-        _, gb, _ = plan.backward(x, v, want_gx=False)
-        return gb.reshape(T, L)
-
-    def dot(u, v):                   # per template Re <u, v>
-        return torch.sum((torch.conj(u) * v).real, dim=-1, keepdim=True)
-
-    b = torch.from_numpy(b_init).to(dev)
-    r = AH(tg - A(b))
-    p = r.clone()
-    rs = dot(r, r)
-    rs0 = rs.clone()
-    it = 0
-    for it in range(1, iters + 1):
-        Mp = AH(A(p))
-        alpha = rs / torch.clamp(dot(p, Mp), min=1e-30)
-        b = b + alpha * p
-        r = r - alpha * Mp
-        rs_new = dot(r, r)
-        if bool(torch.all(rs_new <= (tol * tol) * rs0)):
-            rs = rs_new
-            break
-        p = r + (rs_new / torch.clamp(rs, min=1e-30)) * p
-        rs = rs_new
-    z = A(b)
-    plan.check()
-    plan.close()
-    return b.cpu().numpy(), z[0].cpu().numpy(), it
+def fit_bank(sp, a, d, targets, *, b0=None, outer: int = 25, cg_iters: int = 200,
+             step: float = 1e-3, device: int = 0):
+    """Poles and gains by variable projection: for fixed poles the gains are
+    the least-squares ones (fit_gains), and the loss as a function of the
+    poles alone has the gradient g_a that the adjoint returns for
+    g_z = 2 (z - t) at those gains.  Each outer step moves every template's
+    poles along -g_a (largest move `step`, |a| kept <= 1 - 1e-5), halving the
+    step for templates whose loss did not drop (gains held), then refits the
+    gains.  Returns (a complex64 [T][L], b complex64 [T][L], response
+    [T][N] complex64, overlap per outer step [outer + 1][T])."""
+    import torch
+    f = BankFit(sp, a, d, targets, device)
+    T, L = f.T, f.L
+    b = torch.from_numpy(np.ones((T, L), np.complex64) if b0 is None
+                         else np.asarray(b0, np.complex64)).to(f.dev)
+    b, _ = f.fit_gains(b, cg_iters)
+    z = f.A(b)
+    history = [overlap(z[0].cpu().numpy(), f.t[0].cpu().numpy())]
+    eta = torch.full((T, 1), step, device=f.dev)
+    for _ in range(outer):
+        loss = f.loss(z)
+        ga, _ = f.adjoint(2.0 * (z - f.t))
+        gmax = torch.clamp(torch.abs(ga).amax(dim=-1, keepdim=True), min=1e-30)
+        a0 = f.a
+        done = torch.zeros((T, 1), dtype=torch.bool, device=f.dev)
+        for _try in range(8):
+            an = a0 - (eta / gmax) * ga
+            mag = torch.abs(an)
+            an = torch.where(mag > 1.0 - 1e-5, an / mag * (1.0 - 1e-5), an)
+            better = (f.loss(f.A(b, an)) < loss).reshape(T, 1) & ~done
+            f.a = torch.where(better, an, f.a)
+            done = done | better
+            if bool(torch.all(done)):
+                break
+            eta = torch.where(done, eta, eta * 0.5)
+        eta = torch.where(done, eta * 1.5, eta)   # accepted: try a longer step next
+        b, _ = f.fit_gains(b, cg_iters)
+        z = f.A(b)
+        history.append(overlap(z[0].cpu().numpy(), f.t[0].cpu().numpy()))
+    out = (f.a.cpu().numpy(), b.cpu().numpy(), z[0].cpu().numpy(), np.stack(history))
+    f.close()
+    return out
