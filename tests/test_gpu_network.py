@@ -38,6 +38,9 @@ def assert_same(got, want):
     (1, 9, 777, [0]),                # single detector: the plain peak
     (4, 6, 300, [0, 0, 600, 1024]),  # windows wider than the series
     (8, 3, 1500, [0, 1, 2, 3, 5, 8, 13, 21]),
+    (3, 4, 1, [0, 3, 9]),            # one sample
+    (3, 4, 7, [0, 2, 700]),          # shorter than a thread's run of 8 outputs
+    (2, 3, 4100, [0, 300]),          # window past the scan limit: doubling levels
 ])
 def test_network_peak_matches_oracle(sp, D, T, n, window):
     rng = np.random.default_rng(D * 1000 + n)
