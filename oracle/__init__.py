@@ -281,3 +281,43 @@ def ls_gains(a, d, target):
         A[m, l] = a[l] ** (k[m] - d[l])
     b, *_ = np.linalg.lstsq(A, t, rcond=None)
     return b, A @ b
+
+
+def chi2_groups(off, a, b, p):
+    """Allen's chi^2 bins for every template, read for a bank of single-pole
+    filters: a template's filters sorted by frequency arg(a_l) and cut into p
+    contiguous groups of (as nearly as whole filters allow) equal energy,
+    filter l's energy being that of its impulse response, |b_l|^2 / (1 -
+    |a_l|^2).  Filter l goes to the group holding the midpoint of its share
+    of the cumulative energy.  Returns int32 [Ltot] group indices in 0..p-1."""
+    off = np.asarray(off, np.int64)
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    g = np.zeros(a.shape[0], np.int32)
+    for t in range(off.shape[0] - 1):
+        idx = np.arange(off[t], off[t + 1])
+        if idx.size == 0:
+            continue
+        order = idx[np.argsort(np.angle(a[idx]), kind="stable")]
+        e = np.abs(b[order]) ** 2 / (1.0 - np.abs(a[order]) ** 2)
+        mid = (np.cumsum(e) - 0.5 * e) / np.sum(e)
+        g[order] = np.minimum((mid * p).astype(np.int32), p - 1)
+    return g
+
+
+def chi2_at_peak(z_groups, p):
+    """z_groups: complex [D][T][p][n] partial SNR series of each template's p
+    groups.  z = sum_i z_i; per (detector, template) the first t maximising
+    |z(t)|^2 and chi^2 = p sum_i |z_i(t) - z(t) / p|^2 there (raw z units;
+    for unit white noise its mean is (p - 1) times a group's noise power).
+    Returns (peak |z| float64 [D][T], t int64 [D][T], chi2 float64 [D][T])."""
+    zg = np.asarray(z_groups, np.complex128)
+    z = zg.sum(axis=2)
+    m2 = np.abs(z) ** 2
+    t = np.argmax(m2, axis=-1)
+    D, T = t.shape
+    dd, tt = np.meshgrid(np.arange(D), np.arange(T), indexing="ij")
+    zt = z[dd, tt, t]
+    zi = zg[dd, tt, :, t]                       # [D][T][p]
+    chi2 = p * np.sum(np.abs(zi - zt[..., None] / p) ** 2, axis=-1)
+    return np.abs(zt), t.astype(np.int64), chi2

@@ -513,3 +513,51 @@ def test_ls_gains_recovers_gains_in_the_span_and_leaves_an_orthogonal_residual()
     b, resp = oracle.ls_gains(a, d, t)
     cols = np.stack([response(np.eye(L)[l]) for l in range(L)], axis=1)
     assert np.abs(cols.conj().T @ (t - resp)).max() <= 1e-9 * np.linalg.norm(t) * np.linalg.norm(cols)
+
+
+# ------------------------------------------------- chi^2 veto ---
+# Allen's discriminator with the bins read as frequency groups of a
+# template's filters: chi^2 = p sum_i |z_i - z / p|^2 at the peak.
+
+def test_chi2_groups_are_contiguous_in_frequency_and_balanced():
+    bank = make_bank(5, (40, 120), (0.95, 0.999), 100, seed=190)
+    p = 4
+    g = oracle.chi2_groups(bank.off, bank.a, bank.b, p)
+    for t in range(5):
+        idx = np.arange(bank.off[t], bank.off[t + 1])
+        order = idx[np.argsort(np.angle(bank.a[idx].astype(np.complex128)), kind="stable")]
+        assert np.all(np.diff(g[order]) >= 0)            # contiguous in frequency
+        e = np.abs(bank.b[idx].astype(np.complex128)) ** 2 / (
+            1 - np.abs(bank.a[idx].astype(np.complex128)) ** 2)
+        share = np.array([e[g[idx] == i].sum() for i in range(p)]) / e.sum()
+        assert np.all(np.abs(share - 1 / p) <= e.max() / e.sum())   # within one filter
+
+
+def test_chi2_vanishes_when_the_groups_agree_and_matches_a_hand_case():
+    z = np.zeros((1, 1, 3, 10), np.complex128)
+    z[0, 0, :, 4] = [2 + 1j, 2 + 1j, 2 + 1j]             # equal groups: chi^2 = 0
+    _, t, chi2 = oracle.chi2_at_peak(z, 3)
+    assert t[0, 0] == 4 and chi2[0, 0] == 0.0
+    z[0, 0, :, 4] = [3, 0, 0]                            # one group carries it all
+    pk, t, chi2 = oracle.chi2_at_peak(z, 3)
+    # z = 3, z/p = 1: 3 * ((3-1)^2 + 1 + 1) = 18
+    assert t[0, 0] == 4 and pk[0, 0] == 3.0 and abs(chi2[0, 0] - 18.0) < 1e-12
+
+
+def test_chi2_groups_sum_to_the_template():
+    """Filtering each group as its own template and adding the groups gives
+    the template's z (the bank is linear in its filters)."""
+    bank = make_bank(3, (20, 60), (0.95, 0.999), 50, seed=191)
+    x = make_strain(1, 500, seed=192)
+    p = 3
+    g = oracle.chi2_groups(bank.off, bank.a, bank.b, p)
+    z, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
+    for t in range(3):
+        total = 0
+        for i in range(p):
+            sel = np.arange(bank.off[t], bank.off[t + 1])
+            sel = sel[g[sel] == i]
+            zi, _, _ = oracle.filter_bank(np.array([0, sel.size]), bank.a[sel], bank.b[sel],
+                                          bank.d[sel], x)
+            total = total + zi[0, 0]
+        assert np.allclose(total, z[0, t], rtol=0, atol=1e-12 * np.abs(z[0, t]).max())
