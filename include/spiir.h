@@ -245,6 +245,28 @@ spiir_status spiir_set_band_fir(spiir_plan *plan, int32_t band, const float *tap
                                 int32_t n_taps);
 
 /*
+ * Chi^2 signal-based veto at each template's peak (Allen's discriminator,
+ * the review's chi^2 section).  Its p bins are groups of a template's
+ * filters (contiguous in frequency, equal impulse-response energy; the
+ * Python binding's chi2_split builds the regrouped bank), filtered as
+ * templates of their own, so spiir_filter on the regrouped bank writes the
+ * group series z_i in the layout read here.  Per (detector, template):
+ * z = sum_i z_i (float32, group order), t = the first index maximising
+ * |z|^2 (re*re + im*im, separately rounded products), peak = sqrt(|z(t)|^2)
+ * (correctly rounded) and chi2 = p sum_i |z_i(t) - z(t) / p|^2 (raw z
+ * units; for unit white noise its mean is (p - 1) times a bin's noise
+ * power).
+ *   zg_dev    [n_detectors][n_templates][n_bins][n] complex64, device
+ *   peak_dev, chi2_dev  [n_detectors][n_templates] float32, device
+ *   t_dev     [n_detectors][n_templates] int64, device
+ * No plan; current device; asynchronous on `stream`.  1 <= n_bins <= 64,
+ * n >= 1.  Errors: EINVAL, ECUDA.
+ */
+spiir_status spiir_chi2_peak(const float *zg_dev, int32_t n_detectors, int64_t n_templates,
+                             int32_t n_bins, int64_t n, float *peak_dev, int64_t *t_dev,
+                             float *chi2_dev, void *stream);
+
+/*
  * Network peak across detectors (coincidence of the SNR series).  A signal
  * reaches the detectors at times that differ by at most their light travel
  * time; the review's multi-messenger section localises a source from these

@@ -42,7 +42,7 @@ SYMBOLS = [
     "spiir_peak", "spiir_filter_backward", "spiir_state_get", "spiir_state_set",
     "spiir_check", "spiir_selftest_bounded_wait", "spiir_status_str",
     "spiir_last_error_detail", "spiir_filter_noalloc", "spiir_set_coefficients",
-    "spiir_network_peak", "spiir_set_band_fir",
+    "spiir_network_peak", "spiir_set_band_fir", "spiir_chi2_peak",
 ]
 
 
@@ -106,6 +106,9 @@ def _configure(lib):
     lib.spiir_network_peak.restype = _st
     lib.spiir_set_band_fir.argtypes = [_P, ctypes.c_int32, _P, ctypes.c_int32]
     lib.spiir_set_band_fir.restype = _st
+    lib.spiir_chi2_peak.argtypes = [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
+                                    ctypes.c_int64, _P, _P, _P, _P]
+    lib.spiir_chi2_peak.restype = _st
     lib.spiir_state_get.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int64)]
     lib.spiir_state_get.restype = _st
     lib.spiir_state_set.argtypes = [_P, _P, _P, ctypes.c_int64]
@@ -479,6 +482,59 @@ def network_peak(z, window, *, want_shift: bool = True, stream=None, lib=None):
                                       _ptr(shift), _stream_handle(stream)),
                "spiir_network_peak", lib)
     return rho, t, shift
+
+
+def chi2_split(bank, n_bins: int):
+    """The bank regrouped for the chi^2 veto: every template's filters,
+    sorted by frequency arg(a), cut into n_bins contiguous groups of (as
+    nearly as whole filters allow) equal impulse-response energy
+    |b|^2 / (1 - |a|^2) (a filter joins the group holding the midpoint of
+    its share of the cumulative energy); group i of template t becomes
+    template t * n_bins + i (empty groups stay empty).  Returns a bank
+    object (off, a, b, d, n_det) for Plan; spiir_filter on it writes the
+    group series [D][T][n_bins][n] that chi2_peak reads."""
+    import types
+    off = np.asarray(bank.off, np.int64)
+    a = np.asarray(bank.a, np.complex64)
+    b = np.asarray(bank.b, np.complex64)
+    d = np.asarray(bank.d, np.int32)
+    T = off.shape[0] - 1
+    order, counts = [], []
+    for t in range(T):
+        idx = np.arange(off[t], off[t + 1])
+        a64 = a[idx].astype(np.complex128)
+        srt = np.argsort(np.angle(a64), kind="stable")
+        e = np.abs(b[idx][srt].astype(np.complex128)) ** 2 / (1.0 - np.abs(a64[srt]) ** 2)
+        cum = np.cumsum(e)
+        grp = np.minimum(((cum - 0.5 * e) / cum[-1] * n_bins).astype(np.int64), n_bins - 1) \
+            if idx.size else np.zeros(0, np.int64)
+        for i in range(n_bins):
+            sel = idx[srt][grp == i]
+            order.append(sel)
+            counts.append(sel.size)
+    sel = np.concatenate(order) if order else np.zeros(0, np.int64)
+    new_off = np.zeros(len(counts) + 1, np.int64)
+    new_off[1:] = np.cumsum(counts)
+    return types.SimpleNamespace(off=new_off, a=a[sel], b=b[sel], d=d[sel],
+                                 n_det=int(bank.n_det))
+
+
+def chi2_peak(zg, n_bins: int, *, stream=None, lib=None):
+    """spiir_chi2_peak: zg CUDA complex64 [D][T * n_bins][n] (or [D][T][n_bins][n]).
+    Returns (peak float32 [D][T], t int64 [D][T], chi2 float32 [D][T])."""
+    import torch
+    lib = lib or library()
+    assert zg.is_cuda and zg.dtype == torch.complex64
+    zg = zg.contiguous()
+    D, n = zg.shape[0], zg.shape[-1]
+    T = zg.numel() // (D * n * n_bins)
+    peak = torch.empty((D, T), dtype=torch.float32, device=zg.device)
+    t = torch.empty((D, T), dtype=torch.int64, device=zg.device)
+    chi2 = torch.empty((D, T), dtype=torch.float32, device=zg.device)
+    with torch.cuda.device(zg.device):
+        _check(lib.spiir_chi2_peak(_ptr(zg), D, T, int(n_bins), n, _ptr(peak), _ptr(t),
+                                   _ptr(chi2), _stream_handle(stream)), "spiir_chi2_peak", lib)
+    return peak, t, chi2
 
 
 def spiir_filter(x, a, b, plan):

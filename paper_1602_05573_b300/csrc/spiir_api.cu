@@ -1265,6 +1265,22 @@ spiir_status spiir_set_band_fir(spiir_plan *p, int32_t band, const float *taps, 
     return SPIIR_OK;
 }
 
+spiir_status spiir_chi2_peak(const float *zg_dev, int32_t n_detectors, int64_t n_templates,
+                             int32_t n_bins, int64_t n, float *peak_dev, int64_t *t_dev,
+                             float *chi2_dev, void *stream)
+{
+    if (!zg_dev || !peak_dev || !t_dev || !chi2_dev)
+        return fail(SPIIR_EINVAL, "zg_dev, peak_dev, t_dev and chi2_dev are required");
+    if (n_detectors < 1 || n_templates < 0 || n_bins < 1 || n_bins > 64 || n < 1 ||
+        (int64_t)n_detectors * n_templates > INT32_MAX)
+        return fail(SPIIR_EINVAL, "n_detectors >= 1, 0 <= n_templates, 1 <= n_bins <= 64, n >= 1");
+    cudaError_t e = spiir::launch_chi2_peak(reinterpret_cast<const float2 *>(zg_dev), n_detectors,
+                                            n_templates, n_bins, n, peak_dev, t_dev, chi2_dev,
+                                            (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "chi^2 launch");
+    return SPIIR_OK;
+}
+
 spiir_status spiir_network_peak(const float *z_dev, int32_t n_detectors, int64_t n_templates,
                                 int64_t n, const int32_t *window, float *rho_dev,
                                 int64_t *t_dev, int32_t *shift_dev, void *stream)

@@ -271,4 +271,8 @@ struct NetArgs {
 int network_smem_words(const int32_t *w, int D, int32_t *off_p, int32_t *off_g);
 cudaError_t launch_network_peak(const NetArgs &a, cudaStream_t s);
 
+// Chi^2 at each template's peak from its p group series (spiir_veto.cu)
+cudaError_t launch_chi2_peak(const float2 *zg, int D, int64_t T, int p, int64_t n, float *peak,
+                             int64_t *t, float *chi2, cudaStream_t s);
+
 }  // namespace spiir
