@@ -640,7 +640,7 @@ def run_veto(args):
 
     import paper_1602_05573_b300 as sp
     p = 4
-    bank = workload_bank("batched")
+    bank = workload_bank("batched", n_templates=args.templates or None)
     x = torch.from_numpy(workload_strain("batched")).cuda()
     D, n = x.shape
     T = bank.n_templates
