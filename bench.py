@@ -645,10 +645,7 @@ def run_veto(args):
     D, n = x.shape
     T = bank.n_templates
     split = sp.chi2_split(bank, p)
-    # bins hold a quarter of a template's filters: half warps (16 lanes per
-    # bin template, more filters per lane) whenever every bin fits 16 x 10
-    small = int(np.diff(split.off).max()) <= 160
-    plan = sp.Plan(split, lanes_per_template=16 if small else 0)
+    plan = sp.Plan(split)   # bins of <= 160 filters: the plan picks half warps
     zg = torch.empty((D, T * p, n), dtype=torch.complex64, device="cuda")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -681,7 +678,7 @@ def run_veto(args):
         "config": dict(describe("batched", bank, n), bins=p,
                        l2="every step writes the bins' series (25.8 GB > 126 MB L2)"),
         "veto": {"filter_ms": f_ms, "chi2_ms": c_ms, "bins": p,
-                 "lanes_per_template": 16 if small else 32},
+                 "lanes_per_template": plan.info()["lanes_per_template"]},
         "roofline": {"bound": "hbm", "kernel": "chi2_peak_kernel", "achieved": gbs, "peak": hbm,
                      "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
                      "note": f"algorithmic bytes = the bins' series read once "

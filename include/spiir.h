@@ -107,9 +107,9 @@ typedef struct spiir_options {
                             /* more than 32x this many filters span several warps; */
                             /* 0 = default (10)                                    */
     int32_t lanes_per_template; /* 32, or 16 (two templates per warp, for small     */
-                            /* templates); 0 = 16 when every template has <= 64    */
-                            /* filters and the bank still fills >= 16 warps per SM */
-                            /* at 16 lanes, else 32                                */
+                            /* templates); 0 = 16 when every template has at most  */
+                            /* 16 x max_filters_per_lane filters and the bank      */
+                            /* still fills >= 16 warps per SM at 16 lanes, else 32 */
     int32_t time_segments;  /* plain precision: split each call into this many time */
                             /* segments run in parallel, each from its start state */
                             /* given by the projection below (segments are >= 1    */
