@@ -645,7 +645,10 @@ def run_veto(args):
     D, n = x.shape
     T = bank.n_templates
     split = sp.chi2_split(bank, p)
-    plan = sp.Plan(split)   # bins of <= 160 filters: the plan picks half warps
+    # bins hold about a quarter of a template's filters (energy-balanced, so
+    # some exceed 96): half warps measured faster for this bank as a whole
+    small = int(np.diff(split.off).max()) <= 160
+    plan = sp.Plan(split, lanes_per_template=16 if small else 0)
     zg = torch.empty((D, T * p, n), dtype=torch.complex64, device="cuda")
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):

@@ -108,8 +108,8 @@ typedef struct spiir_options {
                             /* 0 = default (10)                                    */
     int32_t lanes_per_template; /* 32, or 16 (two templates per warp, for small     */
                             /* templates); 0 = 16 when every template has at most  */
-                            /* 16 x max_filters_per_lane filters and the bank      */
-                            /* still fills >= 16 warps per SM at 16 lanes, else 32 */
+                            /* 96 filters (and 16 x max_filters_per_lane) and the  */
+                            /* bank still fills >= 16 warps per SM at 16 lanes     */
     int32_t time_segments;  /* plain precision: split each call into this many time */
                             /* segments run in parallel, each from its start state */
                             /* given by the projection below (segments are >= 1    */

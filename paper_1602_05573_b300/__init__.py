@@ -492,8 +492,10 @@ def chi2_split(bank, n_bins: int):
     its share of the cumulative energy); group i of template t becomes
     template t * n_bins + i (empty groups stay empty).  Returns a bank
     object (off, a, b, d, n_det) for Plan; spiir_filter on it writes the
-    group series [D][T][n_bins][n] that chi2_peak reads (bins of up to 160
-    filters in a large bank run in half warps, the plan's default)."""
+    group series [D][T][n_bins][n] that chi2_peak reads.  Bins of a large
+    bank run faster in half warps (Plan(..., lanes_per_template=16)) when
+    every bin fits 160 filters: more filters per lane for the same
+    cross-lane sums."""
     import types
     off = np.asarray(bank.off, np.int64)
     a = np.asarray(bank.a, np.complex64)

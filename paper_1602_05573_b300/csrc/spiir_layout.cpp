@@ -238,9 +238,11 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
     for (int64_t t = 0; t < L.T; ++t) maxL = std::max<int64_t>(maxL, (int64_t)filters[t].size());
     // (only when the bank is large enough that halving the warp count still
     // leaves >= 16 warps per SM; small banks are latency-bound and need warps).
-    // Templates of up to 16 x Fcap filters qualify: 16 lanes hold them in
-    // more filters per lane (less padding, fewer cross-lane sums per filter)
-    const bool small = (maxL + 15) / 16 <= L.Fcap;
+    // Templates of up to 3 rounds of 32 qualify: at 32 lanes they hold at
+    // most 3 filters per lane, and 16 lanes halve the cross-lane sums per
+    // filter (measured: 25-75 filters 13% faster at 16 lanes, 100-160
+    // filters 4% slower)
+    const bool small = (maxL + 31) / 32 <= 3 && (maxL + 15) / 16 <= L.Fcap;
     const bool many = (L.T * D + 1) / 2 >= 16 * (int64_t)opt.n_sm;
     L.G = opt.G != 0 ? opt.G : (small && many ? 16 : 32);
     if (L.G != 16 && L.G != 32) {

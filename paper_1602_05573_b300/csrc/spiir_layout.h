@@ -36,8 +36,8 @@ struct LayoutOptions {
     int W = 0;          // warps per CTA; 0 = from the bank size
     int Fcap = 0;       // filters per lane cap (1..kMaxF); 0 = default (kMaxF)
     int G = 0;          // lanes per template: 32, or 16 (two templates per warp);
-                        // 0 = 16 when every template fits 16 x Fcap filters and the
-                        // bank still fills >= 16 warps per SM at 16 lanes
+                        // 0 = 16 when every template fits 3 rounds of 32 (and 16 x
+                        // Fcap) and the bank still fills >= 16 warps per SM at 16
     int Tb = 512;       // samples per staged strain block (multiple of 32)
     int C = 0;          // ring copies (1, 2, 4); 0 = default (1)
     int n_sm = 148;     // used to pick W when W == 0

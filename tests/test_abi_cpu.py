@@ -180,17 +180,17 @@ def test_multirate_plan_layout_and_validation():
 
 
 def test_half_warp_mode_for_small_templates():
-    """In a large bank, templates of <= 16 x (filters-per-lane cap) filters
-    pair up in a warp (16 lanes each), so each lane holds twice the filters;
-    larger ones keep 32 lanes."""
+    """In a large bank, templates of <= 96 filters (3 rounds of 32) pair up
+    in a warp (16 lanes each), so each lane holds twice the filters; larger
+    ones keep 32 lanes."""
     many = make_bank(4800, (20, 64), (0.9, 0.99), 100, seed=5)
     assert sp.Plan(many, device=-1).info()["lanes_per_template"] == 16
     # few templates: keep one per warp (latency-bound, needs warps)
     few = make_bank(10, (20, 64), (0.9, 0.99), 100, seed=5)
     assert sp.Plan(few, device=-1).info()["lanes_per_template"] == 32
     assert sp.Plan(few, device=-1, lanes_per_template=16).info()["lanes_per_template"] == 16
-    edge = make_bank(4800, (20, 160), (0.9, 0.99), 100, seed=5)   # 160 = 16 lanes x cap 10
+    edge = make_bank(4800, (20, 96), (0.9, 0.99), 100, seed=5)
     assert sp.Plan(edge, device=-1).info()["lanes_per_template"] == 16
-    assert sp.Plan(edge, device=-1, max_filters_per_lane=8).info()["lanes_per_template"] == 32
-    big = make_bank(4800, (20, 161), (0.9, 0.99), 100, seed=5)
+    assert sp.Plan(edge, device=-1, max_filters_per_lane=5).info()["lanes_per_template"] == 32
+    big = make_bank(4800, (20, 97), (0.9, 0.99), 100, seed=5)
     assert sp.Plan(big, device=-1).info()["lanes_per_template"] == 32
