@@ -228,8 +228,9 @@ spiir_status spiir_peak(spiir_plan *plan, float *peak_abs_dev, int64_t *peak_idx
 
 /*
  * Front end of one band (whitening and/or anti-aliasing before the band's
- * subsampling): from the next spiir_filter call on, band `band` (an index
- * into the bank's bands) sees
+ * subsampling; section "SPIIR method" filters noisy detection data, which a
+ * pipeline whitens first and brings to each band's rate): from the next
+ * spiir_filter call on, band `band` (an index into the bank's bands) sees
  *   x_band[k] = sum_{i < n_taps} taps[i] x[R k - i]
  * (x at the top rate counted from the stream start, x[< 0] = 0, R the
  * band's decimation factor; R = 1 bands too) instead of x[R k].  The plan
