@@ -9,26 +9,25 @@
 //     g_a_l  = sum_k mu_l[k] conj(y_l[k-1]),
 //     g_b_l  = sum_k mu_l[k] x[k-d_l],
 //     g_x[m] = sum_l Re(conj(mu_l[m+d_l]) b_l).
-// The reverse pass needs y_l[k-1] at every k.  Recomputing y backwards
-// through 1/a_l is unstable, so the forward kernel stores the state every Cc
-// samples and this kernel, for each chunk in reverse order, recomputes the
-// chunk forward from its checkpoint (pass A, keeping the state every
-// kAdjSub samples in shared memory) and then, for each kAdjSub-sample span in
-// reverse, recomputes the span into registers (pass B) and runs the adjoint
-// over it.
+// The reverse pass (k6_adjoint: g_a, g_b) needs y_l[k-1] at every k.
+// Recomputing y backwards through 1/a_l is unstable, so the forward kernel
+// stores the state every Cc samples (and, when memory allows, at every
+// kAdjSub-sample span start); without the span starts this kernel, for each
+// chunk in reverse order, recomputes the chunk forward from its checkpoint
+// (pass A, keeping the state every kAdjSub samples in a workspace), then for
+// each kAdjSub-sample span in reverse recomputes the span into registers
+// (pass B) and runs the adjoint over it.
 //
 // Mapping: filters are independent in the adjoint, so the unit of work is a
 // task of two filter rounds (32 filters each) of one template; lane i runs
 // its two filters as one packed FP32x2 pair (every recurrence and gradient
 // update is one fma/mul.rn.f32x2 for both) and keeps mu, g_a, g_b in
 // registers.  Long calls run as time segments of whole checkpoint
-// intervals, each from the adjoint state projected to its end.  A CTA
-// runs W tasks of one detector and stages each chunk's strain window in
-// shared memory; the 16-sample state checkpoints of pass A go to an
-// L2-resident workspace; g_z of the template is read by lanes 0..15 once per
-// span and broadcast with shuffles; g_x is scattered into a shared ring with
-// shared-memory atomics (the layout places a round's 32 delays on 32
-// different banks) and added to global memory per chunk.
+// intervals, each from the adjoint state projected to its end.  A CTA runs
+// W tasks of one detector and stages each chunk's strain window in shared
+// memory; g_z of the template is read by lanes 0..15 once per span and
+// broadcast with shuffles.  g_x comes from k7_adjoint_x (below), in the
+// shifted frame where it is a sum, not a scatter.
 #include "spiir_kernels.h"
 #include "spiir_ptx.h"
 
