@@ -103,3 +103,23 @@ def test_front_end_can_be_removed_and_rejects_bad_arguments(sp):
     with pytest.raises(sp.SpiirError):
         plan.state_set(st, hist, t)                      # front-end history is not in the state
     plan.close()
+
+
+def test_whitening_fir_on_a_single_rate_bank(sp):
+    """A single-rate bank's only band takes a front end too: z equals the
+    oracle's filter bank on the FIR-filtered strain (oracle.band_input)."""
+    from spiir_inputs import make_bank
+    bank = make_bank(6, (20, 100), (0.99, 0.9995), 300, seed=178, n_det=2)
+    x = make_strain(2, 6000, seed=179)
+    taps = np.array([0.9, -0.5, 0.2, -0.05], np.float32)
+    plan = sp.Plan(bank)
+    plan.set_band_fir(0, taps)
+    xt = torch.from_numpy(x).cuda()
+    z = np.concatenate([plan.filter(xt[:, :2048].contiguous()).cpu().numpy(),
+                        plan.filter(xt[:, 2048:].contiguous()).cpu().numpy()], axis=-1)
+    plan.check()
+    plan.close()
+    zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d,
+                                    oracle.band_input(x, taps.astype(np.float64)))
+    rel, _ = rel_errors(z, zref)
+    assert rel.max() <= REL_TOL, rel.max()
