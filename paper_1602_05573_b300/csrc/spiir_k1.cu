@@ -822,10 +822,11 @@ template <> struct K1Bounds<8> { static constexpr int kMinBlocks = 2; };
 template <> struct K1Bounds<10> { static constexpr int kMinBlocks = 2; };
 
 // Steps per cross-lane-sum batch for F filters per lane in a kernel compiled
-// for FCAP (only the 128-register kernels have room for several).
-__host__ __device__ constexpr int unroll_for(int FCAP, int F)
+// for FCAP (only the 128-register kernels have room for several; the time-
+// segmented kernels, which carry more state, only for F <= 4).
+__host__ __device__ constexpr int unroll_for(int FCAP, int F, bool SEG)
 {
-    return FCAP >= 6 ? (F <= 2 ? 4 : (F <= 4 ? 2 : 1)) : 1;
+    return FCAP >= 6 ? (F <= 2 ? 4 : (F <= (SEG ? 4 : 8) ? 2 : 1)) : 1;
 }
 
 // The CTA's F is uniform, so every warp takes the same case.
@@ -834,16 +835,16 @@ __device__ __forceinline__ void dispatch_f(const K1Args &A, int g, int det, floa
                                            float *zbuf, uint32_t bar0, uint32_t bar1)
 {
     const int F = A.group_F[g];
-    if (F == 1) run_unit<LANES, 1, SEG, LOW, unroll_for(FCAP, 1)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 2 ? 2 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 3 ? 3 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 4 ? 4 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 5 ? 5 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 6 ? 6 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 7 ? 7 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 8 ? 8 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 9 ? 9 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 10 ? 10 : 1))>(A, g, det, ring, zbuf, bar0, bar1);
+    if (F == 1) run_unit<LANES, 1, SEG, LOW, unroll_for(FCAP, 1, SEG)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 2 ? 2 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 3 ? 3 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 4 ? 4 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 5 ? 5 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 6 ? 6 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 7 ? 7 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 8 ? 8 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 9 ? 9 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
+    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 10 ? 10 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
     else if (threadIdx.x == 0) atomicOr(A.err, 4);
 }
 
