@@ -283,10 +283,11 @@ spiir_status spiir_chi2_peak(const float *zg_dev, int32_t n_detectors, int64_t n
  *   window     [n_detectors] int32, host; window[0] is ignored, others in
  *              [0, 1024] samples
  *   rho_dev    [n_templates] float32, device
- *   t_dev      [n_templates] int64, device
+ *   t_dev      [n_templates] int64, device (while the call runs it holds a
+ *              per-template reduction key; its final contents are the t*)
  *   shift_dev  [n_templates][n_detectors] int32, device, or NULL (column 0 = 0)
  * No plan: works on any series of that layout, on the current device,
- * asynchronously on `stream`.  1 <= n_detectors <= 8, n >= 1 (n_templates
+ * asynchronously on `stream` (one or two kernels and a memset).  1 <= n_detectors <= 8, n >= 1 (n_templates
  * = 0 is a no-op).
  * Errors: EINVAL, EUNSUPPORTED (windows too wide for shared memory), ECUDA.
  */

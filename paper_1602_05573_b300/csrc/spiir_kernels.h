@@ -266,6 +266,8 @@ struct NetArgs {
     float *rho;                   // [T]
     int64_t *t;                   // [T]
     int32_t *shift;               // [T][D] or null
+    int32_t n_chunks;             // CTAs per template (time chunks; set by the launcher)
+    int32_t chunk_tiles;          // tiles of 2048 outputs per chunk
 };
 // shared-memory words of a tile; fills the per-detector offsets
 int network_smem_words(const int32_t *w, int D, int32_t *off_p, int32_t *off_g);
