@@ -145,13 +145,16 @@ __device__ __forceinline__ void net_pivot_run(const float *p, int w, int i0, flo
     for (int k = RR - 1; k >= 0; --k)
         m[k] = k == RR - 1 ? p[pidx<R>(i0 + k)] : fmaxf(p[pidx<R>(i0 + k)], m[k + 1]);
     // the middle of the prefix in four independent chains (loads issue
-    // ahead of the maxima; max is exact, so the order does not matter)
+    // ahead of the maxima; max is exact, so the order does not matter).
+    // i0 and RR are multiples of 8 and pads fall every 8 or 16 samples, so
+    // each aligned group of 8 samples is 8 consecutive words: one address
+    // per group.
     float r4[4] = {p[pidx<R>(i0 + RR - 1)], -INFINITY, -INFINITY, -INFINITY};
     int j = RR;
-#pragma unroll 2
-    for (; j + 4 <= 2 * w; j += 4) {
+    for (; j + 8 <= 2 * w; j += 8) {
+        const float *b = p + pidx<R>(i0 + j);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) r4[q] = fmaxf(r4[q], p[pidx<R>(i0 + j + q)]);
+        for (int q = 0; q < 8; ++q) r4[q & 3] = fmaxf(r4[q & 3], b[q]);
     }
     for (; j < 2 * w; ++j) r4[0] = fmaxf(r4[0], p[pidx<R>(i0 + j)]);
     float run = fmaxf(fmaxf(r4[0], r4[1]), fmaxf(r4[2], r4[3]));
