@@ -327,14 +327,13 @@ __global__ void __launch_bounds__(kNetMaxThreads) network_finish_kernel(const Ne
 // Outputs per thread for these windows.  Shared-memory loads per output of
 // the window maxima, summed over detectors d >= 1: runs of 8 cost about
 // (2w + 9) / 8 for w >= 4 (2w + 1 below), runs of 16 about (2w + 17) / 16
-// but hold 64 registers, so 32 warps per SM instead of 48 and a slower load
-// phase (0.83 of the run-of-8 rate with windows 0).  Measured on 4096
-// templates x 3 detectors x 65536 samples, the two forms tie at windows
-// 28/28 (16.25 loads per output); runs of 8 are faster below (20/20: 1.239
-// vs 1.390 ms), runs of 16 above (40/40: 1.461 vs 1.692 ms; 64/64: 1.477 vs
-// 2.271 ms).  Windows past the scan limit go by doubling, whose CTA-wide
-// levels want the wider CTA.
-constexpr double kNetR16Loads = 16.0;
+// but, with the same shared memory per CTA and half the threads, 32 warps
+// per SM instead of 48 and a slower load phase.  Measured on 4096 templates x 3 detectors x 65536 samples: runs
+// of 8 are faster up to windows 40/40 (22.25 loads per output; 1.307 vs
+// 1.419 ms) and 10/64 (20.75; 1.267 vs 1.313 ms), runs of 16 from 48/48
+// (26.25; 1.294 vs 1.376 ms; 64/64: 1.312 vs 1.578 ms).  Windows past the
+// scan limit go by doubling, whose CTA-wide levels want the wider CTA.
+constexpr double kNetR16Loads = 24.0;
 
 int net_run_len(const int32_t *w, int D)
 {
