@@ -237,6 +237,7 @@ template <int R>
 __global__ void __launch_bounds__(kNetTile / R) network_peak_kernel(const NetArgs A)
 {
     constexpr int kThreads = kNetTile / R;
+    static_assert(kThreads % R == 0, "padded words advance by a constant per thread stride");
     extern __shared__ float sm[];
     __shared__ float red_v[kThreads / 32];
     __shared__ int64_t red_i[kThreads / 32];
@@ -258,16 +259,21 @@ __global__ void __launch_bounds__(kNetTile / R) network_peak_kernel(const NetArg
             const int M = tile + 2 * w;
             const float2 *row = A.z + ((int64_t)d * A.T + tau) * n;
             float *p = sm + A.off_p[d];
+            // kThreads is a multiple of R, so the padded word advances by a
+            // constant kStep per kThreads samples
+            constexpr int kStep = kThreads + kThreads / R;
             if (t0 - w >= 0 && t0 - w + M <= n) {
                 // interior tile: every position inside the series
                 const float2 *src = row + (t0 - w);
+                int wi = pidx<R>(tid);
 #pragma unroll 8
-                for (int i = tid; i < M; i += kThreads) p[pidx<R>(i)] = mag2(src[i]);
+                for (int i = tid; i < M; i += kThreads, wi += kStep) p[wi] = mag2(src[i]);
             } else {
+                int wi = pidx<R>(tid);
 #pragma unroll 8
-                for (int i = tid; i < M; i += kThreads) {
+                for (int i = tid; i < M; i += kThreads, wi += kStep) {
                     const int64_t pos = t0 - w + i;
-                    p[pidx<R>(i)] = (pos >= 0 && pos < n) ? mag2(row[pos]) : -INFINITY;
+                    p[wi] = (pos >= 0 && pos < n) ? mag2(row[pos]) : -INFINITY;
                 }
             }
         }
