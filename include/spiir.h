@@ -166,7 +166,10 @@ void spiir_options_default(spiir_options *opt);
 
 /*
  * Validate the bank, sort templates by filter count, pack the parameter
- * array, and (device >= 0) allocate the plan's device state on that device.
+ * array, and (device >= 0) allocate the plan's device state on that device
+ * (subsection "Optimized GPU implementation of SPIIR": the per-template
+ * parameter arrays are packed aligned and contiguous, and templates are
+ * mapped to warps or blocks by their filter count).
  * Errors: EINVAL (bad bank or options), ENOMEM, ECUDA, EUNSUPPORTED (device
  * is not compute capability 10.3, or a template is beyond the kernels'
  * limits).  On error *out is set to NULL.
@@ -195,7 +198,9 @@ spiir_status spiir_plan_get_slots(const spiir_plan *plan, int64_t *slot_filter,
 spiir_status spiir_reset(spiir_plan *plan, void *stream);
 
 /*
- * Filter the next n samples of every detector stream.
+ * Filter the next n samples of every detector stream: the summed IIR bank of
+ * subsection "SPIIR method", y_l[k] = a_l y_l[k-1] + b_l x[k - d_l] and
+ * z[k] = sum_l y_l[k] for every (detector, template).
  *   x_dev  [n_detectors][n] float32, row stride n (detector-major)
  *   n      >= 0 samples (top rate for multirate banks)
  *   z_dev  [n_detectors][n_templates][n] complex64 output in the bank's
@@ -215,7 +220,8 @@ spiir_status spiir_filter(spiir_plan *plan, const float *x_dev, int64_t n, float
                           void *stream);
 
 /*
- * Running peak of every (detector, template) since the last reset:
+ * Running peak of every (detector, template) since the last reset (the
+ * largest |z|, which flags a candidate signal, subsection "SPIIR method"):
  *   peak_abs_dev [n_detectors][n_templates] float32  max_k |z[k]|
  *   peak_idx_dev [n_detectors][n_templates] int64    its absolute sample index
  *                                                    (top rate); ties keep the
@@ -246,12 +252,40 @@ spiir_status spiir_set_band_fir(spiir_plan *plan, int32_t band, const float *tap
                                 int32_t n_taps);
 
 /*
+ * Chi^2 bins of every template of a bank (the review's chi^2 section: Allen's
+ * discriminator compares the SNR collected by p frequency bins of equal
+ * template power with each bin's share).  A SPIIR template is a sum over
+ * frequency, one single-pole filter per stretch of the chirp, so a bin is a
+ * contiguous run of a template's filters ordered by arg(a_l) (ties keep bank
+ * order), and a filter's power is its impulse-response energy
+ * |b_l|^2 / (1 - |a_l|^2).  Filter l joins bin floor(p m_l) (at most p - 1),
+ * m_l being the midpoint of its share of the template's cumulative energy,
+ * (cumulative energy up to and including l - half its own) / total, in
+ * double precision; a template of zero energy goes to bin 0.  Bin i of
+ * template t becomes template t * n_bins + i of the regrouped bank (empty
+ * bins stay empty), its filters in frequency order.
+ *   bank        host bank, as for spiir_plan_create (single-rate)
+ *   n_bins      1 <= p <= 64
+ *   group_off   [n_templates * n_bins + 1] int64, host, out: the regrouped
+ *               bank's CSR offsets
+ *   filter_of   [Ltot] int64, host, out: the bank filter at each position of
+ *               the regrouped bank
+ *   a_out, b_out [2 * Ltot] complex64, host, out (or NULL): its poles, gains
+ *   delay_out   [Ltot] int32, host, out (or NULL): its delays
+ * Host only (no device work, no allocation visible to the caller).
+ * Errors: EINVAL (bad bank, n_bins, NULL outputs), EUNSUPPORTED (multirate).
+ */
+spiir_status spiir_chi2_split(const spiir_bank_desc *bank, int32_t n_bins, int64_t *group_off,
+                              int64_t *filter_of, float *a_out, float *b_out,
+                              int32_t *delay_out);
+
+/*
  * Chi^2 signal-based veto at each template's peak (Allen's discriminator,
  * the review's chi^2 section).  Its p bins are groups of a template's
- * filters (contiguous in frequency, equal impulse-response energy; the
- * Python binding's chi2_split builds the regrouped bank), filtered as
- * templates of their own, so spiir_filter on the regrouped bank writes the
- * group series z_i in the layout read here.  Per (detector, template):
+ * filters (contiguous in frequency, equal impulse-response energy;
+ * spiir_chi2_split builds the regrouped bank), filtered as templates of
+ * their own, so spiir_filter on the regrouped bank writes the group series
+ * z_i in the layout read here.  Per (detector, template):
  * z = sum_i z_i (float32, group order), t = the first index maximising
  * |z|^2 (re*re + im*im, separately rounded products), peak = sqrt(|z(t)|^2)
  * (correctly rounded) and chi2 = p sum_i |z_i(t) - z(t) / p|^2 (raw z
@@ -296,9 +330,11 @@ spiir_status spiir_network_peak(const float *z_dev, int32_t n_detectors, int64_t
                                 int64_t *t_dev, int32_t *shift_dev, void *stream);
 
 /*
- * Vector-Jacobian product of one spiir_filter call made from zero state on/*
  * Vector-Jacobian product of one spiir_filter call made from zero state on
- * x_dev (single-rate banks).  grad_z_dev [n_detectors][n_templates][n]
+ * x_dev (single-rate banks): the reverse-time (adjoint) recurrence of the
+ * filter bank, lambda_l[k] = g_z[k] + conj(a_l) lambda_l[k+1], used when the
+ * filter coefficients are fitted to a template (section "SPIIR method":
+ * each template's filters are designed to reproduce its matched filter).  grad_z_dev [n_detectors][n_templates][n]
  * complex64 holds g_z = dL/dRe z + i dL/dIm z (the PyTorch convention);
  * outputs use the same convention and are OVERWRITTEN:
  *   grad_a_dev, grad_b_dev  [Ltot] complex64 (summed over detectors)

@@ -283,13 +283,31 @@ def ls_gains(a, d, target):
     return b, A @ b
 
 
-def chi2_groups(off, a, b, p):
+# planted mistakes understood by chi2_energy / chi2_groups (mutation tests only)
+CHI2_MUTATIONS = ("energy_no_gain", "energy_one_minus_abs", "bin_of_end")
+
+
+def chi2_energy(a, b, *, mutation=None):
+    """Energy of each filter's impulse response, the power a chi^2 bin
+    counts: sum_{k>=0} |b a^k|^2 = |b|^2 / (1 - |a|^2) (float64)."""
+    a = np.asarray(a, np.complex128)
+    b = np.asarray(b, np.complex128)
+    if mutation == "energy_no_gain":
+        return 1.0 / (1.0 - np.abs(a) ** 2)
+    if mutation == "energy_one_minus_abs":
+        return np.abs(b) ** 2 / (1.0 - np.abs(a))
+    return np.abs(b) ** 2 / (1.0 - np.abs(a) ** 2)
+
+
+def chi2_groups(off, a, b, p, *, mutation=None):
     """Allen's chi^2 bins for every template, read for a bank of single-pole
     filters: a template's filters sorted by frequency arg(a_l) and cut into p
     contiguous groups of (as nearly as whole filters allow) equal energy,
-    filter l's energy being that of its impulse response, |b_l|^2 / (1 -
-    |a_l|^2).  Filter l goes to the group holding the midpoint of its share
-    of the cumulative energy.  Returns int32 [Ltot] group indices in 0..p-1."""
+    filter l's energy being that of its impulse response (chi2_energy).
+    Filter l goes to the group holding the midpoint of its share of the
+    cumulative energy, floor(p * (E_cum(l) - E_l / 2) / E_total), at most
+    p - 1; a template of zero energy puts every filter in group 0.  Returns
+    int32 [Ltot] group indices in 0..p-1."""
     off = np.asarray(off, np.int64)
     a = np.asarray(a, np.complex128)
     b = np.asarray(b, np.complex128)
@@ -299,9 +317,12 @@ def chi2_groups(off, a, b, p):
         if idx.size == 0:
             continue
         order = idx[np.argsort(np.angle(a[idx]), kind="stable")]
-        e = np.abs(b[order]) ** 2 / (1.0 - np.abs(a[order]) ** 2)
-        mid = (np.cumsum(e) - 0.5 * e) / np.sum(e)
-        g[order] = np.minimum((mid * p).astype(np.int32), p - 1)
+        e = chi2_energy(a[order], b[order], mutation=mutation)
+        total = np.sum(e)
+        if total == 0.0:
+            continue
+        point = np.cumsum(e) if mutation == "bin_of_end" else np.cumsum(e) - 0.5 * e
+        g[order] = np.minimum((point / total * p).astype(np.int32), p - 1)
     return g
 
 

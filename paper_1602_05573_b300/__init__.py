@@ -42,7 +42,7 @@ SYMBOLS = [
     "spiir_peak", "spiir_filter_backward", "spiir_state_get", "spiir_state_set",
     "spiir_check", "spiir_selftest_bounded_wait", "spiir_status_str",
     "spiir_last_error_detail", "spiir_filter_noalloc", "spiir_set_coefficients",
-    "spiir_network_peak", "spiir_set_band_fir", "spiir_chi2_peak",
+    "spiir_network_peak", "spiir_set_band_fir", "spiir_chi2_peak", "spiir_chi2_split",
 ]
 
 
@@ -109,6 +109,9 @@ def _configure(lib):
     lib.spiir_chi2_peak.argtypes = [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32,
                                     ctypes.c_int64, _P, _P, _P, _P]
     lib.spiir_chi2_peak.restype = _st
+    lib.spiir_chi2_split.argtypes = [ctypes.POINTER(BankDesc), ctypes.c_int32, _P, _P, _P, _P,
+                                     _P]
+    lib.spiir_chi2_split.restype = _st
     lib.spiir_state_get.argtypes = [_P, _P, _P, ctypes.POINTER(ctypes.c_int64)]
     lib.spiir_state_get.restype = _st
     lib.spiir_state_set.argtypes = [_P, _P, _P, ctypes.c_int64]
@@ -484,42 +487,31 @@ def network_peak(z, window, *, want_shift: bool = True, stream=None, lib=None):
     return rho, t, shift
 
 
-def chi2_split(bank, n_bins: int):
-    """The bank regrouped for the chi^2 veto: every template's filters,
-    sorted by frequency arg(a), cut into n_bins contiguous groups of (as
-    nearly as whole filters allow) equal impulse-response energy
-    |b|^2 / (1 - |a|^2) (a filter joins the group holding the midpoint of
-    its share of the cumulative energy); group i of template t becomes
-    template t * n_bins + i (empty groups stay empty).  Returns a bank
-    object (off, a, b, d, n_det) for Plan; spiir_filter on it writes the
-    group series [D][T][n_bins][n] that chi2_peak reads.  Bins of a large
-    bank run faster in half warps (Plan(..., lanes_per_template=16)) when
-    every bin fits 160 filters: more filters per lane for the same
-    cross-lane sums."""
+def chi2_split(bank, n_bins: int, *, lib=None):
+    """The bank regrouped for the chi^2 veto by spiir_chi2_split: every
+    template's filters, ordered by frequency arg(a), cut into n_bins
+    contiguous bins of (as nearly as whole filters allow) equal
+    impulse-response energy; bin i of template t becomes template
+    t * n_bins + i (empty bins stay empty).  Returns a bank object (off, a,
+    b, d, n_det, and filter_of: the bank filter at each position) for Plan;
+    spiir_filter on it writes the bin series [D][T][n_bins][n] that
+    chi2_peak reads.  Bins of a large bank run faster in half warps
+    (Plan(..., lanes_per_template=16)) when every bin fits 160 filters."""
     import types
-    off = np.asarray(bank.off, np.int64)
-    a = np.asarray(bank.a, np.complex64)
-    b = np.asarray(bank.b, np.complex64)
-    d = np.asarray(bank.d, np.int32)
-    T = off.shape[0] - 1
-    order, counts = [], []
-    for t in range(T):
-        idx = np.arange(off[t], off[t + 1])
-        a64 = a[idx].astype(np.complex128)
-        srt = np.argsort(np.angle(a64), kind="stable")
-        e = np.abs(b[idx][srt].astype(np.complex128)) ** 2 / (1.0 - np.abs(a64[srt]) ** 2)
-        cum = np.cumsum(e)
-        grp = np.minimum(((cum - 0.5 * e) / cum[-1] * n_bins).astype(np.int64), n_bins - 1) \
-            if idx.size else np.zeros(0, np.int64)
-        for i in range(n_bins):
-            sel = idx[srt][grp == i]
-            order.append(sel)
-            counts.append(sel.size)
-    sel = np.concatenate(order) if order else np.zeros(0, np.int64)
-    new_off = np.zeros(len(counts) + 1, np.int64)
-    new_off[1:] = np.cumsum(counts)
-    return types.SimpleNamespace(off=new_off, a=a[sel], b=b[sel], d=d[sel],
-                                 n_det=int(bank.n_det))
+    lib = lib or library()
+    desc, keep = bank_desc(bank)
+    T = int(desc.n_templates)
+    ltot = int(keep[0][-1])
+    off = np.empty(T * int(n_bins) + 1, np.int64)
+    filter_of = np.empty(max(ltot, 1), np.int64)
+    a = np.empty(max(ltot, 1), np.complex64)
+    b = np.empty(max(ltot, 1), np.complex64)
+    d = np.empty(max(ltot, 1), np.int32)
+    _check(lib.spiir_chi2_split(ctypes.byref(desc), int(n_bins), _ptr(off), _ptr(filter_of),
+                                _ptr(a), _ptr(b), _ptr(d)), "spiir_chi2_split", lib)
+    del keep
+    return types.SimpleNamespace(off=off, a=a[:ltot], b=b[:ltot], d=d[:ltot],
+                                 filter_of=filter_of[:ltot], n_det=int(bank.n_det))
 
 
 def chi2_peak(zg, n_bins: int, *, stream=None, lib=None):

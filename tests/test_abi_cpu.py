@@ -194,3 +194,63 @@ def test_half_warp_mode_for_small_templates():
     assert sp.Plan(edge, device=-1, max_filters_per_lane=5).info()["lanes_per_template"] == 32
     big = make_bank(4800, (20, 97), (0.9, 0.99), 100, seed=5)
     assert sp.Plan(big, device=-1).info()["lanes_per_template"] == 32
+
+
+# ------------------------------------------------- chi^2 bins (host) ---
+
+def _golden_chi2_bank():
+    import json
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "chi2_bins_hand.json")))
+    bank = bank_of(g["off"], [complex(*v) for v in g["a"]], [complex(*v) for v in g["b"]],
+                   g["d"])
+    return g, bank
+
+
+@pytest.mark.parametrize("p", [2, 3])
+def test_chi2_split_matches_the_hand_worked_bins(p):
+    """spiir_chi2_split on the hand-worked bank: the regrouped bank's
+    filters and offsets exactly as derived by hand."""
+    g, bank = _golden_chi2_bank()
+    sb = sp.chi2_split(bank, p)
+    want = g["regrouped"][str(p)]
+    assert sb.filter_of.tolist() == want["filter_of"]
+    assert sb.off.tolist() == want["group_off"]
+    assert np.array_equal(sb.a, bank.a[sb.filter_of])
+    assert np.array_equal(sb.b, bank.b[sb.filter_of])
+    assert np.array_equal(sb.d, bank.d[sb.filter_of])
+
+
+@pytest.mark.parametrize("p,seed", [(1, 3), (4, 5), (7, 6), (64, 8)])
+def test_chi2_split_matches_the_oracle_groups(p, seed):
+    """The library's bins are the oracle's (oracle.chi2_groups), template by
+    template, each bin's filters in frequency order."""
+    import oracle
+    bank = make_bank(23, (0, 140), (0.9, 0.9999), 50, seed=seed, n_det=2)
+    sb = sp.chi2_split(bank, p)
+    grp = oracle.chi2_groups(bank.off, bank.a, bank.b, p)
+    T = bank.n_templates
+    assert sb.off.shape == (T * p + 1,) and sb.off[-1] == bank.n_filters
+    for t in range(T):
+        idx = np.arange(bank.off[t], bank.off[t + 1])
+        ang = np.angle(bank.a[idx].astype(np.complex128))
+        for i in range(p):
+            got = sb.filter_of[sb.off[t * p + i]:sb.off[t * p + i + 1]]
+            sel = idx[grp[idx] == i]
+            want = sel[np.argsort(ang[grp[idx] == i], kind="stable")]
+            assert got.tolist() == want.tolist(), (t, i)
+
+
+def test_chi2_split_rejects_bad_arguments():
+    _, bank = _golden_chi2_bank()
+    for p in (0, 65):
+        with pytest.raises(sp.SpiirError) as e:
+            sp.chi2_split(bank, p)
+        assert e.value.status == sp.EINVAL
+    from spiir_inputs import make_multirate_bank
+    mb = make_multirate_bank(2, (3, 4), (1, 4), (0.9, 0.99), 5, seed=2)
+    with pytest.raises(sp.SpiirError) as e:
+        sp.chi2_split(mb, 2)
+    assert e.value.status == sp.EUNSUPPORTED
+    desc, keep = sp.bank_desc(bank)
+    lib = sp.library()
+    assert lib.spiir_chi2_split(ctypes.byref(desc), 2, None, None, None, None, None) == sp.EINVAL

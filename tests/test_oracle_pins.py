@@ -519,6 +519,50 @@ def test_ls_gains_recovers_gains_in_the_span_and_leaves_an_orthogonal_residual()
 # Allen's discriminator with the bins read as frequency groups of a
 # template's filters: chi^2 = p sum_i |z_i - z / p|^2 at the peak.
 
+def chi2_golden():
+    g = json.load(open(os.path.join(HERE, "golden", "chi2_bins_hand.json")))
+    a = np.array([complex(*v) for v in g["a"]], np.complex64)
+    b = np.array([complex(*v) for v in g["b"]], np.complex64)
+    return g, np.array(g["off"], np.int64), a, b, np.array(g["d"], np.int32)
+
+
+def pin_chi2_energy(mutation=None):
+    """A filter's bin weight is the energy of its impulse response: the sum
+    of |y[k]|^2 over the output of the (separately pinned) filter bank run
+    on an impulse, long enough that |a|^(2N) is below 1e-17."""
+    bank = make_bank(40, 1, (0.2, 0.99), 30, seed=199)
+    n = 30 + int(np.ceil(np.log(1e-17) / (2 * np.log(0.99)))) + 1
+    x = np.zeros((1, n))
+    x[0, 0] = 1.0
+    y, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
+    measured = np.sum(np.abs(y[0]) ** 2, axis=-1)
+    e = oracle.chi2_energy(bank.a, bank.b, mutation=mutation)
+    return bool(np.all(np.abs(e - measured) <= 1e-12 * measured))
+
+
+def pin_chi2_hand(mutation=None):
+    """The hand-worked grouping of tests/golden/chi2_bins_hand.json."""
+    g, off, a, b, _ = chi2_golden()
+    return all(oracle.chi2_groups(off, a, b, p, mutation=mutation).tolist() == g["groups"][str(p)]
+               for p in (2, 3))
+
+
+CHI2_PINS = [pin_chi2_energy, pin_chi2_hand]
+
+
+@pytest.mark.parametrize("pin", CHI2_PINS, ids=lambda p: p.__name__)
+def test_chi2_pin(pin):
+    assert pin()
+
+
+@pytest.mark.parametrize("name", oracle.CHI2_MUTATIONS)
+def test_chi2_planted_mistake_is_caught(name):
+    """A wrong energy weight (no |b|^2, or 1 - |a| for 1 - |a|^2) or the end
+    of a filter's share instead of its midpoint fails a chi^2 pin."""
+    failed = [p.__name__ for p in CHI2_PINS if not p(mutation=name)]
+    assert failed, f"chi^2 mutation {name} slipped past every pin"
+
+
 def test_chi2_groups_are_contiguous_in_frequency_and_balanced():
     bank = make_bank(5, (40, 120), (0.95, 0.999), 100, seed=190)
     p = 4
