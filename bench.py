@@ -52,7 +52,6 @@ LANE_OPS_PER_UPDATE = 8      # 4 FMA + 2 MUL + 2 ADD (FP32 lane operations)
 # (10 ms) and between sites ~8000 km apart (27 ms), plus a sample
 NETWORK_WINDOWS = [0, 10, 28]
 LANE_OPS_ADJOINT = 20        # reverse pass per filter-update: recompute 6, adjoint 6, grads 8
-B300_SMS = 148
 FP32_LANES_PER_SM = 128
 
 
@@ -67,10 +66,14 @@ def parse():
                              "veto"])
     ap.add_argument("--precision", default="plain",
                     choices=["plain", "compensated", "chunked_fp64", "chunked_tc"])
-    ap.add_argument("--graph", action="store_true",
-                    help="time replays of a captured CUDA graph of the step")
-    ap.add_argument("--autotune", action="store_true",
-                    help="let the plan time candidate layouts on its first call")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time direct calls only (default: also replays of a captured CUDA "
+                         "graph of the step, which give the headline value)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default layout (default: the plan times candidate "
+                         "layouts and launch modes on its first call)")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the other workloads' sub-lines of the default run")
     ap.add_argument("--samples", type=int, default=0,
                     help="override the stream length per step (profiling runs)")
     ap.add_argument("--templates", type=int, default=0,
@@ -264,6 +267,406 @@ def shard_bank(name, rank):
                      w["seed"] + 1000 * rank, w["n_det"])
 
 
+def device_fp32_peak(dev, sm_max_mhz):
+    """FP32 lane-ops/s of the device (T/s): SMs x 128 FP32 lanes x max clock."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    return n_sm * FP32_LANES_PER_SM * sm_max_mhz * 1e6 / 1e12, n_sm
+
+
+def alu_roofline(kernel, lane_ops, kernel_ms, peak_lane, n_sm, sm_max, timing, ops_note,
+                 traffic=None, traffic_note=None):
+    achieved = lane_ops / (kernel_ms / 1e3) / 1e12
+    return {"bound": "alu", "kernel": kernel, "achieved": achieved, "peak": peak_lane,
+            "unit": "T FP32 lane-ops/s", "frac": achieved / peak_lane, "traffic": traffic,
+            "traffic_note": traffic_note,
+            "note": f"{ops_note} / {timing}; peak = {n_sm} SMs x 128 FP32 lanes x "
+                    f"{sm_max:.0f} MHz (derived from unit counts and the measured max clock)"}
+
+
+def tc_roofline(updates_per_step, tc_ms, peaks):
+    """Tensor-core projection: 3 split-BF16 products of the (2 rows per
+    filter) x (2 x 256 window) weights against one window per 256-sample
+    chunk, i.e. 24 algorithmic flops per filter-update."""
+    tc_peak = peaks.get("bf16_tflops") or 1800.0
+    ach = 24.0 * updates_per_step / (tc_ms / 1e3) / 1e12
+    return {"bound": "tensor", "kernel": "tc_project_kernel", "achieved": ach, "peak": tc_peak,
+            "unit": "TFLOP/s", "frac": ach / tc_peak, "traffic": None, "ms_per_step": tc_ms,
+            "note": "24 algorithmic BF16 flops per filter-update / its own CUDA-event time; "
+                    + ("peak = measured cuBLAS bf16 burst" if peaks.get("bf16_tflops")
+                       else "peak = fallback 1.8 PFLOP/s bf16")}
+
+
+def max_rel_error(z_gpu, z_ref):
+    """Per (detector, template): max_k |z_gpu - z_ref| / rms_k |z_ref|; the
+    largest over the sample, and the absolute error that goes with it."""
+    z_gpu = np.asarray(z_gpu).astype(np.complex128)
+    diff = np.abs(z_gpu - z_ref).max(axis=-1)
+    rms = np.sqrt(np.mean(np.abs(z_ref) ** 2, axis=-1))
+    rel = diff / np.maximum(rms, 1e-300)
+    return float(rel.max()), float(diff.max()), rel, diff
+
+
+def argmax_agrees(z_gpu, z_ref, diff):
+    """(exact, in_eps_tie, total): the GPU's first argmax of |z|^2 (float32,
+    as the kernel decides it) against the oracle's: equal, or among the
+    oracle's samples within 4x the measured error of its top."""
+    zr = np.ascontiguousarray(np.asarray(z_gpu).real, np.float32)
+    zi = np.ascontiguousarray(np.asarray(z_gpu).imag, np.float32)
+    idx = np.argmax(zr * zr + zi * zi, axis=-1)
+    mag = np.abs(z_ref)
+    exact = tie = total = 0
+    for i in np.ndindex(mag.shape[:-1]):
+        total += 1
+        top = int(np.argmax(mag[i]))
+        if int(idx[i]) == top:
+            exact += 1
+        elif mag[i][int(idx[i])] >= mag[i].max() - 4 * diff[i]:
+            tie += 1
+    return exact, tie, total
+
+
+def oracle_sample(bank, x, templates, want_z=True):
+    """The CPU-baseline leg of a sub-configuration: the FP64 oracle, as it
+    stands, on a template sample of the workload (all detectors, full
+    length), timed on the host cores.  Its z is what the sub-configuration's
+    accuracy figures compare the GPU's z with."""
+    import oracle
+    sub = bank.subset(templates)
+    n = x.shape[1]
+    t = time.perf_counter()
+    if sub.band_of is not None:
+        z, _, _ = oracle.filter_multirate(sub.off, sub.a, sub.b, sub.d, sub.band_of, sub.decim,
+                                          x, want_z=want_z)
+    else:
+        z, _, _ = oracle.filter_bank(sub.off, sub.a, sub.b, sub.d, x, want_z=want_z)
+    dt = time.perf_counter() - t
+    base = {"value": updates(sub, n) / dt, "unit": "filter-updates/s",
+            "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"{len(templates)} of {bank.n_templates} templates (seeded), all "
+                      f"{bank.n_det} detectors, {n} samples ({dt:.1f} s, FP64, OpenMP over "
+                      f"template x detector)"}
+    return base, z
+
+
+def timed(stream, fn, steps):
+    """Mean CUDA-event milliseconds of fn() over `steps` calls on `stream`."""
+    import torch
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+# ------------------------------------------------------ sub-configs ---
+def sub_plain(sp, dev, stream, peak_lane, n_sm, sm_max):
+    """Plain workload (16 templates x 64 filters, 1 detector, 16384 samples
+    at 4096 Hz): latency-bound.  Graph-replay latency of the whole call and
+    of a 1 s block, with the automatic time segments and without; the
+    oracle on the whole workload is both the CPU baseline and the accuracy
+    reference."""
+    import torch
+    bank = workload_bank("plain")
+    x_host = workload_strain("plain")
+    x = torch.from_numpy(x_host).to(dev)
+    D, n = x.shape
+    T = bank.n_templates
+    upd = updates(bank, n)
+    base, zref = oracle_sample(bank, x_host, list(range(T)))
+    out = {"workload": describe("plain", bank, n)["workload"], "cpu_baseline": base}
+    with ClockSampler(dev.index) as clk:
+        for name, seg in (("segmented", 0), ("unsegmented", 1)):
+            plan = sp.Plan(bank, device=dev.index, time_segments=seg, kernel_timing=True)
+            z = torch.empty((D, T, n), dtype=torch.complex64, device=dev)
+            pa = torch.empty((D, T), dtype=torch.float32, device=dev)
+            pi = torch.empty((D, T), dtype=torch.int64, device=dev)
+            with torch.cuda.stream(stream):
+                # accuracy of the call from zero state
+                plan.reset(stream=stream)
+                plan.filter(x, z, stream=stream)
+                plan.peak(pa, pi, stream=stream)
+                stream.synchronize()
+                zg = z.cpu().numpy()
+                rel, err, _, diff = max_rel_error(zg, zref)
+                ex, tie, tot = argmax_agrees(zg, zref, diff)
+                # K1's own time (events around its launches) over 20 direct calls
+                plan.kernel_times()
+                for _ in range(20):
+                    plan.filter(x, z, stream=stream)
+                stream.synchronize()
+                kt = plan.kernel_times()
+                segs = plan.info()["last_call_segments"]
+                res = {"time_segments": segs, "max_rel_err": rel, "max_abs_err": err,
+                       "argmax": {"exact": ex, "eps_tie": tie, "of": tot}}
+                for what, nb in (("whole call (4 s)", n), ("1 s block", 4096)):
+                    xb = x[:, :nb].contiguous()
+                    zb = torch.empty((D, T, nb), dtype=torch.complex64, device=dev)
+                    g, _, _, _ = plan.capture(xb, zb, pa, pi, warmup=True)
+                    lat = []
+                    for _ in range(100):
+                        a0 = torch.cuda.Event(enable_timing=True)
+                        a1 = torch.cuda.Event(enable_timing=True)
+                        a0.record(stream)
+                        g.replay()
+                        a1.record(stream)
+                        a1.synchronize()
+                        lat.append(a0.elapsed_time(a1))
+                    res[f"latency_ms {what}"] = {"median": float(np.median(lat)),
+                                                 "min": float(np.min(lat))}
+                    del g
+            k_ms, k_n = kt["filter"]
+            tc_ms, tc_n = kt["projection"]
+            med = res["latency_ms whole call (4 s)"]["median"]
+            res["value"] = upd / (med / 1e3)
+            res["unit"] = "filter-updates/s (whole call, graph replay median)"
+            res["roofline"] = alu_roofline(
+                "k1_plain", 8 * upd, k_ms / 20, peak_lane, n_sm, sm_max,
+                f"{k_ms / 20:.4f} ms of K1 per call (CUDA events around its launches, 20 calls)",
+                "8 algorithmic lane-ops per filter-update")
+            if tc_n:
+                res["roofline_projection"] = tc_roofline(upd, tc_ms / 20, measured_peaks())
+            out[name] = res
+            plan.close()
+    out["clocks"] = clk.summary()
+    out["note"] = ("latency-bound: 1.7e7 updates fill a few microseconds of the GPU; the "
+                   "segmented plan runs the call as parallel time segments whose start "
+                   "states come from the tensor-core projection")
+    return out
+
+
+def sub_multirate(sp, dev, stream, peak_lane, n_sm, sm_max, steps=5, warmup=2):
+    """Injection + multirate workload (2048 templates x (60 @ 4096 Hz, 120 @
+    1024 Hz, 120 @ 256 Hz), 2^20 samples at 4096 Hz): one signal, template
+    1234's own top-rate response, time-reversed (s[m] = A Re h[k0 - m]) at
+    sample 700016 with normalised SNR 12 (reading 7), in seeded N(0,1) noise.
+    h and every template's noise rms come from the library's own impulse
+    responses; the recovery check is that the template with the largest
+    normalised peak is the injected one, at the injected time."""
+    import torch
+    bank = workload_bank("multirate")
+    x_noise = workload_strain("multirate")
+    D, n = x_noise.shape
+    T = bank.n_templates
+    tau, k0, lh = 1234, 700_016, 1 << 18
+    # every template's response to an impulse at the stream start (4.3 GB)
+    plan_h = sp.Plan(bank, device=dev.index)
+    delta = torch.zeros((1, lh), dtype=torch.float32, device=dev)
+    delta[0, 0] = 1.0
+    h = plan_h.filter(delta)
+    sigma = torch.sqrt(0.5 * (h[0].abs() ** 2).sum(dim=-1).double()).cpu().numpy()   # [T]
+    ht = h[0, tau].cpu().numpy().astype(np.complex128)
+    del h
+    plan_h.close()
+    torch.cuda.empty_cache()
+    s = np.zeros((1, n))
+    m = np.arange(max(0, k0 - lh + 1), k0 + 1)
+    s[0, m] = ht[k0 - m].real
+    # the noiseless z_tau[k0] of the signal alone (the bands' subsampling
+    # makes the bank time-varying at the top rate, so it is filtered, not
+    # taken from h)
+    plan_1 = sp.Plan(bank.subset([tau]), device=dev.index)
+    zs = plan_1.filter(torch.from_numpy(s.astype(np.float32)).to(dev))
+    zs_k0 = complex(zs[0, 0, k0].item())
+    plan_1.close()
+    del zs
+    amp = 12.0 * sigma[tau] / abs(zs_k0)
+    x_host = np.ascontiguousarray((x_noise.astype(np.float64) + amp * s).astype(np.float32))
+    x = torch.from_numpy(x_host).to(dev)
+    upd = updates(bank, n)
+    plan = sp.Plan(bank, device=dev.index, kernel_timing=True)
+    pa = torch.empty((D, T), dtype=torch.float32, device=dev)
+    pi = torch.empty((D, T), dtype=torch.int64, device=dev)
+
+    def call():
+        plan.filter(x, emit_z=False, stream=stream)
+        plan.peak(pa, pi, stream=stream)
+
+    with torch.cuda.stream(stream):
+        plan.reset(stream=stream)
+        call()
+        stream.synchronize()
+        rho = pa[0].cpu().numpy() / sigma
+        t_hat = int(pi[0, tau].item())
+        won = int(np.argmax(rho))
+        for _ in range(warmup - 1):
+            call()
+        stream.synchronize()
+        plan.kernel_times()
+        with ClockSampler(dev.index) as clk:
+            ms = timed(stream, call, steps)
+        kt = plan.kernel_times()
+    plan.check(stream)
+    k_ms, k_n = kt["filter"]
+    tc_ms, tc_n = kt["projection"]
+    info = plan.info()
+    picks = sorted(set([tau] + [int(t) for t in np.random.default_rng(331).choice(T, 3, replace=False)]))
+    base, _ = oracle_sample(bank, x_host, picks, want_z=False)
+    out = {"workload": describe("multirate", bank, n)["workload"] + " + injection",
+           "value": upd / (ms / 1e3), "unit": "filter-updates/s (band-rate updates)",
+           "ms_per_step": ms, "steps": steps, "warmup": warmup,
+           "time_segments": info["last_call_segments"],
+           "injection": {"template": tau, "sample": k0, "snr": 12.0,
+                         "recovered": bool(won == tau and abs(t_hat - k0) <= 16),
+                         "argmax_template": won, "peak_sample": t_hat,
+                         "rho_injected": float(rho[tau]),
+                         "rho_runner_up": float(np.sort(rho)[-2]),
+                         "rule": "argmax over all 2048 templates of peak |z| / sigma_tau "
+                                 "(sigma_tau^2 = 1/2 sum |h_tau|^2), time within one "
+                                 "coarsest-band sample (16)"},
+           "roofline": alu_roofline(
+               "k1_plain (3 bands)", 8 * upd, k_ms / steps, peak_lane, n_sm, sm_max,
+               f"{k_n / steps:.0f} K1 launch(es), {k_ms / steps:.3f} ms per step (CUDA events "
+               f"around each launch)", "8 algorithmic lane-ops per band-rate filter-update"),
+           "clocks": clk.summary(), "cpu_baseline": base,
+           "l2": "strain (4 MB) L2-resident as in streaming use; no z stored"}
+    if tc_n:
+        out["roofline_projection"] = tc_roofline(upd, tc_ms / steps, measured_peaks())
+    plan.close()
+    return out
+
+
+def sub_precision(sp, dev, stream, peak_lane, n_sm, sm_max, steps=2):
+    """Precision-stress workload (16384 templates x 200 filters, poles
+    0.9999 <= |a| <= 0.999995, 2^20 samples at 1024 Hz): every precision
+    form's speed (two timed full-length calls after a warm-up) and its
+    accuracy on 16 seeded templates of the same full launch (the plan
+    streams the 2^20 samples again in 16 calls of 65536 with z stored, and
+    the sampled rows are compared with the oracle's)."""
+    import torch
+    bank = workload_bank("precision")
+    x_host = workload_strain("precision")
+    x = torch.from_numpy(x_host).to(dev)
+    D, n = x.shape
+    T = bank.n_templates
+    upd = updates(bank, n)
+    picks = sorted(int(t) for t in np.random.default_rng(404).choice(T, 16, replace=False))
+    base, zref = oracle_sample(bank, x_host, picks)
+    piece = 1 << 16
+    zbuf = torch.empty((D, T, piece), dtype=torch.complex64, device=dev)
+    pick_t = torch.tensor(picks, device=dev)
+    out = {"workload": describe("precision", bank, n)["workload"], "cpu_baseline": base,
+           "accuracy_sample": f"templates {picks} of the full launch, all {n} samples",
+           "forms": {}}
+    kernel = {"plain": "k1_plain", "compensated": "k1_compensated",
+              "chunked_fp64": "k1_chunked", "chunked_tc": "k1_anchored"}
+    with ClockSampler(dev.index) as clk:
+        for form in ("plain", "compensated", "chunked_fp64", "chunked_tc"):
+            plan = sp.Plan(bank, device=dev.index, precision=form, kernel_timing=True)
+            xs = x[:, :piece].contiguous()
+
+            def call():
+                plan.filter(x, emit_z=False, stream=stream)
+
+            with torch.cuda.stream(stream):
+                plan.filter(xs, emit_z=False, stream=stream)       # warm-up (weights, tiles)
+                plan.reset(stream=stream)
+                stream.synchronize()
+                plan.kernel_times()
+                ms = timed(stream, call, steps)
+                kt = plan.kernel_times()
+                # accuracy: the same plan from zero state, z of the sampled rows
+                plan.reset(stream=stream)
+                parts = []
+                for at in range(0, n, piece):
+                    plan.filter(x[:, at:at + piece].contiguous(), zbuf, stream=stream)
+                    parts.append(zbuf.index_select(1, pick_t).cpu().numpy())
+                stream.synchronize()
+            plan.check(stream)
+            zg = np.concatenate(parts, axis=-1)
+            rel, err, _, diff = max_rel_error(zg, zref)
+            ex, tie, tot = argmax_agrees(zg, zref, diff)
+            k_ms, k_n = kt["filter"]
+            tc_ms, tc_n = kt["projection"]
+            res = {"value": upd / (ms / 1e3), "unit": "filter-updates/s", "ms_per_step": ms,
+                   "steps": steps, "max_rel_err": rel, "max_abs_err": err,
+                   "argmax": {"exact": ex, "eps_tie": tie, "of": tot},
+                   "roofline": alu_roofline(
+                       kernel[form], 8 * upd, k_ms / steps, peak_lane, n_sm, sm_max,
+                       f"{k_n / steps:.0f} launch(es), {k_ms / steps:.2f} ms per step (CUDA "
+                       f"events around each launch)",
+                       "8 algorithmic lane-ops per filter-update (the form's extra work is "
+                       "not counted)")}
+            if tc_n:
+                res["roofline_projection"] = tc_roofline(upd, tc_ms / steps, measured_peaks())
+            out["forms"][form] = res
+            plan.close()
+    plain = out["forms"]["plain"]["value"]
+    for form, res in out["forms"].items():
+        res["speed_vs_plain"] = res["value"] / plain
+    out["clocks"] = clk.summary()
+    del zbuf
+    torch.cuda.empty_cache()
+    return out
+
+
+def sub_adjoint(sp, dev, stream, peak_lane, n_sm, sm_max, steps=10, warmup=3):
+    """Adjoint workload (256 templates x 200 filters, 65536 samples at 1024
+    Hz): spiir_filter_backward (dL/da, dL/db, dL/dx for a seeded g_z) against
+    the forward call on the same plan; the oracle's adjoint on 8 sampled
+    templates is the CPU baseline and the reference of g_a, g_b there."""
+    import torch
+
+    import oracle
+    bank = workload_bank("adjoint")
+    x_host = workload_strain("adjoint")
+    x = torch.from_numpy(x_host).to(dev)
+    D, n = x.shape
+    T = bank.n_templates
+    upd = updates(bank, n)
+    g = torch.Generator(device=dev).manual_seed(7)
+    gz = torch.randn((D, T, n), dtype=torch.complex64, device=dev, generator=g)
+    plan = sp.Plan(bank, device=dev.index, kernel_timing=True)
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            ga, gb, gx = plan.backward(x, gz, stream=stream)
+        stream.synchronize()
+        plan.kernel_times()
+        with ClockSampler(dev.index) as clk:
+            bw_ms = timed(stream, lambda: plan.backward(x, gz, stream=stream), steps)
+            kt = plan.kernel_times()
+            plan.reset(stream=stream)
+            fw_ms = timed(stream, lambda: plan.filter(x, emit_z=False, stream=stream), steps)
+        ga, gb, gx = plan.backward(x, gz, stream=stream)
+        stream.synchronize()
+    plan.check(stream)
+    picks = sorted(int(t) for t in np.random.default_rng(505).choice(T, 8, replace=False))
+    sub = bank.subset(picks)
+    gz_sub = gz[:, picks].cpu().numpy()
+    t0 = time.perf_counter()
+    ra, rb, _ = oracle.adjoint(sub.off, sub.a, sub.b, sub.d, x_host, gz_sub, want_gx=False)
+    dt = time.perf_counter() - t0
+    fil = np.concatenate([np.arange(bank.off[t], bank.off[t + 1]) for t in picks])
+    ga_s = ga.cpu().numpy()[fil]
+    gb_s = gb.cpu().numpy()[fil]
+    err_a = float(np.max(np.abs(ga_s - ra)) / np.max(np.abs(ra)))
+    err_b = float(np.max(np.abs(gb_s - rb)) / np.max(np.abs(rb)))
+    a_ms, a_n = kt["adjoint"]
+    plan.close()
+    return {
+        "workload": describe("adjoint", bank, n)["workload"],
+        "value": upd / (bw_ms / 1e3), "unit": "filter-updates/s of the backward",
+        "backward_ms": bw_ms, "forward_ms": fw_ms, "backward_over_forward": bw_ms / fw_ms,
+        "steps": steps, "warmup": warmup,
+        "grad_rel_err": {"g_a": err_a, "g_b": err_b,
+                         "of": f"templates {picks}: max |g_gpu - g_oracle| / max |g_oracle|"},
+        "roofline": alu_roofline(
+            "k6_adjoint + k7_adjoint_x", 20 * upd, a_ms / steps, peak_lane, n_sm, sm_max,
+            f"{a_ms / steps:.3f} ms per backward of the reverse pass (k6) and the input-gradient "
+            f"pass (k7) (CUDA events around their launches)",
+            "20 algorithmic lane-ops per filter-update of the reverse pass (recompute 6, "
+            "adjoint recurrence 6, grad a 4, grad b 2, grad x 2)"),
+        "clocks": clk.summary(),
+        "cpu_baseline": {"value": updates(sub, n) / dt, "unit": "filter-updates/s (adjoint)",
+                         "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": f"the FP64 adjoint of {len(picks)} of {T} templates, "
+                                   f"{n} samples, g_a and g_b only ({dt:.1f} s)"},
+    }
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1602_05573_b300 as sp
@@ -285,11 +688,13 @@ def run_ours(args, rank, world, local_rank):
     # z is stored for the workloads whose series fit comfortably in HBM
     emit_z = args.workload in ("batched", "plain")
     adjoint = args.workload == "adjoint"
+    use_graph = not args.no_graph and not adjoint
 
     # kernel_timing: the plan records CUDA events around each of its filter,
     # projection and adjoint launches, on the launching stream (not in graphs)
     plan = sp.Plan(bank, device=local_rank, precision=args.precision,
-                   autotune=args.autotune, kernel_timing=True)
+                   autotune=not args.no_autotune and args.precision == "plain",
+                   kernel_timing=True)
     if args.front_end and bank.decim is not None:
         for j, R in enumerate(bank.decim):
             if R > 1:   # low-pass at the band's Nyquist rate, Hann-windowed sinc
@@ -323,18 +728,12 @@ def run_ours(args, rank, world, local_rank):
         if dist is not None:
             dist.barrier()
 
-    graph = None
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            call()
-        barrier()
-        if args.graph and not adjoint:
-            graph, _, _, _ = plan.capture(x, z, pa, pi, emit_z=emit_z, warmup=False)
-            barrier()
-        step = graph.replay if graph is not None else call
+    def timed_steps(step):
+        """K steps bracketed by a barrier and a device sync on both sides;
+        per-step CUDA events on the launching stream."""
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
               for _ in range(args.steps)]
-        plan.kernel_times()   # drop the warm-up launches' events
+        barrier()
         with ClockSampler(local_rank) as clk:
             t0 = torch.cuda.Event(enable_timing=True)
             t1 = torch.cuda.Event(enable_timing=True)
@@ -345,34 +744,56 @@ def run_ours(args, rank, world, local_rank):
                 ev[i][1].record(stream)
             t1.record(stream)
             barrier()
+        return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev], clk.summary()
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):   # the first call runs the autotuner
+            call()
+        barrier()
+        plan.kernel_times()   # drop the warm-up launches' events
+        direct_ms, direct_steps, direct_clk = timed_steps(call)
         plan.check(stream)
-    ktimes = plan.kernel_times()   # the timed steps' kernels, per class
-    total_ms = t0.elapsed_time(t1)
-    step_times = [a.elapsed_time(b) for a, b in ev]
-    filt_ms = float(np.mean(step_times))
-    total_ms = max_over_ranks(total_ms, dist, dev)
+        ktimes = plan.kernel_times()   # the direct steps' kernels, per class
+        graph = None
+        if use_graph:
+            graph, _, _, _ = plan.capture(x, z, pa, pi, emit_z=emit_z, warmup=False)
+            for _ in range(2):
+                graph.replay()
+            graph_ms, graph_steps, graph_clk = timed_steps(graph.replay)
+            plan.check(stream)
+    direct_ms = max_over_ranks(direct_ms, dist, dev)
+    if graph is not None:
+        graph_ms = max_over_ranks(graph_ms, dist, dev)
+        total_ms, clocks = graph_ms, graph_clk
+    else:
+        total_ms, clocks = direct_ms, direct_clk
     ms_step = total_ms / args.steps
     value = upd * world * args.steps / (total_ms / 1e3)
 
     extra = {}
+    if graph is not None:
+        extra["direct"] = {"value": upd * world * args.steps / (direct_ms / 1e3),
+                           "ms_per_step": direct_ms / args.steps, "clocks": direct_clk,
+                           "what": "the same step as direct C-ABI calls (no graph)"}
     if adjoint:  # forward time on the same plan, for the backward/forward ratio
         with torch.cuda.stream(stream):
             plan.filter(x, emit_z=False, stream=stream)
             barrier()
-            f0 = torch.cuda.Event(enable_timing=True)
-            f1 = torch.cuda.Event(enable_timing=True)
-            f0.record(stream)
-            for _ in range(args.steps):
-                plan.filter(x, emit_z=False, stream=stream)
-            f1.record(stream)
-            barrier()
-        fwd_ms = f0.elapsed_time(f1) / args.steps
+            fwd_ms = timed(stream, lambda: plan.filter(x, emit_z=False, stream=stream),
+                           args.steps)
         extra["adjoint"] = {"backward_ms": ms_step, "forward_ms": fwd_ms,
                             "backward_over_forward": ms_step / fwd_ms}
-    def graph_latency(xb, zb, emit):
-        """Median/min of 100 graph replays of one filter+peak call on xb."""
+
+    if not adjoint and WORKLOADS[args.workload]["kind"] == "single":
+        # peak-SNR latency: graph replay of a call on strain already on the
+        # device until the running peaks are ready (the plan's sample counter
+        # moves on; the throughput numbers above are already taken)
+        rate = WORKLOADS[args.workload]["rate"]
+        nb = min(rate, n)
+        xb = x[:, :nb].contiguous()
+        zb = torch.empty((D, T, nb), dtype=torch.complex64, device=dev) if emit_z else None
         with torch.cuda.stream(stream):
-            g2, _, _, _ = plan.capture(xb, zb, pa, pi, emit_z=emit, warmup=True)
+            g2, _, _, _ = plan.capture(xb, zb, pa, pi, emit_z=emit_z, warmup=True)
             lat = []
             for _ in range(100):
                 a0 = torch.cuda.Event(enable_timing=True)
@@ -382,26 +803,11 @@ def run_ours(args, rank, world, local_rank):
                 a1.record(stream)
                 a1.synchronize()
                 lat.append(a0.elapsed_time(a1))
-        return float(np.median(lat)), float(np.min(lat))
-
-    if not adjoint and WORKLOADS[args.workload]["kind"] == "single":
-        # peak-SNR latency: graph replay of a call on strain already on the
-        # device until the running peaks are ready (the plan's sample counter
-        # moves on; the throughput numbers above are already taken)
-        rate = WORKLOADS[args.workload]["rate"]
-        lat = {}
-        blocks = [("1 s", rate)]
-        if args.workload == "plain":
-            blocks.append((f"{n / rate:g} s (the whole call)", n))
-        for what, nb in blocks:
-            if nb > n:
-                continue
-            xb = x[:, :nb].contiguous()
-            zb = torch.empty((D, T, nb), dtype=torch.complex64, device=dev) if emit_z else None
-            med, mn = graph_latency(xb, zb, emit_z)
-            lat[what] = {"median": med, "min": mn}
-        extra["latency_ms"] = dict(lat, what="graph replay of filter+peak (strain resident), "
-                                             "median and min of 100")
+            del g2
+        extra["latency_ms"] = {f"{nb / rate:g} s block": {"median": float(np.median(lat)),
+                                                          "min": float(np.min(lat))},
+                               "what": "graph replay of filter+peak (strain resident), "
+                                       "median and min of 100"}
 
     if emit_z and D > 1 and not adjoint:
         # coincidence across detectors on the stored z (spiir_network_peak),
@@ -412,14 +818,7 @@ def run_ours(args, rank, world, local_rank):
             for _ in range(args.warmup):
                 sp.network_peak(z, window, stream=stream)
             stream.synchronize()
-            n0 = torch.cuda.Event(enable_timing=True)
-            n1 = torch.cuda.Event(enable_timing=True)
-            n0.record(stream)
-            for _ in range(args.steps):
-                sp.network_peak(z, window, stream=stream)
-            n1.record(stream)
-            n1.synchronize()
-        net_ms = n0.elapsed_time(n1) / args.steps
+            net_ms = timed(stream, lambda: sp.network_peak(z, window, stream=stream), args.steps)
         # algorithmic bytes: z once; the kernel also re-reads a 2w halo per
         # 2048 outputs of every detector d >= 1
         net_bytes = float(z.numel() * 8)
@@ -474,25 +873,18 @@ def run_ours(args, rank, world, local_rank):
     # passes, decimation, segment carry/merge, counter advance; the adjoint:
     # checkpointed K1, projection, K6, K7, finalize), plus the spiir_peak copy
     launches_per_step = info["last_call_launches"] + (0 if adjoint else 1)
-    clocks = clk.summary()
     peaks = measured_peaks()
     sm_max = peaks.get("sm_max_mhz") or clocks.get("sm_max_mhz") or 2032.0
-    peak_lane = B300_SMS * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12   # T lane-ops/s
+    peak_lane, n_sm = device_fp32_peak(dev, sm_max)
     kernel = {"plain": "k1_plain", "compensated": "k1_compensated",
               "chunked_fp64": "k1_chunked", "chunked_tc": "k1_anchored"}[args.precision]
-    # the dominant kernel's own device time over the timed steps (events the
-    # plan records around each launch); graph replays record none, then the
-    # step time stands in
+    # the dominant kernel's own device time over the direct timed steps
+    # (events the plan records around each launch; graph replays record none)
     k_ms, k_n = ktimes["adjoint" if adjoint else "filter"]
     lane_ops = (LANE_OPS_ADJOINT if adjoint else LANE_OPS_PER_UPDATE) * upd
-    if k_n > 0:
-        kernel_ms = k_ms / args.steps
-        timing = (f"{k_n / args.steps:.0f} launch(es) per step, {kernel_ms:.3f} ms per step "
-                  f"(CUDA events around each launch on the launching stream)")
-    else:
-        kernel_ms = filt_ms
-        timing = f"mean step time {filt_ms:.3f} ms (graph replay: no per-launch events)"
-    achieved = lane_ops / (kernel_ms / 1e3) / 1e12
+    kernel_ms = k_ms / args.steps
+    timing = (f"{k_n / args.steps:.0f} launch(es) per step, {kernel_ms:.3f} ms per step "
+              f"(CUDA events around each launch on the launching stream, direct steps)")
     if adjoint:
         kernel = "k6_adjoint + k7_adjoint_x"
     traffic, traffic_note = None, None
@@ -510,6 +902,7 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded N(0,1) strain, random poles/gains/delays)",
         "config": dict(describe(args.workload, bank, n),
                        precision=args.precision, graph=bool(graph is not None),
+                       autotune=not args.no_autotune and args.precision == "plain",
                        z_stored=emit_z, front_end=bool(args.front_end),
                        parallelism=f"template shards x{world}" if world > 1 else "1 GPU",
                        l2=("each step writes the z series (> 126 MB L2), which evicts the "
@@ -519,18 +912,16 @@ def run_ours(args, rank, world, local_rank):
                        plan={k: info[k] for k in ("warps_per_cta", "block_len", "ring_copies",
                                                   "history_len", "smem_bytes",
                                                   "max_filters_per_lane",
-                                                  "bank_conflict_ratio", "n_slots",
-                                                  "last_call_segments")}),
-        "roofline": {"bound": "alu", "kernel": kernel, "achieved": achieved,
-                     "peak": peak_lane, "unit": "T FP32 lane-ops/s",
-                     "frac": achieved / peak_lane, "traffic": traffic,
-                     "traffic_note": traffic_note,
-                     "note": f"{ops_note} x {upd:.4g} updates per step / {timing}; "
-                             f"peak = 148 SMs x 128 FP32 lanes x {sm_max:.0f} MHz (derived "
-                             f"from unit counts and the measured max clock)"},
+                                                  "bank_conflict_ratio", "n_slots", "n_units",
+                                                  "persistent", "tail_templates",
+                                                  "last_call_segments")},
+                       autotune_report=plan.tune_report()),
+        "roofline": alu_roofline(kernel, lane_ops, kernel_ms, peak_lane, n_sm, sm_max, timing,
+                                 f"{ops_note} x {upd:.4g} updates per step", traffic,
+                                 traffic_note),
         "gpu_launches": launches_per_step * args.steps,
         "clocks": clocks,
-        "filter_ms": filt_ms,
+        "filter_ms": float(np.mean(graph_steps if graph is not None else direct_steps)),
         # templates (all detectors, mean filter count) whose 1 s of data is
         # filtered in 1 s at this throughput
         "templates_realtime": upd * world / (ms_step / 1e3) / (bank.n_filters / T * D)
@@ -538,24 +929,26 @@ def run_ours(args, rank, world, local_rank):
     }
     tc_ms, tc_n = ktimes["projection"]
     if tc_n > 0:
-        # tensor-core projection: 3 split-BF16 products of the (2 rows per
-        # filter) x (2 x 256 window) weights against one window per 256-sample
-        # chunk, i.e. 24 algorithmic flops per filter-update
-        tc_flops = 24.0 * upd
-        tc_peak = peaks.get("bf16_tflops") or 1800.0
-        tc_ach = tc_flops / (tc_ms / args.steps / 1e3) / 1e12
-        line["roofline_projection"] = {
-            "bound": "tensor", "kernel": "tc_project_kernel", "achieved": tc_ach,
-            "peak": tc_peak, "unit": "TFLOP/s", "frac": tc_ach / tc_peak, "traffic": None,
-            "ms_per_step": tc_ms / args.steps, "launches_per_step": tc_n / args.steps,
-            "note": "24 algorithmic BF16 flops per filter-update / its own CUDA-event time; "
-                    "peak = measured cuBLAS bf16 burst (MEASURED_PEAKS.json)"
-                    if peaks.get("bf16_tflops") else "peak = fallback 1.8 PFLOP/s bf16"}
+        line["roofline_projection"] = tc_roofline(upd, tc_ms / args.steps, peaks)
+        line["roofline_projection"]["launches_per_step"] = tc_n / args.steps
     line.update(extra)
     if e2e:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and not adjoint:
         line["cpu_baseline"] = cpu_baseline(args.workload, bank, x_host)
+    plan.close()
+    del z
+    torch.cuda.empty_cache()
+    # the other workloads, each with its own clocks and roofline (one GPU)
+    if world == 1 and args.workload == "batched" and not args.headline_only:
+        subs = {}
+        for name, fn in (("plain", sub_plain), ("multirate", sub_multirate),
+                         ("precision", sub_precision), ("adjoint", sub_adjoint)):
+            t = time.perf_counter()
+            subs[name] = fn(sp, dev, stream, peak_lane, n_sm, sm_max)
+            subs[name]["wall_s"] = time.perf_counter() - t
+            torch.cuda.empty_cache()
+        line["configs"] = subs
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

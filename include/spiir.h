@@ -133,7 +133,20 @@ typedef struct spiir_options {
     int32_t tile_chunks;    /* chunked_tc: 256-sample chunks per time tile (the    */
                             /* anchors of one tile are held at once); 0 = auto:    */
                             /* anchors within a quarter of free memory, <= 16 GiB */
-    int32_t reserved[1];
+    int32_t persistent;     /* unsegmented plain calls: 1 = one CTA per (CTA group,  */
+                            /* detector) unit, in launch order largest first (the   */
+                            /* hardware starts each CTA where one has finished);   */
+                            /* 2 = persistent: as many CTAs as fit on the GPU at    */
+                            /* once take the units, largest first, from a device    */
+                            /* counter; 0 = auto: 1, or what the autotuner picked   */
+    int32_t tail_split;     /* plain single-rate banks: the smallest templates run  */
+                            /* on twice their warps so the launch ends on short     */
+                            /* units.  0 = off, -1 = auto (the split, up to 20% of  */
+                            /* the bank's filter rounds, with the shortest         */
+                            /* predicted launch on the resident CTAs), k in 1..200 */
+                            /* = the smallest templates holding k per mille of the  */
+                            /* filter rounds                                        */
+    int32_t reserved[2];
 } spiir_options;
 
 /* Plan statistics (spiir_plan_get_info). */
@@ -156,7 +169,10 @@ typedef struct spiir_plan_info {
                                 /* spiir_filter_backward call launched (not counting */
                                 /* the autotuner's first-call timing launches)       */
     int32_t last_call_segments; /* time segments of the last spiir_filter call      */
-    int32_t reserved[1];
+    int32_t persistent;         /* 1: unsegmented plain calls launch persistent CTAs */
+                                /* (the option, or the autotuner's choice)            */
+    int64_t tail_templates;     /* templates the tail split gave twice their warps   */
+    int64_t resident_ctas;      /* resident CTAs the tail split's launch model used  */
 } spiir_plan_info;
 
 typedef struct spiir_plan spiir_plan;
@@ -182,6 +198,12 @@ spiir_status spiir_plan_destroy(spiir_plan *plan);
 
 /* Statistics of the plan's layout.  Works for host-only plans. */
 spiir_status spiir_plan_get_info(const spiir_plan *plan, spiir_plan_info *info);
+
+/* The autotuner's timings, one "cap/W/C/Tb/tail=ms" entry per candidate
+ * layout ("" before the first call of an autotuned plan, or without
+ * autotune).  The string belongs to the plan and lives until its next
+ * spiir_filter call or its destruction. */
+const char *spiir_plan_tune_report(const spiir_plan *plan);
 
 /*
  * Slot map of a plan, for inspection: slot_filter[s] is the bank filter index

@@ -43,6 +43,7 @@ SYMBOLS = [
     "spiir_check", "spiir_selftest_bounded_wait", "spiir_status_str",
     "spiir_last_error_detail", "spiir_filter_noalloc", "spiir_set_coefficients",
     "spiir_network_peak", "spiir_set_band_fir", "spiir_chi2_peak", "spiir_chi2_split",
+    "spiir_plan_tune_report",
 ]
 
 
@@ -61,7 +62,8 @@ class Options(ctypes.Structure):
                 ("autotune", ctypes.c_int32), ("max_filters_per_lane", ctypes.c_int32),
                 ("lanes_per_template", ctypes.c_int32), ("time_segments", ctypes.c_int32),
                 ("projection", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
-                ("tile_chunks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("tile_chunks", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("tail_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -73,7 +75,8 @@ class PlanInfo(ctypes.Structure):
                 ("max_filters_per_lane", ctypes.c_int32), ("precision", ctypes.c_int32),
                 ("bank_conflict_ratio", ctypes.c_double),
                 ("lanes_per_template", ctypes.c_int32), ("last_call_launches", ctypes.c_int32),
-                ("last_call_segments", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("last_call_segments", ctypes.c_int32), ("persistent", ctypes.c_int32),
+                ("tail_templates", ctypes.c_int64), ("resident_ctas", ctypes.c_int64)]
 
 
 _P = ctypes.c_void_p
@@ -91,6 +94,8 @@ def _configure(lib):
     lib.spiir_plan_destroy.restype = _st
     lib.spiir_plan_get_info.argtypes = [_P, ctypes.POINTER(PlanInfo)]
     lib.spiir_plan_get_info.restype = _st
+    lib.spiir_plan_tune_report.argtypes = [_P]
+    lib.spiir_plan_tune_report.restype = ctypes.c_char_p
     lib.spiir_plan_get_slots.argtypes = [_P, _P, _P]
     lib.spiir_plan_get_slots.restype = _st
     lib.spiir_reset.argtypes = [_P, _P]
@@ -237,7 +242,8 @@ class Plan:
                  chunk_len: int = 256, autotune: bool = False,
                  max_filters_per_lane: int = 0, lanes_per_template: int = 0,
                  time_segments: int = 0, projection: str = "auto",
-                 kernel_timing: bool = False, tile_chunks: int = 0, lib=None):
+                 kernel_timing: bool = False, tile_chunks: int = 0, persistent: str = "auto",
+                 tail_split: int = 0, lib=None):
         self._h = None
         self._lib = lib if lib is not None else _lib
         off = np.ascontiguousarray(bank.off, np.int64)
@@ -273,6 +279,8 @@ class Plan:
         opt.projection = PROJECTIONS[projection]
         opt.kernel_timing = 1 if kernel_timing else 0
         opt.tile_chunks = int(tile_chunks)
+        opt.persistent = {"auto": 0, "off": 1, "on": 2}[persistent]
+        opt.tail_split = int(tail_split)
         h = _P()
         _check(self._lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
                "spiir_plan_create", self._lib)
@@ -309,6 +317,10 @@ class Plan:
         _check(self._lib.spiir_plan_get_info(self._h, ctypes.byref(inf)), "spiir_plan_get_info", self._lib)
         return {name: getattr(inf, name) for name, _ in PlanInfo._fields_
                 if name != "reserved"}
+
+    def tune_report(self) -> str:
+        """The autotuner's timing per candidate layout ("" if it has not run)."""
+        return self._lib.spiir_plan_tune_report(self._h).decode()
 
     def slots(self):
         n = self.info()["n_slots"]

@@ -197,6 +197,8 @@ struct spiir_plan {
     int64_t *peak_idx = nullptr;  // [D][T]
     int32_t *err = nullptr;
     int64_t *t0_dev = nullptr;    // samples since reset, on the device (graph replays advance it)
+    int32_t *queue = nullptr;     // unit counter of persistent filter launches
+    bool persistent = false;      // unsegmented plain calls launch persistent CTAs
     int64_t t0 = 0;               // the same, as enqueued by this host (alignment checks)
     int top = 0;                  // index of the top-rate band
     int maxR = 1;                 // largest decimation factor
@@ -429,6 +431,11 @@ spiir::K1Args k1_args(const spiir_plan *p, const Band &b, int64_t n, float *z, i
     a.t0 = p->t0;
     a.err = p->err;
     a.wait_limit_ns = kWaitLimitNs;
+    // the persistent kernel serves units in stages of non-increasing F
+    bool f_sorted = true;
+    for (int64_t u = 1; u < L.n_units() && f_sorted; ++u)
+        f_sorted = L.group_F[L.units[2 * u]] <= L.group_F[L.units[2 * (u - 1)]];
+    a.queue = (p->persistent && f_sorted) ? p->queue : nullptr;
     return a;
 }
 
@@ -478,6 +485,10 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
         return fail(SPIIR_EINVAL, "unknown precision mode");
     if (opt.chunk_len == 0) opt.chunk_len = 256;
     if (opt.tile_chunks < 0) return fail(SPIIR_EINVAL, "tile_chunks must be >= 0");
+    if (opt.persistent < 0 || opt.persistent > 2)
+        return fail(SPIIR_EINVAL, "persistent must be 0 (auto), 1 (off) or 2 (on)");
+    if (opt.tail_split < -1 || opt.tail_split > 200)
+        return fail(SPIIR_EINVAL, "tail_split must be -1 (off), 0 (auto) or 1..200 per mille");
     if (opt.precision == SPIIR_PREC_CHUNKED_TC && opt.chunk_len != spiir::kTcT)
         return fail(SPIIR_EINVAL, "the tensor-core chunked form uses chunks of " +
                                       std::to_string(spiir::kTcT) + " samples");
@@ -513,6 +524,7 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     p->T = bank->n_templates;
     p->Ltot = bank->filter_off[bank->n_templates];
     p->opt = opt;
+    p->persistent = opt.persistent == 2;
 
     // bands: filter lists per template and band
     std::vector<int> decims;
@@ -537,6 +549,15 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
                                           std::to_string(lo.Tb) + ")");
     }
     lo.n_sm = n_sm;
+    // the tail split serves single-rate plain banks (the persistent launch)
+    // (option 0 = off, -1 = auto, k = per mille; the layout's -1 = off, 0 = auto)
+    lo.tail = (opt.precision == SPIIR_PREC_PLAIN && decims.size() == 1 && opt.tail_split != 0)
+                  ? (opt.tail_split < 0 ? 0 : opt.tail_split)
+                  : -1;
+    if (opt.device >= 0 && lo.tail >= 0) {
+        DeviceGuard g(opt.device);
+        lo.regs = g.ok ? spiir::k1_plain_regs(lo.Fcap == 0 ? spiir::kMaxF : lo.Fcap) : 0;
+    }
     p->bands.resize(decims.size());
     for (size_t j = 0; j < decims.size(); ++j) {
         std::vector<std::vector<int64_t>> lists((size_t)p->T);
@@ -609,7 +630,8 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     if ((e = dalloc(&p->peak_best, (size_t)p->D * p->T)) != cudaSuccess ||
         (e = dalloc(&p->peak_idx, (size_t)p->D * p->T)) != cudaSuccess ||
         (e = dalloc(&p->err, 1)) != cudaSuccess ||
-        (e = dalloc(&p->t0_dev, 1)) != cudaSuccess) {
+        (e = dalloc(&p->t0_dev, 1)) != cudaSuccess ||
+        (e = dalloc(&p->queue, 1)) != cudaSuccess) {
         spiir_plan_destroy(p);
         return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "device allocation failed")
                                               : cuda_fail(e, "cudaMalloc");
@@ -638,6 +660,7 @@ spiir_status spiir_plan_destroy(spiir_plan *p)
         cudaFree(p->peak_idx);
         cudaFree(p->err);
         cudaFree(p->t0_dev);
+        cudaFree(p->queue);
         cudaFree(p->fir_xh);
         cudaFree(p->fir_xt);
         for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
@@ -672,7 +695,15 @@ spiir_status spiir_plan_get_info(const spiir_plan *p, spiir_plan_info *info)
     info->bank_conflict_ratio = rounds > 0 ? wf / rounds : 1.0;
     info->last_call_launches = p->last_launches;
     info->last_call_segments = p->last_segments;
+    info->persistent = p->persistent ? 1 : 0;
+    info->tail_templates = p->bands[p->top].lay.tail_templates;
+    info->resident_ctas = p->bands[p->top].lay.slots_model;
     return SPIIR_OK;
+}
+
+const char *spiir_plan_tune_report(const spiir_plan *p)
+{
+    return p ? p->tune_report.c_str() : "";
 }
 
 spiir_status spiir_plan_get_slots(const spiir_plan *p, int64_t *slot_filter,
@@ -1025,16 +1056,22 @@ spiir_status autotune(spiir_plan *p, const float *x_dev, int64_t n, cudaStream_t
 {
     struct Cand {
         int Fcap, W, C, Tb;
+        int tail;          // layout tail split: -1 off, 0 auto
+        bool persistent;   // persistent launch (else one CTA per unit)
     };
-    static const Cand cands[] = {{10, 4, 1, 512}, {10, 4, 2, 512}, {10, 4, 1, 256},
-                                 {10, 2, 1, 512}, {10, 8, 1, 256}, {8, 4, 1, 512},
-                                 {4, 8, 2, 256},  {4, 4, 1, 512},  {2, 8, 1, 256}};
+    static const Cand cands[] = {
+        {10, 4, 1, 512, -1, false}, {10, 4, 1, 512, -1, true}, {10, 4, 1, 512, 0, false},
+        {10, 4, 2, 512, -1, false}, {10, 4, 1, 256, -1, false}, {10, 2, 1, 512, -1, false},
+        {10, 8, 1, 256, -1, false}, {8, 4, 1, 512, -1, false},  {4, 8, 2, 256, -1, false},
+        {4, 4, 1, 512, -1, false},  {2, 8, 1, 256, -1, false}};
+    const bool forced_launch = p->opt.persistent != 0;
     const int64_t nt = std::min<int64_t>(n, 8192);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e;
     if ((e = cudaEventCreate(&e0)) != cudaSuccess || (e = cudaEventCreate(&e1)) != cudaSuccess)
         return cuda_fail(e, "autotune events");
     float best_ms = 1e30f;
+    bool best_persistent = p->persistent;
     Band best;
     bool have = false;
     std::string report;
@@ -1046,6 +1083,9 @@ spiir_status autotune(spiir_plan *p, const float *x_dev, int64_t n, cudaStream_t
         lo.C = c.C;
         lo.Tb = c.Tb;
         lo.n_sm = p->n_sm;
+        if (forced_launch && c.persistent != p->persistent) continue;
+        lo.tail = p->opt.tail_split > 0 ? p->opt.tail_split : c.tail;
+        if (lo.tail >= 0) lo.regs = spiir::k1_plain_regs(c.Fcap);
         std::string err;
         if (!spiir::build_layout(p->lists, p->D, p->a_host.data(), p->b_host.data(),
                                  p->d_host.data(), lo, &b.lay, &err))
@@ -1064,6 +1104,7 @@ spiir_status autotune(spiir_plan *p, const float *x_dev, int64_t n, cudaStream_t
             continue;
         }
         spiir::K1Args a = k1_args(p, b, nt, nullptr, nt, false);
+        a.queue = c.persistent ? p->queue : nullptr;
         // one untimed launch, then the timed one
         e = spiir::launch_k1(a, b.lay.n_units(), b.lay.smem_bytes(), s);
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
@@ -1079,12 +1120,14 @@ spiir_status autotune(spiir_plan *p, const float *x_dev, int64_t n, cudaStream_t
             return cuda_fail(e, "autotune launch");
         }
         report += "cap" + std::to_string(c.Fcap) + "/W" + std::to_string(c.W) + "/C" +
-                  std::to_string(c.C) + "/Tb" + std::to_string(c.Tb) + "=" +
-                  std::to_string(ms) + "ms ";
+                  std::to_string(c.C) + "/Tb" + std::to_string(c.Tb) + "/tail" +
+                  std::to_string(b.lay.tail_templates) + (c.persistent ? "/persistent" : "") +
+                  "=" + std::to_string(ms) + "ms ";
         if (ms < best_ms) {
             if (have) free_band(best);
             best = b;
             best_ms = ms;
+            best_persistent = c.persistent;
             have = true;
         } else {
             free_band(b);
@@ -1099,6 +1142,7 @@ spiir_status autotune(spiir_plan *p, const float *x_dev, int64_t n, cudaStream_t
             return cuda_fail(e, "autotune reset");
         free_band(p->bands[0]);
         p->bands[0] = best;
+        p->persistent = best_persistent;
     }
     p->tune_report = report;
     p->tuned = true;

@@ -41,6 +41,7 @@
 #include <cstdint>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 
 namespace spiir {
@@ -616,9 +617,16 @@ __device__ __forceinline__ void save_sub16(const K1Args &A, const LANES &L, int6
 // SEG: the CTA serves one time segment of the call; LOW: the call adds lower
 // bands (multirate top band).  Both are compile-time so the plain single-band
 // kernel carries neither's code.
+// Phases of the CTA's two block barriers completed by earlier units (a
+// persistent CTA serves many units on the same barriers): bar0 completes one
+// phase per even block of a unit, bar1 one per odd block.
+struct Phases {
+    uint32_t p0 = 0, p1 = 0;
+};
+
 template <template <int> class LANES, int F, bool SEG, bool LOW, int U>
-__device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float *ring,
-                                         float *zbuf, uint32_t bar0, uint32_t bar1)
+__device__ __forceinline__ bool run_unit(const K1Args &A, int g, int det, float *ring,
+                                         float *zbuf, uint32_t bar0, uint32_t bar1, Phases &ph)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int4 wi = A.warp_info[(int64_t)g * A.W + warp];
@@ -687,7 +695,8 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
     int failed_at = -1;
     for (int j = 0; j < nblk; ++j) {
         const uint32_t bar = (j & 1) ? bar1 : bar0;
-        const bool ok = mbar_wait(bar, (uint32_t)((j >> 1) & 1), A.wait_limit_ns);
+        const bool ok =
+            mbar_wait(bar, (uint32_t)(((j >> 1) + ((j & 1) ? ph.p1 : ph.p0)) & 1), A.wait_limit_ns);
         if (__syncthreads_or(!ok)) {
             failed_at = j;
             break;
@@ -784,14 +793,18 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
             // let copies still in flight land before the CTA's memory is reused:
             // the block that timed out, and the one issued after it (bounded)
             const int j = failed_at;
-            mbar_wait((j & 1) ? bar1 : bar0, (uint32_t)((j >> 1) & 1), A.wait_limit_ns);
+            mbar_wait((j & 1) ? bar1 : bar0,
+                      (uint32_t)(((j >> 1) + ((j & 1) ? ph.p1 : ph.p0)) & 1), A.wait_limit_ns);
             if (j + 1 < nblk)
-                mbar_wait(((j + 1) & 1) ? bar1 : bar0, (uint32_t)(((j + 1) >> 1) & 1),
+                mbar_wait(((j + 1) & 1) ? bar1 : bar0,
+                          (uint32_t)((((j + 1) >> 1) + (((j + 1) & 1) ? ph.p1 : ph.p0)) & 1),
                           A.wait_limit_ns);
         }
-        return;
+        return false;
     }
-    if (!active) return;
+    ph.p0 += (uint32_t)((nblk + 1) / 2);
+    ph.p1 += (uint32_t)(nblk / 2);
+    if (!active) return true;
     L.finish(A, n);
     {
         float2 *sout = !SEG ? A.state
@@ -809,6 +822,7 @@ __device__ __forceinline__ void run_unit(const K1Args &A, int g, int det, float 
         if (tmpl2 >= 0)
             warp_peak_merge(A, peak_best, peak_idx, det, tmpl2, lane, best2, bidx2, own);
     }
+    return true;
 }
 
 // Registers per thread follow the filters-per-lane cap: CTAs of up to 256
@@ -829,23 +843,57 @@ __host__ __device__ constexpr int unroll_for(int FCAP, int F, bool SEG)
     return FCAP >= 6 ? (F <= 2 ? 4 : (F <= (SEG ? 4 : 8) ? 2 : 1)) : 1;
 }
 
-// The CTA's F is uniform, so every warp takes the same case.
+// The CTA's F is uniform, so every warp takes the same case.  Returns false
+// when a bounded wait gave up (the CTA then stops).
 template <template <int> class LANES, int FCAP, bool SEG, bool LOW>
-__device__ __forceinline__ void dispatch_f(const K1Args &A, int g, int det, float *ring,
-                                           float *zbuf, uint32_t bar0, uint32_t bar1)
+__device__ __forceinline__ bool dispatch_f(const K1Args &A, int g, int det, float *ring,
+                                           float *zbuf, uint32_t bar0, uint32_t bar1, Phases &ph)
 {
     const int F = A.group_F[g];
-    if (F == 1) run_unit<LANES, 1, SEG, LOW, unroll_for(FCAP, 1, SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 2 && F == 2) run_unit<LANES, (FCAP >= 2 ? 2 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 2 ? 2 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 3 && F == 3) run_unit<LANES, (FCAP >= 3 ? 3 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 3 ? 3 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 4 && F == 4) run_unit<LANES, (FCAP >= 4 ? 4 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 4 ? 4 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 5 && F == 5) run_unit<LANES, (FCAP >= 5 ? 5 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 5 ? 5 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 6 && F == 6) run_unit<LANES, (FCAP >= 6 ? 6 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 6 ? 6 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 7 && F == 7) run_unit<LANES, (FCAP >= 7 ? 7 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 7 ? 7 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 8 && F == 8) run_unit<LANES, (FCAP >= 8 ? 8 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 8 ? 8 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 9 && F == 9) run_unit<LANES, (FCAP >= 9 ? 9 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 9 ? 9 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (FCAP >= 10 && F == 10) run_unit<LANES, (FCAP >= 10 ? 10 : 1), SEG, LOW, unroll_for(FCAP, (FCAP >= 10 ? 10 : 1), SEG)>(A, g, det, ring, zbuf, bar0, bar1);
-    else if (threadIdx.x == 0) atomicOr(A.err, 4);
+#define SPIIR_K1_CASE(FF)                                                                     \
+    if (FCAP >= FF && F == FF)                                                               \
+        return run_unit<LANES, (FCAP >= FF ? FF : 1), SEG, LOW,                              \
+                        unroll_for(FCAP, (FCAP >= FF ? FF : 1), SEG)>(A, g, det, ring, zbuf, \
+                                                                      bar0, bar1, ph);
+    SPIIR_K1_CASE(1)
+    SPIIR_K1_CASE(2)
+    SPIIR_K1_CASE(3)
+    SPIIR_K1_CASE(4)
+    SPIIR_K1_CASE(5)
+    SPIIR_K1_CASE(6)
+    SPIIR_K1_CASE(7)
+    SPIIR_K1_CASE(8)
+    SPIIR_K1_CASE(9)
+    SPIIR_K1_CASE(10)
+#undef SPIIR_K1_CASE
+    if (threadIdx.x == 0) atomicOr(A.err, 4);
+    return false;
+}
+
+// Persistent CTAs: the units come in order of non-increasing F (the
+// layout sorts them so), so a CTA runs one stage per F, from the cap down,
+// each looping over the units of its F; a stage's loop holds one
+// instantiation of run_unit, and the stages follow each other without an
+// enclosing loop (a loop around all of them keeps every instantiation's
+// hoisted invariants live at once).  Returns the first unit not served.
+template <int FCAP, bool LOW, int F>
+__device__ __forceinline__ int run_stage(const K1Args &A, int u, float *ring, float *zbuf,
+                                         uint32_t bar0, uint32_t bar1, Phases &ph, int *next,
+                                         bool &ok)
+{
+    if constexpr (F <= FCAP) {
+        while (ok && u < A.n_units && A.group_F[A.units[2 * u]] == F) {
+            ok = run_unit<PackedLanes, F, false, LOW, unroll_for(FCAP, F, false)>(
+                A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0, bar1, ph);
+            if (!ok) break;
+            // every warp is done with the ring, the block sums and `next`
+            __syncthreads();
+            if (threadIdx.x == 0) *next = atomicAdd(A.queue, 1);
+            __syncthreads();
+            u = *next;
+        }
+    }
+    return u;
 }
 
 __device__ __forceinline__ void cta_setup(unsigned char *smem, const K1Args &A, float *&ring,
@@ -864,6 +912,8 @@ __device__ __forceinline__ void cta_setup(unsigned char *smem, const K1Args &A, 
     __syncthreads();
 }
 
+// One CTA per unit: CTA b serves unit b (SEG: unit b % n_units of segment
+// b / n_units).
 template <int FCAP, bool SEG, bool LOW>
 __global__ void __launch_bounds__(256, K1Bounds<FCAP>::kMinBlocks) k1_plain(const K1Args A)
 {
@@ -871,9 +921,42 @@ __global__ void __launch_bounds__(256, K1Bounds<FCAP>::kMinBlocks) k1_plain(cons
     float *ring, *zbuf;
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
+    Phases ph;
     const int u = SEG ? (int)(blockIdx.x % A.n_units) : (int)blockIdx.x;
-    dispatch_f<PackedLanes, FCAP, SEG, LOW>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
-                                       bar1);
+    dispatch_f<PackedLanes, FCAP, SEG, LOW>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf,
+                                            bar0, bar1, ph);
+}
+
+// Persistent launch of the unsegmented plain kernel: a grid of at most the
+// resident CTAs takes units in the layout's order (largest F first) from a
+// global counter the launcher zeroes, so the CTAs that finish first take the
+// next unit and the smallest units end the launch (see run_stage).
+template <int FCAP, bool LOW>
+__global__ void __launch_bounds__(256, K1Bounds<FCAP>::kMinBlocks)
+    k1_persistent(const K1Args A)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *ring, *zbuf;
+    uint32_t bar0, bar1;
+    cta_setup(smem, A, ring, zbuf, bar0, bar1);
+    Phases ph;
+    __shared__ int next;
+    if (threadIdx.x == 0) next = atomicAdd(A.queue, 1);
+    __syncthreads();
+    int u = next;
+    bool ok = true;
+    u = run_stage<FCAP, LOW, 10>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    u = run_stage<FCAP, LOW, 9>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    u = run_stage<FCAP, LOW, 8>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    u = run_stage<FCAP, LOW, 7>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    u = run_stage<FCAP, LOW, 6>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    u = run_stage<FCAP, LOW, 5>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    u = run_stage<FCAP, LOW, 4>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    u = run_stage<FCAP, LOW, 3>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    u = run_stage<FCAP, LOW, 2>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    u = run_stage<FCAP, LOW, 1>(A, u, ring, zbuf, bar0, bar1, ph, &next, ok);
+    // a unit out of F order (or an F above the cap) is not served: flag it
+    if (ok && u < A.n_units && threadIdx.x == 0) atomicOr(A.err, 4);
 }
 
 __global__ void __launch_bounds__(256, 2) k1_compensated(const K1Args A)
@@ -883,8 +966,9 @@ __global__ void __launch_bounds__(256, 2) k1_compensated(const K1Args A)
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
     const int u = blockIdx.x % A.n_units;
-    dispatch_f<CompLanes, kPreciseFcap, false, true>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
-                                        bar1);
+    Phases ph;
+    dispatch_f<CompLanes, kPreciseFcap, false, true>(A, A.units[2 * u], A.units[2 * u + 1], ring,
+                                                     zbuf, bar0, bar1, ph);
 }
 
 __global__ void __launch_bounds__(256, 2) k1_chunked(const K1Args A)
@@ -894,8 +978,9 @@ __global__ void __launch_bounds__(256, 2) k1_chunked(const K1Args A)
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
     const int u = blockIdx.x % A.n_units;
-    dispatch_f<ChunkLanes, kPreciseFcap, false, true>(A, A.units[2 * u], A.units[2 * u + 1], ring, zbuf, bar0,
-                                         bar1);
+    Phases ph;
+    dispatch_f<ChunkLanes, kPreciseFcap, false, true>(A, A.units[2 * u], A.units[2 * u + 1], ring,
+                                                      zbuf, bar0, bar1, ph);
 }
 
 __global__ void __launch_bounds__(256, 2) k1_anchored(const K1Args A)
@@ -905,8 +990,9 @@ __global__ void __launch_bounds__(256, 2) k1_anchored(const K1Args A)
     uint32_t bar0, bar1;
     cta_setup(smem, A, ring, zbuf, bar0, bar1);
     const int u = (int)(blockIdx.x % A.n_units);
+    Phases ph;
     dispatch_f<AnchorLanes, kAnchorFcap, true, true>(A, A.units[2 * u], A.units[2 * u + 1], ring,
-                                                     zbuf, bar0, bar1);
+                                                     zbuf, bar0, bar1, ph);
 }
 
 __global__ void peak_out_kernel(const float *best, const int64_t *idx, int64_t count,
@@ -1049,18 +1135,55 @@ __global__ void bounded_wait_probe(int32_t *err, uint64_t limit_ns)
 
 }  // namespace
 
+// CTAs of `k` resident on the device at once (occupancy x SMs), computed
+// once per (kernel, device, shared-memory size).
+static cudaError_t resident_ctas(const void *k, int threads, int smem_bytes, int *out)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<const void *, int, int, int>, int> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_tuple(k, dev, threads, smem_bytes);
+    auto it = done.find(key);
+    if (it != done.end()) {
+        *out = it->second;
+        return cudaSuccess;
+    }
+    int per_sm = 0, n_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem_bytes)) !=
+            cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    *out = done[key] = std::max(1, per_sm) * std::max(1, n_sm);
+    return cudaSuccess;
+}
+
 template <typename Kernel>
 cudaError_t launch_kernel(Kernel k, const K1Args &a, int64_t n_units, int smem_bytes,
-                          cudaStream_t s)
+                          cudaStream_t s, bool persistent = false)
 {
     cudaError_t e = ensure_smem_limit(reinterpret_cast<const void *>(k), smem_bytes);
     if (e != cudaSuccess) return e;
+    if (persistent && a.queue != nullptr) {
+        int ctas = 0;
+        if ((e = resident_ctas(reinterpret_cast<const void *>(k), a.W * 32, smem_bytes, &ctas)) !=
+            cudaSuccess)
+            return e;
+        if ((e = cudaMemsetAsync(a.queue, 0, sizeof(int32_t), s)) != cudaSuccess) return e;
+        const int64_t grid = std::min<int64_t>(n_units, ctas);
+        k<<<(unsigned)grid, a.W * 32, smem_bytes, s>>>(a);
+        return cudaGetLastError();
+    }
+    K1Args g = a;
+    g.queue = nullptr;   // grid mode: one CTA per unit (and segment)
     const int P = a.n_seg > 0 ? (a.n + a.n_seg - 1) / a.n_seg : 1;
     const int P_launch = a.seg_count > 0 ? a.seg_count
                          : a.seg_end != nullptr ? P - 1   // the projection skips the last
                                                 : P;
     if (P_launch <= 0) return cudaSuccess;
-    k<<<(unsigned)(n_units * P_launch), a.W * 32, smem_bytes, s>>>(a);
+    k<<<(unsigned)(n_units * P_launch), a.W * 32, smem_bytes, s>>>(g);
     return cudaGetLastError();
 }
 
@@ -1070,10 +1193,15 @@ cudaError_t launch_k1_cap(const K1Args &a, int64_t n_units, int smem_bytes, cuda
     // several time segments, or span starts to keep (only the segment-capable
     // kernels carry that code; one segment runs there as well)
     const bool seg = a.n_seg < a.n || a.sub16 != nullptr;
-    if (a.n_lower > 0)
-        return seg ? launch_kernel(k1_plain<FCAP, true, true>, a, n_units, smem_bytes, s)
+    if (a.n_lower > 0) {
+        if (seg) return launch_kernel(k1_plain<FCAP, true, true>, a, n_units, smem_bytes, s);
+        return a.queue != nullptr
+                   ? launch_kernel(k1_persistent<FCAP, true>, a, n_units, smem_bytes, s, true)
                    : launch_kernel(k1_plain<FCAP, false, true>, a, n_units, smem_bytes, s);
-    return seg ? launch_kernel(k1_plain<FCAP, true, false>, a, n_units, smem_bytes, s)
+    }
+    if (seg) return launch_kernel(k1_plain<FCAP, true, false>, a, n_units, smem_bytes, s);
+    return a.queue != nullptr
+               ? launch_kernel(k1_persistent<FCAP, false>, a, n_units, smem_bytes, s, true)
                : launch_kernel(k1_plain<FCAP, false, false>, a, n_units, smem_bytes, s);
 }
 
@@ -1096,6 +1224,21 @@ cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStre
     if (a.fcap <= 8) return launch_k1_cap<8>(a, n_units, smem_bytes, s);
     if (a.fcap <= 10) return launch_k1_cap<10>(a, n_units, smem_bytes, s);
     return cudaErrorInvalidValue;
+}
+
+int k1_plain_regs(int fcap)
+{
+    const void *k = fcap <= 2   ? reinterpret_cast<const void *>(k1_plain<2, false, false>)
+                    : fcap <= 4 ? reinterpret_cast<const void *>(k1_plain<4, false, false>)
+                    : fcap <= 6 ? reinterpret_cast<const void *>(k1_plain<6, false, false>)
+                    : fcap <= 8 ? reinterpret_cast<const void *>(k1_plain<8, false, false>)
+                                : reinterpret_cast<const void *>(k1_plain<10, false, false>);
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+    }
+    return fa.numRegs;
 }
 
 cudaError_t ensure_smem_limit(const void *kernel, int smem_bytes)

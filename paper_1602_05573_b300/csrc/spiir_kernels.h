@@ -82,6 +82,10 @@ struct K1Args {
     // the launched segment, [chunks][D][n_slots]; lanes restart from it at each
     // chunk start (null: not this form)
     const float2 *anchors;
+    // persistent launch of the unsegmented plain kernel: a grid of the
+    // resident CTAs takes units from this counter (zeroed by the launcher
+    // before the launch); null = one CTA per unit
+    int32_t *queue;
 };
 constexpr int kAnchorFcap = 8;   // filters per lane in the anchored kernel
 
@@ -169,6 +173,9 @@ cudaError_t launch_set_coefficients(const float2 *a, const float2 *b,
                                     float4 *params, cudaStream_t s);
 
 cudaError_t launch_k1(const K1Args &a, int64_t n_units, int smem_bytes, cudaStream_t s);
+// Registers per thread of the unsegmented single-band plain kernel that a
+// layout with this filters-per-lane cap launches (0 if unknown).
+int k1_plain_regs(int fcap);
 
 // Raise a kernel's dynamic shared-memory limit once per (kernel, device, size).
 cudaError_t ensure_smem_limit(const void *kernel, int smem_bytes);

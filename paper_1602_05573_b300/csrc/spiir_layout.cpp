@@ -3,7 +3,9 @@
 #include "spiir_layout.h"
 
 #include <algorithm>
+#include <functional>
 #include <numeric>
+#include <queue>
 
 namespace spiir {
 
@@ -205,6 +207,69 @@ void place_half(const std::vector<int64_t> &flA, const std::vector<int64_t> &flB
     *wavefronts = wf;
 }
 
+// First-fit packing of templates (F filters per lane, nw warps each, in
+// the layout's sort order) into CTAs of W warps of one F: the F of every
+// CTA in launch order.
+std::vector<int> pack_groups(const std::vector<int> &F, const std::vector<int> &nw,
+                             const std::vector<int64_t> &order, int W)
+{
+    std::vector<int> gF, used;
+    std::vector<size_t> open;
+    int curF = -1;
+    for (int64_t t : order) {
+        if (F[t] != curF) {
+            open.clear();
+            curF = F[t];
+        }
+        size_t gi = gF.size();
+        for (size_t k = 0; k < open.size(); ++k)
+            if (used[open[k]] + nw[t] <= W) {
+                gi = open[k];
+                break;
+            }
+        if (gi == gF.size()) {
+            gF.push_back(F[t]);
+            used.push_back(0);
+            open.push_back(gi);
+        }
+        used[gi] += nw[t];
+        if (used[gi] == W) open.erase(std::find(open.begin(), open.end(), gi));
+    }
+    return gF;
+}
+
+// Predicted length of one launch (filter-round-samples per lane) whose units
+// -- every CTA group x every detector, largest F first -- are taken in order
+// by `slots` resident CTAs, each unit going to the CTA that frees up first
+// (longest-processing-time-first list scheduling).
+double predict_launch(const std::vector<int> &gF, int D, int64_t slots)
+{
+    std::priority_queue<double, std::vector<double>, std::greater<double>> free_at;
+    for (int64_t i = 0; i < slots; ++i) free_at.push(0.0);
+    double end = 0.0;
+    for (int f : gF)
+        for (int d = 0; d < D; ++d) {
+            const double t = free_at.top() + (double)f + kLaneOverhead;
+            free_at.pop();
+            free_at.push(t);
+            end = std::max(end, t);
+        }
+    return end;
+}
+
+std::vector<int64_t> sort_templates(const std::vector<int> &F, const std::vector<int> &nw,
+                                    const std::vector<std::vector<int64_t>> &filters)
+{
+    std::vector<int64_t> order(F.size());
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
+        if (F[x] != F[y]) return F[x] > F[y];
+        if (nw[x] != nw[y]) return nw[x] > nw[y];
+        return filters[x].size() > filters[y].size();
+    });
+    return order;
+}
+
 }  // namespace
 
 bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const float *a,
@@ -307,14 +372,82 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
                "); use fewer ring_copies, fewer warps per CTA or a shorter block_len";
         return false;
     }
+    // tail split (full-warp templates): the smallest templates, by filter
+    // rounds, get twice their warps (F halves), so the units that end the
+    // launch are short.  Auto: the share of the bank's rounds, in steps of 1%
+    // up to 20%, whose predicted launch (predict_launch on the resident CTAs
+    // the kernel's registers and shared memory allow) is shortest.
+    if (opt.tail >= 0 && L.G == 32) {
+        const int regs = opt.regs > 0 ? opt.regs : 128;
+        const int64_t by_regs = 65536 / ((int64_t)regs * 32 * L.W);
+        const int64_t by_smem = (int64_t)(228 * 1024) / (L.smem_bytes() + 1024);
+        const int64_t slots =
+            std::max<int64_t>(1, std::min<int64_t>(std::min(by_regs, by_smem), 32)) * opt.n_sm;
+        L.slots_model = slots;
+        std::vector<int64_t> small(L.T);
+        std::iota(small.begin(), small.end(), 0);
+        std::vector<int64_t> rounds_of(L.T);
+        int64_t total_rounds = 0;
+        for (int64_t t = 0; t < L.T; ++t) {
+            rounds_of[t] = std::max<int64_t>(1, ((int64_t)filters[t].size() + 31) / 32);
+            total_rounds += rounds_of[t];
+        }
+        std::stable_sort(small.begin(), small.end(), [&](int64_t x, int64_t y) {
+            if (rounds_of[x] != rounds_of[y]) return rounds_of[x] < rounds_of[y];
+            return filters[x].size() < filters[y].size();
+        });
+        auto split_first = [&](int64_t k, std::vector<int> &F2, std::vector<int> &nw2) {
+            F2 = F;
+            nw2 = nw;
+            for (int64_t i = 0; i < k; ++i) {
+                const int64_t t = small[i];
+                nw2[t] = 2 * nw[t];
+                F2[t] = (int)((rounds_of[t] + nw2[t] - 1) / nw2[t]);
+            }
+        };
+        // templates that can take twice their warps (each warp keeps >= 1 round)
+        auto splittable = [&](int64_t t) {
+            return 2 * nw[t] <= L.W && rounds_of[t] >= 2 * nw[t];
+        };
+        std::vector<int64_t> cands;   // split counts to compare
+        if (opt.tail > 0) {
+            int64_t k = 0, acc = 0;
+            while (k < L.T && splittable(small[k]) &&
+                   1000 * (acc + rounds_of[small[k]]) <= (int64_t)opt.tail * total_rounds)
+                acc += rounds_of[small[k++]];
+            cands.push_back(k);
+        } else {
+            int64_t k = 0, acc = 0;
+            for (int pct = 0; pct <= 20; ++pct) {
+                while (k < L.T && splittable(small[k]) &&
+                       100 * (acc + rounds_of[small[k]]) <= (int64_t)pct * total_rounds)
+                    acc += rounds_of[small[k++]];
+                if (cands.empty() || cands.back() != k) cands.push_back(k);
+            }
+        }
+        int64_t best_k = 0;
+        double best = 0.0;
+        for (int64_t k : cands) {
+            std::vector<int> F2, nw2;
+            split_first(k, F2, nw2);
+            const double len =
+                predict_launch(pack_groups(F2, nw2, sort_templates(F2, nw2, filters), L.W), D,
+                               slots);
+            if (k == cands.front() || len < best) {
+                best = len;
+                best_k = k;
+            }
+        }
+        if (best_k > 0) {
+            std::vector<int> F2, nw2;
+            split_first(best_k, F2, nw2);
+            F.swap(F2);
+            nw.swap(nw2);
+        }
+        L.tail_templates = best_k;
+    }
     // sort templates: F descending, warps descending, filter count descending
-    std::vector<int64_t> order(L.T);
-    std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
-        if (F[x] != F[y]) return F[x] > F[y];
-        if (nw[x] != nw[y]) return nw[x] > nw[y];
-        return filters[x].size() > filters[y].size();
-    });
+    std::vector<int64_t> order = sort_templates(F, nw, filters);
     // first-fit packing of each template's warps into CTAs of the same F
     struct Group {
         int F;

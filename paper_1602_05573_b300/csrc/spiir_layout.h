@@ -41,7 +41,19 @@ struct LayoutOptions {
     int Tb = 512;       // samples per staged strain block (multiple of 32)
     int C = 0;          // ring copies (1, 2, 4); 0 = default (1)
     int n_sm = 148;     // used to pick W when W == 0
+    // tail split: the smallest templates run on twice their warps, so the
+    // last units of a launch are short.  -1 = off, 0 = auto (the split with
+    // the shortest predicted launch, see predict_launch), k > 0 = the
+    // smallest templates holding k per mille of the bank's filter rounds
+    int tail = -1;
+    int regs = 0;       // registers per thread of the filter kernel (0: 128)
 };
+
+// Filter-round-samples of per-warp work that one step costs beyond its
+// filters' recurrences (the lane's filter sum, the cross-lane
+// transpose-reduce, the strain address updates), in units of one filter's
+// recurrence: a unit of F filters per lane costs about F + this per sample.
+constexpr double kLaneOverhead = 1.75;
 
 // One bank (or one band of a multirate bank) as the kernels see it.
 struct Layout {
@@ -70,6 +82,8 @@ struct Layout {
     std::vector<int64_t> slot_template; // [n_slots]
     std::vector<int32_t> units;         // [n_units][2] (group, detector)
     double conflict_ratio = 1.0;        // mean wavefronts per round of strain loads
+    int64_t tail_templates = 0;         // templates the tail split gave twice their warps
+    int64_t slots_model = 0;            // resident CTAs the split's launch model assumed
 
     int64_t n_groups() const { return (int64_t)group_F.size(); }
     int64_t n_units() const { return (int64_t)units.size() / 2; }

@@ -1,12 +1,13 @@
-"""Batched-launch features: CUDA-graph replay of a streaming call and the
-autotuner.  Both must leave the results identical to ordinary calls / the
-oracle."""
+"""Batched-launch features: CUDA-graph replay of a streaming call, the
+persistent launch (resident CTAs taking units from a counter), the tail
+split of the layout and the autotuner.  Each must agree with the FP64
+oracle (and the graph replay with ordinary calls bit for bit)."""
 import numpy as np
 import pytest
 
 import oracle
 from parity_util import REL_TOL, check_peaks, rel_errors
-from spiir_inputs import make_bank, make_strain
+from spiir_inputs import make_bank, make_strain, workload_bank, workload_strain
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -34,13 +35,69 @@ def test_graph_replay_continues_the_stream(sp):
     g, z, pa, pi = plan.capture(xbuf)
     plan.reset()
     torch.cuda.synchronize()
+    zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
     for i in range(nb):
         xbuf.copy_(torch.from_numpy(x[:, i * blk:(i + 1) * blk].copy()))
         g.replay()
-        assert np.array_equal(z.cpu().numpy(), zs[i])
+        zi = z.cpu().numpy()
+        assert np.array_equal(zi, zs[i])
+        # against the oracle's stream, not only against the ordinary calls
+        rel, _ = rel_errors(zi, zref[..., i * blk:(i + 1) * blk])
+        assert rel.max() <= REL_TOL, (i, rel.max())
     assert torch.equal(pa, pa_ref) and torch.equal(pi, pi_ref)
+    check_peaks(np.concatenate(zs, axis=-1), zref, pa.cpu().numpy(), pi.cpu().numpy())
     _, _, t = plan.state_get()
     assert t == blk * nb
+
+
+@pytest.mark.parametrize("persistent,tail", [("on", 0), ("on", -1), ("off", 100)])
+def test_persistent_launch_and_tail_split_match_oracle(sp, persistent, tail):
+    """A bank of more units than resident CTAs, so persistent CTAs take
+    several units each (their block barriers' phases carry over between
+    units); the tail split gives the smallest templates two warps."""
+    bank = make_bank(2400, (20, 300), (0.99, 0.9995), 600, seed=154, n_det=2)
+    x = make_strain(2, 1500, seed=155)
+    plan = sp.Plan(bank, persistent=persistent, tail_split=tail)
+    info = plan.info()
+    assert info["n_units"] > 592
+    assert info["persistent"] == (1 if persistent == "on" else 0)
+    if tail != 0:
+        assert info["tail_templates"] > 0
+    z = plan.filter(torch.from_numpy(x).cuda()).cpu().numpy()
+    pa, pi = plan.peak()
+    plan.check()
+    zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
+    rel, _ = rel_errors(z, zref)
+    assert rel.max() <= REL_TOL, rel.max()
+    check_peaks(z, zref, pa.cpu().numpy(), pi.cpu().numpy())
+
+
+def test_batched_workload_persistent_graph_sampled(sp):
+    """The full batched workload (4096 templates, 3 detectors, 65536 samples)
+    as one persistent launch captured in a CUDA graph, autotuned layout:
+    twelve sampled (detector, template) series of a replay from zero state
+    against the oracle on the matching sub-bank."""
+    bank = workload_bank("batched")
+    x = workload_strain("batched")
+    plan = sp.Plan(bank, persistent="on", autotune=True)
+    xt = torch.from_numpy(x).cuda()
+    g, z, pa, pi = plan.capture(xt)            # the warm-up call runs the autotuner
+    assert plan.info()["persistent"] == 1
+    plan.reset()
+    torch.cuda.synchronize()
+    g.replay()
+    plan.check()
+    rng = np.random.default_rng(156)
+    for det, t in [(int(rng.integers(0, 3)), int(t)) for t in rng.choice(4096, 12, replace=False)]:
+        sub = bank.subset([t])
+        zref, _, _ = oracle.filter_bank(sub.off, sub.a, sub.b, sub.d, x[det:det + 1])
+        zg = z[det, t].cpu().numpy()[None, None]
+        rel, _ = rel_errors(zg, zref)
+        assert rel.max() <= REL_TOL, (det, t, rel.max())
+        check_peaks(zg, zref, pa[det, t].cpu().numpy()[None, None],
+                    pi[det, t].cpu().numpy()[None, None])
+    del g, z
+    torch.cuda.empty_cache()
 
 
 def test_autotune_picks_a_layout_and_stays_exact(sp):
