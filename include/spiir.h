@@ -429,8 +429,10 @@ spiir_status spiir_selftest_bounded_wait(spiir_plan *plan, uint64_t limit_ns, vo
  *   z_dev         [n_detectors][n_templates][n] complex64 output, or NULL
  *   peak_abs_dev  [n_detectors][n_templates] float32 max |z|
  *   peak_idx_dev  [n_detectors][n_templates] int64 first index of the max
- *                 (-1 would mean that template was not filtered because a
- *                 bounded device wait gave up)
+ * The call does not wait for its device work, so it cannot return
+ * SPIIR_ETIMEOUT (spiir_check needs a plan): if a bounded device wait of the
+ * call gave up, every peak_abs is NaN and every peak_idx -1, and z is
+ * undefined.  A caller checks its peaks after synchronizing the stream.
  * Runs on the caller's current device and `stream`.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress); make
  * that first call before any stream capture.  Every call reuses the same

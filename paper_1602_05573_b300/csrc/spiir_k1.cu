@@ -1005,6 +1005,24 @@ __global__ void peak_out_kernel(const float *best, const int64_t *idx, int64_t c
     out_idx[i] = idx[i];
 }
 
+// The same, for a call whose error word may be set: if a bounded wait of
+// the call gave up, every entry reads (NaN, -1), so the caller sees the
+// failure in its outputs without a status read-back.
+__global__ void peak_out_checked_kernel(const float *best, const int64_t *idx, int64_t count,
+                                        const int32_t *err, float *out_abs, int64_t *out_idx)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    if (*err != 0) {
+        out_abs[i] = __int_as_float(0x7fc00000);
+        out_idx[i] = -1;
+        return;
+    }
+    const float b = best[i];
+    out_abs[i] = b < 0.f ? 0.f : sqrtf(b);
+    out_idx[i] = idx[i];
+}
+
 __global__ void segment_carry_kernel(const float4 *params, const float2 *state,
                                      const float2 *seg_end, float2 *seg_init, int64_t n_slots,
                                      int D, int P, int n_seg)
@@ -1265,6 +1283,16 @@ cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count
     if (count <= 0) return cudaSuccess;
     peak_out_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(best, idx, count, out_abs,
                                                                     out_idx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_peak_out_checked(const float *best, const int64_t *idx, int64_t count,
+                                   const int32_t *err, float *out_abs, int64_t *out_idx,
+                                   cudaStream_t s)
+{
+    if (count <= 0) return cudaSuccess;
+    peak_out_checked_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(best, idx, count, err,
+                                                                            out_abs, out_idx);
     return cudaGetLastError();
 }
 

@@ -231,6 +231,12 @@ cudaError_t launch_tc_project(const TcArgs &a, cudaStream_t s);
 cudaError_t launch_peak_out(const float *best, const int64_t *idx, int64_t count,
                             float *out_abs, int64_t *out_idx, cudaStream_t s);
 
+// The same, except that every entry reads (NaN, -1) when *err is nonzero (a
+// bounded wait of the call gave up).
+cudaError_t launch_peak_out_checked(const float *best, const int64_t *idx, int64_t count,
+                                   const int32_t *err, float *out_abs, int64_t *out_idx,
+                                   cudaStream_t s);
+
 // Segment start states: for every (detector, slot), s_0 = state,
 // s_{p+1} = a^n_seg s_p + seg_end[p] (FP64), seg_init[p] = s_p, p < P.
 cudaError_t launch_segment_carry(const float4 *params, const float2 *state,

@@ -384,18 +384,22 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
         const int64_t slots =
             std::max<int64_t>(1, std::min<int64_t>(std::min(by_regs, by_smem), 32)) * opt.n_sm;
         L.slots_model = slots;
-        std::vector<int64_t> small(L.T);
-        std::iota(small.begin(), small.end(), 0);
         std::vector<int64_t> rounds_of(L.T);
         int64_t total_rounds = 0;
         for (int64_t t = 0; t < L.T; ++t) {
             rounds_of[t] = std::max<int64_t>(1, ((int64_t)filters[t].size() + 31) / 32);
             total_rounds += rounds_of[t];
         }
+        // templates that can take twice their warps (each warp keeps >= 1
+        // round), smallest first
+        std::vector<int64_t> small;
+        for (int64_t t = 0; t < L.T; ++t)
+            if (2 * nw[t] <= L.W && rounds_of[t] >= 2 * nw[t]) small.push_back(t);
         std::stable_sort(small.begin(), small.end(), [&](int64_t x, int64_t y) {
             if (rounds_of[x] != rounds_of[y]) return rounds_of[x] < rounds_of[y];
             return filters[x].size() < filters[y].size();
         });
+        const int64_t n_small = (int64_t)small.size();
         auto split_first = [&](int64_t k, std::vector<int> &F2, std::vector<int> &nw2) {
             F2 = F;
             nw2 = nw;
@@ -405,21 +409,17 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
                 F2[t] = (int)((rounds_of[t] + nw2[t] - 1) / nw2[t]);
             }
         };
-        // templates that can take twice their warps (each warp keeps >= 1 round)
-        auto splittable = [&](int64_t t) {
-            return 2 * nw[t] <= L.W && rounds_of[t] >= 2 * nw[t];
-        };
         std::vector<int64_t> cands;   // split counts to compare
         if (opt.tail > 0) {
             int64_t k = 0, acc = 0;
-            while (k < L.T && splittable(small[k]) &&
+            while (k < n_small &&
                    1000 * (acc + rounds_of[small[k]]) <= (int64_t)opt.tail * total_rounds)
                 acc += rounds_of[small[k++]];
             cands.push_back(k);
         } else {
             int64_t k = 0, acc = 0;
             for (int pct = 0; pct <= 20; ++pct) {
-                while (k < L.T && splittable(small[k]) &&
+                while (k < n_small &&
                        100 * (acc + rounds_of[small[k]]) <= (int64_t)pct * total_rounds)
                     acc += rounds_of[small[k++]];
                 if (cands.empty() || cands.back() != k) cands.push_back(k);

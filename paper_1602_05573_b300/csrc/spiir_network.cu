@@ -404,6 +404,9 @@ static cudaError_t launch_network_r(NetArgs a, int smem, cudaStream_t s)
             }
         }
     }
+    // grid sizes: a.T * C CTAs (the chunk search keeps it <= INT32_MAX) and,
+    // for C == 1, a.T itself, which must then fit a grid dimension as well
+    if (a.T > INT32_MAX || a.T * C > INT32_MAX) return cudaErrorInvalidConfiguration;
     a.n_chunks = (int32_t)C;
     a.chunk_tiles = (int32_t)ct;
     if (C > 1 && (e = cudaMemsetAsync(a.t, 0, (size_t)a.T * sizeof(int64_t), s)) != cudaSuccess)

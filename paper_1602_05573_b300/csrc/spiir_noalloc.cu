@@ -206,8 +206,10 @@ extern "C" spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const 
     a.wait_limit_ns = kWaitLimitNs;
     if ((e = spiir::launch_k1(a, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
         return cuda_fail(e, "spiir_filter_noalloc kernel launch");
-    if ((e = spiir::launch_peak_out(best, bidx, (int64_t)D * T, peak_abs_dev, peak_idx_dev, s)) !=
-        cudaSuccess)
+    // the error word is in the scratch and the call never waits for its
+    // work, so a bounded wait that gave up shows in the peaks: all (NaN, -1)
+    if ((e = spiir::launch_peak_out_checked(best, bidx, (int64_t)D * T, errw, peak_abs_dev,
+                                            peak_idx_dev, s)) != cudaSuccess)
         return cuda_fail(e, "spiir_filter_noalloc peak launch");
     return SPIIR_OK;
 }

@@ -94,8 +94,11 @@ class BankFit:
     def loss(self, z):                           # per template sum |z - t|^2, [T]
         return self.torch.sum(self.torch.abs(z - self.t) ** 2, dim=-1)[0]
 
-    def fit_gains(self, b, iters: int = 400, tol: float = 1e-7):
-        """Conjugate gradients on A^H A b = A^H t from b (per template)."""
+    def fit_gains(self, b, iters: int = 400, tol: float = 1e-7, check_every: int = 8):
+        """Conjugate gradients on A^H A b = A^H t from b (per template).  A
+        template whose residual has dropped by tol stops moving (its step is
+        zeroed on the device); the host reads the convergence flags only every
+        check_every iterations, so the iterations queue without a sync."""
         torch = self.torch
 
         def dot(u, v):
@@ -105,17 +108,20 @@ class BankFit:
         p = r.clone()
         rs = dot(r, r)
         rs0 = torch.clamp(rs.clone(), min=1e-30)
+        active = rs > (tol * tol) * rs0
         it = 0
         for it in range(1, iters + 1):
             Mp = AH(self.A(p))
-            alpha = rs / torch.clamp(dot(p, Mp), min=1e-30)
+            alpha = torch.where(active, rs / torch.clamp(dot(p, Mp), min=1e-30),
+                                torch.zeros_like(rs))
             b = b + alpha * p
             r = r - alpha * Mp
             rs_new = dot(r, r)
-            if bool(torch.all(rs_new <= (tol * tol) * rs0)):
+            active = active & (rs_new > (tol * tol) * rs0)
+            if it % check_every == 0 and not bool(torch.any(active)):
                 break
-            p = r + (rs_new / torch.clamp(rs, min=1e-30)) * p
-            rs = rs_new
+            p = torch.where(active, r + (rs_new / torch.clamp(rs, min=1e-30)) * p, p)
+            rs = torch.where(active, rs_new, rs)
         return b, it
 
 

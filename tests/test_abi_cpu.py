@@ -117,14 +117,16 @@ def test_host_only_plan_refuses_compute():
     assert lib.spiir_reset(p.handle, None) == sp.EINVAL
 
 
-@pytest.mark.parametrize("counts,W,C,Fcap", [
-    ([1, 31, 32, 33, 64, 65, 100, 320], 0, 4, 0),
-    ([5] * 37, 4, 2, 1),
-    ([0, 3, 200, 17], 2, 1, 4),
-    ([1000, 129, 7, 640], 8, 4, 4),
-    ([300, 257, 100], 0, 2, 10),
+@pytest.mark.parametrize("counts,W,C,Fcap,tail", [
+    ([1, 31, 32, 33, 64, 65, 100, 320], 0, 4, 0, 0),
+    ([5] * 37, 4, 2, 1, 0),
+    ([0, 3, 200, 17], 2, 1, 4, 0),
+    ([1000, 129, 7, 640], 8, 4, 4, 0),
+    ([300, 257, 100], 0, 2, 10, 0),
+    ([300, 257, 100, 70, 130, 64], 4, 1, 10, 200),
+    ([1, 31, 32, 33, 64, 65, 100, 320] * 5, 0, 1, 0, -1),
 ])
-def test_slot_layout_covers_every_filter_once(counts, W, C, Fcap):
+def test_slot_layout_covers_every_filter_once(counts, W, C, Fcap, tail):
     rng = np.random.default_rng(3)
     off = np.zeros(len(counts) + 1, np.int64)
     off[1:] = np.cumsum(counts)
@@ -133,8 +135,10 @@ def test_slot_layout_covers_every_filter_once(counts, W, C, Fcap):
     b = (rng.standard_normal(L) + 1j * rng.standard_normal(L)).astype(np.complex64)
     d = rng.integers(0, 700, L).astype(np.int32)
     p = sp.Plan(Bank(off, a, b, d, 2), device=-1, warps_per_cta=W, ring_copies=C,
-                max_filters_per_lane=Fcap)
+                max_filters_per_lane=Fcap, tail_split=tail)
     sf, st = p.slots()
+    if tail > 0:    # the smallest splittable templates took twice their warps
+        assert p.info()["tail_templates"] > 0
     real = sf[sf >= 0]
     assert np.array_equal(np.sort(real), np.arange(L))
     # every real slot serves the template that owns the filter
@@ -254,3 +258,16 @@ def test_chi2_split_rejects_bad_arguments():
     desc, keep = sp.bank_desc(bank)
     lib = sp.library()
     assert lib.spiir_chi2_split(ctypes.byref(desc), 2, None, None, None, None, None) == sp.EINVAL
+
+
+def test_tail_split_halves_the_smallest_templates_filters_per_lane():
+    """Forced tail split on the batched bank: the split templates (100..128
+    filters, 4 rounds) run on two warps of 2 filters per lane; the slot
+    count stays the same (no new padding rounds for even round counts) and
+    the unit count grows."""
+    bank = workload_bank("batched")
+    base = sp.Plan(bank, device=-1).info()
+    split = sp.Plan(bank, device=-1, tail_split=30).info()
+    assert split["tail_templates"] > 0
+    assert split["n_units"] > base["n_units"]
+    assert split["n_slots"] == base["n_slots"]

@@ -50,7 +50,7 @@ def test_graph_replay_continues_the_stream(sp):
     assert t == blk * nb
 
 
-@pytest.mark.parametrize("persistent,tail", [("on", 0), ("on", -1), ("off", 100)])
+@pytest.mark.parametrize("persistent,tail", [("on", 0), ("on", 100), ("off", 100), ("on", -1)])
 def test_persistent_launch_and_tail_split_match_oracle(sp, persistent, tail):
     """A bank of more units than resident CTAs, so persistent CTAs take
     several units each (their block barriers' phases carry over between
@@ -61,7 +61,7 @@ def test_persistent_launch_and_tail_split_match_oracle(sp, persistent, tail):
     info = plan.info()
     assert info["n_units"] > 592
     assert info["persistent"] == (1 if persistent == "on" else 0)
-    if tail != 0:
+    if tail > 0:
         assert info["tail_templates"] > 0
     z = plan.filter(torch.from_numpy(x).cuda()).cpu().numpy()
     pa, pi = plan.peak()

@@ -125,18 +125,43 @@ def test_injection_recovered(sp):
     assert rel.max() <= REL_TOL
 
 
+def noise_rms_all(sp, bank, lh=1 << 18):
+    """Noise rms per quadrature of every template, sqrt(1/2 sum |h|^2), from
+    its top-rate response to an impulse at the stream start (the library's;
+    lh samples hold its energy to ~1e-7 for the slowest band's poles)."""
+    plan = sp.Plan(bank)
+    delta = torch.zeros((1, lh), dtype=torch.float32, device="cuda")
+    delta[0, 0] = 1.0
+    h = plan.filter(delta)
+    sig = torch.sqrt(0.5 * (h[0].abs() ** 2).double().sum(dim=-1)).cpu().numpy()
+    plan.close()
+    del h
+    torch.cuda.empty_cache()
+    return sig
+
+
 def test_multirate_workload_full_size(sp):
     """The full injection+multirate workload (2048 templates x 3 bands,
-    2^20 samples at 4096 Hz) without storing z: the injected template's peak
-    is at the injection time, and 6 sampled templates match the oracle."""
+    2^20 samples at 4096 Hz) without storing z: the injected template has
+    the largest normalised peak (peak |z| / its noise rms) of all 2048 and
+    peaks at the injection time, and 6 sampled templates match the oracle."""
     bank = workload_bank("multirate")
     n, tau, k0 = 1 << 20, 1234, 700_016
     x, sigma = injected_strain(bank, tau, k0, n)
     _, pa, pi = gpu_mr(sp, bank, x, emit_z=False)
     assert abs(int(pi[0, tau]) - k0) <= 16
     assert 10.0 < pa[0, tau] / sigma < 14.0
+    sig_all = noise_rms_all(sp, bank)
+    rho = pa[0] / sig_all
+    assert int(np.argmax(rho)) == tau, (int(np.argmax(rho)), rho[tau], np.sort(rho)[-2])
     rng = np.random.default_rng(331)
     picks = sorted(set([tau] + [int(t) for t in rng.choice(2048, 5, replace=False)]))
+    # the library's noise rms of the sampled templates against the oracle's
+    delta = np.zeros((1, 1 << 18))
+    delta[0, 0] = 1.0
+    href, _, _ = oracle_mr(bank.subset(picks), delta)
+    sig_ref = np.sqrt(0.5 * np.sum(np.abs(href[0]) ** 2, axis=-1))
+    np.testing.assert_allclose(sig_all[picks], sig_ref, rtol=1e-4)
     sub = bank.subset(picks)
     zsub, pas, pis = gpu_mr(sp, sub, x)
     zref, _, _ = oracle_mr(sub, x)

@@ -1,22 +1,23 @@
-"""spiir_filter_noalloc against spiir_filter (GPU).
+"""spiir_filter_noalloc against spiir_filter and against the FP64 oracle (GPU).
 
 spiir_filter_noalloc is for callers that cannot call cudaMalloc/cudaFree --
 for instance when device memory belongs to another allocator or a fixed
 budget, or when a streaming pipeline must not allocate.  It keeps its scratch
 in a static device array inside the library.  These tests call it through the
 C-ABI twice in a row, on different strain, and check each result against a
-fresh plan's spiir_filter/spiir_peak output with the tolerance the parity
-tests use; the second call also shows that nothing of the first call (state,
-strain history, peaks) leaks through the shared array.  This file is named
-so that pytest collects it last.
+fresh plan's spiir_filter/spiir_peak output and against the oracle, with the
+tolerance the parity tests use; the second call also shows that nothing of
+the first call (state, strain history, peaks) leaks through the shared
+array.  This file is named so that pytest collects it last.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
-from parity_util import REL_TOL, rel_errors
-from spiir_inputs import make_bank, make_strain
+import oracle
+from parity_util import REL_TOL, check_peaks, rel_errors
+from spiir_inputs import Bank, make_bank, make_strain
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -73,3 +74,19 @@ def test_noalloc_rejects_problems_beyond_its_scratch(sp):
                                   x.data_ptr(), x.data_ptr(), None)
     assert rc == sp.EINVAL
     assert b"scratch" in lib.spiir_last_error_detail()
+
+
+def test_noalloc_matches_oracle_on_two_calls_in_a_row(sp):
+    """One detector; templates of 1, 31, 33 (two rounds of a warp), 200 and
+    400 filters (400 > 32 x 10: two warps of one CTA at the default cap)."""
+    parts = [make_bank(1, L, (0.99, 0.9995), 900, seed=85 + L) for L in (1, 31, 33, 200, 400)]
+    off = np.concatenate([[0], np.cumsum([p.n_filters for p in parts])]).astype(np.int64)
+    bank = Bank(off, np.concatenate([p.a for p in parts]), np.concatenate([p.b for p in parts]),
+                np.concatenate([p.d for p in parts]), 1)
+    for seed, n in [(86, 3333), (87, 1025)]:
+        xh = make_strain(1, n, seed=seed)
+        z, pa, pi = noalloc_result(sp, bank, torch.from_numpy(xh).cuda())
+        zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, xh)
+        rel, _ = rel_errors(z, zref)
+        assert rel.max() <= REL_TOL, rel.max()
+        check_peaks(z, zref, pa, pi)
