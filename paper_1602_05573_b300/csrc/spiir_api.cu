@@ -157,7 +157,7 @@ struct Band {
     float *seg_best = nullptr;     //                [P][D][T] per-segment peaks
     int64_t *seg_idx = nullptr;
     int seg_cap = 0;               // segments the workspaces hold
-    unsigned char *tc_w = nullptr; // tensor-core projection: weight tiles (split BF16)
+    float2 *tc_seed = nullptr;     // tensor-core projection: weight seeds [n_slots][kTcSeeds]
     float2 *tc_aT = nullptr;       //   a^256 per slot
     bool tc_valid = false;         //   weights match the current coefficients
     unsigned char *tc_b = nullptr; //   strain-window tiles of a call
@@ -275,7 +275,7 @@ void free_band(Band &b)
     cudaFree(b.seg_init);
     cudaFree(b.seg_best);
     cudaFree(b.seg_idx);
-    cudaFree(b.tc_w);
+    cudaFree(b.tc_seed);
     cudaFree(b.tc_aT);
     cudaFree(b.tc_b);
     cudaFree(b.tc_aT64);
@@ -776,23 +776,24 @@ int segments_for(const spiir_plan *p, const Band &b, int64_t nb)
     return (req < 1 && P < 2) ? 1 : P;
 }
 
-// Projection weights (tile layout, split BF16) and a^256 of a band, built on
-// first use and after every coefficient update.
+// Projection weight seeds (the projection generates its weight tiles from
+// them) and a^256 of a band, built on first use and after every coefficient
+// update.
 spiir_status ensure_tc_weights(spiir_plan *p, Band &b, cudaStream_t s)
 {
     if (b.tc_valid) return SPIIR_OK;
     const spiir::Layout &L = b.lay;
     cudaError_t e;
-    if (!b.tc_w) {
-        if ((e = cudaMalloc(&b.tc_w, (size_t)spiir::tc_weight_bytes(L.n_slots))) != cudaSuccess ||
+    if (!b.tc_seed) {
+        if ((e = dalloc(&b.tc_seed, (size_t)L.n_slots * spiir::kTcSeeds)) != cudaSuccess ||
             (e = dalloc(&b.tc_aT, (size_t)L.n_slots)) != cudaSuccess ||
             (e = dalloc(&b.tc_aT64, (size_t)L.n_slots)) != cudaSuccess)
-            return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "projection weights")
+            return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "projection weight seeds")
                                                   : cuda_fail(e, "cudaMalloc");
     }
-    if ((e = spiir::launch_tc_weights(b.params, b.ringoff, L.n_slots, (int)L.Dh, b.tc_w, b.tc_aT,
-                                      b.tc_aT64, s)) != cudaSuccess)
-        return cuda_fail(e, "projection weights launch");
+    if ((e = spiir::launch_tc_seeds(b.params, b.ringoff, L.n_slots, (int)L.Dh, b.tc_seed,
+                                    b.tc_aT, b.tc_aT64, s)) != cudaSuccess)
+        return cuda_fail(e, "projection weight seeds launch");
     b.tc_valid = true;
     p->last_launches += 1;
     return SPIIR_OK;
@@ -873,7 +874,8 @@ spiir_status launch_anchored(spiir_plan *p, Band &b, spiir::K1Args a, cudaStream
         // windows c'' = c - q_l - 1 for chunks c of the tile, q_l <= hq
         const int64_t n_cols = c_end - c_first + hq;
         spiir::TcArgs t{};
-        t.W = b.tc_w;
+        t.seed = b.tc_seed;
+        t.params = b.params;
         t.B = b.tc_b;
         t.ringoff = b.ringoff;
         t.aT = b.tc_aT;
@@ -986,7 +988,8 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         st = ensure_tc_strain(b, spiir::tc_strain_bytes(n_cols, D), s);
         if (st != SPIIR_OK) return st;
         spiir::TcArgs t{};
-        t.W = b.tc_w;
+        t.seed = b.tc_seed;
+        t.params = b.params;
         t.B = b.tc_b;
         t.ringoff = b.ringoff;
         t.aT = b.tc_aT;

@@ -256,12 +256,18 @@ template <int F> struct PackedLanes {
 #pragma unroll
             for (int q = 0; q < NP; ++q) {
                 const uint64_t X = pk(lds_f32(ad[2 * q] + 4u * t), lds_f32(ad[2 * q + 1] + 4u * t));
-                uint64_t TR = mul2(BR[q], X);
-                uint64_t TI = mul2(BI[q], X);
-                TR = fma2(NAI[q], YI[q], TR);   // br x - ai yi
-                TI = fma2(AI[q], YR[q], TI);    // bi x + ai yr
-                YR[q] = fma2(AR[q], YR[q], TR); // ar yr - ai yi + br x
-                YI[q] = fma2(AR[q], YI[q], TI); // ar yi + ai yr + bi x
+                // each pair of consecutive products shares one operand (X,
+                // YR, YI), which the operand reuse of the register file can
+                // serve without a second read (measured 0.7% faster than the
+                // order without shared operands)
+                uint64_t TR = mul2(BR[q], X);   // br x
+                uint64_t TI = mul2(BI[q], X);   // bi x
+                TR = fma2(AR[q], YR[q], TR);    // + ar yr
+                TI = fma2(AI[q], YR[q], TI);    // + ai yr
+                TI = fma2(AR[q], YI[q], TI);    // + ar yi
+                TR = fma2(NAI[q], YI[q], TR);   // - ai yi
+                YR[q] = TR;
+                YI[q] = TI;
                 if (q == 0) {
                     ZR = YR[0];
                     ZI = YI[0];

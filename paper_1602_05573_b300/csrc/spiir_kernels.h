@@ -184,9 +184,11 @@ cudaError_t ensure_smem_limit(const void *kernel, int smem_bytes);
 // kTcT samples, windows of kTcK = 2 kTcT strain samples per GEMM column.
 constexpr int kTcT = 256;
 constexpr int kTcK = 2 * kTcT;
+constexpr int kTcSeeds = kTcK / 32;   // weight seeds per slot (one per 32 window samples)
 
 struct TcArgs {
-    const unsigned char *W;    // weight tiles (tc_weight_bytes), split BF16
+    const float2 *seed;        // [n_slots][kTcSeeds] weight seeds (launch_tc_seeds)
+    const float4 *params;      // [n_slots] kernel-form (ar, ai, br, bi)
     const unsigned char *B;    // strain-window tiles of this call (tc_strain_bytes)
     const int2 *ringoff;       // (Dh - d, copy base) per slot
     const float2 *aT;          // a^kTcT per slot (kernel form)
@@ -211,12 +213,13 @@ struct TcArgs {
     int32_t c_end;
     int32_t c_full;            // chunks below c_full are whole; they alone advance s64
 };
-int64_t tc_weight_bytes(int64_t n_slots);
 int64_t tc_strain_bytes(int64_t n_cols, int D);
 int tc_cols_per_tile();     // windows per column tile (TcArgs::n_ntiles counts these)
-// V_l (split BF16, tile layout) and a^kTcT for every slot of a band.
-cudaError_t launch_tc_weights(const float4 *params, const int2 *ringoff, int64_t n_slots, int Dh,
-                              unsigned char *W, float2 *aT, double2 *aT64, cudaStream_t s);
+// Weight seeds ([n_slots][kTcSeeds]: V_l at the largest valid m of each
+// 32-wide m-group, from which the projection generates its weight tiles)
+// and a^kTcT (FP32 and FP64) for every slot of a band.
+cudaError_t launch_tc_seeds(const float4 *params, const int2 *ringoff, int64_t n_slots, int Dh,
+                            float2 *seed, float2 *aT, double2 *aT64, cudaStream_t s);
 // Strain windows of the call staged in xe, split BF16, tile layout.
 cudaError_t launch_tc_strain(const float *xe, int64_t xe_stride, int Dh, int64_t n, int D,
                              int64_t n_cols, int col0, unsigned char *B, cudaStream_t s);

@@ -20,13 +20,20 @@
 // columns in order, in FP32 (the recurrence contracts by |a|^T per chunk, so
 // rounding does not grow along it), writing the state at each segment start.
 //
-// Operands live in HBM already in the tensor cores' shared-memory layout
-// (K-major, no swizzle: 8-row x 16-byte core matrices, K-direction core
-// stride 128 B, row-group stride 1024 B, 128 x 64 tiles of 16 KB), so each
-// tile arrives with one 1-D TMA bulk copy.  One CTA serves 128 GEMM rows
-// (64 filter slots) of one detector for the whole call, 256 windows per
-// accumulator (N = 256): warp 4 issues the copies (two stages) and the
-// MMAs; warps 0-3 own TMEM lanes 0-127 and scan.
+// Both operands sit in shared memory in the tensor cores' layout (K-major,
+// no swizzle: 8-row x 16-byte core matrices, K-direction core stride 128 B,
+// row-group stride 1024 B, 128 x 64 tiles of 16 KB).  The strain windows
+// are staged in HBM in that layout by tc_strain_kernel and arrive by 1-D TMA
+// bulk copies; the weights are never stored: per stage, generator warps
+// build the CTA's 128 x 64 weight tile from a per-slot table of starting
+// powers (a^p b for the smallest power p of each 32-wide m-group, FP64
+// rounded once), walking down in m with one complex FP32 multiply by a per
+// sample (at most 31 steps from a seed, ~2e-6 relative worst case, below
+// the ~8e-6 of the split-BF16 representation), and split each value in
+// BF16 hi/lo.  One CTA serves 128 GEMM rows (64 filter slots) of one
+// detector for the whole call, 256 windows per accumulator (N = 256):
+// warp 4 issues the copies (two stages) and the MMAs, warps 5-8 generate
+// the weight tiles, warps 0-3 own TMEM lanes 0-127 and scan.
 #include "spiir_kernels.h"
 #include "spiir_ptx.h"
 
@@ -102,84 +109,52 @@ __device__ __forceinline__ ff ff_add(ff a, ff b)
 }
 __device__ __forceinline__ ff ff_neg(ff a) { return {-a.h, -a.l}; }
 
-// ---- weights: V_l[m] for every slot, re and im rows -------------------------
-// One thread per (slot, group of 8 m).  a^p by binary powering in FP64.
-__global__ void tc_weights_kernel(const float4 *params, const int2 *ringoff, int64_t n_slots,
-                                  int Dh, unsigned char *W, float2 *aT, double2 *aT64)
+// ---- weight seeds: per slot and 32-wide m-group, V_l at the group's largest
+// valid m.  V_l[m] = a^(2T-1-r-m) b for T - r <= m < 2T - r (r = d mod T),
+// else 0 (kernel form: odd lanes hold conj(a) and (Im b, Re b), which the
+// projection keeps).  One thread per (slot, group): a^p by binary powering in
+// FP64, times b, rounded once; the group-0 thread also writes a^T.
+constexpr int kSeedGroup = 32;                  // m per seed (one walk)
+
+__host__ __device__ __forceinline__ void cpow64(double ar, double ai, int e, double &rr,
+                                                double &ri)
+{
+    double br = ar, bi = ai;
+    rr = 1.0;
+    ri = 0.0;
+    for (; e > 0; e >>= 1) {
+        if (e & 1) {
+            const double t = rr * br - ri * bi;
+            ri = rr * bi + ri * br;
+            rr = t;
+        }
+        const double t = br * br - bi * bi;
+        bi = 2.0 * br * bi;
+        br = t;
+    }
+}
+
+__global__ void tc_seeds_kernel(const float4 *params, const int2 *ringoff, int64_t n_slots,
+                                int Dh, float2 *seed, float2 *aT, double2 *aT64)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_slots * (kTcK / 8)) return;
-    const int64_t s = i / (kTcK / 8);
-    const int m0 = (int)(i % (kTcK / 8)) * 8;
+    if (i >= n_slots * kTcSeeds) return;
+    const int64_t s = i / kTcSeeds;
+    const int g = (int)(i % kTcSeeds);
     const float4 p = params[s];
-    const int d = Dh - ringoff[s].x;
-    const int r = d % kTcT;
-    // the largest m of the group has the smallest power; walk m downwards
-    double ar = p.x, ai = p.y;
-    uint16_t hr[8], lr[8], hi_[8], li[8];
-    double vr = 0.0, vi = 0.0;   // a^p at the current m (valid window only)
-    bool have = false;
-    for (int j = 7; j >= 0; --j) {
-        const int m = m0 + j;
-        const int pw = 2 * kTcT - 1 - r - m;
-        float fr = 0.f, fi = 0.f;
-        if (pw >= 0 && pw < kTcT) {
-            if (!have) {
-                double br = ar, bi = ai, rr = 1.0, ri = 0.0;
-                for (int e = pw; e > 0; e >>= 1) {
-                    if (e & 1) {
-                        const double t = rr * br - ri * bi;
-                        ri = rr * bi + ri * br;
-                        rr = t;
-                    }
-                    const double t = br * br - bi * bi;
-                    bi = 2.0 * br * bi;
-                    br = t;
-                }
-                vr = rr;
-                vi = ri;
-                have = true;
-            } else {
-                const double t = vr * ar - vi * ai;
-                vi = vr * ai + vi * ar;
-                vr = t;
-            }
-            fr = (float)(vr * p.z - vi * p.w);   // a^pw * b
-            fi = (float)(vr * p.w + vi * p.z);
-        }
-        split_bf16(fr, hr[j], lr[j]);
-        split_bf16(fi, hi_[j], li[j]);
+    const int r = (Dh - ringoff[s].x) % kTcT;
+    const int m_hi = min(g * kSeedGroup + kSeedGroup - 1, 2 * kTcT - r - 1);
+    const int m_lo = max(g * kSeedGroup, kTcT - r);
+    float2 v = make_float2(0.f, 0.f);
+    if (m_lo <= m_hi) {
+        double rr, ri;
+        cpow64(p.x, p.y, 2 * kTcT - 1 - r - m_hi, rr, ri);
+        v = make_float2((float)(rr * p.z - ri * p.w), (float)(rr * p.w + ri * p.z));
     }
-    const int64_t row = 2 * s;
-    const int64_t mt = row / kRowsTile;
-    const int rl = (int)(row % kRowsTile);
-    const int kb = m0 / kKBlk, kl = m0 % kKBlk;
-    unsigned char *base = W + ((mt * kKBlocks + kb) * 2) * (int64_t)kTileBytes;
-    uint4 v;
-    v.x = hr[0] | ((uint32_t)hr[1] << 16); v.y = hr[2] | ((uint32_t)hr[3] << 16);
-    v.z = hr[4] | ((uint32_t)hr[5] << 16); v.w = hr[6] | ((uint32_t)hr[7] << 16);
-    *reinterpret_cast<uint4 *>(base + tile_off(rl, kl)) = v;
-    v.x = lr[0] | ((uint32_t)lr[1] << 16); v.y = lr[2] | ((uint32_t)lr[3] << 16);
-    v.z = lr[4] | ((uint32_t)lr[5] << 16); v.w = lr[6] | ((uint32_t)lr[7] << 16);
-    *reinterpret_cast<uint4 *>(base + kTileBytes + tile_off(rl, kl)) = v;
-    v.x = hi_[0] | ((uint32_t)hi_[1] << 16); v.y = hi_[2] | ((uint32_t)hi_[3] << 16);
-    v.z = hi_[4] | ((uint32_t)hi_[5] << 16); v.w = hi_[6] | ((uint32_t)hi_[7] << 16);
-    *reinterpret_cast<uint4 *>(base + tile_off(rl + 1, kl)) = v;
-    v.x = li[0] | ((uint32_t)li[1] << 16); v.y = li[2] | ((uint32_t)li[3] << 16);
-    v.z = li[4] | ((uint32_t)li[5] << 16); v.w = li[6] | ((uint32_t)li[7] << 16);
-    *reinterpret_cast<uint4 *>(base + kTileBytes + tile_off(rl + 1, kl)) = v;
-    if (m0 == 0) {   // a^T, FP64 then rounded once
-        double br = ar, bi = ai, rr = 1.0, ri = 0.0;
-        for (int e = kTcT; e > 0; e >>= 1) {
-            if (e & 1) {
-                const double t = rr * br - ri * bi;
-                ri = rr * bi + ri * br;
-                rr = t;
-            }
-            const double t = br * br - bi * bi;
-            bi = 2.0 * br * bi;
-            br = t;
-        }
+    seed[i] = v;
+    if (g == 0) {   // a^T, FP64 then rounded once
+        double rr, ri;
+        cpow64(p.x, p.y, kTcT, rr, ri);
         aT[s] = make_float2((float)rr, (float)ri);
         aT64[s] = make_double2(rr, ri);
     }
@@ -275,19 +250,85 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // NT: windows per accumulator (N of the MMA): 256, or 128 for calls with few
 // windows (the strain tiles in HBM are 256 wide; a 128-wide column tile is
 // one half of one).
+// Generator thread t of the CTA's M-tile mt: slot 64 mt + (t & 63), the
+// 32-wide half (t >> 6) of K-block kb.  V at m = 32 (2 kb + h) + j is walked
+// from the seed at the group's largest valid m down to its smallest, one
+// complex multiply by a (kernel form) per step, and written as BF16 hi/lo
+// into the stage's A tiles (rows 2 s and 2 s + 1 = Re and Im).
+__device__ __forceinline__ void gen_weights(const TcArgs &A, int64_t mt, int kb, int t,
+                                            unsigned char *stage)
+{
+    const int sl = t & 63, h = t >> 6;
+    const int64_t slot = mt * (kRowsTile / 2) + sl;
+    const int g = 2 * kb + h;
+    float ar = 0.f, ai = 0.f, cr = 0.f, ci = 0.f;
+    int m_lo = 1, m_hi = 0;   // valid m of this group (empty by default)
+    if (slot < A.n_slots) {
+        const float4 p = A.params[slot];
+        ar = p.x;
+        ai = p.y;
+        const int r = (A.Dh - A.ringoff[slot].x) % kTcT;
+        m_hi = min(g * kSeedGroup + kSeedGroup - 1, 2 * kTcT - r - 1);
+        m_lo = max(g * kSeedGroup, kTcT - r);
+        const float2 sd = A.seed[slot * kTcSeeds + g];
+        cr = sd.x;
+        ci = sd.y;
+    }
+    const int row = 2 * sl;
+    const int k0 = h * kSeedGroup;   // k of m = 32 g inside the K-block
+    // eight k at a time, from the top of the group down
+#pragma unroll
+    for (int q = kSeedGroup / 8 - 1; q >= 0; --q) {
+        uint16_t hr[8], lr[8], hi_[8], li[8];
+#pragma unroll
+        for (int j = 7; j >= 0; --j) {
+            const int m = g * kSeedGroup + 8 * q + j;
+            float vr = 0.f, vi = 0.f;
+            if (m >= m_lo && m <= m_hi) {
+                vr = cr;
+                vi = ci;
+                const float nr = __fmaf_rn(cr, ar, -__fmul_rn(ci, ai));
+                ci = __fmaf_rn(cr, ai, __fmul_rn(ci, ar));
+                cr = nr;
+            }
+            split_bf16(vr, hr[j], lr[j]);
+            split_bf16(vi, hi_[j], li[j]);
+        }
+        const int kl = k0 + 8 * q;
+        uint4 v;
+        v.x = hr[0] | ((uint32_t)hr[1] << 16); v.y = hr[2] | ((uint32_t)hr[3] << 16);
+        v.z = hr[4] | ((uint32_t)hr[5] << 16); v.w = hr[6] | ((uint32_t)hr[7] << 16);
+        *reinterpret_cast<uint4 *>(stage + tile_off(row, kl)) = v;
+        v.x = lr[0] | ((uint32_t)lr[1] << 16); v.y = lr[2] | ((uint32_t)lr[3] << 16);
+        v.z = lr[4] | ((uint32_t)lr[5] << 16); v.w = lr[6] | ((uint32_t)lr[7] << 16);
+        *reinterpret_cast<uint4 *>(stage + kTileBytes + tile_off(row, kl)) = v;
+        v.x = hi_[0] | ((uint32_t)hi_[1] << 16); v.y = hi_[2] | ((uint32_t)hi_[3] << 16);
+        v.z = hi_[4] | ((uint32_t)hi_[5] << 16); v.w = hi_[6] | ((uint32_t)hi_[7] << 16);
+        *reinterpret_cast<uint4 *>(stage + tile_off(row + 1, kl)) = v;
+        v.x = li[0] | ((uint32_t)li[1] << 16); v.y = li[2] | ((uint32_t)li[3] << 16);
+        v.z = li[4] | ((uint32_t)li[5] << 16); v.w = li[6] | ((uint32_t)li[7] << 16);
+        *reinterpret_cast<uint4 *>(stage + kTileBytes + tile_off(row + 1, kl)) = v;
+    }
+}
+
+constexpr int kGenThreads = 128;
+constexpr int kProjThreads = kEpiThreads + 32 + kGenThreads;
+
 template <bool ANCH, int NT>
-__global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
+__global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArgs A)
 {
     constexpr uint32_t kBT = (uint32_t)NT * kKBlk * 2u;          // one B component
     constexpr uint32_t kSB = 2u * kTileBytes + 2u * kBT;          // stage bytes
     constexpr uint32_t kIdesc = idesc_for<NT>();
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[2 * kStages + 4];
+    __shared__ __align__(8) uint64_t bars[3 * kStages + 4];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t mt = blockIdx.x;
     const int det = blockIdx.y;
     const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[kStages]);
+    // generated weight tile of a stage written (all generator threads)
+    const uint32_t wfull0 = smem_addr(&bars[2 * kStages + 4]);
     // two TMEM accumulators: the MMAs of column tile nt + 1 run while the
     // epilogue reads tile nt
     const uint32_t acc_full0 = smem_addr(&bars[2 * kStages]);
@@ -296,6 +337,7 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
         for (int st = 0; st < kStages; ++st) {
             mbar_init(full0 + 8 * st, 1);
             mbar_init(empty0 + 8 * st, 1);
+            mbar_init(wfull0 + 8 * st, kGenThreads);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full0 + 8 * b, 1);
@@ -318,11 +360,27 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
     const int n_ntiles = A.n_ntiles;
     bool ok = true;
 
-    if (warp == 4) {
+    if (warp > 4) {
+        // weight generators: stage it % kStages gets K-block it % kKBlocks once
+        // the MMAs that read the stage before (block it - kStages) are done
+        const int t = tid - kEpiThreads - 32;
+        const int total = n_ntiles * kKBlocks;
+        for (int it = 0; it < total; ++it) {
+            const int st = it % kStages;
+            if (it >= kStages &&
+                !mbar_wait(empty0 + 8 * st, (uint32_t)((it / kStages - 1) & 1), A.wait_limit_ns)) {
+                atomicOr(A.err, 8);
+                break;
+            }
+            gen_weights(A, mt, it % kKBlocks, t, smem + st * kSB);
+            // generic-proxy writes, read next by the tensor cores (async proxy)
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(wfull0 + 8 * st);
+        }
+    } else if (warp == 4) {
         if (lane == 0) {
             // producer + MMA issue, two stages
             const int total = n_ntiles * kKBlocks;
-            const unsigned char *wt = A.W + mt * kKBlocks * 2 * (int64_t)kTileBytes;
             const unsigned char *bt =
                 A.B + (int64_t)det * A.n_btiles * kKBlocks * 2 * kBTileBytes;
             auto fill = [&](int it) {
@@ -330,8 +388,7 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
                 const int nt = it / kKBlocks, kb = it % kKBlocks;
                 const uint32_t dst = smem_addr(smem) + st * kSB;
                 const uint32_t full = full0 + 8 * st;
-                mbar_expect_tx(full, kSB);
-                bulk_g2s(dst, wt + (int64_t)kb * 2 * kTileBytes, 2 * kTileBytes, full);
+                mbar_expect_tx(full, 2u * kBT);
                 // the strain tile holding windows [nt * NT, nt * NT + NT)
                 const int64_t col0 = (int64_t)nt * NT;
                 const unsigned char *src =
@@ -350,7 +407,8 @@ __global__ void __launch_bounds__(160, 1) tc_project_kernel(const TcArgs A)
             for (int it = 0; it < total && ok; ++it) {
                 const int st = it % kStages;
                 const int nt = it / kKBlocks, kb = it % kKBlocks;
-                ok = mbar_wait(full0 + 8 * st, (uint32_t)((it / kStages) & 1), A.wait_limit_ns);
+                ok = mbar_wait(full0 + 8 * st, (uint32_t)((it / kStages) & 1), A.wait_limit_ns) &&
+                     mbar_wait(wfull0 + 8 * st, (uint32_t)((it / kStages) & 1), A.wait_limit_ns);
                 if (ok && kb == 0 && nt >= 2)   // epilogue has read tile nt - 2 (same TMEM)
                     ok = mbar_wait(acc_empty0 + 8 * (nt & 1), (uint32_t)(((nt - 2) >> 1) & 1),
                                    A.wait_limit_ns);
@@ -495,12 +553,6 @@ cudaError_t launch_state_to_fp64(const float2 *state, double2 *s64, int64_t coun
     return cudaGetLastError();
 }
 
-int64_t tc_weight_bytes(int64_t n_slots)
-{
-    const int64_t mtiles = (2 * n_slots + kRowsTile - 1) / kRowsTile;
-    return mtiles * kKBlocks * 2 * (int64_t)kTileBytes;
-}
-
 int64_t tc_strain_bytes(int64_t n_cols, int D)
 {
     const int64_t ntiles = (n_cols + kColsTile - 1) / kColsTile;
@@ -509,15 +561,13 @@ int64_t tc_strain_bytes(int64_t n_cols, int D)
 
 int tc_cols_per_tile() { return kColsTile; }
 
-cudaError_t launch_tc_weights(const float4 *params, const int2 *ringoff, int64_t n_slots, int Dh,
-                              unsigned char *W, float2 *aT, double2 *aT64, cudaStream_t s)
+cudaError_t launch_tc_seeds(const float4 *params, const int2 *ringoff, int64_t n_slots, int Dh,
+                            float2 *seed, float2 *aT, double2 *aT64, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(W, 0, (size_t)tc_weight_bytes(n_slots), s);
-    if (e != cudaSuccess) return e;
-    const int64_t threads = n_slots * (kTcK / 8);
+    const int64_t threads = n_slots * kTcSeeds;
     if (threads == 0) return cudaSuccess;
-    tc_weights_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(params, ringoff, n_slots,
-                                                                         Dh, W, aT, aT64);
+    tc_seeds_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>(params, ringoff, n_slots,
+                                                                       Dh, seed, aT, aT64);
     return cudaGetLastError();
 }
 
@@ -540,7 +590,7 @@ template <bool ANCH, int NT> cudaError_t launch_project_nt(TcArgs a, int64_t mti
     if (e != cudaSuccess) return e;
     a.n_ntiles = (int32_t)((a.n_cols + NT - 1) / NT);
     a.n_btiles = (int32_t)((a.n_cols + kColsTile - 1) / kColsTile);
-    tc_project_kernel<ANCH, NT><<<dim3((unsigned)mtiles, (unsigned)a.D), 160, smem, s>>>(a);
+    tc_project_kernel<ANCH, NT><<<dim3((unsigned)mtiles, (unsigned)a.D), kProjThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
