@@ -52,6 +52,7 @@ LANE_OPS_PER_UPDATE = 8      # 4 FMA + 2 MUL + 2 ADD (FP32 lane operations)
 # (10 ms) and between sites ~8000 km apart (27 ms), plus a sample
 NETWORK_WINDOWS = [0, 10, 28]
 LANE_OPS_ADJOINT = 20        # reverse pass per filter-update: recompute 6, adjoint 6, grads 8
+LANE_OPS_TANGENT = 20        # tangent form: u 4, v 4, g_a sum 4, shifted adjoint 4, g_x 2, g_b 2
 FP32_LANES_PER_SM = 128
 
 
@@ -81,6 +82,8 @@ def parse():
     ap.add_argument("--front-end", action="store_true",
                     help="multirate: windowed-sinc anti-aliasing FIRs (8 R - 1 taps) on the "
                          "decimated bands instead of plain subsampling")
+    ap.add_argument("--adjoint-form", default="auto", choices=["auto", "tangent", "reverse"],
+                    help="--workload adjoint: evaluation of g_a, g_b (the plan option)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -606,8 +609,10 @@ def sub_precision(sp, dev, stream, peak_lane, n_sm, sm_max, steps=2):
 def sub_adjoint(sp, dev, stream, peak_lane, n_sm, sm_max, steps=10, warmup=3):
     """Adjoint workload (256 templates x 200 filters, 65536 samples at 1024
     Hz): spiir_filter_backward (dL/da, dL/db, dL/dx for a seeded g_z) against
-    the forward call on the same plan; the oracle's adjoint on 8 sampled
-    templates is the CPU baseline and the reference of g_a, g_b there."""
+    the forward call on the same plan, in both evaluations of g_a, g_b (the
+    tangent form, the plan's default here, and the reverse form); the
+    oracle's adjoint on 8 sampled templates is the CPU baseline and the
+    reference of g_a, g_b there."""
     import torch
 
     import oracle
@@ -619,20 +624,6 @@ def sub_adjoint(sp, dev, stream, peak_lane, n_sm, sm_max, steps=10, warmup=3):
     upd = updates(bank, n)
     g = torch.Generator(device=dev).manual_seed(7)
     gz = torch.randn((D, T, n), dtype=torch.complex64, device=dev, generator=g)
-    plan = sp.Plan(bank, device=dev.index, kernel_timing=True)
-    with torch.cuda.stream(stream):
-        for _ in range(warmup):
-            ga, gb, gx = plan.backward(x, gz, stream=stream)
-        stream.synchronize()
-        plan.kernel_times()
-        with ClockSampler(dev.index) as clk:
-            bw_ms = timed(stream, lambda: plan.backward(x, gz, stream=stream), steps)
-            kt = plan.kernel_times()
-            plan.reset(stream=stream)
-            fw_ms = timed(stream, lambda: plan.filter(x, emit_z=False, stream=stream), steps)
-        ga, gb, gx = plan.backward(x, gz, stream=stream)
-        stream.synchronize()
-    plan.check(stream)
     picks = sorted(int(t) for t in np.random.default_rng(505).choice(T, 8, replace=False))
     sub = bank.subset(picks)
     gz_sub = gz[:, picks].cpu().numpy()
@@ -640,26 +631,66 @@ def sub_adjoint(sp, dev, stream, peak_lane, n_sm, sm_max, steps=10, warmup=3):
     ra, rb, _ = oracle.adjoint(sub.off, sub.a, sub.b, sub.d, x_host, gz_sub, want_gx=False)
     dt = time.perf_counter() - t0
     fil = np.concatenate([np.arange(bank.off[t], bank.off[t + 1]) for t in picks])
-    ga_s = ga.cpu().numpy()[fil]
-    gb_s = gb.cpu().numpy()[fil]
-    err_a = float(np.max(np.abs(ga_s - ra)) / np.max(np.abs(ra)))
-    err_b = float(np.max(np.abs(gb_s - rb)) / np.max(np.abs(rb)))
-    a_ms, a_n = kt["adjoint"]
-    plan.close()
+
+    def run_form(form):
+        plan = sp.Plan(bank, device=dev.index, kernel_timing=True, adjoint_form=form)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                ga, gb, gx = plan.backward(x, gz, stream=stream)
+            stream.synchronize()
+            plan.kernel_times()
+            with ClockSampler(dev.index) as clk:
+                bw_ms = timed(stream, lambda: plan.backward(x, gz, stream=stream), steps)
+                kt = plan.kernel_times()
+                plan.reset(stream=stream)
+                fw_ms = timed(stream, lambda: plan.filter(x, emit_z=False, stream=stream), steps)
+            ga, gb, gx = plan.backward(x, gz, stream=stream)
+            stream.synchronize()
+        plan.check(stream)
+        launches = plan.info()["last_call_launches"]
+        ga_s = ga.cpu().numpy()[fil]
+        gb_s = gb.cpu().numpy()[fil]
+        err_a = float(np.max(np.abs(ga_s - ra)) / np.max(np.abs(ra)))
+        err_b = float(np.max(np.abs(gb_s - rb)) / np.max(np.abs(rb)))
+        a_ms, _ = kt["adjoint"]
+        plan.close()
+        if form == "reverse":
+            kernel, ops = "k6_adjoint + k7_adjoint_x", LANE_OPS_ADJOINT
+            what = ("k6 (reverse pass) and k7 (input-gradient pass)",
+                    f"{LANE_OPS_ADJOINT} algorithmic lane-ops per filter-update of the reverse "
+                    "pass (recompute 6, adjoint recurrence 6, grad a 4, grad b 2, grad x 2)")
+        else:
+            kernel, ops = "kt_tangent + adj_project + k7_adjoint_x", LANE_OPS_TANGENT
+            what = ("kt_tangent (g_a), the reverse projection and k7 (g_x, g_b)",
+                    f"{LANE_OPS_TANGENT} algorithmic lane-ops per filter-update (u 4, v 4, the "
+                    "g_a sum 4, shifted adjoint recurrence 4, g_x term 2, g_b sum 2)")
+        return {
+            "value": upd / (bw_ms / 1e3), "unit": "filter-updates/s of the backward",
+            "backward_ms": bw_ms, "forward_ms": fw_ms, "backward_over_forward": bw_ms / fw_ms,
+            "launches_per_backward": launches,
+            "grad_rel_err": {"g_a": err_a, "g_b": err_b,
+                             "of": f"templates {picks}: max |g_gpu - g_oracle| / max |g_oracle|"},
+            "roofline": alu_roofline(
+                kernel, ops * upd, a_ms / steps, peak_lane, n_sm, sm_max,
+                f"{a_ms / steps:.3f} ms per backward of {what[0]} (CUDA events around their "
+                f"launches)", what[1]),
+            "clocks": clk.summary(),
+        }
+
+    forms = {f: run_form(f) for f in ("tangent", "reverse")}
+    head = forms["tangent"]
     return {
         "workload": describe("adjoint", bank, n)["workload"],
-        "value": upd / (bw_ms / 1e3), "unit": "filter-updates/s of the backward",
-        "backward_ms": bw_ms, "forward_ms": fw_ms, "backward_over_forward": bw_ms / fw_ms,
+        "form": "tangent (the plan's default for this bank)",
+        "value": head["value"], "unit": head["unit"],
+        "backward_ms": head["backward_ms"], "forward_ms": head["forward_ms"],
+        "backward_over_forward": head["backward_over_forward"],
         "steps": steps, "warmup": warmup,
-        "grad_rel_err": {"g_a": err_a, "g_b": err_b,
-                         "of": f"templates {picks}: max |g_gpu - g_oracle| / max |g_oracle|"},
-        "roofline": alu_roofline(
-            "k6_adjoint + k7_adjoint_x", 20 * upd, a_ms / steps, peak_lane, n_sm, sm_max,
-            f"{a_ms / steps:.3f} ms per backward of the reverse pass (k6) and the input-gradient "
-            f"pass (k7) (CUDA events around their launches)",
-            "20 algorithmic lane-ops per filter-update of the reverse pass (recompute 6, "
-            "adjoint recurrence 6, grad a 4, grad b 2, grad x 2)"),
-        "clocks": clk.summary(),
+        "grad_rel_err": head["grad_rel_err"],
+        "roofline": head["roofline"],
+        "clocks": head["clocks"],
+        "forms": forms,
+        "tangent_speedup_over_reverse": forms["reverse"]["backward_ms"] / head["backward_ms"],
         "cpu_baseline": {"value": updates(sub, n) / dt, "unit": "filter-updates/s (adjoint)",
                          "cores": oracle.max_threads(), "kind": "oracle",
                          "sample": f"the FP64 adjoint of {len(picks)} of {T} templates, "
@@ -694,7 +725,7 @@ def run_ours(args, rank, world, local_rank):
     # projection and adjoint launches, on the launching stream (not in graphs)
     plan = sp.Plan(bank, device=local_rank, precision=args.precision,
                    autotune=not args.no_autotune and args.precision == "plain",
-                   kernel_timing=True)
+                   kernel_timing=True, adjoint_form=args.adjoint_form)
     if args.front_end and bank.decim is not None:
         for j, R in enumerate(bank.decim):
             if R > 1:   # low-pass at the band's Nyquist rate, Hann-windowed sinc
@@ -881,19 +912,26 @@ def run_ours(args, rank, world, local_rank):
     # the dominant kernel's own device time over the direct timed steps
     # (events the plan records around each launch; graph replays record none)
     k_ms, k_n = ktimes["adjoint" if adjoint else "filter"]
-    lane_ops = (LANE_OPS_ADJOINT if adjoint else LANE_OPS_PER_UPDATE) * upd
+    # the auto form is the tangent one on a bank this size (>= 8 warps per SM)
+    reverse = adjoint and args.adjoint_form == "reverse"
+    lane_ops = ((LANE_OPS_ADJOINT if reverse else LANE_OPS_TANGENT) if adjoint
+                else LANE_OPS_PER_UPDATE) * upd
     kernel_ms = k_ms / args.steps
     timing = (f"{k_n / args.steps:.0f} launch(es) per step, {kernel_ms:.3f} ms per step "
               f"(CUDA events around each launch on the launching stream, direct steps)")
     if adjoint:
-        kernel = "k6_adjoint + k7_adjoint_x"
+        kernel = ("k6_adjoint + k7_adjoint_x" if reverse else
+                  "kt_tangent + adj_project + k7_adjoint_x")
     traffic, traffic_note = None, None
     key = ("adjoint" if adjoint else args.workload, args.precision)
     if key in TRAFFIC and not args.samples and not args.templates:
         traffic, traffic_note = TRAFFIC[key]
     ops_note = ("20 algorithmic lane-ops per filter-update of the reverse pass (recompute 6, "
                 "adjoint recurrence 6, grad a 4, grad b 2, grad x 2) over the device time of "
-                "the reverse pass (k6) and the input-gradient pass (k7)" if adjoint else
+                "the reverse pass (k6) and the input-gradient pass (k7)" if reverse else
+                "20 algorithmic lane-ops per filter-update (u 4, v 4, the g_a sum 4, shifted "
+                "adjoint recurrence 4, g_x term 2, g_b sum 2) over the device time of the "
+                "tangent pass, the reverse projection and k7" if adjoint else
                 "8 algorithmic lane-ops per filter-update")
     line = {
         "metric": "filter-updates/s", "value": value, "unit": "filter-updates/s",

@@ -146,8 +146,21 @@ typedef struct spiir_options {
                             /* predicted launch on the resident CTAs), k in 1..200 */
                             /* = the smallest templates holding k per mille of the  */
                             /* filter rounds                                        */
-    int32_t reserved[2];
+    int32_t adjoint_form;   /* how spiir_filter_backward evaluates g_a and g_b:     */
+                            /* SPIIR_ADJOINT_REVERSE (the reverse-time recurrence   */
+                            /* over a checkpointed forward), _TANGENT (one forward  */
+                            /* pass of each filter's derivative recurrences, no     */
+                            /* checkpoints) or _AUTO (tangent when the bank holds   */
+                            /* >= 8 warps per SM at one filter per thread)          */
+    int32_t reserved[1];
 } spiir_options;
+
+/* Evaluation of the adjoint's g_a, g_b (spiir_options.adjoint_form). */
+typedef enum spiir_adjoint_form {
+    SPIIR_ADJOINT_AUTO = 0,
+    SPIIR_ADJOINT_REVERSE = 1,
+    SPIIR_ADJOINT_TANGENT = 2
+} spiir_adjoint_form;
 
 /* Plan statistics (spiir_plan_get_info). */
 typedef struct spiir_plan_info {
@@ -361,7 +374,14 @@ spiir_status spiir_network_peak(const float *z_dev, int32_t n_detectors, int64_t
  * outputs use the same convention and are OVERWRITTEN:
  *   grad_a_dev, grad_b_dev  [Ltot] complex64 (summed over detectors)
  *   grad_x_dev              [n_detectors][n] float32, or NULL
- * The forward is recomputed from state checkpoints kept in plan workspace.
+ * g_a and g_b (spiir_options.adjoint_form): the reverse form recomputes the
+ * forward from state checkpoints kept in plan workspace and runs the adjoint
+ * recurrence backwards in time; the tangent form runs, forward in time, each
+ * filter's unit-gain response u_l[k] = a_l u_l[k-1] + x[k-d_l] and its
+ * derivative recurrence v_l[k] = a_l v_l[k-1] + u_l[k-1], and sums
+ * g_b_l = sum_k g_z[k] conj(u_l[k]), g_a_l = conj(b_l) sum_k g_z[k] conj(v_l[k])
+ * (the same sums as sum_k lambda_l[k] x[k-d_l] and
+ * sum_k lambda_l[k] conj(y_l[k-1]), in the other order).
  * grad_x is summed over filters in the shifted adjoint frame (each filter
  * reads g_z at its own delay, all meet at one output sample) and over
  * templates with float atomics, so its last bits depend on timing.
@@ -454,7 +474,8 @@ spiir_status spiir_filter_noalloc(const spiir_bank_desc *bank, const float *x_de
  *   ms[SPIIR_KERNEL_CLASSES]  total milliseconds per class (host array)
  *   n[SPIIR_KERNEL_CLASSES]   launches per class (host array, may be NULL)
  * Classes: 0 the filter kernel (all K1 passes), 1 the tensor-core
- * projection, 2 the adjoint's reverse pass and its input-gradient pass.
+ * projection, 2 the adjoint's kernels (its reverse pass or its tangent
+ * pass, and its input-gradient pass with that pass's projection).
  * Errors: EINVAL (NULL plan or ms), ECUDA. */
 #define SPIIR_KERNEL_CLASSES 3
 spiir_status spiir_kernel_times(spiir_plan *plan, double *ms, int64_t *n);

@@ -63,7 +63,8 @@ class Options(ctypes.Structure):
                 ("lanes_per_template", ctypes.c_int32), ("time_segments", ctypes.c_int32),
                 ("projection", ctypes.c_int32), ("kernel_timing", ctypes.c_int32),
                 ("tile_chunks", ctypes.c_int32), ("persistent", ctypes.c_int32),
-                ("tail_split", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("tail_split", ctypes.c_int32), ("adjoint_form", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class PlanInfo(ctypes.Structure):
@@ -243,7 +244,7 @@ class Plan:
                  max_filters_per_lane: int = 0, lanes_per_template: int = 0,
                  time_segments: int = 0, projection: str = "auto",
                  kernel_timing: bool = False, tile_chunks: int = 0, persistent: str = "auto",
-                 tail_split: int = 0, lib=None):
+                 tail_split: int = 0, adjoint_form: str = "auto", lib=None):
         self._h = None
         self._lib = lib if lib is not None else _lib
         off = np.ascontiguousarray(bank.off, np.int64)
@@ -281,6 +282,7 @@ class Plan:
         opt.tile_chunks = int(tile_chunks)
         opt.persistent = {"auto": 0, "off": 1, "on": 2}[persistent]
         opt.tail_split = int(tail_split)
+        opt.adjoint_form = {"auto": 0, "reverse": 1, "tangent": 2}[adjoint_form]
         h = _P()
         _check(self._lib.spiir_plan_create(ctypes.byref(desc), ctypes.byref(opt), ctypes.byref(h)),
                "spiir_plan_create", self._lib)

@@ -41,8 +41,16 @@ def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(OBJ, exist_ok=True)
     os.makedirs(LIB_DIR, exist_ok=True)
 
+    headers = glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(ROOT, "include", "*.h")) + \
+        [os.path.abspath(__file__)]
+    hdr_mtime = max(os.path.getmtime(f) for f in headers)
+
     def compile_one(src):
         obj = os.path.join(OBJ, os.path.basename(src) + ".o")
+        # an object newer than its source and every header is reused
+        if not force and os.path.exists(obj) and \
+                os.path.getmtime(obj) >= max(os.path.getmtime(src), hdr_mtime):
+            return obj
         cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
         if verbose and src.endswith(".cu"):
             cmd.insert(1, "-Xptxas=-v")

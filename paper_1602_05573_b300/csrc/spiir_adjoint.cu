@@ -268,11 +268,20 @@ __global__ void __launch_bounds__(256, 2) k6_adjoint(const K6Args A)
 // and writes c for 32 consecutive outputs into a 32 x 32 warp tile, XOR
 // swizzled so that the writes (one row) and the reads (lane j sums row j)
 // both hit 32 banks.  The warps' sums meet in a fixed order and go to g_x
-// with one atomic per output and CTA.  Segment q < P - 1 starts from
-// nu at (q + 1) S, i.e. mu at k_t = (q + 1) S + d, which the reverse pass kept
-// at the top of the 16-sample span holding k_t: at most 16 reverse steps on
-// g_z from there give it.
-template <int NP>
+// with one atomic per output and CTA.
+//
+// Segment q < P - 1 starts from nu[(q + 1) S] = mu[(q + 1) S + d].
+// TAN = false: the reverse pass kept mu at the top of the 16-sample span
+// holding (q + 1) S + d; at most 16 reverse steps on g_z from there give it.
+// TAN = true (the tangent form, which has no reverse pass): A.seeds holds
+// mu at the common time B = (q + 1) S + Dh (the reverse projection over
+// segments shifted by Dh).  The CTA first runs Dh warm-up steps
+// m = B - 1 .. (q + 1) S from zero state with g_z read as zero from B on,
+// which gives nu[(q + 1) S] but for the seed's share, then adds that share,
+//     nu[(q + 1) S] += conj(a)^(Dh - d) mu[B].
+// With TAN the CTA also sums g_b = sum_m nu[m] x[m] (x is the detector's
+// strain, the same for every filter at output m) into A.acc.
+template <int NP, bool TAN>
 __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args A)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -282,6 +291,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
     float *win = reinterpret_cast<float *>(smem);   // [n_win][2][Wd]: re plane, im plane
     float *tile = win + n_win * 2 * Wd;             // [W][32][32]
     float *part = tile + A.W * 1024;                // [W][kK7Chunk]
+    float *xsh = part + A.W * kK7Chunk;             // [kK7Chunk] strain of the chunk (TAN)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int per = A.n_units * A.n_det;
     const int seg = (int)(blockIdx.x / per);
@@ -292,6 +302,8 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
     const int4 head = A.tasks[unit.x];               // the unit's template(s)
     const int n = A.n;
     const int mlo = seg * A.S, mhi = min(n, mlo + A.S);
+    const bool warm = TAN && seg + 1 < A.P;
+    const int gend = warm ? min(n, mhi + A.Dh) : n; // g_z reads as zero from here on
     const bool odd = (lane & 1) != 0;               // stored as conj(a), (Im b, Re b)
     const int wsel = (A.G == 16 && lane >= 16) ? 1 : 0;
     const int tmpl = wsel ? head.w : head.z;
@@ -299,7 +311,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
     const float *pr = win + wsel * 2 * Wd;
 
     // pair p of this lane: the two rounds of task unit.x + NP warp + p
-    uint64_t AR[NP], AI[NP], NAI[NP], BR[NP], BI[NP], NR[NP], NI[NP];
+    uint64_t AR[NP], AI[NP], NAI[NP], BR[NP], BI[NP], NR[NP], NI[NP], GBR[NP], GBI[NP];
     const float *rp[NP][R];
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
@@ -323,7 +335,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
             rp[p][i] = pr + d;
             // start state nu[(q + 1) S] = mu[(q + 1) S + d] (zero past the call)
             const int kt = mhi + d;
-            if (seg + 1 < A.P && kt < n && tmpl >= 0) {
+            if (!TAN && seg + 1 < A.P && kt < n && tmpl >= 0) {
                 const float2 m0 = A.seeds[((int64_t)seg * A.n_det + det) * A.n_slots + slot];
                 float mr = m0.x, mi = m0.y;
                 for (int j = (kt & ~(kAdjSub - 1)) + kAdjSub - 1; j >= kt; --j) {
@@ -344,25 +356,94 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
         BI[p] = pk(bi[0], bi[1]);
         NR[p] = pk(nu_r[0], nu_r[1]);
         NI[p] = pk(nu_i[0], nu_i[1]);
+        GBR[p] = 0;
+        GBI[p] = 0;
     }
     float *wt = tile + warp * 1024;
     float *gxrow = A.gx + (int64_t)det * n;
+    // x[0 .. n) of this detector (TAN)
+    const float *xrow = TAN ? A.xe + (int64_t)det * A.xe_stride + A.Dh : nullptr;
 
-    const int n_chunks = (mhi - mlo + kK7Chunk - 1) / kK7Chunk;
-    for (int c = n_chunks - 1; c >= 0; --c) {
-        const int mc = mlo + c * kK7Chunk;
-        const int cv = min(kK7Chunk, mhi - mc);
+    // g_z window of the chunk starting at output mc, zero from gend on
+    auto stage = [&](int mc) {
         for (int w = 0; w < n_win; ++w) {
             const int t = w ? head.w : head.z;
             const float2 *row = A.gz + ((int64_t)det * A.T + (t >= 0 ? t : 0)) * n;
             float *dr = win + w * 2 * Wd;
             for (int i = threadIdx.x; i < Wd; i += blockDim.x) {
                 const int j = mc + i;
-                const float2 v = (t >= 0 && j < n) ? row[j] : make_float2(0.f, 0.f);
+                const float2 v = (t >= 0 && j < gend) ? row[j] : make_float2(0.f, 0.f);
                 dr[i] = v.x;
                 dr[Wd + i] = v.y;
             }
         }
+    };
+    // one reverse step of pair p at window offset o
+    auto step = [&](int p, int o) {
+        const uint64_t GR = pk(rp[p][0][o], rp[p][1][o]);
+        const uint64_t GI = pk(rp[p][0][Wd + o], rp[p][1][Wd + o]);
+        const uint64_t nR = fma2(AR[p], NR[p], fma2(AI[p], NI[p], GR));
+        const uint64_t nI = fma2(AR[p], NI[p], fma2(NAI[p], NR[p], GI));
+        NR[p] = nR;
+        NI[p] = nI;
+    };
+
+    if (warm) {
+        // warm-up over outputs [mhi, mhi + Dh), no output
+        for (int c = A.Dh / kK7Chunk - 1; c >= 0; --c) {
+            stage(mhi + c * kK7Chunk);
+            __syncthreads();
+            if (active)
+                for (int o = kK7Chunk - 1; o >= 0; --o) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) step(p, o);
+                }
+            __syncthreads();
+        }
+        // the seed's share: nu += conj(a)^(Dh - d) mu[B]
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int k = NP * warp + p;
+            if (!active || k >= unit.y || tmpl < 0) continue;
+            const int4 task = A.tasks[unit.x + k];
+            float nr_[R], ni_[R], ar_[R], ai_[R];
+            upk(NR[p], nr_[0], nr_[1]);
+            upk(NI[p], ni_[0], ni_[1]);
+            upk(AR[p], ar_[0], ar_[1]);
+            upk(AI[p], ai_[0], ai_[1]);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (i >= task.y) continue;
+                const int64_t slot = (int64_t)task.x + (int64_t)i * A.round_stride + lane;
+                const float2 m0 = A.seeds[((int64_t)seg * A.n_det + det) * A.n_slots + slot];
+                // conj(a)^e, e = Dh - d, by binary powering
+                float br_ = ar_[i], bi_ = -ai_[i], pr_ = 1.f, pi_ = 0.f;
+                for (int e = A.ringoff[slot].x; e > 0; e >>= 1) {
+                    if (e & 1) {
+                        const float t = pr_ * br_ - pi_ * bi_;
+                        pi_ = pr_ * bi_ + pi_ * br_;
+                        pr_ = t;
+                    }
+                    const float t = br_ * br_ - bi_ * bi_;
+                    bi_ = 2.f * br_ * bi_;
+                    br_ = t;
+                }
+                nr_[i] += pr_ * m0.x - pi_ * m0.y;
+                ni_[i] += pr_ * m0.y + pi_ * m0.x;
+            }
+            NR[p] = pk(nr_[0], nr_[1]);
+            NI[p] = pk(ni_[0], ni_[1]);
+        }
+    }
+
+    const int n_chunks = (mhi - mlo + kK7Chunk - 1) / kK7Chunk;
+    for (int c = n_chunks - 1; c >= 0; --c) {
+        const int mc = mlo + c * kK7Chunk;
+        const int cv = min(kK7Chunk, mhi - mc);
+        stage(mc);
+        if (TAN)
+            for (int i = threadIdx.x; i < kK7Chunk; i += blockDim.x)
+                xsh[i] = mc + i < n ? xrow[mc + i] : 0.f;
         __syncthreads();
         if (active) {
             // steps at m >= n (the top block of the call's last chunk) run on
@@ -372,17 +453,18 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
 #pragma unroll
                 for (int t = 31; t >= 0; --t) {
                     float c = 0.f;
+                    const float xv = TAN ? xsh[mb + t] : 0.f;
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
-                        const uint64_t GR = pk(rp[p][0][mb + t], rp[p][1][mb + t]);
-                        const uint64_t GI = pk(rp[p][0][Wd + mb + t], rp[p][1][Wd + mb + t]);
-                        const uint64_t nR = fma2(AR[p], NR[p], fma2(AI[p], NI[p], GR));
-                        const uint64_t nI = fma2(AR[p], NI[p], fma2(NAI[p], NR[p], GI));
-                        NR[p] = nR;
-                        NI[p] = nI;
+                        step(p, mb + t);
                         float c0, c1;
                         upk(fma2(NR[p], BR[p], mul2(NI[p], BI[p])), c0, c1);
                         c += c0 + c1;
+                        if (TAN) {
+                            const uint64_t X = pk(xv, xv);
+                            GBR[p] = fma2(NR[p], X, GBR[p]);
+                            GBI[p] = fma2(NI[p], X, GBI[p]);
+                        }
                     }
                     wt[t * 32 + (lane ^ t)] = c;
                 }
@@ -402,6 +484,167 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
             if (v != 0.f) atomicAdd(&gxrow[mc + i], v);
         }
         __syncthreads();
+    }
+    if (TAN && active) {
+        // this segment's share of g_b = sum_m nu[m] x[m], natural form
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            const int k = NP * warp + p;
+            if (k >= unit.y) continue;
+            const int4 task = A.tasks[unit.x + k];
+            float r[R], im[R];
+            upk(GBR[p], r[0], r[1]);
+            upk(GBI[p], im[0], im[1]);
+#pragma unroll
+            for (int i = 0; i < R; ++i) {
+                if (i >= task.y) continue;
+                const int64_t slot = (int64_t)task.x + (int64_t)i * A.round_stride + lane;
+                float *acc = A.acc + (((int64_t)seg * A.n_det + det) * A.n_slots + slot) * 6;
+                acc[4] = r[i];
+                acc[5] = im[i];
+            }
+        }
+    }
+}
+
+// Gradients of a and b in tangent form.  y_l is linear in b_l and starts
+// from zero, so y_l = b_l u_l with the unit-gain response
+//     u_l[k] = a_l u_l[k-1] + x[k-d_l]                      (= dy_l[k]/db_l),
+// and dy_l[k]/da_l = y_l[k-1] + a_l dy_l[k-1]/da_l = b_l v_l[k] with
+//     v_l[k] = a_l v_l[k-1] + u_l[k-1].
+// With g_z[k] = dL/dRe z + i dL/dIm z the gradients (PyTorch convention) are
+//     g_b_l = sum_k g_z[k] conj(u_l[k]),   g_a_l = conj(b_l) sum_k g_z[k] conj(v_l[k]),
+// the adjoint formulas sum_k mu_l[k] x[k-d_l] and sum_k mu_l[k] conj(y_l[k-1])
+// with the order of summation exchanged (mu_l[k] = sum_{j>=k} conj(a_l)^(j-k) g_z[j]).
+// One forward pass in time: no checkpoints, no recompute and no reverse
+// recurrence; 16 FP32 operations per filter-update (u 4, v 4, the two sums
+// 8), or 12 with GB = false, when the input-gradient pass sums g_b instead
+// (sum_m nu[m] x[m] there costs 2).
+//
+// One filter per lane (scalar FFMA: a bank that fills the GPU at one filter
+// per lane needs no time segments).  A CTA of W warps serves W x 32
+// consecutive lanes of the tangent order on one detector: the strain window
+// of each Tb-sample block (Dh history + Tb) is copied into shared memory by
+// cp.async, double buffered; each warp stages its (at most two) templates'
+// g_z 16 samples at a time (one load per lane, fetched a sub-block ahead)
+// and every lane reads its template's row.  Sums restart every block and are
+// added into block-level totals (rounding grows with the block, not the call).
+template <bool GB>
+__global__ void __launch_bounds__(256) kt_tangent(const KTArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int Wd = A.Dh + A.Tb;
+    float *xs = reinterpret_cast<float *>(smem);                     // [2][Wd]
+    float2 *gbw = reinterpret_cast<float2 *>(xs + 2 * Wd);           // [W][36]
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int det = blockIdx.y;
+    const int64_t wg = (int64_t)blockIdx.x * A.W + warp;
+    const bool wact = wg * 32 < A.n_pos;                              // warp-uniform
+    const int2 ln = wact ? A.lanes[wg * 32 + lane] : make_int2(-1, 0);
+    const int2 wt = wact ? A.warp_tmpl[wg] : make_int2(-1, -1);
+    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
+    int xo = 0;
+    if (ln.x >= 0) {
+        const float4 p = A.params[ln.x];
+        const bool odd = (ln.x & 1) != 0;   // stored as conj(a), (Im b, Re b)
+        ar = p.x;
+        ai = odd ? -p.y : p.y;
+        br = odd ? p.w : p.z;
+        bi = odd ? p.z : p.w;
+        xo = A.ringoff[ln.x].x;             // Dh - d
+    }
+    const float nai = -ai;
+    // lane j stages sample (j & 15) of template (j >> 4) of its warp
+    const int st = (lane >> 4) ? wt.y : wt.x;
+    const float2 *grow = st >= 0 ? A.gz + ((int64_t)det * A.T + st) * A.n : nullptr;
+    float2 *gb = gbw + warp * 36;
+    const int gput = (lane >> 4) * 18 + (lane & 15);   // rows 18 apart: different banks
+    const float2 *gr = gb + (ln.y ? 18 : 0);
+    const float *xrow = A.xe + (int64_t)det * A.xe_stride;
+    const int n = A.n, Tb = A.Tb;
+    const int nblk = (n + Tb - 1) / Tb;
+
+    // window of block j: xs[i] = xe[j Tb + i] = x[j Tb + i - Dh]
+    auto issue = [&](int j) {
+        const float *src = xrow + (int64_t)j * Tb;
+        const uint32_t dst = smem_addr(xs + (j & 1) * Wd);
+        for (int i = 4 * (int)threadIdx.x; i < Wd; i += 4 * (int)blockDim.x)
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 4u * i),
+                         "l"(src + i)
+                         : "memory");
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+
+    float ur = 0.f, ui = 0.f, vr = 0.f, vi = 0.f;
+    float Tbr = 0.f, Tbi = 0.f, Tar = 0.f, Tai = 0.f;   // totals of the two sums
+    float2 gnext = make_float2(0.f, 0.f);
+    if (grow != nullptr && (lane & 15) < n) gnext = grow[lane & 15];
+    issue(0);
+    for (int j = 0; j < nblk; ++j) {
+        if (j + 1 < nblk) {
+            issue(j + 1);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+        const float *w = xs + (j & 1) * Wd + xo;
+        const int k0 = j * Tb;
+        const int nv = min(Tb, n - k0);
+        // sum_k g_z conj(u): re = Gr ur + Gi ui, im = Gi ur - Gr ui (two chains);
+        // likewise with v
+        float sbr = 0.f, sbi1 = 0.f, sbi2 = 0.f, sar = 0.f, sai1 = 0.f, sai2 = 0.f;
+        auto step = [&](float x, float2 g) {
+            const float nvr = fmaf(ar, vr, fmaf(nai, vi, ur));   // v <- a v + u
+            const float nvi = fmaf(ar, vi, fmaf(ai, vr, ui));
+            const float nur = fmaf(ar, ur, fmaf(nai, ui, x));    // u <- a u + x
+            const float nui = fmaf(ar, ui, ai * ur);
+            ur = nur;
+            ui = nui;
+            vr = nvr;
+            vi = nvi;
+            if (GB) {
+                sbr = fmaf(g.x, ur, fmaf(g.y, ui, sbr));
+                sbi1 = fmaf(g.y, ur, sbi1);
+                sbi2 = fmaf(g.x, ui, sbi2);
+            }
+            sar = fmaf(g.x, vr, fmaf(g.y, vi, sar));
+            sai1 = fmaf(g.y, vr, sai1);
+            sai2 = fmaf(g.x, vi, sai2);
+        };
+        if (wact) {
+            for (int sb = 0; sb < nv; sb += 16) {
+                gb[gput] = gnext;
+                __syncwarp();
+                {
+                    const int k = k0 + sb + 16 + (lane & 15);
+                    gnext = (grow != nullptr && k < n) ? grow[k] : make_float2(0.f, 0.f);
+                }
+                if (sb + 16 <= nv) {
+#pragma unroll
+                    for (int t = 0; t < 16; ++t) step(w[sb + t], gr[t]);
+                } else {
+                    for (int t = 0; t < nv - sb; ++t) step(w[sb + t], gr[t]);
+                }
+                __syncwarp();
+            }
+        }
+        Tbr += sbr;
+        Tbi += sbi1 - sbi2;
+        Tar += sar;
+        Tai += sai1 - sai2;
+        __syncthreads();   // every warp is done with this buffer before it is refilled
+    }
+    if (ln.x >= 0) {
+        float *acc = A.acc + ((int64_t)det * A.n_slots + ln.x) * 6;
+        acc[0] = 0.f;
+        acc[1] = 0.f;
+        acc[2] = br * Tar + bi * Tai;   // conj(b) sum g_z conj(v)
+        acc[3] = br * Tai - bi * Tar;
+        if (GB) {
+            acc[4] = Tbr;
+            acc[5] = Tbi;
+        }
     }
 }
 
@@ -434,7 +677,7 @@ constexpr int kProjAhead = 8;
 
 __global__ void __launch_bounds__(128) adj_project_kernel(
     const float4 *params, const int32_t *slot_tmpl, const float2 *gz, int64_t n_slots, int D,
-    int64_t T, int64_t n, int64_t seg_len, int P, float2 *E)
+    int64_t T, int64_t n, int64_t seg_len, int64_t off, int P, float2 *E)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t per4 = (int64_t)D * n_slots / kProjSlots;
@@ -460,7 +703,7 @@ __global__ void __launch_bounds__(128) adj_project_kernel(
         const uint64_t AR1 = pk(ar[2], ar[3]), AI1 = pk(ai[2], ai[3]);
         const uint64_t NAI1 = pk(-ai[2], -ai[3]);
         const float2 *g = gz + ((int64_t)det * T + tmpl) * n;
-        const int64_t j0 = (int64_t)q * seg_len, j1 = min(n, j0 + seg_len);
+        const int64_t j0 = (int64_t)q * seg_len + off, j1 = min(n, j0 + seg_len);
         int64_t j = j1;
         // whole groups of kProjAhead samples from the segment's end, then the rest
         for (; j - kProjAhead >= j0; j -= kProjAhead) {
@@ -522,10 +765,11 @@ __device__ void conj_pow(double ar, double ai, int64_t len, double &rr, double &
     }
 }
 
-// mu_end[P-1] = 0; mu_end[q] = E[q+1] + conj(a)^len(q+1) mu_end[q+1] (FP64);
-// every segment but the last has seg_len samples
+// mu_end[P-1] = 0; mu_end[q] = E[q+1] + conj(a)^len(q+1) mu_end[q+1] (FP64),
+// len(q) = the samples of [q seg_len + off, (q + 1) seg_len + off) inside the
+// call: seg_len, except for the one segment the call's end cuts (and 0 past it)
 __global__ void adj_carry_kernel(const float4 *params, const float2 *E, int64_t n_slots, int D,
-                                 int64_t n, int64_t seg_len, int P, float2 *mu_end)
+                                 int64_t n, int64_t seg_len, int64_t off, int P, float2 *mu_end)
 {
     const int64_t ds = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t per = (int64_t)D * n_slots;
@@ -533,13 +777,18 @@ __global__ void adj_carry_kernel(const float4 *params, const float2 *E, int64_t 
     const int64_t s = ds % n_slots;
     const float4 p = params[s];
     const double ar = p.x, ai = (s & 1) ? -(double)p.y : (double)p.y;
-    double fr, fi, lr, li;   // powers for a whole segment and for the last one
+    double fr, fi, lr, li;   // powers for a whole segment and for the cut one
     conj_pow(ar, ai, seg_len, fr, fi);
-    conj_pow(ar, ai, n - (int64_t)(P - 1) * seg_len, lr, li);
+    int64_t cut = -1;        // the segment holding the call's end, and its length
+    for (int q = 1; q < P; ++q) {
+        const int64_t j0 = (int64_t)q * seg_len + off;
+        if (j0 < n && j0 + seg_len > n) cut = q;
+    }
+    if (cut >= 0) conj_pow(ar, ai, n - (cut * seg_len + off), lr, li);
     double mr = 0.0, mi = 0.0;
     mu_end[(int64_t)(P - 1) * per + ds] = make_float2(0.f, 0.f);
     for (int q = P - 2; q >= 0; --q) {
-        const bool last = q + 1 == P - 1;
+        const bool last = q + 1 == cut;
         const double rr = last ? lr : fr, ri = last ? li : fi;
         const float2 e = E[(int64_t)(q + 1) * per + ds];
         const double nr = (double)e.x + rr * mr - ri * mi;
@@ -583,28 +832,61 @@ cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s)
 int k7_smem_bytes(int Dh, int W, int G)
 {
     return (int)(sizeof(float) * ((G == 16 ? 2 : 1) * 2 * (kK7Chunk + Dh) + W * 1024 +
-                                  W * kK7Chunk));
+                                  W * kK7Chunk + kK7Chunk));
+}
+
+template <bool TAN>
+cudaError_t launch_k7_form(const K7Args &a, cudaStream_t s)
+{
+    const int smem = k7_smem_bytes(a.Dh, a.W, a.G);
+    // two tasks per warp (two independent chains per lane), one for half-warp
+    // templates (a unit is then a single task)
+    const void *fn = a.G == 16 ? reinterpret_cast<const void *>(k7_adjoint_x<1, TAN>)
+                               : reinterpret_cast<const void *>(k7_adjoint_x<2, TAN>);
+    cudaError_t e = ensure_smem_limit(fn, smem);
+    if (e != cudaSuccess) return e;
+    const unsigned grid = (unsigned)((int64_t)a.P * a.n_units * a.n_det);
+    if (a.G == 16)
+        k7_adjoint_x<1, TAN><<<grid, a.W * 32, smem, s>>>(a);
+    else
+        k7_adjoint_x<2, TAN><<<grid, a.W * 32, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_k7(const K7Args &a, cudaStream_t s)
 {
     if (a.n_units <= 0 || a.n <= 0) return cudaSuccess;
-    // segments of whole 32-output blocks: only the call's last block runs
-    // past its end (on zero input)
-    if (a.W < 1 || a.W > kK7MaxWarps || a.S % 32 != 0 || (a.P > 1 && a.seeds == nullptr))
+    const bool tan = a.acc != nullptr;
+    // segments of whole 32-output blocks (whole chunks for the warm-up): only
+    // the call's last block runs past its end (on zero input)
+    if (a.W < 1 || a.W > kK7MaxWarps || a.S % 32 != 0 || (a.P > 1 && a.seeds == nullptr) ||
+        (tan && (a.xe == nullptr || a.Dh % kK7Chunk != 0 || a.S % kK7Chunk != 0)))
         return cudaErrorInvalidValue;
-    const int smem = k7_smem_bytes(a.Dh, a.W, a.G);
-    // two tasks per warp (two independent chains per lane), one for half-warp
-    // templates (a unit is then a single task)
-    const void *fn = a.G == 16 ? reinterpret_cast<const void *>(k7_adjoint_x<1>)
-                               : reinterpret_cast<const void *>(k7_adjoint_x<2>);
+    return tan ? launch_k7_form<true>(a, s) : launch_k7_form<false>(a, s);
+}
+
+int kt_smem_bytes(int Dh, int Tb, int W)
+{
+    return (int)(sizeof(float) * 2 * (Dh + Tb) + sizeof(float2) * 36 * W);
+}
+
+cudaError_t launch_kt(const KTArgs &a, int D, cudaStream_t s)
+{
+    if (a.n_pos <= 0 || a.n <= 0 || D <= 0) return cudaSuccess;
+    if (a.W < 1 || a.W > 8 || a.n_pos % 32 != 0 || a.Tb % 16 != 0 || a.Dh % 4 != 0 ||
+        a.xe_stride % 4 != 0 || (reinterpret_cast<uintptr_t>(a.xe) & 15) != 0)
+        return cudaErrorInvalidValue;
+    const int smem = kt_smem_bytes(a.Dh, a.Tb, a.W);
+    const void *fn = a.with_gb ? reinterpret_cast<const void *>(kt_tangent<true>)
+                               : reinterpret_cast<const void *>(kt_tangent<false>);
     cudaError_t e = ensure_smem_limit(fn, smem);
     if (e != cudaSuccess) return e;
-    const unsigned grid = (unsigned)((int64_t)a.P * a.n_units * a.n_det);
-    if (a.G == 16)
-        k7_adjoint_x<1><<<grid, a.W * 32, smem, s>>>(a);
+    const int64_t warps = a.n_pos / 32;
+    const dim3 grid((unsigned)((warps + a.W - 1) / a.W), (unsigned)D);
+    if (a.with_gb)
+        kt_tangent<true><<<grid, a.W * 32, smem, s>>>(a);
     else
-        k7_adjoint_x<2><<<grid, a.W * 32, smem, s>>>(a);
+        kt_tangent<false><<<grid, a.W * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -620,7 +902,7 @@ cudaError_t launch_adj_finalize(const float *acc, const int64_t *slot_filter, in
 
 cudaError_t launch_adj_project(const float4 *params, const int32_t *slot_tmpl, const float2 *gz,
                                int64_t n_slots, int D, int64_t T, int64_t n, int64_t seg_len,
-                               int P, float2 *E, float2 *mu_end, cudaStream_t s)
+                               int64_t off, int P, float2 *E, float2 *mu_end, cudaStream_t s)
 {
     const int64_t per = (int64_t)D * n_slots;
     if (per <= 0 || P < 1) return cudaSuccess;
@@ -628,12 +910,12 @@ cudaError_t launch_adj_project(const float4 *params, const int32_t *slot_tmpl, c
         if (n_slots % kProjSlots != 0) return cudaErrorInvalidValue;
         const int64_t th = (int64_t)(P - 1) * per / kProjSlots;
         adj_project_kernel<<<(unsigned)((th + 127) / 128), 128, 0, s>>>(
-            params, slot_tmpl, gz, n_slots, D, T, n, seg_len, P, E);
+            params, slot_tmpl, gz, n_slots, D, T, n, seg_len, off, P, E);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     adj_carry_kernel<<<(unsigned)((per + 63) / 64), 64, 0, s>>>(params, E, n_slots, D, n, seg_len,
-                                                                 P, mu_end);
+                                                                 off, P, mu_end);
     return cudaGetLastError();
 }
 

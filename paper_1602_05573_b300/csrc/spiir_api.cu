@@ -183,6 +183,9 @@ struct Band {
     int64_t adj_n_units7 = 0;
     int adj_W7 = 1;                // warps per input-gradient CTA (largest unit)
     float2 *adj_seeds = nullptr;   // [P-1][D][n_slots] input-gradient segment seeds
+    int2 *kt_lanes = nullptr;      // tangent form: lanes in tangent order (slot, 0/1)
+    int2 *kt_warp_tmpl = nullptr;  //   the two templates of every warp
+    int64_t kt_n_pos = 0;          //   lanes (multiple of 32)
 };
 
 struct spiir_plan {
@@ -290,6 +293,8 @@ void free_band(Band &b)
     cudaFree(b.adj_units7);
     cudaFree(b.fir);
     cudaFree(b.adj_seeds);
+    cudaFree(b.kt_lanes);
+    cudaFree(b.kt_warp_tmpl);
     b = Band();
 }
 
@@ -487,6 +492,8 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
     if (opt.tile_chunks < 0) return fail(SPIIR_EINVAL, "tile_chunks must be >= 0");
     if (opt.persistent < 0 || opt.persistent > 2)
         return fail(SPIIR_EINVAL, "persistent must be 0 (auto), 1 (off) or 2 (on)");
+    if (opt.adjoint_form < SPIIR_ADJOINT_AUTO || opt.adjoint_form > SPIIR_ADJOINT_TANGENT)
+        return fail(SPIIR_EINVAL, "adjoint_form must be 0 (auto), 1 (reverse) or 2 (tangent)");
     if (opt.tail_split < -1 || opt.tail_split > 200)
         return fail(SPIIR_EINVAL, "tail_split must be -1 (off), 0 (auto) or 1..200 per mille");
     if (opt.precision == SPIIR_PREC_CHUNKED_TC && opt.chunk_len != spiir::kTcT)
@@ -1436,6 +1443,89 @@ spiir_status build_adjoint_tasks(Band &b, int D)
     return SPIIR_OK;
 }
 
+// Tangent order of a band's filters: grouped by template (bank order), each
+// warp of 32 lanes spanning at most two templates (a third starts a new
+// warp), and within a template filters dealt round-robin over their delays
+// mod 32, so that neighbouring lanes read strain at different banks.
+spiir_status build_tangent_order(Band &b, int64_t T)
+{
+    const spiir::Layout &L = b.lay;
+    std::vector<std::vector<int64_t>> per((size_t)T);
+    for (int64_t s = 0; s < L.n_slots; ++s)
+        if (L.slot_filter[s] >= 0 && L.slot_template[s] >= 0) per[L.slot_template[s]].push_back(s);
+    std::vector<int32_t> lanes, wtmpl;
+    int c = 0, t0 = -1, t1 = -1;
+    auto close_warp = [&]() {
+        for (; c < 32; ++c) {
+            lanes.push_back(-1);
+            lanes.push_back(0);
+        }
+        wtmpl.push_back(t0);
+        wtmpl.push_back(t1);
+        c = 0;
+        t0 = t1 = -1;
+    };
+    for (int64_t t = 0; t < T; ++t) {
+        std::vector<std::vector<int64_t>> bucket(32);
+        for (int64_t s : per[t]) {
+            const int d = L.Dh - L.ringoff[2 * s];
+            bucket[((d % 32) + 32) % 32].push_back(s);
+        }
+        std::vector<int64_t> order;
+        for (size_t r = 0; order.size() < per[t].size(); ++r)
+            for (int k = 0; k < 32; ++k)
+                if (r < bucket[k].size()) order.push_back(bucket[k][r]);
+        for (int64_t s : order) {
+            if (c == 32) close_warp();
+            int li;
+            if ((int64_t)t0 == t) li = 0;
+            else if ((int64_t)t1 == t) li = 1;
+            else if (t0 < 0) { t0 = (int)t; li = 0; }
+            else if (t1 < 0) { t1 = (int)t; li = 1; }
+            else { close_warp(); t0 = (int)t; li = 0; }
+            if (s > INT32_MAX) return fail(SPIIR_EUNSUPPORTED, "tangent form: slot index above 2^31");
+            lanes.push_back((int32_t)s);
+            lanes.push_back(li);
+            ++c;
+        }
+    }
+    if (c > 0) close_warp();
+    cudaError_t e;
+    if ((e = dalloc(&b.kt_lanes, lanes.size() / 2)) != cudaSuccess ||
+        (e = cudaMemcpy(b.kt_lanes, lanes.data(), lanes.size() * sizeof(int32_t),
+                        cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = dalloc(&b.kt_warp_tmpl, std::max<size_t>(1, wtmpl.size() / 2))) != cudaSuccess ||
+        (wtmpl.size() > 0 &&
+         (e = cudaMemcpy(b.kt_warp_tmpl, wtmpl.data(), wtmpl.size() * sizeof(int32_t),
+                         cudaMemcpyHostToDevice)) != cudaSuccess))
+        return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "tangent lane order")
+                                              : cuda_fail(e, "tangent lane order upload");
+    b.kt_n_pos = (int64_t)lanes.size() / 2;
+    return SPIIR_OK;
+}
+
+// Warps per tangent CTA: the fewest per-SM warps over the launch (one wave:
+// the busiest SM's warps; several: the mean), larger W on ties.
+int tangent_warps_per_cta(int64_t warps, int D, int Dh, int Tb, int n_sm)
+{
+    int best = 1;
+    double best_cost = 1e300;
+    for (int W = 1; W <= 8; W *= 2) {
+        const int smem = spiir::kt_smem_bytes(Dh, Tb, W);
+        if (smem > 227 * 1024) continue;
+        const int64_t per_sm = std::min<int64_t>({32, (228 * 1024) / (smem + 1024), 32 / W});
+        if (per_sm < 1) continue;
+        const int64_t ctas = (warps + W - 1) / W * D;
+        const double cost = ctas <= per_sm * n_sm ? (double)W * ((ctas + n_sm - 1) / n_sm)
+                                                  : (double)W * ctas / n_sm;
+        if (cost <= best_cost) {
+            best_cost = cost;
+            best = W;
+        }
+    }
+    return best;
+}
+
 spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
                                    const float *grad_z_dev, float *grad_a_dev,
                                    float *grad_b_dev, float *grad_x_dev, void *stream)
@@ -1462,29 +1552,54 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         return err == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "adjoint workspace")
                                                 : cuda_fail(err, "cudaMalloc");
     };
-    if (!b.bw_xe || b.bw_cap < need || b.ckpt_cap < nc) {
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
-            return cuda_fail(e, "cudaStreamSynchronize");
-        cudaFree(b.bw_xe);
-        cudaFree(b.ckpt);
-        b.bw_xe = nullptr;
-        b.ckpt = nullptr;
-        b.bw_xe_stride = L.Dh + need;
-        if ((e = dalloc(&b.bw_xe, (size_t)D * b.bw_xe_stride)) != cudaSuccess) return oom(e);
-        if ((e = dalloc(&b.ckpt, (size_t)nc * D * L.n_slots)) != cudaSuccess) return oom(e);
-        b.bw_cap = need;
-        b.ckpt_cap = nc;
-    }
-    if (!b.bw_state) {
-        if ((e = dalloc(&b.bw_state, (size_t)D * L.n_slots)) != cudaSuccess) return oom(e);
-    }
     if (!b.adj_tasks) {
         spiir_status st = build_adjoint_tasks(b, D);
         if (st != SPIIR_OK) return st;
     }
-    // time segments of whole chunks for the reverse pass (options.time_segments,
-    // or enough CTAs for about four waves of 16 warps per SM, at most 16
-    // segments), each at least one chunk
+    // g_a, g_b: tangent or reverse form
+    // (the tangent form's input-gradient pass warms up over whole 256-sample
+    // chunks: history and checkpoint interval must be whole chunks)
+    bool tangent = false;
+    if (p->opt.adjoint_form != SPIIR_ADJOINT_REVERSE &&
+        spiir::kt_smem_bytes(L.Dh, L.Tb, 1) <= 227 * 1024 &&
+        (!grad_x_dev || (L.Dh % spiir::kK7Chunk == 0 && Cc % spiir::kK7Chunk == 0))) {
+        if (!b.kt_lanes) {
+            spiir_status st = build_tangent_order(b, p->T);
+            if (st != SPIIR_OK) return st;
+        }
+        tangent = p->opt.adjoint_form == SPIIR_ADJOINT_TANGENT ||
+                  (b.kt_n_pos / 32) * D >= 8 * (int64_t)p->n_sm;
+    }
+    if (p->opt.adjoint_form == SPIIR_ADJOINT_TANGENT && !tangent)
+        return fail(SPIIR_EUNSUPPORTED,
+                    "tangent adjoint: strain window above 227 KB, or history or checkpoint "
+                    "interval not a multiple of 256 samples");
+    const bool need_ckpt = !tangent;
+    if (!b.bw_xe || b.bw_cap < need || (need_ckpt && b.ckpt_cap < nc)) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+            return cuda_fail(e, "cudaStreamSynchronize");
+        if (!b.bw_xe || b.bw_cap < need) {
+            cudaFree(b.bw_xe);
+            b.bw_xe = nullptr;
+            b.bw_cap = 0;
+            b.bw_xe_stride = L.Dh + need;
+            if ((e = dalloc(&b.bw_xe, (size_t)D * b.bw_xe_stride)) != cudaSuccess) return oom(e);
+            b.bw_cap = need;
+        }
+        if (need_ckpt && b.ckpt_cap < nc) {
+            cudaFree(b.ckpt);
+            b.ckpt = nullptr;
+            b.ckpt_cap = 0;
+            if ((e = dalloc(&b.ckpt, (size_t)nc * D * L.n_slots)) != cudaSuccess) return oom(e);
+            b.ckpt_cap = nc;
+        }
+    }
+    if (!b.bw_state) {
+        if ((e = dalloc(&b.bw_state, (size_t)D * L.n_slots)) != cudaSuccess) return oom(e);
+    }
+    // time segments of whole chunks for the reverse pass and the input-gradient
+    // pass (options.time_segments, or enough CTAs for about four waves of 16
+    // warps per SM, at most 16 segments), each at least one chunk
     int P = 1;
     {
         const int64_t warps = b.adj_n_units * b.adj_W;
@@ -1504,6 +1619,7 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         cudaFree(b.adj_seeds);
         b.acc = nullptr;
         b.adj_E = b.adj_mu = b.adj_seeds = nullptr;
+        b.adj_seg_cap = 0;
         if ((e = dalloc(&b.acc, (size_t)P * D * L.n_slots * 6)) != cudaSuccess ||
             (e = dalloc(&b.adj_E, (size_t)P * D * L.n_slots)) != cudaSuccess ||
             (e = dalloc(&b.adj_mu, (size_t)P * D * L.n_slots)) != cudaSuccess ||
@@ -1511,118 +1627,151 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
             return oom(e);
         b.adj_seg_cap = P;
     }
-    // zero history + x, zero state and accumulators, zero g_x
+    // zero history + x (and, for the reverse form, zero state and accumulators), zero g_x
     if ((e = cudaMemset2DAsync(b.bw_xe, b.bw_xe_stride * 4, 0, (size_t)L.Dh * 4, D, s)) !=
             cudaSuccess ||
         (e = cudaMemcpy2DAsync(b.bw_xe + L.Dh, b.bw_xe_stride * 4, x_dev, n * 4, n * 4, D,
                                cudaMemcpyDeviceToDevice, s)) != cudaSuccess ||
-        (e = cudaMemsetAsync(b.bw_state, 0, sizeof(float2) * (size_t)D * L.n_slots, s)) !=
-            cudaSuccess ||
-        (e = cudaMemsetAsync(b.acc, 0, sizeof(float) * 6 * (size_t)P * D * L.n_slots, s)) !=
-            cudaSuccess ||
+        (!tangent &&
+         (e = cudaMemsetAsync(b.bw_state, 0, sizeof(float2) * (size_t)D * L.n_slots, s)) !=
+             cudaSuccess) ||
+        ((!tangent || grad_x_dev) &&
+         (e = cudaMemsetAsync(b.acc, 0, sizeof(float) * 6 * (size_t)P * D * L.n_slots, s)) !=
+             cudaSuccess) ||
         (grad_x_dev &&
          (e = cudaMemsetAsync(grad_x_dev, 0, sizeof(float) * (size_t)D * n, s)) != cudaSuccess))
         return cuda_fail(e, "adjoint staging");
-    // forward pass from zero state, keeping the state every Cc samples
-    spiir::K1Args f{};
-    f = k1_args(p, b, n, nullptr, n, false);
-    f.mode = spiir::kModePlain;   // checkpoints come from the FP32 recurrence
-    f.xe = b.bw_xe;
-    f.xe_stride = b.bw_xe_stride;
-    f.state = b.bw_state;
-    f.t0 = 0;
-    f.ckpt = b.ckpt;
-    f.ckpt_blocks = Cc / L.Tb;
-    f.n_det = D;
-    // the forward also keeps the state at every 16-sample span start when that
-    // fits a quarter of free memory (at most 8 GiB): the reverse pass then
-    // skips its per-chunk recompute
-    {
-        const int64_t want = ((n + 15) / 16) * D * L.n_slots;
-        size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
-        const int64_t budget = std::min<int64_t>((int64_t)8 << 30, (int64_t)(free_b / 4));
-        if (b.adj_sub16_cap < want && want * (int64_t)sizeof(float2) <= budget) {
+    p->last_launches = 0;
+    if (grad_x_dev &&
+        spiir::k7_smem_bytes(L.Dh, L.G == 16 ? b.adj_W7 : (b.adj_W7 + 1) / 2, L.G) > 227 * 1024)
+        return fail(SPIIR_EUNSUPPORTED, "adjoint windows above 227 KB of shared memory");
+    spiir::K6Args a{};
+    a.seeds = (P > 1 && grad_x_dev) ? b.adj_seeds : nullptr;
+    if (tangent) {
+        // g_a, g_b: one forward pass of the derivative recurrences
+        spiir::KTArgs t{};
+        t.xe = b.bw_xe;
+        t.xe_stride = b.bw_xe_stride;
+        t.n = (int32_t)n;
+        t.Dh = L.Dh;
+        t.Tb = L.Tb;
+        t.W = tangent_warps_per_cta(b.kt_n_pos / 32, D, L.Dh, L.Tb, p->n_sm);
+        t.gz = reinterpret_cast<const float2 *>(grad_z_dev);
+        t.T = p->T;
+        t.lanes = b.kt_lanes;
+        t.warp_tmpl = b.kt_warp_tmpl;
+        t.n_pos = b.kt_n_pos;
+        t.params = b.params;
+        t.ringoff = b.ringoff;
+        t.n_slots = L.n_slots;
+        t.acc = b.acc;
+        t.with_gb = grad_x_dev == nullptr;   // else the input-gradient pass sums g_b
+        const int tt = time_begin(p, s);
+        if ((e = spiir::launch_kt(t, D, s)) != cudaSuccess)
+            return cuda_fail(e, "tangent adjoint launch");
+        time_end(p, s, tt, kTimeAdj);
+        p->last_launches += 1;
+    } else {
+        // forward pass from zero state, keeping the state every Cc samples
+        spiir::K1Args f{};
+        f = k1_args(p, b, n, nullptr, n, false);
+        f.mode = spiir::kModePlain;   // checkpoints come from the FP32 recurrence
+        f.xe = b.bw_xe;
+        f.xe_stride = b.bw_xe_stride;
+        f.state = b.bw_state;
+        f.t0 = 0;
+        f.ckpt = b.ckpt;
+        f.ckpt_blocks = Cc / L.Tb;
+        f.n_det = D;
+        // the forward also keeps the state at every 16-sample span start when that
+        // fits a quarter of free memory (at most 8 GiB): the reverse pass then
+        // skips its per-chunk recompute
+        {
+            const int64_t want = ((n + 15) / 16) * D * L.n_slots;
+            size_t free_b = 0, total_b = 0;
+            if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+            const int64_t budget = std::min<int64_t>((int64_t)8 << 30, (int64_t)(free_b / 4));
+            if (b.adj_sub16_cap < want && want * (int64_t)sizeof(float2) <= budget) {
+                if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
+                    return cuda_fail(e, "cudaStreamSynchronize");
+                cudaFree(b.adj_sub16);
+                b.adj_sub16 = nullptr;
+                b.adj_sub16_cap = 0;
+                if (dalloc(&b.adj_sub16, (size_t)want) == cudaSuccess) b.adj_sub16_cap = want;
+                else (void)cudaGetLastError();   // fall back to the per-chunk recompute
+            }
+            f.sub16 = (b.adj_sub16_cap >= want && p->precision == SPIIR_PREC_PLAIN) ? b.adj_sub16
+                                                                                     : nullptr;
+        }
+        if (p->precision == SPIIR_PREC_PLAIN) {
+            // time-segmented like a plain call when the bank is small (checkpoints
+            // are written at whole intervals from the call's start either way)
+            const int saved = p->last_segments;
+            spiir_status st = launch_segmented(p, b, f, segments_for(p, b, n), s);
+            p->last_segments = saved;
+            if (st != SPIIR_OK) return st;
+        } else {
+            const int tf = time_begin(p, s);
+            if ((e = spiir::launch_k1(f, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
+                return cuda_fail(e, "adjoint forward launch");
+            time_end(p, s, tf, kTimeK1);
+            p->last_launches += 1;
+        }
+        // reverse pass: projection of the adjoint state to segment ends, then
+        // every segment's reverse pass at once
+        if ((e = spiir::launch_adj_project(b.params, b.adj_slot_tmpl,
+                                           reinterpret_cast<const float2 *>(grad_z_dev), L.n_slots,
+                                           D, p->T, n, cps * Cc, 0, P, b.adj_E, b.adj_mu, s)) !=
+            cudaSuccess)
+            return cuda_fail(e, "adjoint projection launch");
+        const int64_t sub_need = (int64_t)P * b.adj_n_units * b.adj_W * spiir::kAdjRounds *
+                                 (Cc / spiir::kAdjSub) * 32;
+        if (b.adj_sub_cap < sub_need) {
             if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
                 return cuda_fail(e, "cudaStreamSynchronize");
-            cudaFree(b.adj_sub16);
-            b.adj_sub16 = nullptr;
-            b.adj_sub16_cap = 0;
-            if (dalloc(&b.adj_sub16, (size_t)want) == cudaSuccess) b.adj_sub16_cap = want;
-            else (void)cudaGetLastError();   // fall back to the per-chunk recompute
+            cudaFree(b.adj_sub);
+            b.adj_sub = nullptr;
+            if ((e = dalloc(&b.adj_sub, (size_t)sub_need)) != cudaSuccess) return oom(e);
+            b.adj_sub_cap = sub_need;
         }
-        f.sub16 = (b.adj_sub16_cap >= want && p->precision == SPIIR_PREC_PLAIN) ? b.adj_sub16
-                                                                                 : nullptr;
+        a.xe = b.bw_xe;
+        a.xe_stride = b.bw_xe_stride;
+        a.n = (int32_t)n;
+        a.Dh = L.Dh;
+        a.W = b.adj_W;
+        a.Cc = Cc;
+        a.gz = reinterpret_cast<const float2 *>(grad_z_dev);
+        a.T = p->T;
+        a.units = b.adj_units;
+        a.tasks = b.adj_tasks;
+        a.round_stride = L.W * 32;
+        a.G = L.G;
+        a.params = b.params;
+        a.ringoff = b.ringoff;
+        a.ckpt = b.ckpt;
+        a.n_slots = L.n_slots;
+        a.n_det = D;
+        a.acc = b.acc;
+        a.sub = b.adj_sub;
+        a.n_units = (int32_t)b.adj_n_units;
+        a.cps = (int32_t)cps;
+        a.P = P;
+        a.sub16 = f.sub16;
+        a.mu_end = P > 1 ? b.adj_mu : nullptr;
+        if (spiir::k6_smem_bytes(Cc, L.Dh) > 227 * 1024)
+            return fail(SPIIR_EUNSUPPORTED, "adjoint windows above 227 KB of shared memory");
+        const int ta = time_begin(p, s);
+        if ((e = spiir::launch_k6(a, b.adj_n_units, s)) != cudaSuccess)
+            return cuda_fail(e, "adjoint kernel launch");
+        time_end(p, s, ta, kTimeAdj);
+        // projection (+ carry), reverse pass
+        p->last_launches += (P > 1 ? 2 : 1) + 1;
     }
-    p->last_launches = 0;
-    if (p->precision == SPIIR_PREC_PLAIN) {
-        // time-segmented like a plain call when the bank is small (checkpoints
-        // are written at whole intervals from the call's start either way)
-        const int saved = p->last_segments;
-        spiir_status st = launch_segmented(p, b, f, segments_for(p, b, n), s);
-        p->last_segments = saved;
-        if (st != SPIIR_OK) return st;
-    } else {
-        const int tf = time_begin(p, s);
-        if ((e = spiir::launch_k1(f, L.n_units(), L.smem_bytes(), s)) != cudaSuccess)
-            return cuda_fail(e, "adjoint forward launch");
-        time_end(p, s, tf, kTimeK1);
-        p->last_launches += 1;
-    }
-    // reverse pass: projection of the adjoint state to segment ends, then
-    // every segment's reverse pass at once
-    if ((e = spiir::launch_adj_project(b.params, b.adj_slot_tmpl,
-                                       reinterpret_cast<const float2 *>(grad_z_dev), L.n_slots, D,
-                                       p->T, n, cps * Cc, P, b.adj_E, b.adj_mu, s)) != cudaSuccess)
-        return cuda_fail(e, "adjoint projection launch");
-    const int64_t sub_need = (int64_t)P * b.adj_n_units * b.adj_W * spiir::kAdjRounds *
-                             (Cc / spiir::kAdjSub) * 32;
-    if (b.adj_sub_cap < sub_need) {
-        if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
-            return cuda_fail(e, "cudaStreamSynchronize");
-        cudaFree(b.adj_sub);
-        b.adj_sub = nullptr;
-        if ((e = dalloc(&b.adj_sub, (size_t)sub_need)) != cudaSuccess) return oom(e);
-        b.adj_sub_cap = sub_need;
-    }
-    spiir::K6Args a{};
-    a.xe = b.bw_xe;
-    a.xe_stride = b.bw_xe_stride;
-    a.n = (int32_t)n;
-    a.Dh = L.Dh;
-    a.W = b.adj_W;
-    a.Cc = Cc;
-    a.gz = reinterpret_cast<const float2 *>(grad_z_dev);
-    a.T = p->T;
-    a.units = b.adj_units;
-    a.tasks = b.adj_tasks;
-    a.round_stride = L.W * 32;
-    a.G = L.G;
-    a.params = b.params;
-    a.ringoff = b.ringoff;
-    a.ckpt = b.ckpt;
-    a.n_slots = L.n_slots;
-    a.n_det = D;
-    a.acc = b.acc;
-    a.seeds = (P > 1 && grad_x_dev) ? b.adj_seeds : nullptr;
-    a.sub = b.adj_sub;
-    a.n_units = (int32_t)b.adj_n_units;
-    a.cps = (int32_t)cps;
-    a.P = P;
-    a.sub16 = f.sub16;
-    a.mu_end = P > 1 ? b.adj_mu : nullptr;
-    if (spiir::k6_smem_bytes(Cc, L.Dh) > 227 * 1024 ||
-        (grad_x_dev &&
-         spiir::k7_smem_bytes(L.Dh, L.G == 16 ? b.adj_W7 : (b.adj_W7 + 1) / 2, L.G) > 227 * 1024))
-        return fail(SPIIR_EUNSUPPORTED, "adjoint windows above 227 KB of shared memory");
-    const int ta = time_begin(p, s);
-    if ((e = spiir::launch_k6(a, b.adj_n_units, s)) != cudaSuccess)
-        return cuda_fail(e, "adjoint kernel launch");
-    time_end(p, s, ta, kTimeAdj);
     if (grad_x_dev) {
-        // input gradient in the shifted frame, seeded by the reverse pass
+        // input gradient in the shifted frame; its segment seeds come from the
+        // reverse pass, or (tangent form) from its own projection + carry
         spiir::K7Args g{};
-        g.gz = a.gz;
+        g.gz = reinterpret_cast<const float2 *>(grad_z_dev);
         g.T = p->T;
         g.n = (int32_t)n;
         g.Dh = L.Dh;
@@ -1632,7 +1781,7 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         g.units = b.adj_units7;
         g.n_units = (int32_t)b.adj_n_units7;
         g.W = L.G == 16 ? b.adj_W7 : (b.adj_W7 + 1) / 2;
-        g.round_stride = a.round_stride;
+        g.round_stride = L.W * 32;
         g.G = L.G;
         g.params = b.params;
         g.ringoff = b.ringoff;
@@ -1641,18 +1790,31 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         g.seeds = a.seeds;
         g.gx = grad_x_dev;
         const int tg = time_begin(p, s);
+        if (tangent) {
+            // seeds: mu at (q + 1) S + Dh from the reverse projection over
+            // segments shifted by Dh; the pass also sums g_b
+            if ((e = spiir::launch_adj_project(b.params, b.adj_slot_tmpl, g.gz, L.n_slots, D,
+                                               p->T, n, g.S, L.Dh, P, b.adj_E, b.adj_seeds, s)) !=
+                cudaSuccess)
+                return cuda_fail(e, "input-gradient projection launch");
+            g.seeds = P > 1 ? b.adj_seeds : nullptr;
+            g.xe = b.bw_xe;
+            g.xe_stride = b.bw_xe_stride;
+            g.acc = b.acc;
+            p->last_launches += P > 1 ? 2 : 1;
+        }
         if ((e = spiir::launch_k7(g, s)) != cudaSuccess)
             return cuda_fail(e, "adjoint input-gradient launch");
         time_end(p, s, tg, kTimeAdj);
         p->last_launches += 1;
     }
-    if ((e = spiir::launch_adj_finalize(b.acc, b.slot_filter, L.n_slots, D, P,
+    if ((e = spiir::launch_adj_finalize(b.acc, b.slot_filter, L.n_slots, D,
+                                        (tangent && !grad_x_dev) ? 1 : P,
                                         reinterpret_cast<float2 *>(grad_a_dev),
                                         reinterpret_cast<float2 *>(grad_b_dev), s)) !=
         cudaSuccess)
         return cuda_fail(e, "adjoint finalize launch");
-    // forward launches (counted above), projection (+ carry), reverse pass, finalize
-    p->last_launches += (P > 1 ? 2 : 1) + 2;
+    p->last_launches += 1;
     return SPIIR_OK;
 }
 

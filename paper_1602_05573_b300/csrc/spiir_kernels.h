@@ -143,25 +143,58 @@ struct K7Args {
     const int2 *ringoff;
     int64_t n_slots;
     int32_t n_det;
-    const float2 *seeds;       // [P-1][D][n_slots]: mu at the top of the 16-sample span
-                               //  holding (q + 1) S + d, natural form
+    const float2 *seeds;       // [P-1][D][n_slots] natural form: mu at the top of the
+                               //  16-sample span holding (q + 1) S + d (reverse form), or
+                               //  (tangent form, acc != null) mu at (q + 1) S + Dh
     float *gx;                 // [D][n], zeroed by the caller; CTAs add with atomics
+    // tangent form: the input-gradient pass also sums g_b = sum_m nu[m] x[m]
+    const float *xe;           // [D][xe_stride]: Dh zeros, then x
+    int64_t xe_stride;
+    float *acc;                // [P][D][n_slots][6]: entries 4, 5 (g_b) written; null =
+                               //  reverse form
 };
 constexpr int kK7Chunk = 256;   // outputs per staged g_z window
 constexpr int kK7MaxWarps = 8;
 cudaError_t launch_k7(const K7Args &a, cudaStream_t s);
+
+// Gradients of a and b in tangent (forward-mode) form, one filter per lane.
+// Lanes follow the tangent order: filters grouped by template, each warp
+// spanning at most two templates, lanes of a template ordered so that
+// neighbours read strain at different banks.
+struct KTArgs {
+    const float *xe;           // [D][xe_stride]: Dh zeros, then the call's strain; rows
+    int64_t xe_stride;         //  16-byte aligned and >= Dh + ceil(n / Tb) Tb long
+    int32_t n, Dh, Tb;         // samples; history (>= max delay, multiple of 4); block
+                               //  (multiple of 16)
+    int32_t W;                 // warps per CTA
+    const float2 *gz;          // [D][T][n]
+    int64_t T;
+    const int2 *lanes;         // [n_pos] (slot, 0/1: the warp's first or second template);
+                               //  slot -1 = an empty lane
+    const int2 *warp_tmpl;     // [n_pos / 32] the warp's two templates (-1: none)
+    int64_t n_pos;             // lanes, a multiple of 32
+    const float4 *params;      // kernel form (odd slots hold conj(a), (Im b, Re b))
+    const int2 *ringoff;       // (Dh - d, .) per slot
+    int64_t n_slots;
+    float *acc;                // [D][n_slots][6]: (0, 0, g_a, g_b) of each slot's filter
+    int32_t with_gb;           // 0: g_b left to the input-gradient pass (entries 4, 5
+                               //  untouched)
+};
+int kt_smem_bytes(int Dh, int Tb, int W);
+cudaError_t launch_kt(const KTArgs &a, int D, cudaStream_t s);
 int k7_smem_bytes(int Dh, int W, int G);
 constexpr int kAdjSub = 16;    // samples per recomputed span in the adjoint
 constexpr int kAdjRounds = 2;  // filter rounds per adjoint task (independent chains per lane)
 
 cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s);
-// Reverse projection for time-segmented adjoints: for segments q = 1..P-1 of
-// seg_len samples, the adjoint state at the segment's first sample from a
-// zero state at its end, E[q][det][slot]; then mu_end[q] (the state at the
-// start of segment q + 1) for every q, carried backwards in FP64.
+// Reverse projection for time-segmented adjoints: for segments
+// q = 1..P-1, [q seg_len + off, (q + 1) seg_len + off) clipped to the call,
+// the adjoint state at the segment's first sample from a zero state at its
+// end, E[q][det][slot]; then mu_end[q] (the state at (q + 1) seg_len + off,
+// zero at or past the call's end) for every q, carried backwards in FP64.
 cudaError_t launch_adj_project(const float4 *params, const int32_t *slot_tmpl, const float2 *gz,
                                int64_t n_slots, int D, int64_t T, int64_t n, int64_t seg_len,
-                               int P, float2 *E, float2 *mu_end, cudaStream_t s);
+                               int64_t off, int P, float2 *E, float2 *mu_end, cudaStream_t s);
 // smem bytes the adjoint kernel needs
 int k6_smem_bytes(int Cc, int Dh);
 // g_a[f] = sum_det acc[det][s].ga, g_b likewise, for every slot s holding filter f

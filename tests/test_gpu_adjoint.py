@@ -1,6 +1,9 @@
 """The adjoint kernel (spiir_filter_backward) against the FP64 oracle's
 adjoint, which tests/test_oracle_pins.py pins to central differences and to
-the transpose identity.
+the transpose identity.  Both evaluations of g_a, g_b run every case: the
+reverse form (checkpointed forward, reverse-time recurrence) and the tangent
+form (forward-time derivative recurrences); g_x comes from the shifted-frame
+pass seeded by the reverse pass or by its own projection.
 
 Gradient tolerance: the kernel accumulates each g_a, g_b over n samples in
 FP32 from FP32 states, and g_x in shared memory, then into global memory
@@ -16,6 +19,7 @@ from spiir_inputs import make_bank, make_strain, perturb, workload_bank, workloa
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 GRAD_TOL = 1e-3
+FORMS = ["reverse", "tangent"]
 
 
 @pytest.fixture(scope="module")
@@ -37,21 +41,23 @@ def gpu_backward(sp, bank, x, gz, **opts):
     return ga.cpu().numpy(), gb.cpu().numpy(), gx.cpu().numpy()
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("n,D,opts", [(3000, 2, {}), (1024, 1, {}), (777, 1, {"warps_per_cta": 1}),
-                                      (2500, 3, {"max_filters_per_lane": 2})])
-def test_adjoint_matches_oracle(sp, n, D, opts):
+                                      (2500, 3, {"max_filters_per_lane": 2}), (5, 1, {})])
+def test_adjoint_matches_oracle(sp, n, D, opts, form):
     bank = make_bank(7, (20, 150), (0.99, 0.9995), 700, seed=90 + n, n_det=D)
     x = make_strain(D, n, seed=91)
     rng = np.random.default_rng(92)
     gz = (rng.standard_normal((D, 7, n)) + 1j * rng.standard_normal((D, 7, n))).astype(np.complex64)
-    ga, gb, gx = gpu_backward(sp, bank, x, gz, **opts)
+    ga, gb, gx = gpu_backward(sp, bank, x, gz, adjoint_form=form, **opts)
     ra, rb, rx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, gz)
     assert rel_inf(ga, ra) <= GRAD_TOL
     assert rel_inf(gb, rb) <= GRAD_TOL
     assert rel_inf(gx, rx) <= GRAD_TOL
 
 
-def test_adjoint_half_warp_templates(sp):
+@pytest.mark.parametrize("form", FORMS)
+def test_adjoint_half_warp_templates(sp, form):
     """Templates of <= 64 filters share warps (16 lanes each) in the forward
     layout; the adjoint reads each half's own g_z."""
     bank = make_bank(5, (10, 64), (0.99, 0.9995), 500, seed=98, n_det=2)
@@ -59,7 +65,7 @@ def test_adjoint_half_warp_templates(sp):
     rng = np.random.default_rng(100)
     gz = (rng.standard_normal((2, 5, 2100)) + 1j * rng.standard_normal((2, 5, 2100))).astype(
         np.complex64)
-    ga, gb, gx = gpu_backward(sp, bank, x, gz, lanes_per_template=16)
+    ga, gb, gx = gpu_backward(sp, bank, x, gz, lanes_per_template=16, adjoint_form=form)
     ra, rb, rx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, gz)
     assert rel_inf(ga, ra) <= GRAD_TOL
     assert rel_inf(gb, rb) <= GRAD_TOL
@@ -124,8 +130,9 @@ def test_autograd_function_and_a_fitting_step(sp):
     assert float(loss2) < float(loss.detach())
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("P", [1, 3, 5])
-def test_adjoint_time_segments(sp, P):
+def test_adjoint_time_segments(sp, P, form):
     """The reverse pass split into P time segments of whole checkpoint
     intervals (each from the adjoint state projected to its end) gives the
     oracle's gradients."""
@@ -134,15 +141,16 @@ def test_adjoint_time_segments(sp, P):
     x = make_strain(2, n, seed=121)
     rng = np.random.default_rng(122)
     gz = (rng.standard_normal((2, 6, n)) + 1j * rng.standard_normal((2, 6, n))).astype(np.complex64)
-    ga, gb, gx = gpu_backward(sp, bank, x, gz, time_segments=P)
+    ga, gb, gx = gpu_backward(sp, bank, x, gz, time_segments=P, adjoint_form=form)
     ra, rb, rx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, gz)
     assert rel_inf(ga, ra) <= GRAD_TOL
     assert rel_inf(gb, rb) <= GRAD_TOL
     assert rel_inf(gx, rx) <= GRAD_TOL
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("delays", ["equal", "distinct"])
-def test_adjoint_delay_extremes(sp, delays):
+def test_adjoint_delay_extremes(sp, delays, form):
     """g_x gathers every filter's contribution at k - d in shared memory:
     equal delays everywhere make every filter of a round add to the same
     address at once, delays equal to the filter's index in its template make
@@ -159,7 +167,7 @@ def test_adjoint_delay_extremes(sp, delays):
     x = make_strain(2, n, seed=141)
     rng = np.random.default_rng(142)
     gz = (rng.standard_normal((2, 5, n)) + 1j * rng.standard_normal((2, 5, n))).astype(np.complex64)
-    ga, gb, gx = gpu_backward(sp, bank, x, gz)
+    ga, gb, gx = gpu_backward(sp, bank, x, gz, adjoint_form=form)
     ra, rb, rx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, gz)
     assert rel_inf(ga, ra) <= GRAD_TOL
     assert rel_inf(gb, rb) <= GRAD_TOL
