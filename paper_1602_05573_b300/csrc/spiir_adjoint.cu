@@ -304,12 +304,15 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
     const int mlo = seg * A.S, mhi = min(n, mlo + A.S);
     const bool warm = TAN && seg + 1 < A.P;
     const int gend = warm ? min(n, mhi + A.Dh) : n; // g_z reads as zero from here on
-    const bool odd = (lane & 1) != 0;               // stored as conj(a), (Im b, Re b)
     const int wsel = (A.G == 16 && lane >= 16) ? 1 : 0;
     const int tmpl = wsel ? head.w : head.z;
     const float2 *grow = A.gz + ((int64_t)det * A.T + (tmpl >= 0 ? tmpl : 0)) * n;
     const float *pr = win + wsel * 2 * Wd;
 
+    // slot of round i of task kk at this lane
+    auto slot_at = [&](int kk, int i) -> int64_t {
+        return (int64_t)A.tasks[kk].x + (int64_t)i * A.round_stride + lane;
+    };
     // pair p of this lane: the two rounds of task unit.x + NP warp + p
     uint64_t AR[NP], AI[NP], NAI[NP], BR[NP], BI[NP], NR[NP], NI[NP], GBR[NP], GBI[NP];
     const float *rp[NP][R];
@@ -325,7 +328,8 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
             ar[i] = ai[i] = br[i] = bi[i] = nu_r[i] = nu_i[i] = 0.f;
             rp[p][i] = pr;
             if (i >= nr) continue;
-            const int64_t slot = (int64_t)task.x + (int64_t)i * A.round_stride + lane;
+            const int64_t slot = slot_at(unit.x + k, i);
+            const bool odd = (slot & 1) != 0;   // stored as conj(a), (Im b, Re b)
             const float4 q = A.params[slot];
             ar[i] = q.x;
             ai[i] = odd ? -q.y : q.y;
@@ -414,7 +418,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 if (i >= task.y) continue;
-                const int64_t slot = (int64_t)task.x + (int64_t)i * A.round_stride + lane;
+                const int64_t slot = slot_at(unit.x + k, i);
                 const float2 m0 = A.seeds[((int64_t)seg * A.n_det + det) * A.n_slots + slot];
                 // conj(a)^e, e = Dh - d, by binary powering
                 float br_ = ar_[i], bi_ = -ai_[i], pr_ = 1.f, pi_ = 0.f;
@@ -498,7 +502,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
 #pragma unroll
             for (int i = 0; i < R; ++i) {
                 if (i >= task.y) continue;
-                const int64_t slot = (int64_t)task.x + (int64_t)i * A.round_stride + lane;
+                const int64_t slot = slot_at(unit.x + k, i);
                 float *acc = A.acc + (((int64_t)seg * A.n_det + det) * A.n_slots + slot) * 6;
                 acc[4] = r[i];
                 acc[5] = im[i];
@@ -521,17 +525,19 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
 // 8), or 12 with GB = false, when the input-gradient pass sums g_b instead
 // (sum_m nu[m] x[m] there costs 2).
 //
-// One filter per lane (scalar FFMA: a bank that fills the GPU at one filter
-// per lane needs no time segments).  A CTA of W warps serves W x 32
-// consecutive lanes of the tangent order on one detector: the strain window
+// NF filters per lane (NF = 1: scalar FFMA; NF = 2: two filters of one
+// template as a packed FP32x2 pair, half the instructions and one g_z read
+// for both); no time segments (the bank must fill the GPU by itself).  A CTA
+// of W warps serves W x 32 lanes of the tangent order on one detector: the strain window
 // of each Tb-sample block (Dh history + Tb) is copied into shared memory by
 // cp.async, double buffered; each warp stages its (at most two) templates'
-// g_z 16 samples at a time (one load per lane, fetched a sub-block ahead)
+// g_z 16 samples at a time (one load per lane, fetched two sub-blocks ahead)
 // and every lane reads its template's row.  Sums restart every block and are
 // added into block-level totals (rounding grows with the block, not the call).
-template <bool GB>
+template <int NF, bool GB>
 __global__ void __launch_bounds__(256) kt_tangent(const KTArgs A)
 {
+    static_assert(NF == 1 || NF == 2, "one filter per lane, or a packed FP32x2 pair");
     extern __shared__ __align__(16) unsigned char smem[];
     const int Wd = A.Dh + A.Tb;
     float *xs = reinterpret_cast<float *>(smem);                     // [2][Wd]
@@ -539,27 +545,33 @@ __global__ void __launch_bounds__(256) kt_tangent(const KTArgs A)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int det = blockIdx.y;
     const int64_t wg = (int64_t)blockIdx.x * A.W + warp;
-    const bool wact = wg * 32 < A.n_pos;                              // warp-uniform
-    const int2 ln = wact ? A.lanes[wg * 32 + lane] : make_int2(-1, 0);
-    const int2 wt = wact ? A.warp_tmpl[wg] : make_int2(-1, -1);
-    float ar = 0.f, ai = 0.f, br = 0.f, bi = 0.f;
-    int xo = 0;
-    if (ln.x >= 0) {
-        const float4 p = A.params[ln.x];
-        const bool odd = (ln.x & 1) != 0;   // stored as conj(a), (Im b, Re b)
-        ar = p.x;
-        ai = odd ? -p.y : p.y;
-        br = odd ? p.w : p.z;
-        bi = odd ? p.z : p.w;
-        xo = A.ringoff[ln.x].x;             // Dh - d
+    const bool wact = wg * 32 * NF < A.n_pos;                         // warp-uniform
+    // filter f of this lane at position (wg NF + f) 32 + lane; both of one template
+    int2 ln[NF];
+    float ar[NF], ai[NF], br[NF], bi[NF];
+    int xo[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        ln[f] = wact ? A.lanes[(wg * NF + f) * 32 + lane] : make_int2(-1, 0);
+        ar[f] = ai[f] = br[f] = bi[f] = 0.f;
+        xo[f] = 0;
+        if (ln[f].x >= 0) {
+            const float4 p = A.params[ln[f].x];
+            const bool odd = (ln[f].x & 1) != 0;   // stored as conj(a), (Im b, Re b)
+            ar[f] = p.x;
+            ai[f] = odd ? -p.y : p.y;
+            br[f] = odd ? p.w : p.z;
+            bi[f] = odd ? p.z : p.w;
+            xo[f] = A.ringoff[ln[f].x].x;          // Dh - d
+        }
     }
-    const float nai = -ai;
+    const int2 wt = wact ? A.warp_tmpl[wg] : make_int2(-1, -1);
     // lane j stages sample (j & 15) of template (j >> 4) of its warp
     const int st = (lane >> 4) ? wt.y : wt.x;
     const float2 *grow = st >= 0 ? A.gz + ((int64_t)det * A.T + st) * A.n : nullptr;
     float2 *gb = gbw + warp * 36;
     const int gput = (lane >> 4) * 18 + (lane & 15);   // rows 18 apart: different banks
-    const float2 *gr = gb + (ln.y ? 18 : 0);
+    const float2 *gr = gb + (ln[0].y ? 18 : 0);
     const float *xrow = A.xe + (int64_t)det * A.xe_stride;
     const int n = A.n, Tb = A.Tb;
     const int nblk = (n + Tb - 1) / Tb;
@@ -575,10 +587,22 @@ __global__ void __launch_bounds__(256) kt_tangent(const KTArgs A)
         asm volatile("cp.async.commit_group;" ::: "memory");
     };
 
+    // state and sums; NF = 2 keeps the pair packed (lo = filter 0, hi = filter 1)
+    uint64_t AR = 0, AI = 0, NAI = 0, UR = 0, UI = 0, VR = 0, VI = 0;
     float ur = 0.f, ui = 0.f, vr = 0.f, vi = 0.f;
-    float Tbr = 0.f, Tbi = 0.f, Tar = 0.f, Tai = 0.f;   // totals of the two sums
-    float2 gnext = make_float2(0.f, 0.f);
+    if (NF == 2) {
+        AR = pk(ar[0], ar[NF - 1]);
+        AI = pk(ai[0], ai[NF - 1]);
+        NAI = pk(-ai[0], -ai[NF - 1]);
+    }
+    const float nai = -ai[0];
+    float Tbr[NF], Tbi[NF], Tar[NF], Tai[NF];   // totals of the two sums
+#pragma unroll
+    for (int f = 0; f < NF; ++f) Tbr[f] = Tbi[f] = Tar[f] = Tai[f] = 0.f;
+    // g_z of the next two sub-blocks, loaded two sub-blocks ahead of use
+    float2 gnext = make_float2(0.f, 0.f), gnext2 = make_float2(0.f, 0.f);
     if (grow != nullptr && (lane & 15) < n) gnext = grow[lane & 15];
+    if (grow != nullptr && 16 + (lane & 15) < n) gnext2 = grow[16 + (lane & 15)];
     issue(0);
     for (int j = 0; j < nblk; ++j) {
         if (j + 1 < nblk) {
@@ -588,62 +612,107 @@ __global__ void __launch_bounds__(256) kt_tangent(const KTArgs A)
             asm volatile("cp.async.wait_group 0;" ::: "memory");
         }
         __syncthreads();
-        const float *w = xs + (j & 1) * Wd + xo;
+        const float *w0 = xs + (j & 1) * Wd + xo[0];
+        const float *w1 = xs + (j & 1) * Wd + xo[NF - 1];
         const int k0 = j * Tb;
         const int nv = min(Tb, n - k0);
         // sum_k g_z conj(u): re = Gr ur + Gi ui, im = Gi ur - Gr ui (two chains);
         // likewise with v
         float sbr = 0.f, sbi1 = 0.f, sbi2 = 0.f, sar = 0.f, sai1 = 0.f, sai2 = 0.f;
-        auto step = [&](float x, float2 g) {
-            const float nvr = fmaf(ar, vr, fmaf(nai, vi, ur));   // v <- a v + u
-            const float nvi = fmaf(ar, vi, fmaf(ai, vr, ui));
-            const float nur = fmaf(ar, ur, fmaf(nai, ui, x));    // u <- a u + x
-            const float nui = fmaf(ar, ui, ai * ur);
-            ur = nur;
-            ui = nui;
-            vr = nvr;
-            vi = nvi;
-            if (GB) {
-                sbr = fmaf(g.x, ur, fmaf(g.y, ui, sbr));
-                sbi1 = fmaf(g.y, ur, sbi1);
-                sbi2 = fmaf(g.x, ui, sbi2);
+        uint64_t SBR = 0, SBI1 = 0, SBI2 = 0, SAR = 0, SAI1 = 0, SAI2 = 0;
+        auto step = [&](int t, float2 g) {
+            if (NF == 1) {
+                const float x = w0[t];
+                const float nvr = fmaf(ar[0], vr, fmaf(nai, vi, ur));   // v <- a v + u
+                const float nvi = fmaf(ar[0], vi, fmaf(ai[0], vr, ui));
+                const float nur = fmaf(ar[0], ur, fmaf(nai, ui, x));    // u <- a u + x
+                const float nui = fmaf(ar[0], ui, ai[0] * ur);
+                ur = nur;
+                ui = nui;
+                vr = nvr;
+                vi = nvi;
+                if (GB) {
+                    sbr = fmaf(g.x, ur, fmaf(g.y, ui, sbr));
+                    sbi1 = fmaf(g.y, ur, sbi1);
+                    sbi2 = fmaf(g.x, ui, sbi2);
+                }
+                sar = fmaf(g.x, vr, fmaf(g.y, vi, sar));
+                sai1 = fmaf(g.y, vr, sai1);
+                sai2 = fmaf(g.x, vi, sai2);
+            } else {
+                const uint64_t X = pk(w0[t], w1[t]);
+                const uint64_t GR = pk(g.x, g.x), GI = pk(g.y, g.y);
+                const uint64_t NVR = fma2(AR, VR, fma2(NAI, VI, UR));
+                const uint64_t NVI = fma2(AR, VI, fma2(AI, VR, UI));
+                const uint64_t NUR = fma2(AR, UR, fma2(NAI, UI, X));
+                const uint64_t NUI = fma2(AR, UI, mul2(AI, UR));
+                UR = NUR;
+                UI = NUI;
+                VR = NVR;
+                VI = NVI;
+                if (GB) {
+                    SBR = fma2(GR, UR, fma2(GI, UI, SBR));
+                    SBI1 = fma2(GI, UR, SBI1);
+                    SBI2 = fma2(GR, UI, SBI2);
+                }
+                SAR = fma2(GR, VR, fma2(GI, VI, SAR));
+                SAI1 = fma2(GI, VR, SAI1);
+                SAI2 = fma2(GR, VI, SAI2);
             }
-            sar = fmaf(g.x, vr, fmaf(g.y, vi, sar));
-            sai1 = fmaf(g.y, vr, sai1);
-            sai2 = fmaf(g.x, vi, sai2);
         };
         if (wact) {
             for (int sb = 0; sb < nv; sb += 16) {
                 gb[gput] = gnext;
                 __syncwarp();
+                gnext = gnext2;
                 {
-                    const int k = k0 + sb + 16 + (lane & 15);
-                    gnext = (grow != nullptr && k < n) ? grow[k] : make_float2(0.f, 0.f);
+                    const int k = k0 + sb + 32 + (lane & 15);
+                    gnext2 = (grow != nullptr && k < n) ? grow[k] : make_float2(0.f, 0.f);
                 }
                 if (sb + 16 <= nv) {
 #pragma unroll
-                    for (int t = 0; t < 16; ++t) step(w[sb + t], gr[t]);
+                    for (int t = 0; t < 16; ++t) step(sb + t, gr[t]);
                 } else {
-                    for (int t = 0; t < nv - sb; ++t) step(w[sb + t], gr[t]);
+                    for (int t = 0; t < nv - sb; ++t) step(sb + t, gr[t]);
                 }
                 __syncwarp();
             }
         }
-        Tbr += sbr;
-        Tbi += sbi1 - sbi2;
-        Tar += sar;
-        Tai += sai1 - sai2;
+        if (NF == 1) {
+            Tbr[0] += sbr;
+            Tbi[0] += sbi1 - sbi2;
+            Tar[0] += sar;
+            Tai[0] += sai1 - sai2;
+        } else {
+            float lo, hi, lo2, hi2;
+            upk(SBR, lo, hi);
+            Tbr[0] += lo;
+            Tbr[NF - 1] += hi;
+            upk(SBI1, lo, hi);
+            upk(SBI2, lo2, hi2);
+            Tbi[0] += lo - lo2;
+            Tbi[NF - 1] += hi - hi2;
+            upk(SAR, lo, hi);
+            Tar[0] += lo;
+            Tar[NF - 1] += hi;
+            upk(SAI1, lo, hi);
+            upk(SAI2, lo2, hi2);
+            Tai[0] += lo - lo2;
+            Tai[NF - 1] += hi - hi2;
+        }
         __syncthreads();   // every warp is done with this buffer before it is refilled
     }
-    if (ln.x >= 0) {
-        float *acc = A.acc + ((int64_t)det * A.n_slots + ln.x) * 6;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+        if (ln[f].x < 0) continue;
+        float *acc = A.acc + ((int64_t)det * A.n_slots + ln[f].x) * 6;
         acc[0] = 0.f;
         acc[1] = 0.f;
-        acc[2] = br * Tar + bi * Tai;   // conj(b) sum g_z conj(v)
-        acc[3] = br * Tai - bi * Tar;
+        acc[2] = br[f] * Tar[f] + bi[f] * Tai[f];   // conj(b) sum g_z conj(v)
+        acc[3] = br[f] * Tai[f] - bi[f] * Tar[f];
         if (GB) {
-            acc[4] = Tbr;
-            acc[5] = Tbi;
+            acc[4] = Tbr[f];
+            acc[5] = Tbi[f];
         }
     }
 }
@@ -671,9 +740,9 @@ __global__ void adj_finalize(const float *acc, const int64_t *slot_filter, int64
 // start, mu <- g_z + conj(a) mu run backwards over the segment from zero.
 // One thread per (segment, detector, 4 slots): the 4 slots sit in one
 // 32-slot round, so they share one template and one g_z row; they run as two
-// packed FP32x2 pairs, and g_z is loaded 8 samples ahead of the chain.
+// packed FP32x2 pairs, and g_z is loaded a group of 16 samples ahead.
 constexpr int kProjSlots = 4;
-constexpr int kProjAhead = 8;
+constexpr int kProjAhead = 16;
 
 __global__ void __launch_bounds__(128) adj_project_kernel(
     const float4 *params, const int32_t *slot_tmpl, const float2 *gz, int64_t n_slots, int D,
@@ -704,27 +773,7 @@ __global__ void __launch_bounds__(128) adj_project_kernel(
         const uint64_t NAI1 = pk(-ai[2], -ai[3]);
         const float2 *g = gz + ((int64_t)det * T + tmpl) * n;
         const int64_t j0 = (int64_t)q * seg_len + off, j1 = min(n, j0 + seg_len);
-        int64_t j = j1;
-        // whole groups of kProjAhead samples from the segment's end, then the rest
-        for (; j - kProjAhead >= j0; j -= kProjAhead) {
-            float2 G[kProjAhead];
-#pragma unroll
-            for (int t = 0; t < kProjAhead; ++t) G[t] = g[j - 1 - t];
-#pragma unroll
-            for (int t = 0; t < kProjAhead; ++t) {
-                const uint64_t GR = pk(G[t].x, G[t].x), GI = pk(G[t].y, G[t].y);
-                const uint64_t nr0 = fma2(AR0, MR0, fma2(AI0, MI0, GR));
-                const uint64_t ni0 = fma2(AR0, MI0, fma2(NAI0, MR0, GI));
-                const uint64_t nr1 = fma2(AR1, MR1, fma2(AI1, MI1, GR));
-                const uint64_t ni1 = fma2(AR1, MI1, fma2(NAI1, MR1, GI));
-                MR0 = nr0;
-                MI0 = ni0;
-                MR1 = nr1;
-                MI1 = ni1;
-            }
-        }
-        for (; j > j0; --j) {
-            const float2 G1 = g[j - 1];
+        auto step = [&](float2 G1) {
             const uint64_t GR = pk(G1.x, G1.x), GI = pk(G1.y, G1.y);
             const uint64_t nr0 = fma2(AR0, MR0, fma2(AI0, MI0, GR));
             const uint64_t ni0 = fma2(AR0, MI0, fma2(NAI0, MR0, GI));
@@ -734,7 +783,26 @@ __global__ void __launch_bounds__(128) adj_project_kernel(
             MI0 = ni0;
             MR1 = nr1;
             MI1 = ni1;
+        };
+        int64_t j = j1;
+        // whole groups of kProjAhead samples from the segment's end, each
+        // group's g_z loaded while the previous group runs; then the rest
+        if (j - kProjAhead >= j0) {
+            float2 Gc[kProjAhead], Gn[kProjAhead];
+#pragma unroll
+            for (int t = 0; t < kProjAhead; ++t) Gc[t] = g[j - 1 - t];
+            for (; j - kProjAhead >= j0; j -= kProjAhead) {
+                const bool more = j - 2 * kProjAhead >= j0;
+#pragma unroll
+                for (int t = 0; t < kProjAhead; ++t)
+                    Gn[t] = more ? g[j - kProjAhead - 1 - t] : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int t = 0; t < kProjAhead; ++t) step(Gc[t]);
+#pragma unroll
+                for (int t = 0; t < kProjAhead; ++t) Gc[t] = Gn[t];
+            }
         }
+        for (; j > j0; --j) step(g[j - 1]);
     }
     float mr[kProjSlots], mi[kProjSlots];
     upk(MR0, mr[0], mr[1]);
@@ -873,20 +941,27 @@ int kt_smem_bytes(int Dh, int Tb, int W)
 cudaError_t launch_kt(const KTArgs &a, int D, cudaStream_t s)
 {
     if (a.n_pos <= 0 || a.n <= 0 || D <= 0) return cudaSuccess;
-    if (a.W < 1 || a.W > 8 || a.n_pos % 32 != 0 || a.Tb % 16 != 0 || a.Dh % 4 != 0 ||
+    if (a.W < 1 || a.W > 8 || (a.nf != 1 && a.nf != 2) || a.n_pos % (32 * a.nf) != 0 ||
+        a.Tb % 16 != 0 || a.Dh % 4 != 0 ||
         a.xe_stride % 4 != 0 || (reinterpret_cast<uintptr_t>(a.xe) & 15) != 0)
         return cudaErrorInvalidValue;
     const int smem = kt_smem_bytes(a.Dh, a.Tb, a.W);
-    const void *fn = a.with_gb ? reinterpret_cast<const void *>(kt_tangent<true>)
-                               : reinterpret_cast<const void *>(kt_tangent<false>);
+    const void *fn =
+        a.nf == 2 ? (a.with_gb ? reinterpret_cast<const void *>(kt_tangent<2, true>)
+                               : reinterpret_cast<const void *>(kt_tangent<2, false>))
+                  : (a.with_gb ? reinterpret_cast<const void *>(kt_tangent<1, true>)
+                               : reinterpret_cast<const void *>(kt_tangent<1, false>));
     cudaError_t e = ensure_smem_limit(fn, smem);
     if (e != cudaSuccess) return e;
-    const int64_t warps = a.n_pos / 32;
+    const int64_t warps = a.n_pos / (32 * a.nf);
     const dim3 grid((unsigned)((warps + a.W - 1) / a.W), (unsigned)D);
-    if (a.with_gb)
-        kt_tangent<true><<<grid, a.W * 32, smem, s>>>(a);
-    else
-        kt_tangent<false><<<grid, a.W * 32, smem, s>>>(a);
+    if (a.nf == 2) {
+        if (a.with_gb) kt_tangent<2, true><<<grid, a.W * 32, smem, s>>>(a);
+        else kt_tangent<2, false><<<grid, a.W * 32, smem, s>>>(a);
+    } else {
+        if (a.with_gb) kt_tangent<1, true><<<grid, a.W * 32, smem, s>>>(a);
+        else kt_tangent<1, false><<<grid, a.W * 32, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 

@@ -183,9 +183,11 @@ struct Band {
     int64_t adj_n_units7 = 0;
     int adj_W7 = 1;                // warps per input-gradient CTA (largest unit)
     float2 *adj_seeds = nullptr;   // [P-1][D][n_slots] input-gradient segment seeds
-    int2 *kt_lanes = nullptr;      // tangent form: lanes in tangent order (slot, 0/1)
-    int2 *kt_warp_tmpl = nullptr;  //   the two templates of every warp
-    int64_t kt_n_pos = 0;          //   lanes (multiple of 32)
+    // tangent form, for 1 and 2 filters per lane ([nf - 1]): positions in
+    // tangent order (slot, 0/1), the two templates of every warp, positions
+    int2 *kt_lanes[2] = {nullptr, nullptr};
+    int2 *kt_warp_tmpl[2] = {nullptr, nullptr};
+    int64_t kt_n_pos[2] = {0, 0};
 };
 
 struct spiir_plan {
@@ -293,8 +295,10 @@ void free_band(Band &b)
     cudaFree(b.adj_units7);
     cudaFree(b.fir);
     cudaFree(b.adj_seeds);
-    cudaFree(b.kt_lanes);
-    cudaFree(b.kt_warp_tmpl);
+    for (int f = 0; f < 2; ++f) {
+        cudaFree(b.kt_lanes[f]);
+        cudaFree(b.kt_warp_tmpl[f]);
+    }
     b = Band();
 }
 
@@ -1443,27 +1447,38 @@ spiir_status build_adjoint_tasks(Band &b, int D)
     return SPIIR_OK;
 }
 
-// Tangent order of a band's filters: grouped by template (bank order), each
-// warp of 32 lanes spanning at most two templates (a third starts a new
-// warp), and within a template filters dealt round-robin over their delays
-// mod 32, so that neighbouring lanes read strain at different banks.
-spiir_status build_tangent_order(Band &b, int64_t T)
+// Tangent order of a band's filters for nf filters per lane: grouped by
+// template (bank order), a lane's filters from one template, each warp
+// spanning at most two templates (a third starts a new warp).  Filter f of a
+// lane reads strain at bank (Dh - d) mod 32, so it takes a filter whose delay
+// mod 32 no earlier lane's filter f in the warp has, while the template has
+// one (else one from the fullest residue class).  Positions are
+// (warp nf + f) 32 + lane.
+spiir_status build_tangent_order(Band &b, int64_t T, int nf)
 {
     const spiir::Layout &L = b.lay;
     std::vector<std::vector<int64_t>> per((size_t)T);
     for (int64_t s = 0; s < L.n_slots; ++s)
         if (L.slot_filter[s] >= 0 && L.slot_template[s] >= 0) per[L.slot_template[s]].push_back(s);
     std::vector<int32_t> lanes, wtmpl;
+    std::vector<int32_t> row((size_t)nf * 32 * 2);
     int c = 0, t0 = -1, t1 = -1;
-    auto close_warp = [&]() {
-        for (; c < 32; ++c) {
-            lanes.push_back(-1);
-            lanes.push_back(0);
+    uint32_t used[2] = {0, 0};   // residues taken by filter f of the current warp
+    auto reset_rows = [&]() {
+        for (size_t i = 0; i < row.size(); i += 2) {
+            row[i] = -1;
+            row[i + 1] = 0;
         }
+    };
+    reset_rows();
+    auto close_warp = [&]() {
+        lanes.insert(lanes.end(), row.begin(), row.end());
         wtmpl.push_back(t0);
         wtmpl.push_back(t1);
+        reset_rows();
         c = 0;
         t0 = t1 = -1;
+        used[0] = used[1] = 0;
     };
     for (int64_t t = 0; t < T; ++t) {
         std::vector<std::vector<int64_t>> bucket(32);
@@ -1471,11 +1486,8 @@ spiir_status build_tangent_order(Band &b, int64_t T)
             const int d = L.Dh - L.ringoff[2 * s];
             bucket[((d % 32) + 32) % 32].push_back(s);
         }
-        std::vector<int64_t> order;
-        for (size_t r = 0; order.size() < per[t].size(); ++r)
-            for (int k = 0; k < 32; ++k)
-                if (r < bucket[k].size()) order.push_back(bucket[k][r]);
-        for (int64_t s : order) {
+        size_t left = per[t].size(), k0 = 0;
+        while (left > 0) {
             if (c == 32) close_warp();
             int li;
             if ((int64_t)t0 == t) li = 0;
@@ -1483,24 +1495,39 @@ spiir_status build_tangent_order(Band &b, int64_t T)
             else if (t0 < 0) { t0 = (int)t; li = 0; }
             else if (t1 < 0) { t1 = (int)t; li = 1; }
             else { close_warp(); t0 = (int)t; li = 0; }
-            if (s > INT32_MAX) return fail(SPIIR_EUNSUPPORTED, "tangent form: slot index above 2^31");
-            lanes.push_back((int32_t)s);
-            lanes.push_back(li);
+            for (int f = 0; f < nf && left > 0; ++f, --left, ++k0) {
+                int pick = -1;
+                for (int j = 0; j < 32 && pick < 0; ++j) {
+                    const int k = (int)((k0 + j) % 32);
+                    if (!bucket[k].empty() && !(used[f] & (1u << k))) pick = k;
+                }
+                if (pick < 0)
+                    for (int k = 0; k < 32; ++k)
+                        if (pick < 0 || bucket[k].size() > bucket[pick].size()) pick = k;
+                const int64_t s = bucket[pick].back();
+                bucket[pick].pop_back();
+                used[f] |= 1u << pick;
+                if (s > INT32_MAX)
+                    return fail(SPIIR_EUNSUPPORTED, "tangent form: slot index above 2^31");
+                row[2 * ((size_t)f * 32 + c)] = (int32_t)s;
+                row[2 * ((size_t)f * 32 + c) + 1] = li;
+            }
             ++c;
         }
     }
     if (c > 0) close_warp();
+    const int k = nf - 1;
     cudaError_t e;
-    if ((e = dalloc(&b.kt_lanes, lanes.size() / 2)) != cudaSuccess ||
-        (e = cudaMemcpy(b.kt_lanes, lanes.data(), lanes.size() * sizeof(int32_t),
+    if ((e = dalloc(&b.kt_lanes[k], lanes.size() / 2)) != cudaSuccess ||
+        (e = cudaMemcpy(b.kt_lanes[k], lanes.data(), lanes.size() * sizeof(int32_t),
                         cudaMemcpyHostToDevice)) != cudaSuccess ||
-        (e = dalloc(&b.kt_warp_tmpl, std::max<size_t>(1, wtmpl.size() / 2))) != cudaSuccess ||
+        (e = dalloc(&b.kt_warp_tmpl[k], std::max<size_t>(1, wtmpl.size() / 2))) != cudaSuccess ||
         (wtmpl.size() > 0 &&
-         (e = cudaMemcpy(b.kt_warp_tmpl, wtmpl.data(), wtmpl.size() * sizeof(int32_t),
+         (e = cudaMemcpy(b.kt_warp_tmpl[k], wtmpl.data(), wtmpl.size() * sizeof(int32_t),
                          cudaMemcpyHostToDevice)) != cudaSuccess))
         return e == cudaErrorMemoryAllocation ? fail(SPIIR_ENOMEM, "tangent lane order")
                                               : cuda_fail(e, "tangent lane order upload");
-    b.kt_n_pos = (int64_t)lanes.size() / 2;
+    b.kt_n_pos[k] = (int64_t)lanes.size() / 2;
     return SPIIR_OK;
 }
 
@@ -1563,12 +1590,13 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     if (p->opt.adjoint_form != SPIIR_ADJOINT_REVERSE &&
         spiir::kt_smem_bytes(L.Dh, L.Tb, 1) <= 227 * 1024 &&
         (!grad_x_dev || (L.Dh % spiir::kK7Chunk == 0 && Cc % spiir::kK7Chunk == 0))) {
-        if (!b.kt_lanes) {
-            spiir_status st = build_tangent_order(b, p->T);
-            if (st != SPIIR_OK) return st;
-        }
+        for (int nf = 1; nf <= 2; ++nf)
+            if (!b.kt_lanes[nf - 1]) {
+                spiir_status st = build_tangent_order(b, p->T, nf);
+                if (st != SPIIR_OK) return st;
+            }
         tangent = p->opt.adjoint_form == SPIIR_ADJOINT_TANGENT ||
-                  (b.kt_n_pos / 32) * D >= 8 * (int64_t)p->n_sm;
+                  (b.kt_n_pos[0] / 32) * D >= 8 * (int64_t)p->n_sm;
     }
     if (p->opt.adjoint_form == SPIIR_ADJOINT_TANGENT && !tangent)
         return fail(SPIIR_EUNSUPPORTED,
@@ -1655,12 +1683,16 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         t.n = (int32_t)n;
         t.Dh = L.Dh;
         t.Tb = L.Tb;
-        t.W = tangent_warps_per_cta(b.kt_n_pos / 32, D, L.Dh, L.Tb, p->n_sm);
+        // filter pairs per lane when that still gives >= 12 warps per SM (with
+        // fewer, one filter per lane hides latency better: measured on the
+        // 256 x 200-filter bank, 5.4 warps per SM at pairs, 5.96 vs 5.64 ms)
+        t.nf = (b.kt_n_pos[1] / 64) * D >= 12 * (int64_t)p->n_sm ? 2 : 1;
+        t.W = tangent_warps_per_cta(b.kt_n_pos[t.nf - 1] / (32 * t.nf), D, L.Dh, L.Tb, p->n_sm);
         t.gz = reinterpret_cast<const float2 *>(grad_z_dev);
         t.T = p->T;
-        t.lanes = b.kt_lanes;
-        t.warp_tmpl = b.kt_warp_tmpl;
-        t.n_pos = b.kt_n_pos;
+        t.lanes = b.kt_lanes[t.nf - 1];
+        t.warp_tmpl = b.kt_warp_tmpl[t.nf - 1];
+        t.n_pos = b.kt_n_pos[t.nf - 1];
         t.params = b.params;
         t.ringoff = b.ringoff;
         t.n_slots = L.n_slots;

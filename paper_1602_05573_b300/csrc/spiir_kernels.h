@@ -169,10 +169,12 @@ struct KTArgs {
     int32_t W;                 // warps per CTA
     const float2 *gz;          // [D][T][n]
     int64_t T;
-    const int2 *lanes;         // [n_pos] (slot, 0/1: the warp's first or second template);
-                               //  slot -1 = an empty lane
-    const int2 *warp_tmpl;     // [n_pos / 32] the warp's two templates (-1: none)
-    int64_t n_pos;             // lanes, a multiple of 32
+    int32_t nf;                // filters per lane: 1, or 2 (a packed pair of one template)
+    const int2 *lanes;         // [n_pos] position (warp nf + f) 32 + lane: filter f of the
+                               //  lane, (slot, 0/1: the warp's first or second template);
+                               //  slot -1 = empty
+    const int2 *warp_tmpl;     // [n_pos / (32 nf)] the warp's two templates (-1: none)
+    int64_t n_pos;             // positions, a multiple of 32 nf
     const float4 *params;      // kernel form (odd slots hold conj(a), (Im b, Re b))
     const int2 *ringoff;       // (Dh - d, .) per slot
     int64_t n_slots;

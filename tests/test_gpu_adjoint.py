@@ -172,3 +172,28 @@ def test_adjoint_delay_extremes(sp, delays, form):
     assert rel_inf(ga, ra) <= GRAD_TOL
     assert rel_inf(gb, rb) <= GRAD_TOL
     assert rel_inf(gx, rx) <= GRAD_TOL
+
+
+@pytest.mark.parametrize("D", [1, 3])
+def test_adjoint_tangent_filter_pairs(sp, D):
+    """A bank of 220 templates x 151..251 filters: on one detector the
+    tangent pass holds one filter per thread; on three it is large enough to
+    hold two filters of one template per thread (>= 12 warps per SM at
+    pairs), where odd filter counts leave half-empty pairs and warps hold the
+    end of one template and the start of the next."""
+    bank = make_bank(220, (151, 251), (0.99, 0.9995), 600, seed=150, n_det=D)
+    n = 2100
+    x = make_strain(D, n, seed=151)
+    rng = np.random.default_rng(152)
+    gz = (rng.standard_normal((D, 220, n)) + 1j * rng.standard_normal((D, 220, n))).astype(
+        np.complex64)
+    for want_gx in (True, False):
+        plan = sp.Plan(bank, adjoint_form="tangent")
+        xt = torch.from_numpy(x).cuda()
+        ga, gb, gx = plan.backward(xt, torch.from_numpy(gz).cuda(), want_gx=want_gx)
+        plan.check()
+        ra, rb, rx = oracle.adjoint(bank.off, bank.a, bank.b, bank.d, x, gz, want_gx=want_gx)
+        assert rel_inf(ga.cpu().numpy(), ra) <= GRAD_TOL
+        assert rel_inf(gb.cpu().numpy(), rb) <= GRAD_TOL
+        if want_gx:
+            assert rel_inf(gx.cpu().numpy(), rx) <= GRAD_TOL
