@@ -1585,11 +1585,11 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     }
     // g_a, g_b: tangent or reverse form
     // (the tangent form's input-gradient pass warms up over whole 256-sample
-    // chunks: history and checkpoint interval must be whole chunks)
+    // chunks: the history must be whole chunks)
     bool tangent = false;
     if (p->opt.adjoint_form != SPIIR_ADJOINT_REVERSE &&
         spiir::kt_smem_bytes(L.Dh, L.Tb, 1) <= 227 * 1024 &&
-        (!grad_x_dev || (L.Dh % spiir::kK7Chunk == 0 && Cc % spiir::kK7Chunk == 0))) {
+        (!grad_x_dev || L.Dh % spiir::kK7Chunk == 0)) {
         for (int nf = 1; nf <= 2; ++nf)
             if (!b.kt_lanes[nf - 1]) {
                 spiir_status st = build_tangent_order(b, p->T, nf);
@@ -1600,8 +1600,8 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     }
     if (p->opt.adjoint_form == SPIIR_ADJOINT_TANGENT && !tangent)
         return fail(SPIIR_EUNSUPPORTED,
-                    "tangent adjoint: strain window above 227 KB, or history or checkpoint "
-                    "interval not a multiple of 256 samples");
+                    "tangent adjoint: strain window above 227 KB, or history not a multiple "
+                    "of 256 samples");
     const bool need_ckpt = !tangent;
     if (!b.bw_xe || b.bw_cap < need || (need_ckpt && b.ckpt_cap < nc)) {
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -1625,19 +1625,32 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
     if (!b.bw_state) {
         if ((e = dalloc(&b.bw_state, (size_t)D * L.n_slots)) != cudaSuccess) return oom(e);
     }
-    // time segments of whole chunks for the reverse pass and the input-gradient
-    // pass (options.time_segments, or enough CTAs for about four waves of 16
-    // warps per SM, at most 16 segments), each at least one chunk
+    // time segments (options.time_segments, or enough CTAs for about four
+    // waves of 16 warps per SM, at most 16).  Reverse form: whole checkpoint
+    // intervals for the reverse pass and the input-gradient pass.  Tangent
+    // form: only the input-gradient pass is segmented, in whole 256-sample
+    // chunks (every segment but the last warms up over Dh samples; measured
+    // on the 256 x 200-filter bank: 4 segments 6.09 ms per backward, 6: 6.05,
+    // 10: 5.65, 16: 5.74, 32: 6.08).
+    const int W7 = L.G == 16 ? b.adj_W7 : (b.adj_W7 + 1) / 2;
     int P = 1;
+    int64_t S7 = 0;   // input-gradient segment length (tangent form)
     {
         const int64_t warps = b.adj_n_units * b.adj_W;
         const int req = p->opt.time_segments;
         if (req >= 1) P = req;
         else P = (int)std::min<int64_t>(16, std::max<int64_t>(1, (64 * (int64_t)p->n_sm + warps - 1) / warps));
-        P = (int)std::max<int64_t>(1, std::min<int64_t>(P, nc));
+        if (tangent) {
+            const int64_t chunks = (n + spiir::kK7Chunk - 1) / spiir::kK7Chunk;
+            P = (int)std::max<int64_t>(1, std::min<int64_t>(P, chunks));
+            S7 = ((chunks + P - 1) / P) * spiir::kK7Chunk;
+            P = (int)((n + S7 - 1) / S7);
+        } else {
+            P = (int)std::max<int64_t>(1, std::min<int64_t>(P, nc));
+        }
     }
-    const int64_t cps = (nc + P - 1) / P;
-    P = (int)((nc + cps - 1) / cps);
+    const int64_t cps = tangent ? 0 : (nc + P - 1) / P;
+    if (!tangent) P = (int)((nc + cps - 1) / cps);
     if (b.adj_seg_cap < P) {
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
             return cuda_fail(e, "cudaStreamSynchronize");
@@ -1807,12 +1820,12 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         g.T = p->T;
         g.n = (int32_t)n;
         g.Dh = L.Dh;
-        g.S = (int32_t)(cps * Cc);
+        g.S = (int32_t)(tangent ? S7 : cps * Cc);
         g.P = P;
         g.tasks = b.adj_tasks;
         g.units = b.adj_units7;
         g.n_units = (int32_t)b.adj_n_units7;
-        g.W = L.G == 16 ? b.adj_W7 : (b.adj_W7 + 1) / 2;
+        g.W = W7;
         g.round_stride = L.W * 32;
         g.G = L.G;
         g.params = b.params;
