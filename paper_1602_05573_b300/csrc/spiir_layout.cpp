@@ -257,15 +257,22 @@ double predict_launch(const std::vector<int> &gF, int D, int64_t slots)
     return end;
 }
 
+// Templates in launch order: filters per lane, then warps, then filter
+// count, then largest delay, each descending (ties keep bank order).
 std::vector<int64_t> sort_templates(const std::vector<int> &F, const std::vector<int> &nw,
-                                    const std::vector<std::vector<int64_t>> &filters)
+                                    const std::vector<std::vector<int64_t>> &filters,
+                                    const int32_t *d)
 {
+    std::vector<int32_t> dmax(F.size(), 0);
+    for (size_t t = 0; t < F.size(); ++t)
+        for (int64_t f : filters[t]) dmax[t] = std::max(dmax[t], d[f]);
     std::vector<int64_t> order(F.size());
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int64_t x, int64_t y) {
         if (F[x] != F[y]) return F[x] > F[y];
         if (nw[x] != nw[y]) return nw[x] > nw[y];
-        return filters[x].size() > filters[y].size();
+        if (filters[x].size() != filters[y].size()) return filters[x].size() > filters[y].size();
+        return dmax[x] > dmax[y];
     });
     return order;
 }
@@ -431,7 +438,7 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
             std::vector<int> F2, nw2;
             split_first(k, F2, nw2);
             const double len =
-                predict_launch(pack_groups(F2, nw2, sort_templates(F2, nw2, filters), L.W), D,
+                predict_launch(pack_groups(F2, nw2, sort_templates(F2, nw2, filters, d), L.W), D,
                                slots);
             if (k == cands.front() || len < best) {
                 best = len;
@@ -447,7 +454,7 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
         L.tail_templates = best_k;
     }
     // sort templates: F descending, warps descending, filter count descending
-    std::vector<int64_t> order = sort_templates(F, nw, filters);
+    std::vector<int64_t> order = sort_templates(F, nw, filters, d);
     // first-fit packing of each template's warps into CTAs of the same F
     struct Group {
         int F;
