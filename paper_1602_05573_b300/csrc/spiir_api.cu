@@ -219,6 +219,10 @@ struct spiir_plan {
     std::vector<float> a_host, b_host;
     std::vector<int32_t> d_host;
     std::string tune_report;
+    // the tangent adjoint runs its g_a pass beside the input-gradient pass:
+    // a second stream and its fork/join events (created on first use)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int32_t last_launches = 0;    // kernels the last filter/backward call launched
     int32_t last_segments = 1;    // time segments of the last call's top band
     // kernel timing (opt.kernel_timing): event pairs since the last read
@@ -675,6 +679,9 @@ spiir_status spiir_plan_destroy(spiir_plan *p)
         cudaFree(p->fir_xh);
         cudaFree(p->fir_xt);
         for (cudaEvent_t ev : p->ev_pool) cudaEventDestroy(ev);
+        if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+        if (p->ev_join) cudaEventDestroy(p->ev_join);
+        if (p->aux) cudaStreamDestroy(p->aux);
     }
     delete p;
     return SPIIR_OK;
@@ -1688,6 +1695,16 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         return fail(SPIIR_EUNSUPPORTED, "adjoint windows above 227 KB of shared memory");
     spiir::K6Args a{};
     a.seeds = (P > 1 && grad_x_dev) ? b.adj_seeds : nullptr;
+    const bool overlap = tangent && grad_x_dev != nullptr;
+    int t_all = -1;   // one timed window around both passes when they overlap
+    if (overlap) {
+        if (!p->aux &&
+            ((e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+             (e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+             (e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming)) != cudaSuccess))
+            return cuda_fail(e, "adjoint stream");
+        t_all = time_begin(p, s);
+    }
     if (tangent) {
         // g_a, g_b: one forward pass of the derivative recurrences
         spiir::KTArgs t{};
@@ -1711,10 +1728,21 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         t.n_slots = L.n_slots;
         t.acc = b.acc;
         t.with_gb = grad_x_dev == nullptr;   // else the input-gradient pass sums g_b
-        const int tt = time_begin(p, s);
-        if ((e = spiir::launch_kt(t, D, s)) != cudaSuccess)
-            return cuda_fail(e, "tangent adjoint launch");
-        time_end(p, s, tt, kTimeAdj);
+        if (overlap) {
+            // forked onto the plan's second stream: runs beside the
+            // input-gradient pass (one limited by issue latency, the other by
+            // shared memory); joined before the finalize
+            if ((e = cudaEventRecord(p->ev_fork, s)) != cudaSuccess ||
+                (e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0)) != cudaSuccess ||
+                (e = spiir::launch_kt(t, D, p->aux)) != cudaSuccess ||
+                (e = cudaEventRecord(p->ev_join, p->aux)) != cudaSuccess)
+                return cuda_fail(e, "tangent adjoint launch");
+        } else {
+            const int tt = time_begin(p, s);
+            if ((e = spiir::launch_kt(t, D, s)) != cudaSuccess)
+                return cuda_fail(e, "tangent adjoint launch");
+            time_end(p, s, tt, kTimeAdj);
+        }
         p->last_launches += 1;
     } else {
         // forward pass from zero state, keeping the state every Cc samples
@@ -1834,7 +1862,7 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
         g.n_det = D;
         g.seeds = a.seeds;
         g.gx = grad_x_dev;
-        const int tg = time_begin(p, s);
+        const int tg = overlap ? -1 : time_begin(p, s);
         if (tangent) {
             // seeds: mu at (q + 1) S + Dh from the reverse projection over
             // segments shifted by Dh; the pass also sums g_b
@@ -1852,6 +1880,11 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
             return cuda_fail(e, "adjoint input-gradient launch");
         time_end(p, s, tg, kTimeAdj);
         p->last_launches += 1;
+    }
+    if (overlap) {
+        if ((e = cudaStreamWaitEvent(s, p->ev_join, 0)) != cudaSuccess)
+            return cuda_fail(e, "adjoint join");
+        time_end(p, s, t_all, kTimeAdj);
     }
     if ((e = spiir::launch_adj_finalize(b.acc, b.slot_filter, L.n_slots, D,
                                         (tangent && !grad_x_dev) ? 1 : P,
