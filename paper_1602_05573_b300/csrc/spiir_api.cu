@@ -947,10 +947,17 @@ spiir_status launch_anchored(spiir_plan *p, Band &b, spiir::K1Args a, cudaStream
 // true start states; the main pass then runs every segment from its start
 // state and the per-segment peaks are merged in time order.  The chunked
 // tensor-core precision goes to launch_anchored instead.
+// phase: kPhaseAll, or kPhaseProject (segment start states only) followed by
+// kPhaseMain (the filter pass from them) on the same band and arguments.
+constexpr int kPhaseAll = 0, kPhaseProject = 1, kPhaseMain = 2;
+
 spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cudaStream_t s,
-                              int64_t *t0_advance = nullptr)
+                              int64_t *t0_advance = nullptr, int phase = kPhaseAll)
 {
-    if (p->precision == SPIIR_PREC_CHUNKED_TC) return launch_anchored(p, b, a, s, t0_advance);
+    if (p->precision == SPIIR_PREC_CHUNKED_TC) {
+        if (phase == kPhaseProject) return SPIIR_OK;
+        return launch_anchored(p, b, a, s, t0_advance);
+    }
     const spiir::Layout &L = b.lay;
     const int D = p->D;
     const int64_t per = (int64_t)D * L.n_slots;
@@ -966,6 +973,7 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
     cudaError_t e;
     if (t0_advance != nullptr) p->last_segments = std::max(P, 1);
     if (P <= 1) {
+        if (phase == kPhaseProject) return SPIIR_OK;
         const int tk = time_begin(p, s);
         if ((e = spiir::launch_k1(a, L.n_units(), k1_smem(b, a), s)) != cudaSuccess)
             return cuda_fail(e, "filter kernel launch");
@@ -995,7 +1003,9 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
         b.seg_cap = P;
     }
     a.n_seg = (int32_t)n_seg;
-    if (tc) {
+    if (phase == kPhaseMain) {
+        // start states already projected
+    } else if (tc) {
         // segment start states from the split-BF16 GEMM of chunk sums + scan
         spiir_status st = ensure_tc_weights(p, b, s);
         if (st != SPIIR_OK) return st;
@@ -1046,6 +1056,7 @@ spiir_status launch_segmented(spiir_plan *p, Band &b, spiir::K1Args a, int P, cu
                                              D, P, (int)n_seg, s)) != cudaSuccess)
             return cuda_fail(e, "segment projection launch");
     }
+    if (phase == kPhaseProject) return SPIIR_OK;
     // main pass: every segment from its start state
     float *best = a.peak_best;
     int64_t *idx = a.peak_idx;
@@ -1221,73 +1232,124 @@ spiir_status spiir_filter(spiir_plan *p, const float *x_dev, int64_t n, float *z
                                    cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
             return cuda_fail(e, "front-end staging");
     }
-    for (int j : order) {
-        Band &b = p->bands[j];
-        const int64_t nb = (n + b.R - 1) / b.R;   // band samples in this call
-        spiir_status st = ensure_xe(p, b, nb, s);
+    // Multirate calls with two or more lower bands use the plan's second
+    // stream, forked here: the first, third ... lower band runs there; the
+    // top band's staging and segment projection (which need only its own
+    // strain and state) and the other lower bands run on the caller's stream;
+    // both join before the top band's main pass, which reads the lower bands'
+    // sums.  The bands are independent, so the smaller passes fill the GPU
+    // beside the larger.
+    const bool fork = order.size() > 2;
+    if (fork) {
+        if (!p->aux &&
+            ((e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking)) != cudaSuccess ||
+             (e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming)) != cudaSuccess ||
+             (e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming)) != cudaSuccess))
+            return cuda_fail(e, "band stream");
+        if ((e = cudaEventRecord(p->ev_fork, s)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0)) != cudaSuccess)
+            return cuda_fail(e, "band fork");
+    }
+    // xe[:, 0:Dh] = band history, xe[:, Dh:Dh+nb] = this call's band samples
+    auto stage = [&](Band &b, int64_t nb, cudaStream_t bs) -> spiir_status {
+        spiir_status st = ensure_xe(p, b, nb, bs);
         if (st != SPIIR_OK) return st;
         const int64_t Dh = b.lay.Dh;
-        // xe[:, 0:Dh] = band history, xe[:, Dh:Dh+nb] = this call's band samples
         if ((e = cudaMemcpy2DAsync(b.xe, b.xe_stride * 4, b.hist, Dh * 4, Dh * 4, D,
-                                   cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                                   cudaMemcpyDeviceToDevice, bs)) != cudaSuccess)
             return cuda_fail(e, "strain staging copy");
         if (b.fir_len > 0) {
             e = spiir::launch_fir_decimate(p->fir_xt, p->fir_xt_cap, H, D, b.R, nb, b.fir,
-                                           b.fir_len, b.xe, b.xe_stride, Dh, s);
+                                           b.fir_len, b.xe, b.xe_stride, Dh, bs);
             p->last_launches += 1;
         } else if (b.R == 1) {
             e = cudaMemcpy2DAsync(b.xe + Dh, b.xe_stride * 4, x_dev, n * 4, n * 4, D,
-                                  cudaMemcpyDeviceToDevice, s);
+                                  cudaMemcpyDeviceToDevice, bs);
         } else {
-            e = spiir::launch_decimate(x_dev, n, D, b.R, nb, b.xe, b.xe_stride, Dh, s);
+            e = spiir::launch_decimate(x_dev, n, D, b.R, nb, b.xe, b.xe_stride, Dh, bs);
             p->last_launches += 1;
         }
         if (e != cudaSuccess) return cuda_fail(e, "strain staging");
-        if (j != p->top) {
-            if (!b.zb || b.zb_cap < nb) {
-                if (b.zb) {
-                    if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
-                        return cuda_fail(e, "cudaStreamSynchronize");
-                    cudaFree(b.zb);
-                    b.zb = nullptr;
-                }
-                if ((e = dalloc(&b.zb, (size_t)D * p->T * nb)) != cudaSuccess)
-                    return e == cudaErrorMemoryAllocation
-                               ? fail(SPIIR_ENOMEM, "band workspace allocation")
-                               : cuda_fail(e, "cudaMalloc");
-                b.zb_cap = nb;
-            }
-            spiir::K1Args a = k1_args(p, b, nb, reinterpret_cast<float *>(b.zb), nb, false);
-            a.t0 = p->t0 / b.R;
-            st = launch_segmented(p, b, a, segments_for(p, b, nb), s);
-            if (st != SPIIR_OK) return st;
-            spiir::LowerBand &lb = top_args.lower[top_args.n_lower++];
-            lb.z = b.zb;
-            lb.len = nb;
-            lb.R = b.R;
-            lb.shift = -1;
-            for (int sh = 0; sh < 31; ++sh)
-                if ((1 << sh) == b.R) lb.shift = sh;
-        } else {
-            spiir::K1Args a = k1_args(p, b, n, z_dev, n, true);
-            a.t0 = 0;
-            a.t0_dev = p->t0_dev;
-            a.n_lower = top_args.n_lower;
-            // per template: the band samples one block interpolates from
-            int32_t off = 0;
-            for (int i = 0; i < a.n_lower; ++i) {
-                a.lower[i] = top_args.lower[i];
-                a.lower[i].buf_off = off;
-                off += (int32_t)((b.lay.Tb + a.lower[i].R - 1) / a.lower[i].R + 2);
-            }
-            a.low_len = (off + 1) / 2 * 2;
-            st = launch_segmented(p, b, a, segments_for(p, b, n), s, p->t0_dev);
-            if (st != SPIIR_OK) return st;
-        }
-        // band history for the next call: the last Dh band samples of (history, x_b)
+        return SPIIR_OK;
+    };
+    // band history for the next call: the last Dh band samples of (history, x_b)
+    auto keep_history = [&](Band &b, int64_t nb, cudaStream_t bs) -> spiir_status {
+        const int64_t Dh = b.lay.Dh;
         if ((e = cudaMemcpy2DAsync(b.hist, Dh * 4, b.xe + nb, b.xe_stride * 4, Dh * 4, D,
-                                   cudaMemcpyDeviceToDevice, s)) != cudaSuccess)
+                                   cudaMemcpyDeviceToDevice, bs)) != cudaSuccess)
             return cuda_fail(e, "history copy");
+        return SPIIR_OK;
+    };
+    Band &tb = p->bands[p->top];
+    spiir::K1Args ta{};   // the top band's arguments, made once its strain is staged
+    auto stage_top = [&]() -> spiir_status {
+        spiir_status st = stage(tb, n, s);
+        if (st != SPIIR_OK) return st;
+        ta = k1_args(p, tb, n, z_dev, n, true);
+        ta.t0 = 0;
+        ta.t0_dev = p->t0_dev;
+        return SPIIR_OK;
+    };
+    const int top_P = segments_for(p, tb, n);
+    if (fork) {
+        spiir_status st = stage_top();
+        if (st == SPIIR_OK)
+            st = launch_segmented(p, tb, ta, top_P, s, p->t0_dev, kPhaseProject);
+        if (st != SPIIR_OK) return st;
+    }
+    int n_lower_seen = 0;
+    for (int j : order) {
+        if (j == p->top) break;   // the top band comes last (order ends with it)
+        Band &b = p->bands[j];
+        const int64_t nb = (n + b.R - 1) / b.R;   // band samples in this call
+        const cudaStream_t bs = (fork && !(n_lower_seen++ & 1)) ? p->aux : s;
+        spiir_status st = stage(b, nb, bs);
+        if (st != SPIIR_OK) return st;
+        if (!b.zb || b.zb_cap < nb) {
+            if (b.zb) {   // the top band (caller's stream) read it last call
+                if ((e = cudaStreamSynchronize(s)) != cudaSuccess ||
+                    (e = cudaStreamSynchronize(bs)) != cudaSuccess)
+                    return cuda_fail(e, "cudaStreamSynchronize");
+                cudaFree(b.zb);
+                b.zb = nullptr;
+            }
+            if ((e = dalloc(&b.zb, (size_t)D * p->T * nb)) != cudaSuccess)
+                return e == cudaErrorMemoryAllocation
+                           ? fail(SPIIR_ENOMEM, "band workspace allocation")
+                           : cuda_fail(e, "cudaMalloc");
+            b.zb_cap = nb;
+        }
+        spiir::K1Args a = k1_args(p, b, nb, reinterpret_cast<float *>(b.zb), nb, false);
+        a.t0 = p->t0 / b.R;
+        st = launch_segmented(p, b, a, segments_for(p, b, nb), bs);
+        if (st != SPIIR_OK) return st;
+        spiir::LowerBand &lb = top_args.lower[top_args.n_lower++];
+        lb.z = b.zb;
+        lb.len = nb;
+        lb.R = b.R;
+        lb.shift = -1;
+        for (int sh = 0; sh < 31; ++sh)
+            if ((1 << sh) == b.R) lb.shift = sh;
+        if ((st = keep_history(b, nb, bs)) != SPIIR_OK) return st;
+    }
+    if (fork && ((e = cudaEventRecord(p->ev_join, p->aux)) != cudaSuccess ||
+                 (e = cudaStreamWaitEvent(s, p->ev_join, 0)) != cudaSuccess))
+        return cuda_fail(e, "band join");
+    {
+        spiir_status st = fork ? SPIIR_OK : stage_top();
+        if (st != SPIIR_OK) return st;
+        ta.n_lower = top_args.n_lower;
+        // per template: the band samples one block interpolates from
+        int32_t off = 0;
+        for (int i = 0; i < ta.n_lower; ++i) {
+            ta.lower[i] = top_args.lower[i];
+            ta.lower[i].buf_off = off;
+            off += (int32_t)((tb.lay.Tb + ta.lower[i].R - 1) / ta.lower[i].R + 2);
+        }
+        ta.low_len = (off + 1) / 2 * 2;
+        st = launch_segmented(p, tb, ta, top_P, s, p->t0_dev, fork ? kPhaseMain : kPhaseAll);
+        if (st == SPIIR_OK) st = keep_history(tb, n, s);
+        if (st != SPIIR_OK) return st;
     }
     // the last H top-rate samples of (history, x) for the next call's front ends
     if (any_fir && (e = cudaMemcpy2DAsync(p->fir_xh, H * 4, p->fir_xt + n, p->fir_xt_cap * 4,
