@@ -150,8 +150,9 @@ typedef struct spiir_options {
                             /* SPIIR_ADJOINT_REVERSE (the reverse-time recurrence   */
                             /* over a checkpointed forward), _TANGENT (one forward  */
                             /* pass of each filter's derivative recurrences, no     */
-                            /* checkpoints) or _AUTO (tangent when the bank holds   */
-                            /* >= 8 warps per SM at one filter per thread)          */
+                            /* checkpoints) or _AUTO (tangent for calls of <= 8192  */
+                            /* samples, and when the bank holds >= 8 warps per SM  */
+                            /* at one filter per thread, >= 2 without grad_x)      */
     int32_t reserved[1];
 } spiir_options;
 

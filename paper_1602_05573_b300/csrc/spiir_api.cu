@@ -1664,8 +1664,15 @@ spiir_status spiir_filter_backward(spiir_plan *p, const float *x_dev, int64_t n,
                 spiir_status st = build_tangent_order(b, p->T, nf);
                 if (st != SPIIR_OK) return st;
             }
-        tangent = p->opt.adjoint_form == SPIIR_ADJOINT_TANGENT ||
-                  (b.kt_n_pos[0] / 32) * D >= 8 * (int64_t)p->n_sm;
+        // auto: the tangent pass runs every filter over the whole call in one
+        // thread, so it wants a bank of >= 2 warps per SM at one filter per
+        // thread (>= 8 with g_x, whose pass it then shares the GPU with), or a
+        // short call (measured: 7 x 100 filters, 3000 samples, 0.068 vs
+        // 0.163 ms without g_x; 128 x 200, 65536: 1.85 vs 3.22 ms without,
+        // 5.77 vs 4.35 ms with g_x; 64 x 200 x 3 detectors: 4.41 vs 6.24 ms)
+        const int64_t warps1 = (b.kt_n_pos[0] / 32) * D;
+        tangent = p->opt.adjoint_form == SPIIR_ADJOINT_TANGENT || n <= 8192 ||
+                  warps1 >= (grad_x_dev ? 8 : 2) * (int64_t)p->n_sm;
     }
     if (p->opt.adjoint_form == SPIIR_ADJOINT_TANGENT && !tangent)
         return fail(SPIIR_EUNSUPPORTED,

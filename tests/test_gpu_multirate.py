@@ -61,6 +61,21 @@ def test_multirate_parity(sp, n):
     check_peaks(z, zref, pa, pi)
 
 
+@pytest.mark.parametrize("filters,decim", [((40, 60), (1, 2)), ((30, 50, 70, 40), (1, 2, 4, 8))])
+def test_multirate_band_counts(sp, filters, decim):
+    """Two bands (one lower band: no second stream) and four (three lower
+    bands, alternating over the plan's two streams), two detectors, a call
+    ending inside the coarsest band's sample."""
+    bank = make_multirate_bank(9, filters, decim, (0.99, 0.9995), 300, seed=320, n_det=2)
+    n = 6 * 1024 + 8 * 37 + 3
+    x = make_strain(2, n, seed=321)
+    z, pa, pi = gpu_mr(sp, bank, x)
+    zref, _, _ = oracle_mr(bank, x)
+    rel, _ = rel_errors(z, zref)
+    assert rel.max() <= REL_TOL, rel.max()
+    check_peaks(z, zref, pa, pi)
+
+
 def test_multirate_streaming_matches_one_call_outside_hold(sp):
     """Calls of whole multiples of the largest decimation continue the
     stream; only the last 16 samples of each non-final call (interpolated
