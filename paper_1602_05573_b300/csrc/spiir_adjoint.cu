@@ -287,9 +287,14 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
     extern __shared__ __align__(16) unsigned char smem[];
     constexpr int R = kAdjRounds;
     const int n_win = A.G == 16 ? 2 : 1;
+    // g_z ring: window [mc, mc + Wd) of the chunk at output mc, sample j at
+    // position j mod Wd, the first 32 positions mirrored after the end so a
+    // 32-step run never wraps; each chunk after the first brings only its
+    // kK7Chunk new samples
     const int Wd = kK7Chunk + A.Dh;                 // window length
-    float *win = reinterpret_cast<float *>(smem);   // [n_win][2][Wd]: re plane, im plane
-    float *tile = win + n_win * 2 * Wd;             // [W][32][32]
+    const int PL = Wd + 32;                         // plane stride (ring + mirror)
+    float *win = reinterpret_cast<float *>(smem);   // [n_win][2][PL]: re plane, im plane
+    float *tile = win + n_win * 2 * PL;             // [W][32][32]
     float *part = tile + A.W * 1024;                // [W][kK7Chunk]
     float *xsh = part + A.W * kK7Chunk;             // [kK7Chunk] strain of the chunk (TAN)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -307,7 +312,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
     const int wsel = (A.G == 16 && lane >= 16) ? 1 : 0;
     const int tmpl = wsel ? head.w : head.z;
     const float2 *grow = A.gz + ((int64_t)det * A.T + (tmpl >= 0 ? tmpl : 0)) * n;
-    const float *pr = win + wsel * 2 * Wd;
+    const float *pr = win + wsel * 2 * PL;
 
     // slot of round i of task kk at this lane
     auto slot_at = [&](int kk, int i) -> int64_t {
@@ -315,7 +320,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
     };
     // pair p of this lane: the two rounds of task unit.x + NP warp + p
     uint64_t AR[NP], AI[NP], NAI[NP], BR[NP], BI[NP], NR[NP], NI[NP], GBR[NP], GBI[NP];
-    const float *rp[NP][R];
+    int dd[NP][R];   // delays (ring offsets of the window reads)
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
         const int k = NP * warp + p;
@@ -326,7 +331,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
 #pragma unroll
         for (int i = 0; i < R; ++i) {
             ar[i] = ai[i] = br[i] = bi[i] = nu_r[i] = nu_i[i] = 0.f;
-            rp[p][i] = pr;
+            dd[p][i] = 0;
             if (i >= nr) continue;
             const int64_t slot = slot_at(unit.x + k, i);
             const bool odd = (slot & 1) != 0;   // stored as conj(a), (Im b, Re b)
@@ -336,7 +341,7 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
             br[i] = odd ? q.w : q.z;
             bi[i] = odd ? q.z : q.w;
             const int d = A.Dh - A.ringoff[slot].x;
-            rp[p][i] = pr + d;
+            dd[p][i] = d;
             // start state nu[(q + 1) S] = mu[(q + 1) S + d] (zero past the call)
             const int kt = mhi + d;
             if (!TAN && seg + 1 < A.P && kt < n && tmpl >= 0) {
@@ -368,24 +373,42 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
     // x[0 .. n) of this detector (TAN)
     const float *xrow = TAN ? A.xe + (int64_t)det * A.xe_stride + A.Dh : nullptr;
 
-    // g_z window of the chunk starting at output mc, zero from gend on
-    auto stage = [&](int mc) {
+    // g_z samples [j0, j1) into the ring, zero from gend on
+    auto fill = [&](int j0, int j1) {
         for (int w = 0; w < n_win; ++w) {
             const int t = w ? head.w : head.z;
             const float2 *row = A.gz + ((int64_t)det * A.T + (t >= 0 ? t : 0)) * n;
-            float *dr = win + w * 2 * Wd;
-            for (int i = threadIdx.x; i < Wd; i += blockDim.x) {
-                const int j = mc + i;
+            float *dr = win + w * 2 * PL;
+            for (int j = j0 + (int)threadIdx.x; j < j1; j += blockDim.x) {
                 const float2 v = (t >= 0 && j < gend) ? row[j] : make_float2(0.f, 0.f);
-                dr[i] = v.x;
-                dr[Wd + i] = v.y;
+                const int q = j % Wd;
+                dr[q] = v.x;
+                dr[PL + q] = v.y;
+                if (q < 32) {
+                    dr[Wd + q] = v.x;
+                    dr[PL + Wd + q] = v.y;
+                }
             }
         }
     };
-    // one reverse step of pair p at window offset o
-    auto step = [&](int p, int o) {
-        const uint64_t GR = pk(rp[p][0][o], rp[p][1][o]);
-        const uint64_t GI = pk(rp[p][0][Wd + o], rp[p][1][Wd + o]);
+    bool first_chunk = true;
+    auto stage = [&](int mc) {   // the window of the chunk at output mc
+        if (first_chunk) fill(mc, mc + Wd);
+        else fill(mc, mc + kK7Chunk);   // the previous chunk was at mc + kK7Chunk
+        first_chunk = false;
+    };
+    // ring positions of the 32-step run from output m0 up, per pair and round
+    int ob[NP][R];
+    auto run_at = [&](int m0) {
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int i = 0; i < R; ++i) ob[p][i] = (m0 + dd[p][i]) % Wd;
+    };
+    // one reverse step of pair p at output m0 + t of the current run
+    auto step = [&](int p, int t) {
+        const uint64_t GR = pk(pr[ob[p][0] + t], pr[ob[p][1] + t]);
+        const uint64_t GI = pk(pr[PL + ob[p][0] + t], pr[PL + ob[p][1] + t]);
         const uint64_t nR = fma2(AR[p], NR[p], fma2(AI[p], NI[p], GR));
         const uint64_t nI = fma2(AR[p], NI[p], fma2(NAI[p], NR[p], GI));
         NR[p] = nR;
@@ -395,12 +418,17 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
     if (warm) {
         // warm-up over outputs [mhi, mhi + Dh), no output
         for (int c = A.Dh / kK7Chunk - 1; c >= 0; --c) {
-            stage(mhi + c * kK7Chunk);
+            const int mc = mhi + c * kK7Chunk;
+            stage(mc);
             __syncthreads();
             if (active)
-                for (int o = kK7Chunk - 1; o >= 0; --o) {
+                for (int blk = kK7Chunk / 32 - 1; blk >= 0; --blk) {
+                    run_at(mc + blk * 32);
 #pragma unroll
-                    for (int p = 0; p < NP; ++p) step(p, o);
+                    for (int t = 31; t >= 0; --t) {
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) step(p, t);
+                    }
                 }
             __syncthreads();
         }
@@ -454,13 +482,14 @@ __global__ void __launch_bounds__(kK7MaxWarps * 32, 3) k7_adjoint_x(const K7Args
             // g_z = 0 from nu = 0 and give zeros
             for (int blk = (cv + 31) / 32 - 1; blk >= 0; --blk) {
                 const int mb = blk * 32;
+                run_at(mc + mb);
 #pragma unroll
                 for (int t = 31; t >= 0; --t) {
                     float c = 0.f;
                     const float xv = TAN ? xsh[mb + t] : 0.f;
 #pragma unroll
                     for (int p = 0; p < NP; ++p) {
-                        step(p, mb + t);
+                        step(p, t);
                         float c0, c1;
                         upk(fma2(NR[p], BR[p], mul2(NI[p], BI[p])), c0, c1);
                         c += c0 + c1;
@@ -899,7 +928,7 @@ cudaError_t launch_k6(const K6Args &a, int64_t n_units, cudaStream_t s)
 
 int k7_smem_bytes(int Dh, int W, int G)
 {
-    return (int)(sizeof(float) * ((G == 16 ? 2 : 1) * 2 * (kK7Chunk + Dh) + W * 1024 +
+    return (int)(sizeof(float) * ((G == 16 ? 2 : 1) * 2 * (kK7Chunk + Dh + 32) + W * 1024 +
                                   W * kK7Chunk + kK7Chunk));
 }
 
