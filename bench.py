@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "plain", "multirate", "adjoint", "precision", "design",
-                             "veto"])
+                             "veto", "adjoint-forms"])
     ap.add_argument("--precision", default="plain",
                     choices=["plain", "compensated", "chunked_fp64", "chunked_tc"])
     ap.add_argument("--no-graph", action="store_true",
@@ -1073,6 +1073,50 @@ def run_design(args):
     return 0
 
 
+def run_adjoint_forms(args):
+    """The two evaluations of the adjoint's g_a, g_b (reverse and tangent
+    form) on banks from a few templates to thousands, with and without g_x:
+    the crossovers behind the plan's automatic choice.  ms per backward, CUDA
+    events around `steps` calls after `warmup`; one GPU, rank 0."""
+    import torch
+
+    import paper_1602_05573_b300 as sp
+    from spiir_inputs import make_bank, make_strain
+    dev = torch.device("cuda", 0)
+    shapes = [(7, 100, 3000, 1), (16, 64, 16384, 1), (64, 360, 27904, 1), (128, 200, 65536, 1),
+              (256, 200, 65536, 1), (1024, 200, 16384, 1), (64, 200, 65536, 3)]
+    rows = []
+    with ClockSampler(0) as clk:
+        for T, L, n, D in shapes:
+            bank = make_bank(T, L, (0.99, 0.9995), 1024, seed=5, n_det=D)
+            x = torch.from_numpy(make_strain(D, n, seed=6)).to(dev)
+            g = torch.Generator(device=dev).manual_seed(7)
+            gz = torch.randn((D, T, n), dtype=torch.complex64, device=dev, generator=g)
+            row = {"templates": T, "filters": L, "samples": n, "detectors": D}
+            for want_gx in (False, True):
+                for form in ("reverse", "tangent"):
+                    plan = sp.Plan(bank, device=0, adjoint_form=form)
+                    for _ in range(max(1, args.warmup)):
+                        plan.backward(x, gz, want_gx=want_gx)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize(dev)
+                    e0.record()
+                    for _ in range(args.steps):
+                        plan.backward(x, gz, want_gx=want_gx)
+                    e1.record()
+                    torch.cuda.synchronize(dev)
+                    row[f"{form}_{'gx' if want_gx else 'no_gx'}_ms"] = e0.elapsed_time(e1) / args.steps
+                    plan.close()
+            rows.append(row)
+    print(json.dumps({"metric": "ms per backward", "unit": "ms", "higher_is_better": False,
+                      "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "dtype": "f32", "data": "synthetic (seeded N(0,1) strain, random banks)",
+                      "config": {"workload": "adjoint forms: reverse vs tangent over bank sizes"},
+                      "rows": rows, "clocks": clk.summary()}))
+    return 0
+
+
 def run_veto(args):
     """Chi^2 veto on the batched bank: the bank regrouped into 4 frequency
     bins per template (chi2_split), one filter call writing every bin's
@@ -1140,6 +1184,8 @@ def main():
         return run_design(args) if int(os.environ.get("RANK", 0)) == 0 else 0
     if args.workload == "veto" and args.impl != "reference":
         return run_veto(args) if int(os.environ.get("RANK", 0)) == 0 else 0
+    if args.workload == "adjoint-forms" and args.impl != "reference":
+        return run_adjoint_forms(args) if int(os.environ.get("RANK", 0)) == 0 else 0
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
