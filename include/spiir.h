@@ -102,7 +102,9 @@ typedef struct spiir_options {
     int32_t device;         /* CUDA device ordinal; -1 = host-only plan (layout    */
                             /* and statistics, no device memory, no compute)       */
     int32_t autotune;       /* nonzero: time candidate block/copy settings on the  */
-                            /* first spiir_filter call and keep the fastest        */
+                            /* first spiir_filter call and keep the fastest (a     */
+                            /* bank whose calls run in time segments keeps the     */
+                            /* default layout)                                     */
     int32_t max_filters_per_lane; /* 1..10 filters held per thread; templates with */
                             /* more than 32x this many filters span several warps; */
                             /* 0 = default (10)                                    */
@@ -215,7 +217,7 @@ spiir_status spiir_plan_get_info(const spiir_plan *plan, spiir_plan_info *info);
 
 /* The autotuner's timings, one "cap/W/C/Tb/tail=ms" entry per candidate
  * layout ("" before the first call of an autotuned plan, or without
- * autotune).  The string belongs to the plan and lives until its next
+ * autotune; "skipped: ..." when the first call ran in time segments).  The string belongs to the plan and lives until its next
  * spiir_filter call or its destruction. */
 const char *spiir_plan_tune_report(const spiir_plan *plan);
 

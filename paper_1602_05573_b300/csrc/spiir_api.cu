@@ -1097,6 +1097,15 @@ spiir_status autotune(spiir_plan *p, const float *x_dev, int64_t n, cudaStream_t
         {10, 8, 1, 256, -1, false}, {8, 4, 1, 512, -1, false},  {4, 8, 2, 256, -1, false},
         {4, 4, 1, 512, -1, false},  {2, 8, 1, 256, -1, false}};
     const bool forced_launch = p->opt.persistent != 0;
+    // the trials run the candidates unsegmented on a prefix: a call that runs
+    // in time segments (a bank under one wave of 16 warps per SM) would not be
+    // timed the way it runs, so such plans keep the default layout (measured:
+    // the autotuned layout took the adjoint bank's forward from 2.10 to 2.69 ms)
+    if (segments_for(p, p->bands[0], n) > 1) {
+        p->tune_report = "skipped: calls of this bank run in time segments";
+        p->tuned = true;
+        return SPIIR_OK;
+    }
     const int64_t nt = std::min<int64_t>(n, 8192);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e;

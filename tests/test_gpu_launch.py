@@ -103,7 +103,8 @@ def test_batched_workload_persistent_graph_sampled(sp):
 def test_autotune_picks_a_layout_and_stays_exact(sp):
     bank = make_bank(40, (50, 300), (0.99, 0.9995), 1500, seed=152, n_det=2)
     x = make_strain(2, 9000, seed=153)
-    plan = sp.Plan(bank, autotune=True)
+    # unsegmented calls: the autotuner times its candidates the way they run
+    plan = sp.Plan(bank, autotune=True, time_segments=1)
     z = plan.filter(torch.from_numpy(x).cuda()).cpu().numpy()
     pa, pi = plan.peak()
     plan.check()
@@ -116,3 +117,19 @@ def test_autotune_picks_a_layout_and_stays_exact(sp):
     # later calls continue the stream on the chosen layout
     z2 = plan.filter(torch.from_numpy(x[:, :1000].copy()).cuda()).cpu().numpy()
     assert np.isfinite(z2).all()
+
+
+def test_autotune_skips_time_segmented_banks(sp):
+    """A bank whose calls run in time segments keeps the default layout (the
+    autotuner's unsegmented prefix trials would not time it as it runs) and
+    filters exactly."""
+    bank = make_bank(12, (50, 120), (0.99, 0.9995), 500, seed=158)
+    x = make_strain(1, 40000, seed=159)
+    plan = sp.Plan(bank, autotune=True)
+    z = plan.filter(torch.from_numpy(x).cuda()).cpu().numpy()
+    plan.check()
+    assert plan.info()["last_call_segments"] > 1
+    assert plan.tune_report().startswith("skipped")
+    zref, _, _ = oracle.filter_bank(bank.off, bank.a, bank.b, bank.d, x)
+    rel, _ = rel_errors(z, zref)
+    assert rel.max() <= REL_TOL
