@@ -156,6 +156,56 @@ __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb,
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncwarp();
     }
+    // One or two lower bands whose decimation factors divide 32 (and so the
+    // block start k0): lane i always takes samples i mod 32 of the block, so
+    // each band's interpolation weight is fixed per lane and its band sample
+    // advances by 32 / R per step; set up once here instead of per sample.
+    // The arithmetic of each term is that of the general loop below.
+    if (LOW && n_lower >= 1 && n_lower <= 2) {
+        bool fast = true;
+        for (int b = 0; b < n_lower; ++b)
+            fast = fast && A.lower[b].shift >= 0 && A.lower[b].R <= 32 &&
+                   (k0 & (A.lower[b].R - 1)) == 0;
+        if (fast) {
+            const LowerBand &l0 = A.lower[0], &l1 = A.lower[n_lower - 1];
+            const bool two = n_lower == 2;
+            // band sample of this lane's first output, relative to the block's
+            const int r0 = lane >> l0.shift, r1 = lane >> l1.shift;
+            const int st0 = 32 >> l0.shift, st1 = 32 >> l1.shift;
+            const int lo0 = k0 >> l0.shift, lo1 = k0 >> l1.shift;
+            const int last0 = (int)l0.len - 1 - lo0, last1 = (int)l1.len - 1 - lo1;
+            const float f0 = (float)(lane & (l0.R - 1)) / (float)l0.R;
+            const float f1 = (float)(lane & (l1.R - 1)) / (float)l1.R;
+            const float g0 = 1.0f - f0, g1 = 1.0f - f1;
+            const float2 *b0 = low + l0.buf_off, *b1 = low + l1.buf_off;
+            int q0 = r0, q1 = r1;
+            for (int i = lane; i < nv; i += 32, q0 += st0, q1 += st1) {
+                float2 acc = zb[(int64_t)first * A.Tb + i];
+                for (int w = 1; w < nw; ++w) {
+                    const float2 o = zb[(int64_t)(first + w) * A.Tb + i];
+                    acc.x += o.x;
+                    acc.y += o.y;
+                }
+                {
+                    const float2 u = b0[q0], v = b0[q0 + 1 <= last0 ? q0 + 1 : last0];
+                    acc.x += fmaf(f0, v.x, g0 * u.x);
+                    acc.y += fmaf(f0, v.y, g0 * u.y);
+                }
+                if (two) {
+                    const float2 u = b1[q1], v = b1[q1 + 1 <= last1 ? q1 + 1 : last1];
+                    acc.x += fmaf(f1, v.x, g1 * u.x);
+                    acc.y += fmaf(f1, v.y, g1 * u.y);
+                }
+                if (zrow != nullptr) reinterpret_cast<float2 *>(zrow)[k0 + i] = acc;
+                const float p = __fadd_rn(__fmul_rn(acc.x, acc.x), __fmul_rn(acc.y, acc.y));
+                if (p > best) {
+                    best = p;
+                    bidx = k0 + i;
+                }
+            }
+            return;
+        }
+    }
     for (int i = lane; i < nv; i += 32) {
         float2 acc = zb[(int64_t)first * A.Tb + i];
         for (int w = 1; w < nw; ++w) {
