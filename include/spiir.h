@@ -98,7 +98,8 @@ typedef struct spiir_options {
     int32_t block_len;      /* samples per staged strain block; 0 = default       */
     int32_t warps_per_cta;  /* templates per CTA; 0 = chosen from the bank size   */
     int32_t ring_copies;    /* bank-skewed copies of the strain ring: 1, 2 or 4;  */
-                            /* 0 = default                                        */
+                            /* 0 = default: 2 for full-warp layouts of at most 4  */
+                            /* filters per lane (per band), else 1               */
     int32_t device;         /* CUDA device ordinal; -1 = host-only plan (layout    */
                             /* and statistics, no device memory, no compute)       */
     int32_t autotune;       /* nonzero: time candidate block/copy settings on the  */

@@ -295,7 +295,7 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
         *err = "layout: block_len must be a multiple of 32 in [32, 4096]";
         return false;
     }
-    L.C = opt.C == 0 ? 1 : opt.C;
+    L.C = opt.C == 0 ? 1 : opt.C;   // the default is settled below, once F is known
     if (L.C != 1 && L.C != 2 && L.C != 4) {
         *err = "layout: ring_copies must be 1, 2 or 4";
         return false;
@@ -371,8 +371,27 @@ bool build_layout(const std::vector<std::vector<int64_t>> &filters, int D, const
     L.S = L.H + 2;
     L.R = L.S * L.Tb;
     L.Dh = L.H * L.Tb;
-    const int skew = L.C == 1 ? 0 : 32 / L.C;   // bank offset between copies
-    L.CS = L.R + L.Tb + skew;                    // R + Tb is a multiple of 32
+    auto set_copies = [&L](int C) {
+        L.C = C;
+        const int skew = C == 1 ? 0 : 32 / C;   // bank offset between copies
+        L.CS = L.R + L.Tb + skew;               // R + Tb is a multiple of 32
+    };
+    set_copies(L.C);
+    // default copies: with at most 4 filters per lane the strain reads and
+    // the cross-lane sums of a step are few enough that bank conflicts bound
+    // the shared-memory pipe, and a second copy (the placement then spreads a
+    // round over more banks) pays for its larger ring; full warps only
+    // (measured on 2048-template bands: 2 filters per lane 64.8 -> 54.7 ms,
+    // 4 per lane 24.9 -> 23.5 ms; 4 copies no faster than 2; half-warp
+    // templates and banks of more filters per lane no faster with 2)
+    if (opt.C == 0 && L.G == 32) {
+        int maxF = 0;
+        for (int64_t t = 0; t < L.T; ++t) maxF = std::max(maxF, F[t]);
+        if (maxF <= 4) {
+            set_copies(2);
+            if (L.smem_bytes() > 227 * 1024) set_copies(1);
+        }
+    }
     if (L.smem_bytes() > 227 * 1024) {
         *err = "layout: strain ring and partial sums need " + std::to_string(L.smem_bytes()) +
                " bytes of shared memory (max delay " + std::to_string(maxd) +

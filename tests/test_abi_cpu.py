@@ -166,6 +166,26 @@ def test_batched_layout_statistics():
         assert info["smem_bytes"] <= 227 * 1024
 
 
+def test_default_ring_copies_follow_filters_per_lane():
+    """With ring_copies = 0 a full-warp layout of at most 4 filters per lane
+    takes two bank-skewed ring copies (fewer conflicts where the strain
+    reads bound the shared-memory pipe), larger ones one; an explicit count
+    is kept as given."""
+    from spiir_inputs import make_bank
+    few = make_bank(16, 64, (0.99, 0.9995), 1024, seed=5)      # 2 filters per lane
+    many = make_bank(16, 300, (0.99, 0.9995), 1024, seed=5)    # 10 filters per lane
+    info = sp.Plan(few, device=-1).info()
+    assert (info["lanes_per_template"], info["max_filters_per_lane"]) == (32, 2)
+    assert info["ring_copies"] == 2
+    assert sp.Plan(few, device=-1, ring_copies=1).info()["ring_copies"] == 1
+    assert sp.Plan(few, device=-1, ring_copies=4).info()["ring_copies"] == 4
+    assert sp.Plan(few, device=-1, lanes_per_template=16).info()["ring_copies"] == 1
+    assert sp.Plan(many, device=-1).info()["ring_copies"] == 1
+    # the second copy spreads each round over more banks
+    assert (sp.Plan(few, device=-1).info()["bank_conflict_ratio"]
+            < sp.Plan(few, device=-1, ring_copies=1).info()["bank_conflict_ratio"])
+
+
 def test_multirate_plan_layout_and_validation():
     from spiir_inputs import make_multirate_bank
     bank = make_multirate_bank(5, (7, 40, 3), (1, 4, 16), (0.9, 0.99), 50, seed=9)
