@@ -865,8 +865,24 @@ spiir_status launch_anchored(spiir_plan *p, Band &b, spiir::K1Args a, cudaStream
     const int64_t max_chunks = p->opt.tile_chunks > 0
                                    ? (int64_t)p->opt.tile_chunks
                                    : std::max<int64_t>(1, budget / (8 * per));
+    const int64_t hq = L.Dh / spiir::kTcT;
     int64_t n_tile = std::max<int64_t>(unit, max_chunks * spiir::kTcT / unit * unit);
     n_tile = std::min<int64_t>(n_tile, (n + unit - 1) / unit * unit);
+    if (p->opt.tile_chunks <= 0) {
+        // a tile's windows (chunks + hq) fill whole column tiles of the GEMM:
+        // at most the budget's whole column tiles, the call split evenly over
+        // as few tiles as that allows (a tile 4 windows past 512 would take a
+        // third, almost empty, column tile)
+        const int64_t u = unit / spiir::kTcT;   // chunks per whole unit
+        const int64_t cols = spiir::tc_cols_per_tile();
+        const int64_t cap = (n_tile / spiir::kTcT + hq) / cols * cols - hq;
+        const int64_t n_chunks = (n + spiir::kTcT - 1) / spiir::kTcT;
+        if (cap >= u && n_chunks > cap) {
+            const int64_t n_tiles = (n_chunks + cap - 1) / cap;
+            const int64_t per_tile = ((n_chunks + n_tiles - 1) / n_tiles + u - 1) / u * u;
+            n_tile = std::min<int64_t>(n_tile, per_tile * spiir::kTcT);
+        }
+    }
     const int64_t chunks = n_tile / spiir::kTcT;
     if (b.tc_anchor_cap < chunks * per) {
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -878,7 +894,6 @@ spiir_status launch_anchored(spiir_plan *p, Band &b, spiir::K1Args a, cudaStream
                                                   : cuda_fail(e, "cudaMalloc");
         b.tc_anchor_cap = chunks * per;
     }
-    const int64_t hq = L.Dh / spiir::kTcT;
     st = ensure_tc_strain(b, spiir::tc_strain_bytes(chunks + hq, D), s);
     if (st != SPIIR_OK) return st;
     const int64_t tiles = (n + n_tile - 1) / n_tile;

@@ -39,6 +39,8 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <climits>
 #include <cstdint>
 
 namespace spiir {
@@ -73,6 +75,16 @@ __device__ __forceinline__ void split_bf16(float v, uint16_t &hi, uint16_t &lo)
 {
     hi = bf16_bits(v);
     lo = bf16_bits(v - bf16_val(hi));
+}
+// the same split of two values at once: hi and lo words hold (v0, v1) as
+// BF16 pairs, v0 in the low half
+__device__ __forceinline__ void split_bf16x2(float v0, float v1, uint32_t &hi, uint32_t &lo)
+{
+    const __nv_bfloat162 h2 = __floats2bfloat162_rn(v0, v1);
+    hi = *reinterpret_cast<const uint32_t *>(&h2);
+    const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+    const __nv_bfloat162 l2 = __floats2bfloat162_rn(v0 - h0, v1 - h1);
+    lo = *reinterpret_cast<const uint32_t *>(&l2);
 }
 
 // ---- float-float (hi + lo) arithmetic on the FP32 pipe ---------------------
@@ -251,65 +263,107 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // windows (the strain tiles in HBM are 256 wide; a 128-wide column tile is
 // one half of one).
 // Generator thread t of the CTA's M-tile mt: slot 64 mt + (t & 63), the
-// 32-wide half (t >> 6) of K-block kb.  V at m = 32 (2 kb + h) + j is walked
-// from the seed at the group's largest valid m down to its smallest, one
-// complex multiply by a (kernel form) per step, and written as BF16 hi/lo
-// into the stage's A tiles (rows 2 s and 2 s + 1 = Re and Im).
-__device__ __forceinline__ void gen_weights(const TcArgs &A, int64_t mt, int kb, int t,
-                                            unsigned char *stage)
-{
-    const int sl = t & 63, h = t >> 6;
-    const int64_t slot = mt * (kRowsTile / 2) + sl;
-    const int g = 2 * kb + h;
-    float ar = 0.f, ai = 0.f, cr = 0.f, ci = 0.f;
-    int m_lo = 1, m_hi = 0;   // valid m of this group (empty by default)
-    if (slot < A.n_slots) {
-        const float4 p = A.params[slot];
-        ar = p.x;
-        ai = p.y;
-        const int r = (A.Dh - A.ringoff[slot].x) % kTcT;
-        m_hi = min(g * kSeedGroup + kSeedGroup - 1, 2 * kTcT - r - 1);
-        m_lo = max(g * kSeedGroup, kTcT - r);
-        const float2 sd = A.seed[slot * kTcSeeds + g];
-        cr = sd.x;
-        ci = sd.y;
-    }
-    const int row = 2 * sl;
-    const int k0 = h * kSeedGroup;   // k of m = 32 g inside the K-block
-    // eight k at a time, from the top of the group down
-#pragma unroll
-    for (int q = kSeedGroup / 8 - 1; q >= 0; --q) {
-        uint16_t hr[8], lr[8], hi_[8], li[8];
-#pragma unroll
-        for (int j = 7; j >= 0; --j) {
-            const int m = g * kSeedGroup + 8 * q + j;
-            float vr = 0.f, vi = 0.f;
-            if (m >= m_lo && m <= m_hi) {
-                vr = cr;
-                vi = ci;
-                const float nr = __fmaf_rn(cr, ar, -__fmul_rn(ci, ai));
-                ci = __fmaf_rn(cr, ai, __fmul_rn(ci, ar));
-                cr = nr;
-            }
-            split_bf16(vr, hr[j], lr[j]);
-            split_bf16(vi, hi_[j], li[j]);
+// 32-wide half (t >> 6) of each K-block.  V at m = 32 g + 31 - i (i = 0..31
+// from the group's top) is seed a^(i - i0) for the valid m (i >= i0, the
+// seed's position); four independent chains, one per i mod 4, each start at
+// seed a^e (e = 0..3, the chain's first valid position) and step by a^4, so
+// a walk is 8 dependent complex multiplies, not 32.  Values are written as
+// BF16 hi/lo into the stage's A tiles (rows 2 s and 2 s + 1 = Re and Im),
+// two per packed conversion.
+struct WeightGen {
+    int64_t slot;
+    int sl, h, r;
+    bool valid;
+    float ar, ai, a2r, a2i, a3r, a3i, a4r, a4i;   // a^1..a^4 (kernel form), FP64 rounded once
+
+    __device__ __forceinline__ void init(const TcArgs &A, int64_t mt, int t)
+    {
+        sl = t & 63;
+        h = t >> 6;
+        slot = mt * (kRowsTile / 2) + sl;
+        valid = slot < A.n_slots;
+        r = 0;
+        ar = ai = a2r = a2i = a3r = a3i = a4r = a4i = 0.f;
+        if (valid) {
+            const float4 p = A.params[slot];
+            r = (A.Dh - A.ringoff[slot].x) % kTcT;
+            double pr, pi;
+            ar = p.x;
+            ai = p.y;
+            cpow64(p.x, p.y, 2, pr, pi);
+            a2r = (float)pr;
+            a2i = (float)pi;
+            cpow64(p.x, p.y, 3, pr, pi);
+            a3r = (float)pr;
+            a3i = (float)pi;
+            cpow64(p.x, p.y, 4, pr, pi);
+            a4r = (float)pr;
+            a4i = (float)pi;
         }
-        const int kl = k0 + 8 * q;
-        uint4 v;
-        v.x = hr[0] | ((uint32_t)hr[1] << 16); v.y = hr[2] | ((uint32_t)hr[3] << 16);
-        v.z = hr[4] | ((uint32_t)hr[5] << 16); v.w = hr[6] | ((uint32_t)hr[7] << 16);
-        *reinterpret_cast<uint4 *>(stage + tile_off(row, kl)) = v;
-        v.x = lr[0] | ((uint32_t)lr[1] << 16); v.y = lr[2] | ((uint32_t)lr[3] << 16);
-        v.z = lr[4] | ((uint32_t)lr[5] << 16); v.w = lr[6] | ((uint32_t)lr[7] << 16);
-        *reinterpret_cast<uint4 *>(stage + kTileBytes + tile_off(row, kl)) = v;
-        v.x = hi_[0] | ((uint32_t)hi_[1] << 16); v.y = hi_[2] | ((uint32_t)hi_[3] << 16);
-        v.z = hi_[4] | ((uint32_t)hi_[5] << 16); v.w = hi_[6] | ((uint32_t)hi_[7] << 16);
-        *reinterpret_cast<uint4 *>(stage + tile_off(row + 1, kl)) = v;
-        v.x = li[0] | ((uint32_t)li[1] << 16); v.y = li[2] | ((uint32_t)li[3] << 16);
-        v.z = li[4] | ((uint32_t)li[5] << 16); v.w = li[6] | ((uint32_t)li[7] << 16);
-        *reinterpret_cast<uint4 *>(stage + kTileBytes + tile_off(row + 1, kl)) = v;
     }
-}
+    // seed of generator thread t's slot in M-tile mt, K-block kb
+    static __device__ __forceinline__ float2 seed_at(const TcArgs &A, int64_t mt, int t, int kb)
+    {
+        const int64_t sl = mt * (kRowsTile / 2) + (t & 63);
+        return sl < A.n_slots ? A.seed[sl * kTcSeeds + 2 * kb + (t >> 6)] : make_float2(0.f, 0.f);
+    }
+    __device__ __forceinline__ void gen(int kb, float2 sd, unsigned char *stage) const
+    {
+        const int g = 2 * kb + h;
+        int m_lo = 1, m_hi = 0;   // valid m of this group (empty by default)
+        if (valid) {
+            m_hi = min(g * kSeedGroup + kSeedGroup - 1, 2 * kTcT - r - 1);
+            m_lo = max(g * kSeedGroup, kTcT - r);
+        }
+        const int i0 = g * kSeedGroup + kSeedGroup - 1 - m_hi;   // >= 0 when valid
+        // seed a^e, e = 0..3
+        const float s1r = __fmaf_rn(sd.x, ar, -__fmul_rn(sd.y, ai)), s1i = __fmaf_rn(sd.x, ai, __fmul_rn(sd.y, ar));
+        const float s2r = __fmaf_rn(sd.x, a2r, -__fmul_rn(sd.y, a2i)), s2i = __fmaf_rn(sd.x, a2i, __fmul_rn(sd.y, a2r));
+        const float s3r = __fmaf_rn(sd.x, a3r, -__fmul_rn(sd.y, a3i)), s3i = __fmaf_rn(sd.x, a3i, __fmul_rn(sd.y, a3r));
+        float cr[4], ci[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = (k - i0) & 3;
+            cr[k] = e == 0 ? sd.x : e == 1 ? s1r : e == 2 ? s2r : s3r;
+            ci[k] = e == 0 ? sd.y : e == 1 ? s1i : e == 2 ? s2i : s3i;
+        }
+        const int row = 2 * sl;
+        const int k0 = h * kSeedGroup;   // k of m = 32 g inside the K-block
+        // eight k at a time, from the top of the group down
+#pragma unroll
+        for (int q = kSeedGroup / 8 - 1; q >= 0; --q) {
+            float vr[8], vi[8];
+#pragma unroll
+            for (int j = 7; j >= 0; --j) {
+                const int m = g * kSeedGroup + 8 * q + j;
+                const int k = 3 - (j & 3);   // chain of position i = 31 - 8 q - j
+                vr[j] = 0.f;
+                vi[j] = 0.f;
+                if (m >= m_lo && m <= m_hi) {
+                    vr[j] = cr[k];
+                    vi[j] = ci[k];
+                    const float nr = __fmaf_rn(cr[k], a4r, -__fmul_rn(ci[k], a4i));
+                    ci[k] = __fmaf_rn(cr[k], a4i, __fmul_rn(ci[k], a4r));
+                    cr[k] = nr;
+                }
+            }
+            uint32_t hr[4], lr[4], hi_[4], li[4];
+#pragma unroll
+            for (int p2 = 0; p2 < 4; ++p2) {
+                split_bf16x2(vr[2 * p2], vr[2 * p2 + 1], hr[p2], lr[p2]);
+                split_bf16x2(vi[2 * p2], vi[2 * p2 + 1], hi_[p2], li[p2]);
+            }
+            const int kl = k0 + 8 * q;
+            *reinterpret_cast<uint4 *>(stage + tile_off(row, kl)) = make_uint4(hr[0], hr[1], hr[2], hr[3]);
+            *reinterpret_cast<uint4 *>(stage + kTileBytes + tile_off(row, kl)) =
+                make_uint4(lr[0], lr[1], lr[2], lr[3]);
+            *reinterpret_cast<uint4 *>(stage + tile_off(row + 1, kl)) =
+                make_uint4(hi_[0], hi_[1], hi_[2], hi_[3]);
+            *reinterpret_cast<uint4 *>(stage + kTileBytes + tile_off(row + 1, kl)) =
+                make_uint4(li[0], li[1], li[2], li[3]);
+        }
+    }
+};
 
 constexpr int kGenThreads = 128;
 constexpr int kProjThreads = kEpiThreads + 32 + kGenThreads;
@@ -324,8 +378,14 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
     __shared__ __align__(8) uint64_t bars[3 * kStages + 4];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int64_t mt = blockIdx.x;
     const int det = blockIdx.y;
+    // persistent CTAs: M-tiles blockIdx.x, + gridDim.x, ...; the column tiles
+    // of consecutive M-tiles run back to back (tile u = i n_ntiles + nt of
+    // the CTA's i-th M-tile), so one M-tile's last scan overlaps the next
+    // one's MMAs
+    const int64_t mtiles = (2 * A.n_slots + kRowsTile - 1) / kRowsTile;
+    const int n_local = blockIdx.x < mtiles
+                            ? (int)((mtiles - 1 - blockIdx.x) / gridDim.x) + 1 : 0;
     const uint32_t full0 = smem_addr(&bars[0]), empty0 = smem_addr(&bars[kStages]);
     // generated weight tile of a stage written (all generator threads)
     const uint32_t wfull0 = smem_addr(&bars[2 * kStages + 4]);
@@ -358,34 +418,47 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     const int n_ntiles = A.n_ntiles;
+    const int total = n_local * n_ntiles * kKBlocks;   // K-blocks of this CTA
+    auto mt_of = [&](int u) { return (int64_t)blockIdx.x + (int64_t)(u / n_ntiles) * gridDim.x; };
     bool ok = true;
 
     if (warp > 4) {
         // weight generators: stage it % kStages gets K-block it % kKBlocks once
         // the MMAs that read the stage before (block it - kStages) are done
         const int t = tid - kEpiThreads - 32;
-        const int total = n_ntiles * kKBlocks;
+        WeightGen wg;
+        int64_t cur_mt = -1;
+        float2 sd = total > 0 ? WeightGen::seed_at(A, mt_of(0), t, 0) : make_float2(0.f, 0.f);
         for (int it = 0; it < total; ++it) {
             const int st = it % kStages;
+            const int64_t mt = mt_of(it / kKBlocks);
+            if (mt != cur_mt) {
+                wg.init(A, mt, t);
+                cur_mt = mt;
+            }
+            // the next K-block's seed, loaded while this one is generated
+            const float2 sd_next =
+                it + 1 < total ? WeightGen::seed_at(A, mt_of((it + 1) / kKBlocks), t, (it + 1) % kKBlocks)
+                               : sd;
             if (it >= kStages &&
                 !mbar_wait(empty0 + 8 * st, (uint32_t)((it / kStages - 1) & 1), A.wait_limit_ns)) {
                 atomicOr(A.err, 8);
                 break;
             }
-            gen_weights(A, mt, it % kKBlocks, t, smem + st * kSB);
+            wg.gen(it % kKBlocks, sd, smem + st * kSB);
             // generic-proxy writes, read next by the tensor cores (async proxy)
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(wfull0 + 8 * st);
+            sd = sd_next;
         }
     } else if (warp == 4) {
         if (lane == 0) {
             // producer + MMA issue, two stages
-            const int total = n_ntiles * kKBlocks;
             const unsigned char *bt =
                 A.B + (int64_t)det * A.n_btiles * kKBlocks * 2 * kBTileBytes;
             auto fill = [&](int it) {
                 const int st = it % kStages;
-                const int nt = it / kKBlocks, kb = it % kKBlocks;
+                const int nt = (it / kKBlocks) % n_ntiles, kb = it % kKBlocks;
                 const uint32_t dst = smem_addr(smem) + st * kSB;
                 const uint32_t full = full0 + 8 * st;
                 mbar_expect_tx(full, 2u * kBT);
@@ -406,16 +479,16 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
             if (total > 0) fill(0);
             for (int it = 0; it < total && ok; ++it) {
                 const int st = it % kStages;
-                const int nt = it / kKBlocks, kb = it % kKBlocks;
+                const int u = it / kKBlocks, kb = it % kKBlocks;   // accumulator tile, K-block
                 ok = mbar_wait(full0 + 8 * st, (uint32_t)((it / kStages) & 1), A.wait_limit_ns) &&
                      mbar_wait(wfull0 + 8 * st, (uint32_t)((it / kStages) & 1), A.wait_limit_ns);
-                if (ok && kb == 0 && nt >= 2)   // epilogue has read tile nt - 2 (same TMEM)
-                    ok = mbar_wait(acc_empty0 + 8 * (nt & 1), (uint32_t)(((nt - 2) >> 1) & 1),
+                if (ok && kb == 0 && u >= 2)   // epilogue has read tile u - 2 (same TMEM)
+                    ok = mbar_wait(acc_empty0 + 8 * (u & 1), (uint32_t)(((u - 2) >> 1) & 1),
                                    A.wait_limit_ns);
                 if (!ok) break;
                 tc_fence_after();
                 const uint32_t s0 = smem_addr(smem) + st * kSB;
-                const uint32_t acc = tmem + (uint32_t)((nt & 1) * NT);
+                const uint32_t acc = tmem + (uint32_t)((u & 1) * NT);
 #pragma unroll
                 for (int kk = 0; kk < kKBlk / 16; ++kk) {
                     const uint32_t adv = kk * 256u;   // 16 K = two core matrices
@@ -427,7 +500,7 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
                     umma_bf16(acc, al, bh, kIdesc, 1u);
                 }
                 umma_commit(empty0 + 8 * st);          // stage free once these MMAs finish
-                if (kb == kKBlocks - 1) umma_commit(acc_full0 + 8 * (nt & 1));
+                if (kb == kKBlocks - 1) umma_commit(acc_full0 + 8 * (u & 1));
                 if (it + 1 < total) {
                     const int nx = it + 1, sx = nx % kStages;
                     if (nx >= kStages)
@@ -442,6 +515,8 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
         // epilogue: row = TMEM lane; rows 2s, 2s+1 are Re and Im of slot s
         const int row = warp * 32 + lane;
         const int comp = row & 1;
+        for (int mi = 0; mi < n_local && ok; ++mi) {
+        const int64_t mt = mt_of(mi * n_ntiles);
         const int64_t slot = mt * (kRowsTile / 2) + (row >> 1);
         const bool valid = slot < A.n_slots;
         const int64_t ds = (int64_t)det * A.n_slots + slot;
@@ -463,8 +538,75 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
                 if (comp == 0) A.seg_init[ds] = s;
             }
         }
+        // global column col carries chunk c = col + cq of this row
+        const int cq = A.col0 + q + 1;
+        // the columns whose chunks this row's scan uses, [col_lo, col_hi), and
+        // their union over the warp: 16-column groups outside it are skipped
+        int col_lo = ANCH ? A.c_first - cq : -cq;
+        int col_hi = ANCH ? A.c_end - cq : A.c_last + 1 - cq;
+        if (!valid) {
+            col_lo = INT_MAX;
+            col_hi = INT_MIN;
+        }
+        const int w_lo = __reduce_min_sync(0xffffffffu, col_lo);
+        const int w_hi = __reduce_max_sync(0xffffffffu, col_hi);
+        // ANCH, two chunks per step: s(c+2) = A^2 s(c) + (A g(c) + g(c+1)),
+        // A = a^T.  Per thread, the complex product's own component is
+        // P_r x_mine + sigma P_i x_other (sigma = -1 for Re, +1 for Im).
+        ff A2r = {0.f, 0.f}, sA2i = {0.f, 0.f}, saTi = {0.f, 0.f};
+        float ar32 = 0.f, ai32 = 0.f;
+        if (ANCH) {
+            A2r = ff_add(ff_mul(aTr, aTr), ff_neg(ff_mul(aTi, aTi)));
+            const ff p = ff_mul(aTr, aTi);
+            const ff A2i = {2.f * p.h, 2.f * p.l};
+            sA2i = comp ? A2i : ff_neg(A2i);
+            saTi = comp ? aTi : ff_neg(aTi);
+            ar32 = __fadd_rn(aTr.h, aTr.l);
+            ai32 = __fadd_rn(aTi.h, aTi.l);
+        }
+        // non-ANCH: the next chunk after which a segment starts, and its index
+        int nxt = A.cps - 1, seg_b = 1;
+        // ANCH with odd cq: the last column of a group waits for its pair
+        const int par = cq & 1;
+        float pend = 0.f;
+        int pend_c = A.c_end;   // no chunk (>= c_end)
+        // one chunk: the anchor (state before chunk c), then the state advances
+        // (ANCH: rows with en false only take part in the shuffles)
+        auto step1 = [&](float g, int c, bool en = true) {
+            if (ANCH) {
+                // each thread advances its own component; the other one comes
+                // from the partner lane (Re <-> Im)
+                const ff other = {__shfl_xor_sync(0xffffffffu, mine.h, 1),
+                                  __shfl_xor_sync(0xffffffffu, mine.l, 1)};
+                if (en && valid && c >= A.c_first && c < A.c_end) {
+                    const ff sr = comp ? other : mine, si = comp ? mine : other;
+                    if (comp == 0)
+                        A.anchors[(int64_t)(c - A.c_first) * A.D * A.n_slots + ds] =
+                            make_float2(__fadd_rn(sr.h, sr.l), __fadd_rn(si.h, si.l));
+                    if (c < A.c_full) {   // a partial last chunk only gets its anchor
+                        // Re: aTr sr - aTi si + g;  Im: aTr si + aTi sr + g
+                        const ff t = ff_add(ff_mul(aTr, mine), ff_mul(saTi, other));
+                        mine = ff_add(t, ff{g, 0.f});
+                    }
+                }
+            } else {
+                const float other = __shfl_xor_sync(0xffffffffu, g, 1);
+                const float gr = comp ? other : g, gi = comp ? g : other;
+                if (valid && c >= 0 && c <= A.c_last) {
+                    const float nr = fmaf(aT.x, s.x, fmaf(-aT.y, s.y, gr));
+                    const float ni = fmaf(aT.x, s.y, fmaf(aT.y, s.x, gi));
+                    s = make_float2(nr, ni);
+                    if (c == nxt) {   // segment seg_b starts after chunk c
+                        if (comp == 0) A.seg_init[((int64_t)seg_b * A.D + det) * A.n_slots + slot] = s;
+                        nxt += A.cps;
+                        ++seg_b;
+                    }
+                }
+            }
+        };
         for (int nt = 0; nt < n_ntiles; ++nt) {
-            ok = mbar_wait(acc_full0 + 8 * (nt & 1), (uint32_t)((nt >> 1) & 1), A.wait_limit_ns) &&
+            const int u = mi * n_ntiles + nt;
+            ok = mbar_wait(acc_full0 + 8 * (u & 1), (uint32_t)((u >> 1) & 1), A.wait_limit_ns) &&
                  ok;
             if (!__all_sync(0xffffffffu, ok)) {
                 ok = false;
@@ -472,6 +614,8 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
             }
             tc_fence_after();
             for (int c0 = 0; c0 < NT; c0 += 16) {
+                const int gcol = nt * NT + c0;
+                if (gcol + 16 <= w_lo || gcol >= w_hi) continue;   // warp-uniform
                 uint32_t v[16];
                 asm volatile(
                     "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,"
@@ -480,54 +624,66 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
                       "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]),
                       "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
                     : "r"(tmem + ((uint32_t)(warp * 32) << 16) +
-                          (uint32_t)((nt & 1) * NT + c0)));
+                          (uint32_t)((u & 1) * NT + c0)));
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (ANCH) {
+                    // pairs start at even chunks of the call: at even columns
+                    // for even cq, odd columns (the first with the previous
+                    // group's last) for odd cq
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const float g = __uint_as_float(v[j]);
-                    // window c'' = col + col0 feeds chunk c = c'' + q + 1
-                    const int64_t c = (int64_t)nt * NT + c0 + j + A.col0 + q + 1;
-                    if (ANCH) {
-                        // each thread advances its own component; the other one
-                        // comes from the partner lane (Re <-> Im)
-                        const ff other = {__shfl_xor_sync(0xffffffffu, mine.h, 1),
-                                          __shfl_xor_sync(0xffffffffu, mine.l, 1)};
-                        if (valid && c >= A.c_first && c < A.c_end) {
-                            const ff sr = comp ? other : mine, si = comp ? mine : other;
-                            if (comp == 0)
-                                A.anchors[(c - A.c_first) * A.D * A.n_slots + ds] =
-                                    make_float2(__fadd_rn(sr.h, sr.l), __fadd_rn(si.h, si.l));
-                            if (c < A.c_full) {   // a partial last chunk only gets its anchor
-                                // Re: aTr sr - aTi si + g;  Im: aTr si + aTi sr + g
-                                const ff t = comp == 0 ? ff_add(ff_mul(aTr, sr), ff_mul(ff_neg(aTi), si))
-                                                       : ff_add(ff_mul(aTr, si), ff_mul(aTi, sr));
-                                mine = ff_add(t, ff{g, 0.f});
-                            }
+                    for (int k = 0; k < 8; ++k) {
+                        const float ga = par ? (k == 0 ? pend : __uint_as_float(v[2 * k - 1 + (k == 0)]))
+                                             : __uint_as_float(v[2 * k]);
+                        const float gb = par ? __uint_as_float(v[2 * k]) : __uint_as_float(v[2 * k + 1]);
+                        const int c = gcol + 2 * k - par + cq;
+                        // both chunks anchored and advanced: one paired step.  A
+                        // row's pairs depend on its chunk parity alone (not on its
+                        // warp), so a call split at even chunks repeats them exactly
+                        const bool two = valid && c >= A.c_first && c + 1 < A.c_end &&
+                                         c + 1 < A.c_full;
+                        const bool all_two = __all_sync(0xffffffffu, two || !valid);
+                        const float oga = __shfl_xor_sync(0xffffffffu, ga, 1);
+                        const ff o = {__shfl_xor_sync(0xffffffffu, mine.h, 1),
+                                      __shfl_xor_sync(0xffffffffu, mine.l, 1)};
+                        // this thread's component of A g(c) + g(c+1)
+                        const ff h = ff_add(ff_add(ff_mul(aTr, ff{ga, 0.f}),
+                                                   ff_mul(saTi, ff{oga, 0.f})),
+                                            ff{gb, 0.f});
+                        if (two && comp == 0) {
+                            // anchors of chunks c (the carried state, rounded)
+                            // and c + 1 (A s + g(c), in FP32 from the rounded state)
+                            const float r = __fadd_rn(mine.h, mine.l), i = __fadd_rn(o.h, o.l);
+                            float2 *an = A.anchors + (int64_t)(c - A.c_first) * A.D * A.n_slots + ds;
+                            an[0] = make_float2(r, i);
+                            an[(int64_t)A.D * A.n_slots] =
+                                make_float2(fmaf(ar32, r, fmaf(-ai32, i, ga)),
+                                            fmaf(ar32, i, fmaf(ai32, r, oga)));
                         }
-                    } else {
-                        const float other = __shfl_xor_sync(0xffffffffu, g, 1);
-                        const float gr = comp ? other : g, gi = comp ? g : other;
-                        if (valid && c >= 0 && c <= A.c_last) {
-                            const float nr = fmaf(aT.x, s.x, fmaf(-aT.y, s.y, gr));
-                            const float ni = fmaf(aT.x, s.y, fmaf(aT.y, s.x, gi));
-                            s = make_float2(nr, ni);
-                            if ((c + 1) % A.cps == 0 && comp == 0) {
-                                const int64_t b = (c + 1) / A.cps;   // segment starting here
-                                A.seg_init[(b * A.D + det) * A.n_slots + slot] = s;
-                            }
+                        const ff paired = ff_add(ff_add(ff_mul(A2r, mine), ff_mul(sA2i, o)), h);
+                        if (!all_two) {   // rows at a range edge: one chunk at a time
+                            step1(ga, c, !two);
+                            step1(gb, c + 1, !two);
                         }
+                        if (two) mine = paired;
                     }
+                    pend = __uint_as_float(v[15]);
+                    pend_c = gcol + 15 + cq;
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) step1(__uint_as_float(v[j]), gcol + j + cq);
                 }
             }
             tc_fence_before();
-            mbar_arrive(acc_empty0 + 8 * (nt & 1));
+            mbar_arrive(acc_empty0 + 8 * (u & 1));
         }
-        if (ANCH) {   // carried FP64 state after the last chunk
+        if (ANCH) {   // the last column of an odd-cq row, then the carried FP64 state
+            if (ok) step1(par ? pend : 0.f, par ? pend_c : A.c_end);
             const float oh = __shfl_xor_sync(0xffffffffu, mine.h, 1);
             const float ol = __shfl_xor_sync(0xffffffffu, mine.l, 1);
             if (ok && valid && comp == 0)
                 A.s64[ds] = make_double2((double)mine.h + (double)mine.l, (double)oh + (double)ol);
         }
+        }   // M-tiles
         if (!ok && lane == 0) atomicOr(A.err, 8);
     }
     tc_fence_before();
@@ -590,7 +746,13 @@ template <bool ANCH, int NT> cudaError_t launch_project_nt(TcArgs a, int64_t mti
     if (e != cudaSuccess) return e;
     a.n_ntiles = (int32_t)((a.n_cols + NT - 1) / NT);
     a.n_btiles = (int32_t)((a.n_cols + kColsTile - 1) / kColsTile);
-    tc_project_kernel<ANCH, NT><<<dim3((unsigned)mtiles, (unsigned)a.D), kProjThreads, smem, s>>>(a);
+    // one resident CTA per SM (its shared memory), the M-tiles dealt round robin
+    int dev = 0, n_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess ||
+        (e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return e;
+    const int64_t gx = std::min<int64_t>(mtiles, std::max<int64_t>(1, n_sm / std::max(1, a.D)));
+    tc_project_kernel<ANCH, NT><<<dim3((unsigned)gx, (unsigned)a.D), kProjThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
