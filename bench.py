@@ -287,15 +287,22 @@ def alu_roofline(kernel, lane_ops, kernel_ms, peak_lane, n_sm, sm_max, timing, o
                     f"{sm_max:.0f} MHz (derived from unit counts and the measured max clock)"}
 
 
-def tc_roofline(updates_per_step, tc_ms, peaks):
+def tc_roofline(updates_per_step, tc_ms, peaks, segments=0):
     """Tensor-core projection: 3 split-BF16 products of the (2 rows per
     filter) x (2 x 256 window) weights against one window per 256-sample
-    chunk, i.e. 24 algorithmic flops per filter-update."""
+    chunk, i.e. 24 algorithmic flops per filter-update it covers.  The
+    start states of P time segments need the chunks before the last
+    segment's start only, (P - 1) / P of the call (segments = P); the
+    chunked tensor-core form covers every chunk (segments = 0)."""
     tc_peak = peaks.get("bf16_tflops") or 1800.0
-    ach = 24.0 * updates_per_step / (tc_ms / 1e3) / 1e12
+    cover = (segments - 1) / segments if segments > 1 else 1.0
+    ach = 24.0 * updates_per_step * cover / (tc_ms / 1e3) / 1e12
     return {"bound": "tensor", "kernel": "tc_project_kernel", "achieved": ach, "peak": tc_peak,
             "unit": "TFLOP/s", "frac": ach / tc_peak, "traffic": None, "ms_per_step": tc_ms,
-            "note": "24 algorithmic BF16 flops per filter-update / its own CUDA-event time; "
+            "note": "24 algorithmic BF16 flops per filter-update covered "
+                    + (f"((P - 1) / P = {cover:.3f} of the call's updates: the chunks before the "
+                       f"last of {segments} segments)" if segments > 1 else "(every chunk)")
+                    + " / its own CUDA-event time; "
                     + ("peak = measured cuBLAS bf16 burst" if peaks.get("bf16_tflops")
                        else "peak = fallback 1.8 PFLOP/s bf16")}
 
@@ -431,7 +438,8 @@ def sub_plain(sp, dev, stream, peak_lane, n_sm, sm_max):
                 f"{k_ms / 20:.4f} ms of K1 per call (CUDA events around its launches, 20 calls)",
                 "8 algorithmic lane-ops per filter-update")
             if tc_n:
-                res["roofline_projection"] = tc_roofline(upd, tc_ms / 20, measured_peaks())
+                res["roofline_projection"] = tc_roofline(upd, tc_ms / 20, measured_peaks(),
+                                                         segments=segs)
             out[name] = res
             plan.close()
     out["clocks"] = clk.summary()
@@ -529,7 +537,8 @@ def sub_multirate(sp, dev, stream, peak_lane, n_sm, sm_max, steps=5, warmup=2):
            "clocks": clk.summary(), "cpu_baseline": base,
            "l2": "strain (4 MB) L2-resident as in streaming use; no z stored"}
     if tc_n:
-        out["roofline_projection"] = tc_roofline(upd, tc_ms / steps, measured_peaks())
+        out["roofline_projection"] = tc_roofline(upd, tc_ms / steps, measured_peaks(),
+                                                 segments=info["last_call_segments"])
     plan.close()
     return out
 
@@ -976,7 +985,9 @@ def run_ours(args, rank, world, local_rank):
     }
     tc_ms, tc_n = ktimes["projection"]
     if tc_n > 0:
-        line["roofline_projection"] = tc_roofline(upd, tc_ms / args.steps, peaks)
+        line["roofline_projection"] = tc_roofline(
+            upd, tc_ms / args.steps, peaks,
+            segments=0 if args.precision == "chunked_tc" else info["last_call_segments"])
         line["roofline_projection"]["launches_per_step"] = tc_n / args.steps
     line.update(extra)
     if e2e:

@@ -53,7 +53,9 @@ constexpr int kKBlk = 64;                       // K per staged block
 constexpr int kKBlocks = kTcK / kKBlk;          // 8
 constexpr uint32_t kTileBytes = 128u * kKBlk * 2u;   // 16 KB: 128 rows x 64 BF16 (A)
 constexpr uint32_t kBTileBytes = (uint32_t)kColsTile * kKBlk * 2u;   // B: 256 rows x 64
-constexpr int kStages = 2;
+// pipeline stages of (A, B) tiles: 192 KB of shared memory either way
+template <int NT> __host__ __device__ constexpr int stages_for() { return NT == 128 ? 3 : 2; }
+constexpr int kMaxStages = 3;
 constexpr int kEpiThreads = 128;
 
 // byte offset of element (row, k) inside a 128 x 64 tile
@@ -374,8 +376,9 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
     constexpr uint32_t kBT = (uint32_t)NT * kKBlk * 2u;          // one B component
     constexpr uint32_t kSB = 2u * kTileBytes + 2u * kBT;          // stage bytes
     constexpr uint32_t kIdesc = idesc_for<NT>();
+    constexpr int kStages = stages_for<NT>();
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[3 * kStages + 4];
+    __shared__ __align__(8) uint64_t bars[3 * kMaxStages + 4];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int det = blockIdx.y;
@@ -474,9 +477,10 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
                     bulk_g2s(dst + 2 * kTileBytes + kBT, src + kBTileBytes + off, kBT, full);
                 }
             };
-            // block it+1 is copied while the MMAs of block it run; a stage is
-            // refilled once the MMAs that read it (block it-1) have finished
-            if (total > 0) fill(0);
+            // blocks it+1 .. it+kStages-1 are copied while the MMAs of block it
+            // run; a stage is refilled once the MMAs that read it (block it-1)
+            // have finished
+            for (int f = 0; f < kStages - 1 && f < total; ++f) fill(f);
             for (int it = 0; it < total && ok; ++it) {
                 const int st = it % kStages;
                 const int u = it / kKBlocks, kb = it % kKBlocks;   // accumulator tile, K-block
@@ -501,8 +505,8 @@ __global__ void __launch_bounds__(kProjThreads, 1) tc_project_kernel(const TcArg
                 }
                 umma_commit(empty0 + 8 * st);          // stage free once these MMAs finish
                 if (kb == kKBlocks - 1) umma_commit(acc_full0 + 8 * (u & 1));
-                if (it + 1 < total) {
-                    const int nx = it + 1, sx = nx % kStages;
+                if (it + kStages - 1 < total) {
+                    const int nx = it + kStages - 1, sx = nx % kStages;
                     if (nx >= kStages)
                         ok = mbar_wait(empty0 + 8 * sx, (uint32_t)((nx / kStages - 1) & 1),
                                        A.wait_limit_ns);
@@ -740,7 +744,7 @@ cudaError_t launch_tc_strain(const float *xe, int64_t xe_stride, int Dh, int64_t
 
 template <bool ANCH, int NT> cudaError_t launch_project_nt(TcArgs a, int64_t mtiles, cudaStream_t s)
 {
-    constexpr int smem = kStages * (int)(2u * kTileBytes + 2u * (uint32_t)NT * kKBlk * 2u);
+    constexpr int smem = stages_for<NT>() * (int)(2u * kTileBytes + 2u * (uint32_t)NT * kKBlk * 2u);
     const void *k = reinterpret_cast<const void *>(tc_project_kernel<ANCH, NT>);
     cudaError_t e = ensure_smem_limit(k, smem);
     if (e != cudaSuccess) return e;
