@@ -866,21 +866,38 @@ spiir_status launch_anchored(spiir_plan *p, Band &b, spiir::K1Args a, cudaStream
                                    ? (int64_t)p->opt.tile_chunks
                                    : std::max<int64_t>(1, budget / (8 * per));
     const int64_t hq = L.Dh / spiir::kTcT;
-    int64_t n_tile = std::max<int64_t>(unit, max_chunks * spiir::kTcT / unit * unit);
-    n_tile = std::min<int64_t>(n_tile, (n + unit - 1) / unit * unit);
+    const int64_t budget_tile = std::max<int64_t>(unit, max_chunks * spiir::kTcT / unit * unit);
+    int64_t n_tile = std::min<int64_t>(budget_tile, (n + unit - 1) / unit * unit);
     if (p->opt.tile_chunks <= 0) {
-        // a tile's windows (chunks + hq) fill whole column tiles of the GEMM:
-        // at most the budget's whole column tiles, the call split evenly over
-        // as few tiles as that allows (a tile 4 windows past 512 would take a
-        // third, almost empty, column tile)
+        // a tile's windows (chunks + hq) fill k whole column tiles of the
+        // GEMM: k within the budget, chosen for the fewest column tiles over
+        // the call, each time tile counted half a column tile more (its
+        // launches), ties to the larger k; then the call split evenly over
+        // that many time tiles (a tile 4 windows past 512 would take a third,
+        // almost empty, column tile)
         const int64_t u = unit / spiir::kTcT;   // chunks per whole unit
         const int64_t cols = spiir::tc_cols_per_tile();
-        const int64_t cap = (n_tile / spiir::kTcT + hq) / cols * cols - hq;
         const int64_t n_chunks = (n + spiir::kTcT - 1) / spiir::kTcT;
-        if (cap >= u && n_chunks > cap) {
-            const int64_t n_tiles = (n_chunks + cap - 1) / cap;
-            const int64_t per_tile = ((n_chunks + n_tiles - 1) / n_tiles + u - 1) / u * u;
-            n_tile = std::min<int64_t>(n_tile, per_tile * spiir::kTcT);
+        const int64_t k_max = std::min<int64_t>((budget_tile / spiir::kTcT + hq) / cols,
+                                                (n_chunks + hq + cols - 1) / cols);
+        int64_t best_k = 0, best_tiles = 0;
+        double best_cost = 0.0;
+        for (int64_t k = 1; k <= k_max; ++k) {
+            const int64_t cap = (k * cols - hq) / u * u;
+            if (cap < u) continue;
+            const int64_t tl = (n_chunks + cap - 1) / cap;
+            const double cost = (double)tl * ((double)k + 0.5);
+            if (best_k == 0 || cost <= best_cost) {
+                best_k = k;
+                best_tiles = tl;
+                best_cost = cost;
+            }
+        }
+        if (best_k > 0) {
+            const int64_t cap = (best_k * cols - hq) / u * u;
+            const int64_t per_tile =
+                std::min<int64_t>(cap, ((n_chunks + best_tiles - 1) / best_tiles + u - 1) / u * u);
+            n_tile = std::max<int64_t>(unit, std::min<int64_t>(n_tile, per_tile * spiir::kTcT));
         }
     }
     const int64_t chunks = n_tile / spiir::kTcT;
