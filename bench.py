@@ -64,7 +64,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="batched",
                     choices=["batched", "plain", "multirate", "adjoint", "precision", "design",
-                             "veto", "adjoint-forms"])
+                             "veto", "adjoint-forms", "ceiling"])
     ap.add_argument("--precision", default="plain",
                     choices=["plain", "compensated", "chunked_fp64", "chunked_tc"])
     ap.add_argument("--no-graph", action="store_true",
@@ -1189,8 +1189,66 @@ def run_veto(args):
     return 0
 
 
+def run_ceiling(args):
+    """The filter step's FP32 rate in isolation (paper_1602_05573_b300/probe:
+    the recurrence and the cross-lane sum on register-resident coefficients
+    and a conflict-free shared window; no ring, barriers, combine or z
+    stores), for the (filters per lane, lanes per template) cases of the
+    batched bank's layout and for 64 slots per template over 32, 16 and 8
+    lanes; beside the stand-in without the cross-lane sum.  Read against
+    the filter kernel's own rate (per slot-update: the headline's useful
+    fraction times slots / filters)."""
+    import ctypes
+    import torch
+    here = os.path.dirname(os.path.abspath(__file__))
+    path = os.path.join(here, "paper_1602_05573_b300", "_lib", "libspiir_probe.so")
+    if not os.path.exists(path):
+        raise RuntimeError("the probe library is missing: run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    lib.spiir_probe_step.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]
+    lib.spiir_probe_step.restype = ctypes.c_int
+    torch.cuda.init()
+    dev = torch.device("cuda", 0)
+
+    def probe(F, G, ctas=4):
+        ms, fr = ctypes.c_double(), ctypes.c_double()
+        rc = lib.spiir_probe_step(F, G, ctas, max(1000, 40000 // F), ctypes.byref(ms), ctypes.byref(fr))
+        if rc != 0:
+            raise RuntimeError(f"spiir_probe_step({F}, {G}, {ctas}) returned {rc}")
+        return fr.value
+    # the batched bank's layout: templates of up to 16 x 10 filters in half
+    # warps (ceil(n / 16) per lane), larger ones in whole warps (ceil(n / 32))
+    bank = workload_bank("batched")
+    counts = np.diff(np.asarray(bank.off))
+    slots = {}
+    for c in counts:
+        G = 16 if c <= 160 else 32
+        F = -(-int(c) // G)
+        slots[(F, G)] = slots.get((F, G), 0) + F * G
+    with ClockSampler(dev.index) as clk:
+        cases = {}
+        for (F, G) in sorted(slots):
+            cases[f"F{F}/G{G}"] = {"with_sum": probe(F, G), "without_sum": probe(F, 0),
+                                   "slot_share": slots[(F, G)] / sum(slots.values())}
+        mean = sum(v["with_sum"] * v["slot_share"] for v in cases.values())
+        slots64 = {f"F{F}/G{G}": probe(F, G) for F, G in ((2, 32), (4, 16), (8, 8))}
+    line = {"metric": "FP32 fraction of the filter step in isolation",
+            "value": mean, "unit": "of 128 FP32 lanes x SMs x clock",
+            "workload": "probe: 16 warps per SM, 8 lane-ops per filter-update, "
+                        "cross-lane sum over G lanes every 8 samples",
+            "batched_layout": cases,
+            "batched_slot_weighted": mean,
+            "slots64_top_band_shapes": slots64,
+            "clocks": clk.summary()}
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "ceiling" and args.impl != "reference":
+        return run_ceiling(args) if int(os.environ.get("RANK", 0)) == 0 else 0
     if args.workload == "design" and args.impl != "reference":
         return run_design(args) if int(os.environ.get("RANK", 0)) == 0 else 0
     if args.workload == "veto" and args.impl != "reference":

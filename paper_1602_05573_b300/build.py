@@ -3,7 +3,9 @@
     python paper_1602_05573_b300/build.py [--force] [-v]
 
 Produces paper_1602_05573_b300/_lib/libspiir.so from csrc/*.cu and
-csrc/*.cpp (static CUDA runtime, position-independent, -lineinfo).
+csrc/*.cpp (static CUDA runtime, position-independent, -lineinfo), and
+_lib/libspiir_probe.so from probe/step_ceiling.cu (a measurement probe,
+not part of the filter path).
 """
 from __future__ import annotations
 
@@ -72,5 +74,27 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+PROBE_SRC = os.path.join(HERE, "probe", "step_ceiling.cu")
+PROBE_LIB = os.path.join(LIB_DIR, "libspiir_probe.so")
+
+
+def build_probe(force: bool = False) -> str:
+    """The measurement probe (the filter step's FP32 rate in isolation),
+    a library of its own: bench.py --workload ceiling loads it."""
+    if not force and os.path.exists(PROBE_LIB) and \
+            os.path.getmtime(PROBE_LIB) >= max(os.path.getmtime(PROBE_SRC), os.path.getmtime(__file__)):
+        return PROBE_LIB
+    os.makedirs(LIB_DIR, exist_ok=True)
+    tmp = PROBE_LIB + f".{os.getpid()}.tmp"
+    cmd = [NVCC, *ARCH, "-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
+           "-cudart", "static", PROBE_SRC, "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PROBE_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
+
+
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))
+    print(build_probe(force="--force" in sys.argv))
