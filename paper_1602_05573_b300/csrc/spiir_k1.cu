@@ -156,6 +156,16 @@ __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb,
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncwarp();
     }
+    // z store and running peak of sample i (|z|^2 = re*re + im*im, no
+    // contraction: reproducible on the host)
+    auto store_peak = [&](float2 acc, int i) {
+        if (zrow != nullptr) reinterpret_cast<float2 *>(zrow)[k0 + i] = acc;
+        const float p = __fadd_rn(__fmul_rn(acc.x, acc.x), __fmul_rn(acc.y, acc.y));
+        if (p > best) {
+            best = p;
+            bidx = k0 + i;
+        }
+    };
     // One or two lower bands whose decimation factors divide 32 (and so the
     // block start k0): lane i always takes samples i mod 32 of the block, so
     // each band's interpolation weight is fixed per lane and its band sample
@@ -178,8 +188,8 @@ __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb,
             const float f1 = (float)(lane & (l1.R - 1)) / (float)l1.R;
             const float g0 = 1.0f - f0, g1 = 1.0f - f1;
             const float2 *b0 = low + l0.buf_off, *b1 = low + l1.buf_off;
-            int q0 = r0, q1 = r1;
-            for (int i = lane; i < nv; i += 32, q0 += st0, q1 += st1) {
+            // the acc of sample i (band samples q0, q1 of this lane)
+            auto acc_at = [&](int i, int q0, int q1) {
                 float2 acc = zb[(int64_t)first * A.Tb + i];
                 for (int w = 1; w < nw; ++w) {
                     const float2 o = zb[(int64_t)(first + w) * A.Tb + i];
@@ -196,13 +206,19 @@ __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb,
                     acc.x += fmaf(f1, v.x, g1 * u.x);
                     acc.y += fmaf(f1, v.y, g1 * u.y);
                 }
-                if (zrow != nullptr) reinterpret_cast<float2 *>(zrow)[k0 + i] = acc;
-                const float p = __fadd_rn(__fmul_rn(acc.x, acc.x), __fmul_rn(acc.y, acc.y));
-                if (p > best) {
-                    best = p;
-                    bidx = k0 + i;
-                }
+                return acc;
+            };
+            // four samples' loads before their stores and peak updates (in
+            // sample order, so the first index still wins ties)
+            int i = lane, q0 = r0, q1 = r1;
+            for (; i + 96 < nv; i += 128, q0 += 4 * st0, q1 += 4 * st1) {
+                float2 acc[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] = acc_at(i + 32 * u, q0 + u * st0, q1 + u * st1);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) store_peak(acc[u], i + 32 * u);
             }
+            for (; i < nv; i += 32, q0 += st0, q1 += st1) store_peak(acc_at(i, q0, q1), i);
             return;
         }
     }
@@ -225,13 +241,7 @@ __device__ __forceinline__ void combine_block(const K1Args &A, const float2 *zb,
             acc.x += fmaf(f, v.x, (1.0f - f) * u.x);
             acc.y += fmaf(f, v.y, (1.0f - f) * u.y);
         }
-        if (zrow != nullptr) reinterpret_cast<float2 *>(zrow)[k0 + i] = acc;
-        // |z|^2 = re*re + im*im, no contraction (reproducible on the host)
-        const float p = __fadd_rn(__fmul_rn(acc.x, acc.x), __fmul_rn(acc.y, acc.y));
-        if (p > best) {
-            best = p;
-            bidx = k0 + i;
-        }
+        store_peak(acc, i);
     }
 }
 
