@@ -42,7 +42,7 @@ from spiir_inputs import WORKLOADS, updates, workload_bank, workload_strain  # n
 # capture of the current kernel applies.  See profiles/.
 TRAFFIC = {
     ("batched", "plain"): (
-        6.640e9, "k1_plain: 415.0 MB per launch captured on the same bank at 4096 samples "
+        6.592e9, "k1_plain: 412.0 MB per launch captured on the same bank at 4096 samples "
                  "(profiles/k1_plain_batched_medium.md), scaled by samples to 65536 "
                  "(z writes dominate and grow in proportion); algorithmic bytes 6.44e9"),
 }
