@@ -1217,13 +1217,16 @@ def run_ceiling(args):
         if rc != 0:
             raise RuntimeError(f"spiir_probe_step({F}, {G}, {ctas}) returned {rc}")
         return fr.value
-    # the batched bank's layout: templates of up to 16 x 10 filters in half
-    # warps (ceil(n / 16) per lane), larger ones in whole warps (ceil(n / 32))
+    # the batched bank's layout as the library builds it: its lanes per
+    # template G (whole warps for this bank), ceil(n / G) filters per lane
+    import paper_1602_05573_b300 as sp
     bank = workload_bank("batched")
+    plan = sp.Plan(bank, device=dev.index)
+    G = int(plan.info()["lanes_per_template"])
+    plan.close()
     counts = np.diff(np.asarray(bank.off))
     slots = {}
     for c in counts:
-        G = 16 if c <= 160 else 32
         F = -(-int(c) // G)
         slots[(F, G)] = slots.get((F, G), 0) + F * G
     with ClockSampler(dev.index) as clk:

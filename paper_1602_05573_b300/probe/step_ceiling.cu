@@ -12,7 +12,7 @@
 // filter kernel's own rate is read.
 //
 // extern "C" spiir_probe_step(F, G, ctas_per_sm, iters, &ms, &frac):
-// F in {2, 4, 6, 7, 8, 9, 10}, G in {0, 16, 32} (and G = 8 with F = 8),
+// F in 2..10, G in {0, 16, 32} (and G = 8 with F = 8),
 // ctas_per_sm in {4, 6} (128 threads each: 16 or 24 warps per SM), iters >= 1
 // batches per thread.  Returns 0,
 // or -1 for an unsupported combination, or the CUDA error code.  ms is the
@@ -245,7 +245,9 @@ extern "C" int spiir_probe_step(int F, int G, int ctas_per_sm, int iters, double
     if (G == 8) return F == 8 ? run_b<8, 8>(ctas_per_sm, iters, ms, frac) : -1;
     switch (F) {
     case 2: return run_f<2>(G, ctas_per_sm, iters, ms, frac);
+    case 3: return run_f<3>(G, ctas_per_sm, iters, ms, frac);
     case 4: return run_f<4>(G, ctas_per_sm, iters, ms, frac);
+    case 5: return run_f<5>(G, ctas_per_sm, iters, ms, frac);
     case 6: return run_f<6>(G, ctas_per_sm, iters, ms, frac);
     case 7: return run_f<7>(G, ctas_per_sm, iters, ms, frac);
     case 8: return run_f<8>(G, ctas_per_sm, iters, ms, frac);
