@@ -33,6 +33,25 @@ def test_every_declared_function_is_exported():
     assert set(names) <= set(sp.SYMBOLS) | set(names)
 
 
+def test_probe_library_loads_and_exports_its_entry():
+    """The measurement probe (bench.py --workload ceiling) is a library of its
+    own, outside the filter ABI: it builds, loads without a GPU and exports
+    spiir_probe_step (argument checks only; no kernel runs here)."""
+    import importlib.util
+    spec = importlib.util.spec_from_file_location(
+        "_spiir_build", os.path.join(ROOT, "paper_1602_05573_b300", "build.py"))
+    b = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(b)
+    lib = ctypes.CDLL(b.build_probe())
+    f = lib.spiir_probe_step
+    f.restype = ctypes.c_int
+    ms, fr = ctypes.c_double(), ctypes.c_double()
+    # unsupported combinations are refused before any CUDA call
+    assert f(11, 32, 4, 10, ctypes.byref(ms), ctypes.byref(fr)) == -1
+    assert f(7, 8, 4, 10, ctypes.byref(ms), ctypes.byref(fr)) == -1
+    assert f(7, 32, 4, 0, ctypes.byref(ms), ctypes.byref(fr)) == -1
+
+
 def test_status_strings():
     lib = sp.library()
     for st in range(6):
