@@ -599,6 +599,61 @@ spiir_status spiir_plan_create(const spiir_bank_desc *bank, const spiir_options 
                                     &L2, &err))
                 p->bands[j].lay = std::move(L2);
         }
+        // block length for residency: when a multirate top band's filter
+        // kernel (two ring copies and the lower-band buffers) keeps fewer CTAs
+        // on an SM by its shared memory at 512-sample blocks than its registers
+        // allow (3 of 4), the longest shorter block (a multiple of 64) that lets
+        // them all reside.  Measured on the multirate bank: 92.6 -> 89.7 ms per
+        // step at 448 samples.  (Single-rate banks keep their blocks: the
+        // autotuner chooses theirs, and the tangent adjoint wants a history of
+        // whole 256-sample chunks.)
+        bool top_mr = false;   // the multirate top band (the first at the top rate)
+        if (decims.size() > 1 && decims[j] == 1) {
+            top_mr = true;
+            for (size_t i = 0; i < j; ++i) top_mr = top_mr && decims[i] != 1;
+        }
+        if (top_mr && opt.block_len == 0 && opt.precision == SPIIR_PREC_PLAIN &&
+            opt.device >= 0 && p->bands[j].lay.Tb == 512) {
+            // dynamic shared memory of a launch (the call's k1_smem)
+            auto k1_bytes = [&](const spiir::Layout &L) {
+                int low = 0;
+                if (top_mr) {
+                    for (size_t i = 0; i < decims.size(); ++i)
+                        if (i != j) low += (L.Tb + decims[i] - 1) / decims[i] + 2;
+                    low = (low + 1) / 2 * 2;
+                }
+                return L.smem_bytes() + L.W * (32 / L.G) * low * (int)sizeof(float2);
+            };
+            DeviceGuard g(opt.device);
+            int smem_sm = 0, reserved = 0;
+            const int regs = g.ok ? spiir::k1_plain_regs(p->bands[j].lay.Fcap) : 0;
+            if (g.ok && regs > 0 &&
+                cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                       opt.device) == cudaSuccess &&
+                cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock,
+                                       opt.device) == cudaSuccess) {
+                const int threads = p->bands[j].lay.W * 32;
+                const int by_regs = std::min({32, 2048 / threads, 65536 / (threads * regs)});
+                auto by_smem = [&](const spiir::Layout &L) {
+                    return smem_sm / (k1_bytes(L) + reserved);
+                };
+                if (by_smem(p->bands[j].lay) < by_regs) {
+                    for (int tb : {448, 384, 320, 256}) {
+                        spiir::LayoutOptions lo2 = lo;
+                        lo2.Tb = tb;
+                        spiir::Layout L2;
+                        if (spiir::build_layout(lists, p->D, bank->a_reim, bank->b_reim,
+                                                bank->delay, lo2, &L2, &err) &&
+                            by_smem(L2) >= by_regs) {
+                            p->bands[j].lay = std::move(L2);
+                            break;
+                        }
+                    }
+                }
+            } else {
+                (void)cudaGetLastError();
+            }
+        }
     }
     if (p->bands.size() > 1 + spiir::kMaxLowerBands) {
         delete p;
